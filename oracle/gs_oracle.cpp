@@ -1,0 +1,517 @@
+// FP64 CPU oracle for the tile-based Gaussian splatting hot path (projection,
+// duplication + sort, alpha blending, blend gradients).
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the plain, slow definition the CUDA
+// library is checked against.  It shares no code, header or constant with the
+// CUDA path, and only the test suite, the smoke check and the CPU-baseline leg
+// of the benchmark may load it.  Every routine follows the paper's
+// definitions directly (cited per function) and evaluates the splat exponent
+// as the plain quadratic of Eq. 3, never via the dot-product form of Eq. 6
+// (that identity has a routine of its own, oracle_power_eq6, used to pin it).
+//
+// Readings of passages the paper leaves open (each also listed in the design doc):
+//  * conic: Sigma^-1 = [[A, B], [B, C]] is the inverse 2D covariance (Alg. 1);
+//  * pixel (px, py) is evaluated at its centre (px + 0.5, py + 0.5);
+//  * alpha = min(0.99, o * exp(min(power, 0))); a splat is skipped when
+//    alpha < 1/255; compositing stops, without adding the splat, at the first
+//    one whose test transmittance T * (1 - alpha) falls below 1e-4 (Eq. 1 with
+//    the alpha-skip and early-termination rules of Alg. 1);
+//  * n_contrib = 1 + list position of the last splat added, 0 if none;
+//  * tile membership: the 3-sigma square of radius r = ceil(3 sqrt(lambda_max))
+//    around the projected mean; tiles [floor((m - r)/16), floor((m + r)/16)]
+//    per axis, clamped to the image (Sec. 2.1 "intersection detection");
+//  * the 2D covariance gets +lowpass (0.3) on its diagonal before inversion;
+//  * colour from real spherical harmonics up to degree 3, view direction from
+//    the camera centre to the mean, rgb = max(0, sum + 0.5).
+// Parity status per function: every exported routine is pinned by the CPU
+// tests (closed forms, invariants, brute force, library special cases);
+// oracle_blend_grad is pinned by central finite differences of oracle_blend.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+namespace {
+
+constexpr int kTile = 16;
+
+// Camera layout shared with the Python wrapper: 22 doubles
+// [W, H, fx, fy, cx, cy, R00..R22 (row-major), t0, t1, t2, znear, lowpass, pad]
+struct Cam {
+    int W, H;
+    double fx, fy, cx, cy;
+    double R[3][3];
+    double t[3];
+    double znear, lowpass;
+};
+
+Cam read_cam(const double* c) {
+    Cam k;
+    k.W = (int)c[0];
+    k.H = (int)c[1];
+    k.fx = c[2]; k.fy = c[3]; k.cx = c[4]; k.cy = c[5];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) k.R[i][j] = c[6 + 3 * i + j];
+    k.t[0] = c[15]; k.t[1] = c[16]; k.t[2] = c[17];
+    k.znear = c[18];
+    k.lowpass = c[19];
+    return k;
+}
+
+int tiles_x(int W) { return (W + kTile - 1) / kTile; }
+int tiles_y(int H) { return (H + kTile - 1) / kTile; }
+
+// Tile rectangle of a splat: tiles whose [16t, 16t+16) span meets
+// [m - r, m + r] on each axis, clamped to the grid.  Returns false if empty.
+bool tile_rect(double mx, double my, int r, int W, int H, int rect[4]) {
+    if (r <= 0) return false;
+    long x0 = (long)std::floor((mx - r) / kTile);
+    long x1 = (long)std::floor((mx + r) / kTile);
+    long y0 = (long)std::floor((my - r) / kTile);
+    long y1 = (long)std::floor((my + r) / kTile);
+    x0 = std::max(x0, 0L); y0 = std::max(y0, 0L);
+    x1 = std::min(x1, (long)tiles_x(W) - 1);
+    y1 = std::min(y1, (long)tiles_y(H) - 1);
+    if (x0 > x1 || y0 > y1) return false;
+    rect[0] = (int)x0; rect[1] = (int)x1; rect[2] = (int)y0; rect[3] = (int)y1;
+    return true;
+}
+
+// Real spherical harmonics up to degree 3 at unit direction (x, y, z); the
+// normalisations are written as closed forms.  Order within degree l is
+// m = -l..l, and the basis is sqrt(2) Re/Im of the complex harmonics with
+// the Condon-Shortley phase (the convention 3DGS uses).
+void sh_basis(double x, double y, double z, double out[16]) {
+    const double pi = 3.14159265358979323846;
+    const double n0 = 0.5 / std::sqrt(pi);
+    const double n1 = std::sqrt(3.0 / (4.0 * pi));
+    const double n2a = 0.5 * std::sqrt(15.0 / pi);
+    const double n2b = 0.25 * std::sqrt(5.0 / pi);
+    const double n2c = 0.25 * std::sqrt(15.0 / pi);
+    const double n3a = 0.25 * std::sqrt(35.0 / (2.0 * pi));
+    const double n3b = 0.5 * std::sqrt(105.0 / pi);
+    const double n3c = 0.25 * std::sqrt(21.0 / (2.0 * pi));
+    const double n3d = 0.25 * std::sqrt(7.0 / pi);
+    const double n3e = 0.25 * std::sqrt(105.0 / pi);
+    out[0] = n0;
+    out[1] = -n1 * y;
+    out[2] = n1 * z;
+    out[3] = -n1 * x;
+    out[4] = n2a * x * y;
+    out[5] = -n2a * y * z;
+    out[6] = n2b * (2 * z * z - x * x - y * y);
+    out[7] = -n2a * x * z;
+    out[8] = n2c * (x * x - y * y);
+    out[9] = -n3a * y * (3 * x * x - y * y);
+    out[10] = n3b * x * y * z;
+    out[11] = -n3c * y * (4 * z * z - x * x - y * y);
+    out[12] = n3d * z * (2 * z * z - 3 * x * x - 3 * y * y);
+    out[13] = -n3c * x * (4 * z * z - x * x - y * y);
+    out[14] = n3e * z * (x * x - y * y);
+    out[15] = -n3a * x * (x * x - 3 * y * y);
+}
+
+struct Splat {
+    double mx, my, A, B, C, o, c[3];
+};
+
+// Exponent of Eq. 3 for the splat at pixel centre (xp, yp):
+// power = -1/2 A dx^2 - B dx dy - 1/2 C dy^2, dx = x_g - x_p, dy = y_g - y_p.
+inline double power_eq3(const Splat& s, double xp, double yp) {
+    double dx = s.mx - xp, dy = s.my - yp;
+    return -0.5 * s.A * dx * dx - s.B * dx * dy - 0.5 * s.C * dy * dy;
+}
+
+struct PixelResult {
+    double C[3];
+    double T;
+    int n_contrib;
+    bool ambiguous;
+};
+
+// Front-to-back compositing of one pixel over an ordered splat list (Eq. 1 with
+// Alg. 1's alpha-skip and early termination, readings in the header).
+// Decisions that lie within a relative margin of their threshold mark the
+// pixel ambiguous: a lower-precision path may legitimately decide otherwise.
+PixelResult composite_pixel(const std::vector<Splat>& list, double xp, double yp,
+                            const double bg[3], double alpha_margin, double t_margin) {
+    PixelResult r{{0, 0, 0}, 1.0, 0, false};
+    double T = 1.0;
+    for (size_t i = 0; i < list.size(); ++i) {
+        const Splat& s = list[i];
+        double power = std::min(power_eq3(s, xp, yp), 0.0);
+        double raw = s.o * std::exp(power);
+        if (std::fabs(raw - 0.99) <= alpha_margin * 0.99) r.ambiguous = true;
+        double alpha = std::min(0.99, raw);
+        if (std::fabs(alpha - 1.0 / 255.0) <= alpha_margin / 255.0) r.ambiguous = true;
+        if (alpha < 1.0 / 255.0) continue;
+        double testT = T * (1.0 - alpha);
+        if (std::fabs(testT - 1e-4) <= t_margin * 1e-4) r.ambiguous = true;
+        if (testT < 1e-4) break;
+        for (int ch = 0; ch < 3; ++ch) r.C[ch] += s.c[ch] * alpha * T;
+        T = testT;
+        r.n_contrib = (int)i + 1;
+    }
+    for (int ch = 0; ch < 3; ++ch) r.C[ch] += T * bg[ch];
+    r.T = T;
+    return r;
+}
+
+Splat load_splat(uint32_t g, const double* mean2d, const double* conic,
+                 const double* opac, const double* rgb) {
+    Splat s;
+    s.mx = mean2d[2 * (size_t)g];
+    s.my = mean2d[2 * (size_t)g + 1];
+    s.A = conic[3 * (size_t)g];
+    s.B = conic[3 * (size_t)g + 1];
+    s.C = conic[3 * (size_t)g + 2];
+    s.o = opac[g];
+    for (int ch = 0; ch < 3; ++ch) s.c[ch] = rgb[3 * (size_t)g + ch];
+    return s;
+}
+
+template <class F>
+void parallel_for(int n, int n_threads, F f) {
+    if (n_threads <= 1 || n < 2) {
+        for (int i = 0; i < n; ++i) f(i);
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (int k = 0; k < n_threads; ++k)
+        pool.emplace_back([=, &f]() {
+            for (int i = k; i < n; i += n_threads) f(i);
+        });
+    for (auto& th : pool) th.join();
+}
+
+}  // namespace
+
+extern "C" {
+
+int oracle_abi_version() { return 1; }
+
+// Preprocessing of Sec. 2.1 (stage 1): EWA projection of each 3D Gaussian.
+// Outputs per Gaussian g: mean2d (2), cov2d (3: a, b, c with lowpass added),
+// conic (3: A, B, C), depth, radius (0 = culled), rgb (3), rect (4: x0, x1, y0,
+// y1 tiles inclusive, -1 if none) and tiles_touched.
+void oracle_project(int n, const float* means, const float* scales, const float* quats,
+                    const float* sh, int sh_degree, const double* cam_in,
+                    double* mean2d, double* cov2d, double* conic, double* depth,
+                    int32_t* radius, double* rgb, int32_t* rect, int64_t* tiles_touched) {
+    const Cam cam = read_cam(cam_in);
+    const int K = (sh_degree + 1) * (sh_degree + 1);
+    // camera centre in world space: -R^T t
+    double cpos[3];
+    for (int j = 0; j < 3; ++j)
+        cpos[j] = -(cam.R[0][j] * cam.t[0] + cam.R[1][j] * cam.t[1] + cam.R[2][j] * cam.t[2]);
+    for (int g = 0; g < n; ++g) {
+        radius[g] = 0;
+        tiles_touched[g] = 0;
+        for (int k = 0; k < 4; ++k) rect[4 * g + k] = -1;
+        for (int k = 0; k < 2; ++k) mean2d[2 * g + k] = 0;
+        for (int k = 0; k < 3; ++k) { cov2d[3 * g + k] = 0; conic[3 * g + k] = 0; rgb[3 * g + k] = 0; }
+        depth[g] = 0;
+
+        double mw[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
+        double p[3];
+        for (int i = 0; i < 3; ++i)
+            p[i] = cam.R[i][0] * mw[0] + cam.R[i][1] * mw[1] + cam.R[i][2] * mw[2] + cam.t[i];
+        depth[g] = p[2];
+        if (!(p[2] > cam.znear)) continue;
+
+        // rotation of the unit quaternion (w, x, y, z)
+        double qw = quats[4 * g], qx = quats[4 * g + 1], qy = quats[4 * g + 2], qz = quats[4 * g + 3];
+        double qn = std::sqrt(qw * qw + qx * qx + qy * qy + qz * qz);
+        if (!(qn > 0)) continue;
+        qw /= qn; qx /= qn; qy /= qn; qz /= qn;
+        double Rq[3][3] = {
+            {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
+            {2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)},
+            {2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)}};
+        double s[3] = {scales[3 * g], scales[3 * g + 1], scales[3 * g + 2]};
+        // Sigma3 = (Rq S)(Rq S)^T
+        double M[3][3], S3[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) M[i][j] = Rq[i][j] * s[j];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double acc = 0;
+                for (int k = 0; k < 3; ++k) acc += M[i][k] * M[j][k];
+                S3[i][j] = acc;
+            }
+        // Jacobian of the perspective projection at p, times the camera rotation
+        double J[2][3] = {{cam.fx / p[2], 0, -cam.fx * p[0] / (p[2] * p[2])},
+                          {0, cam.fy / p[2], -cam.fy * p[1] / (p[2] * p[2])}};
+        double Tm[2][3];
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 3; ++j)
+                Tm[i][j] = J[i][0] * cam.R[0][j] + J[i][1] * cam.R[1][j] + J[i][2] * cam.R[2][j];
+        double S2[2][2];
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) {
+                double acc = 0;
+                for (int k = 0; k < 3; ++k)
+                    for (int l = 0; l < 3; ++l) acc += Tm[i][k] * S3[k][l] * Tm[j][l];
+                S2[i][j] = acc;
+            }
+        double a = S2[0][0] + cam.lowpass, b = S2[0][1], c = S2[1][1] + cam.lowpass;
+        cov2d[3 * g] = a; cov2d[3 * g + 1] = b; cov2d[3 * g + 2] = c;
+        double det = a * c - b * b;
+        if (!(det > 0)) continue;
+        double mx = cam.fx * p[0] / p[2] + cam.cx;
+        double my = cam.fy * p[1] / p[2] + cam.cy;
+        if (!(std::fabs(mx) <= 8388608.0 && std::fabs(my) <= 8388608.0)) continue;  // 2^23
+        double mid = 0.5 * (a + c);
+        double lmax = mid + std::sqrt(std::max(0.0, 0.25 * (a - c) * (a - c) + b * b));
+        double rr = std::ceil(3.0 * std::sqrt(lmax));
+        int r = (int)std::min(rr, 16777216.0);  // 2^24
+        conic[3 * g] = c / det;
+        conic[3 * g + 1] = -b / det;
+        conic[3 * g + 2] = a / det;
+        mean2d[2 * g] = mx;
+        mean2d[2 * g + 1] = my;
+        int rc[4];
+        if (!tile_rect(mx, my, r, cam.W, cam.H, rc)) continue;
+        radius[g] = r;
+        for (int k = 0; k < 4; ++k) rect[4 * g + k] = rc[k];
+        tiles_touched[g] = (int64_t)(rc[1] - rc[0] + 1) * (rc[3] - rc[2] + 1);
+        // colour from SH, direction camera centre -> mean
+        double d[3] = {mw[0] - cpos[0], mw[1] - cpos[1], mw[2] - cpos[2]};
+        double dn = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        double Y[16];
+        sh_basis(d[0] / dn, d[1] / dn, d[2] / dn, Y);
+        for (int ch = 0; ch < 3; ++ch) {
+            double acc = 0;
+            for (int k = 0; k < K; ++k) acc += (double)sh[((size_t)g * K + k) * 3 + ch] * Y[k];
+            rgb[3 * g + ch] = std::max(0.0, acc + 0.5);
+        }
+    }
+}
+
+// The real SH basis alone, for pinning against a library evaluation.
+void oracle_sh_basis(int n, const double* dirs, double* out) {
+    for (int i = 0; i < n; ++i) sh_basis(dirs[3 * i], dirs[3 * i + 1], dirs[3 * i + 2], out + 16 * i);
+}
+
+// Stages 2-3 of Sec. 2.1: duplicate every splat once per touched tile (in
+// Gaussian order, tiles row-major within its rectangle) with key
+// (tile << 32) | float_bits(depth), then stable-sort by key; tile_ranges[t]
+// = [start, end) of tile t in the sorted list.  Returns the number of
+// instances, or -1 if it exceeds capacity.
+int64_t oracle_bin_sort(int n, const double* mean2d, const int32_t* radius, const float* depth,
+                        int W, int H, int64_t capacity, uint64_t* keys_out, uint32_t* ids_out,
+                        uint32_t* tile_ranges) {
+    std::vector<uint64_t> keys;
+    std::vector<uint32_t> ids;
+    for (int g = 0; g < n; ++g) {
+        int rc[4];
+        if (!tile_rect(mean2d[2 * g], mean2d[2 * g + 1], radius[g], W, H, rc)) continue;
+        uint32_t dbits;
+        std::memcpy(&dbits, &depth[g], 4);
+        for (int ty = rc[2]; ty <= rc[3]; ++ty)
+            for (int tx = rc[0]; tx <= rc[1]; ++tx) {
+                uint64_t tile = (uint64_t)ty * tiles_x(W) + tx;
+                keys.push_back((tile << 32) | dbits);
+                ids.push_back((uint32_t)g);
+            }
+    }
+    int64_t I = (int64_t)keys.size();
+    int ntiles = tiles_x(W) * tiles_y(H);
+    for (int t = 0; t < 2 * ntiles; ++t) tile_ranges[t] = 0;
+    if (I > capacity) return -1;
+    std::vector<size_t> order(I);
+    for (int64_t i = 0; i < I; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t a, size_t b) { return keys[a] < keys[b]; });
+    for (int64_t i = 0; i < I; ++i) {
+        keys_out[i] = keys[order[i]];
+        ids_out[i] = ids[order[i]];
+    }
+    for (int64_t i = 0; i < I; ++i) {
+        uint32_t t = (uint32_t)(keys_out[i] >> 32);
+        if (i == 0 || (uint32_t)(keys_out[i - 1] >> 32) != t) tile_ranges[2 * t] = (uint32_t)i;
+        if (i == I - 1 || (uint32_t)(keys_out[i + 1] >> 32) != t) tile_ranges[2 * t + 1] = (uint32_t)(i + 1);
+    }
+    return I;
+}
+
+// Stage 4 (Eq. 1, Alg. 1): blend every tile over its sorted list.  Image is
+// 3 x H x W (CHW).  Pixel results: T_final, n_contrib and an ambiguity flag.
+void oracle_blend(int W, int H, const uint32_t* tile_ranges, const uint32_t* ids,
+                  const double* mean2d, const double* conic, const double* opac, const double* rgb,
+                  const double* bg, double alpha_margin, double t_margin, int n_threads,
+                  const int32_t* tile_subset, int n_subset,
+                  double* image, double* T_final, int32_t* n_contrib, uint8_t* ambiguous) {
+    const int tx = tiles_x(W);
+    const int ntiles = tx * tiles_y(H);
+    const int count = tile_subset ? n_subset : ntiles;
+    parallel_for(count, n_threads, [&](int k) {
+        int t = tile_subset ? tile_subset[k] : k;
+        std::vector<Splat> list;
+        for (uint32_t i = tile_ranges[2 * t]; i < tile_ranges[2 * t + 1]; ++i)
+            list.push_back(load_splat(ids[i], mean2d, conic, opac, rgb));
+        int x0 = (t % tx) * kTile, y0 = (t / tx) * kTile;
+        for (int py = y0; py < std::min(y0 + kTile, H); ++py)
+            for (int px = x0; px < std::min(x0 + kTile, W); ++px) {
+                PixelResult r = composite_pixel(list, px + 0.5, py + 0.5, bg, alpha_margin, t_margin);
+                size_t pix = (size_t)py * W + px;
+                for (int ch = 0; ch < 3; ++ch) image[(size_t)ch * W * H + pix] = r.C[ch];
+                T_final[pix] = r.T;
+                n_contrib[pix] = r.n_contrib;
+                ambiguous[pix] = r.ambiguous ? 1 : 0;
+            }
+    });
+}
+
+// Per-pixel brute force: every splat whose tile rectangle (if use_rect) covers
+// the pixel's tile, ordered by (float depth, Gaussian index), composited as
+// in oracle_blend.  Independent of duplication, sorting and tile ranges.
+void oracle_brute_force(int n, const double* mean2d, const double* conic, const double* opac,
+                        const double* rgb, const int32_t* radius, const float* depth, int W, int H,
+                        const double* bg, int use_rect, double* image, double* T_final,
+                        int32_t* n_contrib) {
+    std::vector<int> order;
+    for (int g = 0; g < n; ++g)
+        if (radius[g] > 0) order.push_back(g);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return depth[a] < depth[b]; });
+    for (int py = 0; py < H; ++py)
+        for (int px = 0; px < W; ++px) {
+            std::vector<Splat> list;
+            for (int g : order) {
+                if (use_rect) {
+                    int rc[4];
+                    if (!tile_rect(mean2d[2 * g], mean2d[2 * g + 1], radius[g], W, H, rc)) continue;
+                    int tx = px / kTile, ty = py / kTile;
+                    if (tx < rc[0] || tx > rc[1] || ty < rc[2] || ty > rc[3]) continue;
+                }
+                list.push_back(load_splat((uint32_t)g, mean2d, conic, opac, rgb));
+            }
+            PixelResult r = composite_pixel(list, px + 0.5, py + 0.5, bg, 0.0, 0.0);
+            size_t pix = (size_t)py * W + px;
+            for (int ch = 0; ch < 3; ++ch) image[(size_t)ch * W * H + pix] = r.C[ch];
+            T_final[pix] = r.T;
+            n_contrib[pix] = r.n_contrib;
+        }
+}
+
+// Analytic gradient of the blended image (Eq. 1) with respect to each splat's
+// 2D mean, conic, opacity and colour, given dL/d(image) (3 x H x W).  For
+// splat i on a pixel's list (contributors only; skipped splats carry none):
+//   dC/dc_i     = alpha_i T_i
+//   dC/dalpha_i = T_i (c_i - S_i),  S_i = (sum_{k>i} c_k alpha_k T_k + T_f bg) / T_{i+1}
+// S_i is formed from explicit suffix sums, not from a recursion.  Then
+// alpha = o e^p (unclamped branch): dalpha/do = e^p, dalpha/dp = alpha; both
+// zero when the 0.99 clamp is active; dp/d* = 0 when power > 0 was clamped.
+// Outputs are accumulated into the caller's zeroed arrays.
+void oracle_blend_grad(int W, int H, const uint32_t* tile_ranges, const uint32_t* ids,
+                       const double* mean2d, const double* conic, const double* opac,
+                       const double* rgb, const double* bg, const double* dL_dimg,
+                       double* dmean2d, double* dconic, double* dopac, double* drgb) {
+    const int tx = tiles_x(W);
+    const int ntiles = tx * tiles_y(H);
+    for (int t = 0; t < ntiles; ++t) {
+        int x0 = (t % tx) * kTile, y0 = (t / tx) * kTile;
+        for (int py = y0; py < std::min(y0 + kTile, H); ++py)
+            for (int px = x0; px < std::min(x0 + kTile, W); ++px) {
+                const double xp = px + 0.5, yp = py + 0.5;
+                size_t pix = (size_t)py * W + px;
+                double gC[3];
+                for (int ch = 0; ch < 3; ++ch) gC[ch] = dL_dimg[(size_t)ch * W * H + pix];
+                // forward walk, recording contributors
+                struct Rec { uint32_t g; double alpha, T, e, power_raw; bool clamped; };
+                std::vector<Rec> recs;
+                double T = 1.0;
+                for (uint32_t i = tile_ranges[2 * t]; i < tile_ranges[2 * t + 1]; ++i) {
+                    Splat s = load_splat(ids[i], mean2d, conic, opac, rgb);
+                    double praw = power_eq3(s, xp, yp);
+                    double p = std::min(praw, 0.0);
+                    double e = std::exp(p);
+                    double raw = s.o * e;
+                    double alpha = std::min(0.99, raw);
+                    if (alpha < 1.0 / 255.0) continue;
+                    double testT = T * (1.0 - alpha);
+                    if (testT < 1e-4) break;
+                    recs.push_back({ids[i], alpha, T, e, praw, raw > 0.99});
+                    T = testT;
+                }
+                const double Tf = T;
+                const size_t m = recs.size();
+                // suffix[i] = sum_{k>i} c_k alpha_k T_k (per channel)
+                std::vector<double> suffix(3 * (m + 1), 0.0);
+                for (size_t i = m; i-- > 0;) {
+                    Splat s = load_splat(recs[i].g, mean2d, conic, opac, rgb);
+                    for (int ch = 0; ch < 3; ++ch)
+                        suffix[3 * i + ch] = suffix[3 * (i + 1) + ch] + s.c[ch] * recs[i].alpha * recs[i].T;
+                }
+                for (size_t i = 0; i < m; ++i) {
+                    const Rec& r = recs[i];
+                    Splat s = load_splat(r.g, mean2d, conic, opac, rgb);
+                    double Tnext = r.T * (1.0 - r.alpha);
+                    double dL_dalpha = 0;
+                    for (int ch = 0; ch < 3; ++ch) {
+                        double S = (suffix[3 * (i + 1) + ch] + Tf * bg[ch]) / Tnext;
+                        dL_dalpha += r.T * (s.c[ch] - S) * gC[ch];
+                        drgb[3 * (size_t)r.g + ch] += r.alpha * r.T * gC[ch];
+                    }
+                    if (r.clamped) continue;
+                    dopac[r.g] += dL_dalpha * r.e;
+                    if (r.power_raw > 0) continue;
+                    double dL_dp = dL_dalpha * r.alpha;
+                    double dx = s.mx - xp, dy = s.my - yp;
+                    dmean2d[2 * (size_t)r.g] += dL_dp * (-(s.A * dx + s.B * dy));
+                    dmean2d[2 * (size_t)r.g + 1] += dL_dp * (-(s.B * dx + s.C * dy));
+                    dconic[3 * (size_t)r.g] += dL_dp * (-0.5 * dx * dx);
+                    dconic[3 * (size_t)r.g + 1] += dL_dp * (-dx * dy);
+                    dconic[3 * (size_t)r.g + 2] += dL_dp * (-0.5 * dy * dy);
+                }
+            }
+    }
+}
+
+// Eq. 6: the exponent as the dot product v_g . v_p of the Gaussian vector
+// [-A/2, -C/2, -B, -A xh - B yh, -C yh - B xh, -A/2 xh^2 - C/2 yh^2 - B xh yh]
+// and the pixel vector [xb^2, yb^2, xb yb, xb, yb, 1], with xh = x_g - x_c and
+// xb the intra-tile offset such that x_p = x_c - xb (Eqs. 4-5).  Also returns
+// the direct quadratic of Eq. 3 at dx = xh + xb for comparison.
+void oracle_power_eq6(int n, const double* abc, const double* hat, const double* bar,
+                      double* power_dot, double* power_direct) {
+    for (int i = 0; i < n; ++i) {
+        double A = abc[3 * i], B = abc[3 * i + 1], C = abc[3 * i + 2];
+        double xh = hat[2 * i], yh = hat[2 * i + 1];
+        double xb = bar[2 * i], yb = bar[2 * i + 1];
+        double vg[6] = {-0.5 * A, -0.5 * C, -B, -A * xh - B * yh, -C * yh - B * xh,
+                        -0.5 * A * xh * xh - 0.5 * C * yh * yh - B * xh * yh};
+        double vp[6] = {xb * xb, yb * yb, xb * yb, xb, yb, 1.0};
+        double acc = 0;
+        for (int k = 0; k < 6; ++k) acc += vg[k] * vp[k];
+        power_dot[i] = acc;
+        double dx = xh + xb, dy = yh + yb;
+        power_direct[i] = -0.5 * A * dx * dx - B * dx * dy - 0.5 * C * dy * dy;
+    }
+}
+
+// Exponent matrix of one tile (what the tensor-core contraction produces,
+// Eq. 8), evaluated directly with Eq. 3 in FP64: out[j * 256 + p] for list
+// position j of the tile and pixel p = 16 * row + col of the tile (pixels
+// outside the image are still evaluated at their centres).
+void oracle_tile_power(int W, int tile, const uint32_t* tile_ranges, const uint32_t* ids,
+                       const double* mean2d, const double* conic, double* out) {
+    const int tx = tiles_x(W);
+    int x0 = (tile % tx) * kTile, y0 = (tile / tx) * kTile;
+    uint32_t a = tile_ranges[2 * tile], b = tile_ranges[2 * tile + 1];
+    for (uint32_t i = a; i < b; ++i) {
+        uint32_t g = ids[i];
+        Splat s{mean2d[2 * (size_t)g], mean2d[2 * (size_t)g + 1], conic[3 * (size_t)g],
+                conic[3 * (size_t)g + 1], conic[3 * (size_t)g + 2], 1.0, {0, 0, 0}};
+        for (int p = 0; p < kTile * kTile; ++p) {
+            double xp = x0 + (p % kTile) + 0.5, yp = y0 + (p / kTile) + 0.5;
+            out[(size_t)(i - a) * 256 + p] = power_eq3(s, xp, yp);
+        }
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,419 @@
+"""Pins of the FP64 oracle against facts fixed outside it: hand-derived closed
+forms, library routines (scipy densities, rotations, spherical harmonics),
+invariants of Eq. 1, brute force and finite differences.  CPU only."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_02120_gb300 import scenes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _splat_set(mean2d, conic, opac, rgb, radius, depth):
+    return dict(mean2d=np.asarray(mean2d, float), conic=np.asarray(conic, float),
+                opac=np.asarray(opac, float), rgb=np.asarray(rgb, float),
+                radius=np.asarray(radius, np.int32), depth=np.asarray(depth, np.float32))
+
+
+def _blend_set(s, W, H, bg=(0, 0, 0)):
+    bs = oracle.bin_sort(s["mean2d"], s["radius"], s["depth"], W, H)
+    return oracle.blend(W, H, bs["tile_ranges"], bs["ids"], s["mean2d"], s["conic"], s["opac"], s["rgb"], bg=bg)
+
+
+# ---------------------------------------------------------------- Eq. 6 ----
+
+def test_eq6_dot_product_equals_quadratic():
+    """Sec. 3.2, Eq. 6: v_g . v_p reproduces the quadratic exponent of Eq. 3."""
+    rng = np.random.default_rng(1)
+    n = 4000
+    L = rng.standard_normal((n, 2, 2))
+    cov = L @ np.transpose(L, (0, 2, 1)) + 0.1 * np.eye(2)
+    inv = np.linalg.inv(cov)
+    abc = np.stack([inv[:, 0, 0], inv[:, 0, 1], inv[:, 1, 1]], 1)
+    hat = rng.uniform(-40, 40, (n, 2))
+    bar = rng.integers(-7, 8, (n, 2)) + 0.5
+    dot, direct = oracle.power_eq6(abc, hat, bar)
+    # independent evaluation: -1/2 d^T Sigma^-1 d with d = hat + bar
+    d = hat + bar
+    ref = -0.5 * np.einsum("ni,nij,nj->n", d, inv, d)
+    scale = np.abs(abc).max(1) * (np.abs(hat).max(1) + 8) ** 2
+    assert np.max(np.abs(dot - ref) / scale) < 1e-13
+    assert np.max(np.abs(direct - ref) / scale) < 1e-13
+
+
+# ---------------------------------------------------------------- blend ----
+
+def test_single_splat_matches_gaussian_density():
+    """Eq. 2: alpha = o * exp(-1/2 x^T Sigma^-1 x) is the normalised 2D Gaussian
+    density (scipy) scaled by the opacity, clamped at 0.99 and skipped below 1/255."""
+    from scipy.stats import multivariate_normal
+    W, H = 48, 40
+    th = 0.7
+    Rm = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    cov = Rm @ np.diag([25.0, 4.0]) @ Rm.T
+    inv = np.linalg.inv(cov)
+    m = np.array([20.3, 17.8])
+    for o in (0.8, 1.0):
+        s = _splat_set([m], [[inv[0, 0], inv[0, 1], inv[1, 1]]], [o], [[1.0, 0.5, 0.25]], [100], [1.0])
+        r = _blend_set(s, W, H)
+        mvn = multivariate_normal(mean=m, cov=cov)
+        ys, xs = np.mgrid[0:H, 0:W]
+        pts = np.stack([xs + 0.5, ys + 0.5], -1).reshape(-1, 2)
+        ratio = (mvn.pdf(pts) / mvn.pdf(m)).reshape(H, W)
+        alpha = np.minimum(0.99, o * ratio)
+        alpha = np.where(alpha < 1 / 255, 0.0, alpha)
+        for ch, c in enumerate((1.0, 0.5, 0.25)):
+            np.testing.assert_allclose(r["image"][ch], c * alpha, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(r["T_final"], 1 - alpha, rtol=0, atol=1e-12)
+        np.testing.assert_array_equal(r["n_contrib"], (alpha > 0).astype(np.int32))
+
+
+def test_two_splat_composite_golden():
+    """Eq. 1 on a hand-derived two-splat case (tests/golden/two_splat_composite.json)."""
+    with open(os.path.join(GOLDEN, "two_splat_composite.json")) as f:
+        gold = json.load(f)
+    sp = gold["splats"]
+    s = _splat_set([x["mean2d"] for x in sp], [x["conic"] for x in sp], [x["opacity"] for x in sp],
+                   [x["rgb"] for x in sp], [3, 3], [x["depth"] for x in sp])
+    px, py = gold["pixel"]
+    for case in gold["cases"]:
+        r = _blend_set(s, gold["width"], gold["height"], bg=case["bg"])
+        np.testing.assert_allclose(r["image"][:, py, px], case["C"], rtol=0, atol=1e-15)
+        assert r["T_final"][py, px] == pytest.approx(case["T"], abs=1e-15)
+        assert r["n_contrib"][py, px] == case["n_contrib"]
+
+
+def _stack_at_pixel(opacs, W=16, H=16, px=3, py=5):
+    n = len(opacs)
+    return _splat_set([[px + 0.5, py + 0.5]] * n, [[0.5, 0.0, 0.5]] * n, opacs,
+                      [[1.0, 1.0, 1.0]] * n, [2] * n, np.arange(1, n + 1))
+
+
+def test_alpha_skip_clamp_and_termination():
+    """Alg. 1 rules: skip alpha < 1/255, clamp at 0.99, stop once T would drop below 1e-4."""
+    px, py = 3, 5
+    # skip: opacity just under 1/255 contributes nothing, n_contrib counts the later splat
+    r = _blend_set(_stack_at_pixel([0.99 / 255, 0.5]), 16, 16)
+    assert r["T_final"][py, px] == pytest.approx(0.5, abs=1e-15)
+    assert r["n_contrib"][py, px] == 2
+    # clamp: opacity 1 at the centre gives alpha 0.99
+    r = _blend_set(_stack_at_pixel([1.0]), 16, 16)
+    assert r["T_final"][py, px] == pytest.approx(0.01, abs=1e-15)
+    # termination: T = 0.01 * 0.01 = 1e-4 is kept (not below), the third would reach 1e-6: stop
+    r = _blend_set(_stack_at_pixel([1.0, 1.0, 1.0, 0.5]), 16, 16)
+    assert r["n_contrib"][py, px] == 2
+    assert r["T_final"][py, px] == pytest.approx(1e-4, rel=1e-12)
+    assert r["image"][0, py, px] == pytest.approx(0.99 + 0.99 * 0.01, abs=1e-14)
+    # boundaries are strict: alpha == 1/255 exactly is kept (skip only below it)
+    r = _blend_set(_stack_at_pixel([1.0 / 255.0]), 16, 16)
+    assert r["n_contrib"][py, px] == 1
+    assert r["T_final"][py, px] == 1.0 - 1.0 / 255.0
+    # ... and a test transmittance exactly equal to 1e-4 is kept (stop only below it):
+    # 13 splats of alpha 1/2 leave T = 2^-13; alpha = 1 - 1e-4 * 2^13 (exact in FP64)
+    # then gives T * (1 - alpha) == 1e-4 to the last bit.
+    v = 1e-4 * 8192.0
+    last = 1.0 - v
+    assert 1.0 - last == v and (2.0 ** -13) * (1.0 - last) == 1e-4
+    r = _blend_set(_stack_at_pixel([0.5] * 13 + [last, 0.5]), 16, 16)
+    assert r["n_contrib"][py, px] == 14
+    assert r["T_final"][py, px] == 1e-4
+
+
+def test_partition_of_unity_and_monotone_transmittance():
+    """Eq. 1 telescopes: with white splats and a black background, C + T_final = 1;
+    and truncating every list can only raise T (T is non-increasing)."""
+    sc = scenes.tiny_scene(3, n=64, width=64, height=48)
+    cam = sc.cameras[0]
+    pr = oracle.project(sc.means, sc.scales, sc.quats, sc.sh, 0, cam)
+    bs = oracle.bin_sort(pr["mean2d"], pr["radius"], pr["depth"].astype(np.float32), cam.width, cam.height)
+    white = np.ones_like(pr["rgb"])
+    r = oracle.blend(cam.width, cam.height, bs["tile_ranges"], bs["ids"], pr["mean2d"], pr["conic"],
+                     sc.opacities.astype(float), white)
+    assert np.max(np.abs(r["image"][0] + r["T_final"] - 1)) < 1e-12
+    assert (r["n_contrib"] > 0).mean() > 0.3
+    ranges = bs["tile_ranges"].astype(np.int64)
+    ranges[1::2] = np.maximum(ranges[0::2], ranges[1::2] - 1)
+    ranges = ranges.astype(np.uint32)
+    r2 = oracle.blend(cam.width, cam.height, ranges, bs["ids"], pr["mean2d"], pr["conic"],
+                      sc.opacities.astype(float), white)
+    assert np.all(r2["T_final"] >= r["T_final"] - 1e-15)
+
+
+@pytest.mark.parametrize("seed,W,H", [(0, 48, 40), (1, 33, 17), (2, 64, 64), (5, 16, 16)])
+def test_tiled_blend_equals_per_pixel_brute_force(seed, W, H):
+    """Duplication + sort + per-tile blending equals compositing, per pixel, all
+    splats whose rectangle covers the pixel's tile in depth order."""
+    sc = scenes.tiny_scene(seed, n=48, width=W, height=H)
+    cam = sc.cameras[0]
+    pr = oracle.project(sc.means, sc.scales, sc.quats, sc.sh, 0, cam)
+    d32 = pr["depth"].astype(np.float32)
+    bs = oracle.bin_sort(pr["mean2d"], pr["radius"], d32, W, H)
+    bg = (0.1, 0.2, 0.3)
+    tiled = oracle.blend(W, H, bs["tile_ranges"], bs["ids"], pr["mean2d"], pr["conic"],
+                         sc.opacities.astype(float), pr["rgb"], bg=bg)
+    brute = oracle.brute_force(pr["mean2d"], pr["conic"], sc.opacities.astype(float), pr["rgb"],
+                               pr["radius"], d32, W, H, bg=bg, use_rect=True)
+    np.testing.assert_array_equal(tiled["image"], brute["image"])
+    np.testing.assert_array_equal(tiled["T_final"], brute["T_final"])
+    np.testing.assert_array_equal(tiled["n_contrib"], brute["n_contrib"])
+
+
+def test_permutation_invariance():
+    """With distinct depths the render does not depend on the input order."""
+    sc = scenes.tiny_scene(7, n=40, width=48, height=48, sh_degree=1)
+    base = oracle.render(sc)
+    assert len(np.unique(base["project"]["depth"].astype(np.float32))) == sc.n
+    perm = np.random.default_rng(0).permutation(sc.n)
+    sc2 = scenes.Scene(sc.means[perm], sc.scales[perm], sc.quats[perm], sc.opacities[perm], sc.sh[perm],
+                       sc.sh_degree, sc.cameras)
+    other = oracle.render(sc2)
+    np.testing.assert_array_equal(base["blend"]["image"], other["blend"]["image"])
+    np.testing.assert_array_equal(base["blend"]["n_contrib"], other["blend"]["n_contrib"])
+
+
+# ------------------------------------------------------------- bin/sort ----
+
+def test_bin_sort_membership_and_order():
+    """Sec. 2.1 stages 2-3: tile t's list holds exactly the splats whose closed
+    3-sigma square meets the tile's half-open pixel box, ordered by (float
+    depth, index), with key (t << 32) | depth bits."""
+    sc = scenes.tiny_scene(11, n=80, width=70, height=45)
+    cam = sc.cameras[0]
+    pr = oracle.project(sc.means, sc.scales, sc.quats, sc.sh, 0, cam)
+    d32 = pr["depth"].astype(np.float32)
+    bs = oracle.bin_sort(pr["mean2d"], pr["radius"], d32, cam.width, cam.height)
+    tx, ty = cam.tiles_x, cam.tiles_y
+    m, r = pr["mean2d"], pr["radius"].astype(float)
+    total = 0
+    for t in range(tx * ty):
+        a, b = bs["tile_ranges"][2 * t], bs["tile_ranges"][2 * t + 1]
+        got = list(bs["ids"][a:b])
+        x0, y0 = 16 * (t % tx), 16 * (t // tx)
+        meet = ((pr["radius"] > 0) & (m[:, 0] - r < x0 + 16) & (m[:, 0] + r >= x0)
+                & (m[:, 1] - r < y0 + 16) & (m[:, 1] + r >= y0))
+        want = sorted(np.nonzero(meet)[0], key=lambda g: (d32[g], g))
+        assert got == want
+        dbits = d32.view(np.uint32)
+        for i, g in zip(range(a, b), got):
+            assert int(bs["keys"][i]) == (t << 32) | int(dbits[g])
+        total += len(got)
+    assert total == bs["n_instances"] > 0
+
+
+def test_bin_sort_capacity_overflow_reports():
+    sc = scenes.tiny_scene(11, n=20, width=48, height=48)
+    cam = sc.cameras[0]
+    pr = oracle.project(sc.means, sc.scales, sc.quats, sc.sh, 0, cam)
+    bs = oracle.bin_sort(pr["mean2d"], pr["radius"], pr["depth"].astype(np.float32), 48, 48, capacity=1)
+    assert bs["n_instances"] == -1
+
+
+# ------------------------------------------------------------ projection ----
+
+def _cam(W=64, H=48, f=50.0):
+    return scenes.Camera(W, H, f, f, W / 2, H / 2, np.eye(3), np.array([0.0, 0.0, 3.0]))
+
+
+def _one(mean, scale, quat=(1.0, 0.0, 0.0, 0.0), sh=None, deg=0):
+    sh = np.zeros((1, (deg + 1) ** 2, 3), np.float32) if sh is None else np.asarray(sh, np.float32)
+    return (np.asarray([mean], np.float32), np.asarray([scale], np.float32),
+            np.asarray([quat], np.float32), sh, deg)
+
+
+def test_project_isotropic_closed_form():
+    """An isotropic splat on the optical axis at depth z projects to a circle of
+    variance (f s / z)^2 + lowpass centred on the principal point."""
+    cam = _cam()
+    s = np.float32(0.05)
+    pr = oracle.project(*_one((0, 0, 0), (s, s, s)), cam)
+    var = (50.0 * float(s) / 3.0) ** 2 + 0.3
+    np.testing.assert_allclose(pr["cov2d"][0], [var, 0, var], rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(pr["conic"][0], [1 / var, 0, 1 / var], rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(pr["mean2d"][0], [32.0, 24.0], rtol=0, atol=1e-13)
+    assert pr["depth"][0] == pytest.approx(3.0)
+    assert pr["radius"][0] == math.ceil(3 * math.sqrt(var))
+
+
+def test_project_offaxis_closed_form():
+    """Hand-derived EWA for an axis-aligned splat at world (x, 0, 0): with J =
+    [[f/z, 0, -f x/z^2], [0, f/z, 0]], Sigma2 = diag((f/z)^2 sx^2 + (f x/z^2)^2 sz^2,
+    (f/z)^2 sy^2) + lowpass I; quaternion (cos 45, 0, 0, sin 45) swaps sx and sy."""
+    cam = _cam()
+    x = np.float32(0.4)
+    sx, sy, sz = (np.float32(v) for v in (0.03, 0.07, 0.11))
+    f, z = 50.0, 3.0
+    pr = oracle.project(*_one((x, 0, 0), (sx, sy, sz)), cam)
+    a = (f / z) ** 2 * float(sx) ** 2 + (f * float(x) / z ** 2) ** 2 * float(sz) ** 2 + 0.3
+    c = (f / z) ** 2 * float(sy) ** 2 + 0.3
+    np.testing.assert_allclose(pr["cov2d"][0], [a, 0, c], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(pr["mean2d"][0], [f * float(x) / z + 32, 24], rtol=1e-14)
+    h = math.sqrt(0.5)
+    pr2 = oracle.project(*_one((0, 0, 0), (sx, sy, sz), (h, 0, 0, h)), cam)
+    c2 = (f / z) ** 2 * float(sx) ** 2 + 0.3
+    a2 = (f / z) ** 2 * float(sy) ** 2 + 0.3
+    np.testing.assert_allclose(pr2["cov2d"][0], [a2, 0, c2], rtol=1e-6, atol=1e-6)
+
+
+def test_project_matches_numerical_jacobian():
+    """EWA splatting: Sigma2 = J Sigma3 J^T + lowpass I, where J is the Jacobian of
+    the pixel projection of the mean (central differences of the oracle's own
+    mean2d) and Sigma3 = R S^2 R^T from scipy's quaternion rotation."""
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(4)
+    R0 = Rotation.from_euler("xyz", [0.2, -0.3, 0.1]).as_matrix()
+    cam = scenes.Camera(96, 80, 70.0, 65.0, 47.0, 41.0, R0, np.array([0.1, -0.2, 3.5]))
+    for _ in range(6):
+        mean = rng.uniform(-0.6, 0.6, 3).astype(np.float32)
+        scale = np.exp(rng.uniform(-4, -2, 3)).astype(np.float32)
+        q = rng.standard_normal(4)
+        q = (q / np.linalg.norm(q)).astype(np.float32)
+        pr = oracle.project(*_one(mean, scale, q), cam)
+        h = 1e-4
+        J = np.zeros((2, 3))
+        for j in range(3):
+            mp = mean.astype(np.float64).copy()
+            mm = mp.copy()
+            mp[j] += h
+            mm[j] -= h
+            # the oracle takes float32 means, so evaluate the projection in double here
+            def proj(p):
+                pc = cam.R @ p + cam.t
+                return np.array([cam.fx * pc[0] / pc[2] + cam.cx, cam.fy * pc[1] / pc[2] + cam.cy])
+            J[:, j] = (proj(mp) - proj(mm)) / (2 * h)
+        qd = q.astype(np.float64)
+        Rq = Rotation.from_quat([qd[1], qd[2], qd[3], qd[0]]).as_matrix()
+        S3 = Rq @ np.diag(scale.astype(np.float64) ** 2) @ Rq.T
+        S2 = J @ S3 @ J.T + 0.3 * np.eye(2)
+        np.testing.assert_allclose(pr["cov2d"][0], [S2[0, 0], S2[0, 1], S2[1, 1]], rtol=1e-6, atol=1e-8)
+        np.testing.assert_allclose(pr["mean2d"][0], proj(mean.astype(np.float64)), rtol=1e-12)
+        inv = np.linalg.inv(np.array([[pr["cov2d"][0][0], pr["cov2d"][0][1]],
+                                      [pr["cov2d"][0][1], pr["cov2d"][0][2]]]))
+        np.testing.assert_allclose(pr["conic"][0], [inv[0, 0], inv[0, 1], inv[1, 1]], rtol=1e-10)
+
+
+def test_project_camera_rotation_invariance():
+    """Rotating the world by Q = R0^T Rk and viewing it from camera 0 equals
+    viewing the original world from ring camera k (SH degree 0 colours)."""
+    from scipy.spatial.transform import Rotation
+    sc = scenes.tiny_scene(9, n=30, width=64, height=64)
+    ring = scenes.ring_cameras(8, 3.0, [(64, 64)] * 8)
+    c0 = ring[0]
+    for k in (1, 3, 6):
+        ck = ring[k]
+        Q = c0.R.T @ ck.R
+        means2 = (sc.means.astype(np.float64) @ Q.T).astype(np.float32)
+        qs = sc.quats.astype(np.float64)
+        rot = Rotation.from_matrix(Q) * Rotation.from_quat(qs[:, [1, 2, 3, 0]])
+        q2 = rot.as_quat()[:, [3, 0, 1, 2]].astype(np.float32)
+        a = oracle.project(sc.means, sc.scales, sc.quats, sc.sh, 0, ck)
+        b = oracle.project(means2, sc.scales, q2, sc.sh, 0, c0)
+        for key in ("mean2d", "cov2d", "depth", "rgb"):
+            np.testing.assert_allclose(a[key], b[key], rtol=2e-5, atol=2e-5)
+
+
+def test_project_culling():
+    cam = _cam()
+    # behind the camera, and in front of it but nearer than znear
+    pr = oracle.project(*_one((0, 0, -3.5), (0.05, 0.05, 0.05)), cam)
+    assert pr["radius"][0] == 0 and pr["tiles_touched"][0] == 0
+    pr = oracle.project(*_one((0, 0, -2.9), (0.05, 0.05, 0.05)), cam)
+    assert pr["radius"][0] == 0
+    # far outside the image: rectangle empty
+    pr = oracle.project(*_one((30.0, 0, 0), (0.01, 0.01, 0.01)), cam)
+    assert pr["tiles_touched"][0] == 0
+    # degenerate covariance without the low-pass: det = 0, culled
+    c2 = _cam()
+    c2.lowpass = 0.0
+    pr = oracle.project(*_one((0, 0, 0), (0.0, 0.05, 0.05)), c2)
+    assert pr["radius"][0] == 0
+
+
+def test_sh_basis_matches_scipy():
+    """Real SH to degree 3: sqrt(2) Re/Im of scipy's complex harmonics (with the
+    Condon-Shortley phase), order m = -l..l."""
+    from scipy.special import sph_harm_y
+    rng = np.random.default_rng(2)
+    d = rng.standard_normal((200, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    got = oracle.sh_basis(d)
+    theta = np.arccos(np.clip(d[:, 2], -1, 1))
+    phi = np.arctan2(d[:, 1], d[:, 0])
+    k = 0
+    for l in range(4):
+        for m in range(-l, l + 1):
+            Y = sph_harm_y(l, abs(m), theta, phi)
+            if m > 0:
+                ref = math.sqrt(2) * Y.real
+            elif m < 0:
+                ref = math.sqrt(2) * Y.imag
+            else:
+                ref = Y.real
+            np.testing.assert_allclose(got[:, k], ref, rtol=0, atol=1e-12, err_msg=f"l={l} m={m}")
+            k += 1
+
+
+def test_sh_degree0_colour():
+    cam = _cam()
+    sh = np.array([[[0.3, -0.2, -2.5]]], np.float32)
+    pr = oracle.project(*_one((0, 0, 0), (0.05, 0.05, 0.05), sh=sh), cam)
+    y00 = 0.28209479177387814  # 1 / (2 sqrt(pi))
+    want = np.maximum(0, y00 * sh[0, 0].astype(np.float64) + 0.5)
+    np.testing.assert_allclose(pr["rgb"][0], want, rtol=1e-15)
+
+
+# ------------------------------------------------------------- gradients ----
+
+def test_blend_grad_matches_central_differences():
+    """The analytic blend gradient equals FP64 central differences of the loss
+    L = sum(w * image) for every parameter whose perturbation changes no
+    skip / stop decision (two step sizes must agree)."""
+    sc = scenes.tiny_scene(21, n=24, width=40, height=36, sh_degree=1)
+    cam = sc.cameras[0]
+    W, H = cam.width, cam.height
+    pr = oracle.project(sc.means, sc.scales, sc.quats, sc.sh, 1, cam)
+    bs = oracle.bin_sort(pr["mean2d"], pr["radius"], pr["depth"].astype(np.float32), W, H)
+    rng = np.random.default_rng(5)
+    w = rng.standard_normal((3, H, W))
+    bg = (0.2, 0.1, 0.05)
+    params = dict(mean2d=pr["mean2d"].copy(), conic=pr["conic"].copy(),
+                  opacity=sc.opacities.astype(float).copy(), rgb=pr["rgb"].copy())
+
+    def loss(p):
+        r = oracle.blend(W, H, bs["tile_ranges"], bs["ids"], p["mean2d"], p["conic"], p["opacity"],
+                         p["rgb"], bg=bg)
+        return float(np.sum(w * r["image"]))
+
+    g = oracle.blend_grad(W, H, bs["tile_ranges"], bs["ids"], params["mean2d"], params["conic"],
+                          params["opacity"], params["rgb"], w, bg=bg)
+    live = np.nonzero(pr["radius"] > 0)[0]
+    checked = 0
+    for name in ("mean2d", "conic", "opacity", "rgb"):
+        fd_all, an_all = [], []
+        arr = params[name]
+        for gidx in live:
+            for j in range(arr.shape[1] if arr.ndim == 2 else 1):
+                idx = (gidx, j) if arr.ndim == 2 else (gidx,)
+                base = arr[idx]
+                ests = []
+                for h in (1e-6 * max(1.0, abs(base)), 2.5e-7 * max(1.0, abs(base))):
+                    arr[idx] = base + h
+                    lp = loss(params)
+                    arr[idx] = base - h
+                    lm = loss(params)
+                    arr[idx] = base
+                    ests.append((lp - lm) / (2 * h))
+                if abs(ests[0] - ests[1]) > 1e-6 * (abs(ests[0]) + 1e-6):
+                    continue  # a decision flipped inside the step
+                fd_all.append(ests[0])
+                an_all.append(g[name][idx])
+        fd_all, an_all = np.array(fd_all), np.array(an_all)
+        assert len(fd_all) > 0.8 * len(live) * (arr.shape[1] if arr.ndim == 2 else 1)
+        denom = max(np.linalg.norm(fd_all), 1e-12)
+        assert np.linalg.norm(an_all - fd_all) / denom < 1e-6, name
+        checked += len(fd_all)
+    assert checked > 100
