@@ -1,0 +1,445 @@
+#!/usr/bin/env python
+"""Benchmark of the Gaussian-splatting hot path on one GB300 (or N, one
+process per GPU under torchrun, each rendering its own copy of the workload:
+weak scaling, no collective on the data path).
+
+One step = project -> bin/sort -> blend forward (tensor-core variant) ->
+blend backward over the 1280x720, 200k-Gaussian, SH-degree-3 synthetic scene
+(seed 0), inputs resident in HBM.  The metric is Gaussian-pixel evaluations
+per second, evaluations = sum over pixels of n_contrib (the pairs Eq. 1 with
+the skip/stop rules must examine), counted once per forward and once per
+backward.  L2 is flushed (256 MB write) before every timed step.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+instead (the reference arm), on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "blend ms/frame & Gaussian-pixel evals/s (fwd, fwd+bwd) TC vs FP32 CUDA-core"
+UNIT = "Gaussian-pixel evals/s"
+WORKLOAD = "1280x720, 200k Gaussians, SH degree 3, seed 0 (synthetic stand-in for the paper's trained scenes)"
+SM_COUNT_NOMINAL = 152
+MUFU_PER_CLK_SM = 16  # ex2/rcp results per clock per SM (CUDA programming guide throughput table)
+
+# DRAM traffic per launch from ncu captures, keyed by kernel and the SHA-256 of
+# the kernel's source when it was measured (stale entries are not reported).
+KNOWN_TRAFFIC = {}
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--variant", default="fp16_split")
+    p.add_argument("--config", type=int, default=1)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--quick", action="store_true", help="skip the per-variant blend sweep")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        load = [s for s in sm if smax and s > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
+
+
+def source_digest(*names):
+    import hashlib
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2604_02120_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# ------------------------------------------------------------------ ours ----
+
+def run_ours(args):
+    import torch
+    from paper_2604_02120_gb300 import gs, scenes
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    gs.load()
+    sc = scenes.make_config(args.config, seed=0)
+    cam = sc.cameras[0]
+    W, H = cam.width, cam.height
+    dev = gs.scene_to_device(sc)
+    opts = gs.make_opts(args.variant)
+    fp32 = gs.make_opts("fp32")
+    sorter = gs.BinSorter("cuda", capacity=1 << 21)
+    dL = torch.from_numpy(scenes.upstream_grad(0, [cam])[0]).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        proj = gs.project(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam)
+        bs = sorter.run(proj["mean2d"], proj["radius"], proj["depth"], W, H)
+        if ev:
+            ev[0].record(stream)
+        fwd = gs.blend_forward(W, H, bs, proj, dev["opacities"], opts)
+        if ev:
+            ev[1].record(stream)
+        g = gs.blend_backward(W, H, bs, proj, dev["opacities"], opts, fwd, dL)
+        if ev:
+            ev[2].record(stream)
+        return proj, bs, fwd, g
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    assert gs.gs_sync_status() == gs.GS_OK
+    proj, bs, fwd, _ = step()
+    evals_fwd = int(fwd["n_contrib"].sum().item())
+    n_inst = bs["n_instances"]
+
+    K = args.steps
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    st_ev = [(E(), E()) for _ in range(K)]
+    k_ev = [(E(), E(), E()) for _ in range(K)]
+    launches0 = gs.gs_launch_count()
+    with ClockSampler(local) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for k in range(K):
+            flush.zero_()
+            st_ev[k][0].record(stream)
+            step(k_ev[k])
+            st_ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        wall = time.perf_counter() - wall0
+    launches = gs.gs_launch_count() - launches0
+    clocks = clk.summary()
+    assert gs.gs_sync_status() == gs.GS_OK
+    step_ms = [a.elapsed_time(b) for a, b in st_ev]
+    fwd_ms = [a.elapsed_time(b) for a, b, _ in k_ev]
+    bwd_ms = [b.elapsed_time(c) for _, b, c in k_ev]
+    dev_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([dev_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms = float(t.item())
+    evals_step = 2 * evals_fwd  # forward and backward each examine sum(n_contrib) pairs
+    value = ws * evals_step * K / (dev_ms / 1e3)
+
+    # ---- blend-only ms/frame per variant (forward), tensor core vs FP32 CUDA core
+    blend = {}
+    if not args.quick:
+        for name in ["fp32", "fp16", "bf16", "fp16_split", "bf16_split"]:
+            o = gs.make_opts(name)
+            for _ in range(3):
+                gs.blend_forward(W, H, bs, proj, dev["opacities"], o)
+            times = []
+            for _ in range(max(K, 10)):
+                flush.zero_()
+                a, b = E(), E()
+                a.record(stream)
+                out = gs.blend_forward(W, H, bs, proj, dev["opacities"], o)
+                b.record(stream)
+                times.append((a, b))
+            torch.cuda.synchronize()
+            ms = statistics.median(a.elapsed_time(b) for a, b in times)
+            ev = int(out["n_contrib"].sum().item())
+            blend[name] = {"ms_per_frame": round(ms, 5), "evals_per_s": ev / (ms / 1e3)}
+        # backward (FP32 CUDA-core recompute) alone
+        times = []
+        for _ in range(max(K, 10)):
+            flush.zero_()
+            a, b = E(), E()
+            a.record(stream)
+            gs.blend_backward(W, H, bs, proj, dev["opacities"], fp32, fwd, dL)
+            b.record(stream)
+            times.append((a, b))
+        torch.cuda.synchronize()
+        ms = statistics.median(a.elapsed_time(b) for a, b in times)
+        blend["backward_fp32"] = {"ms_per_frame": round(ms, 5), "evals_per_s": evals_fwd / (ms / 1e3)}
+
+    # ---- end to end through the public API with host buffers
+    e2e = run_e2e(args, gs, torch, sc, cam, opts, sorter, dL, flush, evals_step, ws, dist)
+
+    # ---- roofline of the dominant blend kernel (MUFU: one exp2 per evaluated pair)
+    peaks, peak_kind = read_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(local)
+    sms = getattr(props, "multi_processor_count", SM_COUNT_NOMINAL)
+    mufu_peak = MUFU_PER_CLK_SM * sms * sm_max * 1e6 / 1e9  # G ex2 / s
+    f_ms, b_ms = statistics.mean(fwd_ms), statistics.mean(bwd_ms)
+    if f_ms >= b_ms:
+        kern, t_ms, per_pair, src = f"k_blend_tc<{args.variant}>", f_ms, 1, ("blend_tc.cuh",)
+    else:
+        kern, t_ms, per_pair, src = "k_blend_fp32_bwd", b_ms, 2, ("blend_fp32.cu",)
+    achieved = evals_fwd / (t_ms / 1e3) / 1e9
+    peak = mufu_peak / per_pair
+    tr = KNOWN_TRAFFIC.get(kern)
+    traffic = tr["bytes"] if tr and tr.get("src") == source_digest(*src) else None
+    roofline = {"bound": "alu", "kernel": kern, "achieved": round(achieved, 2), "peak": round(peak, 1),
+                "unit": "G evals/s (MUFU ex2-bound)", "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": f"{MUFU_PER_CLK_SM} MUFU ops/clk/SM x {sms} SMs x {sm_max:.0f} MHz "
+                               f"(max SM clock, {peak_kind}) / {per_pair} MUFU op(s) per pair",
+                "launch_ms": round(t_ms, 5)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
+        "ms_per_step": dev_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "blend_variant": args.variant,
+                   "step": "project + bin_sort + blend_forward + blend_backward",
+                   "evals_per_step": evals_step, "instances": n_inst, "pixels": W * H,
+                   "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replica x{ws}"},
+        "breakdown_ms": {"blend_forward": round(f_ms, 5), "blend_backward": round(b_ms, 5),
+                         "project_bin_sort_and_gaps": round(dev_ms / K - f_ms - b_ms, 5)},
+        "wall_ms_per_step": wall * 1e3 / K,
+        "blend_forward_by_variant": blend,
+        "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cam, proj, bs, sc, dL, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, gs, torch, sc, cam, opts, sorter, dL, flush, evals_step, ws, dist):
+    """Same step through the public API from pinned host buffers: H2D of the
+    scene every step, D2H of the image and the four gradient arrays."""
+    W, H = cam.width, cam.height
+    host = {k: torch.from_numpy(getattr(sc, k)).pin_memory() for k in ("means", "scales", "quats", "opacities", "sh")}
+    devb = {k: torch.empty_like(v, device="cuda") for k, v in host.items()}
+    n = sc.n
+    out_h = {"image": torch.empty(3, H, W).pin_memory(), "mean2d": torch.empty(n, 2).pin_memory(),
+             "conic": torch.empty(n, 3).pin_memory(), "opacity": torch.empty(n).pin_memory(),
+             "rgb": torch.empty(n, 3).pin_memory()}
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = sum(v.numel() * v.element_size() for v in out_h.values())
+
+    def step():
+        for k, v in host.items():
+            devb[k].copy_(v, non_blocking=True)
+        dscene = dict(means=devb["means"], scales=devb["scales"], quats=devb["quats"], opacities=devb["opacities"],
+                      sh=devb["sh"], sh_degree=sc.sh_degree)
+        r = gs.render(dscene, cam, opts, sorter)
+        g = gs.blend_backward(W, H, r["bin_sort"], r["project"], devb["opacities"], opts, r["blend"], dL)
+        out_h["image"].copy_(r["blend"]["image"], non_blocking=True)
+        for k in ("mean2d", "conic", "opacity", "rgb"):
+            out_h[k].copy_(g[k], non_blocking=True)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    K = args.steps
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([t], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return {"value": ws * evals_step * K / t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": t * 1e3 / K, "timing": "host wall clock around K steps incl. L2 flush writes"}
+
+
+# ------------------------------------------------------------ CPU oracle ----
+
+def _oracle_sample(oracle, W, H, ranges, ids, mean2d, conic, opac, rgb, dL, tiles, threads):
+    t0 = time.perf_counter()
+    r = oracle.blend(W, H, ranges, ids, mean2d, conic, opac, rgb, n_threads=threads, tile_subset=tiles)
+    oracle.blend_grad(W, H, ranges, ids, mean2d, conic, opac, rgb, dL, n_threads=threads, tile_subset=tiles)
+    dt = time.perf_counter() - t0
+    mask = np.zeros((H, W), bool)
+    tx = (W + 15) // 16
+    for t in tiles:
+        mask[16 * (t // tx):16 * (t // tx) + 16, 16 * (t % tx):16 * (t % tx) + 16] = True
+    evals = 2 * int(r["n_contrib"][mask].sum())
+    return evals, dt
+
+
+def _calibrate(run, order, threads, seconds):
+    """Number of tiles (a prefix of `order`) whose oracle run takes about
+    `seconds`: grow a probe until it takes >= 1 s (or covers everything)."""
+    k = min(len(order), max(threads, 8))
+    while True:
+        dt = run(order[:k])
+        if dt >= 1.0 or k == len(order):
+            break
+        k = min(len(order), 4 * k)
+    return int(min(len(order), max(k, k * seconds / max(dt, 1e-3))))
+
+
+def _busy_tiles(ranges):
+    lens = ranges[1::2].astype(np.int64) - ranges[0::2]
+    return np.nonzero(lens > 0)[0]
+
+
+def cpu_baseline(cam, proj, bs, sc, dL, seconds):
+    """The FP64 oracle (forward blend + gradient) on a random sample of the
+    workload's tiles, on all host cores; evals/s over the sampled pixels."""
+    import oracle
+    W, H = cam.width, cam.height
+    ranges = bs["tile_ranges"].cpu().numpy().view(np.uint32)
+    ids = bs["ids"].cpu().numpy().view(np.uint32)
+    m2 = proj["mean2d"].cpu().numpy().astype(np.float64)
+    co = proj["conic"].cpu().numpy().astype(np.float64)
+    rgb = proj["rgb"].cpu().numpy().astype(np.float64)
+    op = sc.opacities.astype(np.float64)
+    g = dL.cpu().numpy().astype(np.float64)
+    threads = os.cpu_count() or 1
+    busy = _busy_tiles(ranges)
+    order = np.random.default_rng(0).permutation(busy)
+    k = _calibrate(lambda t: _oracle_sample(oracle, W, H, ranges, ids, m2, co, op, rgb, g, t, threads)[1],
+                   order, threads, seconds)
+    ev, dt = _oracle_sample(oracle, W, H, ranges, ids, m2, co, op, rgb, g, order[:k], threads)
+    return {"value": ev / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{k} of {len(busy)} non-empty tiles (random, seed 0), FP64 blend forward + gradient, "
+                      f"{dt:.1f} s", "seconds": dt}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2604_02120_gb300 import scenes
+    sc = scenes.make_config(args.config, seed=0)
+    cam = sc.cameras[0]
+    W, H = cam.width, cam.height
+    pr = oracle.project(sc.means, sc.scales, sc.quats, sc.sh, sc.sh_degree, cam)
+    bs = oracle.bin_sort(pr["mean2d"], pr["radius"], pr["depth"].astype(np.float32), W, H)
+    dL = scenes.upstream_grad(0, [cam])[0].astype(np.float64)
+    op = sc.opacities.astype(np.float64)
+    threads = os.cpu_count() or 1
+    busy = _busy_tiles(bs["tile_ranges"])
+    order = np.random.default_rng(0).permutation(busy)
+    per_step_s = min(6.0, 150.0 / max(1, args.steps + args.warmup))
+    k = _calibrate(lambda t: _oracle_sample(oracle, W, H, bs["tile_ranges"], bs["ids"], pr["mean2d"], pr["conic"],
+                                            op, pr["rgb"], dL, t, threads)[1], order, threads, per_step_s)
+    evals_total, t_total = 0, 0.0
+    for s in range(args.warmup + args.steps):
+        tiles = np.roll(order, -s * k)[:k]
+        ev, dt = _oracle_sample(oracle, W, H, bs["tile_ranges"], bs["ids"], pr["mean2d"], pr["conic"], op,
+                                pr["rgb"], dL, tiles, threads)
+        if s >= args.warmup:
+            evals_total += ev
+            t_total += dt
+    value = evals_total / t_total
+    sample = f"{k} of {len(busy)} non-empty tiles per step (rotating), FP64 blend forward + gradient"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_total * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "step": "FP64 oracle blend forward + gradient on a tile sample"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,217 @@
+/*
+ * gs.h - C ABI of the GB300 (sm_103a) tile-based Gaussian-splatting library.
+ *
+ * The library implements the rendering pipeline of 3D Gaussian Splatting as the
+ * GEMM-GS paper describes it (Sec. 2.1: preprocessing, duplication, sorting,
+ * blending) with the blending stage evaluated either per pixel on CUDA cores
+ * (Alg. 1) or, following Sec. 3 (Eqs. 4-8, Alg. 2), as a tensor-core
+ * contraction of per-splat coefficient rows v_g against intra-tile pixel
+ * monomials v_p = [xb^2, yb^2, xb*yb, xb, yb, 1], followed by exp, the 1/255
+ * skip, the 0.99 clamp and front-to-back compositing with early termination.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named in a call are DEVICE pointers unless the comment says HOST.
+ *    The caller owns all memory; the library never allocates device memory and
+ *    never frees what it is given.  Scratch space is passed in explicitly
+ *    (gs_bin_sort) after a size query.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the legacy
+ *    default stream) unless its comment says it synchronises.
+ *  - Arrays are dense, row-major, float32 unless stated.  Images are CHW:
+ *    image[c * H * W + y * W + x].
+ *  - Pixel (x, y) covers [x, x+1) x [y, y+1) and is evaluated at its centre
+ *    (x + 0.5, y + 0.5).  Tiles are 16 x 16 pixels; tile t = ty * tiles_x + tx
+ *    with tiles_x = ceil(W / 16), tiles_y = ceil(H / 16).
+ *  - A return other than GS_OK leaves outputs unspecified.  Host-detectable
+ *    errors (bad arguments, launch failures) are returned at once.  Faults the
+ *    kernels detect (a device wait that exceeded its time limit) are recorded
+ *    in a per-device error word that gs_sync_status() reads and clears.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st* gs_stream;
+
+typedef enum gs_status {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1,  /* null pointer, negative size, unknown option */
+    GS_ERR_CUDA = 2,         /* a CUDA runtime call failed; see gs_last_error() */
+    GS_ERR_CAPACITY = 3,     /* duplicated instances exceed the caller's capacity */
+    GS_ERR_TIMEOUT = 4,      /* a device-side wait gave up after its time limit */
+    GS_ERR_UNSUPPORTED = 5,  /* no sm_100-family GPU, or option not built */
+    GS_ERR_WORKSPACE = 6     /* workspace smaller than the size query returned */
+} gs_status;
+
+/* Pinhole camera, OpenCV axes (x right, y down, z forward).
+ * p_cam = R p_world + t with world_to_cam = [R | t] row-major 3 x 4. */
+typedef struct gs_camera {
+    int32_t width, height;  /* pixels, >= 1 */
+    float fx, fy, cx, cy;   /* focal lengths and principal point, pixels */
+    float world_to_cam[12];
+    float znear;            /* splats with camera z <= znear are culled (0.2 typical) */
+    float lowpass;          /* added to both diagonal entries of the 2D covariance (0.3 typical) */
+} gs_camera;
+
+/* Blend arithmetic.  FP32 evaluates Eq. 3 per pixel on CUDA cores; the TC
+ * variants evaluate Eq. 6 for a whole tile as a tcgen05 matrix product with
+ * the given operand type and FP32 accumulation.  _SPLIT variants store v_g as
+ * an unevaluated sum of 2 (fp16) or 3 (bf16) operand-type terms. */
+typedef enum gs_variant {
+    GS_BLEND_FP32 = 0,
+    GS_BLEND_TC_FP16 = 1,
+    GS_BLEND_TC_BF16 = 2,
+    GS_BLEND_TC_FP16_SPLIT = 3,
+    GS_BLEND_TC_BF16_SPLIT = 4
+} gs_variant;
+
+/* Options of the blend calls.  All-zero is valid: FP32 variant, defaults. */
+typedef struct gs_blend_opts {
+    int32_t variant;     /* gs_variant */
+    int32_t chunk;       /* TC: splats per pipeline stage, 32/64/128; 0 = default (32) */
+    int32_t stages;      /* TC: pipeline depth 2..4; 0 = default (2) */
+    int32_t ref_origin;  /* TC: 0 = reference pixel at the tile centre (x0+8, y0+8),
+                            1 = centre of the tile's first pixel (x0+0.5, y0+0.5) */
+    float bg[3];         /* background colour added as T_final * bg */
+    int32_t reserved;
+    int64_t timeout_ns;  /* limit of every device-side wait; 0 = 1 s */
+} gs_blend_opts;
+
+/* Library version (major * 100 + minor). */
+int32_t gs_version(void);
+/* Static text for a status code. */
+const char* gs_status_string(gs_status status);
+/* Text of the last failure on the calling host thread ("" if none). */
+const char* gs_last_error(void);
+
+/*
+ * gs_project - preprocessing stage (Sec. 2.1 (a)): EWA projection of n 3D
+ * Gaussians into one camera.
+ *   means n x 3, scales n x 3 (linear standard deviations), quats n x 4
+ *   (w, x, y, z; normalised inside), sh n x K x 3 with K = (sh_degree + 1)^2,
+ *   sh_degree in 0..3.  `cam` is a HOST pointer.
+ * Per Gaussian g (outputs n x 2, n x 3, n, n, n x 3, n):
+ *   p = R mean + t; culled if p.z <= znear.  Sigma3 = (Rq S)(Rq S)^T;
+ *   J = [[fx/z, 0, -fx x/z^2], [0, fy/z, -fy y/z^2]];
+ *   Sigma2 = (J R) Sigma3 (J R)^T + lowpass I = [[a, b], [b, c]];
+ *   culled if det = ac - b^2 <= 0; conic = (c, -b, a) / det, evaluated in FP64
+ *   when the FP32 det is below 1e-6;  mean2d = (fx x/z + cx, fy y/z + cy),
+ *   culled if either coordinate exceeds 2^23 in magnitude;
+ *   radius = min(ceil(3 sqrt(lambda_max(Sigma2))), 2^24);  depth = p.z;
+ *   rgb = max(0, sum_k sh[g][k] Y_k(d) + 0.5), d = unit(mean - camera centre),
+ *   Y_k the real spherical harmonics (sqrt(2) Re/Im of the complex ones with
+ *   the Condon-Shortley phase, m = -l..l within degree l);
+ *   tiles_touched = number of tiles of the rectangle
+ *   [floor((mx - r)/16), floor((mx + r)/16)] x [same for y] clamped to the grid.
+ * Culled Gaussians get radius 0 and tiles_touched 0.
+ */
+gs_status gs_project(int32_t n, const float* means, const float* scales, const float* quats,
+                     const float* sh, int32_t sh_degree, const gs_camera* cam,
+                     float* mean2d, float* conic, float* depth, int32_t* radius, float* rgb,
+                     uint32_t* tiles_touched, gs_stream stream);
+
+/* Bytes of scratch gs_bin_sort needs for n Gaussians, `capacity` instances and
+ * a width x height image.  `bytes` is a HOST pointer. */
+gs_status gs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t width, int32_t height,
+                                     size_t* bytes);
+
+/*
+ * gs_bin_sort - duplication and sorting stages (Sec. 2.1 (b), (c)).
+ * Every Gaussian with radius > 0 is duplicated once per tile of its rectangle
+ * (the rule of gs_project) with key (tile << 32) | float_bits(depth); the
+ * instances are sorted by key, equal keys in Gaussian-index order (the order a
+ * stable sort of the Gaussian-major, row-major-tile duplication gives).
+ *   keys_sorted[capacity] (u64), ids_sorted[capacity] (u32 Gaussian index),
+ *   tile_ranges[2 * num_tiles] (u32 [start, end) per tile, empty = [0, 0)).
+ *   workspace: device scratch of at least gs_bin_sort_workspace_size() bytes,
+ *   256-byte aligned; its contents on entry do not matter.
+ *   n_instances: HOST pointer, receives the number of instances I.
+ * This call synchronises `stream` once (to read I).  If I > capacity it
+ * returns GS_ERR_CAPACITY with *n_instances = I and writes no sorted output.
+ * Requires capacity < 2^32.
+ */
+gs_status gs_bin_sort(int32_t n, const float* mean2d, const int32_t* radius, const float* depth,
+                      int32_t width, int32_t height, int64_t capacity,
+                      void* workspace, size_t workspace_bytes,
+                      uint64_t* keys_sorted, uint32_t* ids_sorted, uint32_t* tile_ranges,
+                      int64_t* n_instances, gs_stream stream);
+
+/*
+ * gs_blend_forward - blending stage (Eq. 1; Alg. 1 for GS_BLEND_FP32, Alg. 2
+ * with Eqs. 6-8 for the TC variants).  For every pixel, over its tile's list
+ * in order: power = -1/2 (A dx^2 + C dy^2) - B dx dy (dx = mx - x, dy = my - y);
+ * alpha = min(0.99, o exp(min(power, 0))); the splat is skipped if
+ * alpha < 1/255; with T' = T (1 - alpha), compositing stops before the splat
+ * if T' < 1e-4; otherwise C += rgb alpha T and T = T'.
+ *   mean2d n x 2, conic n x 3 (A, B, C), opacity n, rgb n x 3: per Gaussian.
+ *   image 3 x H x W = C + T bg;  T_final H x W;  n_contrib H x W (int32) =
+ *   1 + list position of the last splat added, 0 if none.
+ * `opts` is a HOST pointer (NULL = all defaults).
+ */
+gs_status gs_blend_forward(int32_t width, int32_t height, const uint32_t* tile_ranges,
+                           const uint32_t* ids_sorted, const float* mean2d, const float* conic,
+                           const float* opacity, const float* rgb, const gs_blend_opts* opts,
+                           float* image, float* T_final, int32_t* n_contrib, gs_stream stream);
+
+/*
+ * gs_blend_backward - gradient of the blended image with respect to each
+ * Gaussian's mean2d, conic, opacity and rgb, given dL_dimage (3 x H x W) and
+ * the forward call's T_final and n_contrib.  Each pixel walks its list back to
+ * front from n_contrib - 1, recovering T_i = T_{i+1} / (1 - alpha_i) and the
+ * colour behind splat i, S_i (S = bg after the last splat,
+ * S_{i-1} = alpha_i c_i + (1 - alpha_i) S_i):
+ *   dL/dc_i = alpha_i T_i g,  dL/dalpha_i = T_i (c_i - S_i) . g,
+ *   dalpha/do = e^p and dalpha/dp = alpha (both 0 where the 0.99 clamp holds),
+ *   dp/dmx = -(A dx + B dy), dp/dmy = -(B dx + C dy),
+ *   dp/dA = -dx^2/2, dp/dB = -dx dy, dp/dC = -dy^2/2.
+ * alpha is recomputed with the FP32 arithmetic of GS_BLEND_FP32 whatever
+ * opts->variant is.  Gradients are ADDED (atomically) to dmean2d n x 2,
+ * dconic n x 3, dopacity n, drgb n x 3: zero them first.
+ */
+gs_status gs_blend_backward(int32_t width, int32_t height, const uint32_t* tile_ranges,
+                            const uint32_t* ids_sorted, const float* mean2d, const float* conic,
+                            const float* opacity, const float* rgb, const gs_blend_opts* opts,
+                            const float* T_final, const int32_t* n_contrib, const float* dL_dimage,
+                            float* dmean2d, float* dconic, float* dopacity, float* drgb,
+                            gs_stream stream);
+
+/*
+ * gs_tile_power - the exponent matrix M_power = M_g . M_p of Eq. 8 exactly as a
+ * TC variant's blend computes it, for inspection and testing.  For each of the
+ * n_tiles tiles in `tiles` (device int32), every list position j < max_len and
+ * tile pixel p = 16 * row + col: out[(i * max_len + j) * 256 + p] =
+ * log2(e) * power + log2(opacity), the base-2 exponent the blend feeds to exp2.
+ * Positions past a tile's list are left untouched.  opts->variant must be a
+ * TC variant.
+ */
+gs_status gs_tile_power(int32_t width, int32_t height, const uint32_t* tile_ranges,
+                        const uint32_t* ids_sorted, const float* mean2d, const float* conic,
+                        const float* opacity, const gs_blend_opts* opts, const int32_t* tiles,
+                        int32_t n_tiles, int32_t max_len, float* out, gs_stream stream);
+
+/* Number of kernels this library has launched in the calling process (all
+ * devices, all host threads), for accounting of GPU work. */
+int64_t gs_launch_count(void);
+
+/* Synchronise `stream`, then return and clear the device error word of the
+ * current device: GS_ERR_TIMEOUT if a kernel's bounded wait gave up since the
+ * last call, else GS_OK (or GS_ERR_CUDA if synchronising failed). */
+gs_status gs_sync_status(gs_stream stream);
+
+/* Self-test of the bounded device wait used by the tensor-core pipeline: one
+ * CTA waits on an mbarrier that nothing ever arrives on, gives up after
+ * timeout_ns (capped at 1 s) and records GS_ERR_TIMEOUT in the error word,
+ * which gs_sync_status() then returns. */
+gs_status gs_selftest_bounded_wait(int64_t timeout_ns, gs_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H */

@@ -151,13 +151,15 @@ def brute_force(mean2d, conic, opac, rgb, radius, depth, width, height, bg=(0.0,
 
 
 def blend_grad(width, height, tile_ranges, ids, mean2d, conic, opac, rgb, dL_dimage,
-               bg=(0.0, 0.0, 0.0)) -> dict:
+               bg=(0.0, 0.0, 0.0), n_threads=1, tile_subset=None) -> dict:
     n = int(np.asarray(mean2d).shape[0])
     out = dict(mean2d=np.zeros((n, 2)), conic=np.zeros((n, 3)), opacity=np.zeros(n), rgb=np.zeros((n, 3)))
+    subset = None if tile_subset is None else _c(tile_subset, np.int32)
     lib().oracle_blend_grad(
         ctypes.c_int(width), ctypes.c_int(height), _p(_c(tile_ranges, np.uint32)), _p(_c(ids, np.uint32)),
         _p(_c(mean2d, np.float64)), _p(_c(conic, np.float64)), _p(_c(opac, np.float64)),
-        _p(_c(rgb, np.float64)), _p(_c(bg, np.float64)), _p(_c(dL_dimage, np.float64)),
+        _p(_c(rgb, np.float64)), _p(_c(bg, np.float64)), _p(_c(dL_dimage, np.float64)), ctypes.c_int(n),
+        ctypes.c_int(n_threads), _p(subset), ctypes.c_int(0 if subset is None else len(subset)),
         _p(out["mean2d"]), _p(out["conic"]), _p(out["opacity"]), _p(out["rgb"]))
     return out
 

@@ -407,13 +407,29 @@ void oracle_brute_force(int n, const double* mean2d, const double* conic, const 
 // alpha = o e^p (unclamped branch): dalpha/do = e^p, dalpha/dp = alpha; both
 // zero when the 0.99 clamp is active; dp/d* = 0 when power > 0 was clamped.
 // Outputs are accumulated into the caller's zeroed arrays.
+// Tiles are spread over n_threads threads, each accumulating into buffers of
+// its own; the buffers are summed in thread order at the end (so the result
+// is deterministic for a given thread count).  tile_subset, if given, limits
+// the work to those tiles.
 void oracle_blend_grad(int W, int H, const uint32_t* tile_ranges, const uint32_t* ids,
                        const double* mean2d, const double* conic, const double* opac,
-                       const double* rgb, const double* bg, const double* dL_dimg,
-                       double* dmean2d, double* dconic, double* dopac, double* drgb) {
+                       const double* rgb, const double* bg, const double* dL_dimg, int n_gauss,
+                       int n_threads, const int32_t* tile_subset, int n_subset,
+                       double* dmean2d_out, double* dconic_out, double* dopac_out, double* drgb_out) {
     const int tx = tiles_x(W);
     const int ntiles = tx * tiles_y(H);
-    for (int t = 0; t < ntiles; ++t) {
+    const int count = tile_subset ? n_subset : ntiles;
+    const int nt = std::max(1, std::min(n_threads, count));
+    std::vector<std::vector<double>> acc(nt, std::vector<double>(9 * (size_t)n_gauss, 0.0));
+    std::vector<std::thread> pool;
+    for (int k = 0; k < nt; ++k)
+        pool.emplace_back([&, k]() {
+            double* dmean2d = acc[k].data();
+            double* dconic = dmean2d + 2 * (size_t)n_gauss;
+            double* dopac = dconic + 3 * (size_t)n_gauss;
+            double* drgb = dopac + (size_t)n_gauss;
+            for (int idx = k; idx < count; idx += nt) {
+        int t = tile_subset ? tile_subset[idx] : idx;
         int x0 = (t % tx) * kTile, y0 = (t / tx) * kTile;
         for (int py = y0; py < std::min(y0 + kTile, H); ++py)
             for (int px = x0; px < std::min(x0 + kTile, W); ++px) {
@@ -469,6 +485,15 @@ void oracle_blend_grad(int W, int H, const uint32_t* tile_ranges, const uint32_t
                     dconic[3 * (size_t)r.g + 2] += dL_dp * (-0.5 * dy * dy);
                 }
             }
+            }
+        });
+    for (auto& th : pool) th.join();
+    for (int k = 0; k < nt; ++k) {
+        const double* a = acc[k].data();
+        for (size_t i = 0; i < 2 * (size_t)n_gauss; ++i) dmean2d_out[i] += a[i];
+        for (size_t i = 0; i < 3 * (size_t)n_gauss; ++i) dconic_out[i] += a[2 * (size_t)n_gauss + i];
+        for (size_t i = 0; i < (size_t)n_gauss; ++i) dopac_out[i] += a[5 * (size_t)n_gauss + i];
+        for (size_t i = 0; i < 3 * (size_t)n_gauss; ++i) drgb_out[i] += a[6 * (size_t)n_gauss + i];
     }
 }
 

@@ -1,0 +1,223 @@
+// CUDA-core blending (Alg. 1) and its gradient.  One 256-thread block per
+// 16 x 16 tile, one thread per pixel; the tile's list is staged through shared
+// memory in batches of 256 splats (Sec. 2.1 (d)).  The exponent is evaluated
+// per pixel as the quadratic of Eq. 3 in FP32.
+#include "internal.h"
+
+namespace gs {
+namespace {
+
+constexpr int kBatch = 256;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+
+struct SplatSm {
+    float4 geo;  // mx, my, A, B
+    float4 oc;   // C, o, r, g
+    float b;
+};
+
+// alpha of a splat at a pixel; `e` receives exp(min(power, 0)) and `pw` power.
+// Shared by the forward and backward kernels so both take identical decisions.
+__device__ __forceinline__ float splat_alpha(const float4& geo, const float4& oc, float xp, float yp, float& e,
+                                             float& pw, float& dx, float& dy) {
+    dx = geo.x - xp;
+    dy = geo.y - yp;
+    const float q = __fmaf_rn(geo.z * dx, dx, __fmul_rn(oc.x * dy, dy));
+    pw = __fmaf_rn(-geo.w * dx, dy, -0.5f * q);
+    e = __expf(fminf(pw, 0.0f));
+    return fminf(kAlphaMax, oc.y * e);
+}
+
+__device__ __forceinline__ void load_splat(const BlendArgs& a, uint32_t g, SplatSm& s) {
+    const float2 m = a.mean2d[g];
+    s.geo = make_float4(m.x, m.y, a.conic[3 * g], a.conic[3 * g + 1]);
+    s.oc = make_float4(a.conic[3 * g + 2], a.opac[g], a.rgb[3 * g], a.rgb[3 * g + 1]);
+    s.b = a.rgb[3 * g + 2];
+}
+
+__global__ void __launch_bounds__(kBatch) k_blend_fp32_fwd(BlendArgs a) {
+    __shared__ float4 s_geo[kBatch];
+    __shared__ float4 s_oc[kBatch];
+    __shared__ float s_b[kBatch];
+    const int tile = blockIdx.x;
+    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int px = tx * kTile + (threadIdx.x & 15), py = ty * kTile + (threadIdx.x >> 4);
+    const bool inside = px < a.W && py < a.H;
+    const float xp = px + 0.5f, yp = py + 0.5f;
+    const uint32_t start = a.ranges[2 * tile], end = a.ranges[2 * tile + 1];
+    const int len = end > start ? (int)(end - start) : 0;
+
+    float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    int last = 0;
+    bool done = !inside;
+    for (int base = 0; base < len; base += kBatch) {
+        if (__syncthreads_count(done) == kBatch) break;
+        const int i = base + threadIdx.x;
+        if (i < len) {
+            SplatSm s;
+            load_splat(a, a.ids[start + i], s);
+            s_geo[threadIdx.x] = s.geo;
+            s_oc[threadIdx.x] = s.oc;
+            s_b[threadIdx.x] = s.b;
+        }
+        __syncthreads();
+        const int nb = min(kBatch, len - base);
+        for (int j = 0; !done && j < nb; ++j) {
+            const float4 geo = s_geo[j], oc = s_oc[j];
+            float e, pw, dx, dy;
+            const float alpha = splat_alpha(geo, oc, xp, yp, e, pw, dx, dy);
+            if (alpha < kAlphaMin) continue;
+            const float tT = T * (1.0f - alpha);
+            if (tT < kTMin) {
+                done = true;
+                break;
+            }
+            const float w = alpha * T;
+            C0 = __fmaf_rn(oc.z, w, C0);
+            C1 = __fmaf_rn(oc.w, w, C1);
+            C2 = __fmaf_rn(s_b[j], w, C2);
+            T = tT;
+            last = base + j + 1;
+        }
+    }
+    if (inside) {
+        const size_t pix = (size_t)py * a.W + px, plane = (size_t)a.W * a.H;
+        a.image[pix] = C0 + T * a.bg[0];
+        a.image[plane + pix] = C1 + T * a.bg[1];
+        a.image[2 * plane + pix] = C2 + T * a.bg[2];
+        a.T_final[pix] = T;
+        a.n_contrib[pix] = last;
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Back-to-front walk per pixel; per (splat, warp) the nine gradient values are
+// reduced across the warp and added with one atomic each.
+__global__ void __launch_bounds__(kBatch) k_blend_fp32_bwd(BlendArgs a, GradArgs gr) {
+    __shared__ float4 s_geo[kBatch];
+    __shared__ float4 s_oc[kBatch];
+    __shared__ float s_b[kBatch];
+    __shared__ uint32_t s_id[kBatch];
+    __shared__ int s_max;
+    const int tile = blockIdx.x;
+    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int px = tx * kTile + (threadIdx.x & 15), py = ty * kTile + (threadIdx.x >> 4);
+    const bool inside = px < a.W && py < a.H;
+    const float xp = px + 0.5f, yp = py + 0.5f;
+    const uint32_t start = a.ranges[2 * tile];
+    const int lane = threadIdx.x & 31;
+
+    const size_t pix = (size_t)py * a.W + px, plane = (size_t)a.W * a.H;
+    int nc = 0;
+    float T = 1.0f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    if (inside) {
+        nc = gr.n_contrib[pix];
+        T = gr.T_final[pix];
+        g0 = gr.dL_dimage[pix];
+        g1 = gr.dL_dimage[plane + pix];
+        g2 = gr.dL_dimage[2 * plane + pix];
+    }
+    float S0 = a.bg[0], S1 = a.bg[1], S2 = a.bg[2];  // colour behind the current splat
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    atomicMax(&s_max, nc);
+    __syncthreads();
+    const int maxn = s_max;
+
+    for (int hi = maxn; hi > 0; hi -= kBatch) {
+        const int lo = max(0, hi - kBatch);
+        __syncthreads();
+        const int i = lo + threadIdx.x;
+        if (i < hi) {
+            const uint32_t g = a.ids[start + i];
+            SplatSm s;
+            load_splat(a, g, s);
+            s_geo[threadIdx.x] = s.geo;
+            s_oc[threadIdx.x] = s.oc;
+            s_b[threadIdx.x] = s.b;
+            s_id[threadIdx.x] = g;
+        }
+        __syncthreads();
+        for (int j = hi - 1; j >= lo; --j) {
+            const int k = j - lo;
+            const float4 geo = s_geo[k], oc = s_oc[k];
+            const float cb = s_b[k];
+            float dm0 = 0.f, dm1 = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dO = 0.f, dc0 = 0.f, dc1 = 0.f, dc2 = 0.f;
+            bool contrib = false;
+            if (j < nc) {
+                float e, pw, dx, dy;
+                const float alpha = splat_alpha(geo, oc, xp, yp, e, pw, dx, dy);
+                if (alpha >= kAlphaMin) {
+                    contrib = true;
+                    const float Ti = T / (1.0f - alpha);
+                    const float wgt = alpha * Ti;
+                    dc0 = wgt * g0;
+                    dc1 = wgt * g1;
+                    dc2 = wgt * g2;
+                    const float dL_dalpha = Ti * ((oc.z - S0) * g0 + (oc.w - S1) * g1 + (cb - S2) * g2);
+                    S0 = alpha * oc.z + (1.0f - alpha) * S0;
+                    S1 = alpha * oc.w + (1.0f - alpha) * S1;
+                    S2 = alpha * cb + (1.0f - alpha) * S2;
+                    T = Ti;
+                    if (oc.y * e <= kAlphaMax) {  // not clamped
+                        dO = dL_dalpha * e;
+                        if (pw <= 0.0f) {
+                            const float dp = dL_dalpha * alpha;
+                            dm0 = -dp * (geo.z * dx + geo.w * dy);
+                            dm1 = -dp * (geo.w * dx + oc.x * dy);
+                            dA = -0.5f * dp * dx * dx;
+                            dB = -dp * dx * dy;
+                            dC = -0.5f * dp * dy * dy;
+                        }
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+                dm0 = warp_sum(dm0);
+                dm1 = warp_sum(dm1);
+                dA = warp_sum(dA);
+                dB = warp_sum(dB);
+                dC = warp_sum(dC);
+                dO = warp_sum(dO);
+                dc0 = warp_sum(dc0);
+                dc1 = warp_sum(dc1);
+                dc2 = warp_sum(dc2);
+                if (lane == 0) {
+                    const uint32_t g = s_id[k];
+                    atomicAdd(&gr.dmean2d[g].x, dm0);
+                    atomicAdd(&gr.dmean2d[g].y, dm1);
+                    atomicAdd(&gr.dconic[3 * g], dA);
+                    atomicAdd(&gr.dconic[3 * g + 1], dB);
+                    atomicAdd(&gr.dconic[3 * g + 2], dC);
+                    atomicAdd(&gr.dopac[g], dO);
+                    atomicAdd(&gr.drgb[3 * g], dc0);
+                    atomicAdd(&gr.drgb[3 * g + 1], dc1);
+                    atomicAdd(&gr.drgb[3 * g + 2], dc2);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_blend_fp32_fwd(const BlendArgs& a, cudaStream_t s) {
+    k_blend_fp32_fwd<<<a.num_tiles, kBatch, 0, s>>>(a);
+    count_launches();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blend_fp32_bwd(const BlendArgs& a, const GradArgs& g, cudaStream_t s) {
+    k_blend_fp32_bwd<<<a.num_tiles, kBatch, 0, s>>>(a, g);
+    count_launches();
+    return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -1,0 +1,309 @@
+"""Python binding of the C ABI in include/gs.h (ctypes; argument marshalling only).
+
+Every function named gs_* here calls the C entry point of the same name with
+raw device pointers taken from torch tensors; all computation runs in the
+CUDA library ``libgs.so`` built in-tree by ``paper_2604_02120_gb300/build.py``.
+There is no fallback: if the library is missing or fails to load, the calls
+raise.  PyTorch provides device memory and the current CUDA stream only.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgs.so")
+
+GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CUDA, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, GS_ERR_UNSUPPORTED, GS_ERR_WORKSPACE = range(7)
+GS_BLEND_FP32, GS_BLEND_TC_FP16, GS_BLEND_TC_BF16, GS_BLEND_TC_FP16_SPLIT, GS_BLEND_TC_BF16_SPLIT = range(5)
+VARIANTS = {
+    "fp32": GS_BLEND_FP32, "fp16": GS_BLEND_TC_FP16, "bf16": GS_BLEND_TC_BF16,
+    "fp16_split": GS_BLEND_TC_FP16_SPLIT, "bf16_split": GS_BLEND_TC_BF16_SPLIT,
+}
+
+# Entry points declared in include/gs.h
+ABI_FUNCTIONS = (
+    "gs_version", "gs_status_string", "gs_last_error", "gs_project", "gs_bin_sort_workspace_size",
+    "gs_bin_sort", "gs_blend_forward", "gs_blend_backward", "gs_tile_power", "gs_sync_status",
+    "gs_selftest_bounded_wait", "gs_launch_count",
+)
+
+
+class GsError(RuntimeError):
+    def __init__(self, status: int, where: str, text: str):
+        super().__init__(f"{where}: status {status} ({text})")
+        self.status = status
+
+
+class gs_camera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("world_to_cam", ctypes.c_float * 12), ("znear", ctypes.c_float), ("lowpass", ctypes.c_float)]
+
+
+class gs_blend_opts(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("chunk", ctypes.c_int32), ("stages", ctypes.c_int32),
+                ("ref_origin", ctypes.c_int32), ("bg", ctypes.c_float * 3), ("reserved", ctypes.c_int32),
+                ("timeout_ns", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libgs.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    lib.gs_version.restype = i32
+    lib.gs_launch_count.restype = i64
+    lib.gs_status_string.restype = ctypes.c_char_p
+    lib.gs_status_string.argtypes = [ctypes.c_int]
+    lib.gs_last_error.restype = ctypes.c_char_p
+    lib.gs_project.argtypes = [i32, vp, vp, vp, vp, i32, ctypes.POINTER(gs_camera), vp, vp, vp, vp, vp, vp, vp]
+    lib.gs_bin_sort_workspace_size.argtypes = [i32, i64, i32, i32, ctypes.POINTER(sz)]
+    lib.gs_bin_sort.argtypes = [i32, vp, vp, vp, i32, i32, i64, vp, sz, vp, vp, vp, ctypes.POINTER(i64), vp]
+    lib.gs_blend_forward.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(gs_blend_opts), vp, vp, vp, vp]
+    lib.gs_blend_backward.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(gs_blend_opts), vp, vp, vp,
+                                      vp, vp, vp, vp, vp]
+    lib.gs_tile_power.argtypes = [i32, i32, vp, vp, vp, vp, vp, ctypes.POINTER(gs_blend_opts), vp, i32, i32, vp, vp]
+    lib.gs_sync_status.argtypes = [vp]
+    lib.gs_selftest_bounded_wait.argtypes = [i64, vp]
+    for name in ABI_FUNCTIONS:
+        if name not in ("gs_version", "gs_status_string", "gs_last_error", "gs_launch_count"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(st: int, where: str):
+    if st != GS_OK:
+        lib = load()
+        raise GsError(st, where, f"{lib.gs_status_string(st).decode()}; {lib.gs_last_error().decode()}")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_camera(cam) -> gs_camera:
+    """gs_camera from any object with width, height, fx, fy, cx, cy, R, t, znear, lowpass."""
+    c = gs_camera()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    for i in range(3):
+        for j in range(3):
+            c.world_to_cam[4 * i + j] = float(cam.R[i][j])
+        c.world_to_cam[4 * i + 3] = float(cam.t[i])
+    c.znear, c.lowpass = float(cam.znear), float(cam.lowpass)
+    return c
+
+
+def make_opts(variant="fp32", chunk=0, stages=0, ref_origin=0, bg=(0.0, 0.0, 0.0), timeout_ns=0) -> gs_blend_opts:
+    o = gs_blend_opts()
+    o.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    o.chunk, o.stages, o.ref_origin = int(chunk), int(stages), int(ref_origin)
+    for i in range(3):
+        o.bg[i] = float(bg[i])
+    o.timeout_ns = int(timeout_ns)
+    return o
+
+
+# ------------------------------------------------------------- raw entry points
+
+def gs_version() -> int:
+    return int(load().gs_version())
+
+
+def gs_launch_count() -> int:
+    return int(load().gs_launch_count())
+
+
+def gs_project(n, means, scales, quats, sh, sh_degree, cam, mean2d, conic, depth, radius, rgb, tiles_touched,
+               stream=None):
+    camera = cam if isinstance(cam, gs_camera) else make_camera(cam)
+    _check(load().gs_project(n, _ptr(means), _ptr(scales), _ptr(quats), _ptr(sh), sh_degree, ctypes.byref(camera),
+                             _ptr(mean2d), _ptr(conic), _ptr(depth), _ptr(radius), _ptr(rgb), _ptr(tiles_touched),
+                             _stream(stream)), "gs_project")
+
+
+def gs_bin_sort_workspace_size(n, capacity, width, height) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().gs_bin_sort_workspace_size(n, capacity, width, height, ctypes.byref(out)),
+           "gs_bin_sort_workspace_size")
+    return int(out.value)
+
+
+def gs_bin_sort(n, mean2d, radius, depth, width, height, capacity, workspace, keys_sorted, ids_sorted, tile_ranges,
+                stream=None, check=True):
+    """Returns (status, n_instances)."""
+    count = ctypes.c_int64(0)
+    st = load().gs_bin_sort(n, _ptr(mean2d), _ptr(radius), _ptr(depth), width, height, capacity, _ptr(workspace),
+                            workspace.numel() * workspace.element_size() if workspace is not None else 0,
+                            _ptr(keys_sorted), _ptr(ids_sorted), _ptr(tile_ranges), ctypes.byref(count),
+                            _stream(stream))
+    if check:
+        _check(st, "gs_bin_sort")
+    return st, int(count.value)
+
+
+def gs_blend_forward(width, height, tile_ranges, ids_sorted, mean2d, conic, opacity, rgb, opts, image, T_final,
+                     n_contrib, stream=None):
+    _check(load().gs_blend_forward(width, height, _ptr(tile_ranges), _ptr(ids_sorted), _ptr(mean2d), _ptr(conic),
+                                   _ptr(opacity), _ptr(rgb), ctypes.byref(opts), _ptr(image), _ptr(T_final),
+                                   _ptr(n_contrib), _stream(stream)), "gs_blend_forward")
+
+
+def gs_blend_backward(width, height, tile_ranges, ids_sorted, mean2d, conic, opacity, rgb, opts, T_final, n_contrib,
+                      dL_dimage, dmean2d, dconic, dopacity, drgb, stream=None):
+    _check(load().gs_blend_backward(width, height, _ptr(tile_ranges), _ptr(ids_sorted), _ptr(mean2d), _ptr(conic),
+                                    _ptr(opacity), _ptr(rgb), ctypes.byref(opts), _ptr(T_final), _ptr(n_contrib),
+                                    _ptr(dL_dimage), _ptr(dmean2d), _ptr(dconic), _ptr(dopacity), _ptr(drgb),
+                                    _stream(stream)), "gs_blend_backward")
+
+
+def gs_tile_power(width, height, tile_ranges, ids_sorted, mean2d, conic, opacity, opts, tiles, max_len, out,
+                  stream=None):
+    _check(load().gs_tile_power(width, height, _ptr(tile_ranges), _ptr(ids_sorted), _ptr(mean2d), _ptr(conic),
+                                _ptr(opacity), ctypes.byref(opts), _ptr(tiles), int(tiles.numel()), int(max_len),
+                                _ptr(out), _stream(stream)), "gs_tile_power")
+
+
+def gs_sync_status(stream=None) -> int:
+    return int(load().gs_sync_status(_stream(stream)))
+
+
+def gs_selftest_bounded_wait(timeout_ns, stream=None):
+    _check(load().gs_selftest_bounded_wait(int(timeout_ns), _stream(stream)), "gs_selftest_bounded_wait")
+
+
+# ------------------------------------------------------------ tensor helpers
+
+def num_tiles(width, height):
+    return ((width + 15) // 16) * ((height + 15) // 16)
+
+
+def project(means, scales, quats, sh, sh_degree, cam, stream=None) -> dict:
+    n = means.shape[0]
+    dev = means.device
+    f32 = dict(device=dev, dtype=torch.float32)
+    out = dict(mean2d=torch.empty(n, 2, **f32), conic=torch.empty(n, 3, **f32), depth=torch.empty(n, **f32),
+               radius=torch.empty(n, device=dev, dtype=torch.int32), rgb=torch.empty(n, 3, **f32),
+               tiles_touched=torch.empty(n, device=dev, dtype=torch.int32))
+    gs_project(n, means, scales, quats, sh, sh_degree, cam, out["mean2d"], out["conic"], out["depth"],
+               out["radius"], out["rgb"], out["tiles_touched"], stream)
+    return out
+
+
+class BinSorter:
+    """Holds the workspace and output buffers of gs_bin_sort for a capacity,
+    growing them when an instance count exceeds it."""
+
+    def __init__(self, device, capacity=1 << 20):
+        self.device = device
+        self.capacity = 0
+        self.n = -1
+        self.width = self.height = 0
+        self._alloc(capacity)
+
+    def _alloc(self, capacity):
+        self.capacity = int(capacity)
+        self.keys = torch.empty(max(self.capacity, 1), device=self.device, dtype=torch.int64)
+        self.ids = torch.empty(max(self.capacity, 1), device=self.device, dtype=torch.int32)
+        self.workspace = None
+
+    def _ensure_ws(self, n, width, height):
+        need = gs_bin_sort_workspace_size(n, self.capacity, width, height)
+        if self.workspace is None or self.workspace.numel() < need:
+            self.workspace = torch.empty(need + 256, device=self.device, dtype=torch.uint8)
+
+    def run(self, mean2d, radius, depth, width, height, stream=None):
+        n = mean2d.shape[0]
+        ranges = torch.empty(2 * num_tiles(width, height), device=self.device, dtype=torch.int32)
+        for _ in range(2):
+            self._ensure_ws(n, width, height)
+            st, count = gs_bin_sort(n, mean2d, radius, depth, width, height, self.capacity, self.workspace,
+                                    self.keys, self.ids, ranges, stream, check=False)
+            if st == GS_ERR_CAPACITY:
+                self._alloc(int(count * 1.25) + 1024)
+                continue
+            _check(st, "gs_bin_sort")
+            return dict(keys=self.keys[:count], ids=self.ids[:count], tile_ranges=ranges, n_instances=count)
+        raise GsError(GS_ERR_CAPACITY, "gs_bin_sort", "capacity growth failed")
+
+
+def blend_forward(width, height, bs, proj, opacity, opts, stream=None) -> dict:
+    dev = opacity.device
+    image = torch.empty(3, height, width, device=dev, dtype=torch.float32)
+    T = torch.empty(height, width, device=dev, dtype=torch.float32)
+    nc = torch.empty(height, width, device=dev, dtype=torch.int32)
+    gs_blend_forward(width, height, bs["tile_ranges"], bs["ids"], proj["mean2d"], proj["conic"], opacity,
+                     proj["rgb"], opts, image, T, nc, stream)
+    return dict(image=image, T_final=T, n_contrib=nc)
+
+
+def blend_backward(width, height, bs, proj, opacity, opts, fwd, dL_dimage, stream=None) -> dict:
+    n = opacity.shape[0]
+    dev = opacity.device
+    g = dict(mean2d=torch.zeros(n, 2, device=dev), conic=torch.zeros(n, 3, device=dev),
+             opacity=torch.zeros(n, device=dev), rgb=torch.zeros(n, 3, device=dev))
+    gs_blend_backward(width, height, bs["tile_ranges"], bs["ids"], proj["mean2d"], proj["conic"], opacity,
+                      proj["rgb"], opts, fwd["T_final"], fwd["n_contrib"], dL_dimage.contiguous(), g["mean2d"],
+                      g["conic"], g["opacity"], g["rgb"], stream)
+    return g
+
+
+class BlendFunction(torch.autograd.Function):
+    """Differentiable blend: (mean2d, conic, opacity, rgb) -> image, with the
+    tile lists fixed by a preceding gs_bin_sort."""
+
+    @staticmethod
+    def forward(ctx, mean2d, conic, opacity, rgb, tile_ranges, ids, width, height, opts):
+        proj = dict(mean2d=mean2d.contiguous(), conic=conic.contiguous(), rgb=rgb.contiguous())
+        bs = dict(tile_ranges=tile_ranges, ids=ids)
+        out = blend_forward(width, height, bs, proj, opacity.contiguous(), opts)
+        ctx.save_for_backward(proj["mean2d"], proj["conic"], opacity.contiguous(), proj["rgb"], tile_ranges, ids,
+                              out["T_final"], out["n_contrib"])
+        ctx.meta = (width, height, opts)
+        ctx.mark_non_differentiable(out["T_final"], out["n_contrib"])
+        return out["image"], out["T_final"], out["n_contrib"]
+
+    @staticmethod
+    def backward(ctx, dimage, _dT, _dn):
+        mean2d, conic, opacity, rgb, ranges, ids, T, nc = ctx.saved_tensors
+        width, height, opts = ctx.meta
+        g = blend_backward(width, height, dict(tile_ranges=ranges, ids=ids),
+                           dict(mean2d=mean2d, conic=conic, rgb=rgb), opacity, opts,
+                           dict(T_final=T, n_contrib=nc), dimage)
+        return g["mean2d"], g["conic"], g["opacity"], g["rgb"], None, None, None, None, None
+
+
+def scene_to_device(scene, device="cuda") -> dict:
+    t = lambda a: torch.from_numpy(a).to(device).contiguous()  # noqa: E731
+    return dict(means=t(scene.means), scales=t(scene.scales), quats=t(scene.quats), opacities=t(scene.opacities),
+                sh=t(scene.sh), sh_degree=scene.sh_degree)
+
+
+def render(dev_scene, cam, opts, sorter: BinSorter | None = None, stream=None) -> dict:
+    """project -> bin_sort -> blend_forward for one camera."""
+    proj = project(dev_scene["means"], dev_scene["scales"], dev_scene["quats"], dev_scene["sh"],
+                   dev_scene["sh_degree"], cam, stream)
+    sorter = sorter or BinSorter(dev_scene["means"].device)
+    bs = sorter.run(proj["mean2d"], proj["radius"], proj["depth"], cam.width, cam.height, stream)
+    out = blend_forward(cam.width, cam.height, bs, proj, dev_scene["opacities"], opts, stream)
+    return dict(project=proj, bin_sort=bs, blend=out)

@@ -1,0 +1,54 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C ABI
+(binding in paper_2604_02120_gb300.gs) and the FP64 oracle on the same seeded
+inputs."""
+import os
+
+import numpy as np
+import torch
+
+import oracle
+from paper_2604_02120_gb300 import gs, scenes
+
+CORES = os.cpu_count() or 4
+
+
+def gpu_pipeline(scene, cam_index=0, capacity=1 << 20):
+    dev = gs.scene_to_device(scene)
+    cam = scene.cameras[cam_index]
+    proj = gs.project(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam)
+    sorter = gs.BinSorter("cuda", capacity)
+    bs = sorter.run(proj["mean2d"], proj["radius"], proj["depth"], cam.width, cam.height)
+    torch.cuda.synchronize()
+    return dev, cam, proj, bs
+
+
+def to_np(d):
+    return {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in d.items()}
+
+
+def oracle_blend_on_gpu_params(cam, proj_np, bs_np, opac, bg=(0.0, 0.0, 0.0), alpha_margin=1e-4, t_margin=1e-4,
+                               tile_subset=None):
+    """Oracle blend over the GPU's sorted lists and FP32 splat parameters (cast to double)."""
+    return oracle.blend(cam.width, cam.height, bs_np["tile_ranges"].view(np.uint32),
+                        bs_np["ids"].view(np.uint32), proj_np["mean2d"].astype(np.float64),
+                        proj_np["conic"].astype(np.float64), np.asarray(opac, np.float64),
+                        proj_np["rgb"].astype(np.float64), bg=bg, alpha_margin=alpha_margin, t_margin=t_margin,
+                        n_threads=CORES, tile_subset=tile_subset)
+
+
+def blend_gpu(cam, proj, bs, opac, variant="fp32", bg=(0.0, 0.0, 0.0), chunk=0, stages=0, ref_origin=0):
+    opts = gs.make_opts(variant, chunk=chunk, stages=stages, ref_origin=ref_origin, bg=bg)
+    out = gs.blend_forward(cam.width, cam.height, bs, proj, opac, opts)
+    st = gs.gs_sync_status()
+    assert st == gs.GS_OK, f"device status {st}"
+    return to_np(out)
+
+
+def pixel_mask_tiles(cam, tiles):
+    """Boolean H x W mask of the pixels of the given tiles."""
+    m = np.zeros((cam.height, cam.width), bool)
+    tx = cam.tiles_x
+    for t in tiles:
+        x0, y0 = 16 * (t % tx), 16 * (t // tx)
+        m[y0:y0 + 16, x0:x0 + 16] = True
+    return m

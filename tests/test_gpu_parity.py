@@ -1,0 +1,326 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: duplication/sort bit-exact; projection within FP32 rounding; FP32 blend
+within 1e-4 max abs per channel with identical n_contrib on every pixel whose
+decisions are not within rounding of a threshold; tensor-core split variants
+keep the exponent error of every pair that can contribute under 2e-3
+(natural-log units).  Sizes span several tiles, ragged image edges and the
+full 1280x720 / 200k-Gaussian workload."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2604_02120_gb300 import gs, scenes
+
+from gpu_common import CORES, blend_gpu, gpu_pipeline, oracle_blend_on_gpu_params, to_np
+
+pytestmark = pytest.mark.gpu
+
+LOG2E = 1.4426950408889634
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    gs.load()
+
+
+def _scene(kind):
+    if kind == "c0":
+        return scenes.make_config(0)
+    if kind == "c1":
+        return scenes.make_config(1)
+    if kind == "c1_small":
+        return scenes.make_config(1, n=20_000)
+    if kind == "tiny_ragged":
+        return scenes.tiny_scene(3, n=96, width=77, height=45, sh_degree=2)
+    if kind == "tiny_dense":
+        return scenes.tiny_scene(8, n=600, width=64, height=48, sh_degree=3, scale_lo=-2.5, scale_hi=-1.2)
+    raise KeyError(kind)
+
+
+_cache = {}
+
+
+def pipeline(kind):
+    if kind not in _cache:
+        sc = _scene(kind)
+        dev, cam, proj, bs = gpu_pipeline(sc)
+        _cache[kind] = (sc, dev, cam, proj, bs, to_np(proj), to_np(bs))
+    return _cache[kind]
+
+
+# --------------------------------------------------------------- self test --
+
+def test_bounded_wait_reports_timeout():
+    assert gs.gs_sync_status() == gs.GS_OK
+    gs.gs_selftest_bounded_wait(2_000_000)  # 2 ms on an mbarrier nothing arrives on
+    assert gs.gs_sync_status() == gs.GS_ERR_TIMEOUT
+    assert gs.gs_sync_status() == gs.GS_OK  # cleared by the read
+
+
+# -------------------------------------------------------------- projection --
+
+@pytest.mark.parametrize("kind", ["c0", "tiny_ragged", "tiny_dense", "c1"])
+def test_project_matches_oracle(kind):
+    sc, dev, cam, proj, bs, pn, _ = pipeline(kind)
+    ref = oracle.project(sc.means, sc.scales, sc.quats, sc.sh, sc.sh_degree, cam)
+    np.testing.assert_allclose(pn["depth"], ref["depth"], rtol=1e-6, atol=1e-6)
+    live_ref = ref["radius"] > 0
+    live_gpu = pn["radius"] > 0
+    # radius / culling may differ only where the FP64 3 sqrt(lambda) is within
+    # 1e-4 of an integer boundary or the rectangle edge test is marginal
+    lam = 0.5 * (ref["cov2d"][:, 0] + ref["cov2d"][:, 2]) + np.sqrt(
+        np.maximum(0, 0.25 * (ref["cov2d"][:, 0] - ref["cov2d"][:, 2]) ** 2 + ref["cov2d"][:, 1] ** 2))
+    r3 = 3 * np.sqrt(np.maximum(lam, 0))
+    marginal = np.abs(r3 - np.round(r3)) < 1e-4 * np.maximum(1, r3)
+    mism = (pn["radius"] != ref["radius"]) & ~marginal
+    assert mism.sum() <= max(2, int(1e-5 * sc.n)), f"{mism.sum()} radius mismatches"
+    both = live_ref & live_gpu
+    np.testing.assert_allclose(pn["mean2d"][both], ref["mean2d"][both], rtol=1e-5, atol=2e-4)
+    scale = np.abs(ref["conic"][both]).max(1, keepdims=True)
+    assert np.max(np.abs(pn["conic"][both] - ref["conic"][both]) / scale) < 5e-4
+    np.testing.assert_allclose(pn["rgb"][both], ref["rgb"][both], rtol=0, atol=2e-5)
+    assert (pn["tiles_touched"][both] == ref["tiles_touched"][both]).mean() > 0.999
+
+
+# ----------------------------------------------------------------- binning --
+
+@pytest.mark.parametrize("kind", ["c0", "tiny_ragged", "tiny_dense", "c1"])
+def test_bin_sort_bit_exact(kind):
+    sc, dev, cam, proj, bs, pn, bn = pipeline(kind)
+    ref = oracle.bin_sort(pn["mean2d"].astype(np.float64), pn["radius"], pn["depth"], cam.width, cam.height)
+    assert bn["n_instances"] == ref["n_instances"] > 0
+    np.testing.assert_array_equal(bn["keys"].view(np.uint64), ref["keys"])
+    np.testing.assert_array_equal(bn["ids"].view(np.uint32), ref["ids"])
+    np.testing.assert_array_equal(bn["tile_ranges"].view(np.uint32), ref["tile_ranges"])
+
+
+def test_bin_sort_capacity_error_and_empty():
+    sc, dev, cam, proj, bs, pn, bn = pipeline("tiny_ragged")
+    n = sc.n
+    small = 7
+    ws = torch.empty(gs.gs_bin_sort_workspace_size(n, small, cam.width, cam.height) + 256, device="cuda",
+                     dtype=torch.uint8)
+    keys = torch.empty(small, device="cuda", dtype=torch.int64)
+    ids = torch.empty(small, device="cuda", dtype=torch.int32)
+    ranges = torch.empty(2 * cam.num_tiles, device="cuda", dtype=torch.int32)
+    st, count = gs.gs_bin_sort(n, proj["mean2d"], proj["radius"], proj["depth"], cam.width, cam.height, small, ws,
+                               keys, ids, ranges, check=False)
+    assert st == gs.GS_ERR_CAPACITY and count == bn["n_instances"]
+    # all splats culled: zero instances, empty ranges
+    zero_r = torch.zeros_like(proj["radius"])
+    st, count = gs.gs_bin_sort(n, proj["mean2d"], zero_r, proj["depth"], cam.width, cam.height, small, ws, keys, ids,
+                               ranges, check=False)
+    assert st == gs.GS_OK and count == 0
+    assert int(ranges.abs().sum()) == 0
+    # too-small workspace is refused
+    with pytest.raises(gs.GsError):
+        gs.gs_bin_sort(n, proj["mean2d"], proj["radius"], proj["depth"], cam.width, cam.height, small, ws[:64], keys,
+                       ids, ranges)
+
+
+# ------------------------------------------------------------- blend, FP32 --
+
+def _compare(out, ref, tol, nc_exact=True, max_amb=0.01):
+    amb = ref["ambiguous"]
+    ok = ~amb
+    assert amb.mean() <= max_amb, f"{amb.mean():.4%} ambiguous pixels"
+    err = np.abs(out["image"] - ref["image"])[:, ok]
+    assert err.max() <= tol, f"max abs {err.max():.3e} > {tol}"
+    assert np.abs(out["T_final"] - ref["T_final"])[ok].max() <= tol
+    if nc_exact:
+        np.testing.assert_array_equal(out["n_contrib"][ok], ref["n_contrib"][ok])
+    return err
+
+
+@pytest.mark.parametrize("kind,bg", [("c0", (0, 0, 0)), ("tiny_ragged", (0.3, 0.2, 0.1)),
+                                     ("tiny_dense", (0, 0, 0)), ("c1", (0.1, 0.1, 0.1))])
+def test_blend_fp32_matches_oracle(kind, bg):
+    sc, dev, cam, proj, bs, pn, bn = pipeline(kind)
+    out = blend_gpu(cam, proj, bs, dev["opacities"], "fp32", bg=bg)
+    ref = oracle_blend_on_gpu_params(cam, pn, bn, sc.opacities, bg=bg, alpha_margin=1e-4, t_margin=1e-4)
+    _compare(out, ref, 1e-4)
+    assert (out["n_contrib"] > 0).mean() > 0.05
+
+
+# ------------------------------------------------------ blend, tensor core --
+
+TC_VARIANTS = ["fp16", "bf16", "fp16_split", "bf16_split"]
+
+
+def _tile_power_gate(sc, cam, proj, bs, pn, bn, variant, tiles, max_len=256, ref_origin=0):
+    tiles_t = torch.tensor(tiles, device="cuda", dtype=torch.int32)
+    out = torch.full((len(tiles), max_len, 256), float("nan"), device="cuda")
+    opts = gs.make_opts(variant, ref_origin=ref_origin)
+    gs.gs_tile_power(cam.width, cam.height, bs["tile_ranges"], bs["ids"], proj["mean2d"], proj["conic"],
+                     dev_opac(sc), opts, tiles_t, max_len, out)
+    assert gs.gs_sync_status() == gs.GS_OK
+    got = out.cpu().numpy().astype(np.float64)
+    ranges = bn["tile_ranges"].view(np.uint32)
+    ids = bn["ids"].view(np.uint32)
+    errs = []
+    for i, t in enumerate(tiles):
+        p = oracle.tile_power(cam.width, t, ranges, ids, pn["mean2d"].astype(np.float64),
+                              pn["conic"].astype(np.float64))[:max_len]
+        L = p.shape[0]
+        if L == 0:
+            continue
+        o = sc.opacities[ids[ranges[2 * t]:ranges[2 * t] + L]].astype(np.float64)
+        contributes = p >= np.log(1.0 / (255.0 * o))[:, None]
+        want = p * LOG2E + np.log2(o)[:, None]
+        e = np.abs(got[i, :L] - want) / LOG2E
+        errs.append(e[contributes])
+    return np.concatenate(errs) if errs else np.zeros(0)
+
+
+_opac_cache = {}
+
+
+def dev_opac(sc):
+    key = id(sc)
+    if key not in _opac_cache:
+        _opac_cache[key] = torch.from_numpy(sc.opacities).cuda()
+    return _opac_cache[key]
+
+
+def _busy_tiles(bn, k, seed=0):
+    r = bn["tile_ranges"].view(np.uint32)
+    lens = r[1::2].astype(np.int64) - r[0::2]
+    busy = np.nonzero(lens > 0)[0]
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(busy, size=min(k, len(busy)), replace=False)
+    return sorted(int(t) for t in pick)
+
+
+@pytest.mark.parametrize("variant", ["fp16_split", "bf16_split"])
+@pytest.mark.parametrize("kind", ["tiny_dense", "c1"])
+def test_tile_power_split_within_2e3(kind, variant):
+    """Eq. 8's contraction on the tensor cores: every pair that can contribute
+    (power >= ln(1/(255 o))) has |power_TC - power_FP64| <= 2e-3."""
+    sc, dev, cam, proj, bs, pn, bn = pipeline(kind)
+    tiles = _busy_tiles(bn, 24)
+    e = _tile_power_gate(sc, cam, proj, bs, pn, bn, variant, tiles)
+    assert e.size > 1000
+    assert e.max() <= 2e-3, f"max exponent error {e.max():.3e}"
+
+
+@pytest.mark.parametrize("variant", ["fp16", "bf16"])
+def test_tile_power_plain_is_close(variant):
+    """Unsplit operands: the exponent is right to the operand precision."""
+    sc, dev, cam, proj, bs, pn, bn = pipeline("tiny_dense")
+    e = _tile_power_gate(sc, cam, proj, bs, pn, bn, variant, _busy_tiles(bn, 12))
+    bound = 0.1 if variant == "fp16" else 0.8
+    assert e.size > 100 and e.max() < bound
+
+
+@pytest.mark.parametrize("variant", TC_VARIANTS)
+@pytest.mark.parametrize("kind", ["c0", "tiny_ragged", "tiny_dense", "c1"])
+def test_blend_tc_matches_oracle(kind, variant):
+    sc, dev, cam, proj, bs, pn, bn = pipeline(kind)
+    bg = (0.05, 0.1, 0.15)
+    out = blend_gpu(cam, proj, bs, dev["opacities"], variant, bg=bg)
+    if variant.endswith("split"):
+        ref = oracle_blend_on_gpu_params(cam, pn, bn, sc.opacities, bg=bg, alpha_margin=5e-3, t_margin=2e-2)
+        err = _compare(out, ref, 1e-2, nc_exact=True, max_amb=0.05)
+        assert err.mean() < 2e-4
+    else:
+        ref = oracle_blend_on_gpu_params(cam, pn, bn, sc.opacities, bg=bg)
+        err = np.abs(out["image"] - ref["image"])
+        assert err.mean() < (2e-3 if variant == "fp16" else 2e-2)
+
+
+def test_blend_tc_chunk_and_stage_invariant():
+    """Pipeline shape does not change a single bit of the tensor-core result."""
+    sc, dev, cam, proj, bs, pn, bn = pipeline("tiny_dense")
+    base = blend_gpu(cam, proj, bs, dev["opacities"], "fp16_split", chunk=32, stages=2)
+    for chunk, stages in [(32, 4), (64, 2), (128, 2)]:
+        o = blend_gpu(cam, proj, bs, dev["opacities"], "fp16_split", chunk=chunk, stages=stages)
+        for k in ("image", "T_final", "n_contrib"):
+            np.testing.assert_array_equal(o[k], base[k])
+
+
+def test_blend_tc_reference_origin():
+    """Reference pixel at the first pixel of the tile instead of the centre."""
+    sc, dev, cam, proj, bs, pn, bn = pipeline("tiny_dense")
+    e = _tile_power_gate(sc, cam, proj, bs, pn, bn, "fp16_split", _busy_tiles(bn, 12), ref_origin=1)
+    assert e.size > 100 and e.max() <= 2e-3
+    out = blend_gpu(cam, proj, bs, dev["opacities"], "fp16_split", ref_origin=1)
+    ref = oracle_blend_on_gpu_params(cam, pn, bn, sc.opacities, alpha_margin=5e-3, t_margin=2e-2)
+    _compare(out, ref, 1e-2, max_amb=0.05)
+
+
+# ------------------------------------------------------------- backward ----
+
+@pytest.mark.parametrize("kind", ["tiny_ragged", "tiny_dense", "c0"])
+def test_blend_backward_matches_oracle_gradient(kind):
+    sc, dev, cam, proj, bs, pn, bn = pipeline(kind)
+    bg = (0.2, 0.1, 0.05)
+    opts = gs.make_opts("fp32", bg=bg)
+    fwd = gs.blend_forward(cam.width, cam.height, bs, proj, dev["opacities"], opts)
+    rng = np.random.default_rng(1)
+    dL = rng.standard_normal((3, cam.height, cam.width)).astype(np.float32)
+    g = to_np(gs.blend_backward(cam.width, cam.height, bs, proj, dev["opacities"], opts, fwd,
+                                torch.from_numpy(dL).cuda()))
+    assert gs.gs_sync_status() == gs.GS_OK
+    ref = oracle.blend_grad(cam.width, cam.height, bn["tile_ranges"].view(np.uint32), bn["ids"].view(np.uint32),
+                            pn["mean2d"].astype(np.float64), pn["conic"].astype(np.float64),
+                            sc.opacities.astype(np.float64), pn["rgb"].astype(np.float64), dL.astype(np.float64),
+                            bg=bg)
+    for name in ("mean2d", "conic", "opacity", "rgb"):
+        a, b = g[name].astype(np.float64), ref[name]
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
+        assert rel < 1e-3, f"{name}: relative error {rel:.2e}"
+
+
+def test_autograd_function_matches_backward_call():
+    sc, dev, cam, proj, bs, pn, bn = pipeline("tiny_ragged")
+    opts = gs.make_opts("fp32")
+    m = proj["mean2d"].clone().requires_grad_(True)
+    c = proj["conic"].clone().requires_grad_(True)
+    o = dev["opacities"].clone().requires_grad_(True)
+    r = proj["rgb"].clone().requires_grad_(True)
+    img, T, nc = gs.BlendFunction.apply(m, c, o, r, bs["tile_ranges"], bs["ids"], cam.width, cam.height, opts)
+    w = torch.randn_like(img)
+    (img * w).sum().backward()
+    fwd = gs.blend_forward(cam.width, cam.height, bs, proj, dev["opacities"], opts)
+    g = gs.blend_backward(cam.width, cam.height, bs, proj, dev["opacities"], opts, fwd, w)
+    torch.testing.assert_close(m.grad, g["mean2d"], rtol=0, atol=1e-6)
+    torch.testing.assert_close(o.grad, g["opacity"], rtol=0, atol=1e-6)
+
+
+# ---------------------------------------------------------- edge cases ----
+
+def test_zero_gaussians_and_tiny_images():
+    cam = scenes.look_at_camera((0, 0, -3), (0, 0, 0), 1, 1)
+    empty = scenes.tiny_scene(0, n=1, width=1, height=1)
+    dev = gs.scene_to_device(empty)
+    z = lambda *s: torch.empty(*s, device="cuda")  # noqa: E731
+    gs.gs_project(0, dev["means"], dev["scales"], dev["quats"], dev["sh"], 0, cam, z(0, 2), z(0, 3), z(0), z(0),
+                  z(0, 3), z(0))
+    for (W, H) in [(1, 1), (17, 3), (16, 16)]:
+        sc = scenes.tiny_scene(4, n=12, width=W, height=H)
+        d2, cam2, proj, bs = gpu_pipeline(sc)
+        for variant in ("fp32", "fp16_split"):
+            out = blend_gpu(cam2, proj, bs, d2["opacities"], variant, bg=(0.5, 0.5, 0.5))
+            pn, bn = to_np(proj), to_np(bs)
+            ref = oracle_blend_on_gpu_params(cam2, pn, bn, sc.opacities, bg=(0.5, 0.5, 0.5), alpha_margin=5e-3,
+                                             t_margin=2e-2)
+            ok = ~ref["ambiguous"]
+            tol = 1e-4 if variant == "fp32" else 1e-2
+            assert np.abs(out["image"] - ref["image"])[:, ok].max(initial=0) <= tol
+
+
+def test_invalid_arguments_are_rejected():
+    sc, dev, cam, proj, bs, pn, bn = pipeline("tiny_ragged")
+    with pytest.raises(gs.GsError) as ei:
+        gs.gs_blend_forward(cam.width, cam.height, bs["tile_ranges"], bs["ids"], proj["mean2d"], proj["conic"],
+                            dev["opacities"], proj["rgb"], gs.make_opts(9), proj["rgb"], proj["rgb"], proj["radius"])
+    assert ei.value.status == gs.GS_ERR_INVALID_ARG
+    with pytest.raises(gs.GsError) as ei:
+        gs.gs_blend_forward(cam.width, cam.height, bs["tile_ranges"], bs["ids"], proj["mean2d"], proj["conic"],
+                            dev["opacities"], proj["rgb"], gs.make_opts("fp16", chunk=48), proj["rgb"], proj["rgb"],
+                            proj["radius"])
+    assert ei.value.status == gs.GS_ERR_UNSUPPORTED
