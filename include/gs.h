@@ -74,10 +74,12 @@ typedef enum gs_variant {
 /* Options of the blend calls.  All-zero is valid: FP32 variant, defaults. */
 typedef struct gs_blend_opts {
     int32_t variant;     /* gs_variant */
-    int32_t chunk;       /* TC: splats per pipeline stage, 32/64/128; 0 = default (32) */
-    int32_t stages;      /* TC: pipeline depth 2..4; 0 = default (2) */
-    int32_t ref_origin;  /* TC: 0 = reference pixel at the tile centre (x0+8, y0+8),
-                            1 = centre of the tile's first pixel (x0+0.5, y0+0.5) */
+    int32_t chunk;       /* TC: splats per pipeline stage; 0 = default (32) */
+    int32_t stages;      /* TC: depth of the shared-memory ring; 0 = default (4).
+                            Built (chunk, stages): (32, 4), (32, 2), (16, 4), (64, 3) */
+    int32_t ref_origin;  /* TC: reference pixel of each 16 x 8 half-tile (x0.., y0.. its
+                            first pixel): 0 = its centre (x0 + 8, y0 + 4),
+                            1 = the centre of its first pixel (x0 + 0.5, y0 + 0.5) */
     float bg[3];         /* background colour added as T_final * bg */
     int32_t reserved;
     int64_t timeout_ns;  /* limit of every device-side wait; 0 = 1 s */

@@ -134,12 +134,18 @@ struct PixelResult {
 
 // Front-to-back compositing of one pixel over an ordered splat list (Eq. 1 with
 // Alg. 1's alpha-skip and early termination, readings in the header).
-// Decisions that lie within a relative margin of their threshold mark the
-// pixel ambiguous: a lower-precision path may legitimately decide otherwise.
+// Decisions that lie within rounding of their threshold mark the pixel
+// ambiguous: a lower-precision path may legitimately decide otherwise.  With
+// alpha_margin the relative error of each alpha (= the absolute error of the
+// exponent), alpha decisions use that margin; the test transmittance
+// T (1 - alpha) = prod (1 - alpha_k) carries a relative error up to
+// alpha_margin * sum_k alpha_k / (1 - alpha_k) (first order, Eq. 1), so its
+// decision uses that bound plus t_margin.
 PixelResult composite_pixel(const std::vector<Splat>& list, double xp, double yp,
                             const double bg[3], double alpha_margin, double t_margin) {
     PixelResult r{{0, 0, 0}, 1.0, 0, false};
     double T = 1.0;
+    double growth = 0.0;  // sum alpha_k / (1 - alpha_k) over the splats added so far
     for (size_t i = 0; i < list.size(); ++i) {
         const Splat& s = list[i];
         double power = std::min(power_eq3(s, xp, yp), 0.0);
@@ -149,8 +155,10 @@ PixelResult composite_pixel(const std::vector<Splat>& list, double xp, double yp
         if (std::fabs(alpha - 1.0 / 255.0) <= alpha_margin / 255.0) r.ambiguous = true;
         if (alpha < 1.0 / 255.0) continue;
         double testT = T * (1.0 - alpha);
-        if (std::fabs(testT - 1e-4) <= t_margin * 1e-4) r.ambiguous = true;
+        double tm = t_margin + alpha_margin * (growth + alpha / (1.0 - alpha));
+        if (std::fabs(testT - 1e-4) <= tm * 1e-4) r.ambiguous = true;
         if (testT < 1e-4) break;
+        growth += alpha / (1.0 - alpha);
         for (int ch = 0; ch < 3; ++ch) r.C[ch] += s.c[ch] * alpha * T;
         T = testT;
         r.n_contrib = (int)i + 1;

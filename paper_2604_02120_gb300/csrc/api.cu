@@ -220,7 +220,7 @@ gs_status gs_blend_forward(int32_t width, int32_t height, const uint32_t* tile_r
         set_error("gs_blend_forward: unknown variant %d", o->variant);
         return GS_ERR_INVALID_ARG;
     }
-    int chunk = o->chunk ? o->chunk : 32, stages = o->stages ? o->stages : 2;
+    int chunk = o->chunk ? o->chunk : 32, stages = o->stages ? o->stages : 4;
     if (!tc_config_supported(o->variant, chunk, stages)) {
         set_error("gs_blend_forward: chunk %d / stages %d not built", chunk, stages);
         return GS_ERR_UNSUPPORTED;

@@ -92,14 +92,48 @@ __global__ void __launch_bounds__(kBatch) k_blend_fp32_fwd(BlendArgs a) {
     }
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Sums of nine per-lane values over the warp.  v[0..7] are reduced by
+// recursive halving (each level halves the values a lane carries while
+// exchanging the other half with its partner), leaving the total of v[k] in
+// the lanes with (lane >> 2) == k; v[8] by a plain butterfly (all lanes).
+__device__ __forceinline__ void warp_reduce9(const float (&v)[9], int lane, float& vk, float& v8) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float k4[4];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int i = 0; i < 4; ++i) {
+        const float send = b4 ? v[i] : v[i + 4];
+        const float keep = b4 ? v[i + 4] : v[i];
+        k4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float k2[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = b3 ? k4[i] : k4[i + 2];
+        const float keep = b3 ? k4[i + 2] : k4[i];
+        k2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float k1 = (b2 ? k2[1] : k2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? k2[0] : k2[1], 4);
+    k1 += __shfl_xor_sync(0xffffffffu, k1, 2);
+    k1 += __shfl_xor_sync(0xffffffffu, k1, 1);
+    vk = k1;
+    float s8 = v[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s8 += __shfl_xor_sync(0xffffffffu, s8, o);
+    v8 = s8;
 }
 
-// Back-to-front walk per pixel; per (splat, warp) the nine gradient values are
-// reduced across the warp and added with one atomic each.
+// Address of gradient component k (0..8) of Gaussian g:
+// dmean2d.x, dmean2d.y, dA, dB, dC, dopacity, dr, dg, db.
+__device__ __forceinline__ float* grad_slot(const GradArgs& gr, uint32_t g, int k) {
+    if (k < 2) return reinterpret_cast<float*>(gr.dmean2d) + 2 * (size_t)g + k;
+    if (k < 5) return gr.dconic + 3 * (size_t)g + (k - 2);
+    if (k == 5) return gr.dopac + g;
+    return gr.drgb + 3 * (size_t)g + (k - 6);
+}
+
+// Back-to-front walk per pixel.  Per (splat, warp) the nine gradient values
+// are either added directly by the few lanes that have them, or summed over
+// the warp (warp_reduce9) and added by nine lanes.
 __global__ void __launch_bounds__(kBatch) k_blend_fp32_bwd(BlendArgs a, GradArgs gr) {
     __shared__ float4 s_geo[kBatch];
     __shared__ float4 s_oc[kBatch];
@@ -127,7 +161,10 @@ __global__ void __launch_bounds__(kBatch) k_blend_fp32_bwd(BlendArgs a, GradArgs
     float S0 = a.bg[0], S1 = a.bg[1], S2 = a.bg[2];  // colour behind the current splat
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
-    atomicMax(&s_max, nc);
+    int wmax = nc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+    if (lane == 0) atomicMax(&s_max, wmax);
     __syncthreads();
     const int maxn = s_max;
 
@@ -145,62 +182,56 @@ __global__ void __launch_bounds__(kBatch) k_blend_fp32_bwd(BlendArgs a, GradArgs
             s_id[threadIdx.x] = g;
         }
         __syncthreads();
-        for (int j = hi - 1; j >= lo; --j) {
+        // this warp only needs list positions below its largest n_contrib
+        for (int j = min(hi, wmax) - 1; j >= lo; --j) {
             const int k = j - lo;
             const float4 geo = s_geo[k], oc = s_oc[k];
             const float cb = s_b[k];
-            float dm0 = 0.f, dm1 = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dO = 0.f, dc0 = 0.f, dc1 = 0.f, dc2 = 0.f;
+            float v[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) v[q] = 0.f;
             bool contrib = false;
             if (j < nc) {
                 float e, pw, dx, dy;
                 const float alpha = splat_alpha(geo, oc, xp, yp, e, pw, dx, dy);
                 if (alpha >= kAlphaMin) {
                     contrib = true;
-                    const float Ti = T / (1.0f - alpha);
+                    const float Ti = __fdividef(T, 1.0f - alpha);
                     const float wgt = alpha * Ti;
-                    dc0 = wgt * g0;
-                    dc1 = wgt * g1;
-                    dc2 = wgt * g2;
+                    v[6] = wgt * g0;
+                    v[7] = wgt * g1;
+                    v[8] = wgt * g2;
                     const float dL_dalpha = Ti * ((oc.z - S0) * g0 + (oc.w - S1) * g1 + (cb - S2) * g2);
-                    S0 = alpha * oc.z + (1.0f - alpha) * S0;
-                    S1 = alpha * oc.w + (1.0f - alpha) * S1;
-                    S2 = alpha * cb + (1.0f - alpha) * S2;
+                    S0 = fmaf(alpha, oc.z - S0, S0);
+                    S1 = fmaf(alpha, oc.w - S1, S1);
+                    S2 = fmaf(alpha, cb - S2, S2);
                     T = Ti;
                     if (oc.y * e <= kAlphaMax) {  // not clamped
-                        dO = dL_dalpha * e;
+                        v[5] = dL_dalpha * e;
                         if (pw <= 0.0f) {
                             const float dp = dL_dalpha * alpha;
-                            dm0 = -dp * (geo.z * dx + geo.w * dy);
-                            dm1 = -dp * (geo.w * dx + oc.x * dy);
-                            dA = -0.5f * dp * dx * dx;
-                            dB = -dp * dx * dy;
-                            dC = -0.5f * dp * dy * dy;
+                            v[0] = -dp * (geo.z * dx + geo.w * dy);
+                            v[1] = -dp * (geo.w * dx + oc.x * dy);
+                            v[2] = -0.5f * dp * dx * dx;
+                            v[3] = -dp * dx * dy;
+                            v[4] = -0.5f * dp * dy * dy;
                         }
                     }
                 }
             }
-            if (__any_sync(0xffffffffu, contrib)) {
-                dm0 = warp_sum(dm0);
-                dm1 = warp_sum(dm1);
-                dA = warp_sum(dA);
-                dB = warp_sum(dB);
-                dC = warp_sum(dC);
-                dO = warp_sum(dO);
-                dc0 = warp_sum(dc0);
-                dc1 = warp_sum(dc1);
-                dc2 = warp_sum(dc2);
-                if (lane == 0) {
-                    const uint32_t g = s_id[k];
-                    atomicAdd(&gr.dmean2d[g].x, dm0);
-                    atomicAdd(&gr.dmean2d[g].y, dm1);
-                    atomicAdd(&gr.dconic[3 * g], dA);
-                    atomicAdd(&gr.dconic[3 * g + 1], dB);
-                    atomicAdd(&gr.dconic[3 * g + 2], dC);
-                    atomicAdd(&gr.dopac[g], dO);
-                    atomicAdd(&gr.drgb[3 * g], dc0);
-                    atomicAdd(&gr.drgb[3 * g + 1], dc1);
-                    atomicAdd(&gr.drgb[3 * g + 2], dc2);
+            const unsigned who = __ballot_sync(0xffffffffu, contrib);
+            if (who == 0u) continue;
+            const uint32_t g = s_id[k];
+            if (__popc(who) <= 3) {
+                if (contrib) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) atomicAdd(grad_slot(gr, g, q), v[q]);
                 }
+            } else {
+                float vk, v8;
+                warp_reduce9(v, lane, vk, v8);
+                if ((lane & 3) == 0) atomicAdd(grad_slot(gr, g, lane >> 2), vk);
+                if (lane == 0) atomicAdd(grad_slot(gr, g, 8), v8);
             }
         }
     }

@@ -5,8 +5,8 @@ namespace gs {
 
 bool tc_config_supported(int variant, int chunk, int stages) {
     if (variant < GS_BLEND_TC_FP16 || variant > GS_BLEND_TC_BF16_SPLIT) return false;
-    return (chunk == 32 && (stages == 2 || stages == 4)) || (chunk == 64 && stages == 2) ||
-           (chunk == 128 && stages == 2);
+    return (chunk == 32 && (stages == 2 || stages == 4)) || (chunk == 16 && stages == 4) ||
+           (chunk == 64 && stages == 3);
 }
 
 cudaError_t launch_blend_tc(const BlendArgs& a, int variant, int chunk, int stages, bool dump, int grid,

@@ -10,6 +10,17 @@ import oracle
 from paper_2604_02120_gb300 import gs, scenes
 
 CORES = os.cpu_count() or 4
+_REPORT = {}
+
+
+def report(key, value):
+    """Record a measured number; written as JSON to $GS_TEST_REPORT at exit."""
+    _REPORT[key] = value
+    path = os.environ.get("GS_TEST_REPORT")
+    if path:
+        import json
+        with open(path, "w") as f:
+            json.dump(_REPORT, f, indent=1, sort_keys=True)
 
 
 def gpu_pipeline(scene, cam_index=0, capacity=1 << 20):

@@ -13,11 +13,15 @@ import torch
 import oracle
 from paper_2604_02120_gb300 import gs, scenes
 
-from gpu_common import CORES, blend_gpu, gpu_pipeline, oracle_blend_on_gpu_params, to_np
+from gpu_common import CORES, blend_gpu, gpu_pipeline, oracle_blend_on_gpu_params, report, to_np
 
 pytestmark = pytest.mark.gpu
 
 LOG2E = 1.4426950408889634
+# Bound on |exponent error| (natural-log units) the split tensor-core variants
+# are held to when deciding which pixels are ambiguous; the tile-power tests
+# check that the measured error stays within half of it.
+SPLIT_EXP_ERR = 2e-4
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -204,7 +208,11 @@ def test_tile_power_split_within_2e3(kind, variant):
     tiles = _busy_tiles(bn, 24)
     e = _tile_power_gate(sc, cam, proj, bs, pn, bn, variant, tiles)
     assert e.size > 1000
+    report(f"exp_err_{variant}_{kind}",
+           {"max": float(e.max()), "p99": float(np.quantile(e, 0.99)), "pairs": int(e.size)})
     assert e.max() <= 2e-3, f"max exponent error {e.max():.3e}"
+    # the blend comparisons below assume this variant's exponent error bound
+    assert e.max() <= SPLIT_EXP_ERR / 2
 
 
 @pytest.mark.parametrize("variant", ["fp16", "bf16"])
@@ -212,6 +220,7 @@ def test_tile_power_plain_is_close(variant):
     """Unsplit operands: the exponent is right to the operand precision."""
     sc, dev, cam, proj, bs, pn, bn = pipeline("tiny_dense")
     e = _tile_power_gate(sc, cam, proj, bs, pn, bn, variant, _busy_tiles(bn, 12))
+    report(f"exp_err_{variant}_tiny_dense", {"max": float(e.max()), "p99": float(np.quantile(e, 0.99))})
     bound = 0.1 if variant == "fp16" else 0.8
     assert e.size > 100 and e.max() < bound
 
@@ -223,20 +232,23 @@ def test_blend_tc_matches_oracle(kind, variant):
     bg = (0.05, 0.1, 0.15)
     out = blend_gpu(cam, proj, bs, dev["opacities"], variant, bg=bg)
     if variant.endswith("split"):
-        ref = oracle_blend_on_gpu_params(cam, pn, bn, sc.opacities, bg=bg, alpha_margin=5e-3, t_margin=2e-2)
-        err = _compare(out, ref, 1e-2, nc_exact=True, max_amb=0.05)
-        assert err.mean() < 2e-4
+        ref = oracle_blend_on_gpu_params(cam, pn, bn, sc.opacities, bg=bg, alpha_margin=SPLIT_EXP_ERR,
+                                         t_margin=1e-5)
+        err = _compare(out, ref, 1e-3, nc_exact=True, max_amb=0.02)
+        report(f"blend_{variant}_{kind}", {"max_abs": float(err.max()), "mean_abs": float(err.mean()),
+                                           "ambiguous": float(ref["ambiguous"].mean())})
     else:
         ref = oracle_blend_on_gpu_params(cam, pn, bn, sc.opacities, bg=bg)
         err = np.abs(out["image"] - ref["image"])
+        report(f"blend_{variant}_{kind}", {"max_abs": float(err.max()), "mean_abs": float(err.mean())})
         assert err.mean() < (2e-3 if variant == "fp16" else 2e-2)
 
 
 def test_blend_tc_chunk_and_stage_invariant():
     """Pipeline shape does not change a single bit of the tensor-core result."""
     sc, dev, cam, proj, bs, pn, bn = pipeline("tiny_dense")
-    base = blend_gpu(cam, proj, bs, dev["opacities"], "fp16_split", chunk=32, stages=2)
-    for chunk, stages in [(32, 4), (64, 2), (128, 2)]:
+    base = blend_gpu(cam, proj, bs, dev["opacities"], "fp16_split", chunk=32, stages=4)
+    for chunk, stages in [(32, 2), (16, 4), (64, 3)]:
         o = blend_gpu(cam, proj, bs, dev["opacities"], "fp16_split", chunk=chunk, stages=stages)
         for k in ("image", "T_final", "n_contrib"):
             np.testing.assert_array_equal(o[k], base[k])
@@ -247,9 +259,10 @@ def test_blend_tc_reference_origin():
     sc, dev, cam, proj, bs, pn, bn = pipeline("tiny_dense")
     e = _tile_power_gate(sc, cam, proj, bs, pn, bn, "fp16_split", _busy_tiles(bn, 12), ref_origin=1)
     assert e.size > 100 and e.max() <= 2e-3
+    report("exp_err_fp16_split_origin_ref", float(e.max()))
     out = blend_gpu(cam, proj, bs, dev["opacities"], "fp16_split", ref_origin=1)
-    ref = oracle_blend_on_gpu_params(cam, pn, bn, sc.opacities, alpha_margin=5e-3, t_margin=2e-2)
-    _compare(out, ref, 1e-2, max_amb=0.05)
+    ref = oracle_blend_on_gpu_params(cam, pn, bn, sc.opacities, alpha_margin=SPLIT_EXP_ERR, t_margin=1e-5)
+    _compare(out, ref, 1e-3, max_amb=0.02)
 
 
 # ------------------------------------------------------------- backward ----
@@ -306,10 +319,10 @@ def test_zero_gaussians_and_tiny_images():
         for variant in ("fp32", "fp16_split"):
             out = blend_gpu(cam2, proj, bs, d2["opacities"], variant, bg=(0.5, 0.5, 0.5))
             pn, bn = to_np(proj), to_np(bs)
-            ref = oracle_blend_on_gpu_params(cam2, pn, bn, sc.opacities, bg=(0.5, 0.5, 0.5), alpha_margin=5e-3,
-                                             t_margin=2e-2)
+            ref = oracle_blend_on_gpu_params(cam2, pn, bn, sc.opacities, bg=(0.5, 0.5, 0.5),
+                                             alpha_margin=SPLIT_EXP_ERR, t_margin=1e-5)
             ok = ~ref["ambiguous"]
-            tol = 1e-4 if variant == "fp32" else 1e-2
+            tol = 1e-4 if variant == "fp32" else 1e-3
             assert np.abs(out["image"] - ref["image"])[:, ok].max(initial=0) <= tol
 
 
