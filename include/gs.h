@@ -145,6 +145,31 @@ gs_status gs_bin_sort(int32_t n, const float* mean2d, const int32_t* radius, con
                       int64_t* n_instances, gs_stream stream);
 
 /*
+ * gs_bin_sort_noalloc - gs_bin_sort for callers that cannot allocate device
+ * memory (the paper has no counterpart: it is a deployment convenience).
+ * Some callers get only their input and output buffers: code inside a host
+ * framework whose allocator owns the device, plugins, or processes with a
+ * memory budget fixed in advance.  This entry point takes no workspace; its
+ * scratch is one array of gs_bin_sort_noalloc_max_bytes() bytes (64 MiB)
+ * compiled into the library, which every device that loads the library holds
+ * until the process exits.  Arguments and results are those of gs_bin_sort.
+ *  - Returns GS_ERR_WORKSPACE, writing nothing, if gs_bin_sort_workspace_size
+ *    (n, capacity, width, height) exceeds that size.
+ *  - It calls no allocation routine.  The first call on a device looks up
+ *    the array's device address (once per device, that device current); make
+ *    that first call before any stream capture.
+ *  - All calls share the one array: calls that overlap on the GPU (other
+ *    streams, other host threads) race and must be serialised by the caller.
+ *    The array's previous contents never matter (everything read is written
+ *    first within the call).
+ */
+size_t gs_bin_sort_noalloc_max_bytes(void);
+gs_status gs_bin_sort_noalloc(int32_t n, const float* mean2d, const int32_t* radius, const float* depth,
+                              int32_t width, int32_t height, int64_t capacity, uint64_t* keys_sorted,
+                              uint32_t* ids_sorted, uint32_t* tile_ranges, int64_t* n_instances,
+                              gs_stream stream);
+
+/*
  * gs_blend_forward - blending stage (Eq. 1; Alg. 1 for GS_BLEND_FP32, Alg. 2
  * with Eqs. 6-8 for the TC variants).  For every pixel, over its tile's list
  * in order: power = -1/2 (A dx^2 + C dy^2) - B dx dy (dx = mx - x, dy = my - y);

@@ -27,7 +27,7 @@ VARIANTS = {
 ABI_FUNCTIONS = (
     "gs_version", "gs_status_string", "gs_last_error", "gs_project", "gs_bin_sort_workspace_size",
     "gs_bin_sort", "gs_blend_forward", "gs_blend_backward", "gs_tile_power", "gs_sync_status",
-    "gs_selftest_bounded_wait", "gs_launch_count",
+    "gs_selftest_bounded_wait", "gs_launch_count", "gs_bin_sort_noalloc", "gs_bin_sort_noalloc_max_bytes",
 )
 
 
@@ -63,6 +63,8 @@ def load(path: str = LIB_PATH):
     vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
     lib.gs_version.restype = i32
     lib.gs_launch_count.restype = i64
+    lib.gs_bin_sort_noalloc_max_bytes.restype = sz
+    lib.gs_bin_sort_noalloc.argtypes = [i32, vp, vp, vp, i32, i32, i64, vp, vp, vp, ctypes.POINTER(i64), vp]
     lib.gs_status_string.restype = ctypes.c_char_p
     lib.gs_status_string.argtypes = [ctypes.c_int]
     lib.gs_last_error.restype = ctypes.c_char_p
@@ -76,7 +78,8 @@ def load(path: str = LIB_PATH):
     lib.gs_sync_status.argtypes = [vp]
     lib.gs_selftest_bounded_wait.argtypes = [i64, vp]
     for name in ABI_FUNCTIONS:
-        if name not in ("gs_version", "gs_status_string", "gs_last_error", "gs_launch_count"):
+        if name not in ("gs_version", "gs_status_string", "gs_last_error", "gs_launch_count",
+                        "gs_bin_sort_noalloc_max_bytes"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -159,6 +162,23 @@ def gs_bin_sort(n, mean2d, radius, depth, width, height, capacity, workspace, ke
                             _stream(stream))
     if check:
         _check(st, "gs_bin_sort")
+    return st, int(count.value)
+
+
+def gs_bin_sort_noalloc_max_bytes() -> int:
+    return int(load().gs_bin_sort_noalloc_max_bytes())
+
+
+def gs_bin_sort_noalloc(n, mean2d, radius, depth, width, height, capacity, keys_sorted, ids_sorted, tile_ranges,
+                        stream=None, check=True):
+    """gs_bin_sort without a workspace argument (scratch built into the
+    library).  Returns (status, n_instances)."""
+    count = ctypes.c_int64(0)
+    st = load().gs_bin_sort_noalloc(n, _ptr(mean2d), _ptr(radius), _ptr(depth), width, height, capacity,
+                                    _ptr(keys_sorted), _ptr(ids_sorted), _ptr(tile_ranges), ctypes.byref(count),
+                                    _stream(stream))
+    if check:
+        _check(st, "gs_bin_sort_noalloc")
     return st, int(count.value)
 
 
