@@ -75,8 +75,8 @@ typedef enum gs_variant {
 typedef struct gs_blend_opts {
     int32_t variant;     /* gs_variant */
     int32_t chunk;       /* TC: splats per pipeline stage; 0 = default (32) */
-    int32_t stages;      /* TC: depth of the shared-memory ring; 0 = default (4).
-                            Built (chunk, stages): (32, 4), (32, 2), (16, 4), (64, 3) */
+    int32_t stages;      /* TC: depth of the shared-memory ring; 0 = default (2).
+                            Built (chunk, stages): (32, 4), (32, 2), (16, 4), (16, 6) */
     int32_t ref_origin;  /* TC: reference pixel of each 16 x 8 half-tile (x0.., y0.. its
                             first pixel): 0 = its centre (x0 + 8, y0 + 4),
                             1 = the centre of its first pixel (x0 + 0.5, y0 + 0.5) */

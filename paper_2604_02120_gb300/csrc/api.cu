@@ -92,6 +92,9 @@ BlendArgs make_args(int32_t W, int32_t H, const uint32_t* ranges, const uint32_t
     a.timeout_ns = (o && o->timeout_ns > 0) ? (uint64_t)o->timeout_ns : 1000000000ull;
     a.ref_origin = o ? o->ref_origin : 0;
     a.err = error_word();
+    a.num_views = 1;
+    a.total_tiles = a.num_tiles;
+    a.views[0] = ViewDesc{W, H, a.tiles_x, 0, 0};
     return a;
 }
 
@@ -220,7 +223,7 @@ gs_status gs_blend_forward(int32_t width, int32_t height, const uint32_t* tile_r
         set_error("gs_blend_forward: unknown variant %d", o->variant);
         return GS_ERR_INVALID_ARG;
     }
-    int chunk = o->chunk ? o->chunk : 32, stages = o->stages ? o->stages : 4;
+    int chunk = o->chunk ? o->chunk : 32, stages = o->stages ? o->stages : 2;
     if (!tc_config_supported(o->variant, chunk, stages)) {
         set_error("gs_blend_forward: chunk %d / stages %d not built", chunk, stages);
         return GS_ERR_UNSUPPORTED;

@@ -1,24 +1,31 @@
 // Tensor-core blending (Alg. 2, Eqs. 4-8) for sm_100-family GPUs.
 //
-// One CTA per 16 x 16 tile.  The tile is split into an upper and a lower
-// 16 x 8 half; M_p (A operand, 128 x K) holds the monomials
+// Persistent kernel: each CTA pulls tiles from a global queue (an atomic
+// counter) until the queue is empty; the tiles of all views of the call form
+// one queue.  Every 16 x 16 tile is split into an upper and a lower 16 x 8
+// half; M_p (A operand, 128 x K) holds the monomials
 // [xb^2, yb^2, xb yb, xb, yb, 1] of the 128 pixels of a half relative to the
-// half's reference pixel.  For every chunk of CH splats the producer writes
-// 2 CH coefficient rows v_g (Eq. 6): rows [0, CH) referred to the upper half's
-// reference, rows [CH, 2 CH) to the lower half's (8 pixels further down).
-// One tcgen05.mma (M = 128, N = 2 CH, K = 16 or 32) then leaves in TMEM lane
-// r, column j the exponent of splat j at upper pixel r and, at column CH + j,
-// at lower pixel r: each epilogue thread owns two pixels of one lane and
-// composites both with packed f32x2 arithmetic.
+// half's reference pixel and is built once per CTA.  For every chunk of CH
+// splats of a tile the producer writes 2 CH coefficient rows v_g (Eq. 6):
+// rows [0, CH) referred to the upper half's reference, rows [CH, 2 CH) to the
+// lower half's (8 pixels further down).  One tcgen05.mma (M = 128, N = 2 CH,
+// K = 16 or 32) then leaves in TMEM lane r, column j the exponent of splat j
+// at upper pixel r and, at column CH + j, at lower pixel r: each epilogue
+// thread owns two pixels of one lane and composites both with packed f32x2
+// arithmetic.
 //
 // Warps: 0-3 epilogue (warp w reads TMEM lanes 32 w .. 32 w + 31), 4 producer,
-// 5 MMA issue (lane 0) and TMEM owner.  The producer fills a ring of SS
-// shared-memory stages (v_g rows + per-splat colour), the MMA writes a ring of
-// 2 TMEM stages; a stage of either ring is reused once the epilogue (and, for
-// shared memory, the MMA) is done with it.  All waits are bounded by
-// opts.timeout_ns; on expiry the CTA records GS_ERR_TIMEOUT in the device
-// error word, every role leaves its loop, the MMA thread waits (bounded, 1 s)
-// for its last commit and TMEM is freed.
+// 5 MMA issue (lane 0) and TMEM owner.  The producer streams (tile, chunk)
+// items through a ring of SS shared-memory stages (header, v_g rows,
+// per-splat colour) across tile boundaries, so the next tile's gathers
+// overlap the current tile's compositing; the MMA writes a ring of 2 TMEM
+// stages.  An empty tile travels as one stage with n = 0, the end of the
+// queue as n = -1.  When all four epilogue warps of a tile are
+// done (every pixel stopped) the producer skips that tile's remaining chunks.
+// All waits are bounded by opts.timeout_ns; on expiry the CTA records
+// GS_ERR_TIMEOUT in the device error word, every role leaves its loop, the
+// MMA thread commits to a drain barrier of its own and waits (bounded, 1 s)
+// until every MMA it issued has completed; then TMEM is freed.
 //
 // Compositing without branches (per pixel, alpha already clamped):
 //   cull = sat((1/255 - alpha) 2^36)        1 iff alpha < 1/255 (exact: one rounding)
@@ -42,6 +49,7 @@ namespace tc {
 constexpr int kEpiWarps = 4;
 constexpr int kThreads = 192;
 constexpr int kTStages = 2;
+constexpr int kDoneRing = 16;  // tiles in flight between producer and epilogue < kDoneRing
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kTMin = 1e-4f;
 constexpr float kLog2e = 1.4426950408889634f;
@@ -87,10 +95,10 @@ struct Layout {
     static constexpr int OFF_B = A_BYTES;
     static constexpr int OFF_REC = OFF_B + SS * B_BYTES;
     static constexpr int OFF_BAR = OFF_REC + SS * CH * (int)sizeof(Rec);
-    static constexpr int NBAR = 2 * SS + 2 * kTStages;
-    static constexpr int OFF_N = OFF_BAR + NBAR * 8;
-    static constexpr int OFF_MISC = OFF_N + SS * 4;
-    static constexpr int BYTES = OFF_MISC + 16;
+    static constexpr int NBAR = 2 * SS + 2 * kTStages + 1;  // + one drain barrier
+    static constexpr int OFF_HDR = OFF_BAR + NBAR * 8;
+    static constexpr int OFF_MISC = OFF_HDR + SS * 32;
+    static constexpr int BYTES = OFF_MISC + 16 + 4 * kDoneRing;
     static constexpr uint32_t TCOLS_RAW = 2u * kTStages * CH;
     static constexpr uint32_t TCOLS = TCOLS_RAW <= 32 ? 32 : TCOLS_RAW <= 64 ? 64 : TCOLS_RAW <= 128 ? 128
                                       : TCOLS_RAW <= 256 ? 256 : 512;
@@ -129,31 +137,38 @@ __device__ __forceinline__ float box_max_quadratic(float A, float B, float C, fl
 
 // Coefficient row of Eq. 6 for one splat and one reference pixel, in base-2
 // units with log2(o) folded into the constant term: v . v_p = log2(e) power + log2 o.
-// (xh, yh) = splat centre minus reference pixel; (bx0..by1) = the range of the
-// pixel offsets of the half-tile.  A splat that cannot reach alpha >= 1/255 at
-// any point of the half gets a dead row (exponent -200 everywhere).
+// (xh, yh) = splat centre minus reference pixel.  fp16 operands cannot hold
+// coefficients beyond 65504: if any would exceed 30000, the splat is tested
+// against the half-tile's pixel-offset box (bx0..by1) and, if it cannot reach
+// alpha >= 1/255 there, gets a dead row (exponent -200 everywhere); otherwise
+// the coefficients are clamped (only splats far from the tile relative to
+// their size reach this, and the error is stated in the design notes).
 template <bool HALF>
 __device__ __forceinline__ void coeff_row(float A, float B, float C, float l2o, float xh, float yh, float bx0,
                                           float bx1, float by0, float by1, float (&v)[6]) {
     const float ux = fmaf(A, xh, B * yh), uy = fmaf(B, xh, C * yh);
     const float P0 = -0.5f * fmaf(xh, ux, yh * uy);
-    const float qmax = box_max_quadratic(A, B, C, xh + bx0, xh + bx1, yh + by0, yh + by1);
-    const bool live = fmaf(qmax, kLog2e, l2o) >= kLog2AlphaMin - 0.25f;
-    if (live) {
-        v[0] = -0.5f * A * kLog2e;
-        v[1] = -0.5f * C * kLog2e;
-        v[2] = -B * kLog2e;
-        v[3] = -ux * kLog2e;
-        v[4] = -uy * kLog2e;
-        v[5] = fmaf(P0, kLog2e, l2o);
-        if constexpr (HALF) {
+    v[0] = -0.5f * A * kLog2e;
+    v[1] = -0.5f * C * kLog2e;
+    v[2] = -B * kLog2e;
+    v[3] = -ux * kLog2e;
+    v[4] = -uy * kLog2e;
+    v[5] = fmaf(P0, kLog2e, l2o);
+    if constexpr (HALF) {
+        float big = 0.f;
 #pragma unroll
-            for (int i = 0; i < 6; ++i) v[i] = fminf(fmaxf(v[i], -30000.f), 30000.f);
+        for (int i = 0; i < 6; ++i) big = fmaxf(big, fabsf(v[i]));
+        if (big > 30000.f) {
+            const float qmax = box_max_quadratic(A, B, C, xh + bx0, xh + bx1, yh + by0, yh + by1);
+            if (fmaf(qmax, kLog2e, l2o) >= kLog2AlphaMin - 0.25f) {
+#pragma unroll
+                for (int i = 0; i < 6; ++i) v[i] = fminf(fmaxf(v[i], -30000.f), 30000.f);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 5; ++i) v[i] = 0.f;
+                v[5] = kDeadPower;
+            }
         }
-    } else {
-#pragma unroll
-        for (int i = 0; i < 5; ++i) v[i] = 0.f;
-        v[5] = kDeadPower;
     }
 }
 
@@ -194,10 +209,27 @@ __device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, uint32_t (&v)
 }
 
 __device__ __forceinline__ float sat(float x) { return __saturatef(x); }
+
+// Work item of one pipeline stage.  n > 0: chunk [base, base + n) of the
+// tile's list; n == 0: the tile is empty; n < 0: end of the queue.
+struct StageHdr {
+    int tile;  // global tile id
+    int seq;   // this CTA's running tile number
+    int base;  // list position of the chunk's first splat
+    int n;
+    int slot;  // queue position of the tile (gs_tile_power output row)
+    int pad[3];
+};
+
+__device__ __forceinline__ int view_of(const BlendArgs& a, int tile) {
+    int v = 0;
+    while (v + 1 < a.num_views && a.views[v + 1].tile_begin <= tile) ++v;
+    return v;
+}
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
 template <int V, int CH, int SS, bool DUMP>
-__global__ void __launch_bounds__(kThreads, 4) k_blend_tc(BlendArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant__ BlendArgs a) {
     using TR = Traits<V>;
     using LY = Layout<SS, CH, V>;
     constexpr int K = TR::K;
@@ -208,48 +240,19 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(BlendArgs a) {
     uint8_t* sB = smem + LY::OFF_B;
     Rec* sRec = reinterpret_cast<Rec*>(smem + LY::OFF_REC);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + LY::OFF_BAR);
-    int* sN = reinterpret_cast<int*>(smem + LY::OFF_N);
+    StageHdr* sHdr = reinterpret_cast<StageHdr*>(smem + LY::OFF_HDR);
     uint32_t* sTmem = reinterpret_cast<uint32_t*>(smem + LY::OFF_MISC);
-    volatile int* sDone = reinterpret_cast<volatile int*>(smem + LY::OFF_MISC + 4);
-    volatile int* sAbort = reinterpret_cast<volatile int*>(smem + LY::OFF_MISC + 8);
+    volatile int* sAbort = reinterpret_cast<volatile int*>(smem + LY::OFF_MISC + 4);
+    volatile int* sDoneRing = reinterpret_cast<volatile int*>(smem + LY::OFF_MISC + 16);
     auto bar_full = [&](int s) { return smem_u32(bars + s); };
     auto bar_empty = [&](int s) { return smem_u32(bars + SS + s); };
     auto bar_tfull = [&](int t) { return smem_u32(bars + 2 * SS + t); };
     auto bar_tempty = [&](int t) { return smem_u32(bars + 2 * SS + kTStages + t); };
+    const uint32_t bar_drain = smem_u32(bars + 2 * SS + 2 * kTStages);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = DUMP ? a.tiles[blockIdx.x] : (int)blockIdx.x;
-    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const int x0 = tx * kTile, y0 = ty * kTile;
-    const uint32_t start = a.ranges[2 * tile], end = a.ranges[2 * tile + 1];
-    int len = end > start ? (int)(end - start) : 0;
-    if (DUMP && len > a.max_len) len = a.max_len;
-
-    // the two pixels of this epilogue thread: lane r of the accumulator
-    const int r = warp * 32 + lane;  // 0..127 for warps 0-3
-    const int px = x0 + (r & 15), py_up = y0 + (r >> 4), py_lo = py_up + 8;
-    const bool epi = warp < kEpiWarps;
-    const bool in_up = epi && px < a.W && py_up < a.H;
-    const bool in_lo = epi && px < a.W && py_lo < a.H;
-
-    if (len == 0) {  // uniform over the CTA: nothing to blend
-        if (!DUMP) {
-            const size_t plane = (size_t)a.W * a.H;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (h ? in_lo : in_up) {
-                    const size_t p = (size_t)(h ? py_lo : py_up) * a.W + px;
-                    a.image[p] = a.bg[0];
-                    a.image[plane + p] = a.bg[1];
-                    a.image[2 * plane + p] = a.bg[2];
-                    a.T_final[p] = 1.0f;
-                    a.n_contrib[p] = 0;
-                }
-            }
-        }
-        return;
-    }
-    const int nchunks = (len + CH - 1) / CH;
+    const int n_items = a.total_tiles;  // gs_tile_power: the number of listed tiles
+    const bool origin = a.ref_origin != 0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < SS; ++s) {
@@ -260,12 +263,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(BlendArgs a) {
             mbar_init(bar_tfull(t), 1);
             mbar_init(bar_tempty(t), kEpiWarps);
         }
-        *sDone = 0;
+        mbar_init(bar_drain, 1);
         *sAbort = 0;
         mbar_fence_init();
     }
     // pixel matrix M_p of a 16 x 8 half-tile (A operand)
-    const bool origin = a.ref_origin != 0;
     for (int idx = threadIdx.x; idx < 128 * (K / 8); idx += kThreads) {
         const int row = idx / (K / 8), kc = idx % (K / 8);
         const float xb = origin ? -(float)(row & 15) : 7.5f - (float)(row & 15);
@@ -290,13 +292,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(BlendArgs a) {
     const uint32_t tmem = *sTmem;
     const uint64_t tmo = a.timeout_ns;
 
-    if (epi) {
+    if (warp < kEpiWarps) {
         // ------------------------------------------------------- epilogue --
-        float2 T = make_float2(in_up || DUMP ? 1.f : 0.f, in_lo || DUMP ? 1.f : 0.f);
-        float2 Tstop = make_float2(0.f, 0.f), last = make_float2(0.f, 0.f);
-        float2 Cr = make_float2(0.f, 0.f), Cg = Cr, Cb = Cr;
-        bool wdone = DUMP ? false : __all_sync(0xffffffffu, T.x == 0.f && T.y == 0.f);
-        if (!DUMP && wdone && lane == 0) atomicAdd((int*)sDone, 1);
+        const int r = warp * 32 + lane;  // accumulator lane: pixel r of each half
+        int cur_seq = -1, slot = 0;
+        int px = 0, py_up = 0, W = 0, H = 0;
+        bool in_up = false, in_lo = false, wdone = true;
+        long long pix_off = 0;
+        float2 T = make_float2(0.f, 0.f), Tstop = T, last = T, Cr = T, Cg = T, Cb = T;
         for (int k = 0;; ++k) {
             const int s = k % SS, t = k % kTStages;
             const uint32_t ps = (uint32_t)(k / SS) & 1u, pt = (uint32_t)(k / kTStages) & 1u;
@@ -305,10 +308,46 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(BlendArgs a) {
                 atomicOr(a.err, kErrTimeout);
                 break;
             }
-            const int n = sN[s];
-            if (n == 0) break;
+            const StageHdr hd = sHdr[s];
+            if (hd.seq != cur_seq) {
+                if (!DUMP && cur_seq >= 0) {  // write the finished tile's pixels
+                    const size_t plane = (size_t)W * H;
+                    float* img = a.image + 3 * pix_off;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (h ? in_lo : in_up) {
+                            const size_t p = (size_t)(py_up + 8 * h) * W + px;
+                            const float Tf = h ? T.y + Tstop.y : T.x + Tstop.x;
+                            img[p] = (h ? Cr.y : Cr.x) + Tf * a.bg[0];
+                            img[plane + p] = (h ? Cg.y : Cg.x) + Tf * a.bg[1];
+                            img[2 * plane + p] = (h ? Cb.y : Cb.x) + Tf * a.bg[2];
+                            a.T_final[pix_off + p] = Tf;
+                            a.n_contrib[pix_off + p] = (int)(h ? last.y : last.x);
+                        }
+                    }
+                }
+                if (hd.n < 0) break;
+                cur_seq = hd.seq;
+                const int v = view_of(a, hd.tile);
+                const ViewDesc vd = a.views[v];
+                const int lt = hd.tile - vd.tile_begin;
+                W = vd.W;
+                H = vd.H;
+                pix_off = vd.pix_off;
+                px = (lt % vd.tiles_x) * kTile + (r & 15);
+                py_up = (lt / vd.tiles_x) * kTile + (r >> 4);
+                in_up = px < W && py_up < H;
+                in_lo = px < W && py_up + 8 < H;
+                slot = hd.slot;
+                T = make_float2(in_up || DUMP ? 1.f : 0.f, in_lo || DUMP ? 1.f : 0.f);
+                Tstop = last = Cr = Cg = Cb = make_float2(0.f, 0.f);
+                wdone = DUMP ? false : __all_sync(0xffffffffu, T.x == 0.f && T.y == 0.f);
+                if (!DUMP && wdone && lane == 0) atomicAdd((int*)&sDoneRing[cur_seq % kDoneRing], 1);
+            }
             tc_fence_after();
-            if (!wdone) {
+            const int n = hd.n;
+            const int base = hd.base;
+            if (n > 0 && !wdone) {
                 const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * 2 * CH);
                 const Rec* rec = sRec + s * CH;
 #pragma unroll 1
@@ -322,13 +361,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(BlendArgs a) {
                         for (int c = 0; c < 16; ++c) {
                             const int j = c0 + c;
                             if (j < n) {
-                                float* o = a.dump + ((size_t)blockIdx.x * a.max_len + (size_t)k * CH + j) * 256;
+                                float* o = a.dump + ((size_t)slot * a.max_len + (size_t)base + j) * 256;
                                 o[r] = __uint_as_float(vu[c]);
                                 o[r + 128] = __uint_as_float(vl[c]);
                             }
                         }
                     } else {
-                        const float base1 = (float)(k * CH + c0 + 1);
+                        const float base1 = (float)(base + c0 + 1);
 #pragma unroll
                         for (int c = 0; c < 16; ++c) {
                             const Rec rc = rec[c0 + c];
@@ -361,97 +400,104 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(BlendArgs a) {
             }
             tc_fence_before();
             __syncwarp();
+            if (lane == 0) mbar_arrive(bar_tempty(t));
             if (!DUMP && !wdone) {
                 wdone = __all_sync(0xffffffffu, T.x == 0.f && T.y == 0.f);
-                if (wdone && lane == 0) atomicAdd((int*)sDone, 1);
+                if (wdone && lane == 0) atomicAdd((int*)&sDoneRing[cur_seq % kDoneRing], 1);
             }
-            if (lane == 0) {
-                mbar_arrive(bar_tempty(t));
-                mbar_arrive(bar_empty(s));
-            }
-        }
-        if (!DUMP) {
-            const size_t plane = (size_t)a.W * a.H;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (h ? in_lo : in_up) {
-                    const size_t p = (size_t)(h ? py_lo : py_up) * a.W + px;
-                    const float Tf = h ? T.y + Tstop.y : T.x + Tstop.x;
-                    a.image[p] = (h ? Cr.y : Cr.x) + Tf * a.bg[0];
-                    a.image[plane + p] = (h ? Cg.y : Cg.x) + Tf * a.bg[1];
-                    a.image[2 * plane + p] = (h ? Cb.y : Cb.x) + Tf * a.bg[2];
-                    a.T_final[p] = Tf;
-                    a.n_contrib[p] = (int)(h ? last.y : last.x);
-                }
-            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_empty(s));
         }
     } else if (warp == kEpiWarps) {
         // ------------------------------------------------------- producer --
-        // reference pixels of the two halves and the pixel-offset box of a half
-        const float xc = (float)x0 + (origin ? 0.5f : 8.0f);
-        const float yc_up = (float)y0 + (origin ? 0.5f : 4.0f), yc_lo = yc_up + 8.0f;
-        const float bx0 = origin ? -15.0f : -7.5f, bx1 = origin ? 0.0f : 7.5f;
-        const float by0 = origin ? -7.0f : -3.5f, by1 = origin ? 0.0f : 3.5f;
-        for (int k = 0;; ++k) {
-            const int s = k % SS;
-            const uint32_t ps = (uint32_t)(k / SS) & 1u;
-            if (!mbar_wait_bounded(bar_empty(s), ps ^ 1u, tmo, sAbort)) {
-                *sAbort = 1;
-                atomicOr(a.err, kErrTimeout);
-                break;
+        int k = 0;
+        bool quit = false;
+        for (int seq = 0; !quit; ++seq) {
+            int q = 0;
+            if (lane == 0) q = (int)atomicAdd(a.queue, 1u);
+            q = __shfl_sync(0xffffffffu, q, 0);
+            const bool end = q >= n_items;
+            int tile = 0, len = 0;
+            uint32_t start = 0;
+            float xc = 0.f, yc_up = 0.f;
+            if (!end) {
+                tile = DUMP ? a.tiles[q] : q;
+                start = a.ranges[2 * tile];
+                const uint32_t stop = a.ranges[2 * tile + 1];
+                len = stop > start ? (int)(stop - start) : 0;
+                if (DUMP && len > a.max_len) len = a.max_len;
+                const ViewDesc vd = a.views[view_of(a, tile)];
+                const int lt = tile - vd.tile_begin;
+                xc = (float)((lt % vd.tiles_x) * kTile) + (origin ? 0.5f : 8.0f);
+                yc_up = (float)((lt / vd.tiles_x) * kTile) + (origin ? 0.5f : 4.0f);
+                if (lane == 0) sDoneRing[seq % kDoneRing] = 0;
             }
-            const bool stop = k >= nchunks || (!DUMP && *sDone >= kEpiWarps) || *sAbort;
-            if (stop) {
-                if (lane == 0) {
-                    sN[s] = 0;
-                    mbar_arrive(bar_full(s));
+            const float yc_lo = yc_up + 8.0f;
+            const float bx0 = origin ? -15.0f : -7.5f, bx1 = origin ? 0.0f : 7.5f;
+            const float by0 = origin ? -7.0f : -3.5f, by1 = origin ? 0.0f : 3.5f;
+            const int nch = end ? 1 : max(1, (len + CH - 1) / CH);
+            for (int c = 0; c < nch; ++c) {
+                const int s = k % SS;
+                const uint32_t ps = (uint32_t)(k / SS) & 1u;
+                if (!mbar_wait_bounded(bar_empty(s), ps ^ 1u, tmo, sAbort)) {
+                    *sAbort = 1;
+                    atomicOr(a.err, kErrTimeout);
+                    quit = true;
+                    break;
                 }
-                break;
-            }
-            const int base = k * CH;
-            const int n = min(CH, len - base);
-            uint8_t* mB = sB + s * LY::B_BYTES;
-            for (int j = lane; j < CH; j += 32) {
-                float vu[6], vl[6];
-                Rec rc;
-                if (j < n) {
-                    const uint32_t g = a.ids[start + base + j];
-                    const float2 m = a.mean2d[g];
-                    const float A = a.conic[3 * g], B = a.conic[3 * g + 1], C = a.conic[3 * g + 2];
-                    const float o = a.opac[g];
-                    const float l2o = o > 0.f ? __log2f(o) : -INFINITY;
-                    const float xh = m.x - xc;
-                    coeff_row<TR::HALF>(A, B, C, l2o, xh, m.y - yc_up, bx0, bx1, by0, by1, vu);
-                    coeff_row<TR::HALF>(A, B, C, l2o, xh, m.y - yc_lo, bx0, bx1, by0, by1, vl);
-                    const float cap = fminf(l2o, kLog2AlphaMax);
-                    float cr = 0.f, cg = 0.f, cb = 0.f;
-                    if (a.rgb) {
-                        cr = a.rgb[3 * g];
-                        cg = a.rgb[3 * g + 1];
-                        cb = a.rgb[3 * g + 2];
-                    }
-                    rc.rg = make_float4(cr, cr, cg, cg);
-                    rc.bc = make_float4(cb, cb, cap, cap);
-                } else {  // padding column: dead rows, no colour
+                if (*sAbort) {
+                    quit = true;
+                    break;
+                }
+                // every pixel of this tile has stopped: skip its remaining chunks
+                if (!DUMP && c > 0 && sDoneRing[seq % kDoneRing] >= kEpiWarps) break;
+                const int base = c * CH;
+                const int n = end ? -1 : min(CH, len - base);
+                if (n > 0) {
+                    uint8_t* mB = sB + s * LY::B_BYTES;
+                    for (int j = lane; j < CH; j += 32) {
+                        float vu[6], vl[6];
+                        Rec rc;
+                        if (j < n) {
+                            const uint32_t g = a.ids[start + base + j];
+                            const float2 m = a.mean2d[g];
+                            const float A = a.conic[3 * g], B = a.conic[3 * g + 1], C = a.conic[3 * g + 2];
+                            const float o = a.opac[g];
+                            const float l2o = o > 0.f ? __log2f(o) : -INFINITY;
+                            const float xh = m.x - xc;
+                            coeff_row<TR::HALF>(A, B, C, l2o, xh, m.y - yc_up, bx0, bx1, by0, by1, vu);
+                            coeff_row<TR::HALF>(A, B, C, l2o, xh, m.y - yc_lo, bx0, bx1, by0, by1, vl);
+                            const float cap = fminf(l2o, kLog2AlphaMax);
+                            float cr = 0.f, cg = 0.f, cb = 0.f;
+                            if (a.rgb) {
+                                cr = a.rgb[3 * g];
+                                cg = a.rgb[3 * g + 1];
+                                cb = a.rgb[3 * g + 2];
+                            }
+                            rc.rg = make_float4(cr, cr, cg, cg);
+                            rc.bc = make_float4(cb, cb, cap, cap);
+                        } else {  // padding column: dead rows, no colour
 #pragma unroll
-                    for (int i = 0; i < 5; ++i) vu[i] = vl[i] = 0.f;
-                    vu[5] = vl[5] = kDeadPower;
-                    rc.rg = make_float4(0.f, 0.f, 0.f, 0.f);
-                    rc.bc = make_float4(0.f, 0.f, 0.f, 0.f);
+                            for (int i = 0; i < 5; ++i) vu[i] = vl[i] = 0.f;
+                            vu[5] = vl[5] = kDeadPower;
+                            rc.rg = make_float4(0.f, 0.f, 0.f, 0.f);
+                            rc.bc = make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+                        store_coeff_row<V>(mB, j, vu);
+                        store_coeff_row<V>(mB, CH + j, vl);
+                        sRec[s * CH + j] = rc;
+                    }
                 }
-                store_coeff_row<V>(mB, j, vu);
-                store_coeff_row<V>(mB, CH + j, vl);
-                sRec[s * CH + j] = rc;
+                if (lane == 0) sHdr[s] = StageHdr{tile, end ? -2 : seq, base, n, q, {0, 0, 0}};
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar_full(s));
+                ++k;
             }
-            if (lane == 0) sN[s] = n;
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bar_full(s));
+            if (end) quit = true;
         }
     } else if (lane == 0) {
         // ------------------------------------------------------ MMA issue --
-        int last_t = -1;
-        uint32_t last_pt = 0;
         const uint32_t aA = smem_u32(sA);
         for (int k = 0;; ++k) {
             const int s = k % SS, t = k % kTStages;
@@ -461,14 +507,19 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(BlendArgs a) {
                 atomicOr(a.err, kErrTimeout);
                 break;
             }
-            if (sN[s] == 0) {
-                mbar_arrive(bar_tfull(t));
-                break;
-            }
+            // the TMEM stage must be free even for a stage without an MMA, so
+            // that tfull[t] never runs two phases ahead of a waiting epilogue warp
             if (!mbar_wait_bounded(bar_tempty(t), pt ^ 1u, tmo, sAbort)) {
                 *sAbort = 1;
                 atomicOr(a.err, kErrTimeout);
                 break;
+            }
+            const int n = sHdr[s].n;
+            if (n <= 0) {
+                mbar_arrive(bar_tfull(t));
+                if (n < 0) break;
+                mbar_arrive(bar_empty(s));
+                continue;
             }
             tc_fence_after();
             const uint32_t aB = smem_u32(sB + s * LY::B_BYTES);
@@ -480,10 +531,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(BlendArgs a) {
             }
             tc_commit(bar_tfull(t));
             tc_commit(bar_empty(s));
-            last_t = t;
-            last_pt = pt;
         }
-        if (last_t >= 0) mbar_wait_bounded(bar_tfull(last_t), last_pt, 1000000000ull, nullptr);
+        // every MMA this thread issued has finished before TMEM is freed (a
+        // fresh barrier: no phase of another stage can be mistaken for it)
+        tc_commit(bar_drain);
+        mbar_wait_bounded(bar_drain, 0, 1000000000ull, nullptr);
     }
 
     tc_fence_before();
@@ -492,12 +544,37 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(BlendArgs a) {
     if (warp == 5) tmem_dealloc(tmem, LY::TCOLS);
 }
 
+// Persistent grid: as many CTAs as fit on the GPU at once, from the kernel's
+// registers, shared memory and threads and the SM's 512 TMEM columns.
 template <int V, int CH, int SS, bool DUMP>
-cudaError_t launch_inst(const BlendArgs& a, int grid, cudaStream_t s) {
-    constexpr int bytes = Layout<SS, CH, V>::BYTES;
+cudaError_t launch_inst(const BlendArgs& a, int items, cudaStream_t s) {
+    using LY = Layout<SS, CH, V>;
+    constexpr int bytes = LY::BYTES;
     auto kern = k_blend_tc<V, CH, SS, DUMP>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return e;
+    static int per_sm = 0, sms = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+        int dev = 0, smem_sm = 0;
+        cudaFuncAttributes fa{};
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+            return e;
+        if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+        // registers are granted per warp in units of 256
+        const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+        const int by_regs = 65536 / (regs_warp * (kThreads / 32));
+        const int by_smem = smem_sm / (bytes + (int)fa.sharedSizeBytes + 1024);
+        const int by_threads = 2048 / kThreads;
+        const int by_tmem = (int)(512 / LY::TCOLS);
+        per_sm = by_regs;
+        if (by_smem < per_sm) per_sm = by_smem;
+        if (by_threads < per_sm) per_sm = by_threads;
+        if (by_tmem < per_sm) per_sm = by_tmem;
+        if (per_sm < 1) per_sm = 1;
+    }
+    const int grid = items < per_sm * sms ? (items > 0 ? items : 1) : per_sm * sms;
     kern<<<grid, kThreads, bytes, s>>>(a);
     count_launches();
     return cudaGetLastError();

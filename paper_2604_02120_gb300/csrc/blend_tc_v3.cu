@@ -10,7 +10,7 @@ cudaError_t launch_variant<3>(const BlendArgs& a, int chunk, int stages, bool du
     if (chunk == 32 && stages == 4) return launch_inst<3, 32, 4, false>(a, grid, s);
     if (chunk == 32 && stages == 2) return launch_inst<3, 32, 2, false>(a, grid, s);
     if (chunk == 16 && stages == 4) return launch_inst<3, 16, 4, false>(a, grid, s);
-    if (chunk == 64 && stages == 3) return launch_inst<3, 64, 3, false>(a, grid, s);
+    if (chunk == 16 && stages == 6) return launch_inst<3, 16, 6, false>(a, grid, s);
     return cudaErrorInvalidValue;
 }
 

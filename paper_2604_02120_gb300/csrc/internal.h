@@ -5,8 +5,22 @@
 
 namespace gs {
 
+constexpr int kMaxViews = 32;
+
+// One rendered view (camera) of a blend call.  Its tiles are numbered
+// [tile_begin, tile_begin + tiles_x * tiles_y) in the call's global tile
+// space; its outputs start at pixel offset pix_off of the packed per-view
+// arrays (image: 3 * pix_off floats in, CHW per view).
+struct ViewDesc {
+    int W, H, tiles_x, tile_begin;
+    long long pix_off;
+};
+
 struct BlendArgs {
-    int W, H, tiles_x, num_tiles;
+    int W, H, tiles_x, num_tiles;  // single-view shape (the FP32 kernels)
+    int num_views, total_tiles;    // view table (the tensor-core kernel)
+    ViewDesc views[kMaxViews];
+    unsigned* queue;               // tile counter, zero at launch (tensor-core kernel)
     const uint32_t* ranges;
     const uint32_t* ids;
     const float2* mean2d;
