@@ -45,8 +45,8 @@ KNOWN_TRAFFIC = {}
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
-    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--variant", default="fp16_split")
     p.add_argument("--config", type=int, default=1)
@@ -223,7 +223,7 @@ def run_ours(args):
             for _ in range(3):
                 gs.blend_forward(W, H, bs, proj, dev["opacities"], o)
             times = []
-            for _ in range(max(K, 10)):
+            for _ in range(min(max(K, 10), 50)):
                 flush.zero_()
                 a, b = E(), E()
                 a.record(stream)
@@ -236,7 +236,7 @@ def run_ours(args):
             blend[name] = {"ms_per_frame": round(ms, 5), "evals_per_s": ev / (ms / 1e3)}
         # backward (FP32 CUDA-core recompute) alone
         times = []
-        for _ in range(max(K, 10)):
+        for _ in range(min(max(K, 10), 50)):
             flush.zero_()
             a, b = E(), E()
             a.record(stream)
