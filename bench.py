@@ -39,7 +39,11 @@ MUFU_PER_CLK_SM = 16  # ex2/rcp results per clock per SM (CUDA programming guide
 
 # DRAM traffic per launch from ncu captures, keyed by kernel and the SHA-256 of
 # the kernel's source when it was measured (stale entries are not reported).
-KNOWN_TRAFFIC = {}
+KNOWN_TRAFFIC = {
+    # profiles/k_blend_fp32_bwd_1280x720_200k.md, profiles/k_blend_tc_fp16split_1280x720_200k.md
+    "k_blend_fp32_bwd": {"bytes": 32277760, "src": "bad5c4ccbc77e60c"},
+    "k_blend_tc<fp16_split>": {"bytes": 9733376, "src": "02347b0e95328919"},
+}
 
 
 def parse_args():
