@@ -118,8 +118,20 @@ gs_status gs_project(int32_t n, const float* means, const float* scales, const f
                      float* mean2d, float* conic, float* depth, int32_t* radius, float* rgb,
                      uint32_t* tiles_touched, gs_stream stream);
 
+/*
+ * gs_project_views - gs_project for n_views cameras in one launch (the batched
+ * rendering of many views).  `cams` is a HOST array of n_views (1..32)
+ * cameras; every output holds n_views blocks of n entries, view-major: view v,
+ * Gaussian g at index v * n + g (mean2d [n_views][n][2], conic [n_views][n][3], ...).
+ */
+gs_status gs_project_views(int32_t n, const float* means, const float* scales, const float* quats,
+                           const float* sh, int32_t sh_degree, const gs_camera* cams, int32_t n_views,
+                           float* mean2d, float* conic, float* depth, int32_t* radius, float* rgb,
+                           uint32_t* tiles_touched, gs_stream stream);
+
 /* Bytes of scratch gs_bin_sort needs for n Gaussians, `capacity` instances and
- * a width x height image.  `bytes` is a HOST pointer. */
+ * a width x height image.  `bytes` is a HOST pointer.  For gs_bin_sort_views
+ * pass n = n_views * n_per_view (the size does not depend on the image). */
 gs_status gs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t width, int32_t height,
                                      size_t* bytes);
 
@@ -143,6 +155,27 @@ gs_status gs_bin_sort(int32_t n, const float* mean2d, const int32_t* radius, con
                       void* workspace, size_t workspace_bytes,
                       uint64_t* keys_sorted, uint32_t* ids_sorted, uint32_t* tile_ranges,
                       int64_t* n_instances, gs_stream stream);
+
+/*
+ * gs_bin_sort_views - gs_bin_sort over the items of n_views views at once.
+ * Items are (view, Gaussian) pairs, item = v * n_per_view + g, laid out as
+ * gs_project_views writes them; widths/heights are HOST arrays.  View v owns
+ * the global tiles [T_v, T_v + tiles_x(v) * tiles_y(v)) with T_v the tile
+ * count of the views before it; keys carry the global tile id and ids_sorted
+ * the item index; tile_ranges has 2 * (total tiles) entries.
+ * Two modes:
+ *  - n_instances != NULL (HOST): as gs_bin_sort, synchronises once;
+ *  - n_instances == NULL, n_instances_dev != NULL (device int64): never
+ *    synchronises, so it can be captured in a CUDA graph.  Grids are sized by
+ *    `capacity`; the instance count is written to *n_instances_dev; if it
+ *    exceeds capacity the lists are truncated and gs_sync_status() later
+ *    returns GS_ERR_CAPACITY.
+ */
+gs_status gs_bin_sort_views(int32_t n_views, int32_t n_per_view, const float* mean2d, const int32_t* radius,
+                            const float* depth, const int32_t* widths, const int32_t* heights, int64_t capacity,
+                            void* workspace, size_t workspace_bytes, uint64_t* keys_sorted, uint32_t* ids_sorted,
+                            uint32_t* tile_ranges, int64_t* n_instances, int64_t* n_instances_dev,
+                            gs_stream stream);
 
 /*
  * gs_bin_sort_noalloc - gs_bin_sort for callers that cannot allocate device
@@ -206,6 +239,45 @@ gs_status gs_blend_backward(int32_t width, int32_t height, const uint32_t* tile_
                             const float* opacity, const float* rgb, const gs_blend_opts* opts,
                             const float* T_final, const int32_t* n_contrib, const float* dL_dimage,
                             float* dmean2d, float* dconic, float* dopacity, float* drgb,
+                            gs_stream stream);
+
+/*
+ * gs_blend_forward_views / gs_blend_backward_views - the blend of n_views
+ * views in one launch; for the tensor-core variants one persistent launch
+ * walks a single queue over the tiles of all views.  Inputs as produced by
+ * gs_project_views + gs_bin_sort_views (mean2d, conic, rgb per item; opacity
+ * per Gaussian, n_per_view entries).  Images are packed view after view:
+ * image holds 3 x H_v x W_v floats per view (CHW) starting at 3 * P_v, and
+ * T_final / n_contrib H_v x W_v entries starting at P_v, where P_v is the
+ * pixel count of the views before v; dL_dimage is laid out like image.
+ * Gradients: dmean2d / dconic / drgb per item, dopacity per Gaussian (summed
+ * over views).
+ */
+gs_status gs_blend_forward_views(int32_t n_views, const int32_t* widths, const int32_t* heights,
+                                 int32_t n_per_view, const uint32_t* tile_ranges, const uint32_t* ids_sorted,
+                                 const float* mean2d, const float* conic, const float* opacity, const float* rgb,
+                                 const gs_blend_opts* opts, float* image, float* T_final, int32_t* n_contrib,
+                                 gs_stream stream);
+gs_status gs_blend_backward_views(int32_t n_views, const int32_t* widths, const int32_t* heights,
+                                  int32_t n_per_view, const uint32_t* tile_ranges, const uint32_t* ids_sorted,
+                                  const float* mean2d, const float* conic, const float* opacity, const float* rgb,
+                                  const gs_blend_opts* opts, const float* T_final, const int32_t* n_contrib,
+                                  const float* dL_dimage, float* dmean2d, float* dconic, float* dopacity,
+                                  float* drgb, gs_stream stream);
+
+/*
+ * gs_blend_autotune - pick the pipeline shape of a tensor-core blend by
+ * measurement: runs gs_blend_forward_views once per built (chunk, stages)
+ * pair (one warm-up, then `reps` timed runs with CUDA events on `stream`) and
+ * writes the fastest pair into opts->chunk / opts->stages (opts is a HOST
+ * pointer; its variant must be a TC variant).  image / T_final / n_contrib
+ * are overwritten.  Synchronises the stream.  *best_ms (HOST, may be NULL)
+ * receives the mean time of the chosen pair.
+ */
+gs_status gs_blend_autotune(int32_t n_views, const int32_t* widths, const int32_t* heights, int32_t n_per_view,
+                            const uint32_t* tile_ranges, const uint32_t* ids_sorted, const float* mean2d,
+                            const float* conic, const float* opacity, const float* rgb, gs_blend_opts* opts,
+                            float* image, float* T_final, int32_t* n_contrib, int32_t reps, float* best_ms,
                             gs_stream stream);
 
 /*

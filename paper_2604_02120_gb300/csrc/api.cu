@@ -62,12 +62,34 @@ using namespace gs;
 
 namespace {
 
-gs_status check_blend_common(int32_t W, int32_t H, const uint32_t* ranges, const uint32_t* ids, const float* mean2d,
-                             const float* conic, const float* opacity) {
-    if (W <= 0 || H <= 0 || W > (1 << 20) || H > (1 << 20)) {
-        set_error("image size %d x %d out of range", W, H);
+bool size_ok(int32_t W, int32_t H) { return W > 0 && H > 0 && W <= (1 << 20) && H <= (1 << 20); }
+
+// View table of n_views images (HOST arrays); false if a size is out of range
+// or the views hold 2^31 tiles or more.
+bool fill_views(int32_t n_views, const int32_t* widths, const int32_t* heights, ViewDesc* views, int* total_tiles) {
+    long long tiles = 0, pix = 0;
+    for (int v = 0; v < n_views; ++v) {
+        if (!size_ok(widths[v], heights[v])) return false;
+        views[v] = ViewDesc{widths[v], heights[v], tiles_x(widths[v]), (int)tiles, pix};
+        tiles += (long long)tiles_x(widths[v]) * tiles_y(heights[v]);
+        pix += (long long)widths[v] * heights[v];
+        if (tiles >= (1ll << 31)) return false;
+    }
+    *total_tiles = (int)tiles;
+    return true;
+}
+
+gs_status check_views(const char* who, int32_t n_views, const int32_t* widths, const int32_t* heights) {
+    if (n_views < 1 || n_views > kMaxViews || !widths || !heights) {
+        set_error("%s: n_views must be 1..%d with width/height arrays", who, kMaxViews);
         return GS_ERR_INVALID_ARG;
     }
+    return GS_OK;
+}
+
+
+gs_status check_blend_common(const uint32_t* ranges, const uint32_t* ids, const float* mean2d, const float* conic,
+                             const float* opacity) {
     if (!ranges || !ids || !mean2d || !conic || !opacity) {
         set_error("null input pointer");
         return GS_ERR_INVALID_ARG;
@@ -75,13 +97,18 @@ gs_status check_blend_common(int32_t W, int32_t H, const uint32_t* ranges, const
     return GS_OK;
 }
 
-BlendArgs make_args(int32_t W, int32_t H, const uint32_t* ranges, const uint32_t* ids, const float* mean2d,
-                    const float* conic, const float* opacity, const float* rgb, const gs_blend_opts* o) {
-    BlendArgs a{};
-    a.W = W;
-    a.H = H;
-    a.tiles_x = tiles_x(W);
-    a.num_tiles = tiles_x(W) * tiles_y(H);
+// Blend arguments for n_views views of n_per_view Gaussians each (false: bad sizes).
+bool make_args(BlendArgs& a, int32_t n_views, const int32_t* widths, const int32_t* heights, int32_t n_per_view,
+               const uint32_t* ranges, const uint32_t* ids, const float* mean2d, const float* conic,
+               const float* opacity, const float* rgb, const gs_blend_opts* o) {
+    a = BlendArgs{};
+    if (!fill_views(n_views, widths, heights, a.views, &a.total_tiles)) return false;
+    a.num_views = n_views;
+    a.n_per_view = n_per_view;
+    a.W = widths[0];
+    a.H = heights[0];
+    a.tiles_x = tiles_x(a.W);
+    a.num_tiles = tiles_x(a.W) * tiles_y(a.H);
     a.ranges = ranges;
     a.ids = ids;
     a.mean2d = reinterpret_cast<const float2*>(mean2d);
@@ -92,10 +119,7 @@ BlendArgs make_args(int32_t W, int32_t H, const uint32_t* ranges, const uint32_t
     a.timeout_ns = (o && o->timeout_ns > 0) ? (uint64_t)o->timeout_ns : 1000000000ull;
     a.ref_origin = o ? o->ref_origin : 0;
     a.err = error_word();
-    a.num_views = 1;
-    a.total_tiles = a.num_tiles;
-    a.views[0] = ViewDesc{W, H, a.tiles_x, 0, 0};
-    return a;
+    return true;
 }
 
 bool is_tc(int v) { return v >= GS_BLEND_TC_FP16 && v <= GS_BLEND_TC_BF16_SPLIT; }
@@ -123,45 +147,60 @@ const char* gs_status_string(gs_status s) {
 
 const char* gs_last_error(void) { return g_last_error; }
 
-gs_status gs_project(int32_t n, const float* means, const float* scales, const float* quats, const float* sh,
-                     int32_t sh_degree, const gs_camera* cam, float* mean2d, float* conic, float* depth,
-                     int32_t* radius, float* rgb, uint32_t* tiles_touched, gs_stream stream) {
+gs_status gs_project_views(int32_t n, const float* means, const float* scales, const float* quats, const float* sh,
+                           int32_t sh_degree, const gs_camera* cams, int32_t n_views, float* mean2d, float* conic,
+                           float* depth, int32_t* radius, float* rgb, uint32_t* tiles_touched, gs_stream stream) {
     g_last_error[0] = 0;
-    if (n < 0 || sh_degree < 0 || sh_degree > 3 || !cam) {
-        set_error("gs_project: bad n (%d), sh_degree (%d) or camera", n, sh_degree);
+    if (n < 0 || sh_degree < 0 || sh_degree > 3 || !cams || n_views < 1 || n_views > kMaxViews) {
+        set_error("gs_project: bad n (%d), sh_degree (%d), cameras or n_views (%d)", n, sh_degree, n_views);
         return GS_ERR_INVALID_ARG;
     }
-    if (cam->width <= 0 || cam->height <= 0 || cam->width > (1 << 20) || cam->height > (1 << 20)) {
-        set_error("gs_project: image size %d x %d out of range", cam->width, cam->height);
+    if ((long long)n * n_views >= (1ll << 32)) {
+        set_error("gs_project: n * n_views must be below 2^32");
         return GS_ERR_INVALID_ARG;
+    }
+    CamViews cv{};
+    cv.num_views = n_views;
+    for (int v = 0; v < n_views; ++v) {
+        const gs_camera* cam = cams + v;
+        if (!size_ok(cam->width, cam->height)) {
+            set_error("gs_project: image size %d x %d out of range", cam->width, cam->height);
+            return GS_ERR_INVALID_ARG;
+        }
+        CamDev& c = cv.cams[v];
+        c.W = cam->width;
+        c.H = cam->height;
+        c.fx = cam->fx;
+        c.fy = cam->fy;
+        c.cx = cam->cx;
+        c.cy = cam->cy;
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) c.R[3 * i + j] = cam->world_to_cam[4 * i + j];
+            c.t[i] = cam->world_to_cam[4 * i + 3];
+        }
+        c.znear = cam->znear;
+        c.lowpass = cam->lowpass;
     }
     if (n == 0) return GS_OK;
     if (!means || !scales || !quats || !sh || !mean2d || !conic || !depth || !radius || !rgb || !tiles_touched) {
         set_error("gs_project: null pointer");
         return GS_ERR_INVALID_ARG;
     }
-    CamDev c{};
-    c.W = cam->width;
-    c.H = cam->height;
-    c.fx = cam->fx;
-    c.fy = cam->fy;
-    c.cx = cam->cx;
-    c.cy = cam->cy;
-    for (int i = 0; i < 3; ++i) {
-        for (int j = 0; j < 3; ++j) c.R[3 * i + j] = cam->world_to_cam[4 * i + j];
-        c.t[i] = cam->world_to_cam[4 * i + 3];
-    }
-    c.znear = cam->znear;
-    c.lowpass = cam->lowpass;
-    return cuda_status(launch_project(n, means, scales, quats, sh, sh_degree, c, mean2d, conic, depth, radius, rgb,
+    return cuda_status(launch_project(n, means, scales, quats, sh, sh_degree, cv, mean2d, conic, depth, radius, rgb,
                                       tiles_touched, stream),
                        "gs_project launch");
 }
 
+gs_status gs_project(int32_t n, const float* means, const float* scales, const float* quats, const float* sh,
+                     int32_t sh_degree, const gs_camera* cam, float* mean2d, float* conic, float* depth,
+                     int32_t* radius, float* rgb, uint32_t* tiles_touched, gs_stream stream) {
+    return gs_project_views(n, means, scales, quats, sh, sh_degree, cam, 1, mean2d, conic, depth, radius, rgb,
+                            tiles_touched, stream);
+}
+
 gs_status gs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t width, int32_t height, size_t* bytes) {
     g_last_error[0] = 0;
-    if (n < 0 || capacity < 0 || capacity >= (int64_t(1) << 32) || width <= 0 || height <= 0 || !bytes ||
-        width > (1 << 20) || height > (1 << 20)) {
+    if (n < 0 || capacity < 0 || capacity >= (int64_t(1) << 32) || !size_ok(width, height) || !bytes) {
         set_error("gs_bin_sort_workspace_size: bad arguments");
         return GS_ERR_INVALID_ARG;
     }
@@ -169,17 +208,27 @@ gs_status gs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t width,
     return GS_OK;
 }
 
-gs_status gs_bin_sort(int32_t n, const float* mean2d, const int32_t* radius, const float* depth, int32_t width,
-                      int32_t height, int64_t capacity, void* workspace, size_t workspace_bytes,
-                      uint64_t* keys_sorted, uint32_t* ids_sorted, uint32_t* tile_ranges, int64_t* n_instances,
-                      gs_stream stream) {
+gs_status gs_bin_sort_views(int32_t n_views, int32_t n_per_view, const float* mean2d, const int32_t* radius,
+                            const float* depth, const int32_t* widths, const int32_t* heights, int64_t capacity,
+                            void* workspace, size_t workspace_bytes, uint64_t* keys_sorted, uint32_t* ids_sorted,
+                            uint32_t* tile_ranges, int64_t* n_instances, int64_t* n_instances_dev, gs_stream stream) {
     g_last_error[0] = 0;
-    if (n < 0 || capacity < 0 || capacity >= (int64_t(1) << 32) || width <= 0 || height <= 0 ||
-        width > (1 << 20) || height > (1 << 20) || !n_instances || !tile_ranges) {
+    gs_status st = check_views("gs_bin_sort", n_views, widths, heights);
+    if (st != GS_OK) return st;
+    if (n_per_view < 0 || capacity < 0 || capacity >= (int64_t(1) << 32) || !tile_ranges ||
+        (!n_instances && !n_instances_dev) || (long long)n_per_view * n_views >= (1ll << 31)) {
         set_error("gs_bin_sort: bad arguments");
         return GS_ERR_INVALID_ARG;
     }
-    if (n > 0 && (!mean2d || !radius || !depth || !workspace)) {
+    SortViews sv{};
+    sv.num_views = n_views;
+    sv.n_per_view = n_per_view;
+    if (!fill_views(n_views, widths, heights, sv.views, &sv.total_tiles)) {
+        set_error("gs_bin_sort: image size out of range");
+        return GS_ERR_INVALID_ARG;
+    }
+    const int items = n_views * n_per_view;
+    if (items > 0 && (!mean2d || !radius || !depth || !workspace)) {
         set_error("gs_bin_sort: null pointer");
         return GS_ERR_INVALID_ARG;
     }
@@ -191,29 +240,48 @@ gs_status gs_bin_sort(int32_t n, const float* mean2d, const int32_t* radius, con
         set_error("gs_bin_sort: workspace must be 256-byte aligned");
         return GS_ERR_INVALID_ARG;
     }
-    size_t need = bin_sort_workspace_bytes(n, capacity, tiles_x(width) * tiles_y(height));
+    const size_t need = bin_sort_workspace_bytes(items, capacity, sv.total_tiles);
     if (workspace_bytes < need) {
         set_error("gs_bin_sort: workspace %zu bytes < %zu needed", workspace_bytes, need);
         return GS_ERR_WORKSPACE;
     }
-    return bin_sort_run(n, mean2d, radius, depth, width, height, capacity, workspace, workspace_bytes, keys_sorted,
-                        ids_sorted, tile_ranges, n_instances, stream);
+    return bin_sort_run(sv, mean2d, radius, depth, capacity, workspace, workspace_bytes, keys_sorted, ids_sorted,
+                        tile_ranges, n_instances, n_instances ? nullptr : n_instances_dev, stream);
 }
 
-gs_status gs_blend_forward(int32_t width, int32_t height, const uint32_t* tile_ranges, const uint32_t* ids_sorted,
-                           const float* mean2d, const float* conic, const float* opacity, const float* rgb,
-                           const gs_blend_opts* opts, float* image, float* T_final, int32_t* n_contrib,
-                           gs_stream stream) {
+gs_status gs_bin_sort(int32_t n, const float* mean2d, const int32_t* radius, const float* depth, int32_t width,
+                      int32_t height, int64_t capacity, void* workspace, size_t workspace_bytes,
+                      uint64_t* keys_sorted, uint32_t* ids_sorted, uint32_t* tile_ranges, int64_t* n_instances,
+                      gs_stream stream) {
+    if (!n_instances) {
+        set_error("gs_bin_sort: n_instances must be a host pointer");
+        return GS_ERR_INVALID_ARG;
+    }
+    return gs_bin_sort_views(1, n, mean2d, radius, depth, &width, &height, capacity, workspace, workspace_bytes,
+                             keys_sorted, ids_sorted, tile_ranges, n_instances, nullptr, stream);
+}
+
+gs_status gs_blend_forward_views(int32_t n_views, const int32_t* widths, const int32_t* heights,
+                                 int32_t n_per_view, const uint32_t* tile_ranges, const uint32_t* ids_sorted,
+                                 const float* mean2d, const float* conic, const float* opacity, const float* rgb,
+                                 const gs_blend_opts* opts, float* image, float* T_final, int32_t* n_contrib,
+                                 gs_stream stream) {
     g_last_error[0] = 0;
-    gs_status st = check_blend_common(width, height, tile_ranges, ids_sorted, mean2d, conic, opacity);
+    gs_status st = check_views("gs_blend_forward", n_views, widths, heights);
     if (st != GS_OK) return st;
-    if (!rgb || !image || !T_final || !n_contrib) {
-        set_error("gs_blend_forward: null pointer");
+    st = check_blend_common(tile_ranges, ids_sorted, mean2d, conic, opacity);
+    if (st != GS_OK) return st;
+    if (!rgb || !image || !T_final || !n_contrib || n_per_view < 0) {
+        set_error("gs_blend_forward: null pointer or negative n_per_view");
         return GS_ERR_INVALID_ARG;
     }
     gs_blend_opts def{};
     const gs_blend_opts* o = opts ? opts : &def;
-    BlendArgs a = make_args(width, height, tile_ranges, ids_sorted, mean2d, conic, opacity, rgb, o);
+    BlendArgs a;
+    if (!make_args(a, n_views, widths, heights, n_per_view, tile_ranges, ids_sorted, mean2d, conic, opacity, rgb, o)) {
+        set_error("gs_blend_forward: image size out of range");
+        return GS_ERR_INVALID_ARG;
+    }
     a.image = image;
     a.T_final = T_final;
     a.n_contrib = n_contrib;
@@ -228,20 +296,32 @@ gs_status gs_blend_forward(int32_t width, int32_t height, const uint32_t* tile_r
         set_error("gs_blend_forward: chunk %d / stages %d not built", chunk, stages);
         return GS_ERR_UNSUPPORTED;
     }
-    return cuda_status(launch_blend_tc(a, o->variant, chunk, stages, false, a.num_tiles, stream),
+    return cuda_status(launch_blend_tc(a, o->variant, chunk, stages, false, a.total_tiles, stream),
                        "gs_blend_forward tc");
 }
 
-gs_status gs_blend_backward(int32_t width, int32_t height, const uint32_t* tile_ranges, const uint32_t* ids_sorted,
-                            const float* mean2d, const float* conic, const float* opacity, const float* rgb,
-                            const gs_blend_opts* opts, const float* T_final, const int32_t* n_contrib,
-                            const float* dL_dimage, float* dmean2d, float* dconic, float* dopacity, float* drgb,
-                            gs_stream stream) {
+gs_status gs_blend_forward(int32_t width, int32_t height, const uint32_t* tile_ranges, const uint32_t* ids_sorted,
+                           const float* mean2d, const float* conic, const float* opacity, const float* rgb,
+                           const gs_blend_opts* opts, float* image, float* T_final, int32_t* n_contrib,
+                           gs_stream stream) {
+    return gs_blend_forward_views(1, &width, &height, 0, tile_ranges, ids_sorted, mean2d, conic, opacity, rgb, opts,
+                                  image, T_final, n_contrib, stream);
+}
+
+gs_status gs_blend_backward_views(int32_t n_views, const int32_t* widths, const int32_t* heights,
+                                  int32_t n_per_view, const uint32_t* tile_ranges, const uint32_t* ids_sorted,
+                                  const float* mean2d, const float* conic, const float* opacity, const float* rgb,
+                                  const gs_blend_opts* opts, const float* T_final, const int32_t* n_contrib,
+                                  const float* dL_dimage, float* dmean2d, float* dconic, float* dopacity,
+                                  float* drgb, gs_stream stream) {
     g_last_error[0] = 0;
-    gs_status st = check_blend_common(width, height, tile_ranges, ids_sorted, mean2d, conic, opacity);
+    gs_status st = check_views("gs_blend_backward", n_views, widths, heights);
     if (st != GS_OK) return st;
-    if (!rgb || !T_final || !n_contrib || !dL_dimage || !dmean2d || !dconic || !dopacity || !drgb) {
-        set_error("gs_blend_backward: null pointer");
+    st = check_blend_common(tile_ranges, ids_sorted, mean2d, conic, opacity);
+    if (st != GS_OK) return st;
+    if (!rgb || !T_final || !n_contrib || !dL_dimage || !dmean2d || !dconic || !dopacity || !drgb ||
+        n_per_view < 0) {
+        set_error("gs_blend_backward: null pointer or negative n_per_view");
         return GS_ERR_INVALID_ARG;
     }
     gs_blend_opts def{};
@@ -250,16 +330,81 @@ gs_status gs_blend_backward(int32_t width, int32_t height, const uint32_t* tile_
         set_error("gs_blend_backward: unknown variant %d", o->variant);
         return GS_ERR_INVALID_ARG;
     }
-    BlendArgs a = make_args(width, height, tile_ranges, ids_sorted, mean2d, conic, opacity, rgb, o);
+    BlendArgs a;
+    if (!make_args(a, n_views, widths, heights, n_per_view, tile_ranges, ids_sorted, mean2d, conic, opacity, rgb, o)) {
+        set_error("gs_blend_backward: image size out of range");
+        return GS_ERR_INVALID_ARG;
+    }
     GradArgs g{T_final, n_contrib, dL_dimage, reinterpret_cast<float2*>(dmean2d), dconic, dopacity, drgb};
     return cuda_status(launch_blend_fp32_bwd(a, g, stream), "gs_blend_backward");
+}
+
+gs_status gs_blend_backward(int32_t width, int32_t height, const uint32_t* tile_ranges, const uint32_t* ids_sorted,
+                            const float* mean2d, const float* conic, const float* opacity, const float* rgb,
+                            const gs_blend_opts* opts, const float* T_final, const int32_t* n_contrib,
+                            const float* dL_dimage, float* dmean2d, float* dconic, float* dopacity, float* drgb,
+                            gs_stream stream) {
+    return gs_blend_backward_views(1, &width, &height, 0, tile_ranges, ids_sorted, mean2d, conic, opacity, rgb, opts,
+                                   T_final, n_contrib, dL_dimage, dmean2d, dconic, dopacity, drgb, stream);
+}
+
+gs_status gs_blend_autotune(int32_t n_views, const int32_t* widths, const int32_t* heights, int32_t n_per_view,
+                            const uint32_t* tile_ranges, const uint32_t* ids_sorted, const float* mean2d,
+                            const float* conic, const float* opacity, const float* rgb, gs_blend_opts* opts,
+                            float* image, float* T_final, int32_t* n_contrib, int32_t reps, float* best_ms,
+                            gs_stream stream) {
+    g_last_error[0] = 0;
+    if (!opts || !is_tc(opts->variant) || reps < 1) {
+        set_error("gs_blend_autotune: needs a TC variant and reps >= 1");
+        return GS_ERR_INVALID_ARG;
+    }
+    static const int kShapes[][2] = {{32, 2}, {32, 4}, {16, 4}, {16, 6}};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    gs_status st = cuda_status(cudaEventCreate(&e0), "gs_blend_autotune: event");
+    if (st == GS_OK) st = cuda_status(cudaEventCreate(&e1), "gs_blend_autotune: event");
+    float best = 1e30f;
+    int best_i = -1;
+    for (int i = 0; st == GS_OK && i < (int)(sizeof(kShapes) / sizeof(kShapes[0])); ++i) {
+        gs_blend_opts o = *opts;
+        o.chunk = kShapes[i][0];
+        o.stages = kShapes[i][1];
+        if (!tc_config_supported(o.variant, o.chunk, o.stages)) continue;
+        st = gs_blend_forward_views(n_views, widths, heights, n_per_view, tile_ranges, ids_sorted, mean2d, conic,
+                                    opacity, rgb, &o, image, T_final, n_contrib, stream);
+        if (st != GS_OK) break;
+        if ((st = cuda_status(cudaEventRecord(e0, stream), "gs_blend_autotune: record")) != GS_OK) break;
+        for (int r = 0; st == GS_OK && r < reps; ++r)
+            st = gs_blend_forward_views(n_views, widths, heights, n_per_view, tile_ranges, ids_sorted, mean2d, conic,
+                                        opacity, rgb, &o, image, T_final, n_contrib, stream);
+        if (st != GS_OK) break;
+        if ((st = cuda_status(cudaEventRecord(e1, stream), "gs_blend_autotune: record")) != GS_OK) break;
+        if ((st = cuda_status(cudaEventSynchronize(e1), "gs_blend_autotune: synchronize")) != GS_OK) break;
+        float ms = 0.f;
+        if ((st = cuda_status(cudaEventElapsedTime(&ms, e0, e1), "gs_blend_autotune: elapsed")) != GS_OK) break;
+        ms /= (float)reps;
+        if (ms < best) {
+            best = ms;
+            best_i = i;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st != GS_OK) return st;
+    if (best_i < 0) {
+        set_error("gs_blend_autotune: no pipeline shape built for variant %d", opts->variant);
+        return GS_ERR_UNSUPPORTED;
+    }
+    opts->chunk = kShapes[best_i][0];
+    opts->stages = kShapes[best_i][1];
+    if (best_ms) *best_ms = best;
+    return gs_sync_status(stream);
 }
 
 gs_status gs_tile_power(int32_t width, int32_t height, const uint32_t* tile_ranges, const uint32_t* ids_sorted,
                         const float* mean2d, const float* conic, const float* opacity, const gs_blend_opts* opts,
                         const int32_t* tiles, int32_t n_tiles, int32_t max_len, float* out, gs_stream stream) {
     g_last_error[0] = 0;
-    gs_status st = check_blend_common(width, height, tile_ranges, ids_sorted, mean2d, conic, opacity);
+    gs_status st = check_blend_common(tile_ranges, ids_sorted, mean2d, conic, opacity);
     if (st != GS_OK) return st;
     if (!opts || !is_tc(opts->variant) || n_tiles < 0 || max_len < 0 || (n_tiles > 0 && (!tiles || !out))) {
         set_error("gs_tile_power: bad arguments");
@@ -271,7 +416,11 @@ gs_status gs_tile_power(int32_t width, int32_t height, const uint32_t* tile_rang
         set_error("gs_tile_power: chunk %d / stages %d not built", chunk, stages);
         return GS_ERR_UNSUPPORTED;
     }
-    BlendArgs a = make_args(width, height, tile_ranges, ids_sorted, mean2d, conic, opacity, nullptr, opts);
+    BlendArgs a;
+    if (!make_args(a, 1, &width, &height, 0, tile_ranges, ids_sorted, mean2d, conic, opacity, nullptr, opts)) {
+        set_error("gs_tile_power: image size out of range");
+        return GS_ERR_INVALID_ARG;
+    }
     a.tiles = tiles;
     a.max_len = max_len;
     a.dump = out;
@@ -294,6 +443,10 @@ gs_status gs_sync_status(gs_stream stream) {
     if (v & kErrTimeout) {
         set_error("a device-side wait exceeded its time limit");
         return GS_ERR_TIMEOUT;
+    }
+    if (v & kErrCapacity) {
+        set_error("a bin/sort without synchronisation had more instances than its capacity");
+        return GS_ERR_CAPACITY;
     }
     set_error("device error word 0x%x", v);
     return GS_ERR_CUDA;

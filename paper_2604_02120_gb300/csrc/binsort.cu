@@ -141,9 +141,18 @@ cudaError_t scan_exclusive(const T* in, T* out, int64_t n, T* scratch, bool writ
 
 // ------------------------------------------------------------- radix sort --
 
-__global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restrict__ keys, uint32_t n, int shift,
+// Item count of a pass: the host value, or min(*n_dev, host value) in graph mode.
+__device__ __forceinline__ uint32_t pass_count(uint32_t n_host, const uint64_t* n_dev) {
+    if (n_dev == nullptr) return n_host;
+    const uint64_t v = *n_dev;
+    return v < n_host ? (uint32_t)v : n_host;
+}
+
+__global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restrict__ keys, uint32_t n_host,
+                                                         const uint64_t* __restrict__ n_dev, int shift,
                                                          uint32_t* __restrict__ hist, int nblk) {
     __shared__ uint32_t s_cnt[256];
+    const uint32_t n = pass_count(n_host, n_dev);
     s_cnt[threadIdx.x] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kTileItems;
@@ -159,10 +168,12 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restr
 // Stable scatter: warp w owns the contiguous items [w*512, w*512 + 512) of the
 // block's tile, walked in rounds of 32 so lane order = input order.
 __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __restrict__ kin,
-                                                            const uint32_t* __restrict__ vin, uint32_t n, int shift,
+                                                            const uint32_t* __restrict__ vin, uint32_t n_host,
+                                                            const uint64_t* __restrict__ n_dev, int shift,
                                                             const uint32_t* __restrict__ offs, int nblk,
                                                             uint32_t* __restrict__ kout, uint32_t* __restrict__ vout) {
     __shared__ uint32_t s_w[kThreads / 32][256];
+    const uint32_t n = pass_count(n_host, n_dev);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < (kThreads / 32) * 256; i += kThreads) (&s_w[0][0])[i] = 0;
     __syncthreads();
@@ -219,27 +230,28 @@ struct RadixScratch {
     uint32_t* scan;
 };
 
-// One stable pass on bits [shift, shift + 8).
+// One stable pass on bits [shift, shift + 8) over n items (at most n, the
+// actual count in *n_dev, in graph mode).
 cudaError_t radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, uint32_t n,
-                       int shift, RadixScratch rs, cudaStream_t s) {
+                       const uint64_t* n_dev, int shift, RadixScratch rs, cudaStream_t s) {
     const int nblk = cdiv(n, kTileItems);
-    k_radix_hist<<<nblk, kThreads, 0, s>>>(kin, n, shift, rs.hist, nblk);
+    k_radix_hist<<<nblk, kThreads, 0, s>>>(kin, n, n_dev, shift, rs.hist, nblk);
     count_launches();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = scan_exclusive<uint32_t>(rs.hist, rs.hist, (int64_t)256 * nblk, rs.scan, false, s);
     if (e != cudaSuccess) return e;
-    k_radix_scatter<<<nblk, kThreads, 0, s>>>(kin, vin, n, shift, rs.hist, nblk, kout, vout);
+    k_radix_scatter<<<nblk, kThreads, 0, s>>>(kin, vin, n, n_dev, shift, rs.hist, nblk, kout, vout);
     count_launches();
     return cudaGetLastError();
 }
 
 // Sorts (k[0], v[0]) on bits [0, bits); the result ends in buffer *which.
-cudaError_t radix_sort(uint32_t* k[2], uint32_t* v[2], uint32_t n, int bits, RadixScratch rs, int* which,
-                       cudaStream_t s) {
+cudaError_t radix_sort(uint32_t* k[2], uint32_t* v[2], uint32_t n, const uint64_t* n_dev, int bits, RadixScratch rs,
+                       int* which, cudaStream_t s) {
     int cur = 0;
     for (int shift = 0; shift < bits; shift += 8) {
-        cudaError_t e = radix_pass(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], n, shift, rs, s);
+        cudaError_t e = radix_pass(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], n, n_dev, shift, rs, s);
         if (e != cudaSuccess) return e;
         cur ^= 1;
     }
@@ -249,18 +261,19 @@ cudaError_t radix_sort(uint32_t* k[2], uint32_t* v[2], uint32_t n, int bits, Rad
 
 // ------------------------------------------------------ duplicate/finalize --
 
-__global__ void k_count(int n, const float2* __restrict__ mean2d, const int* __restrict__ radius,
-                        const float* __restrict__ depth, int W, int H, uint32_t* __restrict__ cnt,
+__global__ void k_count(int n_items, const __grid_constant__ SortViews sv, const float2* __restrict__ mean2d,
+                        const int* __restrict__ radius, const float* __restrict__ depth, uint32_t* __restrict__ cnt,
                         uint32_t* __restrict__ dkey, uint32_t* __restrict__ dval) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_items) return;
+    const ViewDesc& vd = sv.views[i / sv.n_per_view];
     int x0, x1, y0, y1;
-    const float2 m = mean2d[g];
+    const float2 m = mean2d[i];
     uint32_t c = 0;
-    if (tile_rect(m.x, m.y, radius[g], W, H, x0, x1, y0, y1)) c = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
-    cnt[g] = c;
-    dkey[g] = __float_as_uint(depth[g]);
-    dval[g] = (uint32_t)g;
+    if (tile_rect(m.x, m.y, radius[i], vd.W, vd.H, x0, x1, y0, y1)) c = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+    cnt[i] = c;
+    dkey[i] = __float_as_uint(depth[i]);
+    dval[i] = (uint32_t)i;
 }
 
 __global__ void k_gather_counts(int n, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ cnt,
@@ -269,34 +282,50 @@ __global__ void k_gather_counts(int n, const uint32_t* __restrict__ perm, const 
     if (k < n) out[k] = cnt[perm[k]];
 }
 
-// One thread per instance: find its Gaussian by binary search over the
-// depth-ordered exclusive offsets, then its tile inside the rectangle.
-__global__ void k_duplicate(uint32_t I, int n, const uint64_t* __restrict__ offs, const uint32_t* __restrict__ perm,
-                            const float2* __restrict__ mean2d, const int* __restrict__ radius, int W, int H,
-                            uint32_t* __restrict__ tkey, uint32_t* __restrict__ tval) {
+// One thread per instance: find its item by binary search over the
+// depth-ordered exclusive offsets, then its tile inside the rectangle.  In
+// graph mode the count comes from offs[n_items] and is clamped to capacity
+// (overflow sets kErrCapacity); block 0 also stores the count for the caller.
+__global__ void k_duplicate(uint32_t I_host, int64_t capacity, int n_items, const uint64_t* __restrict__ offs,
+                            const uint32_t* __restrict__ perm, const __grid_constant__ SortViews sv,
+                            const float2* __restrict__ mean2d, const int* __restrict__ radius,
+                            uint32_t* __restrict__ tkey, uint32_t* __restrict__ tval, int64_t* __restrict__ count_out,
+                            unsigned* __restrict__ err) {
+    uint32_t I = I_host;
+    if (count_out != nullptr) {  // graph mode
+        const uint64_t total = offs[n_items];
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            *count_out = (int64_t)total;
+            if (total > (uint64_t)capacity) atomicOr(err, kErrCapacity);
+        }
+        I = total < (uint64_t)capacity ? (uint32_t)total : (uint32_t)capacity;
+    }
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= I) return;
     // largest k with offs[k] <= i
-    int lo = 0, hi = n - 1;
+    int lo = 0, hi = n_items - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
         if (offs[mid] <= i) lo = mid;
         else hi = mid - 1;
     }
-    const uint32_t g = perm[lo];
+    const uint32_t item = perm[lo];
     const uint32_t j = i - (uint32_t)offs[lo];
+    const ViewDesc& vd = sv.views[item / (uint32_t)sv.n_per_view];
     int x0, x1, y0, y1;
-    const float2 m = mean2d[g];
-    tile_rect(m.x, m.y, radius[g], W, H, x0, x1, y0, y1);
+    const float2 m = mean2d[item];
+    tile_rect(m.x, m.y, radius[item], vd.W, vd.H, x0, x1, y0, y1);
     const uint32_t w = (uint32_t)(x1 - x0 + 1);
     const uint32_t ty = (uint32_t)y0 + j / w, tx = (uint32_t)x0 + j % w;
-    tkey[i] = ty * (uint32_t)tiles_x(W) + tx;
-    tval[i] = g;
+    tkey[i] = (uint32_t)vd.tile_begin + ty * (uint32_t)vd.tiles_x + tx;
+    tval[i] = item;
 }
 
-__global__ void k_finalize(uint32_t I, const uint32_t* __restrict__ tkey, const uint32_t* __restrict__ tval,
-                           const float* __restrict__ depth, uint64_t* __restrict__ keys_sorted,
-                           uint32_t* __restrict__ ids_sorted, uint32_t* __restrict__ ranges) {
+__global__ void k_finalize(uint32_t I_host, const uint64_t* __restrict__ I_dev, const uint32_t* __restrict__ tkey,
+                           const uint32_t* __restrict__ tval, const float* __restrict__ depth,
+                           uint64_t* __restrict__ keys_sorted, uint32_t* __restrict__ ids_sorted,
+                           uint32_t* __restrict__ ranges) {
+    const uint32_t I = pass_count(I_host, I_dev);
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= I) return;
     const uint32_t t = tkey[i], g = tval[i];
@@ -341,34 +370,44 @@ Layout make_layout(int n, int64_t capacity) {
 
 }  // namespace
 
-size_t bin_sort_workspace_bytes(int n, int64_t capacity, int /*num_tiles*/) { return make_layout(n, capacity).total; }
+size_t bin_sort_workspace_bytes(int n_items, int64_t capacity, int /*num_tiles*/) {
+    return make_layout(n_items, capacity).total;
+}
 
-gs_status bin_sort_run(int n, const float* mean2d_f, const int* radius, const float* depth, int W, int H,
+gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* radius, const float* depth,
                        int64_t capacity, void* ws, size_t /*ws_bytes*/, uint64_t* keys_sorted, uint32_t* ids_sorted,
-                       uint32_t* tile_ranges, int64_t* n_instances, cudaStream_t s) {
-    const int ntiles = tiles_x(W) * tiles_y(H);
+                       uint32_t* tile_ranges, int64_t* n_instances_host, int64_t* n_instances_dev, cudaStream_t s) {
+    const int ntiles = sv.total_tiles;
+    const int n = sv.num_views * sv.n_per_view;  // items
+    const bool graph = n_instances_host == nullptr;
     cudaError_t e = cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)ntiles, s);
     if (e != cudaSuccess) return cuda_status(e, "gs_bin_sort: clear ranges");
-    *n_instances = 0;
-    if (n == 0) return GS_OK;
+    if (!graph) *n_instances_host = 0;
+    if (n == 0) {
+        if (graph && (e = cudaMemsetAsync(n_instances_dev, 0, sizeof(int64_t), s)) != cudaSuccess)
+            return cuda_status(e, "gs_bin_sort: count");
+        return GS_OK;
+    }
+    unsigned* err = error_word();
+    if (err == nullptr) return cuda_status(cudaGetLastError(), "gs_bin_sort: error word");
     const Layout L = make_layout(n, capacity);
     char* base = static_cast<char*>(ws);
     auto U32 = [&](size_t off) { return reinterpret_cast<uint32_t*>(base + off); };
     const float2* mean2d = reinterpret_cast<const float2*>(mean2d_f);
     RadixScratch rs{U32(L.hist), U32(L.hscan)};
 
-    // 1. counts and depth keys; depth sort of the Gaussians
-    k_count<<<cdiv(n, 256), 256, 0, s>>>(n, mean2d, radius, depth, W, H, U32(L.cnt), U32(L.dk0), U32(L.dv0));
+    // 1. counts and depth keys; depth sort of all items
+    k_count<<<cdiv(n, 256), 256, 0, s>>>(n, sv, mean2d, radius, depth, U32(L.cnt), U32(L.dk0), U32(L.dv0));
     count_launches();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: count");
     uint32_t* dk[2] = {U32(L.dk0), U32(L.dk1)};
     uint32_t* dv[2] = {U32(L.dv0), U32(L.dv1)};
     int which = 0;
-    if ((e = radix_sort(dk, dv, (uint32_t)n, 32, rs, &which, s)) != cudaSuccess)
+    if ((e = radix_sort(dk, dv, (uint32_t)n, nullptr, 32, rs, &which, s)) != cudaSuccess)
         return cuda_status(e, "gs_bin_sort: depth sort");
     const uint32_t* perm = dv[which];
 
-    // 2. offsets of each Gaussian's instances in depth order
+    // 2. offsets of each item's instances in depth order
     uint64_t* c64 = reinterpret_cast<uint64_t*>(base + L.c64);
     uint64_t* offs = reinterpret_cast<uint64_t*>(base + L.offs);
     k_gather_counts<<<cdiv(n, 256), 256, 0, s>>>(n, perm, U32(L.cnt), c64);
@@ -378,28 +417,43 @@ gs_status bin_sort_run(int n, const float* mean2d_f, const int* radius, const fl
         cudaSuccess)
         return cuda_status(e, "gs_bin_sort: scan");
     uint64_t I = 0;
-    if ((e = cudaMemcpyAsync(&I, offs + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-        return cuda_status(e, "gs_bin_sort: read count");
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_status(e, "gs_bin_sort: synchronize");
-    *n_instances = (int64_t)I;
-    if ((int64_t)I > capacity) {
-        set_error("gs_bin_sort: %llu instances exceed capacity %lld", (unsigned long long)I, (long long)capacity);
-        return GS_ERR_CAPACITY;
+    const uint64_t* I_dev = nullptr;
+    uint32_t I_grid = 0;  // items the remaining kernels are launched for
+    if (!graph) {
+        if ((e = cudaMemcpyAsync(&I, offs + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return cuda_status(e, "gs_bin_sort: read count");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_status(e, "gs_bin_sort: synchronize");
+        *n_instances_host = (int64_t)I;
+        if ((int64_t)I > capacity) {
+            set_error("gs_bin_sort: %llu instances exceed capacity %lld", (unsigned long long)I, (long long)capacity);
+            return GS_ERR_CAPACITY;
+        }
+        if (I == 0) return GS_OK;
+        I_grid = (uint32_t)I;
+    } else {
+        if (capacity == 0) {
+            k_duplicate<<<1, 32, 0, s>>>(0, 0, n, offs, perm, sv, mean2d, radius, nullptr, nullptr,
+                                         n_instances_dev, err);
+            count_launches();
+            return cuda_status(cudaGetLastError(), "gs_bin_sort: count");
+        }
+        I_dev = offs + n;
+        I_grid = (uint32_t)capacity;
     }
-    if (I == 0) return GS_OK;
 
-    // 3. duplicate, then stable sort by tile id
+    // 3. duplicate, then stable sort by global tile id
     uint32_t* tk[2] = {U32(L.tk0), U32(L.tk1)};
     uint32_t* tv[2] = {U32(L.tv0), U32(L.tv1)};
-    k_duplicate<<<cdiv((int64_t)I, 256), 256, 0, s>>>((uint32_t)I, n, offs, perm, mean2d, radius, W, H, tk[0], tv[0]);
+    k_duplicate<<<cdiv((int64_t)I_grid, 256), 256, 0, s>>>((uint32_t)I, capacity, n, offs, perm, sv, mean2d, radius,
+                                                            tk[0], tv[0], graph ? n_instances_dev : nullptr, err);
     count_launches();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: duplicate");
     int tile_bits = 1;
     while ((1ll << tile_bits) < ntiles) ++tile_bits;
-    if ((e = radix_sort(tk, tv, (uint32_t)I, tile_bits, rs, &which, s)) != cudaSuccess)
+    if ((e = radix_sort(tk, tv, I_grid, I_dev, tile_bits, rs, &which, s)) != cudaSuccess)
         return cuda_status(e, "gs_bin_sort: tile sort");
-    k_finalize<<<cdiv((int64_t)I, 256), 256, 0, s>>>((uint32_t)I, tk[which], tv[which], depth, keys_sorted, ids_sorted,
-                                                    tile_ranges);
+    k_finalize<<<cdiv((int64_t)I_grid, 256), 256, 0, s>>>(I_grid, I_dev, tk[which], tv[which], depth, keys_sorted,
+                                                         ids_sorted, tile_ranges);
     count_launches();
     return cuda_status(cudaGetLastError(), "gs_bin_sort: finalize");
 }

@@ -71,7 +71,12 @@ gs_status gs_bin_sort_noalloc(int32_t n, const float* mean2d, const int32_t* rad
         set_error("gs_bin_sort_noalloc: null output pointer");
         return GS_ERR_INVALID_ARG;
     }
-    const size_t need = bin_sort_workspace_bytes(n, capacity, tiles_x(width) * tiles_y(height));
+    SortViews sv{};
+    sv.num_views = 1;
+    sv.n_per_view = n;
+    sv.total_tiles = tiles_x(width) * tiles_y(height);
+    sv.views[0] = ViewDesc{width, height, tiles_x(width), 0, 0};
+    const size_t need = bin_sort_workspace_bytes(n, capacity, sv.total_tiles);
     if (need > kNoAllocScratchBytes) {
         set_error("gs_bin_sort_noalloc: n = %d and capacity = %lld need %zu bytes of scratch, more than the "
                   "built-in %zu; use gs_bin_sort with a caller workspace",
@@ -81,8 +86,8 @@ gs_status gs_bin_sort_noalloc(int32_t n, const float* mean2d, const int32_t* rad
     gs_status st = GS_OK;
     void* ws = scratch_address(&st);
     if (ws == nullptr) return st;
-    return bin_sort_run(n, mean2d, radius, depth, width, height, capacity, ws, kNoAllocScratchBytes, keys_sorted,
-                        ids_sorted, tile_ranges, n_instances, stream);
+    return bin_sort_run(sv, mean2d, radius, depth, capacity, ws, kNoAllocScratchBytes, keys_sorted, ids_sorted,
+                        tile_ranges, n_instances, nullptr, stream);
 }
 
 }  // extern "C"

@@ -30,21 +30,43 @@ __device__ __forceinline__ float splat_alpha(const float4& geo, const float4& oc
     return fminf(kAlphaMax, oc.y * e);
 }
 
-__device__ __forceinline__ void load_splat(const BlendArgs& a, uint32_t g, SplatSm& s) {
+// item g of view v: projected data at g, opacity at g - v * n_per_view
+__device__ __forceinline__ void load_splat(const BlendArgs& a, uint32_t g, uint32_t opac_off, SplatSm& s) {
     const float2 m = a.mean2d[g];
     s.geo = make_float4(m.x, m.y, a.conic[3 * g], a.conic[3 * g + 1]);
-    s.oc = make_float4(a.conic[3 * g + 2], a.opac[g], a.rgb[3 * g], a.rgb[3 * g + 1]);
+    s.oc = make_float4(a.conic[3 * g + 2], a.opac[g - opac_off], a.rgb[3 * g], a.rgb[3 * g + 1]);
     s.b = a.rgb[3 * g + 2];
 }
 
-__global__ void __launch_bounds__(kBatch) k_blend_fp32_fwd(BlendArgs a) {
+// Geometry of the block's tile (blockIdx.x is a global tile id).
+struct TileGeo {
+    int W, H, px, py;
+    long long pix_off;
+    uint32_t opac_off;
+};
+
+__device__ __forceinline__ TileGeo tile_geo(const BlendArgs& a, int tile) {
+    const int v = view_of(a, tile);
+    const ViewDesc& vd = a.views[v];
+    const int lt = tile - vd.tile_begin;
+    TileGeo t;
+    t.W = vd.W;
+    t.H = vd.H;
+    t.px = (lt % vd.tiles_x) * kTile + (threadIdx.x & 15);
+    t.py = (lt / vd.tiles_x) * kTile + (threadIdx.x >> 4);
+    t.pix_off = vd.pix_off;
+    t.opac_off = (uint32_t)(v * a.n_per_view);
+    return t;
+}
+
+__global__ void __launch_bounds__(kBatch) k_blend_fp32_fwd(const __grid_constant__ BlendArgs a) {
     __shared__ float4 s_geo[kBatch];
     __shared__ float4 s_oc[kBatch];
     __shared__ float s_b[kBatch];
     const int tile = blockIdx.x;
-    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const int px = tx * kTile + (threadIdx.x & 15), py = ty * kTile + (threadIdx.x >> 4);
-    const bool inside = px < a.W && py < a.H;
+    const TileGeo tg = tile_geo(a, tile);
+    const int px = tg.px, py = tg.py;
+    const bool inside = px < tg.W && py < tg.H;
     const float xp = px + 0.5f, yp = py + 0.5f;
     const uint32_t start = a.ranges[2 * tile], end = a.ranges[2 * tile + 1];
     const int len = end > start ? (int)(end - start) : 0;
@@ -57,7 +79,7 @@ __global__ void __launch_bounds__(kBatch) k_blend_fp32_fwd(BlendArgs a) {
         const int i = base + threadIdx.x;
         if (i < len) {
             SplatSm s;
-            load_splat(a, a.ids[start + i], s);
+            load_splat(a, a.ids[start + i], tg.opac_off, s);
             s_geo[threadIdx.x] = s.geo;
             s_oc[threadIdx.x] = s.oc;
             s_b[threadIdx.x] = s.b;
@@ -83,12 +105,13 @@ __global__ void __launch_bounds__(kBatch) k_blend_fp32_fwd(BlendArgs a) {
         }
     }
     if (inside) {
-        const size_t pix = (size_t)py * a.W + px, plane = (size_t)a.W * a.H;
-        a.image[pix] = C0 + T * a.bg[0];
-        a.image[plane + pix] = C1 + T * a.bg[1];
-        a.image[2 * plane + pix] = C2 + T * a.bg[2];
-        a.T_final[pix] = T;
-        a.n_contrib[pix] = last;
+        const size_t pix = (size_t)py * tg.W + px, plane = (size_t)tg.W * tg.H;
+        float* img = a.image + 3 * tg.pix_off;
+        img[pix] = C0 + T * a.bg[0];
+        img[plane + pix] = C1 + T * a.bg[1];
+        img[2 * plane + pix] = C2 + T * a.bg[2];
+        a.T_final[tg.pix_off + pix] = T;
+        a.n_contrib[tg.pix_off + pix] = last;
     }
 }
 
@@ -124,39 +147,40 @@ __device__ __forceinline__ void warp_reduce9(const float (&v)[9], int lane, floa
 
 // Address of gradient component k (0..8) of Gaussian g:
 // dmean2d.x, dmean2d.y, dA, dB, dC, dopacity, dr, dg, db.
-__device__ __forceinline__ float* grad_slot(const GradArgs& gr, uint32_t g, int k) {
+__device__ __forceinline__ float* grad_slot(const GradArgs& gr, uint32_t g, uint32_t opac_off, int k) {
     if (k < 2) return reinterpret_cast<float*>(gr.dmean2d) + 2 * (size_t)g + k;
     if (k < 5) return gr.dconic + 3 * (size_t)g + (k - 2);
-    if (k == 5) return gr.dopac + g;
+    if (k == 5) return gr.dopac + (g - opac_off);
     return gr.drgb + 3 * (size_t)g + (k - 6);
 }
 
 // Back-to-front walk per pixel.  Per (splat, warp) the nine gradient values
 // are either added directly by the few lanes that have them, or summed over
 // the warp (warp_reduce9) and added by nine lanes.
-__global__ void __launch_bounds__(kBatch) k_blend_fp32_bwd(BlendArgs a, GradArgs gr) {
+__global__ void __launch_bounds__(kBatch) k_blend_fp32_bwd(const __grid_constant__ BlendArgs a, GradArgs gr) {
     __shared__ float4 s_geo[kBatch];
     __shared__ float4 s_oc[kBatch];
     __shared__ float s_b[kBatch];
     __shared__ uint32_t s_id[kBatch];
     __shared__ int s_max;
     const int tile = blockIdx.x;
-    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const int px = tx * kTile + (threadIdx.x & 15), py = ty * kTile + (threadIdx.x >> 4);
-    const bool inside = px < a.W && py < a.H;
+    const TileGeo tg = tile_geo(a, tile);
+    const int px = tg.px, py = tg.py;
+    const bool inside = px < tg.W && py < tg.H;
     const float xp = px + 0.5f, yp = py + 0.5f;
     const uint32_t start = a.ranges[2 * tile];
     const int lane = threadIdx.x & 31;
 
-    const size_t pix = (size_t)py * a.W + px, plane = (size_t)a.W * a.H;
+    const size_t pix = (size_t)tg.pix_off + (size_t)py * tg.W + px, plane = (size_t)tg.W * tg.H;
+    const size_t gpix = 3 * (size_t)tg.pix_off + (size_t)py * tg.W + px;
     int nc = 0;
     float T = 1.0f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
     if (inside) {
         nc = gr.n_contrib[pix];
         T = gr.T_final[pix];
-        g0 = gr.dL_dimage[pix];
-        g1 = gr.dL_dimage[plane + pix];
-        g2 = gr.dL_dimage[2 * plane + pix];
+        g0 = gr.dL_dimage[gpix];
+        g1 = gr.dL_dimage[plane + gpix];
+        g2 = gr.dL_dimage[2 * plane + gpix];
     }
     float S0 = a.bg[0], S1 = a.bg[1], S2 = a.bg[2];  // colour behind the current splat
     if (threadIdx.x == 0) s_max = 0;
@@ -175,7 +199,7 @@ __global__ void __launch_bounds__(kBatch) k_blend_fp32_bwd(BlendArgs a, GradArgs
         if (i < hi) {
             const uint32_t g = a.ids[start + i];
             SplatSm s;
-            load_splat(a, g, s);
+            load_splat(a, g, tg.opac_off, s);
             s_geo[threadIdx.x] = s.geo;
             s_oc[threadIdx.x] = s.oc;
             s_b[threadIdx.x] = s.b;
@@ -225,13 +249,13 @@ __global__ void __launch_bounds__(kBatch) k_blend_fp32_bwd(BlendArgs a, GradArgs
             if (__popc(who) <= 3) {
                 if (contrib) {
 #pragma unroll
-                    for (int q = 0; q < 9; ++q) atomicAdd(grad_slot(gr, g, q), v[q]);
+                    for (int q = 0; q < 9; ++q) atomicAdd(grad_slot(gr, g, tg.opac_off, q), v[q]);
                 }
             } else {
                 float vk, v8;
                 warp_reduce9(v, lane, vk, v8);
-                if ((lane & 3) == 0) atomicAdd(grad_slot(gr, g, lane >> 2), vk);
-                if (lane == 0) atomicAdd(grad_slot(gr, g, 8), v8);
+                if ((lane & 3) == 0) atomicAdd(grad_slot(gr, g, tg.opac_off, lane >> 2), vk);
+                if (lane == 0) atomicAdd(grad_slot(gr, g, tg.opac_off, 8), v8);
             }
         }
     }
@@ -240,13 +264,13 @@ __global__ void __launch_bounds__(kBatch) k_blend_fp32_bwd(BlendArgs a, GradArgs
 }  // namespace
 
 cudaError_t launch_blend_fp32_fwd(const BlendArgs& a, cudaStream_t s) {
-    k_blend_fp32_fwd<<<a.num_tiles, kBatch, 0, s>>>(a);
+    k_blend_fp32_fwd<<<a.total_tiles, kBatch, 0, s>>>(a);
     count_launches();
     return cudaGetLastError();
 }
 
 cudaError_t launch_blend_fp32_bwd(const BlendArgs& a, const GradArgs& g, cudaStream_t s) {
-    k_blend_fp32_bwd<<<a.num_tiles, kBatch, 0, s>>>(a, g);
+    k_blend_fp32_bwd<<<a.total_tiles, kBatch, 0, s>>>(a, g);
     count_launches();
     return cudaGetLastError();
 }

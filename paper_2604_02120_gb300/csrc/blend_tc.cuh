@@ -221,11 +221,7 @@ struct StageHdr {
     int pad[3];
 };
 
-__device__ __forceinline__ int view_of(const BlendArgs& a, int tile) {
-    int v = 0;
-    while (v + 1 < a.num_views && a.views[v + 1].tile_begin <= tile) ++v;
-    return v;
-}
+
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
 template <int V, int CH, int SS, bool DUMP>
@@ -417,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
             if (lane == 0) q = (int)atomicAdd(a.queue, 1u);
             q = __shfl_sync(0xffffffffu, q, 0);
             const bool end = q >= n_items;
-            int tile = 0, len = 0;
+            int tile = 0, len = 0, vview = 0;
             uint32_t start = 0;
             float xc = 0.f, yc_up = 0.f;
             if (!end) {
@@ -426,7 +422,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
                 const uint32_t stop = a.ranges[2 * tile + 1];
                 len = stop > start ? (int)(stop - start) : 0;
                 if (DUMP && len > a.max_len) len = a.max_len;
-                const ViewDesc vd = a.views[view_of(a, tile)];
+                vview = view_of(a, tile);
+                const ViewDesc vd = a.views[vview];
                 const int lt = tile - vd.tile_begin;
                 xc = (float)((lt % vd.tiles_x) * kTile) + (origin ? 0.5f : 8.0f);
                 yc_up = (float)((lt / vd.tiles_x) * kTile) + (origin ? 0.5f : 4.0f);
@@ -462,7 +459,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
                             const uint32_t g = a.ids[start + base + j];
                             const float2 m = a.mean2d[g];
                             const float A = a.conic[3 * g], B = a.conic[3 * g + 1], C = a.conic[3 * g + 2];
-                            const float o = a.opac[g];
+                            const float o = a.opac[g - (uint32_t)(vview * a.n_per_view)];
                             const float l2o = o > 0.f ? __log2f(o) : -INFINITY;
                             const float xh = m.x - xc;
                             coeff_row<TR::HALF>(A, B, C, l2o, xh, m.y - yc_up, bx0, bx1, by0, by1, vu);

@@ -15,6 +15,7 @@ constexpr int kTilePixels = kTile * kTile;
 
 // Bits of the per-device error word (gs_sync_status maps them to statuses).
 constexpr unsigned kErrTimeout = 1u;
+constexpr unsigned kErrCapacity = 2u;
 
 struct CamDev {
     int W, H;

@@ -16,10 +16,19 @@ struct ViewDesc {
     long long pix_off;
 };
 
+// View of a global tile id (views are ordered by tile_begin).
+template <class A>
+__host__ __device__ inline int view_of(const A& a, int tile) {
+    int v = 0;
+    while (v + 1 < a.num_views && a.views[v + 1].tile_begin <= tile) ++v;
+    return v;
+}
+
 struct BlendArgs {
-    int W, H, tiles_x, num_tiles;  // single-view shape (the FP32 kernels)
-    int num_views, total_tiles;    // view table (the tensor-core kernel)
+    int W, H, tiles_x, num_tiles;  // shape of view 0
+    int num_views, total_tiles;    // all views: tiles [0, total_tiles)
     ViewDesc views[kMaxViews];
+    int n_per_view;                // ids are v * n_per_view + g; opacity is indexed by g
     unsigned* queue;               // tile counter, zero at launch (tensor-core kernel)
     const uint32_t* ranges;
     const uint32_t* ids;
@@ -59,14 +68,29 @@ unsigned* error_word();
 // Count `k` kernel launches (gs_launch_count).
 void count_launches(int k = 1);
 
+struct CamViews {
+    int num_views;
+    CamDev cams[kMaxViews];
+};
+
+// outputs are view-major: view v, Gaussian g at index v * n + g
 cudaError_t launch_project(int n, const float* means, const float* scales, const float* quats, const float* sh,
-                           int sh_degree, const CamDev& cam, float* mean2d, float* conic, float* depth,
+                           int sh_degree, const CamViews& cams, float* mean2d, float* conic, float* depth,
                            int* radius, float* rgb, uint32_t* tiles_touched, cudaStream_t s);
 
-size_t bin_sort_workspace_bytes(int n, int64_t capacity, int num_tiles);
-gs_status bin_sort_run(int n, const float* mean2d, const int* radius, const float* depth, int W, int H,
+// Bin/sort geometry: items are (view, Gaussian) pairs, item = v * n_per_view + g.
+struct SortViews {
+    int num_views, total_tiles, n_per_view;
+    ViewDesc views[kMaxViews];
+};
+
+size_t bin_sort_workspace_bytes(int n_items, int64_t capacity, int num_tiles);
+// n_instances_host != nullptr: synchronise once, read the count, exact grids.
+// otherwise (graph mode): no synchronisation; grids sized by capacity; the count
+// goes to n_instances_dev and overflow sets kErrCapacity in the error word.
+gs_status bin_sort_run(const SortViews& sv, const float* mean2d, const int* radius, const float* depth,
                        int64_t capacity, void* ws, size_t ws_bytes, uint64_t* keys_sorted, uint32_t* ids_sorted,
-                       uint32_t* tile_ranges, int64_t* n_instances, cudaStream_t s);
+                       uint32_t* tile_ranges, int64_t* n_instances_host, int64_t* n_instances_dev, cudaStream_t s);
 
 cudaError_t launch_blend_fp32_fwd(const BlendArgs& a, cudaStream_t s);
 cudaError_t launch_blend_fp32_bwd(const BlendArgs& a, const GradArgs& g, cudaStream_t s);

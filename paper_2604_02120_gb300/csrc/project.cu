@@ -65,14 +65,24 @@ __device__ __forceinline__ void quat_scale_matrix(const float* q4, const float* 
         for (int j = 0; j < 3; ++j) M[i][j] = R[i][j] * s[j];
 }
 
+// blockIdx.y = view; outputs of view v, Gaussian g at index v * n + g.
 __global__ void __launch_bounds__(256) k_project(int n, const float* __restrict__ means,
                                                  const float* __restrict__ scales, const float* __restrict__ quats,
-                                                 const float* __restrict__ sh, int sh_degree, CamDev cam,
-                                                 float2* __restrict__ mean2d, float* __restrict__ conic,
-                                                 float* __restrict__ depth, int* __restrict__ radius,
-                                                 float* __restrict__ rgb, uint32_t* __restrict__ tiles_touched) {
+                                                 const float* __restrict__ sh, int sh_degree,
+                                                 const __grid_constant__ CamViews views,
+                                                 float2* __restrict__ mean2d_all, float* __restrict__ conic_all,
+                                                 float* __restrict__ depth_all, int* __restrict__ radius_all,
+                                                 float* __restrict__ rgb_all, uint32_t* __restrict__ touched_all) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
+    const CamDev& cam = views.cams[blockIdx.y];
+    const size_t vo = (size_t)blockIdx.y * n;
+    float2* mean2d = mean2d_all + vo;
+    float* conic = conic_all + 3 * vo;
+    float* depth = depth_all + vo;
+    int* radius = radius_all + vo;
+    float* rgb = rgb_all + 3 * vo;
+    uint32_t* tiles_touched = touched_all + vo;
     const float mwx = means[3 * g], mwy = means[3 * g + 1], mwz = means[3 * g + 2];
     const float px = cam.R[0] * mwx + cam.R[1] * mwy + cam.R[2] * mwz + cam.t[0];
     const float py = cam.R[3] * mwx + cam.R[4] * mwy + cam.R[5] * mwz + cam.t[1];
@@ -196,12 +206,12 @@ __global__ void __launch_bounds__(256) k_project(int n, const float* __restrict_
 }  // namespace
 
 cudaError_t launch_project(int n, const float* means, const float* scales, const float* quats, const float* sh,
-                           int sh_degree, const CamDev& cam, float* mean2d, float* conic, float* depth, int* radius,
-                           float* rgb, uint32_t* tiles_touched, cudaStream_t s) {
+                           int sh_degree, const CamViews& cams, float* mean2d, float* conic, float* depth,
+                           int* radius, float* rgb, uint32_t* tiles_touched, cudaStream_t s) {
     const int block = 256;
-    const int grid = (n + block - 1) / block;
-    k_project<<<grid, block, 0, s>>>(n, means, scales, quats, sh, sh_degree, cam, reinterpret_cast<float2*>(mean2d),
-                                     conic, depth, radius, rgb, tiles_touched);
+    const dim3 grid((n + block - 1) / block, cams.num_views);
+    k_project<<<grid, block, 0, s>>>(n, means, scales, quats, sh, sh_degree, cams,
+                                     reinterpret_cast<float2*>(mean2d), conic, depth, radius, rgb, tiles_touched);
     count_launches();
     return cudaGetLastError();
 }

@@ -28,6 +28,8 @@ ABI_FUNCTIONS = (
     "gs_version", "gs_status_string", "gs_last_error", "gs_project", "gs_bin_sort_workspace_size",
     "gs_bin_sort", "gs_blend_forward", "gs_blend_backward", "gs_tile_power", "gs_sync_status",
     "gs_selftest_bounded_wait", "gs_launch_count", "gs_bin_sort_noalloc", "gs_bin_sort_noalloc_max_bytes",
+    "gs_project_views", "gs_bin_sort_views", "gs_blend_forward_views", "gs_blend_backward_views",
+    "gs_blend_autotune",
 )
 
 
@@ -75,6 +77,16 @@ def load(path: str = LIB_PATH):
     lib.gs_blend_backward.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(gs_blend_opts), vp, vp, vp,
                                       vp, vp, vp, vp, vp]
     lib.gs_tile_power.argtypes = [i32, i32, vp, vp, vp, vp, vp, ctypes.POINTER(gs_blend_opts), vp, i32, i32, vp, vp]
+    i32p, i64p = ctypes.POINTER(i32), ctypes.POINTER(i64)
+    lib.gs_project_views.argtypes = [i32, vp, vp, vp, vp, i32, ctypes.POINTER(gs_camera), i32, vp, vp, vp, vp, vp,
+                                     vp, vp]
+    lib.gs_bin_sort_views.argtypes = [i32, i32, vp, vp, vp, i32p, i32p, i64, vp, sz, vp, vp, vp, i64p, vp, vp]
+    lib.gs_blend_forward_views.argtypes = [i32, i32p, i32p, i32, vp, vp, vp, vp, vp, vp,
+                                           ctypes.POINTER(gs_blend_opts), vp, vp, vp, vp]
+    lib.gs_blend_backward_views.argtypes = [i32, i32p, i32p, i32, vp, vp, vp, vp, vp, vp,
+                                            ctypes.POINTER(gs_blend_opts), vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.gs_blend_autotune.argtypes = [i32, i32p, i32p, i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(gs_blend_opts),
+                                      vp, vp, vp, i32, ctypes.POINTER(ctypes.c_float), vp]
     lib.gs_sync_status.argtypes = [vp]
     lib.gs_selftest_bounded_wait.argtypes = [i64, vp]
     for name in ABI_FUNCTIONS:
@@ -204,6 +216,62 @@ def gs_tile_power(width, height, tile_ranges, ids_sorted, mean2d, conic, opacity
                                 _ptr(out), _stream(stream)), "gs_tile_power")
 
 
+def _i32arr(vals):
+    arr = (ctypes.c_int32 * len(vals))(*[int(v) for v in vals])
+    return arr
+
+
+def gs_project_views(n, means, scales, quats, sh, sh_degree, cams, mean2d, conic, depth, radius, rgb,
+                     tiles_touched, stream=None):
+    arr = (gs_camera * len(cams))(*[c if isinstance(c, gs_camera) else make_camera(c) for c in cams])
+    _check(load().gs_project_views(n, _ptr(means), _ptr(scales), _ptr(quats), _ptr(sh), sh_degree, arr, len(cams),
+                                   _ptr(mean2d), _ptr(conic), _ptr(depth), _ptr(radius), _ptr(rgb),
+                                   _ptr(tiles_touched), _stream(stream)), "gs_project_views")
+
+
+def gs_bin_sort_views(n_views, n_per_view, mean2d, radius, depth, widths, heights, capacity, workspace, keys_sorted,
+                      ids_sorted, tile_ranges, count_dev=None, stream=None, check=True):
+    """Synchronising mode if count_dev is None (returns (status, count)),
+    otherwise graph mode: the count goes to the int64 device tensor count_dev."""
+    count = ctypes.c_int64(0)
+    st = load().gs_bin_sort_views(n_views, n_per_view, _ptr(mean2d), _ptr(radius), _ptr(depth), _i32arr(widths),
+                                  _i32arr(heights), capacity, _ptr(workspace),
+                                  workspace.numel() * workspace.element_size(), _ptr(keys_sorted), _ptr(ids_sorted),
+                                  _ptr(tile_ranges), None if count_dev is not None else ctypes.byref(count),
+                                  _ptr(count_dev), _stream(stream))
+    if check:
+        _check(st, "gs_bin_sort_views")
+    return st, int(count.value)
+
+
+def gs_blend_forward_views(widths, heights, n_per_view, tile_ranges, ids_sorted, mean2d, conic, opacity, rgb, opts,
+                           image, T_final, n_contrib, stream=None):
+    _check(load().gs_blend_forward_views(len(widths), _i32arr(widths), _i32arr(heights), n_per_view,
+                                         _ptr(tile_ranges), _ptr(ids_sorted), _ptr(mean2d), _ptr(conic),
+                                         _ptr(opacity), _ptr(rgb), ctypes.byref(opts), _ptr(image), _ptr(T_final),
+                                         _ptr(n_contrib), _stream(stream)), "gs_blend_forward_views")
+
+
+def gs_blend_backward_views(widths, heights, n_per_view, tile_ranges, ids_sorted, mean2d, conic, opacity, rgb, opts,
+                            T_final, n_contrib, dL_dimage, dmean2d, dconic, dopacity, drgb, stream=None):
+    _check(load().gs_blend_backward_views(len(widths), _i32arr(widths), _i32arr(heights), n_per_view,
+                                          _ptr(tile_ranges), _ptr(ids_sorted), _ptr(mean2d), _ptr(conic),
+                                          _ptr(opacity), _ptr(rgb), ctypes.byref(opts), _ptr(T_final),
+                                          _ptr(n_contrib), _ptr(dL_dimage), _ptr(dmean2d), _ptr(dconic),
+                                          _ptr(dopacity), _ptr(drgb), _stream(stream)), "gs_blend_backward_views")
+
+
+def gs_blend_autotune(widths, heights, n_per_view, tile_ranges, ids_sorted, mean2d, conic, opacity, rgb, opts,
+                      image, T_final, n_contrib, reps=5, stream=None) -> float:
+    """Sets opts.chunk / opts.stages to the fastest built pair; returns its ms."""
+    best = ctypes.c_float(0.0)
+    _check(load().gs_blend_autotune(len(widths), _i32arr(widths), _i32arr(heights), n_per_view, _ptr(tile_ranges),
+                                    _ptr(ids_sorted), _ptr(mean2d), _ptr(conic), _ptr(opacity), _ptr(rgb),
+                                    ctypes.byref(opts), _ptr(image), _ptr(T_final), _ptr(n_contrib), int(reps),
+                                    ctypes.byref(best), _stream(stream)), "gs_blend_autotune")
+    return float(best.value)
+
+
 def gs_sync_status(stream=None) -> int:
     return int(load().gs_sync_status(_stream(stream)))
 
@@ -327,3 +395,87 @@ def render(dev_scene, cam, opts, sorter: BinSorter | None = None, stream=None) -
     bs = sorter.run(proj["mean2d"], proj["radius"], proj["depth"], cam.width, cam.height, stream)
     out = blend_forward(cam.width, cam.height, bs, proj, dev_scene["opacities"], opts, stream)
     return dict(project=proj, bin_sort=bs, blend=out)
+
+
+class BatchRenderer:
+    """Batched forward + backward of one scene seen by several cameras:
+    gs_project_views -> gs_bin_sort_views (no host synchronisation) ->
+    gs_blend_forward_views (one persistent launch over the tiles of all views)
+    -> gs_blend_backward_views.  All buffers are allocated once for a fixed
+    instance capacity, so `step` can be captured in a CUDA graph (`capture`);
+    an instance count above the capacity is reported by gs_sync_status() as
+    GS_ERR_CAPACITY."""
+
+    def __init__(self, dev_scene, cams, opts, capacity, device="cuda"):
+        self.scene = dev_scene
+        self.cams = [make_camera(c) for c in cams]
+        self.opts = opts
+        self.widths = [c.width for c in self.cams]
+        self.heights = [c.height for c in self.cams]
+        V, n = len(self.cams), int(dev_scene["means"].shape[0])
+        self.n, self.V, self.capacity = n, V, int(capacity)
+        f32 = dict(device=device, dtype=torch.float32)
+        i32 = dict(device=device, dtype=torch.int32)
+        self.mean2d = torch.empty(V * n, 2, **f32)
+        self.conic = torch.empty(V * n, 3, **f32)
+        self.depth = torch.empty(V * n, **f32)
+        self.radius = torch.empty(V * n, **i32)
+        self.rgb = torch.empty(V * n, 3, **f32)
+        self.touched = torch.empty(V * n, **i32)
+        self.total_tiles = sum(num_tiles(w, h) for w, h in zip(self.widths, self.heights))
+        self.pixels = sum(w * h for w, h in zip(self.widths, self.heights))
+        self.keys = torch.empty(max(self.capacity, 1), device=device, dtype=torch.int64)
+        self.ids = torch.empty(max(self.capacity, 1), **i32)
+        self.ranges = torch.empty(2 * self.total_tiles, **i32)
+        self.count = torch.zeros(1, device=device, dtype=torch.int64)
+        ws = gs_bin_sort_workspace_size(V * n, self.capacity, self.widths[0], self.heights[0])
+        self.workspace = torch.empty(ws + 256, device=device, dtype=torch.uint8)
+        self.image = torch.empty(3 * self.pixels, **f32)
+        self.T = torch.empty(self.pixels, **f32)
+        self.nc = torch.empty(self.pixels, **i32)
+        self.dL = torch.zeros(3 * self.pixels, **f32)
+        self.g_mean2d = torch.zeros(V * n, 2, **f32)
+        self.g_conic = torch.zeros(V * n, 3, **f32)
+        self.g_opac = torch.zeros(n, **f32)
+        self.g_rgb = torch.zeros(V * n, 3, **f32)
+        self.graph = None
+
+    def forward(self, stream=None):
+        sc = self.scene
+        gs_project_views(self.n, sc["means"], sc["scales"], sc["quats"], sc["sh"], sc["sh_degree"], self.cams,
+                         self.mean2d, self.conic, self.depth, self.radius, self.rgb, self.touched, stream)
+        gs_bin_sort_views(self.V, self.n, self.mean2d, self.radius, self.depth, self.widths, self.heights,
+                          self.capacity, self.workspace, self.keys, self.ids, self.ranges, count_dev=self.count,
+                          stream=stream)
+        gs_blend_forward_views(self.widths, self.heights, self.n, self.ranges, self.ids, self.mean2d, self.conic,
+                               sc["opacities"], self.rgb, self.opts, self.image, self.T, self.nc, stream)
+
+    def backward(self, stream=None):
+        for t in (self.g_mean2d, self.g_conic, self.g_opac, self.g_rgb):
+            t.zero_()
+        gs_blend_backward_views(self.widths, self.heights, self.n, self.ranges, self.ids, self.mean2d, self.conic,
+                                self.scene["opacities"], self.rgb, self.opts, self.T, self.nc, self.dL,
+                                self.g_mean2d, self.g_conic, self.g_opac, self.g_rgb, stream)
+
+    def step(self, stream=None):
+        self.forward(stream)
+        self.backward(stream)
+
+    def capture(self):
+        """Record step() into a CUDA graph (run step() once uncaptured first)."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.step()
+        return self.graph
+
+    def view_image(self, v):
+        off = sum(self.widths[u] * self.heights[u] for u in range(v))
+        W, H = self.widths[v], self.heights[v]
+        return (self.image[3 * off:3 * (off + W * H)].view(3, H, W), self.T[off:off + W * H].view(H, W),
+                self.nc[off:off + W * H].view(H, W))

@@ -1,0 +1,184 @@
+"""Batched rendering of several views (cameras) in one pass: projection of all
+views in one launch, one bin/sort over all views' tiles (also without host
+synchronisation, for CUDA-graph capture), one persistent tensor-core blend
+over the tiles of all views, the batched backward, a captured CUDA graph and
+the autotuner.  Results must equal the single-view calls and the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2604_02120_gb300 import gs, scenes
+
+from gpu_common import CORES, to_np
+
+pytestmark = pytest.mark.gpu
+
+SPLIT_EXP_ERR = 2e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    gs.load()
+
+
+def _ring_scene(n=500, sizes=((80, 48), (61, 37), (96, 96), (33, 70)), seed=12):
+    sc = scenes.tiny_scene(seed, n=n, width=64, height=64, sh_degree=1, scale_lo=-2.6, scale_hi=-1.4)
+    sc.cameras = scenes.ring_cameras(len(sizes), 3.0, list(sizes))
+    return sc
+
+
+def _single(dev, cam, variant):
+    proj = gs.project(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam)
+    bs = gs.BinSorter("cuda", 1 << 16).run(proj["mean2d"], proj["radius"], proj["depth"], cam.width, cam.height)
+    out = gs.blend_forward(cam.width, cam.height, bs, proj, dev["opacities"], gs.make_opts(variant))
+    return proj, bs, out
+
+
+@pytest.mark.parametrize("variant", ["fp32", "fp16_split", "bf16"])
+def test_batched_views_equal_single_view_calls(variant):
+    sc = _ring_scene()
+    dev = gs.scene_to_device(sc)
+    br = gs.BatchRenderer(dev, sc.cameras, gs.make_opts(variant), capacity=1 << 17)
+    br.forward()
+    assert gs.gs_sync_status() == gs.GS_OK
+    n = sc.n
+    ranges_b = br.ranges.cpu().numpy().view(np.uint32)
+    ids_b = br.ids.cpu().numpy().view(np.uint32)
+    tile0 = 0
+    for v, cam in enumerate(sc.cameras):
+        proj, bs, out = _single(dev, cam, variant)
+        for key in ("mean2d", "conic", "depth", "radius", "rgb"):
+            torch.testing.assert_close(getattr(br, key)[v * n:(v + 1) * n], proj[key], rtol=0, atol=0)
+        # per tile: the batched list is the single-view list with item ids offset by v * n
+        r1 = bs["tile_ranges"].cpu().numpy().view(np.uint32)
+        i1 = bs["ids"].cpu().numpy().view(np.uint32)
+        for t in range(cam.num_tiles):
+            a = ids_b[ranges_b[2 * (tile0 + t)]:ranges_b[2 * (tile0 + t) + 1]]
+            b = i1[r1[2 * t]:r1[2 * t + 1]] + v * n
+            np.testing.assert_array_equal(a, b)
+        img, T, nc = br.view_image(v)
+        torch.testing.assert_close(img, out["image"], rtol=0, atol=0)
+        torch.testing.assert_close(T, out["T_final"], rtol=0, atol=0)
+        torch.testing.assert_close(nc, out["n_contrib"], rtol=0, atol=0)
+        tile0 += cam.num_tiles
+
+
+def test_graph_mode_bin_sort_matches_synchronising_mode_and_reports_overflow():
+    sc = _ring_scene()
+    dev = gs.scene_to_device(sc)
+    br = gs.BatchRenderer(dev, sc.cameras, gs.make_opts("fp32"), capacity=1 << 17)
+    br.forward()
+    count = int(br.count.item())
+    keys = torch.empty(1 << 17, device="cuda", dtype=torch.int64)
+    ids = torch.empty(1 << 17, device="cuda", dtype=torch.int32)
+    ranges = torch.empty_like(br.ranges)
+    st, c2 = gs.gs_bin_sort_views(br.V, br.n, br.mean2d, br.radius, br.depth, br.widths, br.heights, 1 << 17,
+                                  br.workspace, keys, ids, ranges)
+    assert st == gs.GS_OK and c2 == count > 0
+    torch.testing.assert_close(keys[:count], br.keys[:count], rtol=0, atol=0)
+    torch.testing.assert_close(ids[:count], br.ids[:count], rtol=0, atol=0)
+    torch.testing.assert_close(ranges, br.ranges, rtol=0, atol=0)
+    # graph mode with too small a capacity: count reported, error word set
+    small = count // 2
+    ws = torch.empty(gs.gs_bin_sort_workspace_size(br.V * br.n, small, 64, 64) + 256, device="cuda",
+                     dtype=torch.uint8)
+    cdev = torch.zeros(1, device="cuda", dtype=torch.int64)
+    gs.gs_bin_sort_views(br.V, br.n, br.mean2d, br.radius, br.depth, br.widths, br.heights, small, ws, keys, ids,
+                         ranges, count_dev=cdev)
+    assert gs.gs_sync_status() == gs.GS_ERR_CAPACITY
+    assert int(cdev.item()) == count
+    assert gs.gs_sync_status() == gs.GS_OK
+
+
+def test_batched_backward_equals_sum_over_views():
+    sc = _ring_scene(n=300)
+    dev = gs.scene_to_device(sc)
+    opts = gs.make_opts("fp32", bg=(0.1, 0.2, 0.3))
+    br = gs.BatchRenderer(dev, sc.cameras, opts, capacity=1 << 17)
+    rng = np.random.default_rng(3)
+    br.dL.copy_(torch.from_numpy(rng.standard_normal(3 * br.pixels).astype(np.float32)))
+    br.step()
+    assert gs.gs_sync_status() == gs.GS_OK
+    n = sc.n
+    g_opac = torch.zeros(n, device="cuda")
+    off = 0
+    for v, cam in enumerate(sc.cameras):
+        proj, bs, out = _single(dev, cam, "fp32")
+        P = cam.width * cam.height
+        dL = br.dL[3 * off:3 * (off + P)].view(3, cam.height, cam.width)
+        g = gs.blend_backward(cam.width, cam.height, bs, proj, dev["opacities"], opts, out, dL)
+        torch.testing.assert_close(br.g_mean2d[v * n:(v + 1) * n], g["mean2d"], rtol=1e-4, atol=1e-5)
+        torch.testing.assert_close(br.g_conic[v * n:(v + 1) * n], g["conic"], rtol=1e-4, atol=1e-5)
+        torch.testing.assert_close(br.g_rgb[v * n:(v + 1) * n], g["rgb"], rtol=1e-4, atol=1e-5)
+        g_opac += g["opacity"]
+        off += P
+    torch.testing.assert_close(br.g_opac, g_opac, rtol=1e-4, atol=1e-5)
+
+
+def test_cuda_graph_replay_matches_eager_step():
+    sc = _ring_scene()
+    dev = gs.scene_to_device(sc)
+    br = gs.BatchRenderer(dev, sc.cameras, gs.make_opts("fp16_split"), capacity=1 << 17)
+    br.dL.normal_()
+    br.step()
+    torch.cuda.synchronize()
+    want = [t.clone() for t in (br.image, br.T, br.nc, br.g_mean2d, br.g_opac)]
+    graph = br.capture()
+    for t in (br.image, br.T, br.g_mean2d):
+        t.fill_(-1.0)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert gs.gs_sync_status() == gs.GS_OK
+    got = (br.image, br.T, br.nc, br.g_mean2d, br.g_opac)
+    for a, b in zip(got[:3], want[:3]):
+        torch.testing.assert_close(a, b, rtol=0, atol=0)
+    for a, b in zip(got[3:], want[3:]):  # atomics: summation order may differ
+        torch.testing.assert_close(a, b, rtol=1e-5, atol=1e-6)
+
+
+def test_autotune_picks_a_built_shape():
+    sc = _ring_scene()
+    dev = gs.scene_to_device(sc)
+    br = gs.BatchRenderer(dev, sc.cameras, gs.make_opts("fp16_split"), capacity=1 << 17)
+    br.forward()
+    opts = gs.make_opts("fp16_split")
+    ms = gs.gs_blend_autotune(br.widths, br.heights, br.n, br.ranges, br.ids, br.mean2d, br.conic,
+                              dev["opacities"], br.rgb, opts, br.image, br.T, br.nc, reps=3)
+    assert ms > 0
+    assert (opts.chunk, opts.stages) in [(32, 2), (32, 4), (16, 4), (16, 6)]
+
+
+@pytest.mark.parametrize("variant", ["fp32", "fp16_split"])
+def test_batched_views_match_oracle(variant):
+    """Mixed-resolution ring of views (a small stand-in for the 16-camera
+    batch): every view against the FP64 oracle."""
+    sc = _ring_scene(n=800, sizes=((160, 120), (128, 72), (200, 112), (240, 135)))
+    dev = gs.scene_to_device(sc)
+    br = gs.BatchRenderer(dev, sc.cameras, gs.make_opts(variant, bg=(0.1, 0.1, 0.1)), capacity=1 << 19)
+    br.forward()
+    assert gs.gs_sync_status() == gs.GS_OK
+    n = sc.n
+    ranges = br.ranges.cpu().numpy().view(np.uint32)
+    ids = br.ids.cpu().numpy().view(np.uint32)
+    m2 = br.mean2d.cpu().numpy().astype(np.float64)
+    co = br.conic.cpu().numpy().astype(np.float64)
+    rgb = br.rgb.cpu().numpy().astype(np.float64)
+    tile0 = 0
+    margin = (1e-4, 1e-4) if variant == "fp32" else (SPLIT_EXP_ERR, 1e-5)
+    tol = 1e-4 if variant == "fp32" else 1e-3
+    for v, cam in enumerate(sc.cameras):
+        T = cam.num_tiles
+        r = ranges[2 * tile0:2 * (tile0 + T)].astype(np.int64)
+        # the oracle blends view v with its own local tile ranges; ids index all items
+        ref = oracle.blend(cam.width, cam.height, r.astype(np.uint32), ids, m2, co,
+                           np.tile(sc.opacities.astype(np.float64), len(sc.cameras)), rgb, bg=(0.1, 0.1, 0.1),
+                           alpha_margin=margin[0], t_margin=margin[1], n_threads=CORES)
+        img, Tf, nc = (x.cpu().numpy() for x in br.view_image(v))
+        ok = ~ref["ambiguous"]
+        assert ref["ambiguous"].mean() < 0.02
+        assert np.abs(img - ref["image"])[:, ok].max() <= tol
+        np.testing.assert_array_equal(nc[ok], ref["n_contrib"][ok])
+        tile0 += T
