@@ -147,10 +147,10 @@ def run_ours(args):
     import torch
     from paper_2604_02120_gb300 import gs, scenes
 
-    ws, rank, local = dist_env()
+    ws_n, rank, local = dist_env()
     torch.cuda.set_device(local)
     dist = None
-    if ws > 1:
+    if ws_n > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     gs.load()
@@ -160,22 +160,39 @@ def run_ours(args):
     dev = gs.scene_to_device(sc)
     opts = gs.make_opts(args.variant)
     fp32 = gs.make_opts("fp32")
-    sorter = gs.BinSorter("cuda", capacity=1 << 21)
     dL = torch.from_numpy(scenes.upstream_grad(0, [cam])[0]).cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
+    # capacity from one synchronising bin/sort; the timed steps then never
+    # synchronise the host (gs_bin_sort_views in graph mode)
+    proj0 = gs.project(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam)
+    count0 = gs.BinSorter("cuda", 1 << 20).run(proj0["mean2d"], proj0["radius"], proj0["depth"], W, H)["n_instances"]
+    capacity = int(count0 * 1.25) + 4096
+    n = sc.n
+    ws = torch.empty(gs.gs_bin_sort_workspace_size(n, capacity, W, H) + 256, dtype=torch.uint8, device="cuda")
+    keys = torch.empty(capacity, dtype=torch.int64, device="cuda")
+    ids = torch.empty(capacity, dtype=torch.int32, device="cuda")
+    ranges = torch.empty(2 * gs.num_tiles(W, H), dtype=torch.int32, device="cuda")
+    count_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
 
     def step(ev=None):
-        proj = gs.project(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam)
-        bs = sorter.run(proj["mean2d"], proj["radius"], proj["depth"], W, H)
         if ev:
             ev[0].record(stream)
-        fwd = gs.blend_forward(W, H, bs, proj, dev["opacities"], opts)
+        proj = gs.project(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam)
         if ev:
             ev[1].record(stream)
-        g = gs.blend_backward(W, H, bs, proj, dev["opacities"], opts, fwd, dL)
+        gs.gs_bin_sort_views(1, n, proj["mean2d"], proj["radius"], proj["depth"], [W], [H], capacity, ws, keys, ids,
+                             ranges, count_dev=count_dev)
+        bs = dict(tile_ranges=ranges, ids=ids)
         if ev:
             ev[2].record(stream)
+        fwd = gs.blend_forward(W, H, bs, proj, dev["opacities"], opts)
+        if ev:
+            ev[3].record(stream)
+        g = gs.blend_backward(W, H, bs, proj, dev["opacities"], opts, fwd, dL)
+        if ev:
+            ev[4].record(stream)
+        bs["n_instances"] = count0
         return proj, bs, fwd, g
 
     for _ in range(max(args.warmup, 3)):
@@ -189,7 +206,7 @@ def run_ours(args):
     K = args.steps
     E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     st_ev = [(E(), E()) for _ in range(K)]
-    k_ev = [(E(), E(), E()) for _ in range(K)]
+    k_ev = [tuple(E() for _ in range(5)) for _ in range(K)]
     launches0 = gs.gs_launch_count()
     with ClockSampler(local) as clk:
         if dist:
@@ -207,17 +224,19 @@ def run_ours(args):
         wall = time.perf_counter() - wall0
     launches = gs.gs_launch_count() - launches0
     clocks = clk.summary()
-    assert gs.gs_sync_status() == gs.GS_OK
+    assert gs.gs_sync_status() == gs.GS_OK  # also catches a capacity overflow of the bin/sort
     step_ms = [a.elapsed_time(b) for a, b in st_ev]
-    fwd_ms = [a.elapsed_time(b) for a, b, _ in k_ev]
-    bwd_ms = [b.elapsed_time(c) for _, b, c in k_ev]
+    proj_ms = [e[0].elapsed_time(e[1]) for e in k_ev]
+    sort_ms = [e[1].elapsed_time(e[2]) for e in k_ev]
+    fwd_ms = [e[2].elapsed_time(e[3]) for e in k_ev]
+    bwd_ms = [e[3].elapsed_time(e[4]) for e in k_ev]
     dev_ms = sum(step_ms)
     if dist:
         t = torch.tensor([dev_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dev_ms = float(t.item())
     evals_step = 2 * evals_fwd  # forward and backward each examine sum(n_contrib) pairs
-    value = ws * evals_step * K / (dev_ms / 1e3)
+    value = ws_n * evals_step * K / (dev_ms / 1e3)
 
     # ---- blend-only ms/frame per variant (forward), tensor core vs FP32 CUDA core
     blend = {}
@@ -252,7 +271,7 @@ def run_ours(args):
         blend["backward_fp32"] = {"ms_per_frame": round(ms, 5), "evals_per_s": evals_fwd / (ms / 1e3)}
 
     # ---- end to end through the public API with host buffers
-    e2e = run_e2e(args, gs, torch, sc, cam, opts, sorter, dL, flush, evals_step, ws, dist)
+    e2e = run_e2e(args, gs, torch, sc, cam, opts, capacity, dL, flush, evals_step, ws_n, dist)
 
     # ---- roofline of the dominant blend kernel (MUFU: one exp2 per evaluated pair)
     peaks, peak_kind = read_peaks()
@@ -276,15 +295,18 @@ def run_ours(args):
                 "launch_ms": round(t_ms, 5)}
 
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_n, "steps": K, "warmup": args.warmup,
         "ms_per_step": dev_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "blend_variant": args.variant,
                    "step": "project + bin_sort + blend_forward + blend_backward",
                    "evals_per_step": evals_step, "instances": n_inst, "pixels": W * H,
-                   "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replica x{ws}"},
-        "breakdown_ms": {"blend_forward": round(f_ms, 5), "blend_backward": round(b_ms, 5),
-                         "project_bin_sort_and_gaps": round(dev_ms / K - f_ms - b_ms, 5)},
+                   "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replica x{ws_n}",
+                   "bin_sort": "no host synchronisation (fixed capacity, count on the device)"},
+        "breakdown_ms": {"project": round(statistics.mean(proj_ms), 5), "bin_sort": round(statistics.mean(sort_ms), 5),
+                         "blend_forward": round(f_ms, 5), "blend_backward": round(b_ms, 5),
+                         "gaps": round(dev_ms / K - f_ms - b_ms - statistics.mean(proj_ms)
+                                       - statistics.mean(sort_ms), 5)},
         "wall_ms_per_step": wall * 1e3 / K,
         "blend_forward_by_variant": blend,
         "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
@@ -297,7 +319,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_e2e(args, gs, torch, sc, cam, opts, sorter, dL, flush, evals_step, ws, dist):
+def run_e2e(args, gs, torch, sc, cam, opts, capacity, dL, flush, evals_step, ws, dist):
     """Same step through the public API from pinned host buffers: H2D of the
     scene every step, D2H of the image and the four gradient arrays."""
     W, H = cam.width, cam.height
@@ -310,16 +332,20 @@ def run_e2e(args, gs, torch, sc, cam, opts, sorter, dL, flush, evals_step, ws, d
     h2d = sum(v.numel() * v.element_size() for v in host.values())
     d2h = sum(v.numel() * v.element_size() for v in out_h.values())
 
+    br = gs.BatchRenderer(dict(means=devb["means"], scales=devb["scales"], quats=devb["quats"],
+                               opacities=devb["opacities"], sh=devb["sh"], sh_degree=sc.sh_degree), [cam], opts,
+                          capacity)
+    br.dL.copy_(dL.reshape(-1))
+
     def step():
         for k, v in host.items():
             devb[k].copy_(v, non_blocking=True)
-        dscene = dict(means=devb["means"], scales=devb["scales"], quats=devb["quats"], opacities=devb["opacities"],
-                      sh=devb["sh"], sh_degree=sc.sh_degree)
-        r = gs.render(dscene, cam, opts, sorter)
-        g = gs.blend_backward(W, H, r["bin_sort"], r["project"], devb["opacities"], opts, r["blend"], dL)
-        out_h["image"].copy_(r["blend"]["image"], non_blocking=True)
-        for k in ("mean2d", "conic", "opacity", "rgb"):
-            out_h[k].copy_(g[k], non_blocking=True)
+        br.step()
+        out_h["image"].copy_(br.image.view(3, H, W), non_blocking=True)
+        out_h["mean2d"].copy_(br.g_mean2d, non_blocking=True)
+        out_h["conic"].copy_(br.g_conic, non_blocking=True)
+        out_h["opacity"].copy_(br.g_opac, non_blocking=True)
+        out_h["rgb"].copy_(br.g_rgb, non_blocking=True)
 
     for _ in range(max(args.warmup, 3)):
         step()

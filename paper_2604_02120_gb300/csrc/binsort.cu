@@ -34,107 +34,143 @@ __device__ __forceinline__ T warp_incl_scan(T v) {
     return v;
 }
 
-// exclusive scan of one value per thread across the block; returns the total
-template <typename T>
-__device__ __forceinline__ T block_excl_scan(T v, T& total, T* s_warp /*[kThreads/32]*/) {
+// exclusive scan of one value per thread across a block of NT threads;
+// returns the thread's exclusive prefix, `total` receives the block's sum.
+template <typename T, int NT>
+__device__ __forceinline__ T block_excl_scan(T v, T& total, T* s_warp /*[NT/32 + 1]*/) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T inc = warp_incl_scan(v);
     if (lane == 31) s_warp[warp] = inc;
     __syncthreads();
     if (warp == 0) {
-        T w = lane < kThreads / 32 ? s_warp[lane] : T(0);
+        T w = lane < NT / 32 ? s_warp[lane] : T(0);
         T wi = warp_incl_scan(w);
-        if (lane < kThreads / 32) s_warp[lane] = wi - w;
-        if (lane == kThreads / 32 - 1) s_warp[kThreads / 32] = wi;
+        if (lane < NT / 32) s_warp[lane] = wi - w;
+        if (lane == NT / 32 - 1) s_warp[NT / 32] = wi;
     }
     __syncthreads();
     T res = inc - v + s_warp[warp];
-    total = s_warp[kThreads / 32];
+    total = s_warp[NT / 32];
     __syncthreads();
     return res;
 }
 
+// Scans run on 1024-thread blocks; a block covers kScanItems<T>() * 1024 elements
+// staged through 64 KB of dynamic shared memory.
+constexpr int kScanThreads = 1024;
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_scan_reduce(const T* __restrict__ in, int64_t n, T* __restrict__ sums) {
-    __shared__ T s_warp[kThreads / 32 + 1];
-    const int64_t base = (int64_t)blockIdx.x * kTileItems;
+constexpr int scan_items() { return sizeof(T) == 8 ? 8 : 16; }
+template <typename T>
+constexpr int scan_tile() { return kScanThreads * scan_items<T>(); }
+
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const T* __restrict__ in, int64_t n, T* __restrict__ sums) {
+    __shared__ T s_warp[kScanThreads / 32 + 1];
+    const int64_t base = (int64_t)blockIdx.x * scan_tile<T>();
     T acc = 0;
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) {
-        int64_t i = base + r * kThreads + threadIdx.x;
+    for (int r = 0; r < scan_items<T>(); ++r) {
+        int64_t i = base + r * kScanThreads + threadIdx.x;
         if (i < n) acc += in[i];
     }
     T total;
-    block_excl_scan<T>(acc, total, s_warp);
+    block_excl_scan<T, kScanThreads>(acc, total, s_warp);
     if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
-// out[i] = sum_{k<i} in[k] (+ block offset); if write_total, out[n] = sum of all.
+// out[i] = sum_{k<i} in[k]; the block's offset is the sum of sums[0 .. block)
+// (each block adds up the block sums before it, at most kScanThreads of them);
+// if write_total, out[n] = sum of all.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_scan_apply(const T* in, int64_t n, const T* __restrict__ block_off,
-                                                         T* out, int write_total) {
-    __shared__ T s_items[kTileItems];
-    __shared__ T s_warp[kThreads / 32 + 1];
-    const int64_t base = (int64_t)blockIdx.x * kTileItems;
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const T* in, int64_t n, const T* __restrict__ sums,
+                                                             int sums_scanned, T* out, int write_total) {
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    T* s_items = reinterpret_cast<T*>(s_raw);
+    __shared__ T s_warp[kScanThreads / 32 + 1];
+    constexpr int IT = scan_items<T>();
+    const int64_t base = (int64_t)blockIdx.x * scan_tile<T>();
+    T off = 0;
+    if (sums != nullptr && sums_scanned) {
+        off = sums[blockIdx.x];
+    } else if (sums != nullptr) {
+        T mine = (int)threadIdx.x < (int)blockIdx.x ? sums[threadIdx.x] : T(0);
+        T tot;
+        block_excl_scan<T, kScanThreads>(mine, tot, s_warp);
+        off = tot;
+    }
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) {
-        int64_t i = base + r * kThreads + threadIdx.x;
-        s_items[r * kThreads + threadIdx.x] = i < n ? in[i] : T(0);
+    for (int r = 0; r < IT; ++r) {
+        int64_t i = base + r * kScanThreads + threadIdx.x;
+        s_items[r * kScanThreads + threadIdx.x] = i < n ? in[i] : T(0);
     }
     __syncthreads();
-    T loc[kItems];
+    T loc[IT];
     T acc = 0;
 #pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-        loc[k] = s_items[threadIdx.x * kItems + k];
+    for (int k = 0; k < IT; ++k) {
+        loc[k] = s_items[threadIdx.x * IT + k];
         acc += loc[k];
     }
     T total;
-    T pre = block_excl_scan<T>(acc, total, s_warp);
-    const T off = block_off ? block_off[blockIdx.x] : T(0);
-    pre += off;
+    T pre = block_excl_scan<T, kScanThreads>(acc, total, s_warp) + off;
 #pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-        s_items[threadIdx.x * kItems + k] = pre;
+    for (int k = 0; k < IT; ++k) {
+        s_items[threadIdx.x * IT + k] = pre;
         pre += loc[k];
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) {
-        int64_t i = base + r * kThreads + threadIdx.x;
-        if (i < n) out[i] = s_items[r * kThreads + threadIdx.x];
+    for (int r = 0; r < IT; ++r) {
+        int64_t i = base + r * kScanThreads + threadIdx.x;
+        if (i < n) out[i] = s_items[r * kScanThreads + threadIdx.x];
     }
     if (write_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = off + total;
 }
 
-// number of scratch elements the recursive scan of n items needs
+// number of scratch elements the scan of n items needs
 size_t scan_scratch_elems(int64_t n) {
     size_t total = 0;
     int64_t m = n;
-    while (m > kTileItems) {
-        m = cdiv(m, kTileItems);
+    const int64_t tile = scan_tile<uint64_t>();  // the smaller tile of the two element types
+    while (m > tile) {
+        m = cdiv(m, tile);
         total += (size_t)m + 64;
     }
-    return total;
+    return total + 64;
 }
 
-// exclusive scan in -> out (may alias), out[n] = total if write_total
+// exclusive scan in -> out (may alias), out[n] = total if write_total.
+// One launch up to one block's tile, two up to kScanThreads blocks, else the
+// block sums are scanned recursively first.
 template <typename T>
 cudaError_t scan_exclusive(const T* in, T* out, int64_t n, T* scratch, bool write_total, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    const int nb = cdiv(n, kTileItems);
+    constexpr int smem = scan_tile<T>() * (int)sizeof(T);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_scan_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int nb = cdiv(n, scan_tile<T>());
     if (nb == 1) {
-        k_scan_apply<T><<<1, kThreads, 0, s>>>(in, n, nullptr, out, write_total ? 1 : 0);
+        k_scan_apply<T><<<1, kScanThreads, smem, s>>>(in, n, nullptr, 0, out, write_total ? 1 : 0);
         count_launches();
         return cudaGetLastError();
     }
     T* sums = scratch;
-    T* next = scratch + nb + 64;
-    k_scan_reduce<T><<<nb, kThreads, 0, s>>>(in, n, sums);
+    k_scan_reduce<T><<<nb, kScanThreads, 0, s>>>(in, n, sums);
     count_launches();
-    cudaError_t e = scan_exclusive<T>(sums, sums, nb, next, false, s);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_scan_apply<T><<<nb, kThreads, 0, s>>>(in, n, sums, out, write_total ? 1 : 0);
+    int scanned = 0;
+    if (nb > kScanThreads) {
+        // too many blocks for a block to add up its predecessors: turn the sums
+        // into exclusive offsets first
+        if ((e = scan_exclusive<T>(sums, sums, nb, scratch + nb + 64, false, s)) != cudaSuccess) return e;
+        scanned = 1;
+    }
+    k_scan_apply<T><<<nb, kScanThreads, smem, s>>>(in, n, sums, scanned, out, write_total ? 1 : 0);
     count_launches();
     return cudaGetLastError();
 }
