@@ -9,19 +9,42 @@
 //      (ceil(log2 tiles / 8) passes instead of ceil((32 + log2 tiles) / 8)).
 // Stability of step 3 keeps the depth order (and the index order of equal
 // depths from step 1) inside each tile.
+//
+// Every radix pass is one launch.  The digit histograms of all passes are
+// counted up front by the kernel that produces the keys (the counts of an LSD
+// pass do not depend on the order the previous pass leaves), and each block
+// finds where its digits go among the blocks before it by decoupled
+// look-back: blocks take tile numbers from an atomic ticket in the order they
+// start, publish their per-digit counts, then add up their predecessors'
+// published counts until one carries an inclusive prefix.  A block only waits
+// for blocks that started before it, so the waits always end; each is still
+// bounded in time and sets the timeout bit of the error word if it gives up.
+// The scan of instance counts in depth order is done the same way inside the
+// duplication kernel, so the whole stage is
+//   memset, count, 4 depth passes, duplicate, ceil(bits / 8) tile passes, finalize.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace gs {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kItems = 16;
-constexpr int kTileItems = kThreads * kItems;  // 4096 items per block
+constexpr uint32_t kSmallPass = 1u << 20;  // passes up to this size use 1024-item tiles, larger ones 4096
+constexpr int kDupItems = 1;                // items per thread of the duplication kernel
+constexpr int kDupTile = kThreads * kDupItems;
+constexpr int kMaxPasses = 8;               // 4 depth passes + up to 4 tile-id passes
+constexpr uint64_t kLookbackLimitNs = 2000000000ull;
 
-inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+inline int pass_items(uint64_t n) { return n <= kSmallPass ? 4 : 16; }
+// Most radix tiles a pass over at most m items can have.
+inline int64_t radix_tiles_max(int64_t m) {
+    return std::max(cdiv(std::min<int64_t>(m, kSmallPass), kThreads * 4), cdiv(m, kThreads * pass_items(m)));
+}
 
-// ------------------------------------------------------------ scan (excl) --
+// ---------------------------------------------------------- block helpers --
 
 template <typename T>
 __device__ __forceinline__ T warp_incl_scan(T v) {
@@ -55,127 +78,111 @@ __device__ __forceinline__ T block_excl_scan(T v, T& total, T* s_warp /*[NT/32 +
     return res;
 }
 
-// Scans run on 1024-thread blocks; a block covers kScanItems<T>() * 1024 elements
-// staged through 64 KB of dynamic shared memory.
-constexpr int kScanThreads = 1024;
-template <typename T>
-constexpr int scan_items() { return sizeof(T) == 8 ? 8 : 16; }
-template <typename T>
-constexpr int scan_tile() { return kScanThreads * scan_items<T>(); }
+// ------------------------------------------------------ look-back status --
+//
+// A status word holds a tag in bits [56, 64) and a count in bits [0, 56).
+// Pass p publishes tag 2p + 1 (this block's own count) and then 2p + 2 (the
+// inclusive prefix up to and including this block); any other tag (zero after
+// the clear, or a value an earlier pass left in the same word) means "not yet".
 
-template <typename T>
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const T* __restrict__ in, int64_t n, T* __restrict__ sums) {
-    __shared__ T s_warp[kScanThreads / 32 + 1];
-    const int64_t base = (int64_t)blockIdx.x * scan_tile<T>();
-    T acc = 0;
-#pragma unroll
-    for (int r = 0; r < scan_items<T>(); ++r) {
-        int64_t i = base + r * kScanThreads + threadIdx.x;
-        if (i < n) acc += in[i];
-    }
-    T total;
-    block_excl_scan<T, kScanThreads>(acc, total, s_warp);
-    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+constexpr uint64_t kValMask = (uint64_t(1) << 56) - 1;
+
+__device__ __forceinline__ void st_status(unsigned long long* p, uint32_t tag, uint64_t v) {
+    const unsigned long long w = ((unsigned long long)tag << 56) | (v & kValMask);
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_status(const unsigned long long* p) {
+    unsigned long long w;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+    return w;
 }
 
-// out[i] = sum_{k<i} in[k]; the block's offset is the sum of sums[0 .. block)
-// (each block adds up the block sums before it, at most kScanThreads of them);
-// if write_total, out[n] = sum of all.
-template <typename T>
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const T* in, int64_t n, const T* __restrict__ sums,
-                                                             int sums_scanned, T* out, int write_total) {
-    extern __shared__ __align__(16) unsigned char s_raw[];
-    T* s_items = reinterpret_cast<T*>(s_raw);
-    __shared__ T s_warp[kScanThreads / 32 + 1];
-    constexpr int IT = scan_items<T>();
-    const int64_t base = (int64_t)blockIdx.x * scan_tile<T>();
-    T off = 0;
-    if (sums != nullptr && sums_scanned) {
-        off = sums[blockIdx.x];
-    } else if (sums != nullptr) {
-        T mine = (int)threadIdx.x < (int)blockIdx.x ? sums[threadIdx.x] : T(0);
-        T tot;
-        block_excl_scan<T, kScanThreads>(mine, tot, s_warp);
-        off = tot;
-    }
+// Sum of the counts of tiles [0, tile) for one digit, walking back from
+// tile - 1 until an inclusive prefix is found.  Eight predecessors are read
+// per round trip; the ready ones nearest to this tile are consumed, up to the
+// first inclusive prefix.
+__device__ __forceinline__ uint64_t lookback_serial(const unsigned long long* status, int64_t tile, int stride,
+                                                    int d, uint32_t tag_agg, unsigned* err) {
+    constexpr int W = 8;
+    uint64_t prefix = 0, t0 = 0;
+    int64_t j = tile - 1;
+    while (j >= 0) {
+        unsigned long long w[W];
 #pragma unroll
-    for (int r = 0; r < IT; ++r) {
-        int64_t i = base + r * kScanThreads + threadIdx.x;
-        s_items[r * kScanThreads + threadIdx.x] = i < n ? in[i] : T(0);
-    }
-    __syncthreads();
-    T loc[IT];
-    T acc = 0;
+        for (int q = 0; q < W; ++q)
+            w[q] = j - q >= 0 ? ld_status(status + (size_t)(j - q) * stride + d)
+                              : ((unsigned long long)(tag_agg + 1) << 56);  // before tile 0: 0
+        int used = 0;
+        bool done = false, blocked = false;
 #pragma unroll
-    for (int k = 0; k < IT; ++k) {
-        loc[k] = s_items[threadIdx.x * IT + k];
-        acc += loc[k];
+        for (int q = 0; q < W; ++q) {
+            if (done || blocked) continue;
+            const uint32_t tag = (uint32_t)(w[q] >> 56);
+            if (tag == tag_agg || tag == tag_agg + 1) {
+                prefix += w[q] & kValMask;
+                ++used;
+                done = tag == tag_agg + 1;
+            } else {
+                blocked = true;
+            }
+        }
+        if (done) break;
+        j -= used;
+        if (blocked) {
+            const uint64_t now = globaltimer_ns();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > kLookbackLimitNs) {
+                atomicOr(err, kErrTimeout);
+                break;
+            }
+        }
     }
-    T total;
-    T pre = block_excl_scan<T, kScanThreads>(acc, total, s_warp) + off;
-#pragma unroll
-    for (int k = 0; k < IT; ++k) {
-        s_items[threadIdx.x * IT + k] = pre;
-        pre += loc[k];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < IT; ++r) {
-        int64_t i = base + r * kScanThreads + threadIdx.x;
-        if (i < n) out[i] = s_items[r * kScanThreads + threadIdx.x];
-    }
-    if (write_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = off + total;
+    return prefix;
 }
 
-// number of scratch elements the scan of n items needs
-size_t scan_scratch_elems(int64_t n) {
-    size_t total = 0;
-    int64_t m = n;
-    const int64_t tile = scan_tile<uint64_t>();  // the smaller tile of the two element types
-    while (m > tile) {
-        m = cdiv(m, tile);
-        total += (size_t)m + 64;
+// The same for a single count per tile, by one warp over windows of 32
+// predecessors (lane l reads tile j - l).  Every lane returns the prefix.
+__device__ __forceinline__ uint64_t lookback_warp(const unsigned long long* status, int64_t tile, uint32_t tag_agg,
+                                                  unsigned* err) {
+    const int lane = threadIdx.x & 31;
+    uint64_t prefix = 0, t0 = 0;
+    int64_t j = tile - 1;
+    while (j >= 0) {
+        const int64_t jj = j - lane;
+        const unsigned long long w =
+            jj >= 0 ? ld_status(status + jj) : ((unsigned long long)(tag_agg + 1) << 56);  // before tile 0: 0
+        const uint32_t tag = (uint32_t)(w >> 56);
+        const unsigned inc = __ballot_sync(0xffffffffu, tag == tag_agg + 1);
+        const unsigned notready = __ballot_sync(0xffffffffu, tag != tag_agg && tag != tag_agg + 1);
+        const int first_inc = inc ? __ffs(inc) - 1 : 32;
+        const unsigned needed = first_inc == 32 ? 0xffffffffu : (0xffffffffu >> (31 - first_inc));
+        if (notready & needed) {
+            const uint64_t now = globaltimer_ns();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > kLookbackLimitNs) {
+                if (lane == 0) atomicOr(err, kErrTimeout);
+                break;
+            }
+            continue;
+        }
+        uint64_t v = lane <= first_inc ? (uint64_t)(w & kValMask) : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        prefix += v;
+        if (first_inc < 32) break;
+        j -= 32;
     }
-    return total + 64;
+    return prefix;
 }
 
-// exclusive scan in -> out (may alias), out[n] = total if write_total.
-// One launch up to one block's tile, two up to kScanThreads blocks, else the
-// block sums are scanned recursively first.
-template <typename T>
-cudaError_t scan_exclusive(const T* in, T* out, int64_t n, T* scratch, bool write_total, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    constexpr int smem = scan_tile<T>() * (int)sizeof(T);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_scan_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    const int nb = cdiv(n, scan_tile<T>());
-    if (nb == 1) {
-        k_scan_apply<T><<<1, kScanThreads, smem, s>>>(in, n, nullptr, 0, out, write_total ? 1 : 0);
-        count_launches();
-        return cudaGetLastError();
-    }
-    T* sums = scratch;
-    k_scan_reduce<T><<<nb, kScanThreads, 0, s>>>(in, n, sums);
-    count_launches();
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    int scanned = 0;
-    if (nb > kScanThreads) {
-        // too many blocks for a block to add up its predecessors: turn the sums
-        // into exclusive offsets first
-        if ((e = scan_exclusive<T>(sums, sums, nb, scratch + nb + 64, false, s)) != cudaSuccess) return e;
-        scanned = 1;
-    }
-    k_scan_apply<T><<<nb, kScanThreads, smem, s>>>(in, n, sums, scanned, out, write_total ? 1 : 0);
-    count_launches();
-    return cudaGetLastError();
+// s_h[bin] += 1 for every active lane, one atomic per distinct bin in the warp
+// (digits of nearby keys often agree, and same-address shared atomics serialise).
+__device__ __forceinline__ void hist_add(uint32_t* s_h, uint32_t bin) {
+    const unsigned peers = __match_any_sync(__activemask(), bin);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&s_h[bin], (uint32_t)__popc(peers));
 }
-
-// ------------------------------------------------------------- radix sort --
 
 // Item count of a pass: the host value, or min(*n_dev, host value) in graph mode.
 __device__ __forceinline__ uint32_t pass_count(uint32_t n_host, const uint64_t* n_dev) {
@@ -184,110 +191,135 @@ __device__ __forceinline__ uint32_t pass_count(uint32_t n_host, const uint64_t* 
     return v < n_host ? (uint32_t)v : n_host;
 }
 
-__global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restrict__ keys, uint32_t n_host,
-                                                         const uint64_t* __restrict__ n_dev, int shift,
-                                                         uint32_t* __restrict__ hist, int nblk) {
-    __shared__ uint32_t s_cnt[256];
-    const uint32_t n = pass_count(n_host, n_dev);
-    s_cnt[threadIdx.x] = 0;
-    __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kTileItems;
-#pragma unroll
-    for (int r = 0; r < kItems; ++r) {
-        int64_t i = base + r * kThreads + threadIdx.x;
-        if (i < n) atomicAdd(&s_cnt[(keys[i] >> shift) & 0xFFu], 1u);
-    }
-    __syncthreads();
-    hist[(size_t)threadIdx.x * nblk + blockIdx.x] = s_cnt[threadIdx.x];
-}
+// ------------------------------------------------------------ radix pass --
 
-// Stable scatter: warp w owns the contiguous items [w*512, w*512 + 512) of the
-// block's tile, walked in rounds of 32 so lane order = input order.
-__global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __restrict__ kin,
-                                                            const uint32_t* __restrict__ vin, uint32_t n_host,
-                                                            const uint64_t* __restrict__ n_dev, int shift,
-                                                            const uint32_t* __restrict__ offs, int nblk,
-                                                            uint32_t* __restrict__ kout, uint32_t* __restrict__ vout) {
-    __shared__ uint32_t s_w[kThreads / 32][256];
+// One stable pass on bits [shift, shift + 8).  The block takes the next tile
+// of TILE items from the ticket; warp w owns the contiguous items
+// [w * 32 ITEMS, (w + 1) * 32 ITEMS) walked in rounds of 32, so lane order is
+// input order, and each item's rank among equal digits comes from
+// __match_any_sync.  Items are placed in shared memory in digit order, then
+// written so that consecutive threads write consecutive addresses of each
+// digit's run.  hist holds the pass's global digit counts.
+template <int ITEMS>
+__global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint32_t* __restrict__ kin,
+                                                       const uint32_t* __restrict__ vin, uint32_t n_host,
+                                                       const uint64_t* __restrict__ n_dev, int shift, int pass_id,
+                                                       const uint32_t* __restrict__ hist, uint32_t* tickets,
+                                                       unsigned long long* status, uint32_t* __restrict__ kout,
+                                                       uint32_t* __restrict__ vout, unsigned* err) {
+    constexpr int TILE = kThreads * ITEMS;
+    __shared__ uint32_t s_w[kThreads / 32][256];  // per-warp digit counts, then local bases
+    __shared__ uint32_t s_dbase[256];              // block-local start of each digit's run
+    __shared__ uint32_t s_goff[256];               // global start of each digit's run
+    __shared__ uint32_t s_warp[kThreads / 32 + 1];
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_key[TILE], s_val[TILE];
     const uint32_t n = pass_count(n_host, n_dev);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&tickets[pass_id], 1u);
     for (int i = threadIdx.x; i < (kThreads / 32) * 256; i += kThreads) (&s_w[0][0])[i] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kTileItems + warp * (kItems * 32);
-    uint32_t k[kItems], v[kItems];
+    const uint32_t tile = s_tile;
+    const int64_t bbase = (int64_t)tile * TILE;
+    if (bbase >= n) return;  // uniform over the block; no later tile is needed either
+    const int cnt = (int)((int64_t)n - bbase < TILE ? (int64_t)n - bbase : TILE);
+    const int wbase = warp * (ITEMS * 32);
+    uint32_t k[ITEMS], v[ITEMS];
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) {
-        int64_t i = base + r * 32 + lane;
-        k[r] = i < n ? kin[i] : 0u;
-        v[r] = i < n ? vin[i] : 0u;
+    for (int r = 0; r < ITEMS; ++r) {
+        const int i = wbase + r * 32 + lane;
+        k[r] = i < cnt ? kin[bbase + i] : 0u;
+        v[r] = i < cnt ? vin[bbase + i] : 0u;
     }
     const unsigned lt = (1u << lane) - 1u;
-    // per-warp digit counts
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) {
-        const bool valid = base + r * 32 + lane < n;
+    for (int r = 0; r < ITEMS; ++r) {
+        const bool valid = wbase + r * 32 + lane < cnt;
         const uint32_t d = valid ? ((k[r] >> shift) & 0xFFu) : (0x100u + lane);
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         if (valid && (peers & lt) == 0) s_w[warp][d] += __popc(peers);
         __syncwarp();
     }
     __syncthreads();
-    // exclusive bases per (warp, digit)
     {
         const int d = threadIdx.x;
-        uint32_t run = offs[(size_t)d * nblk + blockIdx.x];
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) c += s_w[w][d];
+        unsigned long long* mine = status + (size_t)tile * 256 + d;
+        const uint32_t tag_agg = 2u * pass_id + 1u;
+        st_status(mine, tile == 0 ? tag_agg + 1 : tag_agg, c);  // publish first, successors may be waiting
+        uint32_t total;
+        const uint32_t db = block_excl_scan<uint32_t, kThreads>(c, total, s_warp);
+        const uint32_t gstart = block_excl_scan<uint32_t, kThreads>(hist[d], total, s_warp);
+        uint32_t prefix = 0;
+        if (tile > 0) {
+            prefix = (uint32_t)lookback_serial(status, tile, 256, d, tag_agg, err);
+            st_status(mine, tag_agg + 1, prefix + c);
+        }
+        s_dbase[d] = db;
+        s_goff[d] = gstart + prefix;
+        uint32_t run = db;
 #pragma unroll
         for (int w = 0; w < kThreads / 32; ++w) {
-            uint32_t c = s_w[w][d];
+            const uint32_t cw = s_w[w][d];
             s_w[w][d] = run;
-            run += c;
+            run += cw;
         }
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) {
-        const bool valid = base + r * 32 + lane < n;
+    for (int r = 0; r < ITEMS; ++r) {
+        const bool valid = wbase + r * 32 + lane < cnt;
         const uint32_t d = valid ? ((k[r] >> shift) & 0xFFu) : (0x100u + lane);
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         uint32_t pos = 0;
         if (valid) pos = s_w[warp][d] + __popc(peers & lt);
         __syncwarp();
         if (valid) {
-            kout[pos] = k[r];
-            vout[pos] = v[r];
+            s_key[pos] = k[r];
+            s_val[pos] = v[r];
             if ((peers & lt) == 0) s_w[warp][d] += __popc(peers);
         }
         __syncwarp();
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += kThreads) {
+        const uint32_t key = s_key[i];
+        const uint32_t d = (key >> shift) & 0xFFu;
+        const uint32_t g = s_goff[d] + (uint32_t)i - s_dbase[d];
+        if (g < n) {  // always, unless a look-back gave up (timeout bit set)
+            kout[g] = key;
+            vout[g] = s_val[i];
+        }
+    }
 }
 
-struct RadixScratch {
-    uint32_t* hist;
-    uint32_t* scan;
+struct PassScratch {
+    const uint32_t* hist;  // [kMaxPasses][256] digit counts
+    uint32_t* tickets;     // [kMaxPasses]
+    unsigned long long* status;
+    unsigned* err;
 };
 
-// One stable pass on bits [shift, shift + 8) over n items (at most n, the
-// actual count in *n_dev, in graph mode).
-cudaError_t radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, uint32_t n,
-                       const uint64_t* n_dev, int shift, RadixScratch rs, cudaStream_t s) {
-    const int nblk = cdiv(n, kTileItems);
-    k_radix_hist<<<nblk, kThreads, 0, s>>>(kin, n, n_dev, shift, rs.hist, nblk);
-    count_launches();
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = scan_exclusive<uint32_t>(rs.hist, rs.hist, (int64_t)256 * nblk, rs.scan, false, s);
-    if (e != cudaSuccess) return e;
-    k_radix_scatter<<<nblk, kThreads, 0, s>>>(kin, vin, n, n_dev, shift, rs.hist, nblk, kout, vout);
-    count_launches();
-    return cudaGetLastError();
-}
-
-// Sorts (k[0], v[0]) on bits [0, bits); the result ends in buffer *which.
-cudaError_t radix_sort(uint32_t* k[2], uint32_t* v[2], uint32_t n, const uint64_t* n_dev, int bits, RadixScratch rs,
-                       int* which, cudaStream_t s) {
+// Stable LSD sort of (k[0], v[0]) on bits [0, bits) with pass ids
+// first_pass, first_pass + 1, ...; the result ends in buffer *which.  n_host
+// sizes the grid; in graph mode the passes sort min(*n_dev, n_host) items.
+cudaError_t radix_sort(uint32_t* k[2], uint32_t* v[2], uint32_t n_host, const uint64_t* n_dev, int bits,
+                       int first_pass, const PassScratch& ps, int* which, cudaStream_t s) {
     int cur = 0;
-    for (int shift = 0; shift < bits; shift += 8) {
-        cudaError_t e = radix_pass(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], n, n_dev, shift, rs, s);
+    const int items = pass_items(n_host);
+    const int nblk = (int)cdiv(n_host, (int64_t)kThreads * items);
+    for (int p = 0, shift = 0; shift < bits; ++p, shift += 8) {
+        const int id = first_pass + p;
+        if (items == 4)
+            k_onesweep<4><<<nblk, kThreads, 0, s>>>(k[cur], v[cur], n_host, n_dev, shift, id, ps.hist + 256 * id,
+                                                    ps.tickets, ps.status, k[cur ^ 1], v[cur ^ 1], ps.err);
+        else
+            k_onesweep<16><<<nblk, kThreads, 0, s>>>(k[cur], v[cur], n_host, n_dev, shift, id, ps.hist + 256 * id,
+                                                     ps.tickets, ps.status, k[cur ^ 1], v[cur ^ 1], ps.err);
+        count_launches();
+        cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         cur ^= 1;
     }
@@ -297,82 +329,232 @@ cudaError_t radix_sort(uint32_t* k[2], uint32_t* v[2], uint32_t n, const uint64_
 
 // ------------------------------------------------------ duplicate/finalize --
 
-__global__ void k_count(int n_items, const __grid_constant__ SortViews sv, const float2* __restrict__ mean2d,
-                        const int* __restrict__ radius, const float* __restrict__ depth, uint32_t* __restrict__ cnt,
-                        uint32_t* __restrict__ dkey, uint32_t* __restrict__ dval) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_items) return;
-    const ViewDesc& vd = sv.views[i / sv.n_per_view];
-    int x0, x1, y0, y1;
-    const float2 m = mean2d[i];
-    uint32_t c = 0;
-    if (tile_rect(m.x, m.y, radius[i], vd.W, vd.H, x0, x1, y0, y1)) c = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
-    cnt[i] = c;
-    dkey[i] = __float_as_uint(depth[i]);
-    dval[i] = (uint32_t)i;
-}
-
-__global__ void k_gather_counts(int n, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ cnt,
-                                uint64_t* __restrict__ out) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) out[k] = cnt[perm[k]];
-}
-
-// One thread per instance: find its item by binary search over the
-// depth-ordered exclusive offsets, then its tile inside the rectangle.  In
-// graph mode the count comes from offs[n_items] and is clamped to capacity
-// (overflow sets kErrCapacity); block 0 also stores the count for the caller.
-__global__ void k_duplicate(uint32_t I_host, int64_t capacity, int n_items, const uint64_t* __restrict__ offs,
-                            const uint32_t* __restrict__ perm, const __grid_constant__ SortViews sv,
-                            const float2* __restrict__ mean2d, const int* __restrict__ radius,
-                            uint32_t* __restrict__ tkey, uint32_t* __restrict__ tval, int64_t* __restrict__ count_out,
-                            unsigned* __restrict__ err) {
-    uint32_t I = I_host;
-    if (count_out != nullptr) {  // graph mode
-        const uint64_t total = offs[n_items];
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            *count_out = (int64_t)total;
-            if (total > (uint64_t)capacity) atomicOr(err, kErrCapacity);
+// Per item: its tile count and depth key; the depth keys' four digit
+// histograms (pass ids 0..3).  Also clears the tile ranges and the look-back
+// status words for this call.  Each thread takes kCountItems items, strided by
+// the block size, with all loads issued before any use.
+constexpr int kCountItems = 4;
+__global__ void __launch_bounds__(kThreads) k_count(int n_items, const __grid_constant__ SortViews sv,
+                                                    const float2* __restrict__ mean2d,
+                                                    const int* __restrict__ radius, const float* __restrict__ depth,
+                                                    uint32_t* __restrict__ cnt, uint32_t* __restrict__ dkey,
+                                                    uint32_t* __restrict__ dval, uint32_t* __restrict__ hist,
+                                                    uint4* __restrict__ clear, size_t clear_n,
+                                                    uint32_t* __restrict__ ranges, size_t ranges_n) {
+    __shared__ uint32_t s_h[4 * 256];
+    for (int i = threadIdx.x; i < 4 * 256; i += kThreads) s_h[i] = 0;
+    const int64_t base = (int64_t)blockIdx.x * (kThreads * kCountItems) + threadIdx.x;
+    float2 m[kCountItems];
+    int r[kCountItems];
+    uint32_t key[kCountItems];
+#pragma unroll
+    for (int q = 0; q < kCountItems; ++q) {
+        const int64_t i = base + q * kThreads;
+        const bool ok = i < n_items;
+        m[q] = ok ? mean2d[i] : make_float2(0.f, 0.f);
+        r[q] = ok ? radius[i] : 0;
+        key[q] = ok ? __float_as_uint(depth[i]) : 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kCountItems; ++q) {
+        const int64_t i = base + q * kThreads;
+        if (i < n_items) {
+            const ViewDesc& vd = sv.views[(int)i / sv.n_per_view];
+            int x0, x1, y0, y1;
+            uint32_t c = 0;
+            if (tile_rect(m[q].x, m[q].y, r[q], vd.W, vd.H, x0, x1, y0, y1))
+                c = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+            cnt[i] = c;
+            dkey[i] = key[q];
+            dval[i] = (uint32_t)i;
+#pragma unroll
+            for (int p = 0; p < 4; ++p) hist_add(s_h, p * 256 + ((key[q] >> (8 * p)) & 0xFFu));
         }
-        I = total < (uint64_t)capacity ? (uint32_t)total : (uint32_t)capacity;
     }
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= I) return;
-    // largest k with offs[k] <= i
-    int lo = 0, hi = n_items - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (offs[mid] <= i) lo = mid;
-        else hi = mid - 1;
-    }
-    const uint32_t item = perm[lo];
-    const uint32_t j = i - (uint32_t)offs[lo];
-    const ViewDesc& vd = sv.views[item / (uint32_t)sv.n_per_view];
-    int x0, x1, y0, y1;
-    const float2 m = mean2d[item];
-    tile_rect(m.x, m.y, radius[item], vd.W, vd.H, x0, x1, y0, y1);
-    const uint32_t w = (uint32_t)(x1 - x0 + 1);
-    const uint32_t ty = (uint32_t)y0 + j / w, tx = (uint32_t)x0 + j % w;
-    tkey[i] = (uint32_t)vd.tile_begin + ty * (uint32_t)vd.tiles_x + tx;
-    tval[i] = item;
+    const size_t stride = (size_t)gridDim.x * kThreads;
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < clear_n; i += stride) clear[i] = z;
+    for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < ranges_n; i += stride) ranges[i] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * 256; i += kThreads)
+        if (s_h[i]) atomicAdd(&hist[i], s_h[i]);
 }
 
+// Digit histograms of the tile ids [a, a + w) of one rectangle row, by runs:
+// a run inside one aligned block of 256 ids has constant digits 1..3, and its
+// digit-0 values form a contiguous range, added to the difference array s_d0
+// (the histogram of digit 0 is its prefix sum).
+__device__ __forceinline__ void row_hist(uint32_t a, uint32_t w, int passes, int* s_d0, uint32_t* s_h) {
+    while (w > 0) {
+        const uint32_t lo = a & 0xFFu, len = min(w, 256u - lo);
+        atomicAdd(&s_d0[lo], 1);
+        atomicSub(&s_d0[lo + len], 1);
+        for (int p = 1; p < passes; ++p) atomicAdd(&s_h[(p - 1) * 256 + ((a >> (8 * p)) & 0xFFu)], len);
+        a += len;
+        w -= len;
+    }
+}
+
+// Duplication in depth order with the scan of instance counts folded in.
+// Tile t (from the ticket) holds the depth-ordered items
+// [t * kDupTile, (t + 1) * kDupTile) in kDupItems rounds of 256; the tile's
+// instance offset comes from decoupled look-back over the tiles before it.
+// Each item's instances are its rectangle's tile ids, row-major, at
+// [offset, offset + count); items with more than 32 tiles are written by the
+// whole warp together.  Writes stop at `limit`; the total goes to *total and,
+// in graph mode, to *count_out, with kErrCapacity raised when it exceeds the
+// capacity.  The digit histograms of the written instances' tile ids go to
+// hist (tile_passes of them), so a truncated list still sorts into a
+// permutation of what was written.
+__global__ void __launch_bounds__(kThreads) k_duplicate(int n_items, const uint32_t* __restrict__ perm,
+                                                        const uint32_t* __restrict__ cnt,
+                                                        const __grid_constant__ SortViews sv,
+                                                        const float2* __restrict__ mean2d,
+                                                        const int* __restrict__ radius, uint64_t limit,
+                                                        int tile_passes, uint32_t* tickets,
+                                                        unsigned long long* status, uint32_t* __restrict__ tkey,
+                                                        uint32_t* __restrict__ tval, uint32_t* __restrict__ hist,
+                                                        uint64_t* __restrict__ total, int64_t* __restrict__ count_out,
+                                                        unsigned* err) {
+    __shared__ uint64_t s_warp[kThreads / 32 + 1];
+    __shared__ uint64_t s_prefix;
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_h[3 * 256];  // digits 1..3
+    __shared__ int s_d0[257];          // digit 0, as a difference array
+    __shared__ int s_warp_i[kThreads / 32 + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&tickets[kMaxPasses], 1u);
+    for (int i = threadIdx.x; i < 3 * 256; i += kThreads) s_h[i] = 0;
+    for (int i = threadIdx.x; i < 257; i += kThreads) s_d0[i] = 0;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const int64_t base = (int64_t)tile * kDupTile;
+    if (base >= n_items) return;
+
+    uint32_t item[kDupItems], c[kDupItems];
+    uint64_t local[kDupItems];
+    uint64_t tile_sum = 0;
+#pragma unroll
+    for (int r = 0; r < kDupItems; ++r) {
+        const int64_t k = base + r * kThreads + threadIdx.x;
+        item[r] = k < n_items ? perm[k] : 0u;
+        c[r] = k < n_items ? cnt[item[r]] : 0u;
+        uint64_t rt;
+        local[r] = tile_sum + block_excl_scan<uint64_t, kThreads>((uint64_t)c[r], rt, s_warp);
+        tile_sum += rt;
+    }
+    unsigned long long* mine = status + tile;
+    if (warp == 0) {
+        if (lane == 0) st_status(mine, tile == 0 ? 2u : 1u, tile_sum);
+        uint64_t prefix = 0;
+        if (tile > 0) {
+            prefix = lookback_warp(status, tile, 1u, err);
+            if (lane == 0) st_status(mine, 2u, prefix + tile_sum);
+        }
+        if (lane == 0) {
+            s_prefix = prefix;
+            if (base + kDupTile >= n_items) {  // the last tile: the total
+                const uint64_t all = prefix + tile_sum;
+                *total = all;
+                if (count_out != nullptr) {
+                    *count_out = (int64_t)all;
+                    if (all > limit) atomicOr(err, kErrCapacity);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const uint64_t prefix = s_prefix;
+
+#pragma unroll
+    for (int r = 0; r < kDupItems; ++r) {
+        uint32_t w = 1, h = 0, tile0 = 0, tx = 0;
+        if (c[r] > 0) {
+            const ViewDesc& vd = sv.views[item[r] / (uint32_t)sv.n_per_view];
+            int x0, x1, y0, y1;
+            const float2 m = mean2d[item[r]];
+            tile_rect(m.x, m.y, radius[item[r]], vd.W, vd.H, x0, x1, y0, y1);
+            w = (uint32_t)(x1 - x0 + 1);
+            h = (uint32_t)(y1 - y0 + 1);
+            tx = (uint32_t)vd.tiles_x;
+            tile0 = (uint32_t)vd.tile_begin + (uint32_t)y0 * tx + (uint32_t)x0;
+        }
+        const uint64_t off = prefix + local[r];
+        const bool big = c[r] > 32;
+        if (!big) {
+            uint32_t row = tile0, col = 0;
+            for (uint32_t j = 0; j < c[r]; ++j) {
+                const uint64_t pos = off + j;
+                if (pos >= limit) break;
+                const uint32_t t = row + col;
+                tkey[pos] = t;
+                tval[pos] = item[r];
+                if (++col == w) {
+                    col = 0;
+                    row += tx;
+                }
+            }
+            // histogram of the instances written (all of them unless the capacity cuts this item)
+            const uint32_t nw = off >= limit ? 0u : (uint32_t)min((uint64_t)c[r], limit - off);
+            for (uint32_t y = 0; y * w < nw; ++y) row_hist(tile0 + y * tx, min(w, nw - y * w), tile_passes, s_d0, s_h);
+        }
+        unsigned bigs = __ballot_sync(0xffffffffu, big);
+        while (bigs) {
+            const int src = __ffs(bigs) - 1;
+            bigs &= bigs - 1;
+            const uint32_t bi = __shfl_sync(0xffffffffu, item[r], src), bc = __shfl_sync(0xffffffffu, c[r], src);
+            const uint32_t bw = __shfl_sync(0xffffffffu, w, src), bt0 = __shfl_sync(0xffffffffu, tile0, src);
+            const uint32_t btx = __shfl_sync(0xffffffffu, tx, src), bh = __shfl_sync(0xffffffffu, h, src);
+            const uint64_t boff = __shfl_sync(0xffffffffu, off, src);
+            const uint32_t bnw = boff >= limit ? 0u : (uint32_t)min((uint64_t)bc, limit - boff);
+            for (uint32_t y = lane; y < bh && y * bw < bnw; y += 32)
+                row_hist(bt0 + y * btx, min(bw, bnw - y * bw), tile_passes, s_d0, s_h);
+            for (uint32_t j = lane; j < bc; j += 32) {
+                const uint64_t pos = boff + j;
+                if (pos >= limit) break;
+                const uint32_t t = bt0 + (j / bw) * btx + j % bw;
+                tkey[pos] = t;
+                tval[pos] = bi;
+            }
+        }
+    }
+    __syncthreads();
+    {
+        int tot;
+        const int v = s_d0[threadIdx.x];
+        const int d0 = block_excl_scan<int, kThreads>(v, tot, s_warp_i) + v;  // count of digit-0 value threadIdx.x
+        if (d0) atomicAdd(&hist[threadIdx.x], (uint32_t)d0);
+    }
+    for (int i = threadIdx.x; i < (tile_passes - 1) * 256; i += kThreads)
+        if (s_h[i]) atomicAdd(&hist[256 + i], s_h[i]);
+}
+
+// Sorted keys, ids and tile ranges.  Tile ids and item indices are checked
+// against their bounds: after a look-back that gave up (timeout bit set) the
+// passes can leave stale entries, which become item 0 and no range.
 __global__ void k_finalize(uint32_t I_host, const uint64_t* __restrict__ I_dev, const uint32_t* __restrict__ tkey,
-                           const uint32_t* __restrict__ tval, const float* __restrict__ depth,
-                           uint64_t* __restrict__ keys_sorted, uint32_t* __restrict__ ids_sorted,
+                           const uint32_t* __restrict__ tval, const float* __restrict__ depth, uint32_t n_items,
+                           uint32_t num_tiles, uint64_t* __restrict__ keys_sorted, uint32_t* __restrict__ ids_sorted,
                            uint32_t* __restrict__ ranges) {
     const uint32_t I = pass_count(I_host, I_dev);
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= I) return;
-    const uint32_t t = tkey[i], g = tval[i];
+    const uint32_t t = tkey[i];
+    const uint32_t g = tval[i] < n_items ? tval[i] : 0u;
     keys_sorted[i] = ((uint64_t)t << 32) | __float_as_uint(depth[g]);
     ids_sorted[i] = g;
+    if (t >= num_tiles) return;
     if (i == 0 || tkey[i - 1] != t) ranges[2 * t] = i;
     if (i == I - 1 || tkey[i + 1] != t) ranges[2 * t + 1] = i + 1;
 }
 
+// Workspace: per-item arrays, a header cleared by one memset (digit
+// histograms, tickets, total), the look-back status words (cleared by
+// k_count), and the instance key/value double buffers.
 struct Layout {
-    size_t cnt, dk0, dk1, dv0, dv1, c64, offs, sscan, hist, hscan, tk0, tk1, tv0, tv1, total;
+    size_t cnt, dk0, dk1, dv0, dv1, hdr, hist, tickets, total, hdr_bytes, status, status_bytes, tk0, tk1, tv0, tv1,
+        total_bytes;
 };
 
 Layout make_layout(int n, int64_t capacity) {
@@ -389,25 +571,28 @@ Layout make_layout(int n, int64_t capacity) {
     L.dk1 = take(4 * N);
     L.dv0 = take(4 * N);
     L.dv1 = take(4 * N);
-    L.c64 = take(8 * N);
-    L.offs = take(8 * (N + 1));
-    L.sscan = take(8 * scan_scratch_elems((int64_t)N));
-    const int64_t most = (int64_t)(N > C ? N : C);
-    const int64_t hist_elems = (int64_t)256 * cdiv(most, kTileItems);
-    L.hist = take(4 * (size_t)hist_elems);
-    L.hscan = take(4 * scan_scratch_elems(hist_elems));
+    L.hdr = o;
+    L.hist = take(4 * 256 * kMaxPasses);
+    L.tickets = take(4 * (kMaxPasses + 1));
+    L.total = take(8);
+    L.hdr_bytes = o - L.hdr;
+    // status words: 256 per radix tile (the largest tile count of either sort)
+    // plus one per duplication tile
+    const size_t radix_tiles = (size_t)std::max(radix_tiles_max((int64_t)N), radix_tiles_max((int64_t)C));
+    L.status = take(8 * (256 * radix_tiles + (size_t)cdiv((int64_t)N, kDupTile)));
+    L.status_bytes = o - L.status;  // a multiple of 256
     L.tk0 = take(4 * C);
     L.tk1 = take(4 * C);
     L.tv0 = take(4 * C);
     L.tv1 = take(4 * C);
-    L.total = o;
+    L.total_bytes = o;
     return L;
 }
 
 }  // namespace
 
 size_t bin_sort_workspace_bytes(int n_items, int64_t capacity, int /*num_tiles*/) {
-    return make_layout(n_items, capacity).total;
+    return make_layout(n_items, capacity).total_bytes;
 }
 
 gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* radius, const float* depth,
@@ -416,10 +601,11 @@ gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* ra
     const int ntiles = sv.total_tiles;
     const int n = sv.num_views * sv.n_per_view;  // items
     const bool graph = n_instances_host == nullptr;
-    cudaError_t e = cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)ntiles, s);
-    if (e != cudaSuccess) return cuda_status(e, "gs_bin_sort: clear ranges");
+    cudaError_t e;
     if (!graph) *n_instances_host = 0;
     if (n == 0) {
+        if ((e = cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)ntiles, s)) != cudaSuccess)
+            return cuda_status(e, "gs_bin_sort: clear ranges");
         if (graph && (e = cudaMemsetAsync(n_instances_dev, 0, sizeof(int64_t), s)) != cudaSuccess)
             return cuda_status(e, "gs_bin_sort: count");
         return GS_OK;
@@ -430,33 +616,50 @@ gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* ra
     char* base = static_cast<char*>(ws);
     auto U32 = [&](size_t off) { return reinterpret_cast<uint32_t*>(base + off); };
     const float2* mean2d = reinterpret_cast<const float2*>(mean2d_f);
-    RadixScratch rs{U32(L.hist), U32(L.hscan)};
+    uint32_t* hist = U32(L.hist);
+    uint32_t* tickets = U32(L.tickets);
+    uint64_t* total = reinterpret_cast<uint64_t*>(base + L.total);
+    unsigned long long* status = reinterpret_cast<unsigned long long*>(base + L.status);
+    const int64_t radix_status_words = (int64_t)(L.status_bytes / 8) - cdiv(n, kDupTile);
+    unsigned long long* dup_status = status + radix_status_words;
+    const PassScratch ps{hist, tickets, status, err};
 
-    // 1. counts and depth keys; depth sort of all items
-    k_count<<<cdiv(n, 256), 256, 0, s>>>(n, sv, mean2d, radius, depth, U32(L.cnt), U32(L.dk0), U32(L.dv0));
+    // 1. counts, depth keys and their digit histograms; clears
+    if ((e = cudaMemsetAsync(base + L.hdr, 0, L.hdr_bytes, s)) != cudaSuccess)
+        return cuda_status(e, "gs_bin_sort: clear header");
+    const int count_blocks = (int)cdiv(n, kThreads * kCountItems);
+    k_count<<<count_blocks, kThreads, 0, s>>>(n, sv, mean2d, radius, depth, U32(L.cnt), U32(L.dk0), U32(L.dv0), hist,
+                                              reinterpret_cast<uint4*>(status), L.status_bytes / 16, tile_ranges,
+                                              2 * (size_t)ntiles);
     count_launches();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: count");
+
+    // 2. depth sort of all items (pass ids 0..3)
     uint32_t* dk[2] = {U32(L.dk0), U32(L.dk1)};
     uint32_t* dv[2] = {U32(L.dv0), U32(L.dv1)};
     int which = 0;
-    if ((e = radix_sort(dk, dv, (uint32_t)n, nullptr, 32, rs, &which, s)) != cudaSuccess)
+    if ((e = radix_sort(dk, dv, (uint32_t)n, nullptr, 32, 0, ps, &which, s)) != cudaSuccess)
         return cuda_status(e, "gs_bin_sort: depth sort");
     const uint32_t* perm = dv[which];
 
-    // 2. offsets of each item's instances in depth order
-    uint64_t* c64 = reinterpret_cast<uint64_t*>(base + L.c64);
-    uint64_t* offs = reinterpret_cast<uint64_t*>(base + L.offs);
-    k_gather_counts<<<cdiv(n, 256), 256, 0, s>>>(n, perm, U32(L.cnt), c64);
+    // 3. duplicate in depth order (pass ids 4.. for the tile-id histograms)
+    int tile_bits = 1;
+    while ((1ll << tile_bits) < ntiles) ++tile_bits;
+    const int tile_passes = (tile_bits + 7) / 8;
+    uint32_t* tk[2] = {U32(L.tk0), U32(L.tk1)};
+    uint32_t* tv[2] = {U32(L.tv0), U32(L.tv1)};
+    k_duplicate<<<(int)cdiv(n, kDupTile), kThreads, 0, s>>>(n, perm, U32(L.cnt), sv, mean2d, radius, (uint64_t)capacity,
+                                                          tile_passes, tickets, dup_status, tk[0], tv[0],
+                                                          hist + 256 * 4, total, graph ? n_instances_dev : nullptr,
+                                                          err);
     count_launches();
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: gather");
-    if ((e = scan_exclusive<uint64_t>(c64, offs, n, reinterpret_cast<uint64_t*>(base + L.sscan), true, s)) !=
-        cudaSuccess)
-        return cuda_status(e, "gs_bin_sort: scan");
-    uint64_t I = 0;
-    const uint64_t* I_dev = nullptr;
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: duplicate");
+
     uint32_t I_grid = 0;  // items the remaining kernels are launched for
+    const uint64_t* I_dev = nullptr;
     if (!graph) {
-        if ((e = cudaMemcpyAsync(&I, offs + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        uint64_t I = 0;
+        if ((e = cudaMemcpyAsync(&I, total, sizeof(uint64_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
             return cuda_status(e, "gs_bin_sort: read count");
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_status(e, "gs_bin_sort: synchronize");
         *n_instances_host = (int64_t)I;
@@ -467,29 +670,17 @@ gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* ra
         if (I == 0) return GS_OK;
         I_grid = (uint32_t)I;
     } else {
-        if (capacity == 0) {
-            k_duplicate<<<1, 32, 0, s>>>(0, 0, n, offs, perm, sv, mean2d, radius, nullptr, nullptr,
-                                         n_instances_dev, err);
-            count_launches();
-            return cuda_status(cudaGetLastError(), "gs_bin_sort: count");
-        }
-        I_dev = offs + n;
+        if (capacity == 0) return GS_OK;
+        I_dev = total;
         I_grid = (uint32_t)capacity;
     }
 
-    // 3. duplicate, then stable sort by global tile id
-    uint32_t* tk[2] = {U32(L.tk0), U32(L.tk1)};
-    uint32_t* tv[2] = {U32(L.tv0), U32(L.tv1)};
-    k_duplicate<<<cdiv((int64_t)I_grid, 256), 256, 0, s>>>((uint32_t)I, capacity, n, offs, perm, sv, mean2d, radius,
-                                                            tk[0], tv[0], graph ? n_instances_dev : nullptr, err);
-    count_launches();
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: duplicate");
-    int tile_bits = 1;
-    while ((1ll << tile_bits) < ntiles) ++tile_bits;
-    if ((e = radix_sort(tk, tv, I_grid, I_dev, tile_bits, rs, &which, s)) != cudaSuccess)
+    // 4. stable sort by global tile id, then keys, ids and ranges
+    if ((e = radix_sort(tk, tv, I_grid, I_dev, tile_bits, 4, ps, &which, s)) != cudaSuccess)
         return cuda_status(e, "gs_bin_sort: tile sort");
-    k_finalize<<<cdiv((int64_t)I_grid, 256), 256, 0, s>>>(I_grid, I_dev, tk[which], tv[which], depth, keys_sorted,
-                                                         ids_sorted, tile_ranges);
+    k_finalize<<<(int)cdiv((int64_t)I_grid, 256), 256, 0, s>>>(I_grid, I_dev, tk[which], tv[which], depth,
+                                                               (uint32_t)n, (uint32_t)ntiles, keys_sorted,
+                                                               ids_sorted, tile_ranges);
     count_launches();
     return cuda_status(cudaGetLastError(), "gs_bin_sort: finalize");
 }

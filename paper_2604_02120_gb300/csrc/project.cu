@@ -66,13 +66,18 @@ __device__ __forceinline__ void quat_scale_matrix(const float* q4, const float* 
 }
 
 // blockIdx.y = view; outputs of view v, Gaussian g at index v * n + g.
+// SH_DEGREE is a template argument so that the basis and the coefficient loop
+// stay in registers; VEC16 reads the coefficients with 16-byte loads (every
+// Gaussian's block of them 16-byte aligned).
+template <int SH_DEGREE, bool VEC16>
 __global__ void __launch_bounds__(256) k_project(int n, const float* __restrict__ means,
                                                  const float* __restrict__ scales, const float* __restrict__ quats,
-                                                 const float* __restrict__ sh, int sh_degree,
+                                                 const float* __restrict__ sh,
                                                  const __grid_constant__ CamViews views,
                                                  float2* __restrict__ mean2d_all, float* __restrict__ conic_all,
                                                  float* __restrict__ depth_all, int* __restrict__ radius_all,
                                                  float* __restrict__ rgb_all, uint32_t* __restrict__ touched_all) {
+    constexpr int K = (SH_DEGREE + 1) * (SH_DEGREE + 1);
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
     const CamDev& cam = views.cams[blockIdx.y];
@@ -154,23 +159,22 @@ __global__ void __launch_bounds__(256) k_project(int n, const float* __restrict_
             float dx = mwx - cxw, dy = mwy - cyw, dz = mwz - czw;
             float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
             float x = dx * inv, y = dy * inv, z = dz * inv;
-            const int K = (sh_degree + 1) * (sh_degree + 1);
             const float* c = sh + (size_t)g * K * 3;
-            float basis[16];
+            float basis[K];
             basis[0] = kSH0;
-            if (sh_degree >= 1) {
+            if constexpr (SH_DEGREE >= 1) {
                 basis[1] = -kSH1 * y;
                 basis[2] = kSH1 * z;
                 basis[3] = -kSH1 * x;
             }
-            if (sh_degree >= 2) {
+            if constexpr (SH_DEGREE >= 2) {
                 float xx = x * x, yy = y * y, zz = z * z;
                 basis[4] = kSH2[0] * x * y;
                 basis[5] = kSH2[1] * y * z;
                 basis[6] = kSH2[2] * (2.f * zz - xx - yy);
                 basis[7] = kSH2[3] * x * z;
                 basis[8] = kSH2[4] * (xx - yy);
-                if (sh_degree >= 3) {
+                if constexpr (SH_DEGREE >= 3) {
                     basis[9] = kSH3[0] * y * (3.f * xx - yy);
                     basis[10] = kSH3[1] * x * y * z;
                     basis[11] = kSH3[2] * y * (4.f * zz - xx - yy);
@@ -181,11 +185,28 @@ __global__ void __launch_bounds__(256) k_project(int n, const float* __restrict_
                 }
             }
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                float acc = 0.f;
-                for (int k = 0; k < K; ++k) acc += c[3 * k + ch] * basis[k];
-                col[ch] = fmaxf(0.f, acc + 0.5f);
+            for (int ch = 0; ch < 3; ++ch) col[ch] = 0.f;
+            float cf[3 * K];
+            if constexpr (VEC16) {
+#pragma unroll
+                for (int q = 0; q < 3 * K / 4; ++q) {
+                    const float4 v = __ldg(reinterpret_cast<const float4*>(c) + q);
+                    cf[4 * q] = v.x;
+                    cf[4 * q + 1] = v.y;
+                    cf[4 * q + 2] = v.z;
+                    cf[4 * q + 3] = v.w;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 3 * K; ++q) cf[q] = __ldg(c + q);
             }
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) col[ch] += cf[3 * k + ch] * basis[k];
+            }
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) col[ch] = fmaxf(0.f, col[ch] + 0.5f);
         } else {
             cA = cB = cC = 0.f;
             m2 = make_float2(0.f, 0.f);
@@ -210,8 +231,28 @@ cudaError_t launch_project(int n, const float* means, const float* scales, const
                            int* radius, float* rgb, uint32_t* tiles_touched, cudaStream_t s) {
     const int block = 256;
     const dim3 grid((n + block - 1) / block, cams.num_views);
-    k_project<<<grid, block, 0, s>>>(n, means, scales, quats, sh, sh_degree, cams,
-                                     reinterpret_cast<float2*>(mean2d), conic, depth, radius, rgb, tiles_touched);
+    // 16-byte coefficient loads for degrees 1 and 3 (3K a multiple of 4) on an aligned array
+    const bool vec = (reinterpret_cast<uintptr_t>(sh) & 15) == 0;
+    switch (sh_degree) {
+        case 0: k_project<0, false><<<grid, block, 0, s>>>(n, means, scales, quats, sh, cams, reinterpret_cast<float2*>(mean2d), conic, depth, radius, rgb,
+                                       tiles_touched);
+            break;
+        case 1:
+            if (vec) k_project<1, true><<<grid, block, 0, s>>>(n, means, scales, quats, sh, cams, reinterpret_cast<float2*>(mean2d), conic, depth, radius, rgb,
+                                       tiles_touched);
+            else k_project<1, false><<<grid, block, 0, s>>>(n, means, scales, quats, sh, cams, reinterpret_cast<float2*>(mean2d), conic, depth, radius, rgb,
+                                       tiles_touched);
+            break;
+        case 2: k_project<2, false><<<grid, block, 0, s>>>(n, means, scales, quats, sh, cams, reinterpret_cast<float2*>(mean2d), conic, depth, radius, rgb,
+                                       tiles_touched);
+            break;
+        default:
+            if (vec) k_project<3, true><<<grid, block, 0, s>>>(n, means, scales, quats, sh, cams, reinterpret_cast<float2*>(mean2d), conic, depth, radius, rgb,
+                                       tiles_touched);
+            else k_project<3, false><<<grid, block, 0, s>>>(n, means, scales, quats, sh, cams, reinterpret_cast<float2*>(mean2d), conic, depth, radius, rgb,
+                                       tiles_touched);
+            break;
+    }
     count_launches();
     return cudaGetLastError();
 }

@@ -90,6 +90,30 @@ def test_project_matches_oracle(kind):
     assert (pn["tiles_touched"][both] == ref["tiles_touched"][both]).mean() > 0.999
 
 
+@pytest.mark.parametrize("sh_degree", [0, 1, 2, 3])
+def test_project_every_sh_degree_and_unaligned_coefficients(sh_degree):
+    """Colours of every SH degree match the oracle, and a coefficient array
+    that is not 16-byte aligned (it then takes the 4-byte load path) gives
+    bit-identical outputs to an aligned copy."""
+    sc = scenes.tiny_scene(11 + sh_degree, n=700, width=96, height=80, sh_degree=sh_degree)
+    dev = gs.scene_to_device(sc)
+    cam = sc.cameras[0]
+    aligned = gs.project(dev["means"], dev["scales"], dev["quats"], dev["sh"], sh_degree, cam)
+    flat = dev["sh"].reshape(-1)
+    padded = torch.empty(flat.numel() + 1, device="cuda", dtype=torch.float32)
+    padded[1:] = flat
+    shifted = padded[1:]
+    assert shifted.data_ptr() % 16 == 4
+    moved = gs.project(dev["means"], dev["scales"], dev["quats"], shifted, sh_degree, cam)
+    for key in aligned:
+        np.testing.assert_array_equal(to_np(moved)[key], to_np(aligned)[key])
+    ref = oracle.project(sc.means, sc.scales, sc.quats, sc.sh, sh_degree, cam)
+    got = to_np(aligned)
+    both = (ref["radius"] > 0) & (got["radius"] > 0)
+    assert both.sum() > 100
+    np.testing.assert_allclose(got["rgb"][both], ref["rgb"][both], rtol=0, atol=2e-5)
+
+
 # ----------------------------------------------------------------- binning --
 
 @pytest.mark.parametrize("kind", ["c0", "tiny_ragged", "tiny_dense", "c1"])

@@ -226,3 +226,54 @@ def test_sixteen_camera_batch_full_size():
     img, Tf, nc = br.view_image(v)
     torch.testing.assert_close(img, out["image"], rtol=0, atol=0)
     torch.testing.assert_close(nc, out["n_contrib"], rtol=0, atol=0)
+
+
+def test_bin_sort_views_three_tile_digit_passes_match_oracle_per_view():
+    """12 views of 4000 x 4000 pixels hold 750,000 tiles, so the tile-id sort
+    takes three 8-bit passes; 250 tiles per row put rectangle rows across
+    multiples of 256 tile ids.  Every view's lists must equal the oracle's
+    single-view bin/sort, shifted to the view's global tile and item range."""
+    sizes = [(4000, 4000)] * 12
+    sc = scenes.tiny_scene(21, n=300, width=64, height=64, sh_degree=0, scale_lo=-3.5, scale_hi=-2.5)
+    sc.cameras = scenes.ring_cameras(len(sizes), 3.0, sizes)
+    dev = gs.scene_to_device(sc)
+    V, n = len(sizes), sc.n
+    f32 = dict(device="cuda", dtype=torch.float32)
+    out = dict(mean2d=torch.empty(V * n, 2, **f32), conic=torch.empty(V * n, 3, **f32),
+               depth=torch.empty(V * n, **f32), radius=torch.empty(V * n, device="cuda", dtype=torch.int32),
+               rgb=torch.empty(V * n, 3, **f32), touched=torch.empty(V * n, device="cuda", dtype=torch.int32))
+    gs.gs_project_views(n, dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], sc.cameras,
+                        out["mean2d"], out["conic"], out["depth"], out["radius"], out["rgb"], out["touched"])
+    total_tiles = sum(gs.num_tiles(w, h) for w, h in sizes)
+    assert total_tiles > 1 << 16
+    capacity = int(out["touched"].sum().item()) + 1000
+    ws = torch.empty(gs.gs_bin_sort_workspace_size(V * n, capacity, 64, 64) + 256, device="cuda", dtype=torch.uint8)
+    keys = torch.empty(capacity, device="cuda", dtype=torch.int64)
+    ids = torch.empty(capacity, device="cuda", dtype=torch.int32)
+    ranges = torch.empty(2 * total_tiles, device="cuda", dtype=torch.int32)
+    _, count = gs.gs_bin_sort_views(V, n, out["mean2d"], out["radius"], out["depth"], [w for w, _ in sizes],
+                                    [h for _, h in sizes], capacity, ws, keys, ids, ranges)
+    assert gs.gs_sync_status() == gs.GS_OK
+    keys_np = keys[:count].cpu().numpy().view(np.uint64)
+    ids_np = ids[:count].cpu().numpy().view(np.uint32)
+    ranges_np = ranges.cpu().numpy().view(np.uint32)
+    m2 = out["mean2d"].cpu().numpy()
+    rad = out["radius"].cpu().numpy()
+    dep = out["depth"].cpu().numpy()
+    tile0, total = 0, 0
+    for v, (w, h) in enumerate(sizes):
+        sl = slice(v * n, (v + 1) * n)
+        ref = oracle.bin_sort(m2[sl].astype(np.float64), rad[sl], dep[sl], w, h)
+        nt = gs.num_tiles(w, h)
+        lo = int(ranges_np[2 * tile0:2 * (tile0 + nt):2][ref["tile_ranges"][1::2] > 0].min())
+        seg = slice(lo, lo + ref["n_instances"])
+        np.testing.assert_array_equal(ids_np[seg], ref["ids"] + v * n)
+        np.testing.assert_array_equal(keys_np[seg], ref["keys"] + (np.uint64(tile0) << np.uint64(32)))
+        got_r = ranges_np[2 * tile0:2 * (tile0 + nt)].astype(np.int64).reshape(-1, 2)
+        want_r = ref["tile_ranges"].astype(np.int64).reshape(-1, 2)
+        nonempty = want_r[:, 1] > want_r[:, 0]
+        np.testing.assert_array_equal(got_r[nonempty] - lo, want_r[nonempty])
+        assert (got_r[~nonempty] == 0).all()
+        tile0 += nt
+        total += ref["n_instances"]
+    assert total == count
