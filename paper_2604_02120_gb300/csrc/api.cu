@@ -336,6 +336,8 @@ gs_status gs_blend_backward_views(int32_t n_views, const int32_t* widths, const 
         return GS_ERR_INVALID_ARG;
     }
     GradArgs g{T_final, n_contrib, dL_dimage, reinterpret_cast<float2*>(dmean2d), dconic, dopacity, drgb};
+    if (is_tc(o->variant))
+        return cuda_status(launch_blend_tc_bwd(a, g, o->variant, stream), "gs_blend_backward");
     return cuda_status(launch_blend_fp32_bwd(a, g, stream), "gs_blend_backward");
 }
 

@@ -14,7 +14,9 @@ constexpr int kQueueSlots = 1024;
 __device__ unsigned g_tile_queue[kQueueSlots];
 std::atomic<unsigned> g_next_slot{0};
 
-unsigned* queue_slot(cudaStream_t s, cudaError_t* err) {
+}  // namespace
+
+unsigned* tile_queue_slot(cudaStream_t s, cudaError_t* err) {
     static unsigned* base[64] = {nullptr};
     int dev = 0;
     *err = cudaGetDevice(&dev);
@@ -34,8 +36,6 @@ unsigned* queue_slot(cudaStream_t s, cudaError_t* err) {
     return *err == cudaSuccess ? q : nullptr;
 }
 
-}  // namespace
-
 bool tc_config_supported(int variant, int chunk, int stages) {
     if (variant < GS_BLEND_TC_FP16 || variant > GS_BLEND_TC_BF16_SPLIT) return false;
     return (chunk == 32 && (stages == 2 || stages == 4)) || (chunk == 16 && stages == 4) ||
@@ -46,7 +46,7 @@ cudaError_t launch_blend_tc(const BlendArgs& a0, int variant, int chunk, int sta
                             cudaStream_t s) {
     BlendArgs a = a0;
     cudaError_t e = cudaSuccess;
-    a.queue = queue_slot(s, &e);
+    a.queue = tile_queue_slot(s, &e);
     if (a.queue == nullptr) return e;
     a.total_tiles = items;
     switch (variant) {

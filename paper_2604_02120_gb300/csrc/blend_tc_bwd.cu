@@ -1,0 +1,20 @@
+// Dispatch of the tensor-core blend gradient over variants.
+#include "blend_tc_bwd.cuh"
+
+namespace gs {
+
+cudaError_t launch_blend_tc_bwd(const BlendArgs& a0, const GradArgs& g, int variant, cudaStream_t s) {
+    BlendArgs a = a0;
+    cudaError_t e = cudaSuccess;
+    a.queue = tile_queue_slot(s, &e);
+    if (a.queue == nullptr) return e;
+    switch (variant) {
+        case GS_BLEND_TC_FP16: return tc::launch_bwd_variant<GS_BLEND_TC_FP16>(a, g, s);
+        case GS_BLEND_TC_BF16: return tc::launch_bwd_variant<GS_BLEND_TC_BF16>(a, g, s);
+        case GS_BLEND_TC_FP16_SPLIT: return tc::launch_bwd_variant<GS_BLEND_TC_FP16_SPLIT>(a, g, s);
+        case GS_BLEND_TC_BF16_SPLIT: return tc::launch_bwd_variant<GS_BLEND_TC_BF16_SPLIT>(a, g, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace gs

@@ -98,5 +98,10 @@ cudaError_t launch_blend_fp32_bwd(const BlendArgs& a, const GradArgs& g, cudaStr
 cudaError_t launch_blend_tc(const BlendArgs& a, int variant, int chunk, int stages, bool dump, int grid,
                             cudaStream_t s);
 bool tc_config_supported(int variant, int chunk, int stages);
+// Gradient of the tensor-core blend of `variant` (exponents recomputed with the
+// forward pass's tensor-core arithmetic).
+cudaError_t launch_blend_tc_bwd(const BlendArgs& a, const GradArgs& g, int variant, cudaStream_t s);
+// A zeroed tile-queue counter for one persistent launch on stream s.
+unsigned* tile_queue_slot(cudaStream_t s, cudaError_t* err);
 
 }  // namespace gs

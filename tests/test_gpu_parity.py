@@ -312,6 +312,71 @@ def test_blend_backward_matches_oracle_gradient(kind):
         assert rel < 1e-3, f"{name}: relative error {rel:.2e}"
 
 
+def _grad_rel_errors(g, ref):
+    out = {}
+    for name in ("mean2d", "conic", "opacity", "rgb"):
+        a, b = g[name].astype(np.float64), ref[name]
+        out[name] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12))
+    return out
+
+
+@pytest.mark.parametrize("variant", ["fp16_split", "bf16_split"])
+@pytest.mark.parametrize("kind", ["tiny_ragged", "tiny_dense", "c0", "c1_small"])
+def test_tc_blend_backward_matches_oracle_gradient(kind, variant):
+    """The tensor-core backward pass (exponents recomputed by the forward's
+    MMA, per-splat sums over pixels by a second MMA) against the FP64 oracle
+    gradient, with the split variants' exponent error only."""
+    sc, dev, cam, proj, bs, pn, bn = pipeline(kind)
+    bg = (0.2, 0.1, 0.05)
+    opts = gs.make_opts(variant, bg=bg)
+    fwd = gs.blend_forward(cam.width, cam.height, bs, proj, dev["opacities"], opts)
+    rng = np.random.default_rng(1)
+    dL = rng.standard_normal((3, cam.height, cam.width)).astype(np.float32)
+    g = to_np(gs.blend_backward(cam.width, cam.height, bs, proj, dev["opacities"], opts, fwd,
+                                torch.from_numpy(dL).cuda()))
+    assert gs.gs_sync_status() == gs.GS_OK
+    ref = oracle.blend_grad(cam.width, cam.height, bn["tile_ranges"].view(np.uint32), bn["ids"].view(np.uint32),
+                            pn["mean2d"].astype(np.float64), pn["conic"].astype(np.float64),
+                            sc.opacities.astype(np.float64), pn["rgb"].astype(np.float64), dL.astype(np.float64),
+                            bg=bg, n_threads=CORES)
+    rel = _grad_rel_errors(g, ref)
+    report(f"tc_bwd_rel_{variant}_{kind}", rel)
+    for name, e in rel.items():
+        assert e < 1e-3, f"{name}: relative error {e:.2e}"
+
+
+@pytest.mark.parametrize("variant", ["fp16_split", "fp16"])
+def test_tc_blend_backward_gradient_scale_is_exact(variant):
+    """dL/dimage enters the fp16 operands through a per-tile power-of-two
+    scale: multiplying it by 2^40 or 2^-40 scales every gradient by exactly
+    that factor, with no overflow or loss of precision."""
+    sc, dev, cam, proj, bs, pn, bn = pipeline("tiny_dense")
+    opts = gs.make_opts(variant, bg=(0.3, 0.2, 0.1))
+    fwd = gs.blend_forward(cam.width, cam.height, bs, proj, dev["opacities"], opts)
+    dL = torch.randn(3, cam.height, cam.width, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    base = to_np(gs.blend_backward(cam.width, cam.height, bs, proj, dev["opacities"], opts, fwd, dL))
+    assert np.abs(base["mean2d"]).max() > 0
+    for e in (40, -40):
+        got = to_np(gs.blend_backward(cam.width, cam.height, bs, proj, dev["opacities"], opts, fwd, dL * 2.0 ** e))
+        for name in ("mean2d", "conic", "opacity", "rgb"):
+            # atomics add in any order, so compare to rounding, not bits
+            np.testing.assert_allclose(got[name].astype(np.float64) * 2.0 ** -e, base[name], rtol=1e-5,
+                                       atol=1e-6 * np.abs(base[name]).max())
+
+
+def test_tc_blend_backward_origin_reference_matches_centre_reference():
+    sc, dev, cam, proj, bs, pn, bn = pipeline("tiny_dense")
+    dL = torch.randn(3, cam.height, cam.width, device="cuda", generator=torch.Generator("cuda").manual_seed(6))
+    res = []
+    for origin in (0, 1):
+        opts = gs.make_opts("fp16_split", ref_origin=origin)
+        fwd = gs.blend_forward(cam.width, cam.height, bs, proj, dev["opacities"], opts)
+        res.append(to_np(gs.blend_backward(cam.width, cam.height, bs, proj, dev["opacities"], opts, fwd, dL)))
+    for name in ("mean2d", "conic", "opacity", "rgb"):
+        a, b = res[0][name].astype(np.float64), res[1][name].astype(np.float64)
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-3, name
+
+
 def test_autograd_function_matches_backward_call():
     sc, dev, cam, proj, bs, pn, bn = pipeline("tiny_ragged")
     opts = gs.make_opts("fp32")

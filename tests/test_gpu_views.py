@@ -93,10 +93,11 @@ def test_graph_mode_bin_sort_matches_synchronising_mode_and_reports_overflow():
     assert gs.gs_sync_status() == gs.GS_OK
 
 
-def test_batched_backward_equals_sum_over_views():
+@pytest.mark.parametrize("variant", ["fp32", "fp16_split"])
+def test_batched_backward_equals_sum_over_views(variant):
     sc = _ring_scene(n=300)
     dev = gs.scene_to_device(sc)
-    opts = gs.make_opts("fp32", bg=(0.1, 0.2, 0.3))
+    opts = gs.make_opts(variant, bg=(0.1, 0.2, 0.3))
     br = gs.BatchRenderer(dev, sc.cameras, opts, capacity=1 << 17)
     rng = np.random.default_rng(3)
     br.dL.copy_(torch.from_numpy(rng.standard_normal(3 * br.pixels).astype(np.float32)))
@@ -106,7 +107,7 @@ def test_batched_backward_equals_sum_over_views():
     g_opac = torch.zeros(n, device="cuda")
     off = 0
     for v, cam in enumerate(sc.cameras):
-        proj, bs, out = _single(dev, cam, "fp32")
+        proj, bs, out = _single(dev, cam, variant)
         P = cam.width * cam.height
         dL = br.dL[3 * off:3 * (off + P)].view(3, cam.height, cam.width)
         g = gs.blend_backward(cam.width, cam.height, bs, proj, dev["opacities"], opts, out, dL)
