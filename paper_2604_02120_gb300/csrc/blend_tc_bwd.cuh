@@ -10,16 +10,18 @@
 //     reference pixel], so the backward pass recomputes the forward's alpha;
 //  2. the sums over pixels that make up each splat's gradient: every pixel
 //     thread writes two per-(splat, pixel) values, the exponent gradient
-//     dL/dpower and the blending weight w = alpha T, as fp16 hi + lo pairs
-//     into A2 (128 rows = {dpow, w} x {upper, lower half} x {hi, lo} x 16
-//     splats, K = the 128 pixels of a half, stored MN-major so that a thread
-//     writes 8 splats of its pixel with one 16-byte store), and
-//     D2 (128 x 32) = A2 . B2 where B2 holds per pixel the monomials
-//     [xb^2, yb^2, xb yb, xb, yb, 1] of Eq. 6 (exact in fp16) and the pixel's
-//     dL/dimage (hi + lo, separately for each half).  Row (dpow, h, s, j)
-//     of D2 then holds sum_p dpow m_p for splat j over half h, from which the
-//     conic, mean and opacity gradients follow by the chain rule; row
-//     (w, h, s, j) holds sum_p w dL/dC_p, the colour gradient.
+//     dL/dpower (fp16 hi + lo) and the blending weight w = alpha T (fp16),
+//     into A2 (96 rows = dpow {upper, lower half} x {hi, lo} x 16 splats and
+//     w {upper, lower} x 16 splats, K = the 128 pixels of a half, stored
+//     MN-major so that a thread writes 8 splats of its pixel with one 16-byte
+//     store), and D2 (128 x 32) = A2 . B2 where B2 holds per pixel the
+//     monomials [xb^2, yb^2, xb yb, xb, yb, 1] of Eq. 6 (exact in fp16) and
+//     the pixel's dL/dimage (hi + lo, separately for each half).  Row
+//     (dpow, h, s, j) of D2 then holds sum_p dpow m_p for splat j over half
+//     h, from which the conic, mean and opacity gradients follow by the chain
+//     rule; row (w, h, j) holds sum_p w dL/dC_p, the colour gradient.  The MMA
+//     runs with M = 128: rows 96..127 of D2 read past the 96 rows (the next
+//     8-pixel group, or the buffer's padding) and are ignored.
 //
 // Per pixel the splats are visited back to front (chunks in reverse order,
 // splats inside a chunk from last to first), starting from T_final and the
@@ -32,9 +34,12 @@
 // 2^(-E) with 2^E the largest |dL/dimage| of the tile, T by 2^12; the sums
 // are scaled back in the finishing step.
 //
-// The finishing step of a chunk (reading D2, chain rule, atomics) runs while
-// the next chunk is in flight; each epilogue warp finishes its own rows, so
-// the four warps never wait for one another.  All waits are bounded by
+// A2 and D2 are double buffered: chunk c writes A2[c % 2] while the MMA of
+// chunk c - 1 runs, and the finishing step of chunk c - 1 (reading D2, chain
+// rule, atomics) follows chunk c's stores, so the MMA's latency is hidden
+// behind a whole chunk.  At a new tile the pending chunk is finished first
+// (B2 changes).  Each epilogue warp finishes its own rows, so the four warps
+// never wait for one another.  All waits are bounded by
 // opts.timeout_ns as in the forward kernel.
 #pragma once
 
@@ -80,31 +85,33 @@ struct BwdHdr {
 template <int SS, int V>
 struct BwdLayout {
     static constexpr int CH = kBwdChunk;
-    static constexpr int A2_BYTES = 128 * 128 * 2;  // 128 rows x 128 pixels, fp16
+    static constexpr int A2_ROWS = 96;
+    static constexpr int A2_LBO = A2_ROWS / 8 * 128;            // bytes per 8-pixel group: 1536
+    static constexpr int A2_BYTES = 16 * A2_LBO + 512;           // + what the M = 128 MMA reads past row 96
     static constexpr int B2_BYTES = 32 * 128 * 2;   // 32 columns x 128 pixels, fp16
     static constexpr int A1_BYTES = 128 * Traits<V>::ROW_BYTES;
     static constexpr int B1_BYTES = 2 * CH * Traits<V>::ROW_BYTES;
     static constexpr int OFF_A2 = 0;
-    static constexpr int OFF_B2 = OFF_A2 + A2_BYTES;
+    static constexpr int OFF_B2 = OFF_A2 + 2 * A2_BYTES;
     static constexpr int OFF_A1 = OFF_B2 + B2_BYTES;
     static constexpr int OFF_B1 = OFF_A1 + A1_BYTES;
     static constexpr int OFF_REC = OFF_B1 + SS * B1_BYTES;
     static constexpr int OFF_FIN = OFF_REC + SS * CH * (int)sizeof(Rec);
     static constexpr int OFF_BAR = OFF_FIN + SS * CH * (int)sizeof(Fin);
-    // full[SS], empty[SS], tfull[2], tempty[2], a2full, m2done, drain
-    static constexpr int NBAR = 2 * SS + 2 * kTStages + 3;
+    // full[SS], empty[SS], tfull[2], tempty[2], a2full[2], m2done[2], drain
+    static constexpr int NBAR = 2 * SS + 2 * kTStages + 5;
     static constexpr int OFF_HDR = OFF_BAR + NBAR * 8;
     static constexpr int OFF_MISC = OFF_HDR + SS * (int)sizeof(BwdHdr);
     static constexpr int BYTES = OFF_MISC + 16;
-    static constexpr uint32_t D2_COL = 2 * kTStages * CH;  // 64: after the two exponent stages
+    static constexpr uint32_t D2_COL = 2 * kTStages * CH;  // 64: after the two exponent stages; 2 x 32
     static constexpr uint32_t TCOLS = 128;
-    static_assert(D2_COL + 32 <= TCOLS, "TMEM columns");
+    static_assert(D2_COL + 64 <= TCOLS, "TMEM columns");
 };
 
 // 16-byte store into A2 (MN-major: core matrix = 8 pixels x 8 rows; rows
-// contiguous, LBO = 2048 B between 8-pixel groups, SBO = 128 B between 8-row groups).
+// contiguous, SBO = 128 B between 8-row groups, LBO = 1536 B between 8-pixel groups).
 __device__ __forceinline__ void a2_store(uint8_t* A2, int pix, int mblk, const uint4& v) {
-    *reinterpret_cast<uint4*>(A2 + (pix >> 3) * 2048 + mblk * 128 + (pix & 7) * 16) = v;
+    *reinterpret_cast<uint4*>(A2 + (pix >> 3) * 1536 + mblk * 128 + (pix & 7) * 16) = v;
 }
 // One fp16 element of B2 (K-major: core matrix = 8 columns x 8 pixels).
 __device__ __forceinline__ void b2_store(uint8_t* B2, int col, int pix, __half v) {
@@ -143,9 +150,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
     auto bar_empty = [&](int s) { return smem_u32(bars + SS + s); };
     auto bar_tfull = [&](int t) { return smem_u32(bars + 2 * SS + t); };
     auto bar_tempty = [&](int t) { return smem_u32(bars + 2 * SS + kTStages + t); };
-    const uint32_t bar_a2full = smem_u32(bars + 2 * SS + 2 * kTStages);
-    const uint32_t bar_m2done = smem_u32(bars + 2 * SS + 2 * kTStages + 1);
-    const uint32_t bar_drain = smem_u32(bars + 2 * SS + 2 * kTStages + 2);
+    auto bar_a2full = [&](int b) { return smem_u32(bars + 2 * SS + 2 * kTStages + b); };
+    auto bar_m2done = [&](int b) { return smem_u32(bars + 2 * SS + 2 * kTStages + 2 + b); };
+    const uint32_t bar_drain = smem_u32(bars + 2 * SS + 2 * kTStages + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool origin = a.ref_origin != 0;
@@ -159,8 +166,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
             mbar_init(bar_tfull(t), 1);
             mbar_init(bar_tempty(t), kEpiWarps);
         }
-        mbar_init(bar_a2full, kEpiWarps);
-        mbar_init(bar_m2done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(bar_a2full(b), kEpiWarps);
+            mbar_init(bar_m2done(b), 1);
+        }
         mbar_init(bar_drain, 1);
         *sAbort = 0;
         mbar_fence_init();
@@ -182,6 +191,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
     // B2: zero, then the monomial columns 0..5 (the dL/dimage columns are per tile)
     for (int i = threadIdx.x; i < LY::B2_BYTES / 16; i += kThreads)
         reinterpret_cast<uint4*>(sB2)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = threadIdx.x; i < 2 * LY::A2_BYTES / 16; i += kThreads)
+        reinterpret_cast<uint4*>(sA2)[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
     if (threadIdx.x < 128) {
         const int pix = threadIdx.x;
@@ -219,44 +230,65 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
         uint32_t c2 = 0;  // chunks with an A2/MMA2 so far
 
         auto finish = [&]() -> bool {
-            if (!mbar_wait_bounded(bar_m2done, p_c2 & 1u, tmo, sAbort)) {
+            const int pb = (int)(p_c2 & 1u);
+            if (!mbar_wait_bounded(bar_m2done(pb), (p_c2 >> 1) & 1u, tmo, sAbort)) {
                 fail();
                 return false;
             }
             tc_fence_after();
-            uint32_t v[8];
-            const uint32_t col0 = q == 0 ? 0u : (hh == 0 ? 8u : 16u);
-            tmem_ld_32x32b_x8(tmem + ((uint32_t)(warp * 32) << 16) + LY::D2_COL + col0, v);
-            tmem_ld_wait();
-            float S[6];
+            if (warp < 3) {
+                uint32_t v[16];
+                const uint32_t d2 = tmem + ((uint32_t)(warp * 32) << 16) + LY::D2_COL + (uint32_t)(32 * pb);
+                if (warp < 2) {
+                    uint32_t v8[8];
+                    tmem_ld_32x32b_x8(d2, v8);
+                    tmem_ld_wait();
 #pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                S[k] = __uint_as_float(v[k]);
-                S[k] += __shfl_xor_sync(0xffffffffu, S[k], 16);  // hi + lo rows
-            }
-            const int j = lane & 15;
-            const Fin f = sFin[p_stage * CH + j];
-            if (lane < 16 && j < p_n && f.g != 0xffffffffu) {
-                if (q == 0) {
-                    const float xh = f.xh, yh = hh ? f.yh - 8.0f : f.yh;
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) S[k] *= p_undp;
-                    const float Sx = fmaf(xh, S[5], S[3]), Sy = fmaf(yh, S[5], S[4]);
-                    const float Sxx = fmaf(xh, fmaf(xh, S[5], 2.0f * S[3]), S[0]);
-                    const float Syy = fmaf(yh, fmaf(yh, S[5], 2.0f * S[4]), S[1]);
-                    const float Sxy = fmaf(xh, fmaf(yh, S[5], S[4]), fmaf(yh, S[3], S[2]));
-                    float* dm = reinterpret_cast<float*>(gr.dmean2d) + 2 * (size_t)f.g;
-                    atomicAdd(dm, -fmaf(f.A, Sx, f.B * Sy));
-                    atomicAdd(dm + 1, -fmaf(f.B, Sx, f.C * Sy));
-                    float* dc = gr.dconic + 3 * (size_t)f.g;
-                    atomicAdd(dc, -0.5f * Sxx);
-                    atomicAdd(dc + 1, -Sxy);
-                    atomicAdd(dc + 2, -0.5f * Syy);
-                    atomicAdd(gr.dopac + f.og, S[5] * f.inv_o);
+                    for (int k = 0; k < 8; ++k) v[k] = v8[k];
                 } else {
-                    float* dr = gr.drgb + 3 * (size_t)f.g;
+                    tmem_ld_32x32b_x16(d2 + 8u, v);  // columns 8..23: dL/dimage of both halves
+                    tmem_ld_wait();
+                }
+                float S[6];
+                if (warp < 2) {
+                    // rows (h = warp, s = lane >> 4, j = lane & 15): monomial moments, hi + lo
 #pragma unroll
-                    for (int ch = 0; ch < 3; ++ch) atomicAdd(dr + ch, (S[ch] + S[3 + ch]) * p_uncol);
+                    for (int k = 0; k < 6; ++k) S[k] = __uint_as_float(v[k]);
+                } else {
+                    // rows (h = lane >> 4, j = lane & 15): w . dL/dimage (hi + lo columns)
+                    const bool lower = (lane >> 4) != 0;
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch)
+                        S[ch] = lower ? __uint_as_float(v[8 + ch]) + __uint_as_float(v[11 + ch])
+                                      : __uint_as_float(v[ch]) + __uint_as_float(v[3 + ch]);
+                    S[3] = S[4] = S[5] = 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < 6; ++k) S[k] += __shfl_xor_sync(0xffffffffu, S[k], 16);
+                const int j = lane & 15;
+                const Fin f = sFin[p_stage * CH + j];
+                if (lane < 16 && j < p_n && f.g != 0xffffffffu) {
+                    if (warp < 2) {
+                        const float xh = f.xh, yh = warp ? f.yh - 8.0f : f.yh;
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) S[k] *= p_undp;
+                        const float Sx = fmaf(xh, S[5], S[3]), Sy = fmaf(yh, S[5], S[4]);
+                        const float Sxx = fmaf(xh, fmaf(xh, S[5], 2.0f * S[3]), S[0]);
+                        const float Syy = fmaf(yh, fmaf(yh, S[5], 2.0f * S[4]), S[1]);
+                        const float Sxy = fmaf(xh, fmaf(yh, S[5], S[4]), fmaf(yh, S[3], S[2]));
+                        float* dm = reinterpret_cast<float*>(gr.dmean2d) + 2 * (size_t)f.g;
+                        atomicAdd(dm, -fmaf(f.A, Sx, f.B * Sy));
+                        atomicAdd(dm + 1, -fmaf(f.B, Sx, f.C * Sy));
+                        float* dc = gr.dconic + 3 * (size_t)f.g;
+                        atomicAdd(dc, -0.5f * Sxx);
+                        atomicAdd(dc + 1, -Sxy);
+                        atomicAdd(dc + 2, -0.5f * Syy);
+                        atomicAdd(gr.dopac + f.og, S[5] * f.inv_o);
+                    } else {
+                        float* dr = gr.drgb + 3 * (size_t)f.g;
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) atomicAdd(dr + ch, S[ch] * p_uncol);
+                    }
                 }
             }
             tc_fence_before();
@@ -341,10 +373,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
             const Rec* rec = sRec + s * CH;
             const float base = (float)hd.base;
 
-            // back to front over the chunk, two groups of 8 splats; group 1
-            // (splats 8..15) is held in registers across the finishing step of
-            // the previous chunk, whose MMA must complete before A2 is rewritten
-            uint32_t w1[2][2][2][4];  // [q][h][hi/lo][word]
+            // back to front over the chunk in two groups of 8 splats (group 1 =
+            // splats 8..15 first), each group stored to A2[b] as it is done
+            // (the MMA that last read A2[b] finished with chunk c2 - 2)
+            const int b = (int)(c2 & 1u);
+            uint8_t* A2 = sA2 + b * LY::A2_BYTES;
             auto splat = [&](int j, float2& dp, float2& wt) {
                 const Rec rc = rec[j];
                 const float zx = __uint_as_float(pu[j]), zy = __uint_as_float(pl[j]);
@@ -377,48 +410,33 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
                 dp = __fmul2_rn(dLda, __fmul2_rn(aa, un));
             };
 #pragma unroll
-            for (int pr = 7; pr >= 4; --pr) {
-                float2 dpA, wA, dpB, wB;
-                splat(2 * pr + 1, dpA, wA);
-                splat(2 * pr, dpB, wB);
-                const int wd = pr - 4;
-                split2(dpB.x, dpA.x, w1[0][0][0][wd], w1[0][0][1][wd]);
-                split2(dpB.y, dpA.y, w1[0][1][0][wd], w1[0][1][1][wd]);
-                split2(wB.x, wA.x, w1[1][0][0][wd], w1[1][0][1][wd]);
-                split2(wB.y, wA.y, w1[1][1][0][wd], w1[1][1][1][wd]);
+            for (int grp = 1; grp >= 0; --grp) {
+                uint32_t wv[3][2][4];  // [dpow hi, dpow lo, w][h][word]
+#pragma unroll
+                for (int pr = 3; pr >= 0; --pr) {
+                    float2 dpA, wA, dpB, wB;
+                    splat(8 * grp + 2 * pr + 1, dpA, wA);
+                    splat(8 * grp + 2 * pr, dpB, wB);
+                    split2(dpB.x, dpA.x, wv[0][0][pr], wv[1][0][pr]);
+                    split2(dpB.y, dpA.y, wv[0][1][pr], wv[1][1][pr]);
+                    const __half2 hu = __floats2half2_rn(wB.x, wA.x), hl = __floats2half2_rn(wB.y, wA.y);
+                    wv[2][0][pr] = *reinterpret_cast<const uint32_t*>(&hu);
+                    wv[2][1][pr] = *reinterpret_cast<const uint32_t*>(&hl);
+                }
+                // rows: dpow (h, s, j) = 32 h + 16 s + j; w (h, j) = 64 + 16 h + j
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    a2_store(A2, r, 4 * h + grp, make_uint4(wv[0][h][0], wv[0][h][1], wv[0][h][2], wv[0][h][3]));
+                    a2_store(A2, r, 4 * h + 2 + grp, make_uint4(wv[1][h][0], wv[1][h][1], wv[1][h][2], wv[1][h][3]));
+                    a2_store(A2, r, 8 + 2 * h + grp, make_uint4(wv[2][h][0], wv[2][h][1], wv[2][h][2], wv[2][h][3]));
+                }
             }
-            if (p_stage >= 0 && !finish()) break;
-#pragma unroll
-            for (int qq = 0; qq < 2; ++qq)
-#pragma unroll
-                for (int h = 0; h < 2; ++h)
-#pragma unroll
-                    for (int sp = 0; sp < 2; ++sp)
-                        a2_store(sA2, r, qq * 8 + h * 4 + sp * 2 + 1,
-                                 make_uint4(w1[qq][h][sp][0], w1[qq][h][sp][1], w1[qq][h][sp][2], w1[qq][h][sp][3]));
-            uint32_t w0[2][2][2][4];
-#pragma unroll
-            for (int pr = 3; pr >= 0; --pr) {
-                float2 dpA, wA, dpB, wB;
-                splat(2 * pr + 1, dpA, wA);
-                splat(2 * pr, dpB, wB);
-                split2(dpB.x, dpA.x, w0[0][0][0][pr], w0[0][0][1][pr]);
-                split2(dpB.y, dpA.y, w0[0][1][0][pr], w0[0][1][1][pr]);
-                split2(wB.x, wA.x, w0[1][0][0][pr], w0[1][0][1][pr]);
-                split2(wB.y, wA.y, w0[1][1][0][pr], w0[1][1][1][pr]);
-            }
-#pragma unroll
-            for (int qq = 0; qq < 2; ++qq)
-#pragma unroll
-                for (int h = 0; h < 2; ++h)
-#pragma unroll
-                    for (int sp = 0; sp < 2; ++sp)
-                        a2_store(sA2, r, qq * 8 + h * 4 + sp * 2,
-                                 make_uint4(w0[qq][h][sp][0], w0[qq][h][sp][1], w0[qq][h][sp][2], w0[qq][h][sp][3]));
             fence_proxy_async_smem();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(bar_a2full);
+            if (lane == 0) mbar_arrive(bar_a2full(b));
+            // the previous chunk's sums (its MMA has had this whole chunk to finish)
+            if (p_stage >= 0 && !finish()) break;
             p_stage = s;
             p_n = n;
             p_c2 = c2++;
@@ -550,7 +568,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
         }
     } else if (lane == 0) {
         // ------------------------------------------------------ MMA issue --
-        const uint32_t aA1 = smem_u32(sA1), aA2 = smem_u32(sA2), aB2 = smem_u32(sB2);
+        const uint32_t aA1 = smem_u32(sA1), aB2 = smem_u32(sB2);
         bool have_prev = false;
         uint32_t prev_c2 = 0, c2 = 0;
         for (int k = 0;; ++k) {
@@ -579,18 +597,20 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
             }
             // the previous chunk's sums, once its A2 is written
             if (have_prev) {
-                if (!mbar_wait_bounded(bar_a2full, prev_c2 & 1u, tmo, sAbort)) {
+                const int pb = (int)(prev_c2 & 1u);
+                if (!mbar_wait_bounded(bar_a2full(pb), (prev_c2 >> 1) & 1u, tmo, sAbort)) {
                     fail();
                     break;
                 }
                 tc_fence_after();
+                const uint32_t aA2 = smem_u32(sA2 + pb * LY::A2_BYTES);
 #pragma unroll
                 for (int ks = 0; ks < 8; ++ks) {
-                    const uint64_t ad = smem_desc(aA2 + (uint32_t)(ks * 4096), 2048, 128);
+                    const uint64_t ad = smem_desc(aA2 + (uint32_t)(ks * 2 * LY::A2_LBO), LY::A2_LBO, 128);
                     const uint64_t bd = smem_desc(aB2 + (uint32_t)(ks * 256), 128, 2048);
-                    tc_mma_f16(tmem + LY::D2_COL, ad, bd, IDESC2, ks > 0 ? 1u : 0u);
+                    tc_mma_f16(tmem + LY::D2_COL + (uint32_t)(32 * pb), ad, bd, IDESC2, ks > 0 ? 1u : 0u);
                 }
-                tc_commit(bar_m2done);
+                tc_commit(bar_m2done(pb));
                 have_prev = false;
             }
             if (n > 0) {
@@ -618,6 +638,10 @@ cudaError_t launch_bwd_inst(const BlendArgs& a, const GradArgs& g, cudaStream_t 
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;
+        // all of the SM's unified L1/shared storage as shared memory, so that
+        // the residency computed below is what the hardware grants
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
+            return e;
         int dev = 0, smem_sm = 0;
         cudaFuncAttributes fa{};
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
