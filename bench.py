@@ -40,9 +40,9 @@ MUFU_PER_CLK_SM = 16  # ex2/rcp results per clock per SM (CUDA programming guide
 # DRAM traffic per launch from ncu captures, keyed by kernel and the SHA-256 of
 # the kernel's source when it was measured (stale entries are not reported).
 KNOWN_TRAFFIC = {
-    # profiles/k_blend_fp32_bwd_1280x720_200k.md, profiles/k_blend_tc_fp16split_1280x720_200k.md
-    "k_blend_fp32_bwd": {"bytes": 32277760, "src": "bad5c4ccbc77e60c"},
-    "k_blend_tc<fp16_split>": {"bytes": 9733376, "src": "02347b0e95328919"},
+    # profiles/k_blend_tc_fp16split_1280x720_200k.md, profiles/k_blend_tc_bwd_fp16split_1280x720_200k.md
+    "k_blend_tc<fp16_split>": {"bytes": 9733376, "src": "9c55dd86e5be5f23"},
+    "k_blend_tc_bwd<fp16_split>": {"bytes": 31145984, "src": "b2fa1e92864e8648"},
 }
 
 
@@ -273,17 +273,21 @@ def run_ours(args):
     # ---- end to end through the public API with host buffers
     e2e = run_e2e(args, gs, torch, sc, cam, opts, capacity, dL, flush, evals_step, ws_n, dist)
 
-    # ---- roofline of the dominant blend kernel (MUFU: one exp2 per evaluated pair)
+    # ---- roofline of the dominant blend kernel (MUFU-bound: the forward pass
+    # takes one exp2 per evaluated pair, the backward pass an exp2 and a reciprocal)
     peaks, peak_kind = read_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     props = torch.cuda.get_device_properties(local)
     sms = getattr(props, "multi_processor_count", SM_COUNT_NOMINAL)
     mufu_peak = MUFU_PER_CLK_SM * sms * sm_max * 1e6 / 1e9  # G ex2 / s
     f_ms, b_ms = statistics.mean(fwd_ms), statistics.mean(bwd_ms)
+    tc = args.variant != "fp32"
     if f_ms >= b_ms:
-        kern, t_ms, per_pair, src = f"k_blend_tc<{args.variant}>", f_ms, 1, ("blend_tc.cuh",)
+        kern, t_ms, per_pair = (f"k_blend_tc<{args.variant}>" if tc else "k_blend_fp32_fwd"), f_ms, 1
+        src = ("blend_tc.cuh",) if tc else ("blend_fp32.cu",)
     else:
-        kern, t_ms, per_pair, src = "k_blend_fp32_bwd", b_ms, 2, ("blend_fp32.cu",)
+        kern, t_ms, per_pair = (f"k_blend_tc_bwd<{args.variant}>" if tc else "k_blend_fp32_bwd"), b_ms, 2
+        src = ("blend_tc_bwd.cuh", "blend_tc.cuh") if tc else ("blend_fp32.cu",)
     achieved = evals_fwd / (t_ms / 1e3) / 1e9
     peak = mufu_peak / per_pair
     tr = KNOWN_TRAFFIC.get(kern)
