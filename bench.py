@@ -33,16 +33,24 @@ if ROOT not in sys.path:
 
 METRIC = "blend ms/frame & Gaussian-pixel evals/s (fwd, fwd+bwd) TC vs FP32 CUDA-core"
 UNIT = "Gaussian-pixel evals/s"
-WORKLOAD = "1280x720, 200k Gaussians, SH degree 3, seed 0 (synthetic stand-in for the paper's trained scenes)"
+WORKLOADS = {
+    0: "256x256, 10k Gaussians, SH degree 0, seed 0",
+    1: "1280x720, 200k Gaussians, SH degree 3, seed 0",
+    2: "1920x1080, 1M Gaussians in 64 anisotropic clusters, SH degree 0, seed 0",
+    3: "ring camera 0 of 16 (resolution drawn from 640x480..1920x1080), 1.5M clustered Gaussians, seed 0",
+    4: "3840x2160, 3M Gaussians, heavy-tailed scales, Beta(0.5, 0.5) opacity, SH degree 3, seed 0",
+}
+WORKLOAD_NOTE = " (synthetic stand-in for the paper's trained scenes)"
 SM_COUNT_NOMINAL = 152
 MUFU_PER_CLK_SM = 16  # ex2/rcp results per clock per SM (CUDA programming guide throughput table)
 
-# DRAM traffic per launch from ncu captures, keyed by kernel and the SHA-256 of
-# the kernel's source when it was measured (stale entries are not reported).
+# DRAM traffic per launch from ncu captures, keyed by kernel, with the SHA-256 of
+# the kernel's source when it was measured and the workload it was measured on
+# (entries for another source or workload are not reported).
 KNOWN_TRAFFIC = {
     # profiles/k_blend_tc_fp16split_1280x720_200k.md, profiles/k_blend_tc_bwd_fp16split_1280x720_200k.md
-    "k_blend_tc<fp16_split>": {"bytes": 9733376, "src": "9c55dd86e5be5f23"},
-    "k_blend_tc_bwd<fp16_split>": {"bytes": 31145984, "src": "b2fa1e92864e8648"},
+    "k_blend_tc<fp16_split>": {"bytes": 9733376, "src": "9c55dd86e5be5f23", "config": 1},
+    "k_blend_tc_bwd<fp16_split>": {"bytes": 31145984, "src": "b2fa1e92864e8648", "config": 1},
 }
 
 
@@ -291,7 +299,7 @@ def run_ours(args):
     achieved = evals_fwd / (t_ms / 1e3) / 1e9
     peak = mufu_peak / per_pair
     tr = KNOWN_TRAFFIC.get(kern)
-    traffic = tr["bytes"] if tr and tr.get("src") == source_digest(*src) else None
+    traffic = tr["bytes"] if tr and tr["src"] == source_digest(*src) and tr["config"] == args.config else None
     roofline = {"bound": "alu", "kernel": kern, "achieved": round(achieved, 2), "peak": round(peak, 1),
                 "unit": "G evals/s (MUFU ex2-bound)", "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": f"{MUFU_PER_CLK_SM} MUFU ops/clk/SM x {sms} SMs x {sm_max:.0f} MHz "
@@ -302,7 +310,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_n, "steps": K, "warmup": args.warmup,
         "ms_per_step": dev_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "blend_variant": args.variant,
+        "config": {"workload": WORKLOADS[args.config] + WORKLOAD_NOTE, "blend_variant": args.variant,
                    "step": "project + bin_sort + blend_forward + blend_backward",
                    "evals_per_step": evals_step, "instances": n_inst, "pixels": W * H,
                    "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replica x{ws_n}",
@@ -461,7 +469,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_total * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "step": "FP64 oracle blend forward + gradient on a tile sample"},
+            "config": {"workload": WORKLOADS[args.config] + WORKLOAD_NOTE,
+                       "step": "FP64 oracle blend forward + gradient on a tile sample"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

@@ -146,7 +146,10 @@ def _sh(rng, n, degree, dc_std, rest_std):
 
 
 def _f32(a):
-    return np.ascontiguousarray(a, dtype=np.float32)
+    # heavy-tailed log-scales can exceed the float32 range; those scales become
+    # inf (the projection culls such Gaussians)
+    with np.errstate(over="ignore"):
+        return np.ascontiguousarray(a, dtype=np.float32)
 
 
 def _uniform_gaussians(rng, n, degree):
