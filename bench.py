@@ -41,8 +41,6 @@ WORKLOADS = {
     4: "3840x2160, 3M Gaussians, heavy-tailed scales, Beta(0.5, 0.5) opacity, SH degree 3, seed 0",
 }
 WORKLOAD_NOTE = " (synthetic stand-in for the paper's trained scenes)"
-SM_COUNT_NOMINAL = 152
-MUFU_PER_CLK_SM = 16  # ex2/rcp results per clock per SM (CUDA programming guide throughput table)
 
 # DRAM traffic per launch from ncu captures, keyed by kernel, with the SHA-256 of
 # the kernel's source when it was measured and the workload it was measured on
@@ -73,14 +71,6 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
-
-
-def read_peaks():
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return json.load(f), "measured"
-    except OSError:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
 class ClockSampler:
@@ -283,11 +273,9 @@ def run_ours(args):
 
     # ---- roofline of the dominant blend kernel (MUFU-bound: the forward pass
     # takes one exp2 per evaluated pair, the backward pass an exp2 and a reciprocal)
-    peaks, peak_kind = read_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    props = torch.cuda.get_device_properties(local)
-    sms = getattr(props, "multi_processor_count", SM_COUNT_NOMINAL)
-    mufu_peak = MUFU_PER_CLK_SM * sms * sm_max * 1e6 / 1e9  # G ex2 / s
+    # MUFU rates measured on this GPU by the library's own microbenchmark
+    mp = gs.gs_measure_peaks()
+    ex2_g, rcp_g = mp["ex2_per_s"] / 1e9, mp["rcp_per_s"] / 1e9
     f_ms, b_ms = statistics.mean(fwd_ms), statistics.mean(bwd_ms)
     tc = args.variant != "fp32"
     if f_ms >= b_ms:
@@ -297,13 +285,15 @@ def run_ours(args):
         kern, t_ms, per_pair = (f"k_blend_tc_bwd<{args.variant}>" if tc else "k_blend_fp32_bwd"), b_ms, 2
         src = ("blend_tc_bwd.cuh", "blend_tc.cuh") if tc else ("blend_fp32.cu",)
     achieved = evals_fwd / (t_ms / 1e3) / 1e9
-    peak = mufu_peak / per_pair
+    # pairs/s if MUFU were the only limit: an ex2 per pair, plus a reciprocal in the backward pass
+    peak = ex2_g if per_pair == 1 else 1.0 / (1.0 / ex2_g + 1.0 / rcp_g)
     tr = KNOWN_TRAFFIC.get(kern)
     traffic = tr["bytes"] if tr and tr["src"] == source_digest(*src) and tr["config"] == args.config else None
     roofline = {"bound": "alu", "kernel": kern, "achieved": round(achieved, 2), "peak": round(peak, 1),
-                "unit": "G evals/s (MUFU ex2-bound)", "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_source": f"{MUFU_PER_CLK_SM} MUFU ops/clk/SM x {sms} SMs x {sm_max:.0f} MHz "
-                               f"(max SM clock, {peak_kind}) / {per_pair} MUFU op(s) per pair",
+                "unit": "G evals/s (MUFU-bound)", "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": f"gs_measure_peaks on this GPU: {ex2_g:.0f} G ex2/s, {rcp_g:.0f} G rcp/s at "
+                               f"{mp['sm_mhz']:.0f} MHz ({mp['sms']} SMs); "
+                               + ("1 ex2 per pair" if per_pair == 1 else "1 ex2 + 1 rcp per pair"),
                 "launch_ms": round(t_ms, 5)}
 
     line = {

@@ -309,6 +309,24 @@ gs_status gs_sync_status(gs_stream stream);
  * which gs_sync_status() then returns. */
 gs_status gs_selftest_bounded_wait(int64_t timeout_ns, gs_stream stream);
 
+/* Measured peaks of the units that bound the blend kernels (the paper has no
+ * counterpart; it is how rooflines here get their denominators).  Rates are
+ * whole-GPU operations per second at the clock the GPU ran at meanwhile. */
+typedef struct {
+    double ex2_per_s;  /* MUFU ex2.approx.f32 results per second */
+    double rcp_per_s;  /* MUFU rcp.approx.f32 results per second */
+    double fma_per_s;  /* FP32 fused multiply-adds per second (2 FLOPs each) */
+    double sm_mhz;     /* mean SM clock during the three measurements (clock64 / globaltimer) */
+    int32_t sms;       /* streaming multiprocessors */
+} gs_peaks;
+
+/* Run the microbenchmarks on the current device: each fills every thread slot
+ * of every SM with 8 independent dependent chains of one operation and takes
+ * the best of 3 timed launches (about 20 ms in all).  `out` is a HOST pointer.
+ * Synchronises `stream`; uses a small scratch array compiled into the library
+ * (calls that overlap on the GPU race on it, harmlessly for the timing). */
+gs_status gs_measure_peaks(gs_peaks* out, gs_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,8 +29,13 @@ ABI_FUNCTIONS = (
     "gs_bin_sort", "gs_blend_forward", "gs_blend_backward", "gs_tile_power", "gs_sync_status",
     "gs_selftest_bounded_wait", "gs_launch_count", "gs_bin_sort_noalloc", "gs_bin_sort_noalloc_max_bytes",
     "gs_project_views", "gs_bin_sort_views", "gs_blend_forward_views", "gs_blend_backward_views",
-    "gs_blend_autotune",
+    "gs_blend_autotune", "gs_measure_peaks",
 )
+
+
+class gs_peaks(ctypes.Structure):
+    _fields_ = [("ex2_per_s", ctypes.c_double), ("rcp_per_s", ctypes.c_double), ("fma_per_s", ctypes.c_double),
+                ("sm_mhz", ctypes.c_double), ("sms", ctypes.c_int32)]
 
 
 class GsError(RuntimeError):
@@ -89,6 +94,7 @@ def load(path: str = LIB_PATH):
                                       vp, vp, vp, i32, ctypes.POINTER(ctypes.c_float), vp]
     lib.gs_sync_status.argtypes = [vp]
     lib.gs_selftest_bounded_wait.argtypes = [i64, vp]
+    lib.gs_measure_peaks.argtypes = [ctypes.POINTER(gs_peaks), vp]
     for name in ABI_FUNCTIONS:
         if name not in ("gs_version", "gs_status_string", "gs_last_error", "gs_launch_count",
                         "gs_bin_sort_noalloc_max_bytes"):
@@ -278,6 +284,15 @@ def gs_sync_status(stream=None) -> int:
 
 def gs_selftest_bounded_wait(timeout_ns, stream=None):
     _check(load().gs_selftest_bounded_wait(int(timeout_ns), _stream(stream)), "gs_selftest_bounded_wait")
+
+
+def gs_measure_peaks(stream=None) -> dict:
+    """Measured MUFU ex2 / rcp and FP32 FMA rates of the current GPU (whole
+    GPU, per second) and the SM clock during the measurement."""
+    p = gs_peaks()
+    _check(load().gs_measure_peaks(ctypes.byref(p), _stream(stream)), "gs_measure_peaks")
+    return {"ex2_per_s": p.ex2_per_s, "rcp_per_s": p.rcp_per_s, "fma_per_s": p.fma_per_s, "sm_mhz": p.sm_mhz,
+            "sms": p.sms}
 
 
 # ------------------------------------------------------------ tensor helpers

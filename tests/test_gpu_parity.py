@@ -65,6 +65,20 @@ def test_bounded_wait_reports_timeout():
     assert gs.gs_sync_status() == gs.GS_OK  # cleared by the read
 
 
+def test_measured_peaks_are_plausible():
+    """The MUFU and FMA microbenchmarks: rates per SM per clock near the
+    hardware's unit counts (16 MUFU results per SM per clock, 32 for ex2 on
+    parts with the doubled exponential rate; 128 FP32 FMAs), and an SM clock
+    between 0.5 and 3 GHz."""
+    p = gs.gs_measure_peaks()
+    report("measured_peaks", p)
+    assert 500 < p["sm_mhz"] < 3000
+    per_clk = lambda rate: rate / (p["sms"] * p["sm_mhz"] * 1e6)  # noqa: E731
+    assert 8 <= per_clk(p["ex2_per_s"]) <= 34
+    assert 8 <= per_clk(p["rcp_per_s"]) <= 17
+    assert 64 <= per_clk(p["fma_per_s"]) <= 130
+
+
 # -------------------------------------------------------------- projection --
 
 @pytest.mark.parametrize("kind", ["c0", "tiny_ragged", "tiny_dense", "c1"])
