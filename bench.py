@@ -239,7 +239,7 @@ def run_ours(args):
     # ---- blend-only ms/frame per variant (forward), tensor core vs FP32 CUDA core
     blend = {}
     if not args.quick:
-        for name in ["fp32", "fp16", "bf16", "fp16_split", "bf16_split"]:
+        for name in ["fp32", "fp16", "bf16", "fp16_split", "bf16_split", "fp8_split"]:
             o = gs.make_opts(name)
             for _ in range(3):
                 gs.blend_forward(W, H, bs, proj, dev["opacities"], o)

@@ -62,13 +62,16 @@ typedef struct gs_camera {
 /* Blend arithmetic.  FP32 evaluates Eq. 3 per pixel on CUDA cores; the TC
  * variants evaluate Eq. 6 for a whole tile as a tcgen05 matrix product with
  * the given operand type and FP32 accumulation.  _SPLIT variants store v_g as
- * an unevaluated sum of 2 (fp16) or 3 (bf16) operand-type terms. */
+ * an unevaluated sum of 2 (fp16) or 3 (bf16) operand-type terms.  FP8_SPLIT
+ * (a precision trial) uses e4m3 operands: every v_g row scaled by a power of
+ * two and split into 5 terms, the pixel monomials into 2 exact terms. */
 typedef enum gs_variant {
     GS_BLEND_FP32 = 0,
     GS_BLEND_TC_FP16 = 1,
     GS_BLEND_TC_BF16 = 2,
     GS_BLEND_TC_FP16_SPLIT = 3,
-    GS_BLEND_TC_BF16_SPLIT = 4
+    GS_BLEND_TC_BF16_SPLIT = 4,
+    GS_BLEND_TC_FP8_SPLIT = 5
 } gs_variant;
 
 /* Options of the blend calls.  All-zero is valid: FP32 variant, defaults. */

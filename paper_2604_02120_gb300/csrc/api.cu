@@ -122,7 +122,7 @@ bool make_args(BlendArgs& a, int32_t n_views, const int32_t* widths, const int32
     return true;
 }
 
-bool is_tc(int v) { return v >= GS_BLEND_TC_FP16 && v <= GS_BLEND_TC_BF16_SPLIT; }
+bool is_tc(int v) { return v >= GS_BLEND_TC_FP16 && v <= GS_BLEND_TC_FP8_SPLIT; }
 
 }  // namespace
 

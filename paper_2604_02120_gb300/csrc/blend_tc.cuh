@@ -40,6 +40,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "internal.h"
 
@@ -59,16 +60,39 @@ constexpr float kDeadPower = -200.0f;
 constexpr float kCullScale = 68719476736.0f;    // 2^36
 constexpr float kStopScale = 1099511627776.0f;  // 2^40
 
+// Operand encoding of a variant.  K elements of a row: TERMS operand-type terms
+// of v_g times PTERMS terms of the monomials, 6 each (every product of a v_g
+// term with a monomial term gets its own K slot), zero-padded.  FP8: e4m3
+// operands (tcgen05 kind::f8f6f4), each v_g row scaled by a power of two so
+// that its largest coefficient lies in [128, 256), the monomials split into 2
+// exact terms.
 template <int V>
 struct Traits {
-    static constexpr int K = (V == GS_BLEND_TC_BF16_SPLIT) ? 32 : 16;
-    static constexpr int TERMS = (V == GS_BLEND_TC_FP16_SPLIT) ? 2 : (V == GS_BLEND_TC_BF16_SPLIT ? 3 : 1);
-    static constexpr uint32_t FMT = (V == GS_BLEND_TC_BF16 || V == GS_BLEND_TC_BF16_SPLIT) ? 1u : 0u;
+    static constexpr bool FP8 = (V == GS_BLEND_TC_FP8_SPLIT);
+    static constexpr int TERMS = FP8 ? 5 : (V == GS_BLEND_TC_FP16_SPLIT) ? 2 : (V == GS_BLEND_TC_BF16_SPLIT ? 3 : 1);
+    static constexpr int PTERMS = FP8 ? 2 : 1;
+    static constexpr int K = FP8 ? 64 : (V == GS_BLEND_TC_BF16_SPLIT) ? 32 : 16;
+    static constexpr uint32_t FMT = (V == GS_BLEND_TC_BF16 || V == GS_BLEND_TC_BF16_SPLIT) ? 1u : 0u;  // e4m3: 0
     static constexpr bool HALF = (FMT == 0);
-    static constexpr int KSTEPS = K / 16;
-    static constexpr int ROW_BYTES = K * 2;
-    static constexpr int SBO = (K / 8) * 128;  // bytes between 8-row core-matrix groups
+    static constexpr int ROW_BYTES = FP8 ? K : 2 * K;
+    static constexpr int KSTEPS = ROW_BYTES / 32;               // one MMA consumes 32 bytes of every row
+    static constexpr int SBO = (ROW_BYTES / 16) * 128;          // bytes between 8-row core-matrix groups
+    static_assert(6 * TERMS * PTERMS <= K, "operand terms exceed K");
 };
+
+// FP8 term t of v_g is stored multiplied by 2^kFp8Shift[t] and the monomial
+// slots it meets by 2^-kFp8Shift[t] (products unchanged): the small terms move
+// up into e4m3's normal range, the monomials (>= 1/4) stay normal.
+__device__ __forceinline__ float fp8_term_shift(int t) { return t >= 2 ? 16.0f : 1.0f; }
+
+// e4m3 encoding (round to nearest, saturating) and its value
+__device__ __forceinline__ uint8_t to_e4m3(float x) {
+    return (uint8_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+}
+__device__ __forceinline__ float from_e4m3(uint8_t b) {
+    const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)b, __NV_E4M3);
+    return __half2float(__half(h));
+}
 
 template <bool HALF>
 __device__ __forceinline__ uint16_t to_op(float x) {
@@ -88,13 +112,29 @@ struct alignas(16) Rec {
     float4 bc;  // b, b, cap, cap
 };
 
+// tcgen05.mma of the variant's operand kind (f16/bf16 or e4m3)
+template <int V>
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    if constexpr (Traits<V>::FP8)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    else
+        tc_mma_f16(d_tmem, adesc, bdesc, idesc, accumulate);
+}
+
 template <int SS, int CH, int V>
 struct Layout {
     static constexpr int A_BYTES = 128 * Traits<V>::ROW_BYTES;
     static constexpr int B_BYTES = 2 * CH * Traits<V>::ROW_BYTES;
     static constexpr int OFF_B = A_BYTES;
     static constexpr int OFF_REC = OFF_B + SS * B_BYTES;
-    static constexpr int OFF_BAR = OFF_REC + SS * CH * (int)sizeof(Rec);
+    static constexpr int OFF_SCL = OFF_REC + SS * CH * (int)sizeof(Rec);  // FP8: row scales (float2 per splat)
+    static constexpr int OFF_BAR = OFF_SCL + SS * CH * 8;
     static constexpr int NBAR = 2 * SS + 2 * kTStages + 1;  // + one drain barrier
     static constexpr int OFF_HDR = OFF_BAR + NBAR * 8;
     static constexpr int OFF_MISC = OFF_HDR + SS * 32;
@@ -173,29 +213,120 @@ __device__ __forceinline__ void coeff_row(float A, float B, float C, float l2o, 
 }
 
 // Write row r of a B stage: v split into TERMS operand-type terms, each in its
-// own 6-wide K slot, zero padding up to K.
+// own K slots (once per monomial term), zero padding up to K.  Returns the
+// factor that maps the MMA result back to v . v_p (1 unless FP8, whose rows
+// are scaled by a power of two first).
 template <int V>
-__device__ __forceinline__ void store_coeff_row(uint8_t* mB, int r, const float (&v)[6]) {
+__device__ __forceinline__ float store_coeff_row(uint8_t* mB, int r, const float (&v)[6]) {
     using TR = Traits<V>;
-    uint16_t terms[3][6];
+    if constexpr (TR::FP8) {
+        float big = 0.f;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        float rem = v[i];
+        for (int i = 0; i < 6; ++i) big = fmaxf(big, fabsf(v[i]));
+        // 2^E <= big < 2^(E+1); scale 2^(7-E) puts the largest coefficient in [128, 256)
+        const int E = big > 0.f ? ((__float_as_int(big) >> 23) & 0xff) - 127 : 0;
+        const int sh = max(-100, min(100, 7 - E));
+        const float scale = __int_as_float((127 + sh) << 23), inv = __int_as_float((127 - sh) << 23);
+        uint8_t terms[TR::TERMS][6];
 #pragma unroll
-        for (int t = 0; t < TR::TERMS; ++t) {
-            terms[t][i] = to_op<TR::HALF>(rem);
-            rem -= from_op<TR::HALF>(terms[t][i]);
+        for (int i = 0; i < 6; ++i) {
+            float rem = v[i] * scale;
+#pragma unroll
+            for (int t = 0; t < TR::TERMS; ++t) {
+                const float sh = fp8_term_shift(t);
+                terms[t][i] = to_e4m3(rem * sh);
+                rem -= from_e4m3(terms[t][i]) / sh;
+            }
         }
+        // slot k = (t * PTERMS + s) * 6 + i holds term t of v_i (for every monomial term s)
+#pragma unroll
+        for (int kc = 0; kc < TR::ROW_BYTES / 16; ++kc) {
+            uint32_t w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t word = 0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int k = kc * 16 + q * 4 + b;
+                    const uint32_t e = (k < 6 * TR::TERMS * TR::PTERMS)
+                                           ? terms[k / (6 * TR::PTERMS)][k % 6] : 0u;
+                    word |= e << (8 * b);
+                }
+                w[q] = word;
+            }
+            *reinterpret_cast<uint4*>(mB + (r >> 3) * TR::SBO + kc * 128 + (r & 7) * 16) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        return inv;
+    } else {
+        uint16_t terms[3][6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            float rem = v[i];
+#pragma unroll
+            for (int t = 0; t < TR::TERMS; ++t) {
+                terms[t][i] = to_op<TR::HALF>(rem);
+                rem -= from_op<TR::HALF>(terms[t][i]);
+            }
+        }
+#pragma unroll
+        for (int kc = 0; kc < TR::K / 8; ++kc) {
+            uint16_t e[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int kk = kc * 8 + i;
+                e[i] = (kk < 6 * TR::TERMS) ? terms[kk / 6][kk % 6] : (uint16_t)0;
+            }
+            store_row_chunk<V>(mB, r, kc, e);
+        }
+        return 1.0f;
     }
+}
+
+// Row `row` of M_p, the pixel-monomial operand: the 6 monomials of the pixel
+// (offsets xb, yb from its half's reference), in the slot order of
+// store_coeff_row (for FP8 each monomial as 2 exact e4m3 terms).
+template <int V>
+__device__ __forceinline__ void store_mp_row(uint8_t* sA, int row, float xb, float yb) {
+    using TR = Traits<V>;
+    const float vp[6] = {xb * xb, yb * yb, xb * yb, xb, yb, 1.0f};
+    if constexpr (TR::FP8) {
+        float pv[2][6];  // the 2 exact e4m3 terms of each monomial
 #pragma unroll
-    for (int kc = 0; kc < TR::K / 8; ++kc) {
-        uint16_t e[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int kk = kc * 8 + i;
-            e[i] = (kk < 6 * TR::TERMS) ? terms[kk / 6][kk % 6] : (uint16_t)0;
+        for (int i = 0; i < 6; ++i) {
+            pv[0][i] = from_e4m3(to_e4m3(vp[i]));
+            pv[1][i] = vp[i] - pv[0][i];
         }
-        store_row_chunk<V>(mB, r, kc, e);
+#pragma unroll
+        for (int kc = 0; kc < TR::ROW_BYTES / 16; ++kc) {
+            uint32_t w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t word = 0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int k = kc * 16 + q * 4 + b;
+                    const uint32_t e = (k < 6 * TR::TERMS * TR::PTERMS)
+                                           ? to_e4m3(pv[(k / 6) % TR::PTERMS][k % 6] / fp8_term_shift(k / (6 * TR::PTERMS)))
+                                           : 0u;
+                    word |= e << (8 * b);
+                }
+                w[q] = word;
+            }
+            *reinterpret_cast<uint4*>(sA + (row >> 3) * TR::SBO + kc * 128 + (row & 7) * 16) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    } else {
+#pragma unroll
+        for (int kc = 0; kc < TR::K / 8; ++kc) {
+            uint16_t e[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int k = kc * 8 + i;
+                e[i] = (k < 6 * TR::TERMS) ? to_op<TR::HALF>(vp[k % 6]) : (uint16_t)0;
+            }
+            store_row_chunk<V>(sA, row, kc, e);
+        }
     }
 }
 
@@ -235,6 +366,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
     uint8_t* sA = smem;
     uint8_t* sB = smem + LY::OFF_B;
     Rec* sRec = reinterpret_cast<Rec*>(smem + LY::OFF_REC);
+    float2* sScl = reinterpret_cast<float2*>(smem + LY::OFF_SCL);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + LY::OFF_BAR);
     StageHdr* sHdr = reinterpret_cast<StageHdr*>(smem + LY::OFF_HDR);
     uint32_t* sTmem = reinterpret_cast<uint32_t*>(smem + LY::OFF_MISC);
@@ -264,18 +396,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
         mbar_fence_init();
     }
     // pixel matrix M_p of a 16 x 8 half-tile (A operand)
-    for (int idx = threadIdx.x; idx < 128 * (K / 8); idx += kThreads) {
-        const int row = idx / (K / 8), kc = idx % (K / 8);
+    for (int row = threadIdx.x; row < 128; row += kThreads) {
         const float xb = origin ? -(float)(row & 15) : 7.5f - (float)(row & 15);
         const float yb = origin ? -(float)(row >> 4) : 3.5f - (float)(row >> 4);
-        const float vp[6] = {xb * xb, yb * yb, xb * yb, xb, yb, 1.0f};
-        uint16_t e[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int k = kc * 8 + i;
-            e[i] = (k < 6 * TR::TERMS) ? to_op<TR::HALF>(vp[k % 6]) : (uint16_t)0;
-        }
-        store_row_chunk<V>(sA, row, kc, e);
+        store_mp_row<V>(sA, row, xb, yb);
     }
     fence_proxy_async_smem();
     if (warp == 5) {
@@ -352,6 +476,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
                     tmem_ld_32x32b_x16(tb + (uint32_t)c0, vu);
                     tmem_ld_32x32b_x16(tb + (uint32_t)(CH + c0), vl);
                     tmem_ld_wait();
+                    if constexpr (TR::FP8) {  // undo the per-row scaling of the e4m3 operands
+                        const float2* scl = sScl + s * CH;
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) {
+                            const float2 z = __fmul2_rn(make_float2(__uint_as_float(vu[c]), __uint_as_float(vl[c])),
+                                                        scl[c0 + c]);
+                            vu[c] = __float_as_uint(z.x);
+                            vl[c] = __float_as_uint(z.y);
+                        }
+                    }
                     if constexpr (DUMP) {
 #pragma unroll
                         for (int c = 0; c < 16; ++c) {
@@ -480,9 +614,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
                             rc.rg = make_float4(0.f, 0.f, 0.f, 0.f);
                             rc.bc = make_float4(0.f, 0.f, 0.f, 0.f);
                         }
-                        store_coeff_row<V>(mB, j, vu);
-                        store_coeff_row<V>(mB, CH + j, vl);
+                        const float su = store_coeff_row<V>(mB, j, vu);
+                        const float sl = store_coeff_row<V>(mB, CH + j, vl);
                         sRec[s * CH + j] = rc;
+                        if constexpr (TR::FP8) sScl[s * CH + j] = make_float2(su, sl);
                     }
                 }
                 if (lane == 0) sHdr[s] = StageHdr{tile, end ? -2 : seq, base, n, q, {0, 0, 0}};
@@ -524,7 +659,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
             for (int ks = 0; ks < TR::KSTEPS; ++ks) {
                 const uint64_t ad = smem_desc(aA + (uint32_t)(ks * 256), 128, SBO);
                 const uint64_t bd = smem_desc(aB + (uint32_t)(ks * 256), 128, SBO);
-                tc_mma_f16(tmem + (uint32_t)(t * 2 * CH), ad, bd, IDESC, ks > 0 ? 1u : 0u);
+                tc_mma<V>(tmem + (uint32_t)(t * 2 * CH), ad, bd, IDESC, ks > 0 ? 1u : 0u);
             }
             tc_commit(bar_tfull(t));
             tc_commit(bar_empty(s));
@@ -588,6 +723,8 @@ template <>
 cudaError_t launch_variant<3>(const BlendArgs&, int, int, bool, int, cudaStream_t);
 template <>
 cudaError_t launch_variant<4>(const BlendArgs&, int, int, bool, int, cudaStream_t);
+template <>
+cudaError_t launch_variant<5>(const BlendArgs&, int, int, bool, int, cudaStream_t);
 
 }  // namespace tc
 }  // namespace gs

@@ -13,6 +13,7 @@ cudaError_t launch_blend_tc_bwd(const BlendArgs& a0, const GradArgs& g, int vari
         case GS_BLEND_TC_BF16: return tc::launch_bwd_variant<GS_BLEND_TC_BF16>(a, g, s);
         case GS_BLEND_TC_FP16_SPLIT: return tc::launch_bwd_variant<GS_BLEND_TC_FP16_SPLIT>(a, g, s);
         case GS_BLEND_TC_BF16_SPLIT: return tc::launch_bwd_variant<GS_BLEND_TC_BF16_SPLIT>(a, g, s);
+        case GS_BLEND_TC_FP8_SPLIT: return tc::launch_bwd_variant<GS_BLEND_TC_FP8_SPLIT>(a, g, s);
     }
     return cudaErrorInvalidValue;
 }

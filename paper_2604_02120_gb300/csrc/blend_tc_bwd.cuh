@@ -96,7 +96,8 @@ struct BwdLayout {
     static constexpr int OFF_A1 = OFF_B2 + B2_BYTES;
     static constexpr int OFF_B1 = OFF_A1 + A1_BYTES;
     static constexpr int OFF_REC = OFF_B1 + SS * B1_BYTES;
-    static constexpr int OFF_FIN = OFF_REC + SS * CH * (int)sizeof(Rec);
+    static constexpr int OFF_SCL = OFF_REC + SS * CH * (int)sizeof(Rec);  // FP8: row scales
+    static constexpr int OFF_FIN = OFF_SCL + SS * CH * 8;
     static constexpr int OFF_BAR = OFF_FIN + SS * CH * (int)sizeof(Fin);
     // full[SS], empty[SS], tfull[2], tempty[2], a2full[2], m2done[2], drain
     static constexpr int NBAR = 2 * SS + 2 * kTStages + 5;
@@ -142,6 +143,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
     uint8_t* sB1 = smem + LY::OFF_B1;
     Rec* sRec = reinterpret_cast<Rec*>(smem + LY::OFF_REC);
     Fin* sFin = reinterpret_cast<Fin*>(smem + LY::OFF_FIN);
+    float2* sScl = reinterpret_cast<float2*>(smem + LY::OFF_SCL);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + LY::OFF_BAR);
     BwdHdr* sHdr = reinterpret_cast<BwdHdr*>(smem + LY::OFF_HDR);
     uint32_t* sTmem = reinterpret_cast<uint32_t*>(smem + LY::OFF_MISC);
@@ -175,18 +177,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
         mbar_fence_init();
     }
     // M_p of a 16 x 8 half (A operand of the exponent MMA), as in the forward kernel
-    for (int idx = threadIdx.x; idx < 128 * (TR::K / 8); idx += kThreads) {
-        const int row = idx / (TR::K / 8), kc = idx % (TR::K / 8);
+    for (int row = threadIdx.x; row < 128; row += kThreads) {
         const float xb = origin ? -(float)(row & 15) : 7.5f - (float)(row & 15);
         const float yb = origin ? -(float)(row >> 4) : 3.5f - (float)(row >> 4);
-        const float vp[6] = {xb * xb, yb * yb, xb * yb, xb, yb, 1.0f};
-        uint16_t e[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int k = kc * 8 + i;
-            e[i] = (k < 6 * TR::TERMS) ? to_op<TR::HALF>(vp[k % 6]) : (uint16_t)0;
-        }
-        store_row_chunk<V>(sA1, row, kc, e);
+        store_mp_row<V>(sA1, row, xb, yb);
     }
     // B2: zero, then the monomial columns 0..5 (the dL/dimage columns are per tile)
     for (int i = threadIdx.x; i < LY::B2_BYTES / 16; i += kThreads)
@@ -220,7 +214,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
     if (warp < kEpiWarps) {
         // ------------------------------------------------------- epilogue --
         const int r = warp * 32 + lane;
-        const int q = warp >> 1, hh = warp & 1;  // this warp's D2 rows: (q, hh, s = lane >> 4, j = lane & 15)
         int cur_seq = -1;
         float2 T = make_float2(0.f, 0.f), Sg = T, ncf = T, g0 = T, g1 = T, g2 = T;
         // pending chunk (finishing step not done yet)
@@ -367,6 +360,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
             tmem_ld_32x32b_x16(tb, pu);
             tmem_ld_32x32b_x16(tb + (uint32_t)CH, pl);
             tmem_ld_wait();
+            if constexpr (TR::FP8) {  // undo the per-row scaling of the e4m3 operands
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float2 z = __fmul2_rn(make_float2(__uint_as_float(pu[j]), __uint_as_float(pl[j])),
+                                                sScl[s * CH + j]);
+                    pu[j] = __float_as_uint(z.x);
+                    pl[j] = __float_as_uint(z.y);
+                }
+            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(bar_tempty(t));
@@ -550,7 +552,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
                             sFin[s * CH + j] = Fin{0xffffffffu, 0u, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                         }
                     }
-                    store_coeff_row<V>(mB, upper ? j : CH + j, vrow);
+                    const float rs = store_coeff_row<V>(mB, upper ? j : CH + j, vrow);
+                    if constexpr (TR::FP8) reinterpret_cast<float*>(sScl + s * CH + j)[upper ? 0 : 1] = rs;
                 }
                 if (lane == 0) {
                     hd.tile = tile;
@@ -587,7 +590,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
                 for (int ks = 0; ks < TR::KSTEPS; ++ks) {
                     const uint64_t ad = smem_desc(aA1 + (uint32_t)(ks * 256), 128, TR::SBO);
                     const uint64_t bd = smem_desc(aB1 + (uint32_t)(ks * 256), 128, TR::SBO);
-                    tc_mma_f16(tmem + (uint32_t)(t * 2 * CH), ad, bd, IDESC1, ks > 0 ? 1u : 0u);
+                    tc_mma<V>(tmem + (uint32_t)(t * 2 * CH), ad, bd, IDESC1, ks > 0 ? 1u : 0u);
                 }
                 tc_commit(bar_tfull(t));
                 tc_commit(bar_empty(s));
@@ -678,6 +681,8 @@ template <>
 cudaError_t launch_bwd_variant<3>(const BlendArgs&, const GradArgs&, cudaStream_t);
 template <>
 cudaError_t launch_bwd_variant<4>(const BlendArgs&, const GradArgs&, cudaStream_t);
+template <>
+cudaError_t launch_bwd_variant<5>(const BlendArgs&, const GradArgs&, cudaStream_t);
 
 }  // namespace tc
 }  // namespace gs

@@ -1,0 +1,13 @@
+// Tensor-core blend gradient for gs_variant value 5.
+#include "blend_tc_bwd.cuh"
+
+namespace gs {
+namespace tc {
+
+template <>
+cudaError_t launch_bwd_variant<5>(const BlendArgs& a, const GradArgs& g, cudaStream_t s) {
+    return launch_bwd_inst<5>(a, g, s);
+}
+
+}  // namespace tc
+}  // namespace gs

@@ -17,10 +17,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgs.so")
 
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CUDA, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, GS_ERR_UNSUPPORTED, GS_ERR_WORKSPACE = range(7)
-GS_BLEND_FP32, GS_BLEND_TC_FP16, GS_BLEND_TC_BF16, GS_BLEND_TC_FP16_SPLIT, GS_BLEND_TC_BF16_SPLIT = range(5)
+(GS_BLEND_FP32, GS_BLEND_TC_FP16, GS_BLEND_TC_BF16, GS_BLEND_TC_FP16_SPLIT, GS_BLEND_TC_BF16_SPLIT,
+ GS_BLEND_TC_FP8_SPLIT) = range(6)
 VARIANTS = {
     "fp32": GS_BLEND_FP32, "fp16": GS_BLEND_TC_FP16, "bf16": GS_BLEND_TC_BF16,
-    "fp16_split": GS_BLEND_TC_FP16_SPLIT, "bf16_split": GS_BLEND_TC_BF16_SPLIT,
+    "fp16_split": GS_BLEND_TC_FP16_SPLIT, "bf16_split": GS_BLEND_TC_BF16_SPLIT, "fp8_split": GS_BLEND_TC_FP8_SPLIT,
 }
 
 # Entry points declared in include/gs.h

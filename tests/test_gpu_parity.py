@@ -22,6 +22,8 @@ LOG2E = 1.4426950408889634
 # are held to when deciding which pixels are ambiguous; the tile-power tests
 # check that the measured error stays within half of it.
 SPLIT_EXP_ERR = 2e-4
+# the same for the FP8-e4m3 split trial (measured max 7.4e-4; the stated bound is 2e-3)
+FP8_EXP_ERR = 1e-3
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -190,7 +192,7 @@ def test_blend_fp32_matches_oracle(kind, bg):
 
 # ------------------------------------------------------ blend, tensor core --
 
-TC_VARIANTS = ["fp16", "bf16", "fp16_split", "bf16_split"]
+TC_VARIANTS = ["fp16", "bf16", "fp16_split", "bf16_split", "fp8_split"]
 
 
 def _tile_power_gate(sc, cam, proj, bs, pn, bn, variant, tiles, max_len=256, ref_origin=0):
@@ -253,6 +255,22 @@ def test_tile_power_split_within_2e3(kind, variant):
     assert e.max() <= SPLIT_EXP_ERR / 2
 
 
+@pytest.mark.parametrize("kind", ["tiny_dense", "c1"])
+def test_tile_power_fp8_split_trial(kind):
+    """FP8-e4m3 operands (a trial): v_g rows scaled by a power of two and split
+    into 5 e4m3 terms (the last three shifted up by 2^4 against the monomial
+    slots they meet), monomials into 2 exact terms.  The exponent error of
+    every pair that can contribute stays under the 2e-3 bound."""
+    sc, dev, cam, proj, bs, pn, bn = pipeline(kind)
+    e = _tile_power_gate(sc, cam, proj, bs, pn, bn, "fp8_split", _busy_tiles(bn, 24))
+    assert e.size > 1000
+    report(f"exp_err_fp8_split_{kind}",
+           {"max": float(e.max()), "p99": float(np.quantile(e, 0.99)), "pairs": int(e.size)})
+    assert e.max() <= 2e-3, f"max exponent error {e.max():.3e}"
+    # the blend comparison assumes this bound
+    assert e.max() <= FP8_EXP_ERR
+
+
 @pytest.mark.parametrize("variant", ["fp16", "bf16"])
 def test_tile_power_plain_is_close(variant):
     """Unsplit operands: the exponent is right to the operand precision."""
@@ -270,9 +288,11 @@ def test_blend_tc_matches_oracle(kind, variant):
     bg = (0.05, 0.1, 0.15)
     out = blend_gpu(cam, proj, bs, dev["opacities"], variant, bg=bg)
     if variant.endswith("split"):
-        ref = oracle_blend_on_gpu_params(cam, pn, bn, sc.opacities, bg=bg, alpha_margin=SPLIT_EXP_ERR,
+        margin = FP8_EXP_ERR if variant == "fp8_split" else SPLIT_EXP_ERR
+        ref = oracle_blend_on_gpu_params(cam, pn, bn, sc.opacities, bg=bg, alpha_margin=margin,
                                          t_margin=1e-5)
-        err = _compare(out, ref, 1e-3, nc_exact=True, max_amb=0.02)
+        fp8 = variant == "fp8_split"
+        err = _compare(out, ref, 5e-3 if fp8 else 1e-3, nc_exact=True, max_amb=0.1 if fp8 else 0.02)
         report(f"blend_{variant}_{kind}", {"max_abs": float(err.max()), "mean_abs": float(err.mean()),
                                            "ambiguous": float(ref["ambiguous"].mean())})
     else:
@@ -334,7 +354,7 @@ def _grad_rel_errors(g, ref):
     return out
 
 
-@pytest.mark.parametrize("variant", ["fp16_split", "bf16_split"])
+@pytest.mark.parametrize("variant", ["fp16_split", "bf16_split", "fp8_split"])
 @pytest.mark.parametrize("kind", ["tiny_ragged", "tiny_dense", "c0", "c1_small"])
 def test_tc_blend_backward_matches_oracle_gradient(kind, variant):
     """The tensor-core backward pass (exponents recomputed by the forward's
@@ -355,8 +375,9 @@ def test_tc_blend_backward_matches_oracle_gradient(kind, variant):
                             bg=bg, n_threads=CORES)
     rel = _grad_rel_errors(g, ref)
     report(f"tc_bwd_rel_{variant}_{kind}", rel)
+    bar = 1e-2 if variant == "fp8_split" else 1e-3  # the FP8 trial's exponent is good to 2e-3
     for name, e in rel.items():
-        assert e < 1e-3, f"{name}: relative error {e:.2e}"
+        assert e < bar, f"{name}: relative error {e:.2e}"
 
 
 @pytest.mark.parametrize("variant", ["fp16_split", "fp16"])
