@@ -86,6 +86,12 @@ typedef struct gs_blend_opts {
     float bg[3];         /* background colour added as T_final * bg */
     int32_t reserved;
     int64_t timeout_ns;  /* limit of every device-side wait; 0 = 1 s */
+    int32_t shard_count; /* tile sharding across ranks: the call blends only the tiles t
+                            (global tile ids) with t % shard_count == shard_index and leaves
+                            the other tiles' pixels untouched; the backward then adds only
+                            those tiles' contributions, so the sum over shards is the full
+                            gradient.  0 or 1 = all tiles */
+    int32_t shard_index; /* 0 <= shard_index < max(1, shard_count) */
 } gs_blend_opts;
 
 /* Library version (major * 100 + minor). */

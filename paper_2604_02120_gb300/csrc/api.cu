@@ -118,6 +118,9 @@ bool make_args(BlendArgs& a, int32_t n_views, const int32_t* widths, const int32
     for (int c = 0; c < 3; ++c) a.bg[c] = o ? o->bg[c] : 0.0f;
     a.timeout_ns = (o && o->timeout_ns > 0) ? (uint64_t)o->timeout_ns : 1000000000ull;
     a.ref_origin = o ? o->ref_origin : 0;
+    a.shard_count = (o && o->shard_count > 1) ? o->shard_count : 1;
+    a.shard_index = o ? o->shard_index : 0;
+    if (a.shard_index < 0 || a.shard_index >= a.shard_count) return false;
     a.err = error_word();
     return true;
 }
@@ -279,7 +282,7 @@ gs_status gs_blend_forward_views(int32_t n_views, const int32_t* widths, const i
     const gs_blend_opts* o = opts ? opts : &def;
     BlendArgs a;
     if (!make_args(a, n_views, widths, heights, n_per_view, tile_ranges, ids_sorted, mean2d, conic, opacity, rgb, o)) {
-        set_error("gs_blend_forward: image size out of range");
+        set_error("gs_blend_forward: image size or shard out of range");
         return GS_ERR_INVALID_ARG;
     }
     a.image = image;
@@ -296,7 +299,7 @@ gs_status gs_blend_forward_views(int32_t n_views, const int32_t* widths, const i
         set_error("gs_blend_forward: chunk %d / stages %d not built", chunk, stages);
         return GS_ERR_UNSUPPORTED;
     }
-    return cuda_status(launch_blend_tc(a, o->variant, chunk, stages, false, a.total_tiles, stream),
+    return cuda_status(launch_blend_tc(a, o->variant, chunk, stages, false, shard_items(a), stream),
                        "gs_blend_forward tc");
 }
 
@@ -332,7 +335,7 @@ gs_status gs_blend_backward_views(int32_t n_views, const int32_t* widths, const 
     }
     BlendArgs a;
     if (!make_args(a, n_views, widths, heights, n_per_view, tile_ranges, ids_sorted, mean2d, conic, opacity, rgb, o)) {
-        set_error("gs_blend_backward: image size out of range");
+        set_error("gs_blend_backward: image size or shard out of range");
         return GS_ERR_INVALID_ARG;
     }
     GradArgs g{T_final, n_contrib, dL_dimage, reinterpret_cast<float2*>(dmean2d), dconic, dopacity, drgb};

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kBatch) k_blend_fp32_fwd(const __grid_constant
     __shared__ float4 s_geo[kBatch];
     __shared__ float4 s_oc[kBatch];
     __shared__ float s_b[kBatch];
-    const int tile = blockIdx.x;
+    const int tile = blockIdx.x * a.shard_count + a.shard_index;
     const TileGeo tg = tile_geo(a, tile);
     const int px = tg.px, py = tg.py;
     const bool inside = px < tg.W && py < tg.H;
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kBatch) k_blend_fp32_bwd(const __grid_constant
     __shared__ float s_b[kBatch];
     __shared__ uint32_t s_id[kBatch];
     __shared__ int s_max;
-    const int tile = blockIdx.x;
+    const int tile = blockIdx.x * a.shard_count + a.shard_index;
     const TileGeo tg = tile_geo(a, tile);
     const int px = tg.px, py = tg.py;
     const bool inside = px < tg.W && py < tg.H;
@@ -264,13 +264,17 @@ __global__ void __launch_bounds__(kBatch) k_blend_fp32_bwd(const __grid_constant
 }  // namespace
 
 cudaError_t launch_blend_fp32_fwd(const BlendArgs& a, cudaStream_t s) {
-    k_blend_fp32_fwd<<<a.total_tiles, kBatch, 0, s>>>(a);
+    const int items = shard_items(a);
+    if (items == 0) return cudaSuccess;
+    k_blend_fp32_fwd<<<items, kBatch, 0, s>>>(a);
     count_launches();
     return cudaGetLastError();
 }
 
 cudaError_t launch_blend_fp32_bwd(const BlendArgs& a, const GradArgs& g, cudaStream_t s) {
-    k_blend_fp32_bwd<<<a.total_tiles, kBatch, 0, s>>>(a, g);
+    const int items = shard_items(a);
+    if (items == 0) return cudaSuccess;
+    k_blend_fp32_bwd<<<items, kBatch, 0, s>>>(a, g);
     count_launches();
     return cudaGetLastError();
 }

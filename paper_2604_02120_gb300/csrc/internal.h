@@ -43,11 +43,17 @@ struct BlendArgs {
     unsigned* err;
     uint64_t timeout_ns;
     int ref_origin;
+    int shard_count, shard_index;  // tiles t with t % shard_count == shard_index; queue item q is tile q * count + index
     // gs_tile_power only
     const int* tiles;
     int max_len;
     float* dump;
 };
+
+// Number of the call's tiles in its shard.
+inline int shard_items(const BlendArgs& a) {
+    return a.total_tiles > a.shard_index ? (a.total_tiles - a.shard_index + a.shard_count - 1) / a.shard_count : 0;
+}
 
 struct GradArgs {
     const float* T_final;

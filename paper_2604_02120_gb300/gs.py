@@ -54,7 +54,7 @@ class gs_camera(ctypes.Structure):
 class gs_blend_opts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("chunk", ctypes.c_int32), ("stages", ctypes.c_int32),
                 ("ref_origin", ctypes.c_int32), ("bg", ctypes.c_float * 3), ("reserved", ctypes.c_int32),
-                ("timeout_ns", ctypes.c_int64)]
+                ("timeout_ns", ctypes.c_int64), ("shard_count", ctypes.c_int32), ("shard_index", ctypes.c_int32)]
 
 
 _lib = None
@@ -136,13 +136,15 @@ def make_camera(cam) -> gs_camera:
     return c
 
 
-def make_opts(variant="fp32", chunk=0, stages=0, ref_origin=0, bg=(0.0, 0.0, 0.0), timeout_ns=0) -> gs_blend_opts:
+def make_opts(variant="fp32", chunk=0, stages=0, ref_origin=0, bg=(0.0, 0.0, 0.0), timeout_ns=0, shard_count=0,
+              shard_index=0) -> gs_blend_opts:
     o = gs_blend_opts()
     o.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     o.chunk, o.stages, o.ref_origin = int(chunk), int(stages), int(ref_origin)
     for i in range(3):
         o.bg[i] = float(bg[i])
     o.timeout_ns = int(timeout_ns)
+    o.shard_count, o.shard_index = int(shard_count), int(shard_index)
     return o
 
 
@@ -353,9 +355,11 @@ class BinSorter:
 
 def blend_forward(width, height, bs, proj, opacity, opts, stream=None) -> dict:
     dev = opacity.device
-    image = torch.empty(3, height, width, device=dev, dtype=torch.float32)
-    T = torch.empty(height, width, device=dev, dtype=torch.float32)
-    nc = torch.empty(height, width, device=dev, dtype=torch.int32)
+    # a sharded call writes only its tiles' pixels: the others are zero
+    new = torch.zeros if opts.shard_count > 1 else torch.empty
+    image = new(3, height, width, device=dev, dtype=torch.float32)
+    T = new(height, width, device=dev, dtype=torch.float32)
+    nc = new(height, width, device=dev, dtype=torch.int32)
     gs_blend_forward(width, height, bs["tile_ranges"], bs["ids"], proj["mean2d"], proj["conic"], opacity,
                      proj["rgb"], opts, image, T, nc, stream)
     return dict(image=image, T_final=T, n_contrib=nc)
