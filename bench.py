@@ -173,14 +173,16 @@ def run_ours(args):
     ranges = torch.empty(2 * gs.num_tiles(W, H), dtype=torch.int32, device="cuda")
     count_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
 
-    def step(ev=None):
+    def step(ev=None, tight=False):
         if ev:
             ev[0].record(stream)
         proj = gs.project(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam)
         if ev:
             ev[1].record(stream)
+        # opacity-aware lists: the exponent each splat must reach in a tile (gs_alpha_power_min)
+        pmin = gs.alpha_power_min(dev["opacities"]) if tight else None
         gs.gs_bin_sort_views(1, n, proj["mean2d"], proj["radius"], proj["depth"], [W], [H], capacity, ws, keys, ids,
-                             ranges, count_dev=count_dev)
+                             ranges, count_dev=count_dev, conic=proj["conic"] if tight else None, power_min=pmin)
         bs = dict(tile_ranges=ranges, ids=ids)
         if ev:
             ev[2].record(stream)
@@ -235,6 +237,28 @@ def run_ours(args):
         dev_ms = float(t.item())
     evals_step = 2 * evals_fwd  # forward and backward each examine sum(n_contrib) pairs
     value = ws_n * evals_step * K / (dev_ms / 1e3)
+
+    # ---- the same step with opacity-aware tile lists (same image; fewer instances)
+    for _ in range(3):
+        step(tight=True)
+    _, tbs, tfwd, _ = step(tight=True)
+    t_inst = int(count_dev.item())
+    t_evals = 2 * int(tfwd["n_contrib"].sum().item())
+    Kt = min(K, 200)
+    t_ev = [tuple(E() for _ in range(5)) for _ in range(Kt)]
+    for k in range(Kt):
+        flush.zero_()
+        step(t_ev[k], tight=True)
+    torch.cuda.synchronize()
+    assert gs.gs_sync_status() == gs.GS_OK
+    t_ms = statistics.mean(e[0].elapsed_time(e[4]) for e in t_ev)
+    tight_line = {"ms_per_step": round(t_ms, 5), "instances": t_inst, "evals_per_step": t_evals,
+                  "breakdown_ms": {"project": round(statistics.mean(e[0].elapsed_time(e[1]) for e in t_ev), 5),
+                                   "bin_sort": round(statistics.mean(e[1].elapsed_time(e[2]) for e in t_ev), 5),
+                                   "blend_forward": round(statistics.mean(e[2].elapsed_time(e[3]) for e in t_ev), 5),
+                                   "blend_backward": round(statistics.mean(e[3].elapsed_time(e[4]) for e in t_ev), 5)},
+                  "steps": Kt, "note": "gs_bin_sort_views with conic + gs_alpha_power_min: a splat keeps a tile "
+                                       "only if alpha can reach 1/255 there; the image equals the full lists' "}
 
     # ---- blend-only ms/frame per variant (forward), tensor core vs FP32 CUDA core
     blend = {}
@@ -312,6 +336,7 @@ def run_ours(args):
         "wall_ms_per_step": wall * 1e3 / K,
         "blend_forward_by_variant": blend,
         "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
+        "opacity_aware_lists": tight_line,
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cam, proj, bs, sc, dL, args.cpu_seconds)

@@ -179,12 +179,32 @@ gs_status gs_bin_sort(int32_t n, const float* mean2d, const int32_t* radius, con
  *    `capacity`; the instance count is written to *n_instances_dev; if it
  *    exceeds capacity the lists are truncated and gs_sync_status() later
  *    returns GS_ERR_CAPACITY.
+ * Opacity-aware lists (the tighter tile intersection; not in the paper): with
+ * conic (the items' conics, 3 floats each, as gs_project writes them) and
+ * power_min (one float per Gaussian, from gs_alpha_power_min) a splat keeps a
+ * tile of its rectangle only if its exponent can reach power_min at some pixel
+ * centre of the tile, i.e. if the tile's box of centre offsets meets the
+ * ellipse q(d) <= -2 power_min; each rectangle row keeps one run of tiles,
+ * found in closed form from the ellipse's extent within the row.  Dropped
+ * splats would fail the 1/255 test at every pixel of the tile, so images and
+ * T_final are those of the full lists (n_contrib counts list positions and
+ * shrinks).  The rule is FP32 with one rounding per operation, so the lists
+ * are reproducible bit for bit.  A conic that is not positive definite keeps
+ * its whole rectangle; power_min >= 0 keeps no tile.  Both NULL: the full
+ * rectangles.
  */
 gs_status gs_bin_sort_views(int32_t n_views, int32_t n_per_view, const float* mean2d, const int32_t* radius,
-                            const float* depth, const int32_t* widths, const int32_t* heights, int64_t capacity,
+                            const float* depth, const float* conic, const float* power_min,
+                            const int32_t* widths, const int32_t* heights, int64_t capacity,
                             void* workspace, size_t workspace_bytes, uint64_t* keys_sorted, uint32_t* ids_sorted,
                             uint32_t* tile_ranges, int64_t* n_instances, int64_t* n_instances_dev,
                             gs_stream stream);
+
+/* power_min[g] = ln(1 / (255 opacity[g])) - 2e-3 (+inf when opacity < 1.0f/255.0f)
+ * for n Gaussians: the exponent a splat must reach somewhere in a tile for
+ * alpha >= 1/255 there, lowered by a margin above the exponent error of the
+ * FP32 and split tensor-core blends.  Device pointers; asynchronous. */
+gs_status gs_alpha_power_min(int32_t n, const float* opacity, float* power_min, gs_stream stream);
 
 /*
  * gs_bin_sort_noalloc - gs_bin_sort for callers that cannot allocate device

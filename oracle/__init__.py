@@ -85,9 +85,11 @@ def sh_basis(dirs) -> np.ndarray:
     return out
 
 
-def bin_sort(mean2d, radius, depth, width, height, capacity=None) -> dict:
+def bin_sort(mean2d, radius, depth, width, height, capacity=None, conic=None, power_min=None) -> dict:
     """Duplicate + stable sort; mean2d may be the CUDA path's float32 values
-    (converted exactly to double), depth is used through its float32 bits."""
+    (converted exactly to double), depth is used through its float32 bits.
+    With conic and power_min (float32, per Gaussian) a tile is kept only if
+    the splat's exponent can reach power_min in it (opacity-aware lists)."""
     n = int(mean2d.shape[0])
     mean2d = _c(mean2d, np.float64)
     radius = _c(radius, np.int32)
@@ -100,8 +102,13 @@ def bin_sort(mean2d, radius, depth, width, height, capacity=None) -> dict:
     keys = np.zeros(max(cap, 1), np.uint64)
     ids = np.zeros(max(cap, 1), np.uint32)
     ranges = np.zeros(2 * num_tiles(width, height), np.uint32)
+    tight = conic is not None and power_min is not None
+    m32 = _c(mean2d, np.float32) if tight else None
+    c32 = _c(conic, np.float32) if tight else None
+    p32 = _c(power_min, np.float32) if tight else None
     I = lib().oracle_bin_sort(ctypes.c_int(n), _p(mean2d), _p(radius), _p(depth), ctypes.c_int(width),
-                              ctypes.c_int(height), ctypes.c_int64(cap), _p(keys), _p(ids), _p(ranges))
+                              ctypes.c_int(height), ctypes.c_int64(cap), _p(keys), _p(ids), _p(ranges),
+                              _p(m32), _p(c32), _p(p32))
     if I < 0:
         return dict(n_instances=-1, keys=None, ids=None, tile_ranges=ranges)
     return dict(n_instances=int(I), keys=keys[:I], ids=ids[:I], tile_ranges=ranges)

@@ -211,8 +211,19 @@ gs_status gs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t width,
     return GS_OK;
 }
 
+gs_status gs_alpha_power_min(int32_t n, const float* opacity, float* power_min, gs_stream stream) {
+    g_last_error[0] = 0;
+    if (n < 0 || (n > 0 && (!opacity || !power_min))) {
+        set_error("gs_alpha_power_min: bad arguments");
+        return GS_ERR_INVALID_ARG;
+    }
+    return cuda_status(launch_alpha_power_min(n, opacity, power_min, static_cast<cudaStream_t>(stream)),
+                       "gs_alpha_power_min");
+}
+
 gs_status gs_bin_sort_views(int32_t n_views, int32_t n_per_view, const float* mean2d, const int32_t* radius,
-                            const float* depth, const int32_t* widths, const int32_t* heights, int64_t capacity,
+                            const float* depth, const float* conic, const float* power_min, const int32_t* widths,
+                            const int32_t* heights, int64_t capacity,
                             void* workspace, size_t workspace_bytes, uint64_t* keys_sorted, uint32_t* ids_sorted,
                             uint32_t* tile_ranges, int64_t* n_instances, int64_t* n_instances_dev, gs_stream stream) {
     g_last_error[0] = 0;
@@ -226,6 +237,12 @@ gs_status gs_bin_sort_views(int32_t n_views, int32_t n_per_view, const float* me
     SortViews sv{};
     sv.num_views = n_views;
     sv.n_per_view = n_per_view;
+    if ((conic == nullptr) != (power_min == nullptr)) {
+        set_error("gs_bin_sort: conic and power_min go together");
+        return GS_ERR_INVALID_ARG;
+    }
+    sv.conic = conic;
+    sv.power_min = power_min;
     if (!fill_views(n_views, widths, heights, sv.views, &sv.total_tiles)) {
         set_error("gs_bin_sort: image size out of range");
         return GS_ERR_INVALID_ARG;
@@ -260,7 +277,8 @@ gs_status gs_bin_sort(int32_t n, const float* mean2d, const int32_t* radius, con
         set_error("gs_bin_sort: n_instances must be a host pointer");
         return GS_ERR_INVALID_ARG;
     }
-    return gs_bin_sort_views(1, n, mean2d, radius, depth, &width, &height, capacity, workspace, workspace_bytes,
+    return gs_bin_sort_views(1, n, mean2d, radius, depth, nullptr, nullptr, &width, &height, capacity, workspace,
+                             workspace_bytes,
                              keys_sorted, ids_sorted, tile_ranges, n_instances, nullptr, stream);
 }
 

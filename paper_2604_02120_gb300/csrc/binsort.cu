@@ -329,11 +329,76 @@ cudaError_t radix_sort(uint32_t* k[2], uint32_t* v[2], uint32_t n_host, const ui
 
 // ------------------------------------------------------ duplicate/finalize --
 
+// ----------------------------------------------- opacity-aware membership --
+//
+// With sv.conic and sv.power_min set, a splat keeps tile (tx, ty) of its
+// rectangle only if its exponent can reach power_min at some pixel centre of
+// the tile: if the tile's box of centre offsets d = mean - pixel meets the
+// ellipse E = {d : q(d) <= tau2}, q(d) = A dx^2 + 2 B dx dy + C dy^2,
+// tau2 = -2 power_min.  Within the strip of one tile row, E's x-extent is an
+// interval: its right end is E's rightmost point (dy = -(B/C) x_max, x_max =
+// sqrt(tau2 C / det), det = AC - B^2) with dy clamped to the strip, the left
+// end the mirror image, and on a line dy = y the boundary is at
+// dx = (-B y +- sqrt(A tau2 - det y^2)) / A.  So each row keeps one run of
+// tiles, found in O(1).  Floating point decides an integer here, so the rule
+// is FP32 with one IEEE rounding per operation in a fixed order (the oracle
+// repeats it).  Not positive definite: whole rows; tau2 <= 0: no tile.
+struct TightRows {
+    int mode;  // 0: whole rows, 1: no tile, 2: the ellipse rule
+    float mx, my, nB, det, Atau, rA, ymax, dyr;
+};
+
+__device__ __forceinline__ TightRows tight_rows(const SortViews& sv, const float2* mean2d, uint32_t item) {
+    const float2 m = mean2d[item];
+    const uint32_t g = item - (item / (uint32_t)sv.n_per_view) * (uint32_t)sv.n_per_view;
+    const float A = sv.conic[3 * (size_t)item], B = sv.conic[3 * (size_t)item + 1];
+    const float C = sv.conic[3 * (size_t)item + 2];
+    TightRows t{0, m.x, m.y, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const float det = __fsub_rn(__fmul_rn(A, C), __fmul_rn(B, B));
+    if (!(A > 0.f) || !(det > 0.f)) return t;
+    const float tau2 = __fmul_rn(-2.0f, sv.power_min[g]);
+    t.mode = 1;
+    if (!(tau2 > 0.f)) return t;
+    t.mode = 2;
+    t.nB = -B;
+    t.det = det;
+    t.Atau = __fmul_rn(A, tau2);
+    t.rA = __fdiv_rn(1.0f, A);
+    t.ymax = __fsqrt_rn(__fdiv_rn(__fmul_rn(tau2, A), det));
+    const float xmax = __fsqrt_rn(__fdiv_rn(__fmul_rn(tau2, C), det));
+    t.dyr = __fmul_rn(__fdiv_rn(-B, C), xmax);
+    return t;
+}
+
+// The kept tiles [first, last] of row ty within [x0, x1] (first > last: none).
+__device__ __forceinline__ void tight_row(const TightRows& t, int ty, int x0, int x1, int& first, int& last) {
+    first = x0;
+    last = x1;
+    if (t.mode == 0) return;
+    last = x0 - 1;
+    if (t.mode == 1) return;
+    const float lo = fmaxf(__fsub_rn(t.my, __fadd_rn((float)(16 * ty), 15.5f)), -t.ymax);
+    const float hi = fminf(__fsub_rn(t.my, __fadd_rn((float)(16 * ty), 0.5f)), t.ymax);
+    if (!(lo <= hi)) return;
+    const float yr = fminf(fmaxf(t.dyr, lo), hi), yl = fminf(fmaxf(-t.dyr, lo), hi);
+    const float sr = __fsqrt_rn(fmaxf(__fsub_rn(t.Atau, __fmul_rn(t.det, __fmul_rn(yr, yr))), 0.f));
+    const float sl = __fsqrt_rn(fmaxf(__fsub_rn(t.Atau, __fmul_rn(t.det, __fmul_rn(yl, yl))), 0.f));
+    const float xr = __fmul_rn(__fadd_rn(__fmul_rn(t.nB, yr), sr), t.rA);
+    const float xl = __fmul_rn(__fsub_rn(__fmul_rn(t.nB, yl), sl), t.rA);
+    // tile tx has offsets [mx - 16 tx - 15.5, mx - 16 tx - 0.5]
+    const float flo = __fmul_rn(__fsub_rn(__fsub_rn(t.mx, 15.5f), xr), 0.0625f);
+    const float fhi = __fmul_rn(__fsub_rn(__fsub_rn(t.mx, 0.5f), xl), 0.0625f);
+    first = (int)ceilf(fminf(fmaxf(flo, (float)x0), (float)(x1 + 1)));
+    last = (int)floorf(fminf(fmaxf(fhi, (float)(x0 - 1)), (float)x1));
+}
+
 // Per item: its tile count and depth key; the depth keys' four digit
 // histograms (pass ids 0..3).  Also clears the tile ranges and the look-back
-// status words for this call.  Each thread takes kCountItems items, strided by
-// the block size, with all loads issued before any use.
-constexpr int kCountItems = 4;
+// status words for this call.  Each thread takes ITEMS items, strided by the
+// block size, with all loads issued before any use.  TIGHT: opacity-aware
+// counts, one O(1) run per rectangle row.
+constexpr int kCountItems = 4, kCountItemsTight = 2;
+template <bool TIGHT, int ITEMS>
 __global__ void __launch_bounds__(kThreads) k_count(int n_items, const __grid_constant__ SortViews sv,
                                                     const float2* __restrict__ mean2d,
                                                     const int* __restrict__ radius, const float* __restrict__ depth,
@@ -343,12 +408,12 @@ __global__ void __launch_bounds__(kThreads) k_count(int n_items, const __grid_co
                                                     uint32_t* __restrict__ ranges, size_t ranges_n) {
     __shared__ uint32_t s_h[4 * 256];
     for (int i = threadIdx.x; i < 4 * 256; i += kThreads) s_h[i] = 0;
-    const int64_t base = (int64_t)blockIdx.x * (kThreads * kCountItems) + threadIdx.x;
-    float2 m[kCountItems];
-    int r[kCountItems];
-    uint32_t key[kCountItems];
+    const int64_t base = (int64_t)blockIdx.x * (kThreads * ITEMS) + threadIdx.x;
+    float2 m[ITEMS];
+    int r[ITEMS];
+    uint32_t key[ITEMS];
 #pragma unroll
-    for (int q = 0; q < kCountItems; ++q) {
+    for (int q = 0; q < ITEMS; ++q) {
         const int64_t i = base + q * kThreads;
         const bool ok = i < n_items;
         m[q] = ok ? mean2d[i] : make_float2(0.f, 0.f);
@@ -357,20 +422,29 @@ __global__ void __launch_bounds__(kThreads) k_count(int n_items, const __grid_co
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < kCountItems; ++q) {
+    for (int q = 0; q < ITEMS; ++q) {
         const int64_t i = base + q * kThreads;
-        if (i < n_items) {
-            const ViewDesc& vd = sv.views[(int)i / sv.n_per_view];
-            int x0, x1, y0, y1;
-            uint32_t c = 0;
-            if (tile_rect(m[q].x, m[q].y, r[q], vd.W, vd.H, x0, x1, y0, y1))
+        if (i >= n_items) continue;
+        const ViewDesc& vd = sv.views[(int)i / sv.n_per_view];
+        int x0, x1, y0, y1;
+        uint32_t c = 0;
+        if (tile_rect(m[q].x, m[q].y, r[q], vd.W, vd.H, x0, x1, y0, y1)) {
+            if constexpr (TIGHT) {
+                const TightRows t = tight_rows(sv, mean2d, (uint32_t)i);
+                for (int y = y0; y <= y1; ++y) {
+                    int f, l;
+                    tight_row(t, y, x0, x1, f, l);
+                    c += (uint32_t)max(l - f + 1, 0);
+                }
+            } else {
                 c = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
-            cnt[i] = c;
-            dkey[i] = key[q];
-            dval[i] = (uint32_t)i;
-#pragma unroll
-            for (int p = 0; p < 4; ++p) hist_add(s_h, p * 256 + ((key[q] >> (8 * p)) & 0xFFu));
+            }
         }
+        cnt[i] = c;
+        dkey[i] = key[q];
+        dval[i] = (uint32_t)i;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) hist_add(s_h, p * 256 + ((key[q] >> (8 * p)) & 0xFFu));
     }
     const size_t stride = (size_t)gridDim.x * kThreads;
     const uint4 z = make_uint4(0, 0, 0, 0);
@@ -400,13 +474,15 @@ __device__ __forceinline__ void row_hist(uint32_t a, uint32_t w, int passes, int
 // Tile t (from the ticket) holds the depth-ordered items
 // [t * kDupTile, (t + 1) * kDupTile) in kDupItems rounds of 256; the tile's
 // instance offset comes from decoupled look-back over the tiles before it.
-// Each item's instances are its rectangle's tile ids, row-major, at
-// [offset, offset + count); items with more than 32 tiles are written by the
-// whole warp together.  Writes stop at `limit`; the total goes to *total and,
-// in graph mode, to *count_out, with kErrCapacity raised when it exceeds the
-// capacity.  The digit histograms of the written instances' tile ids go to
-// hist (tile_passes of them), so a truncated list still sorts into a
-// permutation of what was written.
+// Each item's instances are its rectangle's tiles (TIGHT: each row's run of
+// tiles that meet the opacity-aware rule), row-major, at [offset, offset +
+// count); an item of more than 32 instances is written by the whole warp.
+// Writes stop at `limit`; the total goes to *total and, in graph
+// mode, to *count_out, with kErrCapacity raised when it exceeds the capacity.
+// The digit histograms of the written instances' tile ids go to hist
+// (tile_passes of them), so a truncated list still sorts into a permutation
+// of what was written.
+template <bool TIGHT>
 __global__ void __launch_bounds__(kThreads) k_duplicate(int n_items, const uint32_t* __restrict__ perm,
                                                         const uint32_t* __restrict__ cnt,
                                                         const __grid_constant__ SortViews sv,
@@ -467,6 +543,7 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(int n_items, const uint3
     __syncthreads();
     const uint64_t prefix = s_prefix;
 
+    if constexpr (!TIGHT) {
 #pragma unroll
     for (int r = 0; r < kDupItems; ++r) {
         uint32_t w = 1, h = 0, tile0 = 0, tx = 0;
@@ -481,43 +558,123 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(int n_items, const uint3
             tile0 = (uint32_t)vd.tile_begin + (uint32_t)y0 * tx + (uint32_t)x0;
         }
         const uint64_t off = prefix + local[r];
+        // written: all of the item's instances unless the capacity cuts it
+        const uint32_t nw = off >= limit ? 0u : (uint32_t)min((uint64_t)c[r], limit - off);
         const bool big = c[r] > 32;
         if (!big) {
             uint32_t row = tile0, col = 0;
-            for (uint32_t j = 0; j < c[r]; ++j) {
-                const uint64_t pos = off + j;
-                if (pos >= limit) break;
-                const uint32_t t = row + col;
-                tkey[pos] = t;
-                tval[pos] = item[r];
+            for (uint32_t j = 0; j < nw; ++j) {
+                tkey[off + j] = row + col;
+                tval[off + j] = item[r];
                 if (++col == w) {
                     col = 0;
                     row += tx;
                 }
             }
-            // histogram of the instances written (all of them unless the capacity cuts this item)
-            const uint32_t nw = off >= limit ? 0u : (uint32_t)min((uint64_t)c[r], limit - off);
             for (uint32_t y = 0; y * w < nw; ++y) row_hist(tile0 + y * tx, min(w, nw - y * w), tile_passes, s_d0, s_h);
         }
         unsigned bigs = __ballot_sync(0xffffffffu, big);
-        while (bigs) {
+        while (bigs) {  // the whole warp: one row's histogram per lane, the instances flat
             const int src = __ffs(bigs) - 1;
             bigs &= bigs - 1;
-            const uint32_t bi = __shfl_sync(0xffffffffu, item[r], src), bc = __shfl_sync(0xffffffffu, c[r], src);
+            const uint32_t bi = __shfl_sync(0xffffffffu, item[r], src), bnw = __shfl_sync(0xffffffffu, nw, src);
             const uint32_t bw = __shfl_sync(0xffffffffu, w, src), bt0 = __shfl_sync(0xffffffffu, tile0, src);
             const uint32_t btx = __shfl_sync(0xffffffffu, tx, src), bh = __shfl_sync(0xffffffffu, h, src);
             const uint64_t boff = __shfl_sync(0xffffffffu, off, src);
-            const uint32_t bnw = boff >= limit ? 0u : (uint32_t)min((uint64_t)bc, limit - boff);
             for (uint32_t y = lane; y < bh && y * bw < bnw; y += 32)
                 row_hist(bt0 + y * btx, min(bw, bnw - y * bw), tile_passes, s_d0, s_h);
-            for (uint32_t j = lane; j < bc; j += 32) {
-                const uint64_t pos = boff + j;
-                if (pos >= limit) break;
-                const uint32_t t = bt0 + (j / bw) * btx + j % bw;
-                tkey[pos] = t;
-                tval[pos] = bi;
+            for (uint32_t j = lane; j < bnw; j += 32) {
+                tkey[boff + j] = bt0 + (j / bw) * btx + j % bw;
+                tval[boff + j] = bi;
             }
         }
+    }
+    } else {
+#pragma unroll
+    for (int r = 0; r < kDupItems; ++r) {
+        int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
+        uint32_t rowbase = 0, tx = 0;
+        TightRows t{};
+        if (c[r] > 0) {
+            const ViewDesc& vd = sv.views[item[r] / (uint32_t)sv.n_per_view];
+            const float2 m = mean2d[item[r]];
+            tile_rect(m.x, m.y, radius[item[r]], vd.W, vd.H, x0, x1, y0, y1);
+            tx = (uint32_t)vd.tiles_x;
+            rowbase = (uint32_t)vd.tile_begin;
+            t = tight_rows(sv, mean2d, item[r]);
+        }
+        const uint64_t off = prefix + local[r];
+        const bool big = c[r] > 32;
+        if (c[r] > 0 && !big) {
+            uint64_t pos = off;
+            for (int y = y0; y <= y1 && pos < limit; ++y) {
+                int f, l;
+                tight_row(t, y, x0, x1, f, l);
+                if (f > l) continue;
+                const uint32_t t0 = rowbase + (uint32_t)y * tx + (uint32_t)f;
+                const uint32_t len = (uint32_t)(l - f + 1);
+                const uint32_t nw = (uint32_t)min((uint64_t)len, limit - pos);  // written (capacity)
+                for (uint32_t j = 0; j < nw; ++j) {
+                    tkey[pos + j] = t0 + j;
+                    tval[pos + j] = item[r];
+                }
+                row_hist(t0, nw, tile_passes, s_d0, s_h);
+                pos += len;
+            }
+        }
+        unsigned bigs = __ballot_sync(0xffffffffu, big);
+        while (bigs) {  // the whole warp, 32 rows at a time
+            const int src = __ffs(bigs) - 1;
+            bigs &= bigs - 1;
+            const uint32_t bi = __shfl_sync(0xffffffffu, item[r], src);
+            const int bx0 = __shfl_sync(0xffffffffu, x0, src), bx1 = __shfl_sync(0xffffffffu, x1, src);
+            const int by0 = __shfl_sync(0xffffffffu, y0, src), by1 = __shfl_sync(0xffffffffu, y1, src);
+            const uint32_t btx = __shfl_sync(0xffffffffu, tx, src), brb = __shfl_sync(0xffffffffu, rowbase, src);
+            uint64_t pos = __shfl_sync(0xffffffffu, off, src);
+            TightRows bt;
+            bt.mode = __shfl_sync(0xffffffffu, t.mode, src);
+            bt.mx = __shfl_sync(0xffffffffu, t.mx, src);
+            bt.my = __shfl_sync(0xffffffffu, t.my, src);
+            bt.nB = __shfl_sync(0xffffffffu, t.nB, src);
+            bt.det = __shfl_sync(0xffffffffu, t.det, src);
+            bt.Atau = __shfl_sync(0xffffffffu, t.Atau, src);
+            bt.rA = __shfl_sync(0xffffffffu, t.rA, src);
+            bt.ymax = __shfl_sync(0xffffffffu, t.ymax, src);
+            bt.dyr = __shfl_sync(0xffffffffu, t.dyr, src);
+            for (int yb = by0; yb <= by1 && pos < limit; yb += 32) {
+                // lane k: row yb + k's run, its offset among the 32 rows' instances and its histogram
+                int f = 0, l = -1;
+                if (yb + lane <= by1) tight_row(bt, yb + lane, bx0, bx1, f, l);
+                const uint32_t len = (uint32_t)max(l - f + 1, 0);
+                uint32_t incl = len;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+                    if (lane >= d) incl += v;
+                }
+                const uint32_t excl = incl - len, rows_total = __shfl_sync(0xffffffffu, incl, 31);
+                const uint32_t t0 = brb + (uint32_t)(yb + lane) * btx + (uint32_t)f;  // used where len > 0
+                const uint64_t rpos = pos + excl;
+                if (len > 0 && rpos < limit)
+                    row_hist(t0, (uint32_t)min((uint64_t)len, limit - rpos), tile_passes, s_d0, s_h);
+                // the instances flat: element j belongs to the last row whose offset is <= j
+                const uint32_t nw = (uint32_t)min((uint64_t)rows_total, limit - pos);
+                for (uint32_t j0 = 0; j0 < nw; j0 += 32) {
+                    const uint32_t j = j0 + lane;
+                    int k = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1)
+                        if (__shfl_sync(0xffffffffu, excl, k + step) <= j) k += step;
+                    const uint32_t kt0 = __shfl_sync(0xffffffffu, t0, k), kex = __shfl_sync(0xffffffffu, excl, k);
+                    if (j < nw) {
+                        tkey[pos + j] = kt0 + (j - kex);
+                        tval[pos + j] = bi;
+                    }
+                }
+                pos += rows_total;
+            }
+        }
+    }
     }
     __syncthreads();
     {
@@ -591,6 +748,28 @@ Layout make_layout(int n, int64_t capacity) {
 
 }  // namespace
 
+namespace {
+// power_min[g] = ln(1 / (255 o_g)) - kTightMargin: the exponent a splat must reach
+// for alpha = o exp(power) >= 1/255, lowered by a margin that covers the
+// exponent error of the blend variants (the split tensor-core ones are <= 1e-3);
+// +inf for o below the blend's FP32 threshold 1/255 (alpha <= o never reaches
+// it; o equal to it still passes where the exponent is 0).
+constexpr float kTightMargin = 2e-3f;
+__global__ void k_alpha_power_min(int n, const float* __restrict__ opacity, float* __restrict__ out) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const float o = opacity[g];
+    out[g] = o >= 1.0f / 255.0f ? -logf(255.0f * o) - kTightMargin : INFINITY;
+}
+}  // namespace
+
+cudaError_t launch_alpha_power_min(int n, const float* opacity, float* out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_alpha_power_min<<<(n + 255) / 256, 256, 0, s>>>(n, opacity, out);
+    count_launches();
+    return cudaGetLastError();
+}
+
 size_t bin_sort_workspace_bytes(int n_items, int64_t capacity, int /*num_tiles*/) {
     return make_layout(n_items, capacity).total_bytes;
 }
@@ -627,10 +806,15 @@ gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* ra
     // 1. counts, depth keys and their digit histograms; clears
     if ((e = cudaMemsetAsync(base + L.hdr, 0, L.hdr_bytes, s)) != cudaSuccess)
         return cuda_status(e, "gs_bin_sort: clear header");
-    const int count_blocks = (int)cdiv(n, kThreads * kCountItems);
-    k_count<<<count_blocks, kThreads, 0, s>>>(n, sv, mean2d, radius, depth, U32(L.cnt), U32(L.dk0), U32(L.dv0), hist,
-                                              reinterpret_cast<uint4*>(status), L.status_bytes / 16, tile_ranges,
-                                              2 * (size_t)ntiles);
+    const bool tight = sv.conic != nullptr;
+    if (tight)
+        k_count<true, kCountItemsTight><<<(int)cdiv(n, kThreads * kCountItemsTight), kThreads, 0, s>>>(
+            n, sv, mean2d, radius, depth, U32(L.cnt), U32(L.dk0), U32(L.dv0), hist, reinterpret_cast<uint4*>(status),
+            L.status_bytes / 16, tile_ranges, 2 * (size_t)ntiles);
+    else
+        k_count<false, kCountItems><<<(int)cdiv(n, kThreads * kCountItems), kThreads, 0, s>>>(
+            n, sv, mean2d, radius, depth, U32(L.cnt), U32(L.dk0), U32(L.dv0), hist, reinterpret_cast<uint4*>(status),
+            L.status_bytes / 16, tile_ranges, 2 * (size_t)ntiles);
     count_launches();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: count");
 
@@ -648,10 +832,10 @@ gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* ra
     const int tile_passes = (tile_bits + 7) / 8;
     uint32_t* tk[2] = {U32(L.tk0), U32(L.tk1)};
     uint32_t* tv[2] = {U32(L.tv0), U32(L.tv1)};
-    k_duplicate<<<(int)cdiv(n, kDupTile), kThreads, 0, s>>>(n, perm, U32(L.cnt), sv, mean2d, radius, (uint64_t)capacity,
-                                                          tile_passes, tickets, dup_status, tk[0], tv[0],
-                                                          hist + 256 * 4, total, graph ? n_instances_dev : nullptr,
-                                                          err);
+    auto dup = tight ? k_duplicate<true> : k_duplicate<false>;
+    dup<<<(int)cdiv(n, kDupTile), kThreads, 0, s>>>(n, perm, U32(L.cnt), sv, mean2d, radius, (uint64_t)capacity,
+                                                    tile_passes, tickets, dup_status, tk[0], tv[0], hist + 256 * 4,
+                                                    total, graph ? n_instances_dev : nullptr, err);
     count_launches();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: duplicate");
 

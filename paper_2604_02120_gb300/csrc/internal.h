@@ -88,9 +88,13 @@ cudaError_t launch_project(int n, const float* means, const float* scales, const
 struct SortViews {
     int num_views, total_tiles, n_per_view;
     ViewDesc views[kMaxViews];
+    // opacity-aware tile lists when both are set: conic per item, power_min per Gaussian
+    const float* conic;
+    const float* power_min;
 };
 
 size_t bin_sort_workspace_bytes(int n_items, int64_t capacity, int num_tiles);
+cudaError_t launch_alpha_power_min(int n, const float* opacity, float* out, cudaStream_t s);
 // n_instances_host != nullptr: synchronise once, read the count, exact grids.
 // otherwise (graph mode): no synchronisation; grids sized by capacity; the count
 // goes to n_instances_dev and overflow sets kErrCapacity in the error word.

@@ -30,7 +30,7 @@ ABI_FUNCTIONS = (
     "gs_bin_sort", "gs_blend_forward", "gs_blend_backward", "gs_tile_power", "gs_sync_status",
     "gs_selftest_bounded_wait", "gs_launch_count", "gs_bin_sort_noalloc", "gs_bin_sort_noalloc_max_bytes",
     "gs_project_views", "gs_bin_sort_views", "gs_blend_forward_views", "gs_blend_backward_views",
-    "gs_blend_autotune", "gs_measure_peaks",
+    "gs_blend_autotune", "gs_measure_peaks", "gs_alpha_power_min",
 )
 
 
@@ -86,7 +86,8 @@ def load(path: str = LIB_PATH):
     i32p, i64p = ctypes.POINTER(i32), ctypes.POINTER(i64)
     lib.gs_project_views.argtypes = [i32, vp, vp, vp, vp, i32, ctypes.POINTER(gs_camera), i32, vp, vp, vp, vp, vp,
                                      vp, vp]
-    lib.gs_bin_sort_views.argtypes = [i32, i32, vp, vp, vp, i32p, i32p, i64, vp, sz, vp, vp, vp, i64p, vp, vp]
+    lib.gs_bin_sort_views.argtypes = [i32, i32, vp, vp, vp, vp, vp, i32p, i32p, i64, vp, sz, vp, vp, vp, i64p, vp, vp]
+    lib.gs_alpha_power_min.argtypes = [i32, vp, vp, vp]
     lib.gs_blend_forward_views.argtypes = [i32, i32p, i32p, i32, vp, vp, vp, vp, vp, vp,
                                            ctypes.POINTER(gs_blend_opts), vp, vp, vp, vp]
     lib.gs_blend_backward_views.argtypes = [i32, i32p, i32p, i32, vp, vp, vp, vp, vp, vp,
@@ -239,11 +240,13 @@ def gs_project_views(n, means, scales, quats, sh, sh_degree, cams, mean2d, conic
 
 
 def gs_bin_sort_views(n_views, n_per_view, mean2d, radius, depth, widths, heights, capacity, workspace, keys_sorted,
-                      ids_sorted, tile_ranges, count_dev=None, stream=None, check=True):
+                      ids_sorted, tile_ranges, count_dev=None, stream=None, check=True, conic=None, power_min=None):
     """Synchronising mode if count_dev is None (returns (status, count)),
-    otherwise graph mode: the count goes to the int64 device tensor count_dev."""
+    otherwise graph mode: the count goes to the int64 device tensor count_dev.
+    conic and power_min (both or neither) select opacity-aware tile lists."""
     count = ctypes.c_int64(0)
-    st = load().gs_bin_sort_views(n_views, n_per_view, _ptr(mean2d), _ptr(radius), _ptr(depth), _i32arr(widths),
+    st = load().gs_bin_sort_views(n_views, n_per_view, _ptr(mean2d), _ptr(radius), _ptr(depth), _ptr(conic),
+                                  _ptr(power_min), _i32arr(widths),
                                   _i32arr(heights), capacity, _ptr(workspace),
                                   workspace.numel() * workspace.element_size(), _ptr(keys_sorted), _ptr(ids_sorted),
                                   _ptr(tile_ranges), None if count_dev is not None else ctypes.byref(count),
@@ -279,6 +282,16 @@ def gs_blend_autotune(widths, heights, n_per_view, tile_ranges, ids_sorted, mean
                                     ctypes.byref(opts), _ptr(image), _ptr(T_final), _ptr(n_contrib), int(reps),
                                     ctypes.byref(best), _stream(stream)), "gs_blend_autotune")
     return float(best.value)
+
+
+def gs_alpha_power_min(n, opacity, power_min, stream=None):
+    _check(load().gs_alpha_power_min(n, _ptr(opacity), _ptr(power_min), _stream(stream)), "gs_alpha_power_min")
+
+
+def alpha_power_min(opacity, stream=None):
+    out = torch.empty_like(opacity)
+    gs_alpha_power_min(opacity.shape[0], opacity, out, stream)
+    return out
 
 
 def gs_sync_status(stream=None) -> int:

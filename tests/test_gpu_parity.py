@@ -190,6 +190,75 @@ def test_blend_fp32_matches_oracle(kind, bg):
     assert (out["n_contrib"] > 0).mean() > 0.05
 
 
+def _tight_sort(cam, proj, pn, dev, capacity=1 << 22):
+    """GPU opacity-aware bin/sort (one view) and the oracle's, on the same
+    float32 inputs and power_min."""
+    n = proj["mean2d"].shape[0]
+    pmin = gs.alpha_power_min(dev["opacities"])
+    ws = torch.empty(gs.gs_bin_sort_workspace_size(n, capacity, cam.width, cam.height) + 256, device="cuda",
+                     dtype=torch.uint8)
+    keys = torch.empty(capacity, device="cuda", dtype=torch.int64)
+    ids = torch.empty(capacity, device="cuda", dtype=torch.int32)
+    ranges = torch.empty(2 * cam.num_tiles, device="cuda", dtype=torch.int32)
+    _, count = gs.gs_bin_sort_views(1, n, proj["mean2d"], proj["radius"], proj["depth"], [cam.width], [cam.height],
+                                    capacity, ws, keys, ids, ranges, conic=proj["conic"], power_min=pmin)
+    assert gs.gs_sync_status() == gs.GS_OK
+    got = dict(n_instances=count, keys=keys[:count].cpu().numpy().view(np.uint64),
+               ids=ids[:count].cpu().numpy().view(np.uint32), tile_ranges=ranges.cpu().numpy().view(np.uint32))
+    ref = oracle.bin_sort(pn["mean2d"].astype(np.float64), pn["radius"], pn["depth"], cam.width, cam.height,
+                          conic=pn["conic"], power_min=pmin.cpu().numpy())
+    bs = dict(tile_ranges=ranges, ids=ids, n_instances=count)
+    return got, ref, bs
+
+
+def test_alpha_power_min_values():
+    """power_min = ln(1/(255 o)) - 2e-3; +inf exactly for o below the blend's
+    float32 threshold 1/255 (o equal to it still passes where power = 0)."""
+    thr = np.float32(1.0) / np.float32(255.0)
+    below = np.nextafter(thr, np.float32(0.0))
+    o = torch.tensor(np.array([1.0, 0.99, 0.5, 0.02, thr, below, 1e-3], np.float32), device="cuda")
+    got = gs.alpha_power_min(o).cpu().numpy().astype(np.float64)
+    on = o.cpu().numpy().astype(np.float64)
+    want = -np.log(255 * on[:5]) - 2e-3
+    np.testing.assert_allclose(got[:5], want, rtol=1e-6, atol=1e-6)
+    assert np.isinf(got[5:]).all()
+
+
+@pytest.mark.parametrize("kind", ["c0", "tiny_ragged", "tiny_dense", "c1"])
+def test_bin_sort_opacity_aware_bit_exact(kind):
+    """Opacity-aware lists: FP32 tile membership with fixed rounding, so the
+    GPU lists equal the oracle's bit for bit, and there are fewer of them."""
+    sc, dev, cam, proj, bs, pn, bn = pipeline(kind)
+    got, ref, _ = _tight_sort(cam, proj, pn, dev)
+    assert got["n_instances"] == ref["n_instances"] > 0
+    assert got["n_instances"] < bn["n_instances"]
+    np.testing.assert_array_equal(got["keys"], ref["keys"])
+    np.testing.assert_array_equal(got["ids"], ref["ids"])
+    np.testing.assert_array_equal(got["tile_ranges"], ref["tile_ranges"])
+    report(f"instances_tight_{kind}", {"full": int(bn["n_instances"]), "tight": int(got["n_instances"])})
+
+
+@pytest.mark.parametrize("variant", ["fp32", "fp16_split"])
+@pytest.mark.parametrize("kind", ["tiny_dense", "c1"])
+def test_opacity_aware_lists_render_the_same_image(kind, variant):
+    """The splats the opacity-aware lists drop fail the 1/255 test at every
+    pixel of the tile: image and T_final are bit for bit those of the full
+    lists, gradients equal up to the order of atomic additions."""
+    sc, dev, cam, proj, bs, pn, bn = pipeline(kind)
+    _, _, tbs = _tight_sort(cam, proj, pn, dev)
+    opts = gs.make_opts(variant, bg=(0.1, 0.2, 0.3))
+    a = gs.blend_forward(cam.width, cam.height, bs, proj, dev["opacities"], opts)
+    b = gs.blend_forward(cam.width, cam.height, tbs, proj, dev["opacities"], opts)
+    torch.testing.assert_close(b["image"], a["image"], rtol=0, atol=0)
+    torch.testing.assert_close(b["T_final"], a["T_final"], rtol=0, atol=0)
+    assert (b["n_contrib"] <= a["n_contrib"]).all()
+    dL = torch.randn(3, cam.height, cam.width, device="cuda", generator=torch.Generator("cuda").manual_seed(4))
+    ga = gs.blend_backward(cam.width, cam.height, bs, proj, dev["opacities"], opts, a, dL)
+    gb = gs.blend_backward(cam.width, cam.height, tbs, proj, dev["opacities"], opts, b, dL)
+    for k in ga:
+        torch.testing.assert_close(gb[k], ga[k], rtol=1e-4, atol=1e-6 * float(ga[k].abs().max()))
+
+
 # ------------------------------------------------------ blend, tensor core --
 
 TC_VARIANTS = ["fp16", "bf16", "fp16_split", "bf16_split", "fp8_split"]

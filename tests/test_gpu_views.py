@@ -229,11 +229,14 @@ def test_sixteen_camera_batch_full_size():
     torch.testing.assert_close(nc, out["n_contrib"], rtol=0, atol=0)
 
 
-def test_bin_sort_views_three_tile_digit_passes_match_oracle_per_view():
+@pytest.mark.parametrize("tight", [False, True])
+def test_bin_sort_views_three_tile_digit_passes_match_oracle_per_view(tight):
     """12 views of 4000 x 4000 pixels hold 750,000 tiles, so the tile-id sort
     takes three 8-bit passes; 250 tiles per row put rectangle rows across
-    multiples of 256 tile ids.  Every view's lists must equal the oracle's
-    single-view bin/sort, shifted to the view's global tile and item range."""
+    multiples of 256 tile ids, and rectangles of hundreds of tiles take the
+    warp-cooperative paths.  Every view's lists (full, or opacity-aware) must
+    equal the oracle's single-view bin/sort, shifted to the view's global tile
+    and item range."""
     sizes = [(4000, 4000)] * 12
     sc = scenes.tiny_scene(21, n=300, width=64, height=64, sh_degree=0, scale_lo=-3.5, scale_hi=-2.5)
     sc.cameras = scenes.ring_cameras(len(sizes), 3.0, sizes)
@@ -252,8 +255,10 @@ def test_bin_sort_views_three_tile_digit_passes_match_oracle_per_view():
     keys = torch.empty(capacity, device="cuda", dtype=torch.int64)
     ids = torch.empty(capacity, device="cuda", dtype=torch.int32)
     ranges = torch.empty(2 * total_tiles, device="cuda", dtype=torch.int32)
+    pmin = gs.alpha_power_min(dev["opacities"]) if tight else None
     _, count = gs.gs_bin_sort_views(V, n, out["mean2d"], out["radius"], out["depth"], [w for w, _ in sizes],
-                                    [h for _, h in sizes], capacity, ws, keys, ids, ranges)
+                                    [h for _, h in sizes], capacity, ws, keys, ids, ranges,
+                                    conic=out["conic"] if tight else None, power_min=pmin)
     assert gs.gs_sync_status() == gs.GS_OK
     keys_np = keys[:count].cpu().numpy().view(np.uint64)
     ids_np = ids[:count].cpu().numpy().view(np.uint32)
@@ -264,7 +269,11 @@ def test_bin_sort_views_three_tile_digit_passes_match_oracle_per_view():
     tile0, total = 0, 0
     for v, (w, h) in enumerate(sizes):
         sl = slice(v * n, (v + 1) * n)
-        ref = oracle.bin_sort(m2[sl].astype(np.float64), rad[sl], dep[sl], w, h)
+        if tight:
+            ref = oracle.bin_sort(m2[sl].astype(np.float64), rad[sl], dep[sl], w, h,
+                                  conic=out["conic"].cpu().numpy()[sl], power_min=pmin.cpu().numpy())
+        else:
+            ref = oracle.bin_sort(m2[sl].astype(np.float64), rad[sl], dep[sl], w, h)
         nt = gs.num_tiles(w, h)
         lo = int(ranges_np[2 * tile0:2 * (tile0 + nt):2][ref["tile_ranges"][1::2] > 0].min())
         seg = slice(lo, lo + ref["n_instances"])

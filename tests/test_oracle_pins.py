@@ -205,6 +205,110 @@ def test_bin_sort_membership_and_order():
     assert total == bs["n_instances"] > 0
 
 
+def _power_min(opac):
+    """ln(1/(255 o)) - 2e-3 in float32, +inf where o is below the blend's
+    float32 threshold 1/255 (the library computes the same with
+    gs_alpha_power_min and hands it to both sides)."""
+    o = np.asarray(opac, np.float64)
+    keep = np.asarray(opac, np.float32) >= np.float32(1.0) / np.float32(255.0)
+    return np.where(keep, -np.log(255 * o) - 2e-3, np.inf).astype(np.float32)
+
+
+def _tight_case(seed, W, H, n=120):
+    sc = scenes.tiny_scene(seed, n=n, width=W, height=H, sh_degree=0, scale_lo=-3.2, scale_hi=-1.2,
+                           opac_lo=0.02, opac_hi=0.99)
+    cam = sc.cameras[0]
+    pr = oracle.project(sc.means, sc.scales, sc.quats, sc.sh, 0, cam)
+    # the kernels' float32 inputs
+    m32, c32 = pr["mean2d"].astype(np.float32), pr["conic"].astype(np.float32)
+    d32 = pr["depth"].astype(np.float32)
+    pmin = _power_min(sc.opacities)
+    full = oracle.bin_sort(m32.astype(np.float64), pr["radius"], d32, W, H)
+    tight = oracle.bin_sort(m32.astype(np.float64), pr["radius"], d32, W, H, conic=c32, power_min=pmin)
+    return sc, cam, m32, c32, d32, pmin, full, tight
+
+
+@pytest.mark.parametrize("seed,W,H", [(3, 70, 45), (4, 64, 64), (9, 33, 50)])
+def test_tight_lists_render_like_full_lists(seed, W, H):
+    """Opacity-aware lists drop only splats that fail alpha >= 1/255 at every
+    pixel of the tile: each tile's list is a sub-sequence of the full one, the
+    composite (Eq. 1 with the skip rule) is bit for bit the same, and fewer
+    instances remain."""
+    sc, cam, m32, c32, d32, pmin, full, tight = _tight_case(seed, W, H)
+    assert 0 < tight["n_instances"] < full["n_instances"]
+    for t in range(cam.num_tiles):
+        a = list(full["ids"][full["tile_ranges"][2 * t]:full["tile_ranges"][2 * t + 1]])
+        b = list(tight["ids"][tight["tile_ranges"][2 * t]:tight["tile_ranges"][2 * t + 1]])
+        it = iter(a)
+        assert all(g in it for g in b), f"tile {t}: not a sub-sequence"
+    args = (m32.astype(np.float64), c32.astype(np.float64), sc.opacities.astype(np.float64),
+            np.full((sc.n, 3), 0.5))
+    bg = (0.2, 0.1, 0.0)
+    rf = oracle.blend(W, H, full["tile_ranges"], full["ids"], *args, bg=bg)
+    rt = oracle.blend(W, H, tight["tile_ranges"], tight["ids"], *args, bg=bg)
+    np.testing.assert_array_equal(rt["image"], rf["image"])
+    np.testing.assert_array_equal(rt["T_final"], rf["T_final"])
+    assert (rt["n_contrib"] <= rf["n_contrib"]).all()
+
+
+def test_tight_lists_keep_every_pair_that_reaches_the_threshold():
+    """Brute force: a splat whose alpha = o exp(power) reaches 1/255 at any pixel
+    centre of a tile (FP64) is in that tile's opacity-aware list."""
+    sc, cam, m32, c32, d32, pmin, full, tight = _tight_case(21, 80, 64, n=200)
+    W, H = cam.width, cam.height
+    o = sc.opacities.astype(np.float64)
+    ys, xs = np.mgrid[0:H, 0:W] + 0.5
+    checked = 0
+    for t in range(cam.num_tiles):
+        x0, y0 = 16 * (t % cam.tiles_x), 16 * (t // cam.tiles_x)
+        px, py = xs[y0:y0 + 16, x0:x0 + 16], ys[y0:y0 + 16, x0:x0 + 16]
+        kept = set(tight["ids"][tight["tile_ranges"][2 * t]:tight["tile_ranges"][2 * t + 1]])
+        for g in full["ids"][full["tile_ranges"][2 * t]:full["tile_ranges"][2 * t + 1]]:
+            A, B, C = c32[g].astype(np.float64)
+            dx, dy = m32[g, 0] - px, m32[g, 1] - py
+            power = -0.5 * (A * dx * dx + 2 * B * dx * dy + C * dy * dy)
+            if (o[g] * np.exp(np.minimum(power, 0.0))).max() >= 1 / 255:
+                assert g in kept, f"tile {t} lost splat {g}"
+                checked += 1
+    assert checked > 100
+
+
+def test_tight_test_is_the_box_maximum():
+    """The opacity-aware rule keeps a splat on a tile exactly when the largest
+    exponent -q/2 over the tile's box of pixel-centre offsets reaches
+    power_min (the box meets the ellipse q <= -2 power_min): the box minimum
+    of q comes from a library box-constrained minimiser (L-BFGS-B, q convex)
+    in FP64, and every decision whose exponent is clear of the threshold by
+    more than rounding must agree."""
+    from scipy.optimize import minimize
+
+    sc, cam, m32, c32, d32, pmin, full, tight = _tight_case(5, 96, 64, n=160)
+    decided = dropped = 0
+    for t in range(cam.num_tiles):
+        tx, ty = t % cam.tiles_x, t // cam.tiles_x
+        kept = set(tight["ids"][tight["tile_ranges"][2 * t]:tight["tile_ranges"][2 * t + 1]])
+        for g in set(full["ids"][full["tile_ranges"][2 * t]:full["tile_ranges"][2 * t + 1]]):
+            A, B, C = c32[g].astype(np.float64)
+            mx, my = m32[g].astype(np.float64)
+            box = [(mx - 16 * tx - 15.5, mx - 16 * tx - 0.5), (my - 16 * ty - 15.5, my - 16 * ty - 0.5)]
+
+            def q(d):
+                return A * d[0] ** 2 + 2 * B * d[0] * d[1] + C * d[1] ** 2
+
+            def dq(d):
+                return np.array([2 * (A * d[0] + B * d[1]), 2 * (B * d[0] + C * d[1])])
+
+            start = np.array([sum(box[0]) / 2, sum(box[1]) / 2])
+            res = minimize(q, start, jac=dq, method="L-BFGS-B", bounds=box, options={"ftol": 1e-15, "gtol": 1e-12})
+            power = -0.5 * max(res.fun, 0.0)
+            if abs(power - float(pmin[g])) <= 1e-4 + 1e-5 * abs(res.fun):
+                continue
+            assert (g in kept) == (power >= pmin[g]), f"tile {t} splat {g}: box max {power} vs {pmin[g]}"
+            decided += 1
+            dropped += g not in kept
+    assert decided > 300 and dropped > 50
+
+
 def test_bin_sort_capacity_overflow_reports():
     sc = scenes.tiny_scene(11, n=20, width=48, height=48)
     cam = sc.cameras[0]
