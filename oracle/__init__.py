@@ -78,6 +78,23 @@ def project(means, scales, quats, sh, sh_degree, cam) -> dict:
     return out
 
 
+def project_backward(means, scales, quats, sh, sh_degree, cam, radius, dmean2d, dconic, drgb) -> dict:
+    """Gradient of ``project`` for one camera: dL/d(means, scales, quats, sh)
+    from dL/d(mean2d, conic, rgb); Gaussians with radius 0 get zeros."""
+    n = int(means.shape[0])
+    K = (sh_degree + 1) ** 2
+    means, scales, quats, sh = (_c(a, np.float32) for a in (means, scales, quats, sh))
+    radius = _c(radius, np.int32)
+    dmean2d, dconic, drgb = (_c(a, np.float64) for a in (dmean2d, dconic, drgb))
+    out = dict(dmeans=np.zeros((n, 3)), dscales=np.zeros((n, 3)), dquats=np.zeros((n, 4)),
+               dsh=np.zeros((n, K, 3)))
+    lib().oracle_project_backward(
+        ctypes.c_int(n), _p(means), _p(scales), _p(quats), _p(sh), ctypes.c_int(sh_degree),
+        _p(camera_array(cam)), _p(radius), _p(dmean2d), _p(dconic), _p(drgb), _p(out["dmeans"]),
+        _p(out["dscales"]), _p(out["dquats"]), _p(out["dsh"]))
+    return out
+
+
 def sh_basis(dirs) -> np.ndarray:
     dirs = _c(dirs, np.float64)
     out = np.zeros((dirs.shape[0], 16))

@@ -115,6 +115,40 @@ void sh_basis(double x, double y, double z, double out[16]) {
     out[15] = -n3a * x * (x * x - 3 * y * y);
 }
 
+// Partial derivatives of the real SH basis of sh_basis with respect to the
+// (unconstrained) coordinates x, y, z of its argument: grad[k] = dY_k/d(x,y,z).
+void sh_basis_grad(double x, double y, double z, double grad[16][3]) {
+    const double pi = 3.14159265358979323846;
+    const double n1 = std::sqrt(3.0 / (4.0 * pi));
+    const double n2a = 0.5 * std::sqrt(15.0 / pi);
+    const double n2b = 0.25 * std::sqrt(5.0 / pi);
+    const double n2c = 0.25 * std::sqrt(15.0 / pi);
+    const double n3a = 0.25 * std::sqrt(35.0 / (2.0 * pi));
+    const double n3b = 0.5 * std::sqrt(105.0 / pi);
+    const double n3c = 0.25 * std::sqrt(21.0 / (2.0 * pi));
+    const double n3d = 0.25 * std::sqrt(7.0 / pi);
+    const double n3e = 0.25 * std::sqrt(105.0 / pi);
+    const double g[16][3] = {
+        {0, 0, 0},
+        {0, -n1, 0},
+        {0, 0, n1},
+        {-n1, 0, 0},
+        {n2a * y, n2a * x, 0},
+        {0, -n2a * z, -n2a * y},
+        {-2 * n2b * x, -2 * n2b * y, 4 * n2b * z},
+        {-n2a * z, 0, -n2a * x},
+        {2 * n2c * x, -2 * n2c * y, 0},
+        {-6 * n3a * x * y, -n3a * (3 * x * x - 3 * y * y), 0},
+        {n3b * y * z, n3b * x * z, n3b * x * y},
+        {2 * n3c * x * y, -n3c * (4 * z * z - x * x - 3 * y * y), -8 * n3c * y * z},
+        {-6 * n3d * x * z, -6 * n3d * y * z, n3d * (6 * z * z - 3 * x * x - 3 * y * y)},
+        {-n3c * (4 * z * z - 3 * x * x - y * y), 2 * n3c * x * y, -8 * n3c * x * z},
+        {2 * n3e * x * z, -2 * n3e * y * z, n3e * (x * x - y * y)},
+        {-n3a * (3 * x * x - 3 * y * y), 6 * n3a * x * y, 0}};
+    for (int k = 0; k < 16; ++k)
+        for (int j = 0; j < 3; ++j) grad[k][j] = g[k][j];
+}
+
 struct Splat {
     double mx, my, A, B, C, o, c[3];
 };
@@ -303,6 +337,161 @@ void oracle_project(int n, const float* means, const float* scales, const float*
 // The real SH basis alone, for pinning against a library evaluation.
 void oracle_sh_basis(int n, const double* dirs, double* out) {
     for (int i = 0; i < n; ++i) sh_basis(dirs[3 * i], dirs[3 * i + 1], dirs[3 * i + 2], out + 16 * i);
+}
+
+// Gradient of the preprocessing stage (Sec. 2.1 (a), the projection of
+// oracle_project; the paper has no backward pass).  Given dL/dmean2d (n x 2),
+// dL/dconic (n x 3, the entries A, B, C of [[A, B], [B, C]]) and dL/drgb
+// (n x 3) of one camera, writes dL/dmeans (n x 3), dL/dscales (n x 3),
+// dL/dquats (n x 4) and dL/dsh (n x K x 3).  A Gaussian with radius[g] == 0
+// (culled by the forward pass) gets zeros.  The chain rule in matrix form:
+//   conic = Sigma2^-1 of [[a, b], [b, c]] -> G = dL/dSigma2 (symmetric);
+//   Sigma2 = T Sigma3 T^T, T = J R:  dSigma3 = T^T G T,  dT = 2 G T Sigma3,
+//   dJ = dT R^T;  J and mean2d are functions of p = R mean + t;
+//   Sigma3 = M M^T, M = Rq(q / |q|) diag(s):  dM = 2 dSigma3 M;
+//   rgb = max(0, sum_k sh_k Y_k(u) + 0.5), u = d / |d|, d = mean - centre:
+//   dsh_k = Y_k drgb (where not clamped), du = sum_k grad Y_k (sh_k . drgb),
+//   dd = (I - u u^T) du / |d|.
+void oracle_project_backward(int n, const float* means, const float* scales, const float* quats,
+                             const float* sh, int sh_degree, const double* cam_in, const int32_t* radius,
+                             const double* dmean2d, const double* dconic, const double* drgb,
+                             double* dmeans, double* dscales, double* dquats, double* dsh) {
+    const Cam cam = read_cam(cam_in);
+    const int K = (sh_degree + 1) * (sh_degree + 1);
+    double cpos[3];
+    for (int j = 0; j < 3; ++j)
+        cpos[j] = -(cam.R[0][j] * cam.t[0] + cam.R[1][j] * cam.t[1] + cam.R[2][j] * cam.t[2]);
+    for (int g = 0; g < n; ++g) {
+        for (int j = 0; j < 3; ++j) { dmeans[3 * g + j] = 0; dscales[3 * g + j] = 0; }
+        for (int j = 0; j < 4; ++j) dquats[4 * g + j] = 0;
+        for (int j = 0; j < 3 * K; ++j) dsh[(size_t)g * 3 * K + j] = 0;
+        if (radius[g] <= 0) continue;
+
+        // forward quantities
+        const double mw[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
+        double p[3];
+        for (int i = 0; i < 3; ++i)
+            p[i] = cam.R[i][0] * mw[0] + cam.R[i][1] * mw[1] + cam.R[i][2] * mw[2] + cam.t[i];
+        const double q[4] = {quats[4 * g], quats[4 * g + 1], quats[4 * g + 2], quats[4 * g + 3]};
+        const double qn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        const double w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, z = q[3] / qn;
+        const double Rq[3][3] = {
+            {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)},
+            {2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)},
+            {2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)}};
+        const double s[3] = {scales[3 * g], scales[3 * g + 1], scales[3 * g + 2]};
+        double M[3][3], S3[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) M[i][j] = Rq[i][j] * s[j];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                S3[i][j] = 0;
+                for (int k = 0; k < 3; ++k) S3[i][j] += M[i][k] * M[j][k];
+            }
+        const double iz = 1.0 / p[2];
+        const double J[2][3] = {{cam.fx * iz, 0, -cam.fx * p[0] * iz * iz}, {0, cam.fy * iz, -cam.fy * p[1] * iz * iz}};
+        double T[2][3];
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 3; ++j)
+                T[i][j] = J[i][0] * cam.R[0][j] + J[i][1] * cam.R[1][j] + J[i][2] * cam.R[2][j];
+        double S2[2][2];
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) {
+                S2[i][j] = 0;
+                for (int k = 0; k < 3; ++k)
+                    for (int l = 0; l < 3; ++l) S2[i][j] += T[i][k] * S3[k][l] * T[j][l];
+            }
+        const double a = S2[0][0] + cam.lowpass, b = S2[0][1], c = S2[1][1] + cam.lowpass;
+        const double det = a * c - b * b;
+
+        // conic (A, B, C) = (c, -b, a) / det  ->  (da, db, dc), then G = [[da, db/2], [db/2, dc]]
+        const double dA = dconic[3 * g], dB = dconic[3 * g + 1], dC = dconic[3 * g + 2];
+        const double d2 = det * det;
+        const double da = (-c * c * dA + b * c * dB - b * b * dC) / d2;
+        const double db = (2 * b * c * dA - (a * c + b * b) * dB + 2 * a * b * dC) / d2;
+        const double dc = (-b * b * dA + a * b * dB - a * a * dC) / d2;
+        const double G[2][2] = {{da, 0.5 * db}, {0.5 * db, dc}};
+
+        // dSigma3 = T^T G T;  dT = 2 G T Sigma3;  dJ = dT R^T
+        double dS3[3][3], GT[2][3], dT[2][3], dJ[2][3];
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 3; ++j) GT[i][j] = G[i][0] * T[0][j] + G[i][1] * T[1][j];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) dS3[i][j] = T[0][i] * GT[0][j] + T[1][i] * GT[1][j];
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 3; ++j) {
+                dT[i][j] = 0;
+                for (int k = 0; k < 3; ++k) dT[i][j] += 2 * GT[i][k] * S3[k][j];
+            }
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 3; ++j) dJ[i][j] = dT[i][0] * cam.R[j][0] + dT[i][1] * cam.R[j][1] + dT[i][2] * cam.R[j][2];
+
+        // p from J and from mean2d = (fx x / z + cx, fy y / z + cy)
+        const double dmx = dmean2d[2 * g], dmy = dmean2d[2 * g + 1];
+        double dp[3];
+        dp[0] = dJ[0][2] * (-cam.fx * iz * iz) + dmx * cam.fx * iz;
+        dp[1] = dJ[1][2] * (-cam.fy * iz * iz) + dmy * cam.fy * iz;
+        dp[2] = dJ[0][0] * (-cam.fx * iz * iz) + dJ[1][1] * (-cam.fy * iz * iz) +
+                dJ[0][2] * (2 * cam.fx * p[0] * iz * iz * iz) + dJ[1][2] * (2 * cam.fy * p[1] * iz * iz * iz) -
+                dmx * cam.fx * p[0] * iz * iz - dmy * cam.fy * p[1] * iz * iz;
+        for (int j = 0; j < 3; ++j)
+            dmeans[3 * g + j] = cam.R[0][j] * dp[0] + cam.R[1][j] * dp[1] + cam.R[2][j] * dp[2];
+
+        // Sigma3 = M M^T:  dM = 2 dSigma3 M;  M = Rq diag(s)
+        double dM[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                dM[i][j] = 0;
+                for (int k = 0; k < 3; ++k) dM[i][j] += 2 * dS3[i][k] * M[k][j];
+            }
+        double dR[3][3];
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0;
+            for (int i = 0; i < 3; ++i) {
+                acc += dM[i][j] * Rq[i][j];
+                dR[i][j] = dM[i][j] * s[j];
+            }
+            dscales[3 * g + j] = acc;
+        }
+        // the rotation matrix's entries as polynomials of the unit quaternion (w, x, y, z)
+        double dqh[4];
+        dqh[0] = 2 * (-z * dR[0][1] + y * dR[0][2] + z * dR[1][0] - x * dR[1][2] - y * dR[2][0] + x * dR[2][1]);
+        dqh[1] = 2 * (y * dR[0][1] + z * dR[0][2] + y * dR[1][0] - 2 * x * dR[1][1] - w * dR[1][2] + z * dR[2][0] +
+                      w * dR[2][1] - 2 * x * dR[2][2]);
+        dqh[2] = 2 * (-2 * y * dR[0][0] + x * dR[0][1] + w * dR[0][2] + x * dR[1][0] + z * dR[1][2] - w * dR[2][0] +
+                      z * dR[2][1] - 2 * y * dR[2][2]);
+        dqh[3] = 2 * (-2 * z * dR[0][0] - w * dR[0][1] + x * dR[0][2] + w * dR[1][0] - 2 * z * dR[1][1] +
+                      y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
+        // q / |q|:  dq = (I - qh qh^T) dqh / |q|
+        const double qh[4] = {w, x, y, z};
+        const double proj = qh[0] * dqh[0] + qh[1] * dqh[1] + qh[2] * dqh[2] + qh[3] * dqh[3];
+        for (int j = 0; j < 4; ++j) dquats[4 * g + j] = (dqh[j] - qh[j] * proj) / qn;
+
+        // colour
+        const double d[3] = {mw[0] - cpos[0], mw[1] - cpos[1], mw[2] - cpos[2]};
+        const double dn = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const double u[3] = {d[0] / dn, d[1] / dn, d[2] / dn};
+        double Y[16], dY[16][3];
+        sh_basis(u[0], u[1], u[2], Y);
+        sh_basis_grad(u[0], u[1], u[2], dY);
+        double dacc[3];
+        for (int ch = 0; ch < 3; ++ch) {
+            double acc = 0;
+            for (int k = 0; k < K; ++k) acc += (double)sh[((size_t)g * K + k) * 3 + ch] * Y[k];
+            dacc[ch] = acc + 0.5 > 0 ? drgb[3 * g + ch] : 0.0;
+        }
+        double du[3] = {0, 0, 0};
+        for (int k = 0; k < K; ++k) {
+            double w_k = 0;
+            for (int ch = 0; ch < 3; ++ch) {
+                dsh[((size_t)g * K + k) * 3 + ch] = Y[k] * dacc[ch];
+                w_k += (double)sh[((size_t)g * K + k) * 3 + ch] * dacc[ch];
+            }
+            for (int j = 0; j < 3; ++j) du[j] += w_k * dY[k][j];
+        }
+        const double ud = u[0] * du[0] + u[1] * du[1] + u[2] * du[2];
+        for (int j = 0; j < 3; ++j) dmeans[3 * g + j] += (du[j] - u[j] * ud) / dn;
+    }
 }
 
 // Stages 2-3 of Sec. 2.1: duplicate every splat once per touched tile (in

@@ -521,3 +521,55 @@ def test_blend_grad_matches_central_differences():
         assert np.linalg.norm(an_all - fd_all) / denom < 1e-6, name
         checked += len(fd_all)
     assert checked > 100
+
+
+def test_project_backward_matches_central_differences():
+    """The analytic projection gradient (means, scales, unnormalised
+    quaternions, SH degree 3) equals central differences of the oracle's own
+    forward projection for L = sum(wm * mean2d) + sum(wc * conic) +
+    sum(wr * rgb), seen from an off-axis camera; a Gaussian whose colour
+    channel is clamped at 0 passes no gradient through it."""
+    n = 14
+    sc = scenes.tiny_scene(12, n=n, width=80, height=64, sh_degree=3, scale_lo=-2.5, scale_hi=-1.2)
+    cam = scenes.look_at_camera((1.1, -0.6, -2.7), (0.05, 0.1, 0.0), 80, 64)
+    rng = np.random.default_rng(5)
+    means = sc.means.astype(np.float32).copy()
+    scales = sc.scales.astype(np.float32).copy()
+    quats = (sc.quats * rng.uniform(0.5, 2.0, (n, 1))).astype(np.float32)  # not unit length
+    sh = sc.sh.astype(np.float32).copy()
+    sh[0, 0, 1] = -4.0  # Gaussian 0's green channel is clamped
+    base = oracle.project(means, scales, quats, sh, 3, cam)
+    live = base["radius"] > 0
+    assert live.sum() >= 10 and base["rgb"][0, 1] == 0.0
+    wm, wc, wr = rng.standard_normal((n, 2)), rng.standard_normal((n, 3)), rng.standard_normal((n, 3))
+    g = oracle.project_backward(means, scales, quats, sh, 3, cam, base["radius"], wm, wc, wr)
+
+    def loss(args):
+        o = oracle.project(*args, 3, cam)
+        assert ((o["radius"] > 0) == live).all()
+        return float((wm * o["mean2d"]).sum() + (wc * o["conic"]).sum() + (wr * o["rgb"]).sum())
+
+    params = [means, scales, quats, sh]
+    for k, (name, key) in enumerate((("means", "dmeans"), ("scales", "dscales"), ("quats", "dquats"),
+                                     ("sh", "dsh"))):
+        arr = params[k]
+        fd, an = [], []
+        for idx in np.ndindex(arr.shape):
+            x = float(arr[idx])
+            h = 1e-3 * max(abs(x), 0.05)
+            xp, xm = np.float32(x + h), np.float32(x - h)
+            arr[idx] = xp
+            lp = loss(params)
+            arr[idx] = xm
+            lm = loss(params)
+            arr[idx] = x
+            fd.append((lp - lm) / (float(xp) - float(xm)))
+            an.append(g[key][idx])
+        fd, an = np.array(fd), np.array(an)
+        scale = np.abs(an).max()
+        assert scale > 0
+        np.testing.assert_allclose(an, fd, rtol=2e-5, atol=2e-5 * scale, err_msg=name)
+    assert not g["dmeans"][~live].any() and not g["dsh"][~live].any()
+    assert (g["dsh"][0, :, 1] == 0).all() and np.abs(g["dsh"][0, :, 0]).max() > 0
+    # the projection depends on q only through q / |q|: its gradient is orthogonal to q
+    assert np.abs((g["dquats"] * quats).sum(1)).max() < 1e-9 * np.abs(g["dquats"]).max()
