@@ -130,6 +130,15 @@ class ClockSampler:
                 "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
 
 
+def read_hbm_peak():
+    """Measured copy bandwidth (GB/s) of this machine's GPUs, else None."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def source_digest(*names):
     import hashlib
     h = hashlib.sha256()
@@ -265,6 +274,34 @@ def run_ours(args):
                   "steps": Kt, "note": "gs_bin_sort_views with conic + gs_alpha_power_min: a splat keeps a tile "
                                        "only if alpha can reach 1/255 there; the image equals the full lists' "}
 
+    # ---- projection backward: dL/d(means, scales, quats, sh) from the blend's
+    # splat gradients (HBM-bound, one thread per Gaussian)
+    pproj, _, _, gb = step()
+    pb_args = (dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam, pproj["radius"],
+               gb["mean2d"], gb["conic"], gb["rgb"])
+    for _ in range(3):
+        gs.project_backward(*pb_args)
+    pb_ev = []
+    for _ in range(min(K, 200)):
+        flush.zero_()
+        a, b = E(), E()
+        a.record(stream)
+        gs.project_backward(*pb_args)
+        b.record(stream)
+        pb_ev.append((a, b))
+    torch.cuda.synchronize()
+    assert gs.gs_sync_status() == gs.GS_OK
+    pb_ms = statistics.median(a.elapsed_time(b) for a, b in pb_ev)
+    Ksh = (sc.sh_degree + 1) ** 2
+    # per Gaussian: means, scales, quats, sh, radius, dmean2d, dconic, drgb read; dmeans, dscales, dquats, dsh written
+    pb_bytes = n * (4 * (3 + 3 + 4 + 3 * Ksh + 1 + 2 + 3 + 3) + 4 * (3 + 3 + 4 + 3 * Ksh))
+    hbm = read_hbm_peak()
+    pb_line = {"ms": round(pb_ms, 5), "bytes_per_gaussian": pb_bytes // n,
+               "achieved_gb_per_s": round(pb_bytes / pb_ms / 1e6, 1),
+               "peak_gb_per_s": hbm, "frac": round(pb_bytes / pb_ms / 1e6 / hbm, 4) if hbm else None,
+               "note": "gs_project_backward alone (k_project_bwd), L2 flushed before each launch, median of "
+                       f"{len(pb_ev)}; peak = measured copy bandwidth"}
+
     # ---- blend-only ms/frame per variant (forward), tensor core vs FP32 CUDA core
     blend = {}
     if not args.quick:
@@ -342,6 +379,7 @@ def run_ours(args):
         "blend_forward_by_variant": blend,
         "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
         "opacity_aware_lists": tight_line,
+        "projection_backward": pb_line,
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cam, proj, bs, sc, dL, args.cpu_seconds)

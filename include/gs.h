@@ -138,6 +138,29 @@ gs_status gs_project_views(int32_t n, const float* means, const float* scales, c
                            float* mean2d, float* conic, float* depth, int32_t* radius, float* rgb,
                            uint32_t* tiles_touched, gs_stream stream);
 
+/*
+ * gs_project_backward - gradient of gs_project_views (the preprocessing stage
+ * of Sec. 2.1 (a); the paper has no backward pass), summed over the views.
+ *   Inputs: the forward's inputs (means, scales, quats, sh, sh_degree, cams,
+ *   n_views; `cams` a HOST array), its radius output (n_views x n, view-major:
+ *   view v, Gaussian g at v * n + g; radius 0 = culled, no gradient) and the
+ *   loss gradient of its outputs in the same layout: dmean2d n_views x n x 2
+ *   (8-byte aligned), dconic n_views x n x 3 (the entries A, B, C of the conic
+ *   [[A, B], [B, C]]), drgb n_views x n x 3 (e.g. gs_blend_backward's outputs).
+ *   Outputs (overwritten): dmeans n x 3, dscales n x 3, dquats n x 4 (of the
+ *   quaternions as given, before normalisation), dsh n x K x 3.
+ * Chain rule through conic = Sigma2^-1, Sigma2 = (J R) Rq S S^T Rq^T (J R)^T
+ * + lowpass I with J at p = R mean + t, mean2d, the normalisation q / |q| and
+ * the SH colour rgb = max(0, sum_k sh_k Y_k(d) + 0.5) (a channel clamped at 0
+ * passes no gradient; the view direction d depends on the mean).  FP32, one
+ * thread per Gaussian; the 2x2 inverse's step in FP64 where the forward used
+ * FP64 (determinant below 1e-6).  Asynchronous.
+ */
+gs_status gs_project_backward(int32_t n, const float* means, const float* scales, const float* quats,
+                              const float* sh, int32_t sh_degree, const gs_camera* cams, int32_t n_views,
+                              const int32_t* radius, const float* dmean2d, const float* dconic, const float* drgb,
+                              float* dmeans, float* dscales, float* dquats, float* dsh, gs_stream stream);
+
 /* Bytes of scratch gs_bin_sort needs for n Gaussians, `capacity` instances and
  * a width x height image.  `bytes` is a HOST pointer.  For gs_bin_sort_views
  * pass n = n_views * n_per_view (the size does not depend on the image). */

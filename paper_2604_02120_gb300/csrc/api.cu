@@ -150,24 +150,14 @@ const char* gs_status_string(gs_status s) {
 
 const char* gs_last_error(void) { return g_last_error; }
 
-gs_status gs_project_views(int32_t n, const float* means, const float* scales, const float* quats, const float* sh,
-                           int32_t sh_degree, const gs_camera* cams, int32_t n_views, float* mean2d, float* conic,
-                           float* depth, int32_t* radius, float* rgb, uint32_t* tiles_touched, gs_stream stream) {
-    g_last_error[0] = 0;
-    if (n < 0 || sh_degree < 0 || sh_degree > 3 || !cams || n_views < 1 || n_views > kMaxViews) {
-        set_error("gs_project: bad n (%d), sh_degree (%d), cameras or n_views (%d)", n, sh_degree, n_views);
-        return GS_ERR_INVALID_ARG;
-    }
-    if ((long long)n * n_views >= (1ll << 32)) {
-        set_error("gs_project: n * n_views must be below 2^32");
-        return GS_ERR_INVALID_ARG;
-    }
-    CamViews cv{};
+// Host cameras -> the kernels' camera table (n_views <= kMaxViews).
+static gs_status make_cam_views(const char* who, const gs_camera* cams, int32_t n_views, CamViews& cv) {
+    cv = CamViews{};
     cv.num_views = n_views;
     for (int v = 0; v < n_views; ++v) {
         const gs_camera* cam = cams + v;
         if (!size_ok(cam->width, cam->height)) {
-            set_error("gs_project: image size %d x %d out of range", cam->width, cam->height);
+            set_error("%s: image size %d x %d out of range", who, cam->width, cam->height);
             return GS_ERR_INVALID_ARG;
         }
         CamDev& c = cv.cams[v];
@@ -184,14 +174,62 @@ gs_status gs_project_views(int32_t n, const float* means, const float* scales, c
         c.znear = cam->znear;
         c.lowpass = cam->lowpass;
     }
+    return GS_OK;
+}
+
+static gs_status check_project_args(const char* who, int32_t n, int32_t sh_degree, const gs_camera* cams,
+                                    int32_t n_views) {
+    if (n < 0 || sh_degree < 0 || sh_degree > 3 || !cams || n_views < 1 || n_views > kMaxViews) {
+        set_error("%s: bad n (%d), sh_degree (%d), cameras or n_views (%d)", who, n, sh_degree, n_views);
+        return GS_ERR_INVALID_ARG;
+    }
+    if ((long long)n * n_views >= (1ll << 32)) {
+        set_error("%s: n * n_views must be below 2^32", who);
+        return GS_ERR_INVALID_ARG;
+    }
+    return GS_OK;
+}
+
+gs_status gs_project_views(int32_t n, const float* means, const float* scales, const float* quats, const float* sh,
+                           int32_t sh_degree, const gs_camera* cams, int32_t n_views, float* mean2d, float* conic,
+                           float* depth, int32_t* radius, float* rgb, uint32_t* tiles_touched, gs_stream stream) {
+    g_last_error[0] = 0;
+    gs_status st = check_project_args("gs_project", n, sh_degree, cams, n_views);
+    if (st != GS_OK) return st;
+    CamViews cv;
+    if ((st = make_cam_views("gs_project", cams, n_views, cv)) != GS_OK) return st;
     if (n == 0) return GS_OK;
     if (!means || !scales || !quats || !sh || !mean2d || !conic || !depth || !radius || !rgb || !tiles_touched) {
         set_error("gs_project: null pointer");
         return GS_ERR_INVALID_ARG;
     }
     return cuda_status(launch_project(n, means, scales, quats, sh, sh_degree, cv, mean2d, conic, depth, radius, rgb,
-                                      tiles_touched, stream),
-                       "gs_project launch");
+                                      tiles_touched, static_cast<cudaStream_t>(stream)),
+                       "gs_project");
+}
+
+gs_status gs_project_backward(int32_t n, const float* means, const float* scales, const float* quats,
+                              const float* sh, int32_t sh_degree, const gs_camera* cams, int32_t n_views,
+                              const int32_t* radius, const float* dmean2d, const float* dconic, const float* drgb,
+                              float* dmeans, float* dscales, float* dquats, float* dsh, gs_stream stream) {
+    g_last_error[0] = 0;
+    gs_status st = check_project_args("gs_project_backward", n, sh_degree, cams, n_views);
+    if (st != GS_OK) return st;
+    CamViews cv;
+    if ((st = make_cam_views("gs_project_backward", cams, n_views, cv)) != GS_OK) return st;
+    if (n == 0) return GS_OK;
+    if (!means || !scales || !quats || !sh || !radius || !dmean2d || !dconic || !drgb || !dmeans || !dscales ||
+        !dquats || !dsh) {
+        set_error("gs_project_backward: null pointer");
+        return GS_ERR_INVALID_ARG;
+    }
+    if ((reinterpret_cast<uintptr_t>(dmean2d) & 7) != 0) {
+        set_error("gs_project_backward: dmean2d must be 8-byte aligned");
+        return GS_ERR_INVALID_ARG;
+    }
+    return cuda_status(launch_project_bwd(n, means, scales, quats, sh, sh_degree, cv, radius, dmean2d, dconic, drgb,
+                                          dmeans, dscales, dquats, dsh, static_cast<cudaStream_t>(stream)),
+                       "gs_project_backward");
 }
 
 gs_status gs_project(int32_t n, const float* means, const float* scales, const float* quats, const float* sh,

@@ -83,6 +83,11 @@ struct CamViews {
 cudaError_t launch_project(int n, const float* means, const float* scales, const float* quats, const float* sh,
                            int sh_degree, const CamViews& cams, float* mean2d, float* conic, float* depth,
                            int* radius, float* rgb, uint32_t* tiles_touched, cudaStream_t s);
+// gradient of launch_project summed over the views (inputs view-major, outputs per Gaussian)
+cudaError_t launch_project_bwd(int n, const float* means, const float* scales, const float* quats, const float* sh,
+                               int sh_degree, const CamViews& cams, const int* radius, const float* dmean2d,
+                               const float* dconic, const float* drgb, float* dmeans, float* dscales, float* dquats,
+                               float* dsh, cudaStream_t s);
 
 // Bin/sort geometry: items are (view, Gaussian) pairs, item = v * n_per_view + g.
 struct SortViews {

@@ -2,18 +2,10 @@
 // thread per Gaussian.  FP32 throughout; the 2D covariance and its inverse are
 // recomputed in FP64 when the FP32 determinant is below 1e-6.
 #include "internal.h"
+#include "sh.cuh"
 
 namespace gs {
 namespace {
-
-// Real SH basis constants (normalisations of the degree 0..3 harmonics).
-__constant__ float kSH0 = 0.28209479177387814f;
-__constant__ float kSH1 = 0.4886025119029199f;
-__constant__ float kSH2[5] = {1.0925484305920792f, -1.0925484305920792f, 0.31539156525252005f,
-                              -1.0925484305920792f, 0.5462742152960396f};
-__constant__ float kSH3[7] = {-0.5900435899266435f, 2.890611442640554f, -0.4570457994644658f,
-                              0.3731763325901154f, -0.4570457994644658f, 1.445305721320277f,
-                              -0.5900435899266435f};
 
 template <typename T>
 struct Cov2 {
@@ -161,29 +153,7 @@ __global__ void __launch_bounds__(256) k_project(int n, const float* __restrict_
             float x = dx * inv, y = dy * inv, z = dz * inv;
             const float* c = sh + (size_t)g * K * 3;
             float basis[K];
-            basis[0] = kSH0;
-            if constexpr (SH_DEGREE >= 1) {
-                basis[1] = -kSH1 * y;
-                basis[2] = kSH1 * z;
-                basis[3] = -kSH1 * x;
-            }
-            if constexpr (SH_DEGREE >= 2) {
-                float xx = x * x, yy = y * y, zz = z * z;
-                basis[4] = kSH2[0] * x * y;
-                basis[5] = kSH2[1] * y * z;
-                basis[6] = kSH2[2] * (2.f * zz - xx - yy);
-                basis[7] = kSH2[3] * x * z;
-                basis[8] = kSH2[4] * (xx - yy);
-                if constexpr (SH_DEGREE >= 3) {
-                    basis[9] = kSH3[0] * y * (3.f * xx - yy);
-                    basis[10] = kSH3[1] * x * y * z;
-                    basis[11] = kSH3[2] * y * (4.f * zz - xx - yy);
-                    basis[12] = kSH3[3] * z * (2.f * zz - 3.f * xx - 3.f * yy);
-                    basis[13] = kSH3[4] * x * (4.f * zz - xx - yy);
-                    basis[14] = kSH3[5] * z * (xx - yy);
-                    basis[15] = kSH3[6] * x * (xx - 3.f * yy);
-                }
-            }
+            sh_basis<SH_DEGREE>(x, y, z, basis);
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) col[ch] = 0.f;
             float cf[3 * K];

@@ -30,7 +30,7 @@ ABI_FUNCTIONS = (
     "gs_bin_sort", "gs_blend_forward", "gs_blend_backward", "gs_tile_power", "gs_sync_status",
     "gs_selftest_bounded_wait", "gs_launch_count", "gs_bin_sort_noalloc", "gs_bin_sort_noalloc_max_bytes",
     "gs_project_views", "gs_bin_sort_views", "gs_blend_forward_views", "gs_blend_backward_views",
-    "gs_blend_autotune", "gs_measure_peaks", "gs_alpha_power_min",
+    "gs_blend_autotune", "gs_measure_peaks", "gs_alpha_power_min", "gs_project_backward",
 )
 
 
@@ -88,6 +88,8 @@ def load(path: str = LIB_PATH):
                                      vp, vp]
     lib.gs_bin_sort_views.argtypes = [i32, i32, vp, vp, vp, vp, vp, i32p, i32p, i64, vp, sz, vp, vp, vp, i64p, vp, vp]
     lib.gs_alpha_power_min.argtypes = [i32, vp, vp, vp]
+    lib.gs_project_backward.argtypes = [i32, vp, vp, vp, vp, i32, ctypes.POINTER(gs_camera), i32, vp, vp, vp, vp,
+                                        vp, vp, vp, vp, vp]
     lib.gs_blend_forward_views.argtypes = [i32, i32p, i32p, i32, vp, vp, vp, vp, vp, vp,
                                            ctypes.POINTER(gs_blend_opts), vp, vp, vp, vp]
     lib.gs_blend_backward_views.argtypes = [i32, i32p, i32p, i32, vp, vp, vp, vp, vp, vp,
@@ -239,6 +241,14 @@ def gs_project_views(n, means, scales, quats, sh, sh_degree, cams, mean2d, conic
                                    _ptr(tiles_touched), _stream(stream)), "gs_project_views")
 
 
+def gs_project_backward(n, means, scales, quats, sh, sh_degree, cams, radius, dmean2d, dconic, drgb, dmeans, dscales,
+                        dquats, dsh, stream=None):
+    arr = (gs_camera * len(cams))(*[c if isinstance(c, gs_camera) else make_camera(c) for c in cams])
+    _check(load().gs_project_backward(n, _ptr(means), _ptr(scales), _ptr(quats), _ptr(sh), sh_degree, arr, len(cams),
+                                      _ptr(radius), _ptr(dmean2d), _ptr(dconic), _ptr(drgb), _ptr(dmeans),
+                                      _ptr(dscales), _ptr(dquats), _ptr(dsh), _stream(stream)), "gs_project_backward")
+
+
 def gs_bin_sort_views(n_views, n_per_view, mean2d, radius, depth, widths, heights, capacity, workspace, keys_sorted,
                       ids_sorted, tile_ranges, count_dev=None, stream=None, check=True, conic=None, power_min=None):
     """Synchronising mode if count_dev is None (returns (status, count)),
@@ -326,6 +336,21 @@ def project(means, scales, quats, sh, sh_degree, cam, stream=None) -> dict:
                tiles_touched=torch.empty(n, device=dev, dtype=torch.int32))
     gs_project(n, means, scales, quats, sh, sh_degree, cam, out["mean2d"], out["conic"], out["depth"],
                out["radius"], out["rgb"], out["tiles_touched"], stream)
+    return out
+
+
+def project_backward(means, scales, quats, sh, sh_degree, cams, radius, dmean2d, dconic, drgb, stream=None) -> dict:
+    """dL/d(means, scales, quats, sh) from dL/d(mean2d, conic, rgb) of
+    gs_project / gs_project_views outputs (view-major for several cameras),
+    summed over the views."""
+    cams = cams if isinstance(cams, (list, tuple)) else [cams]
+    n = means.shape[0]
+    f32 = dict(device=means.device, dtype=torch.float32)
+    out = dict(dmeans=torch.empty(n, 3, **f32), dscales=torch.empty(n, 3, **f32), dquats=torch.empty(n, 4, **f32),
+               dsh=torch.empty(sh.shape, **f32))
+    gs_project_backward(n, means, scales, quats, sh, sh_degree, cams, radius, dmean2d.contiguous(),
+                        dconic.contiguous(), drgb.contiguous(), out["dmeans"], out["dscales"], out["dquats"],
+                        out["dsh"], stream)
     return out
 
 
