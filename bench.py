@@ -302,6 +302,9 @@ def run_ours(args):
                "note": "gs_project_backward alone (k_project_bwd), L2 flushed before each launch, median of "
                        f"{len(pb_ev)}; peak = measured copy bandwidth"}
 
+    # ---- small scene: projection + bin/sort fused into one cooperative launch
+    small_line = run_small_fused(gs, torch, opts, flush, min(K, 200))
+
     # ---- blend-only ms/frame per variant (forward), tensor core vs FP32 CUDA core
     blend = {}
     if not args.quick:
@@ -380,6 +383,7 @@ def run_ours(args):
         "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
         "opacity_aware_lists": tight_line,
         "projection_backward": pb_line,
+        "small_scene_fused": small_line,
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cam, proj, bs, sc, dL, args.cpu_seconds)
@@ -387,6 +391,62 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def run_small_fused(gs, torch, opts, flush, K):
+    """The 256x256, 10k-Gaussian scene (the launch-bound case): the step with
+    gs_project + gs_bin_sort_views (graph mode, 9 launches) against the step
+    with gs_project_bin_small (one cooperative launch), both followed by the
+    same blend forward and backward; L2 flushed before every step."""
+    from paper_2604_02120_gb300 import scenes
+    sc = scenes.make_config(0, seed=0)
+    cam = sc.cameras[0]
+    W, H, n = cam.width, cam.height, sc.n
+    dev = gs.scene_to_device(sc)
+    dL = torch.from_numpy(scenes.upstream_grad(0, [cam])[0]).cuda()
+    stream = torch.cuda.current_stream()
+    capacity = 1 << 20
+    ws = torch.empty(gs.gs_bin_sort_workspace_size(n, capacity, W, H) + 256, dtype=torch.uint8, device="cuda")
+    keys = torch.empty(capacity, dtype=torch.int64, device="cuda")
+    ids = torch.empty(capacity, dtype=torch.int32, device="cuda")
+    ranges = torch.empty(2 * gs.num_tiles(W, H), dtype=torch.int32, device="cuda")
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    args3 = (dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam)
+
+    def unfused():
+        proj = gs.project(*args3)
+        gs.gs_bin_sort_views(1, n, proj["mean2d"], proj["radius"], proj["depth"], [W], [H], capacity, ws, keys, ids,
+                             ranges, count_dev=count)
+        return proj, dict(tile_ranges=ranges, ids=ids)
+
+    def fused():
+        return gs.project_bin_small(*args3, max_per_tile=1024)
+
+    out = {}
+    for name, front in (("unfused", unfused), ("fused", fused)):
+        def step():
+            proj, bs = front()
+            fwd = gs.blend_forward(W, H, bs, proj, dev["opacities"], opts)
+            gs.blend_backward(W, H, bs, proj, dev["opacities"], opts, fwd, dL)
+        for _ in range(3):
+            step()
+        ev = []
+        for _ in range(K):
+            flush.zero_()
+            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record(stream)
+            proj, bs = front()
+            b.record(stream)
+            fwd = gs.blend_forward(W, H, bs, proj, dev["opacities"], opts)
+            gs.blend_backward(W, H, bs, proj, dev["opacities"], opts, fwd, dL)
+            c.record(stream)
+            ev.append((a, b, c))
+        torch.cuda.synchronize()
+        assert gs.gs_sync_status() == gs.GS_OK
+        out[name] = {"ms_per_step": round(statistics.median(a.elapsed_time(c) for a, b, c in ev), 5),
+                     "project_bin_ms": round(statistics.median(a.elapsed_time(b) for a, b, c in ev), 5)}
+    out["workload"] = "256x256, 10k Gaussians, SH degree 0, seed 0; step = project + bin + blend fwd + bwd"
+    return out
 
 
 def run_e2e(args, gs, torch, sc, cam, opts, capacity, dL, flush, evals_step, ws, dist):

@@ -139,6 +139,38 @@ gs_status gs_project_views(int32_t n, const float* means, const float* scales, c
                            uint32_t* tiles_touched, gs_stream stream);
 
 /*
+ * gs_project_bin_small - gs_project and the per-tile lists of gs_bin_sort for
+ * one camera in ONE cooperative launch, for small scenes (Sec. 2.1 (a)-(c);
+ * the fusion is not in the paper).  For a few thousand to tens of thousands
+ * of Gaussians the separate bin/sort stage is mostly launch latency; here the
+ * blocks project every Gaussian, meet at a grid barrier, and each builds the
+ * list of its tiles by gathering the splats that cover the tile and ordering
+ * them by (depth bits, Gaussian index) in shared memory.  The gather scans all
+ * n splats for every tile (O(tiles * n) work), so larger scenes belong to
+ * gs_bin_sort.
+ *   Inputs as gs_project (`cam` a HOST pointer); power_min NULL for the full
+ *   rectangles, else one float per Gaussian (gs_alpha_power_min) for the
+ *   opacity-aware lists of gs_bin_sort_views (the conics are the ones this
+ *   call writes).  max_per_tile in 1..GS_SMALL_MAX_PER_TILE with
+ *   tiles * max_per_tile < 2^32.
+ *   Outputs: those of gs_project (mean2d 8-byte aligned); ids, tiles x
+ *   max_per_tile: tile t's list at ids[t * max_per_tile ...]; tile_ranges
+ *   (2 per tile) [t * max_per_tile, t * max_per_tile + count), so tile t's
+ *   list is ids[tile_ranges[2t] .. tile_ranges[2t+1]) and equals gs_bin_sort's
+ *   list of tile t, as the blend calls take it.
+ * A tile with more than max_per_tile splats keeps an unspecified subset and
+ * gs_sync_status() later returns GS_ERR_CAPACITY; a grid barrier that waited
+ * longer than 1 s sets GS_ERR_TIMEOUT.  The grid barrier's counter is one
+ * word in the library, so calls must not run concurrently.  Asynchronous.
+ */
+#define GS_SMALL_MAX_PER_TILE 16384
+gs_status gs_project_bin_small(int32_t n, const float* means, const float* scales, const float* quats,
+                               const float* sh, int32_t sh_degree, const gs_camera* cam, const float* power_min,
+                               int32_t max_per_tile, float* mean2d, float* conic, float* depth, int32_t* radius,
+                               float* rgb, uint32_t* tiles_touched, uint32_t* ids, uint32_t* tile_ranges,
+                               gs_stream stream);
+
+/*
  * gs_project_backward - gradient of gs_project_views (the preprocessing stage
  * of Sec. 2.1 (a); the paper has no backward pass), summed over the views.
  *   Inputs: the forward's inputs (means, scales, quats, sh, sh_degree, cams,

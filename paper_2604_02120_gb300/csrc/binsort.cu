@@ -25,6 +25,7 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "tight.cuh"
 
 namespace gs {
 namespace {
@@ -331,65 +332,12 @@ cudaError_t radix_sort(uint32_t* k[2], uint32_t* v[2], uint32_t n_host, const ui
 
 // ----------------------------------------------- opacity-aware membership --
 //
-// With sv.conic and sv.power_min set, a splat keeps tile (tx, ty) of its
-// rectangle only if its exponent can reach power_min at some pixel centre of
-// the tile: if the tile's box of centre offsets d = mean - pixel meets the
-// ellipse E = {d : q(d) <= tau2}, q(d) = A dx^2 + 2 B dx dy + C dy^2,
-// tau2 = -2 power_min.  Within the strip of one tile row, E's x-extent is an
-// interval: its right end is E's rightmost point (dy = -(B/C) x_max, x_max =
-// sqrt(tau2 C / det), det = AC - B^2) with dy clamped to the strip, the left
-// end the mirror image, and on a line dy = y the boundary is at
-// dx = (-B y +- sqrt(A tau2 - det y^2)) / A.  So each row keeps one run of
-// tiles, found in O(1).  Floating point decides an integer here, so the rule
-// is FP32 with one IEEE rounding per operation in a fixed order (the oracle
-// repeats it).  Not positive definite: whole rows; tau2 <= 0: no tile.
-struct TightRows {
-    int mode;  // 0: whole rows, 1: no tile, 2: the ellipse rule
-    float mx, my, nB, det, Atau, rA, ymax, dyr;
-};
-
-__device__ __forceinline__ TightRows tight_rows(const SortViews& sv, const float2* mean2d, uint32_t item) {
+// With sv.conic and sv.power_min set, tiles are kept by the rule of tight.cuh.
+__device__ __forceinline__ TightRows item_tight_rows(const SortViews& sv, const float2* mean2d, uint32_t item) {
     const float2 m = mean2d[item];
     const uint32_t g = item - (item / (uint32_t)sv.n_per_view) * (uint32_t)sv.n_per_view;
-    const float A = sv.conic[3 * (size_t)item], B = sv.conic[3 * (size_t)item + 1];
-    const float C = sv.conic[3 * (size_t)item + 2];
-    TightRows t{0, m.x, m.y, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const float det = __fsub_rn(__fmul_rn(A, C), __fmul_rn(B, B));
-    if (!(A > 0.f) || !(det > 0.f)) return t;
-    const float tau2 = __fmul_rn(-2.0f, sv.power_min[g]);
-    t.mode = 1;
-    if (!(tau2 > 0.f)) return t;
-    t.mode = 2;
-    t.nB = -B;
-    t.det = det;
-    t.Atau = __fmul_rn(A, tau2);
-    t.rA = __fdiv_rn(1.0f, A);
-    t.ymax = __fsqrt_rn(__fdiv_rn(__fmul_rn(tau2, A), det));
-    const float xmax = __fsqrt_rn(__fdiv_rn(__fmul_rn(tau2, C), det));
-    t.dyr = __fmul_rn(__fdiv_rn(-B, C), xmax);
-    return t;
-}
-
-// The kept tiles [first, last] of row ty within [x0, x1] (first > last: none).
-__device__ __forceinline__ void tight_row(const TightRows& t, int ty, int x0, int x1, int& first, int& last) {
-    first = x0;
-    last = x1;
-    if (t.mode == 0) return;
-    last = x0 - 1;
-    if (t.mode == 1) return;
-    const float lo = fmaxf(__fsub_rn(t.my, __fadd_rn((float)(16 * ty), 15.5f)), -t.ymax);
-    const float hi = fminf(__fsub_rn(t.my, __fadd_rn((float)(16 * ty), 0.5f)), t.ymax);
-    if (!(lo <= hi)) return;
-    const float yr = fminf(fmaxf(t.dyr, lo), hi), yl = fminf(fmaxf(-t.dyr, lo), hi);
-    const float sr = __fsqrt_rn(fmaxf(__fsub_rn(t.Atau, __fmul_rn(t.det, __fmul_rn(yr, yr))), 0.f));
-    const float sl = __fsqrt_rn(fmaxf(__fsub_rn(t.Atau, __fmul_rn(t.det, __fmul_rn(yl, yl))), 0.f));
-    const float xr = __fmul_rn(__fadd_rn(__fmul_rn(t.nB, yr), sr), t.rA);
-    const float xl = __fmul_rn(__fsub_rn(__fmul_rn(t.nB, yl), sl), t.rA);
-    // tile tx has offsets [mx - 16 tx - 15.5, mx - 16 tx - 0.5]
-    const float flo = __fmul_rn(__fsub_rn(__fsub_rn(t.mx, 15.5f), xr), 0.0625f);
-    const float fhi = __fmul_rn(__fsub_rn(__fsub_rn(t.mx, 0.5f), xl), 0.0625f);
-    first = (int)ceilf(fminf(fmaxf(flo, (float)x0), (float)(x1 + 1)));
-    last = (int)floorf(fminf(fmaxf(fhi, (float)(x0 - 1)), (float)x1));
+    return tight_rows(m.x, m.y, sv.conic[3 * (size_t)item], sv.conic[3 * (size_t)item + 1],
+                      sv.conic[3 * (size_t)item + 2], sv.power_min[g]);
 }
 
 // Per item: its tile count and depth key; the depth keys' four digit
@@ -430,7 +378,7 @@ __global__ void __launch_bounds__(kThreads) k_count(int n_items, const __grid_co
         uint32_t c = 0;
         if (tile_rect(m[q].x, m[q].y, r[q], vd.W, vd.H, x0, x1, y0, y1)) {
             if constexpr (TIGHT) {
-                const TightRows t = tight_rows(sv, mean2d, (uint32_t)i);
+                const TightRows t = item_tight_rows(sv, mean2d, (uint32_t)i);
                 for (int y = y0; y <= y1; ++y) {
                     int f, l;
                     tight_row(t, y, x0, x1, f, l);
@@ -601,7 +549,7 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(int n_items, const uint3
             tile_rect(m.x, m.y, radius[item[r]], vd.W, vd.H, x0, x1, y0, y1);
             tx = (uint32_t)vd.tiles_x;
             rowbase = (uint32_t)vd.tile_begin;
-            t = tight_rows(sv, mean2d, item[r]);
+            t = item_tight_rows(sv, mean2d, item[r]);
         }
         const uint64_t off = prefix + local[r];
         const bool big = c[r] > 32;

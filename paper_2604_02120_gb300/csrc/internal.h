@@ -83,6 +83,11 @@ struct CamViews {
 cudaError_t launch_project(int n, const float* means, const float* scales, const float* quats, const float* sh,
                            int sh_degree, const CamViews& cams, float* mean2d, float* conic, float* depth,
                            int* radius, float* rgb, uint32_t* tiles_touched, cudaStream_t s);
+// projection + per-tile lists in one cooperative launch (one view, small scenes)
+cudaError_t launch_project_bin_small(int n, const float* means, const float* scales, const float* quats,
+                                     const float* sh, int sh_degree, const CamViews& cams, const float* power_min,
+                                     int max_per_tile, float* mean2d, float* conic, float* depth, int* radius,
+                                     float* rgb, uint32_t* touched, uint32_t* ids, uint32_t* ranges, cudaStream_t s);
 // gradient of launch_project summed over the views (inputs view-major, outputs per Gaussian)
 cudaError_t launch_project_bwd(int n, const float* means, const float* scales, const float* quats, const float* sh,
                                int sh_degree, const CamViews& cams, const int* radius, const float* dmean2d,

@@ -31,6 +31,7 @@ ABI_FUNCTIONS = (
     "gs_selftest_bounded_wait", "gs_launch_count", "gs_bin_sort_noalloc", "gs_bin_sort_noalloc_max_bytes",
     "gs_project_views", "gs_bin_sort_views", "gs_blend_forward_views", "gs_blend_backward_views",
     "gs_blend_autotune", "gs_measure_peaks", "gs_alpha_power_min", "gs_project_backward",
+    "gs_project_bin_small",
 )
 
 
@@ -88,6 +89,8 @@ def load(path: str = LIB_PATH):
                                      vp, vp]
     lib.gs_bin_sort_views.argtypes = [i32, i32, vp, vp, vp, vp, vp, i32p, i32p, i64, vp, sz, vp, vp, vp, i64p, vp, vp]
     lib.gs_alpha_power_min.argtypes = [i32, vp, vp, vp]
+    lib.gs_project_bin_small.argtypes = [i32, vp, vp, vp, vp, i32, ctypes.POINTER(gs_camera), vp, i32, vp, vp, vp,
+                                         vp, vp, vp, vp, vp, vp]
     lib.gs_project_backward.argtypes = [i32, vp, vp, vp, vp, i32, ctypes.POINTER(gs_camera), i32, vp, vp, vp, vp,
                                         vp, vp, vp, vp, vp]
     lib.gs_blend_forward_views.argtypes = [i32, i32p, i32p, i32, vp, vp, vp, vp, vp, vp,
@@ -239,6 +242,38 @@ def gs_project_views(n, means, scales, quats, sh, sh_degree, cams, mean2d, conic
     _check(load().gs_project_views(n, _ptr(means), _ptr(scales), _ptr(quats), _ptr(sh), sh_degree, arr, len(cams),
                                    _ptr(mean2d), _ptr(conic), _ptr(depth), _ptr(radius), _ptr(rgb),
                                    _ptr(tiles_touched), _stream(stream)), "gs_project_views")
+
+
+def gs_project_bin_small(n, means, scales, quats, sh, sh_degree, cam, power_min, max_per_tile, mean2d, conic, depth,
+                         radius, rgb, tiles_touched, ids, tile_ranges, stream=None):
+    camera = cam if isinstance(cam, gs_camera) else make_camera(cam)
+    _check(load().gs_project_bin_small(n, _ptr(means), _ptr(scales), _ptr(quats), _ptr(sh), sh_degree,
+                                       ctypes.byref(camera), _ptr(power_min), int(max_per_tile), _ptr(mean2d),
+                                       _ptr(conic), _ptr(depth), _ptr(radius), _ptr(rgb), _ptr(tiles_touched),
+                                       _ptr(ids), _ptr(tile_ranges), _stream(stream)), "gs_project_bin_small")
+
+
+SMALL_MAX_PER_TILE = 16384
+
+
+def project_bin_small(means, scales, quats, sh, sh_degree, cam, max_per_tile=1024, power_min=None,
+                      stream=None):
+    """gs_project + per-tile lists in one cooperative launch (small scenes).
+    Returns (proj, bs): the gs_project outputs and a bin/sort dict
+    (tile_ranges, ids) that the blend calls take as gs_bin_sort's."""
+    n = means.shape[0]
+    dev = means.device
+    f32 = dict(device=dev, dtype=torch.float32)
+    proj = dict(mean2d=torch.empty(n, 2, **f32), conic=torch.empty(n, 3, **f32), depth=torch.empty(n, **f32),
+                radius=torch.empty(n, device=dev, dtype=torch.int32), rgb=torch.empty(n, 3, **f32),
+                tiles_touched=torch.empty(n, device=dev, dtype=torch.int32))
+    nt = num_tiles(cam.width, cam.height)
+    ids = torch.empty(nt * max_per_tile, device=dev, dtype=torch.int32)
+    ranges = torch.empty(2 * nt, device=dev, dtype=torch.int32)
+    gs_project_bin_small(n, means, scales, quats, sh, sh_degree, cam, power_min, max_per_tile, proj["mean2d"],
+                         proj["conic"], proj["depth"], proj["radius"], proj["rgb"], proj["tiles_touched"], ids, ranges,
+                         stream)
+    return proj, dict(tile_ranges=ranges, ids=ids)
 
 
 def gs_project_backward(n, means, scales, quats, sh, sh_degree, cams, radius, dmean2d, dconic, drgb, dmeans, dscales,

@@ -1,0 +1,109 @@
+"""Parity of gs_project_bin_small (projection + per-tile lists in one
+cooperative launch, for small scenes) with gs_project + gs_bin_sort and with
+the FP64 oracle's bin/sort, through the C ABI.
+
+Bars: projection outputs bit-identical to gs_project's; every tile's list
+bit-identical to gs_bin_sort's (full rectangles and opacity-aware) and to the
+oracle's; images blended from the fused lists bit-identical; a tile over
+max_per_tile reports GS_ERR_CAPACITY."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2604_02120_gb300 import gs, scenes
+
+from gpu_common import to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    gs.load()
+
+
+def _scene(kind):
+    if kind == "c0":
+        return scenes.make_config(0)
+    if kind == "c0_sh3":
+        return scenes.make_config(1, n=10_000)
+    if kind == "tiny_ragged":
+        return scenes.tiny_scene(3, n=96, width=77, height=45, sh_degree=2)
+    if kind == "tiny_dense":
+        return scenes.tiny_scene(8, n=600, width=64, height=48, sh_degree=3, scale_lo=-2.5, scale_hi=-1.2)
+    raise KeyError(kind)
+
+
+def _tile_lists(ranges, ids):
+    r = ranges.view(np.uint32).reshape(-1, 2)
+    return [ids[a:b].view(np.uint32).tolist() for a, b in r]
+
+
+@pytest.mark.parametrize("tight", [False, True])
+@pytest.mark.parametrize("kind", ["c0", "c0_sh3", "tiny_ragged", "tiny_dense"])
+def test_fused_lists_equal_bin_sort(kind, tight):
+    sc = _scene(kind)
+    cam = sc.cameras[0]
+    dev = gs.scene_to_device(sc)
+    pmin = gs.alpha_power_min(dev["opacities"]) if tight else None
+    fproj, fbs = gs.project_bin_small(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam,
+                                      max_per_tile=2048, power_min=pmin)
+    assert gs.gs_sync_status() == gs.GS_OK
+    proj = gs.project(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam)
+    for k in ("mean2d", "conic", "depth", "radius", "rgb", "tiles_touched"):
+        assert torch.equal(fproj[k], proj[k]), k
+    n = sc.n
+    if tight:
+        cap = 1 << 22
+        ws = torch.empty(gs.gs_bin_sort_workspace_size(n, cap, cam.width, cam.height) + 256, device="cuda",
+                         dtype=torch.uint8)
+        keys = torch.empty(cap, device="cuda", dtype=torch.int64)
+        ids = torch.empty(cap, device="cuda", dtype=torch.int32)
+        ranges = torch.empty(2 * cam.num_tiles, device="cuda", dtype=torch.int32)
+        _, count = gs.gs_bin_sort_views(1, n, proj["mean2d"], proj["radius"], proj["depth"], [cam.width],
+                                        [cam.height], cap, ws, keys, ids, ranges, conic=proj["conic"],
+                                        power_min=pmin)
+        bs = dict(tile_ranges=ranges, ids=ids[:count])
+    else:
+        bs = gs.BinSorter("cuda", 1 << 20).run(proj["mean2d"], proj["radius"], proj["depth"], cam.width, cam.height)
+    assert gs.gs_sync_status() == gs.GS_OK
+    got = _tile_lists(fbs["tile_ranges"].cpu().numpy(), fbs["ids"].cpu().numpy())
+    want = _tile_lists(bs["tile_ranges"].cpu().numpy(), bs["ids"].cpu().numpy())
+    assert got == want
+    pn = to_np(proj)
+    ref = oracle.bin_sort(pn["mean2d"].astype(np.float64), pn["radius"], pn["depth"], cam.width, cam.height,
+                          conic=pn["conic"] if tight else None,
+                          power_min=pmin.cpu().numpy() if tight else None)
+    assert got == _tile_lists(ref["tile_ranges"], ref["ids"])
+    assert sum(len(x) for x in got) > 0
+    # the blend takes the fused lists as they are
+    opts = gs.make_opts("fp16_split", bg=(0.1, 0.2, 0.3))
+    a = gs.blend_forward(cam.width, cam.height, bs, proj, dev["opacities"], opts)
+    b = gs.blend_forward(cam.width, cam.height, fbs, fproj, dev["opacities"], opts)
+    assert gs.gs_sync_status() == gs.GS_OK
+    for k in ("image", "T_final", "n_contrib"):
+        assert torch.equal(a[k], b[k]), k
+
+
+def test_fused_capacity_overflow_reports():
+    sc = _scene("tiny_dense")
+    cam = sc.cameras[0]
+    dev = gs.scene_to_device(sc)
+    assert gs.gs_sync_status() == gs.GS_OK
+    gs.project_bin_small(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam,
+                         max_per_tile=4)
+    assert gs.gs_sync_status() == gs.GS_ERR_CAPACITY
+    assert gs.gs_sync_status() == gs.GS_OK
+
+
+def test_fused_rejects_bad_arguments():
+    sc = _scene("tiny_ragged")
+    cam = sc.cameras[0]
+    dev = gs.scene_to_device(sc)
+    for mpt in (0, gs.SMALL_MAX_PER_TILE + 1):
+        with pytest.raises(gs.GsError):
+            gs.project_bin_small(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam,
+                                 max_per_tile=mpt)
