@@ -165,7 +165,6 @@ def run_ours(args):
     cam = sc.cameras[0]
     W, H = cam.width, cam.height
     dev = gs.scene_to_device(sc)
-    opts = gs.make_opts(args.variant)
     fp32 = gs.make_opts("fp32")
     dL = torch.from_numpy(scenes.upstream_grad(0, [cam])[0]).cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -185,6 +184,11 @@ def run_ours(args):
     # (and the forward outputs that index them) stay intact for the timings below
     t_keys, t_ids = torch.empty_like(keys), torch.empty_like(ids)
     t_ranges, t_count = torch.empty_like(ranges), torch.zeros_like(count_dev)
+    # longest tile lists first (gs_tile_order after every bin/sort)
+    order, t_order = torch.empty(gs.num_tiles(W, H), dtype=torch.int32, device="cuda"), \
+        torch.empty(gs.num_tiles(W, H), dtype=torch.int32, device="cuda")
+    opts = gs.make_opts(args.variant, tile_order=order)
+    t_opts = gs.make_opts(args.variant, tile_order=t_order)
 
     def step(ev=None, tight=False):
         if ev:
@@ -197,13 +201,15 @@ def run_ours(args):
         k_, i_, r_, c_ = (t_keys, t_ids, t_ranges, t_count) if tight else (keys, ids, ranges, count_dev)
         gs.gs_bin_sort_views(1, n, proj["mean2d"], proj["radius"], proj["depth"], [W], [H], capacity, ws, k_, i_,
                              r_, count_dev=c_, conic=proj["conic"] if tight else None, power_min=pmin)
+        o_ = t_opts if tight else opts
+        gs.tile_order(r_, [W], [H], out=t_order if tight else order)
         bs = dict(tile_ranges=r_, ids=i_)
         if ev:
             ev[2].record(stream)
-        fwd = gs.blend_forward(W, H, bs, proj, dev["opacities"], opts)
+        fwd = gs.blend_forward(W, H, bs, proj, dev["opacities"], o_)
         if ev:
             ev[3].record(stream)
-        g = gs.blend_backward(W, H, bs, proj, dev["opacities"], opts, fwd, dL)
+        g = gs.blend_backward(W, H, bs, proj, dev["opacities"], o_, fwd, dL)
         if ev:
             ev[4].record(stream)
         bs["n_instances"] = count0
@@ -303,13 +309,13 @@ def run_ours(args):
                        f"{len(pb_ev)}; peak = measured copy bandwidth"}
 
     # ---- small scene: projection + bin/sort fused into one cooperative launch
-    small_line = run_small_fused(gs, torch, opts, flush, min(K, 200))
+    small_line = run_small_fused(gs, torch, gs.make_opts(args.variant), flush, min(K, 200))
 
     # ---- blend-only ms/frame per variant (forward), tensor core vs FP32 CUDA core
     blend = {}
     if not args.quick:
         for name in ["fp32", "fp16", "bf16", "fp16_split", "bf16_split", "fp8_split"]:
-            o = gs.make_opts(name)
+            o = gs.make_opts(name, tile_order=order)  # the main step's lists and order
             for _ in range(3):
                 gs.blend_forward(W, H, bs, proj, dev["opacities"], o)
             times = []
@@ -370,7 +376,8 @@ def run_ours(args):
         "ms_per_step": dev_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.config] + WORKLOAD_NOTE, "blend_variant": args.variant,
-                   "step": "project + bin_sort + blend_forward + blend_backward",
+                   "step": "project + bin_sort + tile_order + blend_forward + blend_backward",
+                   "tile_order": "longest list first (gs_tile_order)",
                    "evals_per_step": evals_step, "instances": n_inst, "pixels": W * H,
                    "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replica x{ws_n}",
                    "bin_sort": "no host synchronisation (fixed capacity, count on the device)"},

@@ -92,6 +92,13 @@ typedef struct gs_blend_opts {
                             those tiles' contributions, so the sum over shards is the full
                             gradient.  0 or 1 = all tiles */
     int32_t shard_index; /* 0 <= shard_index < max(1, shard_count) */
+    const uint32_t* tile_order; /* NULL: tiles in id order.  Else a DEVICE array, a permutation of the
+                                   call's global tile ids (e.g. from gs_tile_order): the kernels take
+                                   the tile at position p of it in place of tile p, so persistent
+                                   blocks start on the longest lists; with sharding, a shard takes the
+                                   positions p with p % shard_count == shard_index.  It must have one
+                                   entry per tile of the call; an entry >= the tile count is clamped
+                                   (a wrong image, never an access outside the tile ranges) */
 } gs_blend_opts;
 
 /* Library version (major * 100 + minor). */
@@ -254,6 +261,20 @@ gs_status gs_bin_sort_views(int32_t n_views, int32_t n_per_view, const float* me
                             void* workspace, size_t workspace_bytes, uint64_t* keys_sorted, uint32_t* ids_sorted,
                             uint32_t* tile_ranges, int64_t* n_instances, int64_t* n_instances_dev,
                             gs_stream stream);
+
+/*
+ * gs_tile_order - the global tile ids of n_views views (widths/heights HOST
+ * arrays, as gs_bin_sort_views) ordered longest list first, from a sorted
+ * list's tile_ranges, into tile_order (one uint32 per tile) for
+ * gs_blend_opts.tile_order (not in the paper: a scheduling aid).  Persistent
+ * blend blocks take tiles from a queue; taking the longest lists first keeps
+ * the last blocks from finishing long after the others.  Buckets of a
+ * quarter octave of list length, longest bucket first; the order within a
+ * bucket is unspecified (the images do not depend on it).  One block, one
+ * launch; asynchronous.
+ */
+gs_status gs_tile_order(int32_t n_views, const int32_t* widths, const int32_t* heights, const uint32_t* tile_ranges,
+                        uint32_t* tile_order, gs_stream stream);
 
 /* power_min[g] = ln(1 / (255 opacity[g])) - 2e-3 (+inf when opacity < 1.0f/255.0f)
  * for n Gaussians: the exponent a splat must reach somewhere in a tile for

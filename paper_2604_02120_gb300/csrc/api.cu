@@ -121,6 +121,8 @@ bool make_args(BlendArgs& a, int32_t n_views, const int32_t* widths, const int32
     a.shard_count = (o && o->shard_count > 1) ? o->shard_count : 1;
     a.shard_index = o ? o->shard_index : 0;
     if (a.shard_index < 0 || a.shard_index >= a.shard_count) return false;
+    a.order = o ? o->tile_order : nullptr;
+    a.order_tiles = a.total_tiles;
     a.err = error_word();
     return true;
 }
@@ -278,6 +280,25 @@ gs_status gs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t width,
     }
     *bytes = bin_sort_workspace_bytes(n, capacity, tiles_x(width) * tiles_y(height));
     return GS_OK;
+}
+
+gs_status gs_tile_order(int32_t n_views, const int32_t* widths, const int32_t* heights, const uint32_t* tile_ranges,
+                        uint32_t* tile_order, gs_stream stream) {
+    g_last_error[0] = 0;
+    gs_status st = check_views("gs_tile_order", n_views, widths, heights);
+    if (st != GS_OK) return st;
+    ViewDesc views[kMaxViews];
+    int total = 0;
+    if (!fill_views(n_views, widths, heights, views, &total)) {
+        set_error("gs_tile_order: bad views");
+        return GS_ERR_INVALID_ARG;
+    }
+    if (!tile_ranges || !tile_order) {
+        set_error("gs_tile_order: null pointer");
+        return GS_ERR_INVALID_ARG;
+    }
+    return cuda_status(launch_tile_order(total, tile_ranges, tile_order, static_cast<cudaStream_t>(stream)),
+                       "gs_tile_order");
 }
 
 gs_status gs_alpha_power_min(int32_t n, const float* opacity, float* power_min, gs_stream stream) {

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kBatch) k_blend_fp32_fwd(const __grid_constant
     __shared__ float4 s_geo[kBatch];
     __shared__ float4 s_oc[kBatch];
     __shared__ float s_b[kBatch];
-    const int tile = blockIdx.x * a.shard_count + a.shard_index;
+    const int tile = tile_at(a, blockIdx.x * a.shard_count + a.shard_index);
     const TileGeo tg = tile_geo(a, tile);
     const int px = tg.px, py = tg.py;
     const bool inside = px < tg.W && py < tg.H;
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kBatch) k_blend_fp32_bwd(const __grid_constant
     __shared__ float s_b[kBatch];
     __shared__ uint32_t s_id[kBatch];
     __shared__ int s_max;
-    const int tile = blockIdx.x * a.shard_count + a.shard_index;
+    const int tile = tile_at(a, blockIdx.x * a.shard_count + a.shard_index);
     const TileGeo tg = tile_geo(a, tile);
     const int px = tg.px, py = tg.py;
     const bool inside = px < tg.W && py < tg.H;

@@ -551,7 +551,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
             uint32_t start = 0;
             float xc = 0.f, yc_up = 0.f;
             if (!end) {
-                tile = DUMP ? a.tiles[q] : q * a.shard_count + a.shard_index;
+                tile = DUMP ? a.tiles[q] : tile_at(a, q * a.shard_count + a.shard_index);
                 start = a.ranges[2 * tile];
                 const uint32_t stop = a.ranges[2 * tile + 1];
                 len = stop > start ? (int)(stop - start) : 0;

@@ -8,7 +8,7 @@ cudaError_t launch_blend_tc_bwd(const BlendArgs& a0, const GradArgs& g, int vari
     cudaError_t e = cudaSuccess;
     a.queue = tile_queue_slot(s, &e);
     if (a.queue == nullptr) return e;
-    a.total_tiles = shard_items(a0);  // queue length; item q is tile q * shard_count + shard_index
+    a.total_tiles = shard_items(a0);  // queue length; item q is position q * shard_count + shard_index of the order
     switch (variant) {
         case GS_BLEND_TC_FP16: return tc::launch_bwd_variant<GS_BLEND_TC_FP16>(a, g, s);
         case GS_BLEND_TC_BF16: return tc::launch_bwd_variant<GS_BLEND_TC_BF16>(a, g, s);

@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
             float xc = 0.f, yc_up = 0.f;
             BwdHdr hd{};
             if (!end) {
-                tile = qi * a.shard_count + a.shard_index;
+                tile = tile_at(a, qi * a.shard_count + a.shard_index);
                 start = a.ranges[2 * tile];
                 const uint32_t stop = a.ranges[2 * tile + 1];
                 len = stop > start ? (int)(stop - start) : 0;

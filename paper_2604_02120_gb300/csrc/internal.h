@@ -43,12 +43,23 @@ struct BlendArgs {
     unsigned* err;
     uint64_t timeout_ns;
     int ref_origin;
-    int shard_count, shard_index;  // tiles t with t % shard_count == shard_index; queue item q is tile q * count + index
+    int shard_count, shard_index;  // queue item q takes position p = q * count + index of the tile order
+    const uint32_t* order;         // the tile at position p: order[p] (nullptr: tile p)
+    int order_tiles;               // the call's tile count; order entries are clamped below it
     // gs_tile_power only
     const int* tiles;
     int max_len;
     float* dump;
 };
+
+// The tile at position p of the call's tile order.
+// A bad order entry is clamped, so a corrupt order gives a wrong image, never
+// an access outside the tile ranges.
+__host__ __device__ inline int tile_at(const BlendArgs& a, int p) {
+    if (!a.order) return p;
+    const uint32_t t = a.order[p];
+    return t < (uint32_t)a.order_tiles ? (int)t : a.order_tiles - 1;
+}
 
 // Number of the call's tiles in its shard.
 inline int shard_items(const BlendArgs& a) {
@@ -83,6 +94,8 @@ struct CamViews {
 cudaError_t launch_project(int n, const float* means, const float* scales, const float* quats, const float* sh,
                            int sh_degree, const CamViews& cams, float* mean2d, float* conic, float* depth,
                            int* radius, float* rgb, uint32_t* tiles_touched, cudaStream_t s);
+// tiles by decreasing list length (a permutation of 0..ntiles-1)
+cudaError_t launch_tile_order(int ntiles, const uint32_t* ranges, uint32_t* order, cudaStream_t s);
 // projection + per-tile lists in one cooperative launch (one view, small scenes)
 cudaError_t launch_project_bin_small(int n, const float* means, const float* scales, const float* quats,
                                      const float* sh, int sh_degree, const CamViews& cams, const float* power_min,

@@ -31,7 +31,7 @@ ABI_FUNCTIONS = (
     "gs_selftest_bounded_wait", "gs_launch_count", "gs_bin_sort_noalloc", "gs_bin_sort_noalloc_max_bytes",
     "gs_project_views", "gs_bin_sort_views", "gs_blend_forward_views", "gs_blend_backward_views",
     "gs_blend_autotune", "gs_measure_peaks", "gs_alpha_power_min", "gs_project_backward",
-    "gs_project_bin_small",
+    "gs_project_bin_small", "gs_tile_order",
 )
 
 
@@ -55,7 +55,8 @@ class gs_camera(ctypes.Structure):
 class gs_blend_opts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("chunk", ctypes.c_int32), ("stages", ctypes.c_int32),
                 ("ref_origin", ctypes.c_int32), ("bg", ctypes.c_float * 3), ("reserved", ctypes.c_int32),
-                ("timeout_ns", ctypes.c_int64), ("shard_count", ctypes.c_int32), ("shard_index", ctypes.c_int32)]
+                ("timeout_ns", ctypes.c_int64), ("shard_count", ctypes.c_int32), ("shard_index", ctypes.c_int32),
+                ("tile_order", ctypes.c_void_p)]
 
 
 _lib = None
@@ -89,6 +90,7 @@ def load(path: str = LIB_PATH):
                                      vp, vp]
     lib.gs_bin_sort_views.argtypes = [i32, i32, vp, vp, vp, vp, vp, i32p, i32p, i64, vp, sz, vp, vp, vp, i64p, vp, vp]
     lib.gs_alpha_power_min.argtypes = [i32, vp, vp, vp]
+    lib.gs_tile_order.argtypes = [i32, i32p, i32p, vp, vp, vp]
     lib.gs_project_bin_small.argtypes = [i32, vp, vp, vp, vp, i32, ctypes.POINTER(gs_camera), vp, i32, vp, vp, vp,
                                          vp, vp, vp, vp, vp, vp]
     lib.gs_project_backward.argtypes = [i32, vp, vp, vp, vp, i32, ctypes.POINTER(gs_camera), i32, vp, vp, vp, vp,
@@ -143,7 +145,10 @@ def make_camera(cam) -> gs_camera:
 
 
 def make_opts(variant="fp32", chunk=0, stages=0, ref_origin=0, bg=(0.0, 0.0, 0.0), timeout_ns=0, shard_count=0,
-              shard_index=0) -> gs_blend_opts:
+              shard_index=0, tile_order=None) -> gs_blend_opts:
+    """Blend options; tile_order (a device tensor from tile_order(), kept
+    alive by the caller while the options are used) makes the kernels take
+    the longest tile lists first."""
     o = gs_blend_opts()
     o.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     o.chunk, o.stages, o.ref_origin = int(chunk), int(stages), int(ref_origin)
@@ -151,6 +156,7 @@ def make_opts(variant="fp32", chunk=0, stages=0, ref_origin=0, bg=(0.0, 0.0, 0.0
         o.bg[i] = float(bg[i])
     o.timeout_ns = int(timeout_ns)
     o.shard_count, o.shard_index = int(shard_count), int(shard_index)
+    o.tile_order = None if tile_order is None else tile_order.data_ptr()
     return o
 
 
@@ -254,6 +260,18 @@ def gs_project_bin_small(n, means, scales, quats, sh, sh_degree, cam, power_min,
 
 
 SMALL_MAX_PER_TILE = 16384
+
+
+def gs_tile_order(widths, heights, tile_ranges, order, stream=None):
+    _check(load().gs_tile_order(len(widths), _i32arr(widths), _i32arr(heights), _ptr(tile_ranges), _ptr(order),
+                                _stream(stream)), "gs_tile_order")
+
+
+def tile_order(tile_ranges, widths, heights, out=None, stream=None):
+    """Global tile ids, longest list first (gs_tile_order), for make_opts(tile_order=...)."""
+    out = torch.empty(tile_ranges.numel() // 2, device=tile_ranges.device, dtype=torch.int32) if out is None else out
+    gs_tile_order(list(widths), list(heights), tile_ranges, out, stream)
+    return out
 
 
 def project_bin_small(means, scales, quats, sh, sh_degree, cam, max_per_tile=1024, power_min=None,
@@ -497,12 +515,13 @@ class BatchRenderer:
     -> gs_blend_backward_views.  All buffers are allocated once for a fixed
     instance capacity, so `step` can be captured in a CUDA graph (`capture`);
     an instance count above the capacity is reported by gs_sync_status() as
-    GS_ERR_CAPACITY."""
+    GS_ERR_CAPACITY.  With longest_first the blends take the tiles in the
+    order of gs_tile_order (longest list first), computed after every sort."""
 
-    def __init__(self, dev_scene, cams, opts, capacity, device="cuda"):
+    def __init__(self, dev_scene, cams, opts, capacity, device="cuda", longest_first=True):
         self.scene = dev_scene
         self.cams = [make_camera(c) for c in cams]
-        self.opts = opts
+        self.opts = gs_blend_opts.from_buffer_copy(opts)
         self.widths = [c.width for c in self.cams]
         self.heights = [c.height for c in self.cams]
         V, n = len(self.cams), int(dev_scene["means"].shape[0])
@@ -520,6 +539,8 @@ class BatchRenderer:
         self.keys = torch.empty(max(self.capacity, 1), device=device, dtype=torch.int64)
         self.ids = torch.empty(max(self.capacity, 1), **i32)
         self.ranges = torch.empty(2 * self.total_tiles, **i32)
+        self.order = torch.empty(self.total_tiles, **i32) if longest_first else None
+        self.opts.tile_order = self.order.data_ptr() if longest_first else opts.tile_order
         self.count = torch.zeros(1, device=device, dtype=torch.int64)
         ws = gs_bin_sort_workspace_size(V * n, self.capacity, self.widths[0], self.heights[0])
         self.workspace = torch.empty(ws + 256, device=device, dtype=torch.uint8)
@@ -540,6 +561,8 @@ class BatchRenderer:
         gs_bin_sort_views(self.V, self.n, self.mean2d, self.radius, self.depth, self.widths, self.heights,
                           self.capacity, self.workspace, self.keys, self.ids, self.ranges, count_dev=self.count,
                           stream=stream)
+        if self.order is not None:
+            gs_tile_order(self.widths, self.heights, self.ranges, self.order, stream)
         gs_blend_forward_views(self.widths, self.heights, self.n, self.ranges, self.ids, self.mean2d, self.conic,
                                sc["opacities"], self.rgb, self.opts, self.image, self.T, self.nc, stream)
 

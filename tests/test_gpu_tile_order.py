@@ -1,0 +1,89 @@
+"""gs_tile_order (longest tile list first) and gs_blend_opts.tile_order.
+
+The order is a permutation of the tile ids whose length buckets never
+increase; blending in that order gives bit for bit the same image, T_final
+and n_contrib as in id order (each tile is one block's work), and the same
+gradients up to the order of the atomic additions; with sharding the shards
+still cover every pixel once."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2604_02120_gb300 import gs, scenes
+
+from gpu_common import gpu_pipeline, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    gs.load()
+
+
+def _bucket(lens):
+    lens = np.asarray(lens, np.int64)
+    out = lens.copy()
+    big = lens >= 4
+    lg = np.floor(np.log2(np.maximum(lens, 1))).astype(np.int64)
+    out[big] = 4 * lg[big] + ((lens[big] >> (lg[big] - 2)) & 3) - 4
+    return out
+
+
+@pytest.mark.parametrize("kind", ["c0", "c1_small"])
+def test_tile_order_is_longest_first_permutation(kind):
+    sc = scenes.make_config(0) if kind == "c0" else scenes.make_config(1, n=20_000)
+    dev, cam, proj, bs = gpu_pipeline(sc)
+    order = gs.tile_order(bs["tile_ranges"], [cam.width], [cam.height]).cpu().numpy()
+    assert gs.gs_sync_status() == gs.GS_OK
+    r = bs["tile_ranges"].cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+    lens = r[:, 1] - r[:, 0]
+    assert sorted(order.tolist()) == list(range(cam.num_tiles))
+    b = _bucket(lens[order])
+    assert (np.diff(b) <= 0).all()
+    assert b[0] == _bucket([lens.max()])[0]  # the first tile is in the longest lists' bucket
+
+
+@pytest.mark.parametrize("variant", ["fp32", "fp16_split"])
+def test_ordered_blend_equals_id_order(variant):
+    sc = scenes.make_config(1, n=20_000)
+    dev, cam, proj, bs = gpu_pipeline(sc)
+    order = gs.tile_order(bs["tile_ranges"], [cam.width], [cam.height])
+    bg = (0.2, 0.1, 0.05)
+    plain = gs.make_opts(variant, bg=bg)
+    ordered = gs.make_opts(variant, bg=bg, tile_order=order)
+    a = gs.blend_forward(cam.width, cam.height, bs, proj, dev["opacities"], plain)
+    b = gs.blend_forward(cam.width, cam.height, bs, proj, dev["opacities"], ordered)
+    for k in ("image", "T_final", "n_contrib"):
+        assert torch.equal(a[k], b[k]), k
+    dL = torch.randn(3, cam.height, cam.width, device="cuda", generator=torch.Generator("cuda").manual_seed(2))
+    ga = to_np(gs.blend_backward(cam.width, cam.height, bs, proj, dev["opacities"], plain, a, dL))
+    gb = to_np(gs.blend_backward(cam.width, cam.height, bs, proj, dev["opacities"], ordered, b, dL))
+    assert gs.gs_sync_status() == gs.GS_OK
+    for k in ga:
+        np.testing.assert_allclose(gb[k], ga[k], rtol=1e-4, atol=1e-6 * np.abs(ga[k]).max())
+
+
+def test_ordered_shards_cover_every_pixel_once():
+    sc = scenes.make_config(0)
+    dev, cam, proj, bs = gpu_pipeline(sc)
+    order = gs.tile_order(bs["tile_ranges"], [cam.width], [cam.height])
+    full = gs.blend_forward(cam.width, cam.height, bs, proj, dev["opacities"], gs.make_opts("fp16_split"))
+    seen = torch.zeros(cam.height, cam.width, device="cuda", dtype=torch.int32)
+    img = torch.zeros_like(full["image"])
+    for k in range(3):
+        o = gs.make_opts("fp16_split", shard_count=3, shard_index=k, tile_order=order)
+        out = gs.blend_forward(cam.width, cam.height, bs, proj, dev["opacities"], o)
+        touched = torch.zeros_like(seen)
+        ordn = order.cpu().numpy()
+        for p in range(k, cam.num_tiles, 3):
+            t = int(ordn[p])
+            ty, tx = divmod(t, cam.tiles_x)
+            touched[16 * ty:16 * ty + 16, 16 * tx:16 * tx + 16] = 1
+        seen += touched
+        img += out["image"] * touched
+    assert gs.gs_sync_status() == gs.GS_OK
+    assert (seen == 1).all()
+    assert torch.equal(img, full["image"])
