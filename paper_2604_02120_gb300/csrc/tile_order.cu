@@ -14,6 +14,7 @@ namespace {
 
 constexpr int kOrderThreads = 1024;
 constexpr int kBuckets = 4 * 32;
+constexpr int kOrderBatch = 8;
 
 __device__ __forceinline__ int length_bucket(uint32_t len) {
     if (len < 4) return (int)len;
@@ -26,22 +27,53 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(int ntiles, const 
     __shared__ unsigned s_count[kBuckets], s_next[kBuckets];
     for (int b = threadIdx.x; b < kBuckets; b += kOrderThreads) s_count[b] = 0;
     __syncthreads();
-    for (int t = threadIdx.x; t < ntiles; t += kOrderThreads) {
-        const uint32_t a = ranges[2 * t], b = ranges[2 * t + 1];
-        atomicAdd(&s_count[length_bucket(b > a ? b - a : 0u)], 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {  // longest bucket first
-        unsigned acc = 0;
-        for (int b = kBuckets - 1; b >= 0; --b) {
-            s_next[b] = acc;
-            acc += s_count[b];
+    const int lane = threadIdx.x & 31;
+    // kOrderBatch tiles per thread and round, all loads issued before any use;
+    // one shared atomic per distinct bucket in a warp (most tiles share a few)
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int t0 = 0; t0 < ntiles; t0 += kOrderThreads * kOrderBatch) {
+            uint2 rg[kOrderBatch];
+#pragma unroll
+            for (int u = 0; u < kOrderBatch; ++u) {
+                const int t = t0 + u * kOrderThreads + (int)threadIdx.x;
+                rg[u] = t < ntiles ? make_uint2(ranges[2 * t], ranges[2 * t + 1]) : make_uint2(0u, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < kOrderBatch; ++u) {
+                const int t = t0 + u * kOrderThreads + (int)threadIdx.x;
+                const bool ok = t < ntiles;
+                const int bk = ok ? length_bucket(rg[u].y > rg[u].x ? rg[u].y - rg[u].x : 0u) : -1;
+                const unsigned peers = __match_any_sync(0xffffffffu, bk);
+                const int leader = __ffs(peers) - 1;
+                if (pass == 0) {
+                    if (ok && lane == leader) atomicAdd(&s_count[bk], (unsigned)__popc(peers));
+                } else {
+                    unsigned base = 0;
+                    if (ok && lane == leader) base = atomicAdd(&s_next[bk], (unsigned)__popc(peers));
+                    base = __shfl_sync(0xffffffffu, base, leader);
+                    if (ok) order[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)t;
+                }
+            }
         }
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < ntiles; t += kOrderThreads) {
-        const uint32_t a = ranges[2 * t], b = ranges[2 * t + 1];
-        order[atomicAdd(&s_next[length_bucket(b > a ? b - a : 0u)], 1u)] = (uint32_t)t;
+        __syncthreads();
+        if (pass == 0 && threadIdx.x < 32) {  // longest bucket first: lane l takes buckets from the top down
+            unsigned c[kBuckets / 32], sum = 0;
+#pragma unroll
+            for (int i = 0; i < kBuckets / 32; ++i) sum += (c[i] = s_count[kBuckets - 1 - (kBuckets / 32) * lane - i]);
+            unsigned incl = sum;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned v = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += v;
+            }
+            unsigned acc = incl - sum;
+#pragma unroll
+            for (int i = 0; i < kBuckets / 32; ++i) {
+                s_next[kBuckets - 1 - (kBuckets / 32) * lane - i] = acc;
+                acc += c[i];
+            }
+        }
+        __syncthreads();
     }
 }
 
