@@ -176,13 +176,12 @@ def run_ours(args):
     capacity = int(count0 * 1.25) + 4096
     n = sc.n
     ws = torch.empty(gs.gs_bin_sort_workspace_size(n, capacity, W, H) + 256, dtype=torch.uint8, device="cuda")
-    keys = torch.empty(capacity, dtype=torch.int64, device="cuda")
-    ids = torch.empty(capacity, dtype=torch.int32, device="cuda")
+    ids = torch.empty(capacity, dtype=torch.int32, device="cuda")  # the blends need no sorted keys
     ranges = torch.empty(2 * gs.num_tiles(W, H), dtype=torch.int32, device="cuda")
     count_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
     # the opacity-aware step sorts into buffers of its own, so the full lists
     # (and the forward outputs that index them) stay intact for the timings below
-    t_keys, t_ids = torch.empty_like(keys), torch.empty_like(ids)
+    t_ids = torch.empty_like(ids)
     t_ranges, t_count = torch.empty_like(ranges), torch.zeros_like(count_dev)
     # longest tile lists first (gs_tile_order after every bin/sort)
     order, t_order = torch.empty(gs.num_tiles(W, H), dtype=torch.int32, device="cuda"), \
@@ -198,8 +197,8 @@ def run_ours(args):
             ev[1].record(stream)
         # opacity-aware lists: the exponent each splat must reach in a tile (gs_alpha_power_min)
         pmin = gs.alpha_power_min(dev["opacities"]) if tight else None
-        k_, i_, r_, c_ = (t_keys, t_ids, t_ranges, t_count) if tight else (keys, ids, ranges, count_dev)
-        gs.gs_bin_sort_views(1, n, proj["mean2d"], proj["radius"], proj["depth"], [W], [H], capacity, ws, k_, i_,
+        i_, r_, c_ = (t_ids, t_ranges, t_count) if tight else (ids, ranges, count_dev)
+        gs.gs_bin_sort_views(1, n, proj["mean2d"], proj["radius"], proj["depth"], [W], [H], capacity, ws, None, i_,
                              r_, count_dev=c_, conic=proj["conic"] if tight else None, power_min=pmin)
         o_ = t_opts if tight else opts
         gs.tile_order(r_, [W], [H], out=t_order if tight else order)
@@ -414,7 +413,6 @@ def run_small_fused(gs, torch, opts, flush, K):
     stream = torch.cuda.current_stream()
     capacity = 1 << 20
     ws = torch.empty(gs.gs_bin_sort_workspace_size(n, capacity, W, H) + 256, dtype=torch.uint8, device="cuda")
-    keys = torch.empty(capacity, dtype=torch.int64, device="cuda")
     ids = torch.empty(capacity, dtype=torch.int32, device="cuda")
     ranges = torch.empty(2 * gs.num_tiles(W, H), dtype=torch.int32, device="cuda")
     count = torch.zeros(1, dtype=torch.int64, device="cuda")
@@ -422,7 +420,7 @@ def run_small_fused(gs, torch, opts, flush, K):
 
     def unfused():
         proj = gs.project(*args3)
-        gs.gs_bin_sort_views(1, n, proj["mean2d"], proj["radius"], proj["depth"], [W], [H], capacity, ws, keys, ids,
+        gs.gs_bin_sort_views(1, n, proj["mean2d"], proj["radius"], proj["depth"], [W], [H], capacity, ws, None, ids,
                              ranges, count_dev=count)
         return proj, dict(tile_ranges=ranges, ids=ids)
 

@@ -212,7 +212,9 @@ gs_status gs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t width,
  * (the rule of gs_project) with key (tile << 32) | float_bits(depth); the
  * instances are sorted by key, equal keys in Gaussian-index order (the order a
  * stable sort of the Gaussian-major, row-major-tile duplication gives).
- *   keys_sorted[capacity] (u64), ids_sorted[capacity] (u32 Gaussian index),
+ *   keys_sorted[capacity] (u64; may be NULL: the blend calls read only the
+ *   ids and ranges, and without keys the last kernel writes 8 bytes less
+ *   per instance), ids_sorted[capacity] (u32 Gaussian index),
  *   tile_ranges[2 * num_tiles] (u32 [start, end) per tile, empty = [0, 0)).
  *   workspace: device scratch of at least gs_bin_sort_workspace_size() bytes,
  *   256-byte aligned; its contents on entry do not matter.

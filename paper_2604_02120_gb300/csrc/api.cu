@@ -342,7 +342,7 @@ gs_status gs_bin_sort_views(int32_t n_views, int32_t n_per_view, const float* me
         set_error("gs_bin_sort: null pointer");
         return GS_ERR_INVALID_ARG;
     }
-    if (capacity > 0 && (!keys_sorted || !ids_sorted)) {
+    if (capacity > 0 && !ids_sorted) {
         set_error("gs_bin_sort: null output pointer");
         return GS_ERR_INVALID_ARG;
     }

@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(int n_items, const uint3
         if (s_h[i]) atomicAdd(&hist[256 + i], s_h[i]);
 }
 
-// Sorted keys, ids and tile ranges.  Tile ids and item indices are checked
+// Sorted keys (if asked for), ids and tile ranges.  Tile ids and item indices are checked
 // against their bounds: after a look-back that gave up (timeout bit set) the
 // passes can leave stale entries, which become item 0 and no range.
 __global__ void k_finalize(uint32_t I_host, const uint64_t* __restrict__ I_dev, const uint32_t* __restrict__ tkey,
@@ -647,7 +647,7 @@ __global__ void k_finalize(uint32_t I_host, const uint64_t* __restrict__ I_dev, 
     if (i >= I) return;
     const uint32_t t = tkey[i];
     const uint32_t g = tval[i] < n_items ? tval[i] : 0u;
-    keys_sorted[i] = ((uint64_t)t << 32) | __float_as_uint(depth[g]);
+    if (keys_sorted != nullptr) keys_sorted[i] = ((uint64_t)t << 32) | __float_as_uint(depth[g]);
     ids_sorted[i] = g;
     if (t >= num_tiles) return;
     if (i == 0 || tkey[i - 1] != t) ranges[2 * t] = i;

@@ -67,7 +67,7 @@ gs_status gs_bin_sort_noalloc(int32_t n, const float* mean2d, const int32_t* rad
         set_error("gs_bin_sort_noalloc: null pointer");
         return GS_ERR_INVALID_ARG;
     }
-    if (capacity > 0 && (!keys_sorted || !ids_sorted)) {
+    if (capacity > 0 && !ids_sorted) {
         set_error("gs_bin_sort_noalloc: null output pointer");
         return GS_ERR_INVALID_ARG;
     }

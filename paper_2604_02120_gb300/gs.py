@@ -536,7 +536,6 @@ class BatchRenderer:
         self.touched = torch.empty(V * n, **i32)
         self.total_tiles = sum(num_tiles(w, h) for w, h in zip(self.widths, self.heights))
         self.pixels = sum(w * h for w, h in zip(self.widths, self.heights))
-        self.keys = torch.empty(max(self.capacity, 1), device=device, dtype=torch.int64)
         self.ids = torch.empty(max(self.capacity, 1), **i32)
         self.ranges = torch.empty(2 * self.total_tiles, **i32)
         self.order = torch.empty(self.total_tiles, **i32) if longest_first else None
@@ -559,7 +558,7 @@ class BatchRenderer:
         gs_project_views(self.n, sc["means"], sc["scales"], sc["quats"], sc["sh"], sc["sh_degree"], self.cams,
                          self.mean2d, self.conic, self.depth, self.radius, self.rgb, self.touched, stream)
         gs_bin_sort_views(self.V, self.n, self.mean2d, self.radius, self.depth, self.widths, self.heights,
-                          self.capacity, self.workspace, self.keys, self.ids, self.ranges, count_dev=self.count,
+                          self.capacity, self.workspace, None, self.ids, self.ranges, count_dev=self.count,
                           stream=stream)
         if self.order is not None:
             gs_tile_order(self.widths, self.heights, self.ranges, self.order, stream)

@@ -547,3 +547,22 @@ def test_blend_tc_never_sits_out_a_wait_limit(chunk, stages):
     torch.cuda.synchronize()
     assert (time.perf_counter() - t0) / 3 < 0.05
     assert gs.gs_sync_status() == gs.GS_OK
+
+
+def test_bin_sort_without_keys_gives_the_same_lists():
+    """keys_sorted is optional: with NULL the ids and tile ranges are those of
+    the call that writes keys (graph mode, count on the device)."""
+    sc, dev, cam, proj, bs, pn, bn = pipeline("c1_small")
+    n, cap = sc.n, 1 << 21
+    ws = torch.empty(gs.gs_bin_sort_workspace_size(n, cap, cam.width, cam.height) + 256, device="cuda",
+                     dtype=torch.uint8)
+    ids = torch.empty(cap, device="cuda", dtype=torch.int32)
+    ranges = torch.empty(2 * cam.num_tiles, device="cuda", dtype=torch.int32)
+    count = torch.zeros(1, device="cuda", dtype=torch.int64)
+    gs.gs_bin_sort_views(1, n, proj["mean2d"], proj["radius"], proj["depth"], [cam.width], [cam.height], cap, ws,
+                         None, ids, ranges, count_dev=count)
+    assert gs.gs_sync_status() == gs.GS_OK
+    c = int(count.item())
+    assert c == bn["n_instances"]
+    np.testing.assert_array_equal(ids[:c].cpu().numpy(), bn["ids"])
+    np.testing.assert_array_equal(ranges.cpu().numpy(), bn["tile_ranges"])

@@ -78,7 +78,6 @@ def test_graph_mode_bin_sort_matches_synchronising_mode_and_reports_overflow():
     st, c2 = gs.gs_bin_sort_views(br.V, br.n, br.mean2d, br.radius, br.depth, br.widths, br.heights, 1 << 17,
                                   br.workspace, keys, ids, ranges)
     assert st == gs.GS_OK and c2 == count > 0
-    torch.testing.assert_close(keys[:count], br.keys[:count], rtol=0, atol=0)
     torch.testing.assert_close(ids[:count], br.ids[:count], rtol=0, atol=0)
     torch.testing.assert_close(ranges, br.ranges, rtol=0, atol=0)
     # graph mode with too small a capacity: count reported, error word set
