@@ -508,6 +508,72 @@ def render(dev_scene, cam, opts, sorter: BinSorter | None = None, stream=None) -
     return dict(project=proj, bin_sort=bs, blend=out)
 
 
+class PipelinedRenderer:
+    """Forward + backward of a stream of frames whose inputs live in (pinned)
+    host memory, with the copies overlapped: frame k's host-to-device copy
+    runs on an upload stream while frame k-1 computes, and its results go
+    back on a download stream while frame k+1 computes, so a frame costs
+    about max(compute, copies) instead of their sum.  Two BatchRenderers
+    alternate (double-buffered device inputs and outputs); compute runs on
+    the current stream.  The frames must be independent (rendering many
+    scenes or camera sets): a training loop, whose next inputs depend on this
+    step's gradients, gains nothing from it.
+
+    submit(k, host_in, host_out) enqueues frame k: host_in maps
+    means/scales/quats/opacities/sh to pinned tensors shaped like the scene,
+    host_out maps image/mean2d/conic/opacity/rgb to pinned tensors shaped
+    like the renderer's outputs; wait(k) blocks until frame k's results are
+    in host_out."""
+
+    KEYS = ("means", "scales", "quats", "opacities", "sh")
+
+    def __init__(self, template_scene, sh_degree, cams, opts, capacity, dL, device="cuda"):
+        self.r = []
+        for _ in range(2):
+            dev = {k: torch.empty_like(template_scene[k], device=device) for k in self.KEYS}
+            dev["sh_degree"] = sh_degree
+            r = BatchRenderer(dev, cams, opts, capacity, device)
+            r.dL.copy_(dL.reshape(-1))
+            self.r.append(r)
+        self.up, self.down = torch.cuda.Stream(device), torch.cuda.Stream(device)
+        E = torch.cuda.Event
+        self.in_ready = [E(), E()]
+        self.done = [E(), E()]
+        self.out_done = [E(), E()]
+        self.used = [False, False]
+        self.frame_slot = {}
+
+    def submit(self, k, host_in, host_out):
+        i = k % 2
+        r = self.r[i]
+        cur = torch.cuda.current_stream()
+        with torch.cuda.stream(self.up):
+            if self.used[i]:
+                self.up.wait_event(self.done[i])  # the last frame on these buffers has read its inputs
+            for key in self.KEYS:
+                r.scene[key].copy_(host_in[key], non_blocking=True)
+            self.in_ready[i].record(self.up)
+        cur.wait_event(self.in_ready[i])
+        if self.used[i]:
+            cur.wait_event(self.out_done[i])  # its results have left the output buffers
+        r.step()
+        self.done[i].record(cur)
+        with torch.cuda.stream(self.down):
+            self.down.wait_event(self.done[i])
+            H, W = r.heights[0], r.widths[0]
+            host_out["image"].copy_(r.image.view(3, H, W), non_blocking=True)
+            host_out["mean2d"].copy_(r.g_mean2d, non_blocking=True)
+            host_out["conic"].copy_(r.g_conic, non_blocking=True)
+            host_out["opacity"].copy_(r.g_opac, non_blocking=True)
+            host_out["rgb"].copy_(r.g_rgb, non_blocking=True)
+            self.out_done[i].record(self.down)
+        self.used[i] = True
+        self.frame_slot[k] = i
+
+    def wait(self, k):
+        self.out_done[self.frame_slot[k]].synchronize()
+
+
 class BatchRenderer:
     """Batched forward + backward of one scene seen by several cameras:
     gs_project_views -> gs_bin_sort_views (no host synchronisation) ->
