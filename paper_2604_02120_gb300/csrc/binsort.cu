@@ -178,6 +178,26 @@ __device__ __forceinline__ uint64_t lookback_warp(const unsigned long long* stat
     return prefix;
 }
 
+// The lanes of the warp whose digit equals this lane's, among the valid lanes
+// (an invalid lane gets only itself).  A full 8-bit digit takes one ballot
+// per bit, a cost that does not grow with the number of distinct digits in
+// the warp (random digits: up to 32); a digit with fewer significant bits
+// (the last pass over a short key) takes __match_any_sync, cheap when few
+// values can occur.
+template <bool FULL>
+__device__ __forceinline__ unsigned digit_peers(uint32_t d, bool valid) {
+    const unsigned lane_bit = 1u << (threadIdx.x & 31);
+    if constexpr (!FULL) return __match_any_sync(0xffffffffu, valid ? d : 0x100u + (threadIdx.x & 31));
+    unsigned m = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const unsigned bal = __ballot_sync(0xffffffffu, bit);
+        m &= bit ? bal : ~bal;
+    }
+    return valid ? m : lane_bit;
+}
+
 // s_h[bin] += 1 for every active lane, one atomic per distinct bin in the warp
 // (digits of nearby keys often agree, and same-address shared atomics serialise).
 __device__ __forceinline__ void hist_add(uint32_t* s_h, uint32_t bin) {
@@ -197,11 +217,12 @@ __device__ __forceinline__ uint32_t pass_count(uint32_t n_host, const uint64_t* 
 // One stable pass on bits [shift, shift + 8).  The block takes the next tile
 // of TILE items from the ticket; warp w owns the contiguous items
 // [w * 32 ITEMS, (w + 1) * 32 ITEMS) walked in rounds of 32, so lane order is
-// input order, and each item's rank among equal digits comes from
-// __match_any_sync.  Items are placed in shared memory in digit order, then
+// input order, and each item's rank among equal digits comes from the lanes
+// with the same digit (digit_peers; FULL: all 8 bits of the digit occur in
+// the keys).  Items are placed in shared memory in digit order, then
 // written so that consecutive threads write consecutive addresses of each
 // digit's run.  hist holds the pass's global digit counts.
-template <int ITEMS>
+template <int ITEMS, bool FULL>
 __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint32_t* __restrict__ kin,
                                                        const uint32_t* __restrict__ vin, uint32_t n_host,
                                                        const uint64_t* __restrict__ n_dev, int shift, int pass_id,
@@ -236,8 +257,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint32_t* __rest
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
         const bool valid = wbase + r * 32 + lane < cnt;
-        const uint32_t d = valid ? ((k[r] >> shift) & 0xFFu) : (0x100u + lane);
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t d = (k[r] >> shift) & 0xFFu;
+        const unsigned peers = digit_peers<FULL>(d, valid);
         if (valid && (peers & lt) == 0) s_w[warp][d] += __popc(peers);
         __syncwarp();
     }
@@ -272,8 +293,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint32_t* __rest
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
         const bool valid = wbase + r * 32 + lane < cnt;
-        const uint32_t d = valid ? ((k[r] >> shift) & 0xFFu) : (0x100u + lane);
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t d = (k[r] >> shift) & 0xFFu;
+        const unsigned peers = digit_peers<FULL>(d, valid);
         uint32_t pos = 0;
         if (valid) pos = s_w[warp][d] + __popc(peers & lt);
         __syncwarp();
@@ -313,12 +334,11 @@ cudaError_t radix_sort(uint32_t* k[2], uint32_t* v[2], uint32_t n_host, const ui
     const int nblk = (int)cdiv(n_host, (int64_t)kThreads * items);
     for (int p = 0, shift = 0; shift < bits; ++p, shift += 8) {
         const int id = first_pass + p;
-        if (items == 4)
-            k_onesweep<4><<<nblk, kThreads, 0, s>>>(k[cur], v[cur], n_host, n_dev, shift, id, ps.hist + 256 * id,
-                                                    ps.tickets, ps.status, k[cur ^ 1], v[cur ^ 1], ps.err);
-        else
-            k_onesweep<16><<<nblk, kThreads, 0, s>>>(k[cur], v[cur], n_host, n_dev, shift, id, ps.hist + 256 * id,
-                                                     ps.tickets, ps.status, k[cur ^ 1], v[cur ^ 1], ps.err);
+        const bool full = bits - shift >= 8;
+        auto kern = items == 4 ? (full ? k_onesweep<4, true> : k_onesweep<4, false>)
+                               : (full ? k_onesweep<16, true> : k_onesweep<16, false>);
+        kern<<<nblk, kThreads, 0, s>>>(k[cur], v[cur], n_host, n_dev, shift, id, ps.hist + 256 * id, ps.tickets,
+                                       ps.status, k[cur ^ 1], v[cur ^ 1], ps.err);
         count_launches();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
