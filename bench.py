@@ -317,6 +317,8 @@ def run_ours(args):
 
     # ---- small scene: projection + bin/sort fused into one cooperative launch
     small_line = run_small_fused(gs, torch, gs.make_opts(args.variant), flush, min(K, 200))
+    # ---- all cameras of the ring scene in one batched step (one launch per stage over every view)
+    batched_line = run_batched(gs, torch, sc, dev, args.variant, flush, min(K, 50)) if args.config == 3 else None
 
     # ---- blend-only ms/frame per variant (forward), tensor core vs FP32 CUDA core
     blend = {}
@@ -399,6 +401,7 @@ def run_ours(args):
         "opacity_aware_lists": tight_line,
         "projection_backward": pb_line,
         "small_scene_fused": small_line,
+        **({"batched_views": batched_line} if batched_line else {}),
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cam, proj, bs, sc, dL, args.cpu_seconds)
@@ -461,6 +464,81 @@ def run_small_fused(gs, torch, opts, flush, K):
                      "project_bin_ms": round(statistics.median(a.elapsed_time(b) for a, b, c in ev), 5)}
     out["workload"] = "256x256, 10k Gaussians, SH degree 0, seed 0; step = project + bin + blend fwd + bwd"
     return out
+
+
+def run_batched(gs, torch, sc, dev, variant, flush, K):
+    """Every camera of the scene in one BatchRenderer step (gs_project_views ->
+    gs_bin_sort_views -> tile order -> one persistent forward and one backward
+    over the tiles of all views), replayed as a CUDA graph, against the views
+    rendered one after another with the single-view calls (same step each)."""
+    from paper_2604_02120_gb300 import scenes
+    cams = sc.cameras
+    V, n = len(cams), sc.n
+    stream = torch.cuda.current_stream()
+    # capacity from one synchronising sort of all views
+    f32 = dict(device="cuda", dtype=torch.float32)
+    m2, co = torch.empty(V * n, 2, **f32), torch.empty(V * n, 3, **f32)
+    de, rg = torch.empty(V * n, **f32), torch.empty(V * n, 3, **f32)
+    ra, tt = (torch.empty(V * n, device="cuda", dtype=torch.int32) for _ in range(2))
+    gs.gs_project_views(n, dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cams, m2, co, de,
+                        ra, rg, tt)
+    widths, heights = [c.width for c in cams], [c.height for c in cams]
+    cap0 = 1 << 20  # an overflowing synchronising sort still reports the instance count
+    ws = torch.empty(gs.gs_bin_sort_workspace_size(V * n, cap0, widths[0], heights[0]) + 256, dtype=torch.uint8,
+                     device="cuda")
+    ids = torch.empty(cap0, dtype=torch.int32, device="cuda")
+    rng = torch.empty(2 * sum(gs.num_tiles(w, h) for w, h in zip(widths, heights)), dtype=torch.int32, device="cuda")
+    st, count = gs.gs_bin_sort_views(V, n, m2, ra, de, widths, heights, cap0, ws, None, ids, rng, check=False)
+    assert st in (gs.GS_OK, gs.GS_ERR_CAPACITY) and count > 0
+    del ws, ids, rng, m2, co, de, rg, ra, tt
+    capacity = int(count * 1.25) + 4096
+    dL = torch.from_numpy(np.concatenate([g.reshape(-1) for g in scenes.upstream_grad(0, cams)])).cuda()
+    br = gs.BatchRenderer(dev, cams, gs.make_opts(variant), capacity)
+    br.dL.copy_(dL)
+    br.step()
+    br.capture()
+    for _ in range(3):
+        br.graph.replay()
+    ev = []
+    for _ in range(K):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        br.graph.replay()
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    assert gs.gs_sync_status() == gs.GS_OK
+    batched = statistics.median(a.elapsed_time(b) for a, b in ev)
+    evals = 2 * int(br.nc.sum().item())
+    del br
+    # the same views one after another (single-view calls, each sorted and blended on its own)
+    opts = gs.make_opts(variant)
+    sorters = [gs.BinSorter("cuda", 1 << 22) for _ in cams]
+    dls = [torch.from_numpy(g).cuda() for g in scenes.upstream_grad(0, cams)]
+
+    def seq():
+        for cam, so, g in zip(cams, sorters, dls):
+            proj = gs.project(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam)
+            bs = so.run(proj["mean2d"], proj["radius"], proj["depth"], cam.width, cam.height)
+            fwd = gs.blend_forward(cam.width, cam.height, bs, proj, dev["opacities"], opts)
+            gs.blend_backward(cam.width, cam.height, bs, proj, dev["opacities"], opts, fwd, g)
+    for _ in range(2):
+        seq()
+    ev = []
+    for _ in range(min(K, 10)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        seq()
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    sequential = statistics.median(a.elapsed_time(b) for a, b in ev)
+    return {"views": V, "instances": int(count), "evals_per_step": evals, "batched_ms": round(batched, 4),
+            "batched_evals_per_s": evals / (batched / 1e3), "sequential_ms": round(sequential, 4),
+            "note": "batched: BatchRenderer step of all views captured in a CUDA graph; sequential: per view "
+                    "gs_project + gs_bin_sort (synchronising) + blend forward + backward; L2 flushed before each"}
 
 
 def run_e2e(args, gs, torch, sc, cam, opts, capacity, dL, flush, evals_step, ws, dist):
