@@ -9,7 +9,7 @@
 // as the plain quadratic of Eq. 3, never via the dot-product form of Eq. 6
 // (that identity has a routine of its own, oracle_power_eq6, used to pin it).
 //
-// Readings of passages the paper leaves open (each also listed in the design doc):
+// Readings of passages the paper leaves open:
 //  * conic: Sigma^-1 = [[A, B], [B, C]] is the inverse 2D covariance (Alg. 1);
 //  * pixel (px, py) is evaluated at its centre (px + 0.5, py + 0.5);
 //  * alpha = min(0.99, o * exp(min(power, 0))); a splat is skipped when

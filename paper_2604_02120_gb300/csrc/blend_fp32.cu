@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kBatch) k_blend_fp32_fwd(const __grid_constant
     const uint32_t start = a.ranges[2 * tile], end = a.ranges[2 * tile + 1];
     const int len = end > start ? (int)(end - start) : 0;
 
-    float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    float T = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f;
     int last = 0;
     bool done = !inside;
     for (int base = 0; base < len; base += kBatch) {
@@ -97,9 +97,9 @@ __global__ void __launch_bounds__(kBatch) k_blend_fp32_fwd(const __grid_constant
                 break;
             }
             const float w = alpha * T;
-            C0 = __fmaf_rn(oc.z, w, C0);
-            C1 = __fmaf_rn(oc.w, w, C1);
-            C2 = __fmaf_rn(s_b[j], w, C2);
+            cr = __fmaf_rn(oc.z, w, cr);
+            cg = __fmaf_rn(oc.w, w, cg);
+            cb = __fmaf_rn(s_b[j], w, cb);
             T = tT;
             last = base + j + 1;
         }
@@ -107,9 +107,9 @@ __global__ void __launch_bounds__(kBatch) k_blend_fp32_fwd(const __grid_constant
     if (inside) {
         const size_t pix = (size_t)py * tg.W + px, plane = (size_t)tg.W * tg.H;
         float* img = a.image + 3 * tg.pix_off;
-        img[pix] = C0 + T * a.bg[0];
-        img[plane + pix] = C1 + T * a.bg[1];
-        img[2 * plane + pix] = C2 + T * a.bg[2];
+        img[pix] = cr + T * a.bg[0];
+        img[plane + pix] = cg + T * a.bg[1];
+        img[2 * plane + pix] = cb + T * a.bg[2];
         a.T_final[tg.pix_off + pix] = T;
         a.n_contrib[tg.pix_off + pix] = last;
     }

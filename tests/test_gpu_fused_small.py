@@ -26,9 +26,9 @@ def _lib():
 
 
 def _scene(kind):
-    if kind == "c0":
+    if kind == "256x256_10k":
         return scenes.make_config(0)
-    if kind == "c0_sh3":
+    if kind == "1280x720_10k_sh3":
         return scenes.make_config(1, n=10_000)
     if kind == "tiny_ragged":
         return scenes.tiny_scene(3, n=96, width=77, height=45, sh_degree=2)
@@ -43,7 +43,7 @@ def _tile_lists(ranges, ids):
 
 
 @pytest.mark.parametrize("tight", [False, True])
-@pytest.mark.parametrize("kind", ["c0", "c0_sh3", "tiny_ragged", "tiny_dense"])
+@pytest.mark.parametrize("kind", ["256x256_10k", "1280x720_10k_sh3", "tiny_ragged", "tiny_dense"])
 def test_fused_lists_equal_bin_sort(kind, tight):
     sc = _scene(kind)
     cam = sc.cameras[0]

@@ -34,11 +34,11 @@ def _lib():
 
 
 def _scene(kind):
-    if kind == "c0":
+    if kind == "256x256_10k":
         return scenes.make_config(0)
-    if kind == "c1":
+    if kind == "1280x720_200k":
         return scenes.make_config(1)
-    if kind == "c1_small":
+    if kind == "1280x720_20k":
         return scenes.make_config(1, n=20_000)
     if kind == "tiny_ragged":
         return scenes.tiny_scene(3, n=96, width=77, height=45, sh_degree=2)
@@ -83,7 +83,7 @@ def test_measured_peaks_are_plausible():
 
 # -------------------------------------------------------------- projection --
 
-@pytest.mark.parametrize("kind", ["c0", "tiny_ragged", "tiny_dense", "c1"])
+@pytest.mark.parametrize("kind", ["256x256_10k", "tiny_ragged", "tiny_dense", "1280x720_200k"])
 def test_project_matches_oracle(kind):
     sc, dev, cam, proj, bs, pn, _ = pipeline(kind)
     ref = oracle.project(sc.means, sc.scales, sc.quats, sc.sh, sc.sh_degree, cam)
@@ -132,7 +132,7 @@ def test_project_every_sh_degree_and_unaligned_coefficients(sh_degree):
 
 # ----------------------------------------------------------------- binning --
 
-@pytest.mark.parametrize("kind", ["c0", "tiny_ragged", "tiny_dense", "c1"])
+@pytest.mark.parametrize("kind", ["256x256_10k", "tiny_ragged", "tiny_dense", "1280x720_200k"])
 def test_bin_sort_bit_exact(kind):
     sc, dev, cam, proj, bs, pn, bn = pipeline(kind)
     ref = oracle.bin_sort(pn["mean2d"].astype(np.float64), pn["radius"], pn["depth"], cam.width, cam.height)
@@ -180,8 +180,8 @@ def _compare(out, ref, tol, nc_exact=True, max_amb=0.01):
     return err
 
 
-@pytest.mark.parametrize("kind,bg", [("c0", (0, 0, 0)), ("tiny_ragged", (0.3, 0.2, 0.1)),
-                                     ("tiny_dense", (0, 0, 0)), ("c1", (0.1, 0.1, 0.1))])
+@pytest.mark.parametrize("kind,bg", [("256x256_10k", (0, 0, 0)), ("tiny_ragged", (0.3, 0.2, 0.1)),
+                                     ("tiny_dense", (0, 0, 0)), ("1280x720_200k", (0.1, 0.1, 0.1))])
 def test_blend_fp32_matches_oracle(kind, bg):
     sc, dev, cam, proj, bs, pn, bn = pipeline(kind)
     out = blend_gpu(cam, proj, bs, dev["opacities"], "fp32", bg=bg)
@@ -224,7 +224,7 @@ def test_alpha_power_min_values():
     assert np.isinf(got[5:]).all()
 
 
-@pytest.mark.parametrize("kind", ["c0", "tiny_ragged", "tiny_dense", "c1"])
+@pytest.mark.parametrize("kind", ["256x256_10k", "tiny_ragged", "tiny_dense", "1280x720_200k"])
 def test_bin_sort_opacity_aware_bit_exact(kind):
     """Opacity-aware lists: FP32 tile membership with fixed rounding, so the
     GPU lists equal the oracle's bit for bit, and there are fewer of them."""
@@ -239,7 +239,7 @@ def test_bin_sort_opacity_aware_bit_exact(kind):
 
 
 @pytest.mark.parametrize("variant", ["fp32", "fp16_split"])
-@pytest.mark.parametrize("kind", ["tiny_dense", "c1"])
+@pytest.mark.parametrize("kind", ["tiny_dense", "1280x720_200k"])
 def test_opacity_aware_lists_render_the_same_image(kind, variant):
     """The splats the opacity-aware lists drop fail the 1/255 test at every
     pixel of the tile: image and T_final are bit for bit those of the full
@@ -309,7 +309,7 @@ def _busy_tiles(bn, k, seed=0):
 
 
 @pytest.mark.parametrize("variant", ["fp16_split", "bf16_split"])
-@pytest.mark.parametrize("kind", ["tiny_dense", "c1"])
+@pytest.mark.parametrize("kind", ["tiny_dense", "1280x720_200k"])
 def test_tile_power_split_within_2e3(kind, variant):
     """Eq. 8's contraction on the tensor cores: every pair that can contribute
     (power >= ln(1/(255 o))) has |power_TC - power_FP64| <= 2e-3."""
@@ -324,7 +324,7 @@ def test_tile_power_split_within_2e3(kind, variant):
     assert e.max() <= SPLIT_EXP_ERR / 2
 
 
-@pytest.mark.parametrize("kind", ["tiny_dense", "c1"])
+@pytest.mark.parametrize("kind", ["tiny_dense", "1280x720_200k"])
 def test_tile_power_fp8_split_trial(kind):
     """FP8-e4m3 operands (a trial): v_g rows scaled by a power of two and split
     into 5 e4m3 terms (the last three shifted up by 2^4 against the monomial
@@ -351,7 +351,7 @@ def test_tile_power_plain_is_close(variant):
 
 
 @pytest.mark.parametrize("variant", TC_VARIANTS)
-@pytest.mark.parametrize("kind", ["c0", "tiny_ragged", "tiny_dense", "c1"])
+@pytest.mark.parametrize("kind", ["256x256_10k", "tiny_ragged", "tiny_dense", "1280x720_200k"])
 def test_blend_tc_matches_oracle(kind, variant):
     sc, dev, cam, proj, bs, pn, bn = pipeline(kind)
     bg = (0.05, 0.1, 0.15)
@@ -394,7 +394,7 @@ def test_blend_tc_reference_origin():
 
 # ------------------------------------------------------------- backward ----
 
-@pytest.mark.parametrize("kind", ["tiny_ragged", "tiny_dense", "c0"])
+@pytest.mark.parametrize("kind", ["tiny_ragged", "tiny_dense", "256x256_10k"])
 def test_blend_backward_matches_oracle_gradient(kind):
     sc, dev, cam, proj, bs, pn, bn = pipeline(kind)
     bg = (0.2, 0.1, 0.05)
@@ -424,7 +424,7 @@ def _grad_rel_errors(g, ref):
 
 
 @pytest.mark.parametrize("variant", ["fp16_split", "bf16_split", "fp8_split"])
-@pytest.mark.parametrize("kind", ["tiny_ragged", "tiny_dense", "c0", "c1_small"])
+@pytest.mark.parametrize("kind", ["tiny_ragged", "tiny_dense", "256x256_10k", "1280x720_20k"])
 def test_tc_blend_backward_matches_oracle_gradient(kind, variant):
     """The tensor-core backward pass (exponents recomputed by the forward's
     MMA, per-splat sums over pixels by a second MMA) against the FP64 oracle
@@ -537,7 +537,7 @@ def test_blend_tc_never_sits_out_a_wait_limit(chunk, stages):
     """A correct result can hide a bounded wait that ran out its limit (1 s by
     default).  On the full 1280x720 workload a blend takes well under 50 ms."""
     import time
-    sc, dev, cam, proj, bs, pn, bn = pipeline("c1")
+    sc, dev, cam, proj, bs, pn, bn = pipeline("1280x720_200k")
     opts = gs.make_opts("fp16_split", chunk=chunk, stages=stages)
     gs.blend_forward(cam.width, cam.height, bs, proj, dev["opacities"], opts)
     torch.cuda.synchronize()
@@ -552,7 +552,7 @@ def test_blend_tc_never_sits_out_a_wait_limit(chunk, stages):
 def test_bin_sort_without_keys_gives_the_same_lists():
     """keys_sorted is optional: with NULL the ids and tile ranges are those of
     the call that writes keys (graph mode, count on the device)."""
-    sc, dev, cam, proj, bs, pn, bn = pipeline("c1_small")
+    sc, dev, cam, proj, bs, pn, bn = pipeline("1280x720_20k")
     n, cap = sc.n, 1 << 21
     ws = torch.empty(gs.gs_bin_sort_workspace_size(n, cap, cam.width, cam.height) + 256, device="cuda",
                      dtype=torch.uint8)

@@ -30,11 +30,11 @@ def _lib():
 
 
 def _scene(kind):
-    if kind == "c0":
+    if kind == "256x256_10k":
         return scenes.make_config(0)
-    if kind == "c1":
+    if kind == "1280x720_200k":
         return scenes.make_config(1)
-    if kind == "c2_small":
+    if kind == "1920x1080_clustered_100k":
         return scenes.make_config(2, n=100_000)
     if kind == "tiny_ragged":
         return scenes.tiny_scene(3, n=96, width=77, height=45, sh_degree=2)
@@ -64,7 +64,8 @@ def _rel_errors(g, ref, keep):
     return out
 
 
-@pytest.mark.parametrize("kind", ["c0", "tiny_ragged", "tiny_dense", "c2_small", "c1"])
+@pytest.mark.parametrize("kind", ["256x256_10k", "tiny_ragged", "tiny_dense", "1920x1080_clustered_100k",
+                                  "1280x720_200k"])
 def test_project_backward_matches_oracle(kind):
     sc = _scene(kind)
     cam = sc.cameras[0]

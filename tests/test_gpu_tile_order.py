@@ -32,9 +32,9 @@ def _bucket(lens):
     return out
 
 
-@pytest.mark.parametrize("kind", ["c0", "c1_small"])
+@pytest.mark.parametrize("kind", ["256x256_10k", "1280x720_20k"])
 def test_tile_order_is_longest_first_permutation(kind):
-    sc = scenes.make_config(0) if kind == "c0" else scenes.make_config(1, n=20_000)
+    sc = scenes.make_config(0) if kind == "256x256_10k" else scenes.make_config(1, n=20_000)
     dev, cam, proj, bs = gpu_pipeline(sc)
     order = gs.tile_order(bs["tile_ranges"], [cam.width], [cam.height]).cpu().numpy()
     assert gs.gs_sync_status() == gs.GS_OK

@@ -51,7 +51,7 @@ def _no_alloc(cam, proj, capacity):
     return count, keys[:count].cpu().numpy(), ids[:count].cpu().numpy(), ranges.cpu().numpy()
 
 
-@pytest.mark.parametrize("kind", ["tiny", "c1"])
+@pytest.mark.parametrize("kind", ["tiny", "1280x720_200k"])
 def test_no_alloc_bin_sort_matches_workspace_version_twice(kind):
     """Two calls in a row (the second reuses the built-in scratch the first
     left behind) agree bit for bit with gs_bin_sort; sorting is integer work,
@@ -59,7 +59,7 @@ def test_no_alloc_bin_sort_matches_workspace_version_twice(kind):
     scene = scenes.tiny_scene(5, n=300, width=93, height=61, sh_degree=1) if kind == "tiny" \
         else scenes.make_config(1)
     cam, proj = _projected(scene)
-    capacity = 3_000_000 if kind == "c1" else 20_000
+    capacity = 3_000_000 if kind == "1280x720_200k" else 20_000
     want = _with_workspace(cam, proj, capacity)
     assert want[0] > 0
     for _ in range(2):
