@@ -173,3 +173,29 @@ def test_project_backward_rejects_unaligned_dmean2d():
     with pytest.raises(gs.GsError):
         gs.project_backward(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam,
                             proj["radius"], buf[1:], dc, dc)
+
+
+def test_project_backward_sh1_without_lowpass():
+    """SH degree 1 and a camera without the 2D low-pass, with splats small
+    enough that some 2D covariances have an FP32 determinant below 1e-6 (the
+    forward's and the backward's FP64 branch)."""
+    sc = scenes.tiny_scene(14, n=400, width=70, height=52, sh_degree=1, scale_lo=-8.0, scale_hi=-3.0)
+    cam = scenes.look_at_camera((0.4, -0.3, -2.8), (0.0, 0.0, 0.0), 70, 52, lowpass=0.0)
+    dev = gs.scene_to_device(sc)
+    proj = gs.project(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam)
+    pn = to_np(proj)
+    ref_cov = oracle.project(sc.means, sc.scales, sc.quats, sc.sh, sc.sh_degree, cam)["cov2d"]
+    det = ref_cov[:, 0] * ref_cov[:, 2] - ref_cov[:, 1] ** 2
+    assert ((det < 1e-6) & (pn["radius"] > 0)).sum() > 0  # the FP64 branch runs
+    dm, dc, dr = _upstream(sc.n, 5)
+    g = to_np(gs.project_backward(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam,
+                                  proj["radius"], torch.from_numpy(dm).cuda(), torch.from_numpy(dc).cuda(),
+                                  torch.from_numpy(dr).cuda()))
+    assert gs.gs_sync_status() == gs.GS_OK
+    ref = oracle.project_backward(sc.means, sc.scales, sc.quats, sc.sh, sc.sh_degree, cam, pn["radius"], dm, dc,
+                                  dr)
+    keep = (pn["radius"] > 0) & ~_clamp_ambiguous(sc, cam, pn["rgb"])
+    rel = _rel_errors(g, ref, keep)
+    report("project_bwd_rel_sh1_no_lowpass", rel)
+    for key, e in rel.items():
+        assert e < 1e-4, f"{key}: relative error {e:.2e}"

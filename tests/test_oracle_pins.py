@@ -523,29 +523,31 @@ def test_blend_grad_matches_central_differences():
     assert checked > 100
 
 
-def test_project_backward_matches_central_differences():
+@pytest.mark.parametrize("deg,lowpass", [(3, 0.3), (0, 0.3), (1, 0.3), (2, 0.0)])
+def test_project_backward_matches_central_differences(deg, lowpass):
     """The analytic projection gradient (means, scales, unnormalised
-    quaternions, SH degree 3) equals central differences of the oracle's own
-    forward projection for L = sum(wm * mean2d) + sum(wc * conic) +
-    sum(wr * rgb), seen from an off-axis camera; a Gaussian whose colour
-    channel is clamped at 0 passes no gradient through it."""
+    quaternions, SH of every degree) equals central differences of the
+    oracle's own forward projection for L = sum(wm * mean2d) + sum(wc * conic)
+    + sum(wr * rgb), seen from an off-axis camera, with and without the 2D
+    low-pass; a Gaussian whose colour channel is clamped at 0 passes no
+    gradient through it."""
     n = 14
-    sc = scenes.tiny_scene(12, n=n, width=80, height=64, sh_degree=3, scale_lo=-2.5, scale_hi=-1.2)
-    cam = scenes.look_at_camera((1.1, -0.6, -2.7), (0.05, 0.1, 0.0), 80, 64)
+    sc = scenes.tiny_scene(12, n=n, width=80, height=64, sh_degree=deg, scale_lo=-2.5, scale_hi=-1.2)
+    cam = scenes.look_at_camera((1.1, -0.6, -2.7), (0.05, 0.1, 0.0), 80, 64, lowpass=lowpass)
     rng = np.random.default_rng(5)
     means = sc.means.astype(np.float32).copy()
     scales = sc.scales.astype(np.float32).copy()
     quats = (sc.quats * rng.uniform(0.5, 2.0, (n, 1))).astype(np.float32)  # not unit length
     sh = sc.sh.astype(np.float32).copy()
     sh[0, 0, 1] = -4.0  # Gaussian 0's green channel is clamped
-    base = oracle.project(means, scales, quats, sh, 3, cam)
+    base = oracle.project(means, scales, quats, sh, deg, cam)
     live = base["radius"] > 0
     assert live.sum() >= 10 and base["rgb"][0, 1] == 0.0
     wm, wc, wr = rng.standard_normal((n, 2)), rng.standard_normal((n, 3)), rng.standard_normal((n, 3))
-    g = oracle.project_backward(means, scales, quats, sh, 3, cam, base["radius"], wm, wc, wr)
+    g = oracle.project_backward(means, scales, quats, sh, deg, cam, base["radius"], wm, wc, wr)
 
     def loss(args):
-        o = oracle.project(*args, 3, cam)
+        o = oracle.project(*args, deg, cam)
         assert ((o["radius"] > 0) == live).all()
         return float((wm * o["mean2d"]).sum() + (wc * o["conic"]).sum() + (wr * o["rgb"]).sum())
 
