@@ -179,11 +179,10 @@ __device__ __forceinline__ uint64_t lookback_warp(const unsigned long long* stat
 }
 
 // The lanes of the warp whose digit equals this lane's, among the valid lanes
-// (an invalid lane gets only itself).  A full 8-bit digit takes one ballot
-// per bit, a cost that does not grow with the number of distinct digits in
-// the warp (random digits: up to 32); a digit with fewer significant bits
-// (the last pass over a short key) takes __match_any_sync, cheap when few
-// values can occur.
+// (an invalid lane gets only itself).  FULL: one ballot per bit of the 8-bit
+// digit, a cost that does not grow with the number of distinct digits in the
+// warp (random digits: up to 32); otherwise __match_any_sync, cheap when the
+// digit has only a few significant bits (the last pass over a short key).
 template <bool FULL>
 __device__ __forceinline__ unsigned digit_peers(uint32_t d, bool valid) {
     const unsigned lane_bit = 1u << (threadIdx.x & 31);
@@ -218,8 +217,8 @@ __device__ __forceinline__ uint32_t pass_count(uint32_t n_host, const uint64_t* 
 // of TILE items from the ticket; warp w owns the contiguous items
 // [w * 32 ITEMS, (w + 1) * 32 ITEMS) walked in rounds of 32, so lane order is
 // input order, and each item's rank among equal digits comes from the lanes
-// with the same digit (digit_peers; FULL: all 8 bits of the digit occur in
-// the keys).  Items are placed in shared memory in digit order, then
+// with the same digit (digit_peers; FULL: ballots, for digits of more than
+// 4 significant bits).  Items are placed in shared memory in digit order, then
 // written so that consecutive threads write consecutive addresses of each
 // digit's run.  hist holds the pass's global digit counts.
 template <int ITEMS, bool FULL>
@@ -334,7 +333,9 @@ cudaError_t radix_sort(uint32_t* k[2], uint32_t* v[2], uint32_t n_host, const ui
     const int nblk = (int)cdiv(n_host, (int64_t)kThreads * items);
     for (int p = 0, shift = 0; shift < bits; ++p, shift += 8) {
         const int id = first_pass + p;
-        const bool full = bits - shift >= 8;
+        // ballots unless the digit has at most 4 significant bits (16 values: match_any is cheaper);
+        // the ballot of an unused high bit is the same for every lane
+        const bool full = bits - shift > 4;
         auto kern = items == 4 ? (full ? k_onesweep<4, true> : k_onesweep<4, false>)
                                : (full ? k_onesweep<16, true> : k_onesweep<16, false>);
         kern<<<nblk, kThreads, 0, s>>>(k[cur], v[cur], n_host, n_dev, shift, id, ps.hist + 256 * id, ps.tickets,
