@@ -287,6 +287,19 @@ def run_ours(args):
                   "steps": Kt, "note": "gs_bin_sort_views with conic + gs_alpha_power_min: a splat keeps a tile "
                                        "only if alpha can reach 1/255 there; the image equals the full lists' "}
 
+    # ---- issued pairs: every chunk a tile evaluates before its exit, at all 256 pixels
+    issued_line = None
+    if args.variant != "fp32":
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        o_cnt = gs.make_opts(args.variant, chunk=opts.chunk, stages=opts.stages, tile_order=order, issued_pairs=cnt)
+        out_c = gs.blend_forward(W, H, bs, proj, dev["opacities"], o_cnt)
+        issued = int(cnt.item())
+        assert gs.gs_sync_status() == gs.GS_OK and torch.equal(out_c["n_contrib"], fwd["n_contrib"])
+        issued_line = {"evaluated_per_frame": evals_fwd, "issued_per_frame": issued,
+                       "issued_over_evaluated": round(issued / max(evals_fwd, 1), 3),
+                       "note": "evaluated = sum of n_contrib (the metric's pairs); issued = 256 x the splats of "
+                               "every chunk the tensor-core forward evaluates before a tile's exit"}
+
     # ---- projection backward: dL/d(means, scales, quats, sh) from the blend's
     # splat gradients (HBM-bound, one thread per Gaussian)
     pproj, _, _, gb = step()
@@ -400,6 +413,7 @@ def run_ours(args):
         "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
         "opacity_aware_lists": tight_line,
         "projection_backward": pb_line,
+        **({"forward_pairs": issued_line} if issued_line else {}),
         "small_scene_fused": small_line,
         **({"batched_views": batched_line} if batched_line else {}),
     }

@@ -99,6 +99,11 @@ typedef struct gs_blend_opts {
                                    positions p with p % shard_count == shard_index.  It must have one
                                    entry per tile of the call; an entry >= the tile count is clamped
                                    (a wrong image, never an access outside the tile ranges) */
+    uint64_t* issued_pairs;     /* NULL, or a DEVICE counter the tensor-core forward adds its issued
+                                   Gaussian-pixel pairs to: 256 x the splats of every chunk it
+                                   evaluates before a tile's exit (every pixel stopped), whether or
+                                   not a pixel still needs them; the evaluated pairs of Eq. 1 are the
+                                   sum of n_contrib.  The caller zeroes it */
 } gs_blend_opts;
 
 /* Library version (major * 100 + minor). */

@@ -123,6 +123,7 @@ bool make_args(BlendArgs& a, int32_t n_views, const int32_t* widths, const int32
     if (a.shard_index < 0 || a.shard_index >= a.shard_count) return false;
     a.order = o ? o->tile_order : nullptr;
     a.order_tiles = a.total_tiles;
+    a.issued = o ? reinterpret_cast<unsigned long long*>(o->issued_pairs) : nullptr;  // same width, 64 bits
     a.err = error_word();
     return true;
 }

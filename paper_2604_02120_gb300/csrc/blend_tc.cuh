@@ -542,6 +542,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
         // ------------------------------------------------------- producer --
         int k = 0;
         bool quit = false;
+        unsigned long long issued = 0;  // splats of the chunks this block issued
         for (int seq = 0; !quit; ++seq) {
             int q = 0;
             if (lane == 0) q = (int)atomicAdd(a.queue, 1u);
@@ -585,6 +586,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
                 const int base = c * CH;
                 const int n = end ? -1 : min(CH, len - base);
                 if (n > 0) {
+                    issued += (unsigned long long)n;
                     uint8_t* mB = sB + s * LY::B_BYTES;
                     for (int j = lane; j < CH; j += 32) {
                         float vu[6], vl[6];
@@ -628,6 +630,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
             }
             if (end) quit = true;
         }
+        // issued pairs: every chunk is evaluated at all 256 pixels of its tile
+        if (!DUMP && lane == 0 && a.issued != nullptr && issued) atomicAdd(a.issued, issued * 256ull);
     } else if (lane == 0) {
         // ------------------------------------------------------ MMA issue --
         const uint32_t aA = smem_u32(sA);

@@ -46,6 +46,7 @@ struct BlendArgs {
     int shard_count, shard_index;  // queue item q takes position p = q * count + index of the tile order
     const uint32_t* order;         // the tile at position p: order[p] (nullptr: tile p)
     int order_tiles;               // the call's tile count; order entries are clamped below it
+    unsigned long long* issued;    // if set, the TC forward adds 256 x the splats of every chunk it issues
     // gs_tile_power only
     const int* tiles;
     int max_len;

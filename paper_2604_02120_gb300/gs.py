@@ -56,7 +56,7 @@ class gs_blend_opts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("chunk", ctypes.c_int32), ("stages", ctypes.c_int32),
                 ("ref_origin", ctypes.c_int32), ("bg", ctypes.c_float * 3), ("reserved", ctypes.c_int32),
                 ("timeout_ns", ctypes.c_int64), ("shard_count", ctypes.c_int32), ("shard_index", ctypes.c_int32),
-                ("tile_order", ctypes.c_void_p)]
+                ("tile_order", ctypes.c_void_p), ("issued_pairs", ctypes.c_void_p)]
 
 
 _lib = None
@@ -145,7 +145,7 @@ def make_camera(cam) -> gs_camera:
 
 
 def make_opts(variant="fp32", chunk=0, stages=0, ref_origin=0, bg=(0.0, 0.0, 0.0), timeout_ns=0, shard_count=0,
-              shard_index=0, tile_order=None) -> gs_blend_opts:
+              shard_index=0, tile_order=None, issued_pairs=None) -> gs_blend_opts:
     """Blend options; tile_order (a device tensor from tile_order(), kept
     alive by the caller while the options are used) makes the kernels take
     the longest tile lists first."""
@@ -157,6 +157,7 @@ def make_opts(variant="fp32", chunk=0, stages=0, ref_origin=0, bg=(0.0, 0.0, 0.0
     o.timeout_ns = int(timeout_ns)
     o.shard_count, o.shard_index = int(shard_count), int(shard_index)
     o.tile_order = None if tile_order is None else tile_order.data_ptr()
+    o.issued_pairs = None if issued_pairs is None else issued_pairs.data_ptr()
     return o
 
 

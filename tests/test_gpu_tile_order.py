@@ -87,3 +87,39 @@ def test_ordered_shards_cover_every_pixel_once():
     assert gs.gs_sync_status() == gs.GS_OK
     assert (seen == 1).all()
     assert torch.equal(img, full["image"])
+
+
+def _opaque_wall(n=50):
+    """One 16x16 tile covered by n large, nearly opaque splats: every pixel
+    stops within three of them."""
+    f = np.float32
+    means = np.zeros((n, 3), f)
+    means[:, 2] = np.linspace(-1.0, 0.5, n, dtype=f)  # distinct depths in front of nothing else
+    scales = np.full((n, 3), 5.0, f)
+    quats = np.tile(np.array([1, 0, 0, 0], f), (n, 1))
+    opac = np.full(n, 0.99, f)
+    sh = np.zeros((n, 1, 3), f)
+    return scenes.Scene(means, scales, quats, opac, sh, 0, [scenes.look_at_camera((0, 0, -3), (0, 0, 0), 16, 16)])
+
+
+def test_issued_pairs_counter():
+    """gs_blend_opts.issued_pairs: the tensor-core forward's issued pairs lie
+    between the evaluated pairs (sum of n_contrib) and 256 x the instances
+    (three scenes, one where every pixel stops within three splats), and
+    equal 256 x the instances when no pixel can stop early (opacities scaled
+    down)."""
+    dense = scenes.tiny_scene(8, n=600, width=64, height=48, sh_degree=3, scale_lo=-2.5, scale_hi=-1.2)
+    for sc, scale in ((dense, 0.02), (scenes.make_config(0), 1.0), (_opaque_wall(), 1.0)):
+        dev, cam, proj, bs = gpu_pipeline(sc)
+        n_inst = int(bs["n_instances"])
+        issued = torch.zeros(1, device="cuda", dtype=torch.int64)
+        o = gs.make_opts("fp16_split", chunk=32, issued_pairs=issued)
+        out = gs.blend_forward(cam.width, cam.height, bs, proj, (dev["opacities"] * scale).contiguous(), o)
+        assert gs.gs_sync_status() == gs.GS_OK
+        got = int(issued.item())
+        evaluated = int(out["n_contrib"].sum().item())
+        assert evaluated <= got <= 256 * n_inst
+        if scale < 1.0:
+            assert got == 256 * n_inst
+        if sc.n == 50:  # the producer may issue the second chunk before the first reports every pixel stopped
+            assert n_inst == 50 and (out["n_contrib"] <= 3).all()
