@@ -459,9 +459,10 @@ def blend_forward(width, height, bs, proj, opacity, opts, stream=None) -> dict:
 
 def blend_backward(width, height, bs, proj, opacity, opts, fwd, dL_dimage, stream=None) -> dict:
     n = opacity.shape[0]
-    dev = opacity.device
-    g = dict(mean2d=torch.zeros(n, 2, device=dev), conic=torch.zeros(n, 3, device=dev),
-             opacity=torch.zeros(n, device=dev), rgb=torch.zeros(n, 3, device=dev))
+    # the four outputs accumulate by atomics: views of one buffer, zeroed by one fill
+    buf = torch.zeros(9 * n, device=opacity.device)
+    g = dict(mean2d=buf[:2 * n].view(n, 2), conic=buf[2 * n:5 * n].view(n, 3), opacity=buf[5 * n:6 * n],
+             rgb=buf[6 * n:].view(n, 3))
     gs_blend_backward(width, height, bs["tile_ranges"], bs["ids"], proj["mean2d"], proj["conic"], opacity,
                       proj["rgb"], opts, fwd["T_final"], fwd["n_contrib"], dL_dimage.contiguous(), g["mean2d"],
                       g["conic"], g["opacity"], g["rgb"], stream)
@@ -614,10 +615,12 @@ class BatchRenderer:
         self.T = torch.empty(self.pixels, **f32)
         self.nc = torch.empty(self.pixels, **i32)
         self.dL = torch.zeros(3 * self.pixels, **f32)
-        self.g_mean2d = torch.zeros(V * n, 2, **f32)
-        self.g_conic = torch.zeros(V * n, 3, **f32)
-        self.g_opac = torch.zeros(n, **f32)
-        self.g_rgb = torch.zeros(V * n, 3, **f32)
+        # the gradients accumulate by atomics: views of one buffer, zeroed by one fill per step
+        self.g_buf = torch.zeros(8 * V * n + n, **f32)
+        self.g_mean2d = self.g_buf[:2 * V * n].view(V * n, 2)
+        self.g_conic = self.g_buf[2 * V * n:5 * V * n].view(V * n, 3)
+        self.g_rgb = self.g_buf[5 * V * n:8 * V * n].view(V * n, 3)
+        self.g_opac = self.g_buf[8 * V * n:]
         self.graph = None
 
     def forward(self, stream=None):
@@ -633,8 +636,7 @@ class BatchRenderer:
                                sc["opacities"], self.rgb, self.opts, self.image, self.T, self.nc, stream)
 
     def backward(self, stream=None):
-        for t in (self.g_mean2d, self.g_conic, self.g_opac, self.g_rgb):
-            t.zero_()
+        self.g_buf.zero_()
         gs_blend_backward_views(self.widths, self.heights, self.n, self.ranges, self.ids, self.mean2d, self.conic,
                                 self.scene["opacities"], self.rgb, self.opts, self.T, self.nc, self.dL,
                                 self.g_mean2d, self.g_conic, self.g_opac, self.g_rgb, stream)
