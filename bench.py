@@ -47,9 +47,9 @@ WORKLOAD_NOTE = " (synthetic stand-in for the paper's trained scenes)"
 # (entries for another source or workload are not reported).
 KNOWN_TRAFFIC = {
     # profiles/k_blend_tc_fp16split_1280x720_200k.md, profiles/k_blend_tc_bwd_fp16split_1280x720_200k.md
-    # (dram__bytes_read.sum + dram__bytes_write.sum, median over the captured launches; forward at chunk 32, 4 stages)
-    "k_blend_tc<fp16_split>": {"bytes": 10168576, "src": "432feb543d0bac90", "config": 1},
-    "k_blend_tc_bwd<fp16_split>": {"bytes": 31104512, "src": "78a83c91bfb88214", "config": 1},
+    # (dram__bytes_read.sum + dram__bytes_write.sum, median over the captured launches; forward at chunk 32)
+    "k_blend_tc<fp16_split>": {"bytes": 9740672, "src": "7883918f27afdcf3", "config": 1},
+    "k_blend_tc_bwd<fp16_split>": {"bytes": 31102976, "src": "f5180fa46d1ff5c8", "config": 1},
 }
 
 

@@ -49,7 +49,7 @@ namespace gs {
 namespace tc {
 
 constexpr int kBwdChunk = 16;
-constexpr int kBwdStages = 4;
+constexpr int kBwdStages = 6;  // the deepest ring that keeps 3 blocks per SM (75.9 KB of shared memory each)
 constexpr float kTScale = 4096.0f;  // 2^12
 
 __device__ __forceinline__ void tmem_ld_32x32b_x8(uint32_t taddr, uint32_t (&v)[8]) {
