@@ -445,6 +445,14 @@ class BinSorter:
         raise GsError(GS_ERR_CAPACITY, "gs_bin_sort", "capacity growth failed")
 
 
+def _list_ids(bs):
+    """The sorted ids, or a one-element placeholder when there are no
+    instances (every tile range is then empty and nothing is read; the C ABI
+    takes no null pointer)."""
+    ids = bs["ids"]
+    return ids if ids.numel() > 0 else torch.zeros(1, device=ids.device, dtype=ids.dtype)
+
+
 def blend_forward(width, height, bs, proj, opacity, opts, stream=None) -> dict:
     dev = opacity.device
     # a sharded call writes only its tiles' pixels: the others are zero
@@ -452,7 +460,7 @@ def blend_forward(width, height, bs, proj, opacity, opts, stream=None) -> dict:
     image = new(3, height, width, device=dev, dtype=torch.float32)
     T = new(height, width, device=dev, dtype=torch.float32)
     nc = new(height, width, device=dev, dtype=torch.int32)
-    gs_blend_forward(width, height, bs["tile_ranges"], bs["ids"], proj["mean2d"], proj["conic"], opacity,
+    gs_blend_forward(width, height, bs["tile_ranges"], _list_ids(bs), proj["mean2d"], proj["conic"], opacity,
                      proj["rgb"], opts, image, T, nc, stream)
     return dict(image=image, T_final=T, n_contrib=nc)
 
@@ -463,7 +471,7 @@ def blend_backward(width, height, bs, proj, opacity, opts, fwd, dL_dimage, strea
     buf = torch.zeros(9 * n, device=opacity.device)
     g = dict(mean2d=buf[:2 * n].view(n, 2), conic=buf[2 * n:5 * n].view(n, 3), opacity=buf[5 * n:6 * n],
              rgb=buf[6 * n:].view(n, 3))
-    gs_blend_backward(width, height, bs["tile_ranges"], bs["ids"], proj["mean2d"], proj["conic"], opacity,
+    gs_blend_backward(width, height, bs["tile_ranges"], _list_ids(bs), proj["mean2d"], proj["conic"], opacity,
                       proj["rgb"], opts, fwd["T_final"], fwd["n_contrib"], dL_dimage.contiguous(), g["mean2d"],
                       g["conic"], g["opacity"], g["rgb"], stream)
     return g
