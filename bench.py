@@ -417,7 +417,7 @@ def run_ours(args):
         "small_scene_fused": small_line,
         **({"batched_views": batched_line} if batched_line else {}),
     }
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and ws_n == 1 and not args.no_cpu_baseline:  # the oracle on the host cores: N = 1 only
         line["cpu_baseline"] = cpu_baseline(cam, proj, bs, sc, dL, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
