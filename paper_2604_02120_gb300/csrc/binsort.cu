@@ -445,9 +445,10 @@ __device__ __forceinline__ void row_hist(uint32_t a, uint32_t w, int passes, int
 // instance offset comes from decoupled look-back over the tiles before it.
 // Each item's instances are its rectangle's tiles (TIGHT: each row's run of
 // tiles that meet the opacity-aware rule), row-major, at [offset, offset +
-// count).  Full rectangles: each warp writes its 32 items' instances as one
-// flat, coalesced range.  TIGHT: one thread per item, an item of more than 32
-// instances by the whole warp.
+// count).  Full rectangles: each warp writes its items of at most 32
+// instances as one flat, coalesced sequence, then each bigger item with the
+// whole warp.  TIGHT: one thread per item, an item of more than 32 instances
+// by the whole warp.
 // Writes stop at `limit`; the total goes to *total and, in graph
 // mode, to *count_out, with kErrCapacity raised when it exceeds the capacity.
 // The digit histograms of the written instances' tile ids go to hist
@@ -534,37 +535,48 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(int n_items, const uint3
         const bool big = c[r] > 32;
         if (!big)
             for (uint32_t y = 0; y * w < nw; ++y) row_hist(tile0 + y * tx, min(w, nw - y * w), tile_passes, s_d0, s_h);
-        unsigned bigs = __ballot_sync(0xffffffffu, big);
-        while (bigs) {  // the whole warp: one row's histogram per lane
-            const int src = __ffs(bigs) - 1;
-            bigs &= bigs - 1;
-            const uint32_t bnw = __shfl_sync(0xffffffffu, nw, src);
-            const uint32_t bw = __shfl_sync(0xffffffffu, w, src), bt0 = __shfl_sync(0xffffffffu, tile0, src);
-            const uint32_t btx = __shfl_sync(0xffffffffu, tx, src), bh = __shfl_sync(0xffffffffu, h, src);
-            for (uint32_t y = lane; y < bh && y * bw < bnw; y += 32)
-                row_hist(bt0 + y * btx, min(bw, bnw - y * bw), tile_passes, s_d0, s_h);
+        // Items of at most 32 instances, flat and coalesced: the warp walks the
+        // concatenation of their ranges (offsets exs, compacted over these items)
+        // 32 positions at a time; position j belongs to the last lane whose
+        // range starts at or before j (a lane without such an item shares its
+        // start with the next lane).
+        const uint32_t cs = big ? 0u : c[r];
+        uint32_t incl = cs;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
         }
-        // The warp's instances, flat: its 32 items' ranges are consecutive, so
-        // the warp writes [wbase, wbase + wn) 32 positions at a time (coalesced);
-        // position j belongs to the last lane whose range starts at or before j
-        // (a lane without instances shares its start with the next lane).
-        const uint64_t wbase = __shfl_sync(0xffffffffu, off, 0);
-        const uint32_t ex = (uint32_t)(off - wbase);
-        const uint32_t wend = __shfl_sync(0xffffffffu, ex + c[r], 31);
-        const uint32_t wn = wbase >= limit ? 0u : (uint32_t)min((uint64_t)wend, limit - wbase);
-        for (uint32_t j0 = 0; j0 < wn; j0 += 32) {
+        const uint32_t exs = incl - cs, tot_s = __shfl_sync(0xffffffffu, incl, 31);
+        for (uint32_t j0 = 0; j0 < tot_s; j0 += 32) {
             const uint32_t j = j0 + lane;
             int k = 0;
 #pragma unroll
             for (int step = 16; step > 0; step >>= 1)
-                if (__shfl_sync(0xffffffffu, ex, k + step) <= j) k += step;
-            const uint32_t q = j - __shfl_sync(0xffffffffu, ex, k);
+                if (__shfl_sync(0xffffffffu, exs, k + step) <= j) k += step;
+            const uint32_t q = j - __shfl_sync(0xffffffffu, exs, k);
+            const uint64_t p = __shfl_sync(0xffffffffu, off, k) + q;
             const uint32_t kw = __shfl_sync(0xffffffffu, w, k);  // 1 for a lane without instances
             const uint32_t kt = __shfl_sync(0xffffffffu, tile0, k) + (q / kw) * __shfl_sync(0xffffffffu, tx, k) + q % kw;
             const uint32_t ki = __shfl_sync(0xffffffffu, item[r], k);
-            if (j < wn) {
-                tkey[wbase + j] = kt;
-                tval[wbase + j] = ki;
+            if (j < tot_s && p < limit) {
+                tkey[p] = kt;
+                tval[p] = ki;
+            }
+        }
+        unsigned bigs = __ballot_sync(0xffffffffu, big);
+        while (bigs) {  // a bigger item: the whole warp, one row's histogram per lane, the instances flat
+            const int src = __ffs(bigs) - 1;
+            bigs &= bigs - 1;
+            const uint32_t bi = __shfl_sync(0xffffffffu, item[r], src), bnw = __shfl_sync(0xffffffffu, nw, src);
+            const uint32_t bw = __shfl_sync(0xffffffffu, w, src), bt0 = __shfl_sync(0xffffffffu, tile0, src);
+            const uint32_t btx = __shfl_sync(0xffffffffu, tx, src), bh = __shfl_sync(0xffffffffu, h, src);
+            const uint64_t boff = __shfl_sync(0xffffffffu, off, src);
+            for (uint32_t y = lane; y < bh && y * bw < bnw; y += 32)
+                row_hist(bt0 + y * btx, min(bw, bnw - y * bw), tile_passes, s_d0, s_h);
+            for (uint32_t j = lane; j < bnw; j += 32) {
+                tkey[boff + j] = bt0 + (j / bw) * btx + j % bw;
+                tval[boff + j] = bi;
             }
         }
     }
