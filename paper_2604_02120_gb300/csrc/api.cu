@@ -45,15 +45,17 @@ gs_status cuda_status(cudaError_t e, const char* what) {
 void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 unsigned* error_word() {
-    static unsigned* addr[64] = {nullptr};
+    static std::atomic<unsigned*> addr[64] = {};  // per device; threads may look it up at once
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    if (addr[dev] == nullptr) {
+    unsigned* a = addr[dev].load(std::memory_order_acquire);
+    if (a == nullptr) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_error_word) != cudaSuccess) return nullptr;
-        addr[dev] = static_cast<unsigned*>(p);
+        a = static_cast<unsigned*>(p);
+        addr[dev].store(a, std::memory_order_release);
     }
-    return addr[dev];
+    return a;
 }
 
 }  // namespace gs

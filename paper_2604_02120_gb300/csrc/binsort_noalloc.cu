@@ -5,6 +5,7 @@
 // gs_bin_sort takes from the caller lives here in one statically sized device
 // array instead.  Every device that loads this library holds the array
 // (kNoAllocScratchBytes) until the process exits.
+#include <atomic>
 #include <cstdio>
 
 #include "internal.h"
@@ -21,7 +22,7 @@ static __device__ __align__(256) unsigned char g_bin_sort_scratch[kNoAllocScratc
 // Device address of g_bin_sort_scratch for the current device, looked up once
 // per device (in host code the symbol only names a host-side stand-in).
 void* scratch_address(gs_status* st) {
-    static void* addr[64] = {nullptr};
+    static std::atomic<void*> addr[64] = {};  // per device; threads may look it up at once
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) {
@@ -33,17 +34,17 @@ void* scratch_address(gs_status* st) {
         *st = GS_ERR_UNSUPPORTED;
         return nullptr;
     }
-    if (addr[dev] == nullptr) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_bin_sort_scratch);
+    void* a = addr[dev].load(std::memory_order_acquire);
+    if (a == nullptr) {
+        e = cudaGetSymbolAddress(&a, g_bin_sort_scratch);
         if (e != cudaSuccess) {
             *st = cuda_status(e, "gs_bin_sort_noalloc: scratch address");
             return nullptr;
         }
-        addr[dev] = p;
+        addr[dev].store(a, std::memory_order_release);
     }
     *st = GS_OK;
-    return addr[dev];
+    return a;
 }
 
 }  // namespace

@@ -17,7 +17,7 @@ std::atomic<unsigned> g_next_slot{0};
 }  // namespace
 
 unsigned* tile_queue_slot(cudaStream_t s, cudaError_t* err) {
-    static unsigned* base[64] = {nullptr};
+    static std::atomic<unsigned*> base[64] = {};  // per device; threads may look it up at once
     int dev = 0;
     *err = cudaGetDevice(&dev);
     if (*err != cudaSuccess) return nullptr;
@@ -25,13 +25,15 @@ unsigned* tile_queue_slot(cudaStream_t s, cudaError_t* err) {
         *err = cudaErrorInvalidDevice;
         return nullptr;
     }
-    if (base[dev] == nullptr) {
+    unsigned* b = base[dev].load(std::memory_order_acquire);
+    if (b == nullptr) {
         void* p = nullptr;
         *err = cudaGetSymbolAddress(&p, g_tile_queue);
         if (*err != cudaSuccess) return nullptr;
-        base[dev] = static_cast<unsigned*>(p);
+        b = static_cast<unsigned*>(p);
+        base[dev].store(b, std::memory_order_release);
     }
-    unsigned* q = base[dev] + (g_next_slot.fetch_add(1, std::memory_order_relaxed) % kQueueSlots);
+    unsigned* q = b + (g_next_slot.fetch_add(1, std::memory_order_relaxed) % kQueueSlots);
     *err = cudaMemsetAsync(q, 0, sizeof(unsigned), s);
     return *err == cudaSuccess ? q : nullptr;
 }

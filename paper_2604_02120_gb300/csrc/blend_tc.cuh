@@ -687,14 +687,16 @@ cudaError_t launch_inst(const BlendArgs& a, int items, cudaStream_t s) {
     using LY = Layout<SS, CH, V>;
     constexpr int bytes = LY::BYTES;
     auto kern = k_blend_tc<V, CH, SS, DUMP>;
-    static int per_sm = 0, sms = 0;
-    if (per_sm == 0) {
+    static std::mutex mu;
+    static LaunchShape cache;
+    LaunchShape sh;
+    const cudaError_t es = cached_shape(mu, cache, sh, [&](LaunchShape& r) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;
         int dev = 0, smem_sm = 0;
         cudaFuncAttributes fa{};
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&r.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
             return e;
         if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
@@ -704,13 +706,15 @@ cudaError_t launch_inst(const BlendArgs& a, int items, cudaStream_t s) {
         const int by_smem = smem_sm / (bytes + (int)fa.sharedSizeBytes + 1024);
         const int by_threads = 2048 / kThreads;
         const int by_tmem = (int)(512 / LY::TCOLS);
-        per_sm = by_regs;
-        if (by_smem < per_sm) per_sm = by_smem;
-        if (by_threads < per_sm) per_sm = by_threads;
-        if (by_tmem < per_sm) per_sm = by_tmem;
-        if (per_sm < 1) per_sm = 1;
-    }
-    const int grid = items < per_sm * sms ? (items > 0 ? items : 1) : per_sm * sms;
+        r.per_sm = by_regs;
+        if (by_smem < r.per_sm) r.per_sm = by_smem;
+        if (by_threads < r.per_sm) r.per_sm = by_threads;
+        if (by_tmem < r.per_sm) r.per_sm = by_tmem;
+        if (r.per_sm < 1) r.per_sm = 1;
+        return cudaSuccess;
+    });
+    if (es != cudaSuccess) return es;
+    const int grid = items < sh.per_sm * sh.sms ? (items > 0 ? items : 1) : sh.per_sm * sh.sms;
     kern<<<grid, kThreads, bytes, s>>>(a);
     count_launches();
     return cudaGetLastError();

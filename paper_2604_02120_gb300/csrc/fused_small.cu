@@ -155,18 +155,30 @@ cudaError_t launch_fused(int n, const float* means, const float* scales, const f
     while (pow2 < max_per_tile) pow2 <<= 1;
     const size_t smem = sizeof(unsigned long long) * (size_t)pow2;
     // residency for the last shared-memory size, as for the other kernels once per process
+    // (under a lock: host threads may call at the same time)
+    static std::mutex mu;
     static size_t cached_smem = 0;
-    static int per_sm = 0, sms = 0;
+    static int cached_per_sm = 0, cached_sms = 0;
+    int per_sm = 0, sms = 0;
     cudaError_t e;
-    if (smem != cached_smem) {
-        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-            return e;
-        int dev = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFusedThreads, smem)) != cudaSuccess)
-            return e;
-        cached_smem = smem;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (smem != cached_smem) {
+            if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+                cudaSuccess)
+                return e;
+            int dev = 0, s_sms = 0, s_per_sm = 0;
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+            if ((e = cudaDeviceGetAttribute(&s_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s_per_sm, kern, kFusedThreads, smem)) !=
+                cudaSuccess)
+                return e;
+            cached_sms = s_sms;
+            cached_per_sm = s_per_sm;
+            cached_smem = smem;
+        }
+        per_sm = cached_per_sm;
+        sms = cached_sms;
     }
     const int ntiles = tiles_x(cams.cams[0].W) * tiles_y(cams.cams[0].H);
     // every block must be resident (cooperative launch); no more blocks than the larger phase needs

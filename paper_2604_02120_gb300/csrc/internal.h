@@ -1,9 +1,31 @@
 // Host-side declarations shared by the translation units of the library.
 #pragma once
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace gs {
+
+// Launch shape of a persistent kernel: blocks resident per SM and SM count.
+// `make` computes it once per process, under the lock, because host threads
+// may launch at the same time; a failed computation is retried by the next
+// call.  `make` sets per_sm >= 1.
+struct LaunchShape {
+    int per_sm = 0, sms = 0;
+};
+template <typename F>
+cudaError_t cached_shape(std::mutex& mu, LaunchShape& cache, LaunchShape& out, F make) {
+    std::lock_guard<std::mutex> lock(mu);
+    if (cache.per_sm == 0) {
+        LaunchShape s;
+        const cudaError_t e = make(s);
+        if (e != cudaSuccess) return e;
+        cache = s;
+    }
+    out = cache;
+    return cudaSuccess;
+}
 
 constexpr int kMaxViews = 32;
 

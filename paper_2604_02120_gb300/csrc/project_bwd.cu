@@ -263,12 +263,16 @@ cudaError_t launch_deg(int n, cudaStream_t s, const float* means, const float* s
                        const float* dconic, const float* drgb, float* dmeans, float* dscales, float* dquats,
                        float* dsh) {
     const size_t smem = 2 * sizeof(float) * kProjBwdThreads * sh_row<D>();
-    static bool attr = false;  // set once per process, as for the blend kernels
-    if (!attr) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(k_project_bwd<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
+    static std::mutex mu;  // the attribute is set once per process, as for the blend kernels
+    static bool attr = false;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!attr) {
+            const cudaError_t e =
+                cudaFuncSetAttribute(k_project_bwd<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
     }
     k_project_bwd<D><<<(n + kProjBwdThreads - 1) / kProjBwdThreads, kProjBwdThreads, smem, s>>>(
         n, means, scales, quats, sh, cams, radius, reinterpret_cast<const float2*>(dmean2d), dconic, drgb, dmeans,
