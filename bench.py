@@ -232,11 +232,42 @@ def run_ours(args):
     evals_fwd = int(fwd["n_contrib"].sum().item())
     n_inst = bs["n_instances"]
 
+    # ---- the step as four CUDA graphs (projection; bin/sort and tile order;
+    # forward; backward), replayed with CUDA events between them on the
+    # launching stream: the stage chain without per-launch host and queue gaps
+    graphs = []
+
+    def capture(fn):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            r = fn()
+        graphs.append(g)
+        return r
+
+    launches_c = gs.gs_launch_count()
+    g_proj = capture(lambda: gs.project(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam))
+
+    def sort_stage():
+        gs.gs_bin_sort_views(1, n, g_proj["mean2d"], g_proj["radius"], g_proj["depth"], [W], [H], capacity, ws, None,
+                             ids, ranges, count_dev=count_dev)
+        gs.tile_order(ranges, [W], [H], out=order)
+
+    capture(sort_stage)
+    g_bs = dict(tile_ranges=ranges, ids=ids)
+    g_fwd = capture(lambda: gs.blend_forward(W, H, g_bs, g_proj, dev["opacities"], opts))
+    capture(lambda: gs.blend_backward(W, H, g_bs, g_proj, dev["opacities"], opts, g_fwd, dL))
+    launches_per_step = gs.gs_launch_count() - launches_c  # the library's kernels in the four graphs
+    for _ in range(3):
+        for g in graphs:
+            g.replay()
+    torch.cuda.synchronize()
+    assert gs.gs_sync_status() == gs.GS_OK
+    assert torch.equal(g_fwd["image"], fwd["image"]) and torch.equal(g_fwd["n_contrib"], fwd["n_contrib"])
+
     K = args.steps
     E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     st_ev = [(E(), E()) for _ in range(K)]
     k_ev = [tuple(E() for _ in range(5)) for _ in range(K)]
-    launches0 = gs.gs_launch_count()
     with ClockSampler(local) as clk:
         if dist:
             dist.barrier()
@@ -245,13 +276,16 @@ def run_ours(args):
         for k in range(K):
             flush.zero_()
             st_ev[k][0].record(stream)
-            step(k_ev[k])
+            k_ev[k][0].record(stream)
+            for i, g in enumerate(graphs):
+                g.replay()
+                k_ev[k][i + 1].record(stream)
             st_ev[k][1].record(stream)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         wall = time.perf_counter() - wall0
-    launches = gs.gs_launch_count() - launches0
+    launches = launches_per_step * K
     clocks = clk.summary()
     assert gs.gs_sync_status() == gs.GS_OK  # also catches a capacity overflow of the bin/sort
     step_ms = [a.elapsed_time(b) for a, b in st_ev]
@@ -266,6 +300,18 @@ def run_ours(args):
         dev_ms = float(t.item())
     evals_step = 2 * evals_fwd  # forward and backward each examine sum(n_contrib) pairs
     value = ws_n * evals_step * K / (dev_ms / 1e3)
+
+    # ---- the same step launched call by call (no graphs), for comparison
+    Ke = min(K, 200)
+    e_ev = [(E(), E()) for _ in range(Ke)]
+    for k in range(Ke):
+        flush.zero_()
+        e_ev[k][0].record(stream)
+        step()
+        e_ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    assert gs.gs_sync_status() == gs.GS_OK
+    eager_ms = statistics.mean(a.elapsed_time(b) for a, b in e_ev)
 
     # ---- the same step with opacity-aware tile lists (same image; fewer instances)
     for _ in range(3):
@@ -405,12 +451,16 @@ def run_ours(args):
                    "blend_shape": tuned or "per-tile FP32 blocks",
                    "evals_per_step": evals_step, "instances": n_inst, "pixels": W * H,
                    "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replica x{ws_n}",
-                   "bin_sort": "no host synchronisation (fixed capacity, count on the device)"},
+                   "bin_sort": "no host synchronisation (fixed capacity, count on the device)",
+                   "launch": "each stage (project; bin_sort + tile_order; forward; backward) replayed as a CUDA "
+                             "graph, CUDA events between the stages"},
         "breakdown_ms": {"project": round(statistics.mean(proj_ms), 5), "bin_sort": round(statistics.mean(sort_ms), 5),
                          "blend_forward": round(f_ms, 5), "blend_backward": round(b_ms, 5),
                          "gaps": round(dev_ms / K - f_ms - b_ms - statistics.mean(proj_ms)
                                        - statistics.mean(sort_ms), 5)},
         "wall_ms_per_step": wall * 1e3 / K,
+        "eager_ms_per_step": round(eager_ms, 5),
+        "launches_per_step": launches_per_step,
         "blend_forward_by_variant": blend,
         "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
         "opacity_aware_lists": tight_line,
