@@ -646,14 +646,15 @@ def run_e2e(args, gs, torch, sc, cam, opts, capacity, dL, flush, evals_step, ws,
         return t
 
     # serialised
-    devb = {k: torch.empty_like(v, device="cuda") for k, v in host.items()}
+    devb = {k: v.to("cuda") for k, v in host.items()}
     br = gs.BatchRenderer(dict(devb, sh_degree=sc.sh_degree), [cam], opts, capacity)
     br.dL.copy_(dL.reshape(-1))
+    br.capture()  # the step replayed as one CUDA graph
 
     def step_serial(k):
         for key, v in host.items():
             devb[key].copy_(v, non_blocking=True)
-        br.step()
+        br.graph.replay()
         out_h["image"].copy_(br.image.view(3, H, W), non_blocking=True)
         out_h["mean2d"].copy_(br.g_mean2d, non_blocking=True)
         out_h["conic"].copy_(br.g_conic, non_blocking=True)
@@ -663,14 +664,15 @@ def run_e2e(args, gs, torch, sc, cam, opts, capacity, dL, flush, evals_step, ws,
     t_serial = timed(step_serial)
     del br, devb
     # pipelined
-    pr = gs.PipelinedRenderer(host, sc.sh_degree, [cam], opts, capacity, dL)
+    pr = gs.PipelinedRenderer(host, sc.sh_degree, [cam], opts, capacity, dL, graphs=True)
     t = timed(lambda k: pr.submit(k, host, out_h))
     K = args.steps
     return {"value": ws * evals_step * K / t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": t * 1e3 / K, "serialised_ms_per_step": t_serial * 1e3 / K,
             "timing": "host wall clock around K steps incl. L2 flush writes; every step copies its inputs in and its "
                       "image and gradients out; pipelined: step k+1's upload and step k-1's download overlap step "
-                      "k's compute (independent frames); serialised_ms_per_step: copy in, compute, copy out"}
+                      "k's compute (independent frames); serialised_ms_per_step: copy in, compute, copy out; "
+                      "the compute of a step is one CUDA graph replay (gs.BatchRenderer.capture)"}
 
 
 # ------------------------------------------------------------ CPU oracle ----

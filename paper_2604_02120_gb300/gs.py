@@ -527,7 +527,8 @@ class PipelinedRenderer:
     alternate (double-buffered device inputs and outputs); compute runs on
     the current stream.  The frames must be independent (rendering many
     scenes or camera sets): a training loop, whose next inputs depend on this
-    step's gradients, gains nothing from it.
+    step's gradients, gains nothing from it.  graphs=True replays each
+    renderer's step as a CUDA graph.
 
     submit(k, host_in, host_out) enqueues frame k: host_in maps
     means/scales/quats/opacities/sh to pinned tensors shaped like the scene,
@@ -537,13 +538,20 @@ class PipelinedRenderer:
 
     KEYS = ("means", "scales", "quats", "opacities", "sh")
 
-    def __init__(self, template_scene, sh_degree, cams, opts, capacity, dL, device="cuda"):
+    def __init__(self, template_scene, sh_degree, cams, opts, capacity, dL, device="cuda", graphs=False):
+        # graphs: each renderer's step is recorded once in a CUDA graph (after
+        # one run on the template scene's values) and replayed per frame, one
+        # host call instead of one per kernel
         self.r = []
         for _ in range(2):
             dev = {k: torch.empty_like(template_scene[k], device=device) for k in self.KEYS}
             dev["sh_degree"] = sh_degree
             r = BatchRenderer(dev, cams, opts, capacity, device)
             r.dL.copy_(dL.reshape(-1))
+            if graphs:
+                for k in self.KEYS:
+                    dev[k].copy_(template_scene[k])
+                r.capture()
             self.r.append(r)
         self.up, self.down = torch.cuda.Stream(device), torch.cuda.Stream(device)
         E = torch.cuda.Event
@@ -566,7 +574,10 @@ class PipelinedRenderer:
         cur.wait_event(self.in_ready[i])
         if self.used[i]:
             cur.wait_event(self.out_done[i])  # its results have left the output buffers
-        r.step()
+        if r.graph is not None:
+            r.graph.replay()
+        else:
+            r.step()
         self.done[i].record(cur)
         with torch.cuda.stream(self.down):
             self.down.wait_event(self.done[i])

@@ -23,14 +23,15 @@ def _host(sc):
              ("sh", sc.sh))}
 
 
-def test_pipelined_frames_equal_separate_renders():
+@pytest.mark.parametrize("graphs", [False, True])
+def test_pipelined_frames_equal_separate_renders(graphs):
     a, b = scenes.make_config(0, seed=0), scenes.make_config(0, seed=1)
     cam = a.cameras[0]
     dL = torch.from_numpy(scenes.upstream_grad(0, [cam])[0]).cuda()
     opts = gs.make_opts("fp16_split", bg=(0.1, 0.2, 0.3))
     ha, hb = _host(a), _host(b)
     n = a.n
-    pr = gs.PipelinedRenderer(ha, a.sh_degree, [cam], opts, 1 << 20, dL)
+    pr = gs.PipelinedRenderer(ha, a.sh_degree, [cam], opts, 1 << 20, dL, graphs=graphs)
 
     def outs():
         return {"image": torch.empty(3, cam.height, cam.width).pin_memory(), "mean2d": torch.empty(n, 2).pin_memory(),
