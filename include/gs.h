@@ -25,6 +25,18 @@
  *    errors (bad arguments, launch failures) are returned at once.  Faults the
  *    kernels detect (a device wait that exceeded its time limit) are recorded
  *    in a per-device error word that gs_sync_status() reads and clears.
+ *  - Host threads may call the library at the same time, each on its own
+ *    stream: launch shapes are computed once under a lock, and each persistent
+ *    blend launch takes its own tile-queue slot (a pool of 1024).  Exceptions:
+ *    gs_project_bin_small and gs_bin_sort_noalloc calls must not overlap (one
+ *    grid-barrier word, one scratch area), and the error word is shared, so
+ *    gs_sync_status() may report another call's fault.
+ *  - Calls that do not synchronise can be recorded in a CUDA graph.  The
+ *    synchronising ones are gs_bin_sort, gs_bin_sort_noalloc and
+ *    gs_bin_sort_views with a host count, gs_blend_autotune,
+ *    gs_measure_peaks and gs_sync_status.  The first call of an entry point
+ *    on a device sets kernel attributes and looks up device symbols: make it
+ *    before any capture.
  */
 #ifndef GS_H
 #define GS_H
