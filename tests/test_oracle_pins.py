@@ -575,3 +575,51 @@ def test_project_backward_matches_central_differences(deg, lowpass):
     assert (g["dsh"][0, :, 1] == 0).all() and np.abs(g["dsh"][0, :, 0]).max() > 0
     # the projection depends on q only through q / |q|: its gradient is orthogonal to q
     assert np.abs((g["dquats"] * quats).sum(1)).max() < 1e-9 * np.abs(g["dquats"]).max()
+
+
+@pytest.mark.parametrize("seed,W,H", [(0, 48, 40), (3, 77, 45)])
+def test_three_sigma_rectangle_bounds_what_it_drops(seed, W, H):
+    """Tile membership by the 3-sigma square (reading 9): at every pixel
+    centre outside the tiles a splat is listed on, its alpha is at most
+    o e^-4.5, because the square reaches ceil(3 sqrt(lambda_max)) pixels and
+    the Mahalanobis distance beyond it is at least 3 (FP64, every splat and
+    pixel).  The truncation this causes is reported: the brute-force image
+    with and without the rectangle."""
+    from gpu_common import report
+
+    sc = scenes.tiny_scene(seed, n=64, width=W, height=H, opac_lo=0.3, opac_hi=0.99)
+    cam = sc.cameras[0]
+    pr = oracle.project(sc.means, sc.scales, sc.quats, sc.sh, 0, cam)
+    d32 = pr["depth"].astype(np.float32)
+    bs = oracle.bin_sort(pr["mean2d"], pr["radius"], d32, W, H)
+    o = sc.opacities.astype(np.float64)
+    ys, xs = np.mgrid[0:H, 0:W] + 0.5
+    tile_of = (ys.astype(int) // 16) * cam.tiles_x + xs.astype(int) // 16
+    listed = [set() for _ in range(sc.n)]
+    for t in range(cam.num_tiles):
+        for g in bs["ids"][bs["tile_ranges"][2 * t]:bs["tile_ranges"][2 * t + 1]]:
+            listed[g].add(t)
+    worst, worst_alpha, outside = 0.0, 0.0, 0
+    for g in range(sc.n):
+        if pr["radius"][g] <= 0:
+            continue
+        mask = ~np.isin(tile_of, list(listed[g]))
+        A, B, C = pr["conic"][g]
+        dx, dy = pr["mean2d"][g, 0] - xs[mask], pr["mean2d"][g, 1] - ys[mask]
+        power = -0.5 * (A * dx * dx + 2 * B * dx * dy + C * dy * dy)
+        if power.size:
+            worst = max(worst, float((np.exp(power)).max()))
+            worst_alpha = max(worst_alpha, float(o[g] * np.exp(power.max())))
+            outside += int(power.size)
+            assert power.max() <= -4.5 + 1e-9, (g, power.max())
+    assert outside > 1000
+    bg = (0.1, 0.2, 0.3)
+    args = (pr["mean2d"], pr["conic"], o, pr["rgb"], pr["radius"], d32, W, H)
+    rect = oracle.brute_force(*args, bg=bg, use_rect=True)
+    full = oracle.brute_force(*args, bg=bg, use_rect=False)
+    diff = np.abs(rect["image"] - full["image"])
+    report(f"three_sigma_truncation_{W}x{H}", {"max_abs_image": float(diff.max()),
+                                             "pixels_changed": float((diff.max(0) > 0).mean()),
+                                             "max_exp_power_outside": worst, "max_alpha_outside": worst_alpha})
+    if worst_alpha < 1 / 255:  # every dropped pair would be skipped: the rectangle changes nothing
+        assert diff.max() == 0 and np.array_equal(rect["n_contrib"] > 0, full["n_contrib"] > 0)
