@@ -577,8 +577,9 @@ def test_project_backward_matches_central_differences(deg, lowpass):
     assert np.abs((g["dquats"] * quats).sum(1)).max() < 1e-9 * np.abs(g["dquats"]).max()
 
 
-@pytest.mark.parametrize("seed,W,H", [(0, 48, 40), (3, 77, 45)])
-def test_three_sigma_rectangle_bounds_what_it_drops(seed, W, H):
+@pytest.mark.parametrize("seed,W,H,n,scales", [(0, 48, 40, 64, (-3.0, -1.5)), (3, 77, 45, 64, (-3.0, -1.5)),
+                                                (7, 160, 128, 600, (-2.2, -0.6))])
+def test_three_sigma_rectangle_bounds_what_it_drops(seed, W, H, n, scales):
     """Tile membership by the 3-sigma square (reading 9): at every pixel
     centre outside the tiles a splat is listed on, its alpha is at most
     o e^-4.5, because the square reaches ceil(3 sqrt(lambda_max)) pixels and
@@ -587,7 +588,8 @@ def test_three_sigma_rectangle_bounds_what_it_drops(seed, W, H):
     with and without the rectangle."""
     from gpu_common import report
 
-    sc = scenes.tiny_scene(seed, n=64, width=W, height=H, opac_lo=0.3, opac_hi=0.99)
+    sc = scenes.tiny_scene(seed, n=n, width=W, height=H, scale_lo=scales[0], scale_hi=scales[1], opac_lo=0.3,
+                           opac_hi=0.99)
     cam = sc.cameras[0]
     pr = oracle.project(sc.means, sc.scales, sc.quats, sc.sh, 0, cam)
     d32 = pr["depth"].astype(np.float32)
