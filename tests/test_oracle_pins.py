@@ -625,3 +625,80 @@ def test_three_sigma_rectangle_bounds_what_it_drops(seed, W, H, n, scales):
                                              "max_exp_power_outside": worst, "max_alpha_outside": worst_alpha})
     if worst_alpha < 1 / 255:  # every dropped pair would be skipped: the rectangle changes nothing
         assert diff.max() == 0 and np.array_equal(rect["n_contrib"] > 0, full["n_contrib"] > 0)
+
+
+def test_blend_grad_central_differences_at_1080p_clustered():
+    """The analytic blend gradient at full scale (1920x1080, 1M clustered
+    Gaussians, 11.4M instances): for 16 seeded visible Gaussians (non-zero
+    analytic gradient, listed on at most 4 tiles), each of the 9 blend
+    parameters is perturbed by h = 1e-4 max(1, |theta|) (1e-4 px for the
+    mean, a position) and only the tiles the
+    splat is listed on are re-rendered (the loss changes nowhere else).  A
+    parameter is discarded when a decision flips inside the step (the two step
+    sizes disagree, or n_contrib changes); the relative L2 error per group
+    must stay below 1e-3 and is reported."""
+    from gpu_common import report
+
+    sc = scenes.make_config(2, seed=0)
+    cam = sc.cameras[0]
+    W, H = cam.width, cam.height
+    pr = oracle.project(sc.means, sc.scales, sc.quats, sc.sh, sc.sh_degree, cam)
+    bs = oracle.bin_sort(pr["mean2d"], pr["radius"], pr["depth"].astype(np.float32), W, H)
+    rng = np.random.default_rng(17)
+    w = rng.standard_normal((3, H, W))
+    bg = (0.1, 0.2, 0.3)
+    p = dict(mean2d=np.ascontiguousarray(pr["mean2d"], np.float64), conic=np.ascontiguousarray(pr["conic"], np.float64),
+             opacity=sc.opacities.astype(np.float64), rgb=np.ascontiguousarray(pr["rgb"], np.float64))
+    ranges = bs["tile_ranges"]
+    lens = ranges[1::2].astype(np.int64) - ranges[0::2]
+    inst_tile = np.repeat(np.arange(cam.num_tiles), lens)
+    g_an = oracle.blend_grad(W, H, ranges, bs["ids"], p["mean2d"], p["conic"], p["opacity"], p["rgb"], w, bg=bg,
+                             n_threads=os.cpu_count() or 1)
+    listed = np.bincount(bs["ids"], minlength=sc.n)
+    visible = np.nonzero((g_an["opacity"] != 0) & (listed > 0) & (listed <= 4))[0]
+    sample = rng.choice(visible, 16, replace=False)  # visible, and cheap to re-render
+    chosen = np.zeros(sc.n, bool)
+    chosen[sample] = True
+    sel = chosen[bs["ids"]]
+    tiles_of = {int(g): np.unique(inst_tile[sel & (bs["ids"] == g)]).astype(np.int32) for g in sample}
+
+    def loss(tiles):
+        r = oracle.blend(W, H, ranges, bs["ids"], p["mean2d"], p["conic"], p["opacity"], p["rgb"], bg=bg,
+                         tile_subset=tiles)
+        tx = tiles % cam.tiles_x
+        ty = tiles // cam.tiles_x
+        total, ncs = 0.0, []
+        for x0, y0 in zip(16 * tx, 16 * ty):
+            total += float(np.sum(w[:, y0:y0 + 16, x0:x0 + 16] * r["image"][:, y0:y0 + 16, x0:x0 + 16]))
+            ncs.append(r["n_contrib"][y0:y0 + 16, x0:x0 + 16].copy())
+        return total, ncs
+
+    rel, discarded, nonzero = {}, 0, 0
+    for name, arr in p.items():
+        fd_all, an_all = [], []
+        for g in sample:
+            for j in range(arr.shape[1] if arr.ndim == 2 else 1):
+                idx = (g, j) if arr.ndim == 2 else (g,)
+                base = arr[idx]
+                ests, flipped = [], False
+                scale = 1.0 if name == "mean2d" else max(1.0, abs(base))  # a position: steps in pixels
+                for h in (1e-4 * scale, 2.5e-5 * scale):
+                    arr[idx] = base + h
+                    lp, ncp = loss(tiles_of[int(g)])
+                    arr[idx] = base - h
+                    lm, ncm = loss(tiles_of[int(g)])
+                    arr[idx] = base
+                    ests.append((lp - lm) / (2 * h))
+                    flipped |= any(not np.array_equal(a, b) for a, b in zip(ncp, ncm))
+                if flipped or abs(ests[0] - ests[1]) > 1e-4 * (abs(ests[0]) + 1e-9):
+                    discarded += 1
+                    continue
+                fd_all.append(ests[0])
+                an_all.append(g_an[name][idx])
+                nonzero += an_all[-1] != 0
+        fd_all, an_all = np.array(fd_all), np.array(an_all)
+        rel[name] = float(np.linalg.norm(an_all - fd_all) / max(np.linalg.norm(fd_all), 1e-30))
+    report("blend_grad_fd_1080p_clustered", {"rel_l2": rel, "discarded": discarded, "checked_nonzero": int(nonzero)})
+    assert discarded <= 0.2 * 16 * 9 and nonzero >= 100
+    for name, e in rel.items():
+        assert e < 1e-3, (name, e)
