@@ -69,6 +69,26 @@ def parse_args():
     return p.parse_args()
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type); never raises."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:  # lscpu missing or failing: fall through
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine() or "unknown"
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -730,7 +750,7 @@ def cpu_baseline(cam, proj, bs, sc, dL, seconds):
     while reps == 0 or dt < seconds:
         e1, d1 = _oracle_sample(oracle, W, H, ranges, ids, m2, co, op, rgb, g, order[:k], threads)
         ev, dt, reps = ev + e1, dt + d1, reps + 1
-    return {"value": ev / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+    return {"value": ev / dt, "unit": UNIT, "cores": threads, "cpu_model": cpu_model(), "kind": "oracle",
             "sample": f"{k} of {len(busy)} non-empty tiles (random, seed 0) x {reps}, FP64 blend forward + "
                       f"gradient, {dt:.1f} s", "seconds": dt}
 
@@ -769,7 +789,8 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.config] + WORKLOAD_NOTE,
                        "step": "FP64 oracle blend forward + gradient on a tile sample"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "cpu_model": cpu_model(), "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -32,6 +32,7 @@ def test_reference_arm_json_line(oracle_lib):
     assert d["config"]["workload"].startswith("256x256, 10k Gaussians")
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert isinstance(cb["cpu_model"], str) and cb["cpu_model"]
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
