@@ -42,3 +42,26 @@ def test_reference_arm_other_ranks_exit_quietly():
     p = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}, "--config", "0", "--steps", "1", "--warmup", "0")
     assert p.returncode == 0, p.stderr[-2000:]
     assert not [l for l in p.stdout.splitlines() if l.startswith("{")]
+
+
+def test_gpu_arm_cpu_baseline_leg(oracle_lib):
+    """bench.cpu_baseline (the GPU arm's oracle leg) on CPU tensors of the
+    256x256 workload: a bounded run that reports its sample, threads and CPU model."""
+    import numpy as np
+    import torch
+
+    import bench
+    import oracle
+    from paper_2604_02120_gb300 import scenes
+
+    sc = scenes.make_config(0)
+    cam = sc.cameras[0]
+    pr = oracle.project(sc.means, sc.scales, sc.quats, sc.sh, sc.sh_degree, cam)
+    d32 = pr["depth"].astype(np.float32)
+    bs = oracle.bin_sort(pr["mean2d"], pr["radius"], d32, cam.width, cam.height)
+    proj = {k: torch.from_numpy(np.ascontiguousarray(pr[k], np.float32)) for k in ("mean2d", "conic", "rgb")}
+    tb = dict(tile_ranges=torch.from_numpy(bs["tile_ranges"].view(np.int32)), ids=torch.from_numpy(bs["ids"].view(np.int32)))
+    dL = torch.from_numpy(scenes.upstream_grad(0, [cam])[0])
+    cb = bench.cpu_baseline(cam, proj, tb, sc, dL, 0.5)
+    assert cb["kind"] == "oracle" and cb["value"] > 0 and cb["cores"] >= 1 and cb["cpu_model"]
+    assert cb["seconds"] >= 0.5 and "non-empty tiles" in cb["sample"]
