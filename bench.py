@@ -257,9 +257,13 @@ def run_ours(args):
     # launching stream: the stage chain without per-launch host and queue gaps
     graphs = []
 
+    # with a process group, its watchdog thread queries CUDA events while the
+    # main thread captures: only this thread's calls are checked then
+    mode = {"capture_error_mode": "thread_local"} if dist else {}
+
     def capture(fn):
         g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
+        with torch.cuda.graph(g, **mode):
             r = fn()
         graphs.append(g)
         return r
