@@ -28,6 +28,23 @@ __global__ void k_selftest_wait(uint64_t limit_ns, unsigned* err) {
 }
 }  // namespace
 
+void clear_error() { g_last_error[0] = 0; }
+
+static bool size_ok(int32_t W, int32_t H) { return W > 0 && H > 0 && W <= (1 << 20) && H <= (1 << 20); }
+
+bool fill_views(int32_t n_views, const int32_t* widths, const int32_t* heights, ViewDesc* views, int* total_tiles) {
+    long long tiles = 0, pix = 0;
+    for (int v = 0; v < n_views; ++v) {
+        if (!size_ok(widths[v], heights[v])) return false;
+        views[v] = ViewDesc{widths[v], heights[v], tiles_x(widths[v]), (int)tiles, pix};
+        tiles += (long long)tiles_x(widths[v]) * tiles_y(heights[v]);
+        pix += (long long)widths[v] * heights[v];
+        if (tiles >= (1ll << 31)) return false;
+    }
+    *total_tiles = (int)tiles;
+    return true;
+}
+
 void set_error(const char* fmt, ...) {
     va_list ap;
     va_start(ap, fmt);
@@ -63,23 +80,6 @@ unsigned* error_word() {
 using namespace gs;
 
 namespace {
-
-bool size_ok(int32_t W, int32_t H) { return W > 0 && H > 0 && W <= (1 << 20) && H <= (1 << 20); }
-
-// View table of n_views images (HOST arrays); false if a size is out of range
-// or the views hold 2^31 tiles or more.
-bool fill_views(int32_t n_views, const int32_t* widths, const int32_t* heights, ViewDesc* views, int* total_tiles) {
-    long long tiles = 0, pix = 0;
-    for (int v = 0; v < n_views; ++v) {
-        if (!size_ok(widths[v], heights[v])) return false;
-        views[v] = ViewDesc{widths[v], heights[v], tiles_x(widths[v]), (int)tiles, pix};
-        tiles += (long long)tiles_x(widths[v]) * tiles_y(heights[v]);
-        pix += (long long)widths[v] * heights[v];
-        if (tiles >= (1ll << 31)) return false;
-    }
-    *total_tiles = (int)tiles;
-    return true;
-}
 
 gs_status check_views(const char* who, int32_t n_views, const int32_t* widths, const int32_t* heights) {
     if (n_views < 1 || n_views > kMaxViews || !widths || !heights) {
@@ -277,11 +277,14 @@ gs_status gs_project(int32_t n, const float* means, const float* scales, const f
 
 gs_status gs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t width, int32_t height, size_t* bytes) {
     g_last_error[0] = 0;
-    if (n < 0 || capacity < 0 || capacity >= (int64_t(1) << 32) || !size_ok(width, height) || !bytes) {
+    ViewDesc view;
+    int total_tiles = 0;
+    if (n < 0 || capacity < 0 || capacity >= (int64_t(1) << 32) || !bytes ||
+        !fill_views(1, &width, &height, &view, &total_tiles)) {
         set_error("gs_bin_sort_workspace_size: bad arguments");
         return GS_ERR_INVALID_ARG;
     }
-    *bytes = bin_sort_workspace_bytes(n, capacity, tiles_x(width) * tiles_y(height));
+    *bytes = bin_sort_workspace_bytes(n, capacity, total_tiles);
     return GS_OK;
 }
 

@@ -59,8 +59,13 @@ size_t gs_bin_sort_noalloc_max_bytes(void) { return kNoAllocScratchBytes; }
 gs_status gs_bin_sort_noalloc(int32_t n, const float* mean2d, const int32_t* radius, const float* depth,
                               int32_t width, int32_t height, int64_t capacity, uint64_t* keys_sorted,
                               uint32_t* ids_sorted, uint32_t* tile_ranges, int64_t* n_instances, gs_stream stream) {
-    if (n < 0 || capacity < 0 || capacity >= (int64_t(1) << 32) || width <= 0 || height <= 0 ||
-        width > (1 << 20) || height > (1 << 20) || !n_instances || !tile_ranges) {
+    clear_error();
+    SortViews sv{};
+    sv.num_views = 1;
+    sv.n_per_view = n;
+    // the same view check as gs_bin_sort: each side 1..2^20 and fewer than 2^31 tiles
+    if (n < 0 || capacity < 0 || capacity >= (int64_t(1) << 32) || !n_instances || !tile_ranges ||
+        !fill_views(1, &width, &height, sv.views, &sv.total_tiles)) {
         set_error("gs_bin_sort_noalloc: bad arguments");
         return GS_ERR_INVALID_ARG;
     }
@@ -72,11 +77,6 @@ gs_status gs_bin_sort_noalloc(int32_t n, const float* mean2d, const int32_t* rad
         set_error("gs_bin_sort_noalloc: null output pointer");
         return GS_ERR_INVALID_ARG;
     }
-    SortViews sv{};
-    sv.num_views = 1;
-    sv.n_per_view = n;
-    sv.total_tiles = tiles_x(width) * tiles_y(height);
-    sv.views[0] = ViewDesc{width, height, tiles_x(width), 0, 0};
     const size_t need = bin_sort_workspace_bytes(n, capacity, sv.total_tiles);
     if (need > kNoAllocScratchBytes) {
         set_error("gs_bin_sort_noalloc: n = %d and capacity = %lld need %zu bytes of scratch, more than the "

@@ -99,8 +99,14 @@ struct GradArgs {
     float* drgb;
 };
 
-// Thread-local error text (gs_last_error).
+// Thread-local error text (gs_last_error); clear_error empties it at the
+// start of a call.
 void set_error(const char* fmt, ...);
+void clear_error();
+// View table of n_views images (HOST width/height arrays) and their total
+// tile count; false if a size is out of range (each side 1..2^20) or the
+// views hold 2^31 tiles or more.
+bool fill_views(int32_t n_views, const int32_t* widths, const int32_t* heights, ViewDesc* views, int* total_tiles);
 // A CUDA error from the last launch or runtime call, mapped to a status.
 gs_status cuda_status(cudaError_t e, const char* what);
 // Device address of the current device's error word.

@@ -131,3 +131,31 @@ def test_small_entry_point_checks(lib):
     _expect(lib, lib.gs_alpha_power_min(-1, P, P, None), INVALID, "gs_alpha_power_min")
     _expect(lib, lib.gs_alpha_power_min(10, None, P, None), INVALID, "gs_alpha_power_min")
     _expect(lib, lib.gs_selftest_bounded_wait(-1, None), INVALID, "gs_selftest_bounded_wait")
+
+
+def test_bin_sort_noalloc_checks(lib):
+    """The allocation-free bin/sort rejects what gs_bin_sort rejects, before
+    any CUDA call: sizes beyond 2^20 per side, images of 2^31 tiles or more
+    (where tiles_x * tiles_y would overflow an int), null pointers, and
+    sizes whose scratch exceeds the built-in array."""
+    cnt = ctypes.c_int64(0)
+
+    def call(n=100, w=64, h=48, cap=1000, m=P, ids=P, ranges=P, ninst=ctypes.byref(cnt)):
+        return lib.gs_bin_sort_noalloc(n, m, P, P, w, h, cap, None, ids, ranges, ninst, None)
+
+    _expect(lib, call(n=-1), INVALID, "gs_bin_sort_noalloc")
+    _expect(lib, call(w=0), INVALID, "gs_bin_sort_noalloc")
+    _expect(lib, call(h=(1 << 20) + 1), INVALID, "gs_bin_sort_noalloc")
+    _expect(lib, call(w=1 << 20, h=1 << 19), INVALID, "gs_bin_sort_noalloc")  # 2^31 tiles
+    _expect(lib, call(w=1 << 20, h=1 << 20), INVALID, "gs_bin_sort_noalloc")  # 2^32 tiles
+    _expect(lib, call(cap=1 << 32), INVALID, "gs_bin_sort_noalloc")
+    _expect(lib, call(m=None), INVALID, "gs_bin_sort_noalloc")
+    _expect(lib, call(ids=None), INVALID, "gs_bin_sort_noalloc")
+    _expect(lib, call(ranges=None), INVALID, "gs_bin_sort_noalloc")
+    _expect(lib, call(ninst=None), INVALID, "gs_bin_sort_noalloc")
+    _expect(lib, call(n=1 << 24, cap=1 << 28), WORKSPACE, "gs_bin_sort_noalloc")
+    # a successful check leaves no earlier message behind: the size query succeeds and clears it
+    need = ctypes.c_size_t(0)
+    assert lib.gs_bin_sort_workspace_size(100, 1000, 64, 48, ctypes.byref(need)) == gs.GS_OK
+    assert lib.gs_last_error() == b""
+    assert lib.gs_bin_sort_workspace_size(100, 1000, 1 << 20, 1 << 20, ctypes.byref(need)) == INVALID
