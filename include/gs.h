@@ -263,16 +263,19 @@ gs_status gs_bin_sort(int32_t n, const float* mean2d, const int32_t* radius, con
  * Opacity-aware lists (the tighter tile intersection; not in the paper): with
  * conic (the items' conics, 3 floats each, as gs_project writes them) and
  * power_min (one float per Gaussian, from gs_alpha_power_min) a splat keeps a
- * tile of its rectangle only if its exponent can reach power_min at some pixel
- * centre of the tile, i.e. if the tile's box of centre offsets meets the
- * ellipse q(d) <= -2 power_min; each rectangle row keeps one run of tiles,
- * found in closed form from the ellipse's extent within the row.  Dropped
- * splats would fail the 1/255 test at every pixel of the tile, so images and
- * T_final are those of the full lists (n_contrib counts list positions and
- * shrinks).  The rule is FP32 with one rounding per operation, so the lists
- * are reproducible bit for bit.  A conic that is not positive definite keeps
- * its whole rectangle; power_min >= 0 keeps no tile.  Both NULL: the full
- * rectangles.
+ * tile of its rectangle only if its exponent can reach power_min somewhere in
+ * the tile's box of pixel-centre offsets, i.e. if that box meets the region
+ * q(d) = A dx^2 + 2 B dx dy + C dy^2 <= -2 power_min; each rectangle row keeps
+ * one run of tiles, found in closed form from the region's extent within the
+ * row (an ellipse, or for a nearly singular or indefinite conic, as needle-
+ * shaped splats give, a band around its null line).  Dropped splats would
+ * fail the 1/255 test at every pixel of the tile, so images and T_final are
+ * those of the full lists (n_contrib counts list positions and shrinks).  The
+ * rule is FP32 with one rounding per operation in a fixed order, so the lists
+ * are reproducible bit for bit; against the exact (FP64) decision they differ
+ * only on pairs whose box lies within rounding of the threshold.  A or C <= 0
+ * keeps the whole rectangle; power_min >= 0 keeps no tile.  Both NULL: the
+ * full rectangles.
  */
 gs_status gs_bin_sort_views(int32_t n_views, int32_t n_per_view, const float* mean2d, const int32_t* radius,
                             const float* depth, const float* conic, const float* power_min,
@@ -315,10 +318,16 @@ gs_status gs_alpha_power_min(int32_t n, const float* opacity, float* power_min, 
  *  - It calls no allocation routine.  The first call on a device looks up
  *    the array's device address (once per device, that device current); make
  *    that first call before any stream capture.
+ *  - Rejects with GS_ERR_INVALID_ARG, before any CUDA call, what gs_bin_sort
+ *    rejects: a side outside 1..2^20, an image of 2^31 tiles or more, null
+ *    pointers.
  *  - All calls share the one array: calls that overlap on the GPU (other
  *    streams, other host threads) race and must be serialised by the caller.
  *    The array's previous contents never matter (everything read is written
  *    first within the call).
+ *  - The array's device address is kept for the life of the process: a
+ *    cudaDeviceReset between calls is not supported (the same holds for the
+ *    library's error word).
  */
 size_t gs_bin_sort_noalloc_max_bytes(void);
 gs_status gs_bin_sort_noalloc(int32_t n, const float* mean2d, const int32_t* radius, const float* depth,

@@ -106,7 +106,10 @@ def bin_sort(mean2d, radius, depth, width, height, capacity=None, conic=None, po
     """Duplicate + stable sort; mean2d may be the CUDA path's float32 values
     (converted exactly to double), depth is used through its float32 bits.
     With conic and power_min (float32, per Gaussian) a tile is kept only if
-    the splat's exponent can reach power_min in it (opacity-aware lists)."""
+    the largest exponent over the tile's box of pixel-centre offsets reaches
+    power_min (opacity-aware lists, decided in FP64); then ``ambiguous`` holds
+    one row (tile, Gaussian, decision) per rectangle pair whose decision lies
+    within rounding of the threshold."""
     n = int(mean2d.shape[0])
     mean2d = _c(mean2d, np.float64)
     radius = _c(radius, np.int32)
@@ -120,15 +123,22 @@ def bin_sort(mean2d, radius, depth, width, height, capacity=None, conic=None, po
     ids = np.zeros(max(cap, 1), np.uint32)
     ranges = np.zeros(2 * num_tiles(width, height), np.uint32)
     tight = conic is not None and power_min is not None
-    m32 = _c(mean2d, np.float32) if tight else None
     c32 = _c(conic, np.float32) if tight else None
     p32 = _c(power_min, np.float32) if tight else None
-    I = lib().oracle_bin_sort(ctypes.c_int(n), _p(mean2d), _p(radius), _p(depth), ctypes.c_int(width),
-                              ctypes.c_int(height), ctypes.c_int64(cap), _p(keys), _p(ids), _p(ranges),
-                              _p(m32), _p(c32), _p(p32))
+    amb_cap = 1 << 16
+    while True:
+        amb = np.zeros((amb_cap, 3), np.int64)
+        n_amb = ctypes.c_int64(0)
+        I = lib().oracle_bin_sort(ctypes.c_int(n), _p(mean2d), _p(radius), _p(depth), ctypes.c_int(width),
+                                  ctypes.c_int(height), ctypes.c_int64(cap), _p(keys), _p(ids), _p(ranges),
+                                  _p(c32), _p(p32), _p(amb), ctypes.c_int64(amb_cap), ctypes.byref(n_amb))
+        if n_amb.value <= amb_cap:
+            break
+        amb_cap = int(n_amb.value)
+    amb = amb[:n_amb.value]
     if I < 0:
-        return dict(n_instances=-1, keys=None, ids=None, tile_ranges=ranges)
-    return dict(n_instances=int(I), keys=keys[:I], ids=ids[:I], tile_ranges=ranges)
+        return dict(n_instances=-1, keys=None, ids=None, tile_ranges=ranges, ambiguous=amb)
+    return dict(n_instances=int(I), keys=keys[:I], ids=ids[:I], tile_ranges=ranges, ambiguous=amb)
 
 
 def _count_instances(mean2d, radius, width, height) -> int:

@@ -499,92 +499,90 @@ void oracle_project_backward(int n, const float* means, const float* scales, con
 // (tile << 32) | float_bits(depth), then stable-sort by key; tile_ranges[t]
 // = [start, end) of tile t in the sorted list.  Returns the number of
 // instances, or -1 if it exceeds capacity.
-// Opacity-aware tile membership (the tighter intersection of the "next"
-// steps): keep tile (tx, ty) for a splat if its exponent can reach power_min
-// at some pixel centre of the tile, that is if the tile's box of centre
-// offsets d = mean - pixel meets the ellipse E = {d : q(d) <= tau2}, with
-// q(d) = A dx^2 + 2 B dx dy + C dy^2 and tau2 = -2 power_min.  Within the strip
-// of one tile row, E's x-extent is an interval: its right end lies on the
-// boundary where dq/dy = 0 (dy = -(B/C) dx, so at dy = -(B/C) x_max with
-// x_max = sqrt(tau2 C / det) and det = AC - B^2) unless the strip cuts that
-// point off, when it lies on the strip edge nearest to it; the left end is the
-// mirror image.  On a line dy = y the boundary is at
-// dx = (-B y +- sqrt(A tau2 - det y^2)) / A.  The row keeps the tiles whose
-// x-range of offsets meets that interval.  Floating point decides an integer
-// here, so the rule is FP32 with one IEEE rounding per operation in the order
-// written (no contraction), and power_min comes from the caller.  Not positive
-// definite: the whole row; tau2 <= 0: no tile.
-struct TightRows {
-    int mode;  // 0: whole rows, 1: no tile, 2: the ellipse rule
-    float mx, my, nB, det, Atau, rA, ymax, dyr;
-};
-
-static TightRows tight_rows(float mx, float my, float A, float B, float C, float pmin) {
-    TightRows t{};
-    t.mx = mx;
-    t.my = my;
-    const float det = A * C - B * B;
-    if (!(A > 0.f) || !(det > 0.f)) return t;
-    const float tau2 = -2.0f * pmin;
-    t.mode = 1;
-    if (!(tau2 > 0.f)) return t;
-    t.mode = 2;
-    t.nB = -B;
-    t.det = det;
-    t.Atau = A * tau2;
-    t.rA = 1.0f / A;
-    t.ymax = std::sqrt((tau2 * A) / det);
-    const float xmax = std::sqrt((tau2 * C) / det);
-    t.dyr = (-B / C) * xmax;
-    return t;
+// Opacity-aware tile membership (the tighter tile intersection; the paper
+// combines its blend with such culling, Sec. 4.2, but defines none), written
+// as its definition: a splat keeps tile (tx, ty) iff the largest exponent of
+// Eq. 3 over the tile's box of pixel-centre offsets d = mean - pixel,
+// [mx - 16 tx - 15.5, mx - 16 tx - 0.5] x [my - 16 ty - 15.5, my - 16 ty - 0.5],
+// reaches power_min, i.e. iff min over the box of
+// q(d) = A dx^2 + 2 B dx dy + C dy^2 is <= tau2 = -2 power_min (so no tile if
+// tau2 <= 0, which includes power_min = +inf).
+// With A > 0 and C > 0, q restricted to any line dx = const or dy = const is
+// a convex parabola, and q has no local minimum inside a box unless the box
+// holds the origin (there q = 0 <= tau2, whatever the sign of AC - B^2).  So
+// the box minimum is 0 if the box holds the origin, else the least of the
+// four edge minima, each the parabola's vertex clamped to the edge.  A <= 0 or
+// C <= 0 (never from a projected covariance): the whole rectangle is kept.
+static double box_min_q(double A, double B, double C, double x0, double x1, double y0, double y1) {
+    if (x0 > x1 || y0 > y1) return std::numeric_limits<double>::infinity();  // an empty (over-shrunk) box
+    if (x0 <= 0 && 0 <= x1 && y0 <= 0 && 0 <= y1) return 0.0;
+    auto q = [&](double x, double y) { return A * x * x + 2 * B * x * y + C * y * y; };
+    double best = std::numeric_limits<double>::infinity();
+    for (double x : {x0, x1}) best = std::min(best, q(x, std::clamp(-B * x / C, y0, y1)));
+    for (double y : {y0, y1}) best = std::min(best, q(std::clamp(-B * y / A, x0, x1), y));
+    return best;
 }
 
-// The kept tiles [first, last] of row ty within [x0, x1] (first > last: none).
-static void tight_row(const TightRows& t, int ty, int x0, int x1, int* first, int* last) {
-    *first = x0;
-    *last = x1;
-    if (t.mode == 0) return;
-    *last = x0 - 1;
-    if (t.mode == 1) return;
-    const float lo = std::fmax(t.my - ((float)(16 * ty) + 15.5f), -t.ymax);
-    const float hi = std::fmin(t.my - ((float)(16 * ty) + 0.5f), t.ymax);
-    if (!(lo <= hi)) return;
-    const float yr = std::fmin(std::fmax(t.dyr, lo), hi), yl = std::fmin(std::fmax(-t.dyr, lo), hi);
-    const float sr = std::sqrt(std::fmax(t.Atau - t.det * (yr * yr), 0.f));
-    const float sl = std::sqrt(std::fmax(t.Atau - t.det * (yl * yl), 0.f));
-    const float xr = (t.nB * yr + sr) * t.rA, xl = (t.nB * yl - sl) * t.rA;
-    // tile tx has offsets [mx - 16 tx - 15.5, mx - 16 tx - 0.5]
-    const float flo = ((t.mx - 15.5f) - xr) * 0.0625f, fhi = ((t.mx - 0.5f) - xl) * 0.0625f;
-    *first = (int)std::ceil(std::fmin(std::fmax(flo, (float)x0), (float)(x1 + 1)));
-    *last = (int)std::floor(std::fmin(std::fmax(fhi, (float)(x0 - 1)), (float)x1));
+// Decision for one (splat, tile) pair: 1 keep, 0 drop.  *ambiguous is set when
+// the decision could go either way under rounding of float32 inputs and
+// arithmetic: it changes somewhere within the box grown or shrunk by
+// delta = 2^-20 (max(|mx|, |my|) + 16) px per side (float32 offsets of
+// coordinates near |m| carry errors of about 2^-24 |m|) or tau2 scaled by
+// 1 +- 1e-5.
+static int tight_keep(double mx, double my, double A, double B, double C, double pmin, int tx, int ty, bool* ambiguous) {
+    *ambiguous = false;
+    if (!(A > 0) || !(C > 0)) return 1;
+    const double tau2 = -2.0 * pmin;
+    if (!(tau2 > 0)) return 0;
+    const double x0 = mx - 16.0 * tx - 15.5, x1 = mx - 16.0 * tx - 0.5;
+    const double y0 = my - 16.0 * ty - 15.5, y1 = my - 16.0 * ty - 0.5;
+    const int keep = box_min_q(A, B, C, x0, x1, y0, y1) <= tau2;
+    const double d = std::ldexp(std::max(std::fabs(mx), std::fabs(my)) + 16.0, -20);
+    const bool sure_keep = box_min_q(A, B, C, x0 + d, x1 - d, y0 + d, y1 - d) <= tau2 * (1 - 1e-5);
+    const bool sure_drop = box_min_q(A, B, C, x0 - d, x1 + d, y0 - d, y1 + d) > tau2 * (1 + 1e-5);
+    *ambiguous = !(sure_keep || sure_drop);
+    return keep;
 }
 
+// With conic_f and power_min (the CUDA path's float32 values, taken exactly
+// as doubles) a tile is kept only per tight_keep; every pair of the
+// rectangles whose decision is ambiguous is written to amb_out as
+// (tile, Gaussian, decision) triples, up to amb_cap, and counted in *amb_count.
 int64_t oracle_bin_sort(int n, const double* mean2d, const int32_t* radius, const float* depth,
                         int W, int H, int64_t capacity, uint64_t* keys_out, uint32_t* ids_out,
-                        uint32_t* tile_ranges, const float* mean2d_f, const float* conic_f,
-                        const float* power_min) {
+                        uint32_t* tile_ranges, const float* conic_f, const float* power_min,
+                        int64_t* amb_out, int64_t amb_cap, int64_t* amb_count) {
     std::vector<uint64_t> keys;
     std::vector<uint32_t> ids;
-    const bool tight = conic_f != nullptr && power_min != nullptr && mean2d_f != nullptr;
+    const bool tight = conic_f != nullptr && power_min != nullptr;
+    int64_t n_amb = 0;
     for (int g = 0; g < n; ++g) {
         int rc[4];
         if (!tile_rect(mean2d[2 * g], mean2d[2 * g + 1], radius[g], W, H, rc)) continue;
         uint32_t dbits;
         std::memcpy(&dbits, &depth[g], 4);
-        TightRows tr{};
-        if (tight)
-            tr = tight_rows(mean2d_f[2 * g], mean2d_f[2 * g + 1], conic_f[3 * g], conic_f[3 * g + 1],
-                            conic_f[3 * g + 2], power_min[g]);
-        for (int ty = rc[2]; ty <= rc[3]; ++ty) {
-            int first = rc[0], last = rc[1];
-            if (tight) tight_row(tr, ty, rc[0], rc[1], &first, &last);
-            for (int tx = first; tx <= last; ++tx) {
-                uint64_t tile = (uint64_t)ty * tiles_x(W) + tx;
+        for (int ty = rc[2]; ty <= rc[3]; ++ty)
+            for (int tx = rc[0]; tx <= rc[1]; ++tx) {
+                const uint64_t tile = (uint64_t)ty * tiles_x(W) + tx;
+                if (tight) {
+                    bool amb = false;
+                    const int keep = tight_keep(mean2d[2 * g], mean2d[2 * g + 1], conic_f[3 * g],
+                                                conic_f[3 * g + 1], conic_f[3 * g + 2], power_min[g], tx, ty, &amb);
+                    if (amb) {
+                        if (amb_out && n_amb < amb_cap) {
+                            amb_out[3 * n_amb] = (int64_t)tile;
+                            amb_out[3 * n_amb + 1] = g;
+                            amb_out[3 * n_amb + 2] = keep;
+                        }
+                        ++n_amb;
+                    }
+                    if (!keep) continue;
+                }
                 keys.push_back((tile << 32) | dbits);
                 ids.push_back((uint32_t)g);
             }
-        }
     }
+    if (amb_count) *amb_count = n_amb;
     int64_t I = (int64_t)keys.size();
     int ntiles = tiles_x(W) * tiles_y(H);
     for (int t = 0; t < 2 * ntiles; ++t) tile_ranges[t] = 0;

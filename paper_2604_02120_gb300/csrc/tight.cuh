@@ -3,41 +3,63 @@
 // kernel.
 //
 // A splat keeps tile (tx, ty) of its rectangle only if its exponent can reach
-// power_min at some pixel centre of the tile: if the tile's box of centre offsets d = mean - pixel meets the
-// ellipse E = {d : q(d) <= tau2}, q(d) = A dx^2 + 2 B dx dy + C dy^2,
-// tau2 = -2 power_min.  Within the strip of one tile row, E's x-extent is an
-// interval: its right end is E's rightmost point (dy = -(B/C) x_max, x_max =
-// sqrt(tau2 C / det), det = AC - B^2) with dy clamped to the strip, the left
-// end the mirror image, and on a line dy = y the boundary is at
-// dx = (-B y +- sqrt(A tau2 - det y^2)) / A.  So each row keeps one run of
-// tiles, found in O(1).  Floating point decides an integer here, so the rule
-// is FP32 with one IEEE rounding per operation in a fixed order (the oracle
-// repeats it).  Not positive definite: whole rows; tau2 <= 0: no tile.
+// power_min at some pixel centre of the tile: if the tile's box of centre
+// offsets d = mean - pixel meets the region E = {d : q(d) <= tau2},
+// q(d) = A dx^2 + 2 B dx dy + C dy^2, tau2 = -2 power_min.  On a line dy = y,
+// E is the interval dx in [(-B y - s(y)) / A, (-B y + s(y)) / A] with
+// s(y) = sqrt(A tau2 - det y^2), det = AC - B^2, so within the strip of one
+// tile row E's x-extent is one interval and the row keeps one run of tiles,
+// found in O(1):
+//  - det > 0 (an ellipse): the right end x_r(y) is concave, largest at E's
+//    rightmost point dy = -(B/C) x_max (x_max = sqrt(tau2 C / det)), or at the
+//    strip edge nearest to it; the left end mirrored; |dy| <= sqrt(tau2 A / det).
+//  - det <= 0 (a degenerate or indefinite form; a Gaussian with one huge
+//    scale projects to a nearly singular conic): x_r(y) is convex, so it is
+//    largest at one of the strip's two edges; the left end mirrored.
+// det comes from Kahan's FMA evaluation of AC - B^2 (the rounding error of
+// B^2 is recovered exactly by an FMA and added back), accurate to a few units
+// in the last place of det itself: the plain float32 difference cancels to
+// zero or below for needle-shaped splats and would keep their whole
+// rectangle.  FP32 throughout, rounding per operation in a fixed order (no
+// contraction).  A <= 0 or C <= 0: whole rows; tau2 <= 0: no tile.
 #pragma once
 
 namespace gs {
 
 struct TightRows {
-    int mode;  // 0: whole rows, 1: no tile, 2: the ellipse rule
+    int mode;  // 0: whole rows, 1: no tile, 2: ellipse (det > 0), 3: det <= 0
     float mx, my, nB, det, Atau, rA, ymax, dyr;
 };
 
 __device__ __forceinline__ TightRows tight_rows(float mx, float my, float A, float B, float C, float pmin) {
     TightRows t{0, mx, my, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const float det = __fsub_rn(__fmul_rn(A, C), __fmul_rn(B, B));
-    if (!(A > 0.f) || !(det > 0.f)) return t;
+    if (!(A > 0.f) || !(C > 0.f)) return t;
+    const float bb = __fmul_rn(B, B);
+    const float bb_err = __fmaf_rn(-B, B, bb);  // bb - B*B, exact
+    const float det = __fadd_rn(__fmaf_rn(A, C, -bb), bb_err);
     const float tau2 = __fmul_rn(-2.0f, pmin);
     t.mode = 1;
     if (!(tau2 > 0.f)) return t;
-    t.mode = 2;
     t.nB = -B;
     t.det = det;
     t.Atau = __fmul_rn(A, tau2);
     t.rA = __fdiv_rn(1.0f, A);
-    t.ymax = __fsqrt_rn(__fdiv_rn(__fmul_rn(tau2, A), det));
-    const float xmax = __fsqrt_rn(__fdiv_rn(__fmul_rn(tau2, C), det));
-    t.dyr = __fmul_rn(__fdiv_rn(-B, C), xmax);
+    if (det > 0.f) {
+        t.mode = 2;
+        t.ymax = __fsqrt_rn(__fdiv_rn(__fmul_rn(tau2, A), det));
+        // -(B/C) x_max = -B sqrt(tau2 / (C det)); 0 for B = 0 even if the root overflows
+        t.dyr = (B == 0.f) ? 0.f : __fmul_rn(-B, __fsqrt_rn(__fdiv_rn(tau2, __fmul_rn(C, det))));
+    } else {
+        t.mode = 3;
+        t.ymax = __int_as_float(0x7f800000);  // +inf: the form is unbounded along its null line
+    }
     return t;
+}
+
+// Right (sign +1) or left (sign -1) end of E's x-extent on the line dy = y.
+__device__ __forceinline__ float tight_end(const TightRows& t, float y, float sign) {
+    const float s = __fsqrt_rn(fmaxf(__fsub_rn(t.Atau, __fmul_rn(t.det, __fmul_rn(y, y))), 0.f));
+    return __fmul_rn(__fadd_rn(__fmul_rn(t.nB, y), sign * s), t.rA);
 }
 
 // The kept tiles [first, last] of row ty within [x0, x1] (first > last: none).
@@ -50,11 +72,14 @@ __device__ __forceinline__ void tight_row(const TightRows& t, int ty, int x0, in
     const float lo = fmaxf(__fsub_rn(t.my, __fadd_rn((float)(16 * ty), 15.5f)), -t.ymax);
     const float hi = fminf(__fsub_rn(t.my, __fadd_rn((float)(16 * ty), 0.5f)), t.ymax);
     if (!(lo <= hi)) return;
-    const float yr = fminf(fmaxf(t.dyr, lo), hi), yl = fminf(fmaxf(-t.dyr, lo), hi);
-    const float sr = __fsqrt_rn(fmaxf(__fsub_rn(t.Atau, __fmul_rn(t.det, __fmul_rn(yr, yr))), 0.f));
-    const float sl = __fsqrt_rn(fmaxf(__fsub_rn(t.Atau, __fmul_rn(t.det, __fmul_rn(yl, yl))), 0.f));
-    const float xr = __fmul_rn(__fadd_rn(__fmul_rn(t.nB, yr), sr), t.rA);
-    const float xl = __fmul_rn(__fsub_rn(__fmul_rn(t.nB, yl), sl), t.rA);
+    float xr, xl;
+    if (t.mode == 2) {
+        xr = tight_end(t, fminf(fmaxf(t.dyr, lo), hi), 1.f);
+        xl = tight_end(t, fminf(fmaxf(-t.dyr, lo), hi), -1.f);
+    } else {
+        xr = fmaxf(tight_end(t, lo, 1.f), tight_end(t, hi, 1.f));
+        xl = fminf(tight_end(t, lo, -1.f), tight_end(t, hi, -1.f));
+    }
     // tile tx has offsets [mx - 16 tx - 15.5, mx - 16 tx - 0.5]
     const float flo = __fmul_rn(__fsub_rn(__fsub_rn(t.mx, 15.5f), xr), 0.0625f);
     const float fhi = __fmul_rn(__fsub_rn(__fsub_rn(t.mx, 0.5f), xl), 0.0625f);

@@ -63,3 +63,47 @@ def pixel_mask_tiles(cam, tiles):
         x0, y0 = 16 * (t % tx), 16 * (t // tx)
         m[y0:y0 + 16, x0:x0 + 16] = True
     return m
+
+
+def check_tight_lists(got, ref, full, max_amb_frac=1e-3):
+    """GPU opacity-aware lists against the oracle's FP64 definition.
+
+    got, ref, full: dicts with tile_ranges (2 per tile, [start, end)), ids and
+    optionally keys; `ref` from oracle.bin_sort with conic and power_min (its
+    ``ambiguous`` rows are the pairs whose decision lies within rounding of
+    the threshold), `full` the full-rectangle lists (GPU or oracle: they are
+    bit-exact).  Asserts that
+      * every tile's GPU list is a sub-sequence of its full list (same order),
+        and the ranges tile the id array in tile order;
+      * the GPU keeps exactly the pairs the definition keeps, except pairs
+        reported ambiguous;
+      * ambiguous pairs are at most max_amb_frac of the kept pairs;
+      * keys, where given, are those of the full list at the same pairs.
+    Returns (number of ambiguous pairs, number of pairs decided otherwise)."""
+    def codes(d):
+        r = np.asarray(d["tile_ranges"]).view(np.uint32).astype(np.int64)
+        lens = r[1::2] - r[0::2]
+        tiles = np.repeat(np.arange(lens.size, dtype=np.int64), np.maximum(lens, 0))
+        n = int(lens.sum())
+        ids = np.asarray(d["ids"]).view(np.uint32)[:n].astype(np.int64)
+        starts = np.concatenate([[0], np.cumsum(lens)[:-1]])
+        assert (r[0::2][lens > 0] == starts[lens > 0]).all(), "ranges do not tile the id array in tile order"
+        return (tiles << 32) | ids
+
+    g, rf, fl = codes(got), codes(ref), codes(full)
+    amb = np.asarray(ref["ambiguous"], np.int64).reshape(-1, 3)
+    amb_codes = (amb[:, 0] << 32) | amb[:, 1]
+    diff = np.setxor1d(g, rf)
+    assert np.isin(diff, amb_codes).all(), \
+        f"{int((~np.isin(diff, amb_codes)).sum())} pairs decided otherwise than the FP64 definition and not ambiguous"
+    assert amb.shape[0] <= max_amb_frac * max(rf.size, 1), f"{amb.shape[0]} ambiguous pairs of {rf.size}"
+    order = np.argsort(fl, kind="stable")
+    pos = order[np.clip(np.searchsorted(fl[order], g), 0, max(fl.size - 1, 0))]
+    assert fl.size > 0 or g.size == 0
+    if g.size:
+        assert (fl[pos] == g).all(), "a kept pair is not on the splat's rectangle"
+        assert (np.diff(pos) > 0).all(), "opacity-aware lists are not sub-sequences of the full lists"
+    if got.get("keys") is not None and full.get("keys") is not None and g.size:
+        np.testing.assert_array_equal(np.asarray(got["keys"]).view(np.uint64)[:g.size],
+                                      np.asarray(full["keys"]).view(np.uint64)[pos])
+    return int(amb.shape[0]), int(diff.size)

@@ -13,7 +13,8 @@ import torch
 import oracle
 from paper_2604_02120_gb300 import gs, scenes
 
-from gpu_common import CORES, blend_gpu, gpu_pipeline, oracle_blend_on_gpu_params, report, to_np
+from gpu_common import (CORES, blend_gpu, check_tight_lists, gpu_pipeline, oracle_blend_on_gpu_params, report,
+                        to_np)
 
 pytestmark = pytest.mark.gpu
 
@@ -225,17 +226,18 @@ def test_alpha_power_min_values():
 
 
 @pytest.mark.parametrize("kind", ["256x256_10k", "tiny_ragged", "tiny_dense", "1280x720_200k"])
-def test_bin_sort_opacity_aware_bit_exact(kind):
-    """Opacity-aware lists: FP32 tile membership with fixed rounding, so the
-    GPU lists equal the oracle's bit for bit, and there are fewer of them."""
+def test_bin_sort_opacity_aware_matches_definition(kind):
+    """Opacity-aware lists against the FP64 definition (the largest exponent
+    over the tile's box of pixel-centre offsets reaches power_min): the GPU
+    keeps exactly the pairs the definition keeps, except the few whose
+    decision lies within rounding of the threshold (counted and bounded), in
+    the full lists' order, and fewer than the full lists."""
     sc, dev, cam, proj, bs, pn, bn = pipeline(kind)
     got, ref, _ = _tight_sort(cam, proj, pn, dev)
-    assert got["n_instances"] == ref["n_instances"] > 0
-    assert got["n_instances"] < bn["n_instances"]
-    np.testing.assert_array_equal(got["keys"], ref["keys"])
-    np.testing.assert_array_equal(got["ids"], ref["ids"])
-    np.testing.assert_array_equal(got["tile_ranges"], ref["tile_ranges"])
-    report(f"instances_tight_{kind}", {"full": int(bn["n_instances"]), "tight": int(got["n_instances"])})
+    n_amb, n_diff = check_tight_lists(got, ref, bn)
+    assert 0 < got["n_instances"] < bn["n_instances"]
+    report(f"instances_tight_{kind}", {"full": int(bn["n_instances"]), "tight": int(got["n_instances"]),
+                                       "oracle": int(ref["n_instances"]), "ambiguous": n_amb, "decided_otherwise": n_diff})
 
 
 @pytest.mark.parametrize("variant", ["fp32", "fp16_split"])

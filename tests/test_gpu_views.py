@@ -10,7 +10,7 @@ import torch
 import oracle
 from paper_2604_02120_gb300 import gs, scenes
 
-from gpu_common import CORES, to_np
+from gpu_common import CORES, check_tight_lists, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -268,21 +268,26 @@ def test_bin_sort_views_three_tile_digit_passes_match_oracle_per_view(tight):
     tile0, total = 0, 0
     for v, (w, h) in enumerate(sizes):
         sl = slice(v * n, (v + 1) * n)
-        if tight:
+        nt = gs.num_tiles(w, h)
+        got_r = ranges_np[2 * tile0:2 * (tile0 + nt)].astype(np.int64).reshape(-1, 2)
+        busy = got_r[:, 1] > got_r[:, 0]
+        assert busy.any()
+        lo, hi = int(got_r[busy, 0].min()), int(got_r[busy, 1].max())
+        assert (got_r[~busy] == 0).all()
+        # this view's lists, taken back to the view's own tile ids and Gaussian indices
+        view = dict(tile_ranges=np.where(busy[:, None], got_r - lo, 0).astype(np.uint32).reshape(-1),
+                    ids=(ids_np[lo:hi] - np.uint32(v * n)).astype(np.uint32),
+                    keys=keys_np[lo:hi] - (np.uint64(tile0) << np.uint64(32)))
+        full = oracle.bin_sort(m2[sl].astype(np.float64), rad[sl], dep[sl], w, h)
+        if tight:  # the FP64 definition, up to pairs within rounding of the threshold
             ref = oracle.bin_sort(m2[sl].astype(np.float64), rad[sl], dep[sl], w, h,
                                   conic=out["conic"].cpu().numpy()[sl], power_min=pmin.cpu().numpy())
+            check_tight_lists(view, ref, full)
         else:
-            ref = oracle.bin_sort(m2[sl].astype(np.float64), rad[sl], dep[sl], w, h)
-        nt = gs.num_tiles(w, h)
-        lo = int(ranges_np[2 * tile0:2 * (tile0 + nt):2][ref["tile_ranges"][1::2] > 0].min())
-        seg = slice(lo, lo + ref["n_instances"])
-        np.testing.assert_array_equal(ids_np[seg], ref["ids"] + v * n)
-        np.testing.assert_array_equal(keys_np[seg], ref["keys"] + (np.uint64(tile0) << np.uint64(32)))
-        got_r = ranges_np[2 * tile0:2 * (tile0 + nt)].astype(np.int64).reshape(-1, 2)
-        want_r = ref["tile_ranges"].astype(np.int64).reshape(-1, 2)
-        nonempty = want_r[:, 1] > want_r[:, 0]
-        np.testing.assert_array_equal(got_r[nonempty] - lo, want_r[nonempty])
-        assert (got_r[~nonempty] == 0).all()
+            assert hi - lo == full["n_instances"]
+            np.testing.assert_array_equal(view["ids"], full["ids"])
+            np.testing.assert_array_equal(view["keys"], full["keys"])
+            np.testing.assert_array_equal(view["tile_ranges"], full["tile_ranges"])
         tile0 += nt
-        total += ref["n_instances"]
+        total += hi - lo
     assert total == count

@@ -279,10 +279,12 @@ def test_tight_test_is_the_box_maximum():
     power_min (the box meets the ellipse q <= -2 power_min): the box minimum
     of q comes from a library box-constrained minimiser (L-BFGS-B, q convex)
     in FP64, and every decision whose exponent is clear of the threshold by
-    more than rounding must agree."""
+    more than rounding must agree.  The pairs the oracle reports as
+    ambiguous are exactly those near the threshold."""
     from scipy.optimize import minimize
 
     sc, cam, m32, c32, d32, pmin, full, tight = _tight_case(5, 96, 64, n=160)
+    amb = {(int(t), int(g)) for t, g, _ in tight["ambiguous"]}
     decided = dropped = 0
     for t in range(cam.num_tiles):
         tx, ty = t % cam.tiles_x, t // cam.tiles_x
@@ -303,10 +305,100 @@ def test_tight_test_is_the_box_maximum():
             power = -0.5 * max(res.fun, 0.0)
             if abs(power - float(pmin[g])) <= 1e-4 + 1e-5 * abs(res.fun):
                 continue
+            assert (t, int(g)) not in amb, f"tile {t} splat {g}: clear of the threshold but reported ambiguous"
             assert (g in kept) == (power >= pmin[g]), f"tile {t} splat {g}: box max {power} vs {pmin[g]}"
             decided += 1
             dropped += g not in kept
     assert decided > 300 and dropped > 50
+
+
+def _dense_box_min(A, B, C, box, n=1601):
+    """min of q over the box sampled on its four edges and an interior grid
+    (an upper bound of the true minimum, within |grad q| * h / 2)."""
+    (x0, x1), (y0, y1) = box
+    xs, ys = np.linspace(x0, x1, n), np.linspace(y0, y1, n)
+    pts = [(xs, np.full(n, y0)), (xs, np.full(n, y1)), (np.full(n, x0), ys), (np.full(n, x1), ys)]
+    gx, gy = np.meshgrid(np.linspace(x0, x1, 81), np.linspace(y0, y1, 81))
+    pts.append((gx.ravel(), gy.ravel()))
+    return min(float((A * x * x + 2 * B * x * y + C * y * y).min()) for x, y in pts)
+
+
+def test_tight_rule_on_needles_and_indefinite_conics():
+    """Nearly singular and indefinite conics (the projected 2D covariance of
+    a Gaussian with one huge scale gives A C - B^2 ~ 0, and rounded to float32
+    it can come out <= 0): the box minimum is still that of q over the box,
+    which a dense sampling of the box bounds from above; every pair the
+    sampling puts clearly below or above the threshold is decided that way,
+    and an indefinite form keeps the tiles near its zero lines only."""
+    rng = np.random.default_rng(3)
+    W, H = 160, 128
+    n = 24
+    mean2d = np.column_stack([rng.uniform(-40, W + 40, n), rng.uniform(-40, H + 40, n)]).astype(np.float32)
+    theta = rng.uniform(0, np.pi, n)
+    a2 = 10.0 ** rng.uniform(-2, 0, n)           # curvature across the needle
+    b2 = a2 * 10.0 ** rng.uniform(-9, -5, n)     # along it: A C - B^2 = a2 b2 ~ 0
+    b2[n // 2:] = -b2[n // 2:]                   # half of them indefinite
+    c, s_ = np.cos(theta), np.sin(theta)
+    conic = np.column_stack([a2 * c * c + b2 * s_ * s_, (a2 - b2) * c * s_, a2 * s_ * s_ + b2 * c * c])
+    conic = conic.astype(np.float32)
+    assert (conic[:, 0] > 0).all() and (conic[:, 2] > 0).all()
+    opac = rng.uniform(0.05, 0.9, n)
+    pmin = _power_min(opac)
+    radius = np.full(n, 400, np.int32)
+    depth = np.arange(1, n + 1, dtype=np.float32)
+    full = oracle.bin_sort(mean2d.astype(np.float64), radius, depth, W, H)
+    tight = oracle.bin_sort(mean2d.astype(np.float64), radius, depth, W, H, conic=conic, power_min=pmin)
+    assert full["n_instances"] == n * ((W // 16) * (H // 16))
+    amb = {(int(t), int(g)) for t, g, _ in tight["ambiguous"]}
+    tx_n = (W + 15) // 16
+    clear = kept_n = 0
+    for t in range(tx_n * ((H + 15) // 16)):
+        tx, ty = t % tx_n, t // tx_n
+        kept = set(tight["ids"][tight["tile_ranges"][2 * t]:tight["tile_ranges"][2 * t + 1]].tolist())
+        for g in range(n):
+            A, B, C = conic[g].astype(np.float64)
+            mx, my = mean2d[g].astype(np.float64)
+            tau2 = -2.0 * float(pmin[g])
+            box = [(mx - 16 * tx - 15.5, mx - 16 * tx - 0.5), (my - 16 * ty - 15.5, my - 16 * ty - 0.5)]
+            qs = _dense_box_min(A, B, C, box)
+            # the sampled minimum is within |grad q| * h of the true one (h = 15/1600)
+            slack = 2 * (abs(A) * 200 + abs(B) * 200 + abs(C) * 200) * (15.0 / 1600) + 1e-9
+            if qs - slack > tau2 * (1 + 1e-5):
+                assert g not in kept, f"tile {t} needle {g}: kept, sampled box min {qs} > tau2 {tau2}"
+            elif qs <= tau2 * (1 - 1e-5):
+                assert g in kept, f"tile {t} needle {g}: dropped, sampled box min {qs} <= tau2 {tau2}"
+                kept_n += 1
+            else:
+                continue
+            assert (t, g) not in amb
+            clear += 1
+    assert clear > 0.9 * n * tx_n * ((H + 15) // 16) and 0 < kept_n < tight["n_instances"] + 1
+    assert tight["n_instances"] < 0.5 * full["n_instances"]
+
+
+def test_tight_rule_exact_threshold_is_kept_and_ambiguous():
+    """A box whose minimum of q equals tau2 exactly (isotropic conic A = C = 1,
+    B = 0, tau2 = 4, the box's near edge 2 px from the mean and the mean's
+    row inside the box) is kept (max power = power_min reaches it) and is
+    reported ambiguous; moved 1e-6 px further it is dropped and still
+    ambiguous; moved 0.01 px further it is dropped and clear."""
+    W, H = 64, 32
+    shifts = [0.0, 1e-6, 0.01]
+    # splat k sits right of tile (0, 0): the tile's offsets run x in [mx - 15.5, mx - 0.5]
+    mean2d = np.array([[15.5 + 2.0 + s, 8.0] for s in shifts], np.float64)
+    mean2d = mean2d.astype(np.float32).astype(np.float64)
+    conic = np.tile(np.array([1.0, 0.0, 1.0], np.float32), (len(shifts), 1))
+    pmin = np.full(len(shifts), -2.0, np.float32)
+    radius = np.full(len(shifts), 6, np.int32)
+    depth = np.arange(1, len(shifts) + 1, dtype=np.float32)
+    tight = oracle.bin_sort(mean2d, radius, depth, W, H, conic=conic, power_min=pmin)
+    kept0 = set(tight["ids"][tight["tile_ranges"][0]:tight["tile_ranges"][1]].tolist())
+    amb = {(int(t), int(g)): int(k) for t, g, k in tight["ambiguous"]}
+    x0 = mean2d[:, 0] - 15.5
+    assert x0[0] == 2.0 and x0[1] > 2.0
+    assert 0 in kept0 and amb.get((0, 0)) == 1
+    assert 1 not in kept0 and amb.get((0, 1)) == 0
+    assert 2 not in kept0 and (0, 2) not in amb
 
 
 def test_bin_sort_capacity_overflow_reports():
