@@ -116,6 +116,15 @@ typedef struct gs_blend_opts {
                                    evaluates before a tile's exit (every pixel stopped), whether or
                                    not a pixel still needs them; the evaluated pairs of Eq. 1 are the
                                    sum of n_contrib.  The caller zeroes it */
+    const float* splat_records; /* NULL, or a DEVICE table from gs_pack_splats over the call's items
+                                   (the same mean2d, conic, opacity, rgb), 16-byte aligned: the
+                                   tensor-core kernels then stage each chunk's splat records into
+                                   shared memory with TMA gather copies (cp.async.bulk.tensor
+                                   tile::gather4) issued chunks ahead, instead of loading the splat
+                                   arrays thread by thread.  Same results bit for bit; ignored by the
+                                   FP32 variant */
+    int64_t splat_record_count; /* rows of splat_records (n_items of gs_pack_splats), 1 .. 2^31 - 1;
+                                   a row beyond it reads as zeros, never outside the table */
 } gs_blend_opts;
 
 /* Library version (major * 100 + minor). */
@@ -305,6 +314,20 @@ gs_status gs_tile_order(int32_t n_views, const int32_t* widths, const int32_t* h
 gs_status gs_alpha_power_min(int32_t n, const float* opacity, float* power_min, gs_stream stream);
 
 /*
+ * gs_pack_splats - the splat parameters the blends read, packed per item into
+ * one 64-byte record (not in the paper: the data layout of the staged,
+ * pipelined splat loads of Sec. 3.4 on this GPU), for gs_blend_opts.splat_records.
+ * Items are view-major as in the *_views calls: item v * n_per_view + g.
+ *   mean2d n_items x 2, conic n_items x 3, rgb n_items x 3 (may be NULL: zero
+ *   colour), opacity n_per_view (indexed by g): DEVICE inputs.
+ *   records: DEVICE output, n_items x 16 floats, 16-byte aligned:
+ *   [mx, my, A, B, C, log2 o, min(log2 o, log2 0.99), 1/o, r, g, b, g (bits), 0, 0, 0, 0]
+ *   (log2 0 = -inf, 1/0 = 0).  One launch; asynchronous.
+ */
+gs_status gs_pack_splats(int32_t n_items, int32_t n_per_view, const float* mean2d, const float* conic,
+                         const float* opacity, const float* rgb, float* records, gs_stream stream);
+
+/*
  * gs_bin_sort_noalloc - gs_bin_sort for callers that cannot allocate device
  * memory (the paper has no counterpart: it is a deployment convenience).
  * Some callers get only their input and output buffers: code inside a host
@@ -363,9 +386,17 @@ gs_status gs_blend_forward(int32_t width, int32_t height, const uint32_t* tile_r
  *   dalpha/do = e^p and dalpha/dp = alpha (both 0 where the 0.99 clamp holds),
  *   dp/dmx = -(A dx + B dy), dp/dmy = -(B dx + C dy),
  *   dp/dA = -dx^2/2, dp/dB = -dx dy, dp/dC = -dy^2/2.
- * alpha is recomputed with the FP32 arithmetic of GS_BLEND_FP32 whatever
- * opts->variant is.  Gradients are ADDED (atomically) to dmean2d n x 2,
- * dconic n x 3, dopacity n, drgb n x 3: zero them first.
+ * alpha is recomputed with the arithmetic of the forward call's variant, so
+ * the backward pass skips and stops exactly where the forward did:
+ *  - GS_BLEND_FP32: the FP32 quadratic of Eq. 3 (Alg. 1), one block per tile;
+ *  - every tensor-core variant: the forward's own Eq. 6 contraction on the
+ *    tensor cores (the same v_g rows and operand terms, FP32 accumulate); the
+ *    per-splat sums over a tile's pixels (dL/dpower times the monomials, and
+ *    the colour weights) are a second tensor-core contraction with fp16
+ *    operands (dL/dpower as fp16 hi + lo, the weight alpha T as one fp16).
+ * Pass the same opts->variant as the forward call that produced T_final and
+ * n_contrib.  Gradients are ADDED (atomically) to dmean2d n x 2, dconic n x 3,
+ * dopacity n, drgb n x 3: zero them first.
  */
 gs_status gs_blend_backward(int32_t width, int32_t height, const uint32_t* tile_ranges,
                             const uint32_t* ids_sorted, const float* mean2d, const float* conic,

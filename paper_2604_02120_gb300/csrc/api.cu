@@ -1,6 +1,7 @@
 // C ABI entry points: argument checks, status reporting, the per-device error
 // word, and dispatch to the kernels of the other translation units.
 #include <atomic>
+#include <cstddef>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -79,6 +80,10 @@ unsigned* error_word() {
 
 using namespace gs;
 
+// The options struct is part of the ABI (the Python binding mirrors it).
+static_assert(sizeof(gs_blend_opts) == 80, "gs_blend_opts layout");
+static_assert(offsetof(gs_blend_opts, splat_records) == 64, "gs_blend_opts layout");
+
 namespace {
 
 gs_status check_views(const char* who, int32_t n_views, const int32_t* widths, const int32_t* heights) {
@@ -127,6 +132,14 @@ bool make_args(BlendArgs& a, int32_t n_views, const int32_t* widths, const int32
     a.order_tiles = a.total_tiles;
     a.issued = o ? reinterpret_cast<unsigned long long*>(o->issued_pairs) : nullptr;  // same width, 64 bits
     a.err = error_word();
+    a.use_rec = 0;
+    if (o && o->splat_records) {
+        if (o->splat_record_count < 1 || o->splat_record_count >= (int64_t(1) << 31) ||
+            (reinterpret_cast<uintptr_t>(o->splat_records) & 15u) != 0)
+            return false;
+        if (encode_rec_map(&a.rec_map, o->splat_records, (int)o->splat_record_count) != cudaSuccess) return false;
+        a.use_rec = 1;
+    }
     return true;
 }
 
@@ -307,6 +320,21 @@ gs_status gs_tile_order(int32_t n_views, const int32_t* widths, const int32_t* h
                        "gs_tile_order");
 }
 
+gs_status gs_pack_splats(int32_t n_items, int32_t n_per_view, const float* mean2d, const float* conic,
+                         const float* opacity, const float* rgb, float* records, gs_stream stream) {
+    g_last_error[0] = 0;
+    if (n_items < 0 || n_per_view < 0 || (n_items > 0 && (n_per_view == 0 || n_items % n_per_view != 0)) ||
+        (n_items > 0 && (!mean2d || !conic || !opacity || !records)) ||
+        (reinterpret_cast<uintptr_t>(records) & 15u) != 0 || (reinterpret_cast<uintptr_t>(mean2d) & 7u) != 0) {
+        set_error("gs_pack_splats: bad arguments (n_items a multiple of n_per_view > 0, 16-byte aligned records, "
+                  "8-byte aligned mean2d)");
+        return GS_ERR_INVALID_ARG;
+    }
+    return cuda_status(launch_pack_splats(n_items, n_per_view, reinterpret_cast<const float2*>(mean2d), conic, opacity,
+                                          rgb, records, static_cast<cudaStream_t>(stream)),
+                       "gs_pack_splats");
+}
+
 gs_status gs_alpha_power_min(int32_t n, const float* opacity, float* power_min, gs_stream stream) {
     g_last_error[0] = 0;
     if (n < 0 || (n > 0 && (!opacity || !power_min))) {
@@ -396,7 +424,7 @@ gs_status gs_blend_forward_views(int32_t n_views, const int32_t* widths, const i
     const gs_blend_opts* o = opts ? opts : &def;
     BlendArgs a;
     if (!make_args(a, n_views, widths, heights, n_per_view, tile_ranges, ids_sorted, mean2d, conic, opacity, rgb, o)) {
-        set_error("gs_blend_forward: image size or shard out of range");
+        set_error("gs_blend_forward: image size, shard or splat records out of range");
         return GS_ERR_INVALID_ARG;
     }
     a.image = image;
@@ -449,7 +477,7 @@ gs_status gs_blend_backward_views(int32_t n_views, const int32_t* widths, const 
     }
     BlendArgs a;
     if (!make_args(a, n_views, widths, heights, n_per_view, tile_ranges, ids_sorted, mean2d, conic, opacity, rgb, o)) {
-        set_error("gs_blend_backward: image size or shard out of range");
+        set_error("gs_blend_backward: image size, shard or splat records out of range");
         return GS_ERR_INVALID_ARG;
     }
     GradArgs g{T_final, n_contrib, dL_dimage, reinterpret_cast<float2*>(dmean2d), dconic, dopacity, drgb};

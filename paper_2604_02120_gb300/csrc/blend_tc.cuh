@@ -127,6 +127,17 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t
         tc_mma_f16(d_tmem, adesc, bdesc, idesc, accumulate);
 }
 
+// A work item of the TMA producer: one chunk of a tile (n > 0), an empty
+// tile (n == 0) or the end of the queue (n < 0).
+struct ProdItem {
+    int tile, seq, base, n, q, vview;
+    uint32_t start;
+    float xc, yc;
+    int pad[3];
+};
+
+constexpr int kRecStages = 4;  // TMA record stages: copies run this many chunks minus one ahead
+
 template <int SS, int CH, int V>
 struct Layout {
     static constexpr int A_BYTES = 128 * Traits<V>::ROW_BYTES;
@@ -134,10 +145,13 @@ struct Layout {
     static constexpr int OFF_B = A_BYTES;
     static constexpr int OFF_REC = OFF_B + SS * B_BYTES;
     static constexpr int OFF_SCL = OFF_REC + SS * CH * (int)sizeof(Rec);  // FP8: row scales (float2 per splat)
-    static constexpr int OFF_BAR = OFF_SCL + SS * CH * 8;
-    static constexpr int NBAR = 2 * SS + 2 * kTStages + 1;  // + one drain barrier
+    static constexpr int RS = kRecStages;
+    static constexpr int OFF_RECT = (OFF_SCL + SS * CH * 8 + 255) / 256 * 256;  // TMA record ring (256-aligned)
+    static constexpr int OFF_BAR = OFF_RECT + RS * CH * kRecBytes;
+    static constexpr int NBAR = 2 * SS + 2 * kTStages + 1 + RS;  // + one drain barrier + the record stages
     static constexpr int OFF_HDR = OFF_BAR + NBAR * 8;
-    static constexpr int OFF_MISC = OFF_HDR + SS * 32;
+    static constexpr int OFF_ITEM = OFF_HDR + SS * 32;
+    static constexpr int OFF_MISC = OFF_ITEM + RS * (int)sizeof(ProdItem);
     static constexpr int BYTES = OFF_MISC + 16 + 4 * kDoneRing;
     static constexpr uint32_t TCOLS_RAW = 2u * kTStages * CH;
     static constexpr uint32_t TCOLS = TCOLS_RAW <= 32 ? 32 : TCOLS_RAW <= 64 ? 64 : TCOLS_RAW <= 128 ? 128
@@ -377,6 +391,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
     auto bar_tfull = [&](int t) { return smem_u32(bars + 2 * SS + t); };
     auto bar_tempty = [&](int t) { return smem_u32(bars + 2 * SS + kTStages + t); };
     const uint32_t bar_drain = smem_u32(bars + 2 * SS + 2 * kTStages);
+    auto bar_rec = [&](int r) { return smem_u32(bars + 2 * SS + 2 * kTStages + 1 + r); };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_items = a.total_tiles;  // gs_tile_power: the number of listed tiles
@@ -392,6 +407,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
             mbar_init(bar_tempty(t), kEpiWarps);
         }
         mbar_init(bar_drain, 1);
+        for (int r = 0; r < LY::RS; ++r) mbar_init(bar_rec(r), 1);
         *sAbort = 0;
         mbar_fence_init();
     }
@@ -538,6 +554,155 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
             __syncwarp();
             if (lane == 0) mbar_arrive(bar_empty(s));
         }
+    } else if (warp == kEpiWarps && !DUMP && a.use_rec) {
+        // ------------------------------------------------ producer (TMA) --
+        // Three stages per chunk, as in Sec. 3.4, each a step ahead of the
+        // next: (1) the work item (tile ticket, its range, the chunk's ids),
+        // (2) the chunk's splat records gathered into a shared-memory ring by
+        // TMA (tile::gather4: four 64-byte rows per copy) RS - 1 items before
+        // (3) its v_g rows are built from that ring into the B stage.  The
+        // copies of the next chunks, across tile boundaries, are in flight
+        // while this chunk's rows are built.
+        constexpr int RS = LY::RS;
+        ProdItem* sIt = reinterpret_cast<ProdItem*>(smem + LY::OFF_ITEM);
+        const float* sRecT = reinterpret_cast<const float*>(smem + LY::OFF_RECT);
+        const float bx0 = origin ? -15.0f : -7.5f, bx1 = origin ? 0.0f : 7.5f;
+        const float by0 = origin ? -7.0f : -3.5f, by1 = origin ? 0.0f : 3.5f;
+        // generator state (warp-uniform)
+        int g_seq = -1, g_tile = 0, g_q = 0, g_view = 0, g_len = 0, g_nch = 0, g_c = 0;
+        uint32_t g_start = 0;
+        float g_xc = 0.f, g_yc = 0.f;
+        bool g_end = false;
+        auto gen_next = [&]() -> ProdItem {
+            for (;;) {
+                if (g_end) return ProdItem{0, -2, 0, -1, g_q, 0, 0u, 0.f, 0.f, {0, 0, 0}};
+                // the next chunk of this tile, unless every pixel of the tile has stopped
+                if (g_c < g_nch && !(g_c > 0 && sDoneRing[g_seq % kDoneRing] >= kEpiWarps)) break;
+                int q = 0;
+                if (lane == 0) q = (int)atomicAdd(a.queue, 1u);
+                q = __shfl_sync(0xffffffffu, q, 0);
+                g_q = q;
+                if (q >= n_items) {
+                    g_end = true;
+                    continue;
+                }
+                ++g_seq;
+                g_tile = tile_at(a, q * a.shard_count + a.shard_index);
+                g_start = a.ranges[2 * g_tile];
+                const uint32_t stop = a.ranges[2 * g_tile + 1];
+                g_len = stop > g_start ? (int)(stop - g_start) : 0;
+                g_view = view_of(a, g_tile);
+                const ViewDesc vd = a.views[g_view];
+                const int lt = g_tile - vd.tile_begin;
+                g_xc = (float)((lt % vd.tiles_x) * kTile) + (origin ? 0.5f : 8.0f);
+                g_yc = (float)((lt / vd.tiles_x) * kTile) + (origin ? 0.5f : 4.0f);
+                g_nch = max(1, (g_len + CH - 1) / CH);
+                g_c = 0;
+                if (lane == 0) sDoneRing[g_seq % kDoneRing] = 0;
+            }
+            const int base = g_c * CH;
+            ++g_c;
+            return ProdItem{g_tile, g_seq, base, g_len > 0 ? min(CH, g_len - base) : 0, g_q, g_view, g_start,
+                            g_xc, g_yc, {0, 0, 0}};
+        };
+        // stage (2) for an item in record stage rs: the ids, then ceil(n / 4)
+        // gather copies (rows past n repeat id 0, a row of the table); an item
+        // without splats just completes the stage's phase
+        auto issue = [&](const ProdItem& it, int rs) {
+            if (it.n <= 0) {
+                if (lane == 0) mbar_arrive(bar_rec(rs));
+                return;
+            }
+            const uint32_t g = lane < it.n ? a.ids[it.start + it.base + lane] : 0u;
+            const int src = 4 * (lane & 7);
+            const uint32_t g0 = __shfl_sync(0xffffffffu, g, src), g1 = __shfl_sync(0xffffffffu, g, src + 1);
+            const uint32_t g2 = __shfl_sync(0xffffffffu, g, src + 2), g3 = __shfl_sync(0xffffffffu, g, src + 3);
+            const int ng = (it.n + 3) >> 2;
+            if (lane == 0) mbar_arrive_expect_tx(bar_rec(rs), (uint32_t)(ng * 4 * kRecBytes));
+            __syncwarp();
+            if (lane < ng)
+                tma_gather4(smem_u32(sRecT + ((size_t)rs * CH + 4 * lane) * kRecFloats), &a.rec_map, 0, g0, g1, g2,
+                            g3, bar_rec(rs));
+        };
+        int k = 0, ri = 0, wi = 0;
+        bool gen_done = false, quit = false;
+        unsigned long long issued = 0;
+        for (; ri < RS - 1 && !gen_done; ++ri) {
+            const ProdItem it = gen_next();
+            __syncwarp();
+            if (lane == 0) sIt[ri % RS] = it;
+            issue(it, ri % RS);
+            gen_done = it.n < 0;
+        }
+        while (!quit) {
+            if (!gen_done) {  // keep RS - 1 items in flight
+                const ProdItem it = gen_next();
+                __syncwarp();
+                if (lane == 0) sIt[ri % RS] = it;
+                issue(it, ri % RS);
+                gen_done = it.n < 0;
+                ++ri;
+            }
+            __syncwarp();
+            const ProdItem it = sIt[wi % RS];
+            const int rs = wi % RS;
+            if (!mbar_wait_bounded(bar_rec(rs), (uint32_t)(wi / RS) & 1u, tmo, sAbort)) {
+                *sAbort = 1;
+                atomicOr(a.err, kErrTimeout);
+                break;
+            }
+            ++wi;
+            // a later chunk of a tile whose pixels have all stopped is dropped
+            if (it.n > 0 && it.base > 0 && sDoneRing[it.seq % kDoneRing] >= kEpiWarps) continue;
+            const int s = k % SS;
+            const uint32_t ps = (uint32_t)(k / SS) & 1u;
+            if (!mbar_wait_bounded(bar_empty(s), ps ^ 1u, tmo, sAbort)) {
+                *sAbort = 1;
+                atomicOr(a.err, kErrTimeout);
+                break;
+            }
+            if (*sAbort) break;
+            const int n = it.n;
+            if (n > 0) {
+                issued += (unsigned long long)n;
+                uint8_t* mB = sB + s * LY::B_BYTES;
+                const float yc_lo = it.yc + 8.0f;
+                for (int j = lane; j < CH; j += 32) {
+                    float vu[6], vl[6];
+                    Rec rc;
+                    if (j < n) {
+                        const float4* rp = reinterpret_cast<const float4*>(sRecT + ((size_t)rs * CH + j) * kRecFloats);
+                        const float4 r0 = rp[0], r1 = rp[1], r2 = rp[2];
+                        const float xh = r0.x - it.xc;
+                        coeff_row<TR::HALF>(r0.z, r0.w, r1.x, r1.y, xh, r0.y - it.yc, bx0, bx1, by0, by1, vu);
+                        coeff_row<TR::HALF>(r0.z, r0.w, r1.x, r1.y, xh, r0.y - yc_lo, bx0, bx1, by0, by1, vl);
+                        rc.rg = make_float4(r2.x, r2.x, r2.y, r2.y);
+                        rc.bc = make_float4(r2.z, r2.z, r1.z, r1.z);
+                    } else {  // padding column: dead rows, no colour
+#pragma unroll
+                        for (int i = 0; i < 5; ++i) vu[i] = vl[i] = 0.f;
+                        vu[5] = vl[5] = kDeadPower;
+                        rc.rg = make_float4(0.f, 0.f, 0.f, 0.f);
+                        rc.bc = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                    const float su = store_coeff_row<V>(mB, j, vu);
+                    const float sl = store_coeff_row<V>(mB, CH + j, vl);
+                    sRec[s * CH + j] = rc;
+                    if constexpr (TR::FP8) sScl[s * CH + j] = make_float2(su, sl);
+                }
+            }
+            if (lane == 0) sHdr[s] = StageHdr{it.tile, n < 0 ? -2 : it.seq, it.base, n, it.q, {0, 0, 0}};
+            // orders this warp's shared-memory reads and writes before the MMA's
+            // reads and before the next TMA copies into the record ring
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_full(s));
+            ++k;
+            if (n < 0) quit = true;
+        }
+        // copies still in flight (after a timeout) land before the block leaves
+        for (; wi < ri; ++wi) mbar_wait_bounded(bar_rec(wi % RS), (uint32_t)(wi / RS) & 1u, 1000000000ull, nullptr);
+        if (lane == 0 && a.issued != nullptr && issued) atomicAdd(a.issued, issued * 256ull);
     } else if (warp == kEpiWarps) {
         // ------------------------------------------------------- producer --
         int k = 0;

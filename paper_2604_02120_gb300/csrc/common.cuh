@@ -103,6 +103,24 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
     }
 }
 
+// Arrive on the barrier and raise its expected transaction bytes (one TMA stage).
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// TMA gather of four rows of a 2D tensor map (box: the row's first `box x`
+// elements, one row high) to 4 consecutive boxes at dst (shared memory),
+// completion counted in bytes on the mbarrier.  This GPU's own memory only
+// (no cluster multicast).
+__device__ __forceinline__ void tma_gather4(uint32_t dst, const void* map, int x, uint32_t r0, uint32_t r1,
+                                            uint32_t r2, uint32_t r3, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+        "l"(map), "r"(x), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(bar)
+        : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }

@@ -1,6 +1,8 @@
 // Host-side declarations shared by the translation units of the library.
 #pragma once
 
+#include <cuda.h>
+
 #include <mutex>
 
 #include "common.cuh"
@@ -73,7 +75,25 @@ struct BlendArgs {
     const int* tiles;
     int max_len;
     float* dump;
+    // Packed splat records (kRecFloats floats per item, gs_pack_splats) and
+    // the TMA descriptor of that table (2D: kRecFloats x items, box 16 x 1):
+    // when use_rec is set the tensor-core kernels stage each chunk's records
+    // into shared memory with tile::gather4 copies instead of loading the
+    // splat arrays thread by thread.
+    int use_rec;
+    alignas(64) CUtensorMap rec_map;
 };
+
+// Packed per-item splat record of gs_pack_splats, in floats:
+// [0] mean x, [1] mean y, [2..4] conic A, B, C, [5] log2 opacity (-inf if 0),
+// [6] min(log2 opacity, log2 0.99), [7] 1 / opacity (0 if 0), [8..10] rgb,
+// [11] the Gaussian index g of item v * n_per_view + g (as bits), [12..15] 0.
+constexpr int kRecFloats = 16;
+constexpr int kRecBytes = 4 * kRecFloats;
+cudaError_t launch_pack_splats(int n_items, int n_per_view, const float2* mean2d, const float* conic,
+                               const float* opac, const float* rgb, float* rec, cudaStream_t s);
+// Encode the TMA descriptor of a record table of n_items rows (16-byte aligned).
+cudaError_t encode_rec_map(CUtensorMap* map, const void* rec, int n_items);
 
 // The tile at position p of the call's tile order.
 // A bad order entry is clamped, so a corrupt order gives a wrong image, never

@@ -31,7 +31,7 @@ ABI_FUNCTIONS = (
     "gs_selftest_bounded_wait", "gs_launch_count", "gs_bin_sort_noalloc", "gs_bin_sort_noalloc_max_bytes",
     "gs_project_views", "gs_bin_sort_views", "gs_blend_forward_views", "gs_blend_backward_views",
     "gs_blend_autotune", "gs_measure_peaks", "gs_alpha_power_min", "gs_project_backward",
-    "gs_project_bin_small", "gs_tile_order",
+    "gs_project_bin_small", "gs_tile_order", "gs_pack_splats",
 )
 
 
@@ -56,7 +56,8 @@ class gs_blend_opts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("chunk", ctypes.c_int32), ("stages", ctypes.c_int32),
                 ("ref_origin", ctypes.c_int32), ("bg", ctypes.c_float * 3), ("reserved", ctypes.c_int32),
                 ("timeout_ns", ctypes.c_int64), ("shard_count", ctypes.c_int32), ("shard_index", ctypes.c_int32),
-                ("tile_order", ctypes.c_void_p), ("issued_pairs", ctypes.c_void_p)]
+                ("tile_order", ctypes.c_void_p), ("issued_pairs", ctypes.c_void_p),
+                ("splat_records", ctypes.c_void_p), ("splat_record_count", ctypes.c_int64)]
 
 
 _lib = None
@@ -90,6 +91,7 @@ def load(path: str = LIB_PATH):
                                      vp, vp]
     lib.gs_bin_sort_views.argtypes = [i32, i32, vp, vp, vp, vp, vp, i32p, i32p, i64, vp, sz, vp, vp, vp, i64p, vp, vp]
     lib.gs_alpha_power_min.argtypes = [i32, vp, vp, vp]
+    lib.gs_pack_splats.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp]
     lib.gs_tile_order.argtypes = [i32, i32p, i32p, vp, vp, vp]
     lib.gs_project_bin_small.argtypes = [i32, vp, vp, vp, vp, i32, ctypes.POINTER(gs_camera), vp, i32, vp, vp, vp,
                                          vp, vp, vp, vp, vp, vp]
@@ -145,10 +147,11 @@ def make_camera(cam) -> gs_camera:
 
 
 def make_opts(variant="fp32", chunk=0, stages=0, ref_origin=0, bg=(0.0, 0.0, 0.0), timeout_ns=0, shard_count=0,
-              shard_index=0, tile_order=None, issued_pairs=None) -> gs_blend_opts:
+              shard_index=0, tile_order=None, issued_pairs=None, splat_records=None) -> gs_blend_opts:
     """Blend options; tile_order (a device tensor from tile_order(), kept
     alive by the caller while the options are used) makes the kernels take
-    the longest tile lists first."""
+    the longest tile lists first; splat_records (from pack_splats, kept alive
+    likewise) makes the tensor-core kernels stage splats by TMA gathers."""
     o = gs_blend_opts()
     o.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     o.chunk, o.stages, o.ref_origin = int(chunk), int(stages), int(ref_origin)
@@ -158,7 +161,15 @@ def make_opts(variant="fp32", chunk=0, stages=0, ref_origin=0, bg=(0.0, 0.0, 0.0
     o.shard_count, o.shard_index = int(shard_count), int(shard_index)
     o.tile_order = None if tile_order is None else tile_order.data_ptr()
     o.issued_pairs = None if issued_pairs is None else issued_pairs.data_ptr()
+    set_records(o, splat_records)
     return o
+
+
+def set_records(opts, records):
+    """Point the options at a packed record table (None: the load-based path)."""
+    opts.splat_records = None if records is None else records.data_ptr()
+    opts.splat_record_count = 0 if records is None else int(records.shape[0])
+    return opts
 
 
 # ------------------------------------------------------------- raw entry points
@@ -352,6 +363,20 @@ def gs_alpha_power_min(n, opacity, power_min, stream=None):
     _check(load().gs_alpha_power_min(n, _ptr(opacity), _ptr(power_min), _stream(stream)), "gs_alpha_power_min")
 
 
+def gs_pack_splats(n_items, n_per_view, mean2d, conic, opacity, rgb, records, stream=None):
+    _check(load().gs_pack_splats(n_items, n_per_view, _ptr(mean2d), _ptr(conic), _ptr(opacity), _ptr(rgb),
+                                 _ptr(records), _stream(stream)), "gs_pack_splats")
+
+
+def pack_splats(proj, opacity, out=None, stream=None):
+    """Packed splat records (n_items x 16 floats) of a projection's outputs
+    (one view, or view-major items of several views over the same opacity)."""
+    n_items = proj["mean2d"].shape[0]
+    rec = out if out is not None else torch.empty(n_items, 16, device=opacity.device, dtype=torch.float32)
+    gs_pack_splats(n_items, opacity.shape[0], proj["mean2d"], proj["conic"], opacity, proj["rgb"], rec, stream)
+    return rec
+
+
 def alpha_power_min(opacity, stream=None):
     out = torch.empty_like(opacity)
     gs_alpha_power_min(opacity.shape[0], opacity, out, stream)
@@ -538,7 +563,8 @@ class PipelinedRenderer:
 
     KEYS = ("means", "scales", "quats", "opacities", "sh")
 
-    def __init__(self, template_scene, sh_degree, cams, opts, capacity, dL, device="cuda", graphs=False):
+    def __init__(self, template_scene, sh_degree, cams, opts, capacity, dL, device="cuda", graphs=False,
+                 opacity_aware=False):
         # graphs: each renderer's step is recorded once in a CUDA graph (after
         # one run on the template scene's values) and replayed per frame, one
         # host call instead of one per kernel
@@ -546,7 +572,7 @@ class PipelinedRenderer:
         for _ in range(2):
             dev = {k: torch.empty_like(template_scene[k], device=device) for k in self.KEYS}
             dev["sh_degree"] = sh_degree
-            r = BatchRenderer(dev, cams, opts, capacity, device)
+            r = BatchRenderer(dev, cams, opts, capacity, device, opacity_aware=opacity_aware)
             r.dL.copy_(dL.reshape(-1))
             if graphs:
                 for k in self.KEYS:
@@ -603,9 +629,14 @@ class BatchRenderer:
     instance capacity, so `step` can be captured in a CUDA graph (`capture`);
     an instance count above the capacity is reported by gs_sync_status() as
     GS_ERR_CAPACITY.  With longest_first the blends take the tiles in the
-    order of gs_tile_order (longest list first), computed after every sort."""
+    order of gs_tile_order (longest list first), computed after every sort.
+    With opacity_aware the lists are the opacity-aware ones (gs_alpha_power_min
+    and the conics passed to gs_bin_sort_views): same images, fewer instances.
+    With tma_records the splats are packed after projection (gs_pack_splats)
+    and the tensor-core forward stages them by TMA gathers."""
 
-    def __init__(self, dev_scene, cams, opts, capacity, device="cuda", longest_first=True):
+    def __init__(self, dev_scene, cams, opts, capacity, device="cuda", longest_first=True, opacity_aware=False,
+                 tma_records=False):
         self.scene = dev_scene
         self.cams = [make_camera(c) for c in cams]
         self.opts = gs_blend_opts.from_buffer_copy(opts)
@@ -628,6 +659,9 @@ class BatchRenderer:
         self.order = torch.empty(self.total_tiles, **i32) if longest_first else None
         self.opts.tile_order = self.order.data_ptr() if longest_first else opts.tile_order
         self.count = torch.zeros(1, device=device, dtype=torch.int64)
+        self.pmin = torch.empty(n, **f32) if opacity_aware else None
+        self.rec = torch.empty(V * n, 16, **f32) if tma_records and V * n > 0 else None
+        set_records(self.opts, self.rec)
         ws = gs_bin_sort_workspace_size(V * n, self.capacity, self.widths[0], self.heights[0])
         self.workspace = torch.empty(ws + 256, device=device, dtype=torch.uint8)
         self.image = torch.empty(3 * self.pixels, **f32)
@@ -646,9 +680,14 @@ class BatchRenderer:
         sc = self.scene
         gs_project_views(self.n, sc["means"], sc["scales"], sc["quats"], sc["sh"], sc["sh_degree"], self.cams,
                          self.mean2d, self.conic, self.depth, self.radius, self.rgb, self.touched, stream)
+        if self.rec is not None:
+            gs_pack_splats(self.V * self.n, self.n, self.mean2d, self.conic, sc["opacities"], self.rgb, self.rec,
+                           stream)
+        if self.pmin is not None:
+            gs_alpha_power_min(self.n, sc["opacities"], self.pmin, stream)
         gs_bin_sort_views(self.V, self.n, self.mean2d, self.radius, self.depth, self.widths, self.heights,
                           self.capacity, self.workspace, None, self.ids, self.ranges, count_dev=self.count,
-                          stream=stream)
+                          stream=stream, conic=self.conic if self.pmin is not None else None, power_min=self.pmin)
         if self.order is not None:
             gs_tile_order(self.widths, self.heights, self.ranges, self.order, stream)
         gs_blend_forward_views(self.widths, self.heights, self.n, self.ranges, self.ids, self.mean2d, self.conic,
