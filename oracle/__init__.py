@@ -102,14 +102,16 @@ def sh_basis(dirs) -> np.ndarray:
     return out
 
 
-def bin_sort(mean2d, radius, depth, width, height, capacity=None, conic=None, power_min=None) -> dict:
+def bin_sort(mean2d, radius, depth, width, height, capacity=None, conic=None, power_min=None,
+             tile_mask=None) -> dict:
     """Duplicate + stable sort; mean2d may be the CUDA path's float32 values
     (converted exactly to double), depth is used through its float32 bits.
     With conic and power_min (float32, per Gaussian) a tile is kept only if
     the largest exponent over the tile's box of pixel-centre offsets reaches
     power_min (opacity-aware lists, decided in FP64); then ``ambiguous`` holds
     one row (tile, Gaussian, decision) per rectangle pair whose decision lies
-    within rounding of the threshold."""
+    within rounding of the threshold.  tile_mask (bool per tile): lists for
+    the marked tiles only, the others empty."""
     n = int(mean2d.shape[0])
     mean2d = _c(mean2d, np.float64)
     radius = _c(radius, np.int32)
@@ -118,7 +120,7 @@ def bin_sort(mean2d, radius, depth, width, height, capacity=None, conic=None, po
     # itself; size buffers generously first, then trim.
     cap = capacity if capacity is not None else None
     if cap is None:
-        cap = _count_instances(mean2d, radius, width, height)
+        cap = _count_instances(mean2d, radius, width, height, tile_mask)
     keys = np.zeros(max(cap, 1), np.uint64)
     ids = np.zeros(max(cap, 1), np.uint32)
     ranges = np.zeros(2 * num_tiles(width, height), np.uint32)
@@ -131,7 +133,8 @@ def bin_sort(mean2d, radius, depth, width, height, capacity=None, conic=None, po
         n_amb = ctypes.c_int64(0)
         I = lib().oracle_bin_sort(ctypes.c_int(n), _p(mean2d), _p(radius), _p(depth), ctypes.c_int(width),
                                   ctypes.c_int(height), ctypes.c_int64(cap), _p(keys), _p(ids), _p(ranges),
-                                  _p(c32), _p(p32), _p(amb), ctypes.c_int64(amb_cap), ctypes.byref(n_amb))
+                                  _p(c32), _p(p32), _p(amb), ctypes.c_int64(amb_cap), ctypes.byref(n_amb),
+                                  _p(None if tile_mask is None else _c(tile_mask, np.uint8)))
         if n_amb.value <= amb_cap:
             break
         amb_cap = int(n_amb.value)
@@ -141,9 +144,23 @@ def bin_sort(mean2d, radius, depth, width, height, capacity=None, conic=None, po
     return dict(n_instances=int(I), keys=keys[:I], ids=ids[:I], tile_ranges=ranges, ambiguous=amb)
 
 
-def _count_instances(mean2d, radius, width, height) -> int:
+def _count_instances(mean2d, radius, width, height, tile_mask=None) -> int:
     # only used to size the output buffers; the oracle recomputes rectangles
     tx, ty = (width + 15) // 16, (height + 15) // 16
+    if tile_mask is not None:  # at most every marked tile's share of the rectangles that meet it
+        m = np.asarray(tile_mask, bool).reshape(ty, tx)
+        cols, rows = m.any(0), m.any(1)
+        cnt = 0
+        r = radius.astype(np.float64)
+        x0 = np.clip(np.floor((mean2d[:, 0] - r) / 16), 0, tx - 1).astype(np.int64)
+        x1 = np.clip(np.floor((mean2d[:, 0] + r) / 16), 0, tx - 1).astype(np.int64)
+        y0 = np.clip(np.floor((mean2d[:, 1] - r) / 16), 0, ty - 1).astype(np.int64)
+        y1 = np.clip(np.floor((mean2d[:, 1] + r) / 16), 0, ty - 1).astype(np.int64)
+        ccol = np.concatenate([[0], np.cumsum(cols)])
+        crow = np.concatenate([[0], np.cumsum(rows)])
+        live = radius > 0
+        cnt = ((ccol[x1 + 1] - ccol[x0]) * (crow[y1 + 1] - crow[y0]))[live].sum()
+        return int(min(cnt, int(m.sum()) * int(live.sum())))
     r = radius.astype(np.float64)
     x0 = np.clip(np.floor((mean2d[:, 0] - r) / 16), 0, None)
     x1 = np.clip(np.floor((mean2d[:, 0] + r) / 16), None, tx - 1)
@@ -154,20 +171,29 @@ def _count_instances(mean2d, radius, width, height) -> int:
 
 
 def blend(width, height, tile_ranges, ids, mean2d, conic, opac, rgb, bg=(0.0, 0.0, 0.0),
-          alpha_margin=0.0, t_margin=0.0, n_threads=1, tile_subset=None) -> dict:
+          alpha_margin=0.0, t_margin=0.0, n_threads=1, tile_subset=None, sum_margin=0.0, sum_slack=0.0) -> dict:
+    """Blend over the sorted lists (Eq. 1, Alg. 1's rules) in FP64.  The
+    margins describe a lower-precision path's rounding (the oracle's decisions
+    do not depend on them): a pixel is ``ambiguous`` when one of its decisions
+    lies within that rounding of its threshold, and ``err_bound`` is the
+    first-order bound the same rounding puts on its colour.  alpha_margin:
+    relative error of alpha; t_margin: relative error of the transmittance
+    product; sum_margin: exponent error per unit of the magnitude sum of
+    Eq. 3's terms, with offsets enlarged by sum_slack pixels."""
     image = np.zeros((3, height, width))
     T = np.zeros((height, width))
     nc = np.zeros((height, width), np.int32)
     amb = np.zeros((height, width), np.uint8)
+    eb = np.zeros((height, width))
     subset = None if tile_subset is None else _c(tile_subset, np.int32)
+    margins = np.array([alpha_margin, t_margin, sum_margin, sum_slack], np.float64)
     lib().oracle_blend(
         ctypes.c_int(width), ctypes.c_int(height), _p(_c(tile_ranges, np.uint32)), _p(_c(ids, np.uint32)),
         _p(_c(mean2d, np.float64)), _p(_c(conic, np.float64)), _p(_c(opac, np.float64)),
-        _p(_c(rgb, np.float64)), _p(_c(bg, np.float64)), ctypes.c_double(alpha_margin),
-        ctypes.c_double(t_margin), ctypes.c_int(n_threads), _p(subset),
+        _p(_c(rgb, np.float64)), _p(_c(bg, np.float64)), _p(margins), ctypes.c_int(n_threads), _p(subset),
         ctypes.c_int(0 if subset is None else len(subset)),
-        _p(image), _p(T), _p(nc), _p(amb))
-    return dict(image=image, T_final=T, n_contrib=nc, ambiguous=amb.astype(bool))
+        _p(image), _p(T), _p(nc), _p(amb), _p(eb))
+    return dict(image=image, T_final=T, n_contrib=nc, ambiguous=amb.astype(bool), err_bound=eb)
 
 
 def brute_force(mean2d, conic, opac, rgb, radius, depth, width, height, bg=(0.0, 0.0, 0.0),

@@ -165,40 +165,68 @@ struct PixelResult {
     double T;
     int n_contrib;
     bool ambiguous;
+    double err_bound;
 };
+
+// Rounding model of a lower-precision blend, for deciding which pixels are
+// ambiguous (reading 12).  alpha: relative error of every alpha (= absolute
+// error of the exponent) from the exponential and constants; t: relative error
+// of the transmittance product from its own roundings; sum: error of the
+// exponent per unit of the magnitude sum of Eq. 3's three terms (evaluating a
+// sum in floating point errs by at most a small multiple of the unit roundoff
+// times the sum of the terms' magnitudes, which is large against the exponent
+// itself for a nearly singular conic far from the splat's centre); slack:
+// offsets enlarged by this many pixels for that sum (a path that evaluates the
+// exponent relative to a reference pixel within `slack` of the pixel).
+struct Margins {
+    double alpha, t, sum, slack;
+};
+
+// Magnitude sum of Eq. 3's terms, 1/2 |A| ax^2 + |B| ax ay + 1/2 |C| ay^2, with
+// ax = |dx| + slack, ay = |dy| + slack.
+inline double power_terms_magnitude(const Splat& s, double xp, double yp, double slack) {
+    const double ax = std::fabs(s.mx - xp) + slack, ay = std::fabs(s.my - yp) + slack;
+    return 0.5 * std::fabs(s.A) * ax * ax + std::fabs(s.B) * ax * ay + 0.5 * std::fabs(s.C) * ay * ay;
+}
 
 // Front-to-back compositing of one pixel over an ordered splat list (Eq. 1 with
 // Alg. 1's alpha-skip and early termination, readings in the header).
 // Decisions that lie within rounding of their threshold mark the pixel
-// ambiguous: a lower-precision path may legitimately decide otherwise.  With
-// alpha_margin the relative error of each alpha (= the absolute error of the
-// exponent), alpha decisions use that margin; the test transmittance
+// ambiguous: a lower-precision path may legitimately decide otherwise.  Each
+// alpha carries a relative error up to eps = m.alpha + m.sum * (magnitude sum),
+// and alpha decisions use that margin; the test transmittance
 // T (1 - alpha) = prod (1 - alpha_k) carries a relative error up to
-// alpha_margin * sum_k alpha_k / (1 - alpha_k) (first order, Eq. 1), so its
-// decision uses that bound plus t_margin.
+// m.t + sum_k eps_k alpha_k / (1 - alpha_k) (first order, Eq. 1), so its
+// decision uses that bound.  err_bound: the first-order bound those errors put
+// on the pixel's colour (each weight alpha_i T_i off by at most its alpha's
+// and its T's relative errors), largest channel.
 PixelResult composite_pixel(const std::vector<Splat>& list, double xp, double yp,
-                            const double bg[3], double alpha_margin, double t_margin) {
-    PixelResult r{{0, 0, 0}, 1.0, 0, false};
+                            const double bg[3], const Margins& m) {
+    PixelResult r{{0, 0, 0}, 1.0, 0, false, 0.0};
     double T = 1.0;
-    double growth = 0.0;  // sum alpha_k / (1 - alpha_k) over the splats added so far
+    double growth = 0.0;  // sum eps_k alpha_k / (1 - alpha_k) over the splats added so far
     for (size_t i = 0; i < list.size(); ++i) {
         const Splat& s = list[i];
         double power = std::min(power_eq3(s, xp, yp), 0.0);
+        const double eps = m.alpha + (m.sum > 0 ? m.sum * power_terms_magnitude(s, xp, yp, m.slack) : 0.0);
         double raw = s.o * std::exp(power);
-        if (std::fabs(raw - 0.99) <= alpha_margin * 0.99) r.ambiguous = true;
+        if (std::fabs(raw - 0.99) <= eps * 0.99) r.ambiguous = true;
         double alpha = std::min(0.99, raw);
-        if (std::fabs(alpha - 1.0 / 255.0) <= alpha_margin / 255.0) r.ambiguous = true;
+        if (std::fabs(alpha - 1.0 / 255.0) <= eps / 255.0) r.ambiguous = true;
         if (alpha < 1.0 / 255.0) continue;
         double testT = T * (1.0 - alpha);
-        double tm = t_margin + alpha_margin * (growth + alpha / (1.0 - alpha));
+        double tm = m.t + growth + eps * alpha / (1.0 - alpha);
         if (std::fabs(testT - 1e-4) <= tm * 1e-4) r.ambiguous = true;
         if (testT < 1e-4) break;
-        growth += alpha / (1.0 - alpha);
+        const double cmax = std::max({std::fabs(s.c[0]), std::fabs(s.c[1]), std::fabs(s.c[2])});
+        r.err_bound += cmax * alpha * T * (eps + growth + m.t);
+        growth += eps * alpha / (1.0 - alpha);
         for (int ch = 0; ch < 3; ++ch) r.C[ch] += s.c[ch] * alpha * T;
         T = testT;
         r.n_contrib = (int)i + 1;
     }
     for (int ch = 0; ch < 3; ++ch) r.C[ch] += T * bg[ch];
+    r.err_bound += T * std::max({std::fabs(bg[0]), std::fabs(bg[1]), std::fabs(bg[2])}) * (growth + m.t);
     r.T = T;
     return r;
 }
@@ -548,10 +576,12 @@ static int tight_keep(double mx, double my, double A, double B, double C, double
 // as doubles) a tile is kept only per tight_keep; every pair of the
 // rectangles whose decision is ambiguous is written to amb_out as
 // (tile, Gaussian, decision) triples, up to amb_cap, and counted in *amb_count.
+// tile_mask (one byte per tile, may be NULL): only the tiles marked non-zero
+// get lists (the others stay empty), for sampling a large image.
 int64_t oracle_bin_sort(int n, const double* mean2d, const int32_t* radius, const float* depth,
                         int W, int H, int64_t capacity, uint64_t* keys_out, uint32_t* ids_out,
                         uint32_t* tile_ranges, const float* conic_f, const float* power_min,
-                        int64_t* amb_out, int64_t amb_cap, int64_t* amb_count) {
+                        int64_t* amb_out, int64_t amb_cap, int64_t* amb_count, const uint8_t* tile_mask) {
     std::vector<uint64_t> keys;
     std::vector<uint32_t> ids;
     const bool tight = conic_f != nullptr && power_min != nullptr;
@@ -564,6 +594,7 @@ int64_t oracle_bin_sort(int n, const double* mean2d, const int32_t* radius, cons
         for (int ty = rc[2]; ty <= rc[3]; ++ty)
             for (int tx = rc[0]; tx <= rc[1]; ++tx) {
                 const uint64_t tile = (uint64_t)ty * tiles_x(W) + tx;
+                if (tile_mask && !tile_mask[tile]) continue;
                 if (tight) {
                     bool amb = false;
                     const int keep = tight_keep(mean2d[2 * g], mean2d[2 * g + 1], conic_f[3 * g],
@@ -605,11 +636,14 @@ int64_t oracle_bin_sort(int n, const double* mean2d, const int32_t* radius, cons
 
 // Stage 4 (Eq. 1, Alg. 1): blend every tile over its sorted list.  Image is
 // 3 x H x W (CHW).  Pixel results: T_final, n_contrib and an ambiguity flag.
+// margins: {alpha, t, sum, slack} of the rounding model (Margins); err_bound
+// (may be NULL) receives each pixel's first-order colour error bound.
 void oracle_blend(int W, int H, const uint32_t* tile_ranges, const uint32_t* ids,
                   const double* mean2d, const double* conic, const double* opac, const double* rgb,
-                  const double* bg, double alpha_margin, double t_margin, int n_threads,
+                  const double* bg, const double* margins, int n_threads,
                   const int32_t* tile_subset, int n_subset,
-                  double* image, double* T_final, int32_t* n_contrib, uint8_t* ambiguous) {
+                  double* image, double* T_final, int32_t* n_contrib, uint8_t* ambiguous, double* err_bound) {
+    const Margins mg{margins[0], margins[1], margins[2], margins[3]};
     const int tx = tiles_x(W);
     const int ntiles = tx * tiles_y(H);
     const int count = tile_subset ? n_subset : ntiles;
@@ -621,8 +655,9 @@ void oracle_blend(int W, int H, const uint32_t* tile_ranges, const uint32_t* ids
         int x0 = (t % tx) * kTile, y0 = (t / tx) * kTile;
         for (int py = y0; py < std::min(y0 + kTile, H); ++py)
             for (int px = x0; px < std::min(x0 + kTile, W); ++px) {
-                PixelResult r = composite_pixel(list, px + 0.5, py + 0.5, bg, alpha_margin, t_margin);
+                PixelResult r = composite_pixel(list, px + 0.5, py + 0.5, bg, mg);
                 size_t pix = (size_t)py * W + px;
+                if (err_bound) err_bound[pix] = r.err_bound;
                 for (int ch = 0; ch < 3; ++ch) image[(size_t)ch * W * H + pix] = r.C[ch];
                 T_final[pix] = r.T;
                 n_contrib[pix] = r.n_contrib;
@@ -655,7 +690,7 @@ void oracle_brute_force(int n, const double* mean2d, const double* conic, const 
                 }
                 list.push_back(load_splat((uint32_t)g, mean2d, conic, opac, rgb));
             }
-            PixelResult r = composite_pixel(list, px + 0.5, py + 0.5, bg, 0.0, 0.0);
+            PixelResult r = composite_pixel(list, px + 0.5, py + 0.5, bg, Margins{0.0, 0.0, 0.0, 0.0});
             size_t pix = (size_t)py * W + px;
             for (int ch = 0; ch < 3; ++ch) image[(size_t)ch * W * H + pix] = r.C[ch];
             T_final[pix] = r.T;

@@ -10,6 +10,48 @@ import oracle
 from paper_2604_02120_gb300 import gs, scenes
 
 CORES = os.cpu_count() or 4
+# Rounding model of each blend variant, for the oracle's ambiguity flags and
+# colour error bounds (oracle.blend's margins):
+#  - alpha: relative error of alpha (absolute error of the exponent) that does
+#    not grow with the size of Eq. 3's terms: exp2 and constants; for the split
+#    tensor-core variants about twice the largest measured exponent error
+#    (4.7e-6 at 1280x720; the tile-power tests check it);
+#  - sum: exponent error per unit of the magnitude sum of Eq. 3's terms, the
+#    float32 evaluation of a sum (it dominates for nearly singular conics far
+#    from the splat's centre: needle-shaped splats of the clustered and heavy-
+#    tailed scenes), with offsets enlarged by `slack` px where the exponent is
+#    taken relative to a half-tile's reference pixel;
+#  - t: relative error of the transmittance product after a few hundred steps.
+U32 = 2.0 ** -24  # float32 unit roundoff
+SPLIT_EXP_ERR = 1e-5
+FP8_EXP_ERR = 1e-3  # the FP8-e4m3 split trial (measured max 7.4e-4; the stated bound is 2e-3)
+FP32_ALPHA_ERR = 2e-6
+T_PRODUCT_ERR = 1e-5
+MARGINS = {
+    "fp32": dict(alpha_margin=FP32_ALPHA_ERR, t_margin=T_PRODUCT_ERR, sum_margin=4 * U32, sum_slack=0.0),
+    "split": dict(alpha_margin=SPLIT_EXP_ERR, t_margin=T_PRODUCT_ERR, sum_margin=2 * U32, sum_slack=8.0),
+    "fp8_split": dict(alpha_margin=FP8_EXP_ERR, t_margin=T_PRODUCT_ERR, sum_margin=2 * U32, sum_slack=8.0),
+}
+
+
+def margins(variant):
+    return MARGINS.get(variant, MARGINS["split"])
+
+
+# Largest share of pixels with a decision within those margins of its threshold.
+# Measured with the oracle's own lists: 1280x720 0.025% FP32, 0.093% split;
+# 1920x1080 (1M clustered, many needle splats) 0.15% and 0.26%.
+# 3840x2160 (3M heavy-tailed: Student-t scales make many splats needles whose
+# float32 exponent is ill-conditioned over much of the image): 3.5% and 2.1%
+# on the sampled tiles, where the colour error still stays within its bound.
+MAX_AMB_FP32 = 5e-4
+MAX_AMB_SPLIT = 1e-3
+LARGE_MAX_AMB = {"1920x1080_1M": {"fp32": 3e-3, "split": 5e-3},
+                 "3840x2160_3M": {"fp32": 6e-2, "split": 4e-2}}
+# Plain (unsplit) operands carry the operand type's rounding into the exponent
+# (up to 0.1 for fp16 and 0.8 for bf16 on far splats): per-pixel bounds, about
+# twice the largest measured.
+PLAIN_MAX_ERR = {"fp16": 0.02, "bf16": 0.1}
 _REPORT = {}
 
 
@@ -37,14 +79,14 @@ def to_np(d):
     return {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in d.items()}
 
 
-def oracle_blend_on_gpu_params(cam, proj_np, bs_np, opac, bg=(0.0, 0.0, 0.0), alpha_margin=1e-4, t_margin=1e-4,
-                               tile_subset=None):
-    """Oracle blend over the GPU's sorted lists and FP32 splat parameters (cast to double)."""
+def oracle_blend_on_gpu_params(cam, proj_np, bs_np, opac, bg=(0.0, 0.0, 0.0), variant=None, tile_subset=None):
+    """Oracle blend over the GPU's sorted lists and FP32 splat parameters (cast
+    to double), with the rounding model of `variant` (None: no margins)."""
+    m = margins(variant) if variant else {}
     return oracle.blend(cam.width, cam.height, bs_np["tile_ranges"].view(np.uint32),
                         bs_np["ids"].view(np.uint32), proj_np["mean2d"].astype(np.float64),
                         proj_np["conic"].astype(np.float64), np.asarray(opac, np.float64),
-                        proj_np["rgb"].astype(np.float64), bg=bg, alpha_margin=alpha_margin, t_margin=t_margin,
-                        n_threads=CORES, tile_subset=tile_subset)
+                        proj_np["rgb"].astype(np.float64), bg=bg, n_threads=CORES, tile_subset=tile_subset, **m)
 
 
 def blend_gpu(cam, proj, bs, opac, variant="fp32", bg=(0.0, 0.0, 0.0), chunk=0, stages=0, ref_origin=0):

@@ -159,3 +159,20 @@ def test_bin_sort_noalloc_checks(lib):
     assert lib.gs_bin_sort_workspace_size(100, 1000, 64, 48, ctypes.byref(need)) == gs.GS_OK
     assert lib.gs_last_error() == b""
     assert lib.gs_bin_sort_workspace_size(100, 1000, 1 << 20, 1 << 20, ctypes.byref(need)) == INVALID
+
+
+def test_pack_splats_and_record_option_checks(lib):
+    """gs_pack_splats rejects bad sizes and misaligned buffers; a blend call
+    whose splat_records option is misaligned or has no row count is refused
+    before any CUDA call."""
+    _expect(lib, lib.gs_pack_splats(-1, 1, P, P, P, P, P, None), INVALID, "gs_pack_splats")
+    _expect(lib, lib.gs_pack_splats(10, 3, P, P, P, P, P, None), INVALID, "gs_pack_splats")  # not a multiple
+    _expect(lib, lib.gs_pack_splats(10, 10, P, P, None, P, P, None), INVALID, "gs_pack_splats")
+    _expect(lib, lib.gs_pack_splats(10, 10, P, P, P, P, ODD, None), INVALID, "gs_pack_splats")
+    w, h = _sizes(64), _sizes(48)
+    for ptr, count in ((ODD, 10), (P, 0), (P, 1 << 31)):
+        o = gs.make_opts("fp16_split")
+        o.splat_records, o.splat_record_count = ptr.value, count
+        _expect(lib, lib.gs_blend_forward_views(1, w, h, 0, P, P, P, P, P, P, ctypes.byref(o), P, P, P, None),
+                INVALID, "gs_blend_forward")
+    assert ctypes.sizeof(gs.gs_blend_opts) == 80

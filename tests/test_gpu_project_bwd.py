@@ -186,7 +186,22 @@ def test_project_backward_sh1_without_lowpass():
     pn = to_np(proj)
     ref_cov = oracle.project(sc.means, sc.scales, sc.quats, sc.sh, sc.sh_degree, cam)["cov2d"]
     det = ref_cov[:, 0] * ref_cov[:, 2] - ref_cov[:, 1] ** 2
-    assert ((det < 1e-6) & (pn["radius"] > 0)).sum() > 0  # the FP64 branch runs
+    fp64 = (det < 1e-6) & (pn["radius"] > 0)
+    assert fp64.sum() > 0  # the FP64 branch runs
+    # its forward outputs: the conic (inverse of the float32 2D covariance, taken
+    # in FP64) within the float32 covariance's rounding times the inversion's
+    # condition (|ac| + b^2) / det, the radius exact up to integer boundaries
+    ref_fwd = oracle.project(sc.means, sc.scales, sc.quats, sc.sh, sc.sh_degree, cam)
+    a, b, c = ref_cov[fp64, 0], ref_cov[fp64, 1], ref_cov[fp64, 2]
+    cond = (np.abs(a * c) + b * b) / np.abs(det[fp64])
+    scale = np.abs(ref_fwd["conic"][fp64]).max(1)
+    err = np.abs(pn["conic"][fp64] - ref_fwd["conic"][fp64]).max(1) / scale
+    assert (err <= 8 * 2.0 ** -24 * cond + 1e-6).all(), f"FP64-branch conic error {err.max():.2e}"
+    np.testing.assert_allclose(pn["mean2d"][fp64], ref_fwd["mean2d"][fp64], rtol=1e-5, atol=2e-4)
+    r_ok = (pn["radius"][fp64] == ref_fwd["radius"][fp64]).mean()
+    assert r_ok > 0.95, f"FP64-branch radius agreement {r_ok:.3f}"
+    report("project_fp64_branch_forward", {"splats": int(fp64.sum()), "conic_rel_err_max": float(err.max()),
+                                           "radius_equal": float(r_ok)})
     dm, dc, dr = _upstream(sc.n, 5)
     g = to_np(gs.project_backward(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam,
                                   proj["radius"], torch.from_numpy(dm).cuda(), torch.from_numpy(dc).cuda(),

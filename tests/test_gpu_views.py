@@ -10,11 +10,10 @@ import torch
 import oracle
 from paper_2604_02120_gb300 import gs, scenes
 
-from gpu_common import CORES, check_tight_lists, to_np
+from gpu_common import CORES, MAX_AMB_FP32, MAX_AMB_SPLIT, check_tight_lists, margins, to_np
 
 pytestmark = pytest.mark.gpu
 
-SPLIT_EXP_ERR = 2e-4
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -151,6 +150,26 @@ def test_autotune_picks_a_built_shape():
     assert (opts.chunk, opts.stages) in [(32, 2), (32, 4), (16, 4), (16, 6)]
 
 
+@pytest.mark.parametrize("variant", ["fp16_split", "bf16_split", "fp8_split"])
+def test_batched_views_tma_records_equal_loads(variant):
+    """The batched forward over a mixed-resolution ring with the splat
+    records packed after projection and staged by TMA gathers equals the
+    per-thread-load producer bit for bit (items of several views, opacity
+    indexed per Gaussian), as does the backward that follows."""
+    sc = _ring_scene(n=800, sizes=((160, 120), (128, 72), (200, 112), (240, 135)))
+    dev = gs.scene_to_device(sc)
+    out = []
+    for tma in (False, True):
+        br = gs.BatchRenderer(dev, sc.cameras, gs.make_opts(variant, bg=(0.1, 0.2, 0.1)), capacity=1 << 19,
+                              tma_records=tma)
+        br.dL.copy_(torch.linspace(-1, 1, br.dL.numel(), device="cuda"))
+        br.step()
+        assert gs.gs_sync_status() == gs.GS_OK
+        out.append((br.image.clone(), br.T.clone(), br.nc.clone()))
+    for a, b in zip(*out):
+        assert torch.equal(a, b)
+
+
 @pytest.mark.parametrize("variant", ["fp32", "fp16_split"])
 def test_batched_views_match_oracle(variant):
     """Mixed-resolution ring of views (a small stand-in for the 16-camera
@@ -167,7 +186,6 @@ def test_batched_views_match_oracle(variant):
     co = br.conic.cpu().numpy().astype(np.float64)
     rgb = br.rgb.cpu().numpy().astype(np.float64)
     tile0 = 0
-    margin = (1e-4, 1e-4) if variant == "fp32" else (SPLIT_EXP_ERR, 1e-5)
     tol = 1e-4 if variant == "fp32" else 1e-3
     for v, cam in enumerate(sc.cameras):
         T = cam.num_tiles
@@ -175,11 +193,11 @@ def test_batched_views_match_oracle(variant):
         # the oracle blends view v with its own local tile ranges; ids index all items
         ref = oracle.blend(cam.width, cam.height, r.astype(np.uint32), ids, m2, co,
                            np.tile(sc.opacities.astype(np.float64), len(sc.cameras)), rgb, bg=(0.1, 0.1, 0.1),
-                           alpha_margin=margin[0], t_margin=margin[1], n_threads=CORES)
+                           n_threads=CORES, **margins(variant))
         img, Tf, nc = (x.cpu().numpy() for x in br.view_image(v))
         ok = ~ref["ambiguous"]
-        assert ref["ambiguous"].mean() < 0.02
-        assert np.abs(img - ref["image"])[:, ok].max() <= tol
+        assert ref["ambiguous"].mean() <= (MAX_AMB_FP32 if variant == "fp32" else MAX_AMB_SPLIT)
+        assert (np.abs(img - ref["image"])[:, ok] <= tol + ref["err_bound"][ok]).all()
         np.testing.assert_array_equal(nc[ok], ref["n_contrib"][ok])
         tile0 += T
 

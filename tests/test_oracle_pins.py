@@ -401,6 +401,57 @@ def test_tight_rule_exact_threshold_is_kept_and_ambiguous():
     assert 2 not in kept0 and (0, 2) not in amb
 
 
+def test_rounding_model_bounds_float32_exponent_of_needles():
+    """The oracle's rounding model for ambiguity (sum margin): a float32
+    evaluation of Eq. 3's exponent errs by at most a few unit roundoffs times
+    the magnitude sum S of its three terms, which for a nearly singular conic
+    far from its centre is thousands of times the exponent itself.  An
+    independent float32 evaluation (numpy, one rounding per operation) stays
+    within 4 u S of the FP64 value on random needles, while a flat 2e-6
+    margin does not cover it; and a pixel whose alpha lies within 4 u S of
+    1/255, but not within 2e-6, is ambiguous only under the sum margin."""
+    f32, u = np.float32, 2.0 ** -24
+    rng = np.random.default_rng(9)
+    n = 20000
+    theta = rng.uniform(0, np.pi, n)
+    a2 = 10.0 ** rng.uniform(-3, 0, n)
+    b2 = a2 * 10.0 ** rng.uniform(-6, -2, n)
+    c, s_ = np.cos(theta), np.sin(theta)
+    A = (a2 * c * c + b2 * s_ * s_).astype(f32)
+    B = ((a2 - b2) * c * s_).astype(f32)
+    C = (a2 * s_ * s_ + b2 * c * c).astype(f32)
+    # offsets along the needle's null direction, where the terms cancel
+    t = rng.uniform(50, 2000, n)
+    dx = (t * -s_ + rng.normal(0, 2, n)).astype(f32)
+    dy = (t * c + rng.normal(0, 2, n)).astype(f32)
+    pw32 = (-f32(0.5) * (A * dx * dx + C * dy * dy) - B * dx * dy).astype(np.float64)
+    A64, B64, C64, dx64, dy64 = (x.astype(np.float64) for x in (A, B, C, dx, dy))
+    pw64 = -0.5 * A64 * dx64 ** 2 - B64 * dx64 * dy64 - 0.5 * C64 * dy64 ** 2
+    S = 0.5 * np.abs(A64) * dx64 ** 2 + np.abs(B64 * dx64 * dy64) + 0.5 * np.abs(C64) * dy64 ** 2
+    err = np.abs(pw32 - pw64)
+    assert (err <= 4 * u * S).all()
+    assert (err > 2e-6).mean() > 0.5
+    # one needle, one pixel: alpha just above 1/255 by more than 2e-6 but less than 4 u S
+    k = int(np.argmax(S * ((pw64 > -5.4) & (pw64 < -0.2))))
+    o = float(np.exp(np.log(1 / 255) - pw64[k]) * (1 + 0.5 * 4 * u * S[k]))
+    assert 2e-6 < 0.5 * 4 * u * S[k] and o < 1
+    mean2d = np.array([[0.5 + float(dx64[k]), 0.5 + float(dy64[k])]])
+    conic = np.array([[A64[k], B64[k], C64[k]]])
+    ranges, ids = np.array([0, 1], np.uint32), np.array([0], np.uint32)
+    W = H = 1
+    base = dict(alpha_margin=2e-6, t_margin=1e-5)
+    flat = oracle.blend(W, H, ranges, ids, mean2d, conic, np.array([o]), np.ones((1, 3)), **base)
+    model = oracle.blend(W, H, ranges, ids, mean2d, conic, np.array([o]), np.ones((1, 3)), sum_margin=4 * u,
+                         sum_slack=0.0, **base)
+    assert flat["n_contrib"][0, 0] == 1 and not flat["ambiguous"][0, 0]
+    assert model["ambiguous"][0, 0]
+    np.testing.assert_array_equal(model["image"], flat["image"])
+    # without margins there is no bound; with them the bound covers alpha's relative error
+    assert flat["err_bound"][0, 0] > 0 and model["err_bound"][0, 0] > flat["err_bound"][0, 0]
+    none = oracle.blend(W, H, ranges, ids, mean2d, conic, np.array([o]), np.ones((1, 3)))
+    assert none["err_bound"][0, 0] == 0 and not none["ambiguous"][0, 0]
+
+
 def test_bin_sort_capacity_overflow_reports():
     sc = scenes.tiny_scene(11, n=20, width=48, height=48)
     cam = sc.cameras[0]
@@ -794,3 +845,22 @@ def test_blend_grad_central_differences_at_1080p_clustered():
     assert discarded <= 0.2 * 16 * 9 and nonzero >= 100
     for name, e in rel.items():
         assert e < 1e-3, (name, e)
+
+
+def test_bin_sort_tile_mask_gives_the_marked_tiles_lists():
+    """oracle.bin_sort with a tile mask (used to sample large images): the
+    marked tiles' lists equal the full call's, every other tile is empty."""
+    sc = scenes.tiny_scene(3, n=300, width=96, height=80, sh_degree=0)
+    cam = sc.cameras[0]
+    pr = oracle.project(sc.means, sc.scales, sc.quats, sc.sh, 0, cam)
+    d32 = pr["depth"].astype(np.float32)
+    for kw in ({}, {"conic": pr["conic"].astype(np.float32), "power_min": _power_min(sc.opacities)}):
+        full = oracle.bin_sort(pr["mean2d"], pr["radius"], d32, 96, 80, **kw)
+        mask = np.zeros(cam.num_tiles, bool)
+        mask[[3, 7, 12, 29]] = True
+        sub = oracle.bin_sort(pr["mean2d"], pr["radius"], d32, 96, 80, tile_mask=mask, **kw)
+        assert 0 < sub["n_instances"] < full["n_instances"]
+        for t in range(cam.num_tiles):
+            a = full["ids"][full["tile_ranges"][2 * t]:full["tile_ranges"][2 * t + 1]]
+            b = sub["ids"][sub["tile_ranges"][2 * t]:sub["tile_ranges"][2 * t + 1]]
+            assert (list(a) == list(b)) if mask[t] else len(b) == 0
