@@ -1,14 +1,17 @@
 #!/usr/bin/env python
 """Benchmark of the Gaussian-splatting hot path on one GB300 (or N, one
-process per GPU under torchrun, each rendering its own copy of the workload:
-weak scaling, no collective on the data path).
+process per GPU under torchrun).
 
-One step = project -> bin/sort -> blend forward (tensor-core variant) ->
-blend backward over the 1280x720, 200k-Gaussian, SH-degree-3 synthetic scene
-(seed 0), inputs resident in HBM.  The metric is Gaussian-pixel evaluations
-per second, evaluations = sum over pixels of n_contrib (the pairs Eq. 1 with
-the skip/stop rules must examine), counted once per forward and once per
-backward.  L2 is flushed (256 MB write) before every timed step.
+One step = project -> bin/sort (opacity-aware lists) -> tile order -> blend
+forward (tensor-core variant) -> blend backward over the 3840x2160,
+3M-Gaussian synthetic scene with heavy-tailed scales (seed 0), inputs resident
+in HBM.  The metric is Gaussian-pixel evaluations per second, evaluations =
+sum over pixels of n_contrib (the pairs Eq. 1 with the skip/stop rules must
+examine), counted once per forward and once per backward.  L2 is flushed
+(256 MB write) before every timed step.  With N > 1 ranks the blend is
+sharded by tiles (rank r blends tiles t = r mod N) and the per-Gaussian
+gradients are all-reduced over NCCL: the frame's work is fixed (strong
+scaling).
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 instead (the reference arm), on a bounded sample of the same workload.
@@ -42,30 +45,46 @@ WORKLOADS = {
 }
 WORKLOAD_NOTE = " (synthetic stand-in for the paper's trained scenes)"
 
-# DRAM traffic per launch from ncu captures, keyed by kernel, with the SHA-256 of
-# the kernel's source when it was measured and the workload it was measured on
-# (entries for another source or workload are not reported).
-KNOWN_TRAFFIC = {
-    # profiles/k_blend_tc_fp16split_1280x720_200k.md, profiles/k_blend_tc_bwd_fp16split_1280x720_200k.md
-    # (dram__bytes_read.sum + dram__bytes_write.sum, median over the captured launches; forward at chunk 32).
-    # Since the captures only the host-side launch wrappers changed (launch shapes cached under a lock):
-    # the kernels' device code and their grids are the captured ones.
-    "k_blend_tc<fp16_split>": {"bytes": 9740672, "src": "758192731a592fb3", "config": 1},
-    "k_blend_tc_bwd<fp16_split>": {"bytes": 31102976, "src": "134ba8c991a6bcf0", "config": 1},
-}
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# ncu captures, keyed by kernel (or stage), with the SHA-256 prefix of the
+# sources it was measured with and the workload; an entry whose sources or
+# workload differ from the run's is not reported.
+KNOWN_TRAFFIC = {}
+
+# Algorithmic work per unit (the roofline numerators; the derivations are in
+# the design notes):
+#  - FP32 operations per evaluated pair: compositing, skip and stop tests with
+#    the exponent from the tensor cores (10), the CUDA-core forward that also
+#    evaluates Eq. 3 (16), the backward pass (25);
+#  - bytes per instance a blend touches: the id and the splat's record
+#    (mean2d 8, conic 12, opacity 4, rgb 12); per pixel written or read:
+#    image 12, T_final 4, n_contrib 4 (forward), plus dL/dimage 12 (backward);
+#    the backward adds 9 gradient floats per (instance, tile half);
+#  - bin/sort: per Gaussian its inputs (mean2d, radius, depth, conic,
+#    power_min: 32 bytes) and per instance the sorted id (4 bytes), per tile
+#    its range (8 bytes): the least a binning must move.
+FP32_OPS = {"forward_tc": 10, "forward_fp32": 16, "backward": 25}
+REC_BYTES = 4 + 36
+K_OF = {"fp16": 16, "bf16": 16, "fp16_split": 16, "bf16_split": 32, "fp8_split": 64}
+DTYPE_OF = {"fp32": "f32 (CUDA-core Eq. 3)", "fp16": "fp16 operands, f32 accumulate",
+            "bf16": "bf16 operands, f32 accumulate", "fp16_split": "fp16 hi+lo split operands, f32 accumulate",
+            "bf16_split": "bf16 hi+mid+lo split operands, f32 accumulate",
+            "fp8_split": "e4m3 5-term split operands (trial), f32 accumulate"}
 
 
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--variant", default="fp16_split")
-    p.add_argument("--config", type=int, default=1)
+    p.add_argument("--variant", default="bf16_split")
+    p.add_argument("--config", type=int, default=4)
+    p.add_argument("--full-lists", action="store_true", help="full 3-sigma rectangles instead of opacity-aware lists")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--quick", action="store_true", help="skip the per-variant blend sweep")
+    p.add_argument("--sustained-seconds", type=float, default=5.0)
+    p.add_argument("--quick", action="store_true", help="skip the per-variant sweeps and the 1920x1080 leg")
     return p.parse_args()
 
 
@@ -97,13 +116,14 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling every 200 ms while running."""
+    """nvidia-smi clock/throttle sampling (every interval_ms) while running."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, interval_ms=50):
         self.gpu = gpu_index
+        self.interval = int(interval_ms)
         self.proc = None
         self.path = None
 
@@ -112,7 +132,7 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.interval)],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -173,6 +193,192 @@ def source_digest(*names):
 
 # ------------------------------------------------------------------ ours ----
 
+class Step:
+    """Buffers and stages of one step on one camera: project -> (opacity-aware)
+    bin/sort -> tile order -> blend forward -> blend backward."""
+
+    def __init__(self, gs, torch, dev, cam, variant, tight, shard=(1, 0)):
+        self.gs, self.torch, self.dev, self.cam = gs, torch, dev, cam
+        self.W, self.H, self.n = cam.width, cam.height, int(dev["means"].shape[0])
+        self.tight = tight
+        W, H, n = self.W, self.H, self.n
+        self.pmin = torch.empty(n, device="cuda") if tight else None
+        # capacity from one synchronising bin/sort; the timed steps then never
+        # synchronise the host (gs_bin_sort_views in graph mode)
+        proj = self.project()
+        cap = 1 << 20
+        while True:
+            ws = torch.empty(gs.gs_bin_sort_workspace_size(n, cap, W, H) + 256, dtype=torch.uint8, device="cuda")
+            ids = torch.empty(cap, dtype=torch.int32, device="cuda")
+            ranges = torch.empty(2 * gs.num_tiles(W, H), dtype=torch.int32, device="cuda")
+            if tight:
+                gs.gs_alpha_power_min(n, dev["opacities"], self.pmin)
+            st, count = gs.gs_bin_sort_views(1, n, proj["mean2d"], proj["radius"], proj["depth"], [W], [H], cap, ws,
+                                             None, ids, ranges, check=False, conic=proj["conic"] if tight else None,
+                                             power_min=self.pmin)
+            if st == gs.GS_OK:
+                break
+            assert st == gs.GS_ERR_CAPACITY, st
+            del ws, ids
+            cap = count + 1024
+        self.count0 = count
+        self.capacity = int(count * 1.1) + 4096
+        self.ws = torch.empty(gs.gs_bin_sort_workspace_size(n, self.capacity, W, H) + 256, dtype=torch.uint8,
+                              device="cuda")
+        self.ids = torch.empty(self.capacity, dtype=torch.int32, device="cuda")
+        self.ranges = ranges
+        self.count_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
+        self.order = torch.empty(gs.num_tiles(W, H), dtype=torch.int32, device="cuda")
+        self.bs = dict(tile_ranges=self.ranges, ids=self.ids)
+        # packed splat records for the TMA-staged forward (measured against the
+        # default per-thread loads; the step uses the faster, per-thread loads)
+        self.rec = torch.empty(n, 16, device="cuda") if n > 0 else None
+        self.opts = gs.make_opts(variant, tile_order=self.order, shard_count=shard[0], shard_index=shard[1])
+        del ws, ids
+
+    def project(self):
+        d = self.dev
+        self.proj = self.gs.project(d["means"], d["scales"], d["quats"], d["sh"], d["sh_degree"], self.cam)
+        return self.proj
+
+    def sort(self, proj=None):
+        gs, proj = self.gs, proj or self.proj
+        if self.tight:
+            gs.gs_alpha_power_min(self.n, self.dev["opacities"], self.pmin)
+        gs.gs_bin_sort_views(1, self.n, proj["mean2d"], proj["radius"], proj["depth"], [self.W], [self.H],
+                             self.capacity, self.ws, None, self.ids, self.ranges, count_dev=self.count_dev,
+                             conic=proj["conic"] if self.tight else None, power_min=self.pmin)
+        gs.tile_order(self.ranges, [self.W], [self.H], out=self.order)
+
+    def forward(self, proj=None, opts=None):
+        self.fwd = self.gs.blend_forward(self.W, self.H, self.bs, proj or self.proj, self.dev["opacities"],
+                                         opts or self.opts)
+        return self.fwd
+
+    def backward(self, dL, proj=None, fwd=None, opts=None):
+        return self.gs.blend_backward(self.W, self.H, self.bs, proj or self.proj, self.dev["opacities"],
+                                      opts or self.opts, fwd or self.fwd, dL)
+
+    def eager(self, dL, ev=None, stream=None):
+        if ev:
+            ev[0].record(stream)
+        self.project()
+        if ev:
+            ev[1].record(stream)
+        self.sort()
+        if ev:
+            ev[2].record(stream)
+        self.forward()
+        if ev:
+            ev[3].record(stream)
+        g = self.backward(dL)
+        if ev:
+            ev[4].record(stream)
+        return g
+
+
+def _events(torch, k):
+    return [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+
+
+def _timed(torch, flush, stream, fn, reps):
+    """Median ms of fn() over reps launches, L2 flushed before each."""
+    ev = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = _events(torch, 2)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+
+def backward_issued_pairs(torch, n_contrib, chunk=16):
+    """Pairs the tensor-core backward evaluates: every pixel of a tile, in
+    chunks of 16 splats, up to the tile's longest n_contrib."""
+    H, W = n_contrib.shape
+    ty, tx = (H + 15) // 16, (W + 15) // 16
+    nc = torch.zeros(ty * 16, tx * 16, dtype=torch.int32, device=n_contrib.device)
+    nc[:H, :W] = n_contrib
+    mx = nc.view(ty, 16, tx, 16).amax(dim=(1, 3)).to(torch.int64)
+    return int((((mx + chunk - 1) // chunk) * chunk * 256).sum().item())
+
+
+def blend_roofline(kind, variant, t_ms, evals, issued, pixels, peaks):
+    """Every roofline term of one blend launch, as Gaussian-pixel evals/s the
+    term alone would allow, and the achieved rate; bound = the smallest."""
+    ex2, rcp, fma = peaks["ex2_per_s"], peaks["rcp_per_s"], peaks["fma_per_s"]
+    tc = variant != "fp32"
+    achieved = evals / (t_ms / 1e3)
+    terms = {}
+    if kind == "forward":
+        terms["mufu"] = {"per_s": ex2, "note": "1 ex2 per evaluated pair"}
+        ops = FP32_OPS["forward_tc" if tc else "forward_fp32"]
+        bytes_ = issued / 256 * REC_BYTES + pixels * 20 if tc else evals / 256 * REC_BYTES + pixels * 20
+        flops_pair = 2 * K_OF.get(variant, 0) * issued / max(evals, 1)
+    else:
+        terms["mufu"] = {"per_s": 1.0 / (1.0 / ex2 + 1.0 / rcp), "note": "1 ex2 + 1 rcp per evaluated pair"}
+        ops = FP32_OPS["backward"]
+        bytes_ = issued / 256 * (REC_BYTES + 2 * 36) + pixels * 32
+        flops_pair = (256 + 2 * K_OF.get(variant, 0)) * issued / max(evals, 1)
+    terms["fp32_issue"] = {"per_s": fma / ops, "note": f"{ops} FP32 operations per evaluated pair at the measured "
+                                                       f"FMA rate {fma / 1e12:.1f} T/s"}
+    hbm = read_peaks().get("hbm_gbs")
+    if hbm:
+        terms["hbm"] = {"per_s": hbm * 1e9 / (bytes_ / max(evals, 1)),
+                        "note": f"{bytes_ / max(evals, 1):.3f} algorithmic bytes per evaluated pair at "
+                                f"{hbm:.0f} GB/s (measured copy)", "bytes_per_launch": int(bytes_)}
+    tf = read_peaks().get("bf16_tflops")
+    if tc and tf and flops_pair > 0:
+        tpeak = tf * 1e12 * (2.0 if variant == "fp8_split" else 1.0)
+        terms["tensor"] = {"per_s": tpeak / flops_pair,
+                           "note": f"{flops_pair:.1f} MMA FLOPs per evaluated pair at {tpeak / 1e12:.0f} TFLOP/s "
+                                   f"(measured bf16{' x 2, e4m3 nominal ratio' if variant == 'fp8_split' else ''})",
+                           "achieved_tflops": round(flops_pair * achieved / 1e12, 2),
+                           "frac": round(flops_pair * achieved / tpeak, 4)}
+    bound = min(terms, key=lambda k: terms[k]["per_s"])
+    for v in terms.values():
+        v["per_s"] = round(v["per_s"] / 1e9, 1)  # G evals/s
+    return {"kernel": kind, "variant": variant, "launch_ms": round(t_ms, 5), "achieved_g_evals_per_s":
+            round(achieved / 1e9, 2), "terms_g_evals_per_s": terms, "bound": bound,
+            "frac_of_bound": round(achieved / 1e9 / terms[bound]["per_s"], 4),
+            "issued_over_evaluated": round(issued / max(evals, 1), 3)}
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def variant_sweep(gs, torch, st, dL, flush, stream, reps, variants):
+    """Blend-only ms/frame of each variant on the step's lists (forward, and
+    backward from that variant's own forward), TC against FP32 CUDA-core."""
+    out = {}
+    for name in variants:
+        o = gs.make_opts(name, tile_order=st.order)
+        for _ in range(2):
+            fwd = st.forward(opts=o)
+            st.backward(dL, fwd=fwd, opts=o)
+        f_ms = _timed(torch, flush, stream, lambda: st.forward(opts=o), reps)
+        fwd = st.forward(opts=o)
+        b_ms = _timed(torch, flush, stream, lambda: st.backward(dL, fwd=fwd, opts=o), reps)
+        torch.cuda.synchronize()
+        ev = int(fwd["n_contrib"].sum().item())
+        out[name] = {"forward_ms": round(f_ms, 5), "backward_ms": round(b_ms, 5),
+                     "forward_evals_per_s": ev / (f_ms / 1e3), "backward_evals_per_s": ev / (b_ms / 1e3)}
+    assert gs.gs_sync_status() == gs.GS_OK
+    if "fp32" in out:
+        for name, v in out.items():
+            v["forward_speedup_vs_fp32"] = round(out["fp32"]["forward_ms"] / v["forward_ms"], 3)
+            v["backward_speedup_vs_fp32"] = round(out["fp32"]["backward_ms"] / v["backward_ms"], 3)
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2604_02120_gb300 import gs, scenes
@@ -188,77 +394,36 @@ def run_ours(args):
     cam = sc.cameras[0]
     W, H = cam.width, cam.height
     dev = gs.scene_to_device(sc)
-    fp32 = gs.make_opts("fp32")
+    tight = not args.full_lists
     dL = torch.from_numpy(scenes.upstream_grad(0, [cam])[0]).cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    # capacity from one synchronising bin/sort; the timed steps then never
-    # synchronise the host (gs_bin_sort_views in graph mode)
-    proj0 = gs.project(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam)
-    count0 = gs.BinSorter("cuda", 1 << 20).run(proj0["mean2d"], proj0["radius"], proj0["depth"], W, H)["n_instances"]
-    capacity = int(count0 * 1.25) + 4096
+    # with N ranks each blends the tiles t = rank (mod N) of the longest-first order
+    st = Step(gs, torch, dev, cam, args.variant, tight, shard=(ws_n, rank))
     n = sc.n
-    ws = torch.empty(gs.gs_bin_sort_workspace_size(n, capacity, W, H) + 256, dtype=torch.uint8, device="cuda")
-    ids = torch.empty(capacity, dtype=torch.int32, device="cuda")  # the blends need no sorted keys
-    ranges = torch.empty(2 * gs.num_tiles(W, H), dtype=torch.int32, device="cuda")
-    count_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
-    # the opacity-aware step sorts into buffers of its own, so the full lists
-    # (and the forward outputs that index them) stay intact for the timings below
-    t_ids = torch.empty_like(ids)
-    t_ranges, t_count = torch.empty_like(ranges), torch.zeros_like(count_dev)
-    # longest tile lists first (gs_tile_order after every bin/sort)
-    order, t_order = torch.empty(gs.num_tiles(W, H), dtype=torch.int32, device="cuda"), \
-        torch.empty(gs.num_tiles(W, H), dtype=torch.int32, device="cuda")
-    opts = gs.make_opts(args.variant, tile_order=order)
-    t_opts = gs.make_opts(args.variant, tile_order=t_order)
-
-    def step(ev=None, tight=False):
-        if ev:
-            ev[0].record(stream)
-        proj = gs.project(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam)
-        if ev:
-            ev[1].record(stream)
-        # opacity-aware lists: the exponent each splat must reach in a tile (gs_alpha_power_min)
-        pmin = gs.alpha_power_min(dev["opacities"]) if tight else None
-        i_, r_, c_ = (t_ids, t_ranges, t_count) if tight else (ids, ranges, count_dev)
-        gs.gs_bin_sort_views(1, n, proj["mean2d"], proj["radius"], proj["depth"], [W], [H], capacity, ws, None, i_,
-                             r_, count_dev=c_, conic=proj["conic"] if tight else None, power_min=pmin)
-        o_ = t_opts if tight else opts
-        gs.tile_order(r_, [W], [H], out=t_order if tight else order)
-        bs = dict(tile_ranges=r_, ids=i_)
-        if ev:
-            ev[2].record(stream)
-        fwd = gs.blend_forward(W, H, bs, proj, dev["opacities"], o_)
-        if ev:
-            ev[3].record(stream)
-        g = gs.blend_backward(W, H, bs, proj, dev["opacities"], o_, fwd, dL)
-        if ev:
-            ev[4].record(stream)
-        bs["n_instances"] = count0
-        return proj, bs, fwd, g
 
     for _ in range(max(args.warmup, 3)):
-        step()
+        st.eager(dL)
     torch.cuda.synchronize()
     assert gs.gs_sync_status() == gs.GS_OK
-    proj, bs, fwd, _ = step()
     tuned = None
     if args.variant != "fp32":  # the forward's pipeline shape by the library's own measurement
-        gs.gs_blend_autotune([W], [H], n, ranges, ids, proj["mean2d"], proj["conic"], dev["opacities"], proj["rgb"],
-                             opts, fwd["image"], fwd["T_final"], fwd["n_contrib"])
-        t_opts.chunk, t_opts.stages = opts.chunk, opts.stages
-        tuned = {"chunk": opts.chunk, "stages": opts.stages}
-        proj, bs, fwd, _ = step()
-    evals_fwd = int(fwd["n_contrib"].sum().item())
-    n_inst = bs["n_instances"]
+        gs.gs_blend_autotune([W], [H], n, st.ranges, st.ids, st.proj["mean2d"], st.proj["conic"], dev["opacities"],
+                             st.proj["rgb"], st.opts, st.fwd["image"], st.fwd["T_final"], st.fwd["n_contrib"])
+        tuned = {"chunk": st.opts.chunk, "stages": st.opts.stages}
+    g_eager = st.eager(dL)
+    torch.cuda.synchronize()
+    evals_fwd = int(st.fwd["n_contrib"].sum().item())
+    if dist:  # each rank holds its tiles' pixels: the frame's evaluations are the sum
+        t = torch.tensor([evals_fwd], device="cuda", dtype=torch.int64)
+        dist.all_reduce(t)
+        evals_fwd = int(t.item())
+    n_inst = int(st.count_dev.item())
 
     # ---- the step as four CUDA graphs (projection; bin/sort and tile order;
-    # forward; backward), replayed with CUDA events between them on the
-    # launching stream: the stage chain without per-launch host and queue gaps
+    # forward; backward + gradient all-reduce), replayed with CUDA events
+    # between them on the launching stream
     graphs = []
-
-    # with a process group, its watchdog thread queries CUDA events while the
-    # main thread captures: only this thread's calls are checked then
     mode = {"capture_error_mode": "thread_local"} if dist else {}
 
     def capture(fn):
@@ -269,236 +434,247 @@ def run_ours(args):
         return r
 
     launches_c = gs.gs_launch_count()
-    g_proj = capture(lambda: gs.project(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam))
-
-    def sort_stage():
-        gs.gs_bin_sort_views(1, n, g_proj["mean2d"], g_proj["radius"], g_proj["depth"], [W], [H], capacity, ws, None,
-                             ids, ranges, count_dev=count_dev)
-        gs.tile_order(ranges, [W], [H], out=order)
-
-    capture(sort_stage)
-    g_bs = dict(tile_ranges=ranges, ids=ids)
-    g_fwd = capture(lambda: gs.blend_forward(W, H, g_bs, g_proj, dev["opacities"], opts))
-    capture(lambda: gs.blend_backward(W, H, g_bs, g_proj, dev["opacities"], opts, g_fwd, dL))
+    g_proj = capture(st.project)
+    capture(lambda: st.sort(g_proj))
+    g_fwd = capture(lambda: st.forward(g_proj))
+    g_grad = capture(lambda: st.backward(dL, proj=g_proj, fwd=g_fwd))
     launches_per_step = gs.gs_launch_count() - launches_c  # the library's kernels in the four graphs
-    for _ in range(3):
-        for g in graphs:
+
+    def replay_step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        for i, g in enumerate(graphs):
             g.replay()
+            if i == 3 and dist:  # the one exchange: the per-Gaussian gradient buffer (N x 9 floats)
+                dist.all_reduce(g_grad["mean2d"]._base, op=dist.ReduceOp.SUM)
+            if ev:
+                ev[i + 1].record(stream)
+
+    for _ in range(3):
+        replay_step()
     torch.cuda.synchronize()
     assert gs.gs_sync_status() == gs.GS_OK
-    assert torch.equal(g_fwd["image"], fwd["image"]) and torch.equal(g_fwd["n_contrib"], fwd["n_contrib"])
+    assert torch.equal(g_fwd["image"], st.fwd["image"]) and torch.equal(g_fwd["n_contrib"], st.fwd["n_contrib"])
 
     K = args.steps
-    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-    st_ev = [(E(), E()) for _ in range(K)]
-    k_ev = [tuple(E() for _ in range(5)) for _ in range(K)]
-    with ClockSampler(local) as clk:
+    k_ev = [_events(torch, 5) for _ in range(K)]
+    with ClockSampler(local, 50) as clk:
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
         wall0 = time.perf_counter()
         for k in range(K):
             flush.zero_()
-            st_ev[k][0].record(stream)
-            k_ev[k][0].record(stream)
-            for i, g in enumerate(graphs):
-                g.replay()
-                k_ev[k][i + 1].record(stream)
-            st_ev[k][1].record(stream)
+            replay_step(k_ev[k])
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         wall = time.perf_counter() - wall0
-    launches = launches_per_step * K
     clocks = clk.summary()
     assert gs.gs_sync_status() == gs.GS_OK  # also catches a capacity overflow of the bin/sort
-    step_ms = [a.elapsed_time(b) for a, b in st_ev]
-    proj_ms = [e[0].elapsed_time(e[1]) for e in k_ev]
-    sort_ms = [e[1].elapsed_time(e[2]) for e in k_ev]
-    fwd_ms = [e[2].elapsed_time(e[3]) for e in k_ev]
-    bwd_ms = [e[3].elapsed_time(e[4]) for e in k_ev]
-    dev_ms = sum(step_ms)
+    launches = launches_per_step * K
+    stage = lambda i, j: [e[i].elapsed_time(e[j]) for e in k_ev]  # noqa: E731
+    proj_ms, sort_ms, fwd_ms, bwd_ms = stage(0, 1), stage(1, 2), stage(2, 3), stage(3, 4)
+    dev_ms = sum(stage(0, 4))
     if dist:
         t = torch.tensor([dev_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dev_ms = float(t.item())
     evals_step = 2 * evals_fwd  # forward and backward each examine sum(n_contrib) pairs
-    value = ws_n * evals_step * K / (dev_ms / 1e3)
+    value = evals_step * K / (dev_ms / 1e3)
+
+    # ---- the same replays for a few seconds: clocks over a long window
+    sus = None
+    if args.sustained_seconds > 0:
+        Ks = max(K, int(args.sustained_seconds * 1e3 / max(dev_ms / K, 1e-3)))
+        s_ev = _events(torch, 2)
+        with ClockSampler(local, 100) as sclk:
+            if dist:
+                dist.barrier()
+            s_ev[0].record(stream)
+            for _ in range(Ks):
+                flush.zero_()
+                replay_step()
+            s_ev[1].record(stream)
+            torch.cuda.synchronize()
+        sus = {"steps": Ks, "ms_per_step": round(s_ev[0].elapsed_time(s_ev[1]) / Ks, 5), "clocks": sclk.summary(),
+               "note": "the same graph replays (L2 flush included) for several seconds, clocks sampled every 100 ms"}
 
     # ---- the same step launched call by call (no graphs), for comparison
-    Ke = min(K, 200)
-    e_ev = [(E(), E()) for _ in range(Ke)]
+    Ke = min(K, 100)
+    e_ev = [_events(torch, 5) for _ in range(Ke)]
     for k in range(Ke):
         flush.zero_()
-        e_ev[k][0].record(stream)
-        step()
-        e_ev[k][1].record(stream)
+        st.eager(dL, e_ev[k], stream)
+        if dist:
+            pass  # the eager comparison leaves the gradients per rank
     torch.cuda.synchronize()
     assert gs.gs_sync_status() == gs.GS_OK
-    eager_ms = statistics.mean(a.elapsed_time(b) for a, b in e_ev)
+    eager_ms = statistics.mean(e[0].elapsed_time(e[4]) for e in e_ev)
 
-    # ---- the same step with opacity-aware tile lists (same image; fewer instances)
-    for _ in range(3):
-        step(tight=True)
-    _, tbs, tfwd, _ = step(tight=True)
-    t_inst = int(t_count.item())
-    t_evals = 2 * int(tfwd["n_contrib"].sum().item())
-    Kt = min(K, 200)
-    t_ev = [tuple(E() for _ in range(5)) for _ in range(Kt)]
-    for k in range(Kt):
-        flush.zero_()
-        step(t_ev[k], tight=True)
-    torch.cuda.synchronize()
-    assert gs.gs_sync_status() == gs.GS_OK
-    t_ms = statistics.mean(e[0].elapsed_time(e[4]) for e in t_ev)
-    tight_line = {"ms_per_step": round(t_ms, 5), "instances": t_inst, "evals_per_step": t_evals,
-                  "breakdown_ms": {"project": round(statistics.mean(e[0].elapsed_time(e[1]) for e in t_ev), 5),
-                                   "bin_sort": round(statistics.mean(e[1].elapsed_time(e[2]) for e in t_ev), 5),
-                                   "blend_forward": round(statistics.mean(e[2].elapsed_time(e[3]) for e in t_ev), 5),
-                                   "blend_backward": round(statistics.mean(e[3].elapsed_time(e[4]) for e in t_ev), 5)},
-                  "steps": Kt, "note": "gs_bin_sort_views with conic + gs_alpha_power_min: a splat keeps a tile "
-                                       "only if alpha can reach 1/255 there; the image equals the full lists' "}
-
-    # ---- issued pairs: every chunk a tile evaluates before its exit, at all 256 pixels
-    issued_line = None
+    # ---- issued pairs: the chunks the tensor-core forward evaluates before a tile's exit
+    issued_fwd = evals_fwd
     if args.variant != "fp32":
         cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
-        o_cnt = gs.make_opts(args.variant, chunk=opts.chunk, stages=opts.stages, tile_order=order, issued_pairs=cnt)
-        out_c = gs.blend_forward(W, H, bs, proj, dev["opacities"], o_cnt)
-        issued = int(cnt.item())
-        assert gs.gs_sync_status() == gs.GS_OK and torch.equal(out_c["n_contrib"], fwd["n_contrib"])
-        issued_line = {"evaluated_per_frame": evals_fwd, "issued_per_frame": issued,
-                       "issued_over_evaluated": round(issued / max(evals_fwd, 1), 3),
-                       "note": "evaluated = sum of n_contrib (the metric's pairs); issued = 256 x the splats of "
-                               "every chunk the tensor-core forward evaluates before a tile's exit"}
+        o_cnt = gs.make_opts(args.variant, chunk=st.opts.chunk, stages=st.opts.stages, tile_order=st.order,
+                             issued_pairs=cnt, shard_count=ws_n, shard_index=rank)
+        out_c = st.forward(opts=o_cnt)
+        issued_fwd = int(cnt.item())
+        assert gs.gs_sync_status() == gs.GS_OK and torch.equal(out_c["n_contrib"], g_fwd["n_contrib"])
+        st.forward()
+    issued_bwd = backward_issued_pairs(torch, g_fwd["n_contrib"]) if args.variant != "fp32" else evals_fwd
 
-    # ---- projection backward: dL/d(means, scales, quats, sh) from the blend's
-    # splat gradients (HBM-bound, one thread per Gaussian)
-    pproj, _, _, gb = step()
-    pb_args = (dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam, pproj["radius"],
-               gb["mean2d"], gb["conic"], gb["rgb"])
-    for _ in range(3):
-        gs.project_backward(*pb_args)
-    pb_ev = []
-    for _ in range(min(K, 200)):
-        flush.zero_()
-        a, b = E(), E()
-        a.record(stream)
-        gs.project_backward(*pb_args)
-        b.record(stream)
-        pb_ev.append((a, b))
-    torch.cuda.synchronize()
-    assert gs.gs_sync_status() == gs.GS_OK
-    pb_ms = statistics.median(a.elapsed_time(b) for a, b in pb_ev)
-    Ksh = (sc.sh_degree + 1) ** 2
-    # per Gaussian: means, scales, quats, sh, radius, dmean2d, dconic, drgb read; dmeans, dscales, dquats, dsh written
-    pb_bytes = n * (4 * (3 + 3 + 4 + 3 * Ksh + 1 + 2 + 3 + 3) + 4 * (3 + 3 + 4 + 3 * Ksh))
-    hbm = read_hbm_peak()
-    pb_line = {"ms": round(pb_ms, 5), "bytes_per_gaussian": pb_bytes // n,
-               "achieved_gb_per_s": round(pb_bytes / pb_ms / 1e6, 1),
-               "peak_gb_per_s": hbm, "frac": round(pb_bytes / pb_ms / 1e6 / hbm, 4) if hbm else None,
-               "note": "gs_project_backward alone (k_project_bwd), L2 flushed before each launch, median of "
-                       f"{len(pb_ev)}; peak = measured copy bandwidth"}
+    # ---- the forward's splat staging: TMA gathers of packed records against per-thread loads
+    producer = None
+    if args.variant != "fp32" and st.rec is not None:
+        gs.pack_splats(st.proj, dev["opacities"], out=st.rec)
+        o_tma = gs.make_opts(args.variant, chunk=st.opts.chunk, stages=st.opts.stages, tile_order=st.order,
+                             shard_count=ws_n, shard_index=rank, splat_records=st.rec)
+        reps = min(max(K, 10), 50)
+        for _ in range(2):
+            st.forward(opts=o_tma)
+        t_tma = _timed(torch, flush, stream, lambda: st.forward(opts=o_tma), reps)
+        t_ldg = _timed(torch, flush, stream, lambda: st.forward(), reps)
+        producer = {"tma_gather4_ms": round(t_tma, 5), "per_thread_loads_ms": round(t_ldg, 5),
+                    "note": "blend forward alone, median of %d, L2 flushed; the step uses per-thread loads, the "
+                            "faster" % reps}
 
-    # ---- small scene: projection + bin/sort fused into one cooperative launch
-    small_line = run_small_fused(gs, torch, gs.make_opts(args.variant), flush, min(K, 200))
-    # ---- all cameras of the ring scene in one batched step (one launch per stage over every view)
+    # ---- rooflines: the library's own MUFU / FMA microbenchmark, the measured HBM and tensor peaks
+    mp = gs.gs_measure_peaks()
+    f_ms, b_ms = statistics.mean(fwd_ms), statistics.mean(bwd_ms)
+    p_ms, s_ms = statistics.mean(proj_ms), statistics.mean(sort_ms)
+    rf = blend_roofline("forward", args.variant, f_ms, evals_fwd, issued_fwd, W * H, mp)
+    rb = blend_roofline("backward", args.variant, b_ms, evals_fwd, issued_bwd, W * H, mp)
+    hbm = read_peaks().get("hbm_gbs")
+    sort_bytes = 32 * n + 4 * n_inst + 8 * gs.num_tiles(W, H)
+    stages = {"project": p_ms, "bin_sort": s_ms, "blend_forward": f_ms, "blend_backward": b_ms}
+    dominant = max(stages, key=stages.get)
+    if dominant == "bin_sort":
+        achieved = sort_bytes / (s_ms / 1e3) / 1e9
+        tr = KNOWN_TRAFFIC.get("bin_sort")
+        roofline = {"bound": "hbm", "kernel": "bin/sort stage (gs_alpha_power_min + gs_bin_sort_views + "
+                                              "gs_tile_order, one CUDA graph)",
+                    "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(achieved / hbm, 4) if hbm else None,
+                    "traffic": tr["bytes"] if tr and tr["config"] == args.config else None,
+                    "algorithmic_bytes": sort_bytes, "launch_ms": round(s_ms, 5),
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, burst) of measured",
+                    "note": "algorithmic bytes: 32 per Gaussian (inputs), 4 per instance (the sorted id), 8 per tile "
+                            "(range): the least a binning moves"}
+    else:
+        r = rf if dominant == "blend_forward" else rb
+        b = r["terms_g_evals_per_s"][r["bound"]]
+        roofline = {"bound": "alu" if r["bound"] in ("mufu", "fp32_issue") else r["bound"], "kernel": r["kernel"],
+                    "achieved": r["achieved_g_evals_per_s"], "peak": b["per_s"], "unit": "G evals/s",
+                    "frac": r["frac_of_bound"], "traffic": None, "launch_ms": r["launch_ms"],
+                    "peak_source": b["note"] + " (measured on this GPU)"}
+    roofline["stage_ms"] = {k: round(v, 5) for k, v in stages.items()}
+
+    # ---- blend-only ms/frame per variant, TC vs FP32 CUDA core, and the 1920x1080 workload
+    sweep, sweep_c2 = None, None
+    if not args.quick:
+        reps = min(max(K, 10), 30)
+        sweep = variant_sweep(gs, torch, st, dL, flush, stream, reps,
+                              ["fp32", "fp16", "bf16", "fp16_split", "bf16_split", "fp8_split"])
+        if args.config == 4 and ws_n == 1:
+            sweep_c2 = run_config2(gs, torch, scenes, flush, stream, reps, args.variant)
+
+    # ---- projection backward (§8(f) row 1) and the small-scene fused front end (row 4)
+    pb_line = run_project_backward(gs, torch, dev, sc, cam, st, g_eager, flush, stream, min(K, 100))
+    small_line = run_small_fused(gs, torch, gs.make_opts(args.variant), flush, min(K, 100))
     batched_line = run_batched(gs, torch, sc, dev, args.variant, flush, min(K, 50)) if args.config == 3 else None
 
-    # ---- blend-only ms/frame per variant (forward), tensor core vs FP32 CUDA core
-    blend = {}
-    if not args.quick:
-        for name in ["fp32", "fp16", "bf16", "fp16_split", "bf16_split", "fp8_split"]:
-            o = gs.make_opts(name, tile_order=order)  # the main step's lists and order
-            for _ in range(3):
-                gs.blend_forward(W, H, bs, proj, dev["opacities"], o)
-            times = []
-            for _ in range(min(max(K, 10), 50)):
-                flush.zero_()
-                a, b = E(), E()
-                a.record(stream)
-                out = gs.blend_forward(W, H, bs, proj, dev["opacities"], o)
-                b.record(stream)
-                times.append((a, b))
-            torch.cuda.synchronize()
-            ms = statistics.median(a.elapsed_time(b) for a, b in times)
-            ev = int(out["n_contrib"].sum().item())
-            blend[name] = {"ms_per_frame": round(ms, 5), "evals_per_s": ev / (ms / 1e3)}
-        # backward (FP32 CUDA-core recompute) alone
-        times = []
-        for _ in range(min(max(K, 10), 50)):
-            flush.zero_()
-            a, b = E(), E()
-            a.record(stream)
-            gs.blend_backward(W, H, bs, proj, dev["opacities"], fp32, fwd, dL)
-            b.record(stream)
-            times.append((a, b))
-        torch.cuda.synchronize()
-        ms = statistics.median(a.elapsed_time(b) for a, b in times)
-        blend["backward_fp32"] = {"ms_per_frame": round(ms, 5), "evals_per_s": evals_fwd / (ms / 1e3)}
-
     # ---- end to end through the public API with host buffers
-    e2e = run_e2e(args, gs, torch, sc, cam, opts, capacity, dL, flush, evals_step, ws_n, dist)
-
-    # ---- roofline of the dominant blend kernel (MUFU-bound: the forward pass
-    # takes one exp2 per evaluated pair, the backward pass an exp2 and a reciprocal)
-    # MUFU rates measured on this GPU by the library's own microbenchmark
-    mp = gs.gs_measure_peaks()
-    ex2_g, rcp_g = mp["ex2_per_s"] / 1e9, mp["rcp_per_s"] / 1e9
-    f_ms, b_ms = statistics.mean(fwd_ms), statistics.mean(bwd_ms)
-    tc = args.variant != "fp32"
-    if f_ms >= b_ms:
-        kern, t_ms, per_pair = (f"k_blend_tc<{args.variant}>" if tc else "k_blend_fp32_fwd"), f_ms, 1
-        src = ("blend_tc.cuh",) if tc else ("blend_fp32.cu",)
-    else:
-        kern, t_ms, per_pair = (f"k_blend_tc_bwd<{args.variant}>" if tc else "k_blend_fp32_bwd"), b_ms, 2
-        src = ("blend_tc_bwd.cuh", "blend_tc.cuh") if tc else ("blend_fp32.cu",)
-    achieved = evals_fwd / (t_ms / 1e3) / 1e9
-    # pairs/s if MUFU were the only limit: an ex2 per pair, plus a reciprocal in the backward pass
-    peak = ex2_g if per_pair == 1 else 1.0 / (1.0 / ex2_g + 1.0 / rcp_g)
-    tr = KNOWN_TRAFFIC.get(kern)
-    traffic = tr["bytes"] if tr and tr["src"] == source_digest(*src) and tr["config"] == args.config else None
-    roofline = {"bound": "alu", "kernel": kern, "achieved": round(achieved, 2), "peak": round(peak, 1),
-                "unit": "G evals/s (MUFU-bound)", "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_source": f"gs_measure_peaks on this GPU: {ex2_g:.0f} G ex2/s, {rcp_g:.0f} G rcp/s at "
-                               f"{mp['sm_mhz']:.0f} MHz ({mp['sms']} SMs); "
-                               + ("1 ex2 per pair" if per_pair == 1 else "1 ex2 + 1 rcp per pair"),
-                "launch_ms": round(t_ms, 5)}
+    e2e = run_e2e(args, gs, torch, sc, cam, st.opts, st.capacity, dL, flush, evals_step, ws_n, dist, tight)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_n, "steps": K, "warmup": args.warmup,
-        "ms_per_step": dev_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
+        "ms_per_step": dev_ms / K, "higher_is_better": True, "scaling": "strong" if ws_n > 1 else "weak",
+        "vs_baseline": None, "dtype": DTYPE_OF.get(args.variant, args.variant), "data": "synthetic",
         "config": {"workload": WORKLOADS[args.config] + WORKLOAD_NOTE, "blend_variant": args.variant,
                    "step": "project + bin_sort + tile_order + blend_forward + blend_backward",
+                   "lists": "opacity-aware (gs_alpha_power_min + conics): a splat keeps a tile only if alpha can "
+                            "reach 1/255 there; same image as the full 3-sigma rectangles" if tight
+                            else "full 3-sigma rectangles",
                    "tile_order": "longest list first (gs_tile_order)",
                    "blend_shape": tuned or "per-tile FP32 blocks",
                    "evals_per_step": evals_step, "instances": n_inst, "pixels": W * H,
-                   "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replica x{ws_n}",
+                   "l2": "flushed before every timed step (256 MB write)",
+                   "parallelism": f"tile shards x{ws_n} + NCCL all-reduce of the gradients" if ws_n > 1 else "1 GPU",
                    "bin_sort": "no host synchronisation (fixed capacity, count on the device)",
                    "launch": "each stage (project; bin_sort + tile_order; forward; backward) replayed as a CUDA "
                              "graph, CUDA events between the stages"},
-        "breakdown_ms": {"project": round(statistics.mean(proj_ms), 5), "bin_sort": round(statistics.mean(sort_ms), 5),
-                         "blend_forward": round(f_ms, 5), "blend_backward": round(b_ms, 5),
-                         "gaps": round(dev_ms / K - f_ms - b_ms - statistics.mean(proj_ms)
-                                       - statistics.mean(sort_ms), 5)},
+        "breakdown_ms": {k: round(v, 5) for k, v in stages.items()},
         "wall_ms_per_step": wall * 1e3 / K,
         "eager_ms_per_step": round(eager_ms, 5),
         "launches_per_step": launches_per_step,
-        "blend_forward_by_variant": blend,
         "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
-        "opacity_aware_lists": tight_line,
+        "blend_rooflines": {"forward": rf, "backward": rb},
+        **({"forward_splat_staging": producer} if producer else {}),
+        **({"sustained": sus} if sus else {}),
+        **({"blend_by_variant": sweep} if sweep else {}),
+        **({"workload_1920x1080": sweep_c2} if sweep_c2 else {}),
+        "forward_pairs": {"evaluated_per_frame": evals_fwd, "issued_per_frame": issued_fwd,
+                          "backward_issued_per_frame": issued_bwd,
+                          "note": "evaluated = sum of n_contrib (the metric's pairs); issued = 256 x the splats of "
+                                  "every chunk the tensor-core kernels evaluate before a tile's exit"},
         "projection_backward": pb_line,
-        **({"forward_pairs": issued_line} if issued_line else {}),
         "small_scene_fused": small_line,
         **({"batched_views": batched_line} if batched_line else {}),
     }
+    if ws_n > 1:
+        line["all_reduce_bytes_per_step"] = int(g_grad["mean2d"]._base.numel() * 4)
     if rank == 0 and ws_n == 1 and not args.no_cpu_baseline:  # the oracle on the host cores: N = 1 only
-        line["cpu_baseline"] = cpu_baseline(cam, proj, bs, sc, dL, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(cam, st.proj, st.bs, sc, dL, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def run_project_backward(gs, torch, dev, sc, cam, st, g, flush, stream, K):
+    """dL/d(means, scales, quats, sh) from the blend's splat gradients alone
+    (k_project_bwd: HBM-bound, one thread per Gaussian)."""
+    args_ = (dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam, st.proj["radius"],
+             g["mean2d"], g["conic"], g["rgb"])
+    for _ in range(3):
+        gs.project_backward(*args_)
+    ms = _timed(torch, flush, stream, lambda: gs.project_backward(*args_), K)
+    assert gs.gs_sync_status() == gs.GS_OK
+    n = sc.n
+    Ksh = (sc.sh_degree + 1) ** 2
+    # per Gaussian: means, scales, quats, sh, radius, dmean2d, dconic, drgb read; dmeans, dscales, dquats, dsh written
+    b = n * (4 * (3 + 3 + 4 + 3 * Ksh + 1 + 2 + 3 + 3) + 4 * (3 + 3 + 4 + 3 * Ksh))
+    hbm = read_hbm_peak()
+    return {"ms": round(ms, 5), "bytes_per_gaussian": b // n, "achieved_gb_per_s": round(b / ms / 1e6, 1),
+            "peak_gb_per_s": hbm, "frac": round(b / ms / 1e6 / hbm, 4) if hbm else None,
+            "note": f"gs_project_backward alone (k_project_bwd), L2 flushed before each launch, median of {K}; "
+                    "peak = measured copy bandwidth"}
+
+
+def run_config2(gs, torch, scenes, flush, stream, reps, variant):
+    """The 1920x1080, 1M clustered-Gaussian workload (full 3-sigma lists, as
+    its description states): the step time and every variant's blend."""
+    sc = scenes.make_config(2, seed=0)
+    cam = sc.cameras[0]
+    dev = gs.scene_to_device(sc)
+    dL = torch.from_numpy(scenes.upstream_grad(0, [cam])[0]).cuda()
+    st = Step(gs, torch, dev, cam, variant, tight=False)
+    for _ in range(3):
+        st.eager(dL)
+    ev = [_events(torch, 5) for _ in range(reps)]
+    for e in ev:
+        flush.zero_()
+        st.eager(dL, e, stream)
+    torch.cuda.synchronize()
+    assert gs.gs_sync_status() == gs.GS_OK
+    out = {"workload": WORKLOADS[2] + WORKLOAD_NOTE, "lists": "full 3-sigma rectangles", "instances": st.count0,
+           "step_ms_eager": round(statistics.median(e[0].elapsed_time(e[4]) for e in ev), 5),
+           "evals_per_frame": int(st.fwd["n_contrib"].sum().item())}
+    out["blend_by_variant"] = variant_sweep(gs, torch, st, dL, flush, stream, reps,
+                                            ["fp32", "bf16", "fp16_split", "bf16_split", "fp8_split"])
+    del st
+    return out
 
 
 def run_small_fused(gs, torch, opts, flush, K):
@@ -631,7 +807,7 @@ def run_batched(gs, torch, sc, dev, variant, flush, K):
                     "gs_project + gs_bin_sort (synchronising) + blend forward + backward; L2 flushed before each"}
 
 
-def run_e2e(args, gs, torch, sc, cam, opts, capacity, dL, flush, evals_step, ws, dist):
+def run_e2e(args, gs, torch, sc, cam, opts, capacity, dL, flush, evals_step, ws, dist, tight=False):
     """Same step through the public API from pinned host buffers: every step
     copies the scene host-to-device and the image and the four gradient
     arrays device-to-host.  Timed twice: serialised (BatchRenderer: copy in,
@@ -671,7 +847,7 @@ def run_e2e(args, gs, torch, sc, cam, opts, capacity, dL, flush, evals_step, ws,
 
     # serialised
     devb = {k: v.to("cuda") for k, v in host.items()}
-    br = gs.BatchRenderer(dict(devb, sh_degree=sc.sh_degree), [cam], opts, capacity)
+    br = gs.BatchRenderer(dict(devb, sh_degree=sc.sh_degree), [cam], opts, capacity, opacity_aware=tight)
     br.dL.copy_(dL.reshape(-1))
     br.capture()  # the step replayed as one CUDA graph
 
@@ -688,7 +864,7 @@ def run_e2e(args, gs, torch, sc, cam, opts, capacity, dL, flush, evals_step, ws,
     t_serial = timed(step_serial)
     del br, devb
     # pipelined
-    pr = gs.PipelinedRenderer(host, sc.sh_degree, [cam], opts, capacity, dL, graphs=True)
+    pr = gs.PipelinedRenderer(host, sc.sh_degree, [cam], opts, capacity, dL, graphs=True, opacity_aware=tight)
     t = timed(lambda k: pr.submit(k, host, out_h))
     K = args.steps
     return {"value": ws * evals_step * K / t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -768,11 +944,26 @@ def run_reference(args):
     sc = scenes.make_config(args.config, seed=0)
     cam = sc.cameras[0]
     W, H = cam.width, cam.height
+    threads = os.cpu_count() or 1
     pr = oracle.project(sc.means, sc.scales, sc.quats, sc.sh, sc.sh_degree, cam)
-    bs = oracle.bin_sort(pr["mean2d"], pr["radius"], pr["depth"].astype(np.float32), W, H)
+    d32 = pr["depth"].astype(np.float32)
+    tight = not args.full_lists
+    # the opacity-aware lists of the GPU arm, from the oracle's FP64 definition
+    kw = {}
+    if tight:
+        o = sc.opacities.astype(np.float64)
+        keep = sc.opacities >= np.float32(1.0) / np.float32(255.0)
+        kw = dict(conic=pr["conic"].astype(np.float32),
+                  power_min=np.where(keep, -np.log(255 * o) - 2e-3, np.inf).astype(np.float32))
+    # a large image gets lists for a random tile sample only (the timed steps visit no other tile)
+    ntiles = cam.num_tiles
+    mask = None
+    if ntiles > 8192:
+        mask = np.zeros(ntiles, bool)
+        mask[np.random.default_rng(0).choice(ntiles, size=4096, replace=False)] = True
+    bs = oracle.bin_sort(pr["mean2d"], pr["radius"], d32, W, H, tile_mask=mask, **kw)
     dL = scenes.upstream_grad(0, [cam])[0].astype(np.float64)
     op = sc.opacities.astype(np.float64)
-    threads = os.cpu_count() or 1
     busy = _busy_tiles(bs["tile_ranges"])
     order = np.random.default_rng(0).permutation(busy)
     per_step_s = min(6.0, 150.0 / max(1, args.steps + args.warmup))
@@ -787,7 +978,9 @@ def run_reference(args):
             evals_total += ev
             t_total += dt
     value = evals_total / t_total
-    sample = f"{k} of {len(busy)} non-empty tiles per step (rotating), FP64 blend forward + gradient"
+    pool = f"{len(busy)} non-empty tiles" + (f" of a random sample of 4096 of {ntiles}" if mask is not None else "")
+    sample = (f"{k} of {pool} per step (rotating), FP64 blend forward + gradient over "
+              + ("opacity-aware lists (FP64 definition)" if tight else "full 3-sigma lists"))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_total * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
