@@ -361,21 +361,43 @@ def variant_sweep(gs, torch, st, dL, flush, stream, reps, variants):
     out = {}
     for name in variants:
         o = gs.make_opts(name, tile_order=st.order)
+        fwd = st.forward(opts=o)
+        bwd_ok = name != "fp32_persistent"  # forward only
+        if name != "fp32":  # each variant's pipeline shapes by the library's own measurement
+            gs.gs_blend_autotune([st.W], [st.H], st.n, st.ranges, st.ids, st.proj["mean2d"], st.proj["conic"],
+                                 st.dev["opacities"], st.proj["rgb"], o, fwd["image"], fwd["T_final"],
+                                 fwd["n_contrib"], reps=3)
+            fwd = st.forward(opts=o)
+            if bwd_ok:
+                scratch = {k: torch.empty(st.n * c, device="cuda") for k, c in (("mean2d", 2), ("conic", 3),
+                                                                                  ("opacity", 1), ("rgb", 3))}
+                gs.gs_blend_autotune_backward([st.W], [st.H], st.n, st.ranges, st.ids, st.proj["mean2d"],
+                                              st.proj["conic"], st.dev["opacities"], st.proj["rgb"], o,
+                                              fwd["T_final"], fwd["n_contrib"], dL, scratch, reps=3)
+                del scratch
         for _ in range(2):
             fwd = st.forward(opts=o)
-            st.backward(dL, fwd=fwd, opts=o)
+            if bwd_ok:
+                st.backward(dL, fwd=fwd, opts=o)
         f_ms = _timed(torch, flush, stream, lambda: st.forward(opts=o), reps)
         fwd = st.forward(opts=o)
-        b_ms = _timed(torch, flush, stream, lambda: st.backward(dL, fwd=fwd, opts=o), reps)
+        b_ms = _timed(torch, flush, stream, lambda: st.backward(dL, fwd=fwd, opts=o), reps) if bwd_ok else None
         torch.cuda.synchronize()
         ev = int(fwd["n_contrib"].sum().item())
-        out[name] = {"forward_ms": round(f_ms, 5), "backward_ms": round(b_ms, 5),
-                     "forward_evals_per_s": ev / (f_ms / 1e3), "backward_evals_per_s": ev / (b_ms / 1e3)}
+        out[name] = {"forward_ms": round(f_ms, 5), "backward_ms": round(b_ms, 5) if b_ms else None,
+                     "shape": None if name == "fp32" else {"chunk": o.chunk, "stages": o.stages,
+                                                           "bwd_stages": o.bwd_stages},
+                     "forward_evals_per_s": ev / (f_ms / 1e3),
+                     "backward_evals_per_s": ev / (b_ms / 1e3) if b_ms else None}
     assert gs.gs_sync_status() == gs.GS_OK
     if "fp32" in out:
         for name, v in out.items():
             v["forward_speedup_vs_fp32"] = round(out["fp32"]["forward_ms"] / v["forward_ms"], 3)
-            v["backward_speedup_vs_fp32"] = round(out["fp32"]["backward_ms"] / v["backward_ms"], 3)
+            if v["backward_ms"]:
+                v["backward_speedup_vs_fp32"] = round(out["fp32"]["backward_ms"] / v["backward_ms"], 3)
+    if "fp32_persistent" in out:  # the tensor cores against CUDA cores inside the same kernel
+        for name, v in out.items():
+            v["forward_speedup_vs_persistent_fp32"] = round(out["fp32_persistent"]["forward_ms"] / v["forward_ms"], 3)
     return out
 
 
@@ -407,10 +429,16 @@ def run_ours(args):
     torch.cuda.synchronize()
     assert gs.gs_sync_status() == gs.GS_OK
     tuned = None
-    if args.variant != "fp32":  # the forward's pipeline shape by the library's own measurement
+    if args.variant != "fp32":  # the pipeline shapes by the library's own measurement
         gs.gs_blend_autotune([W], [H], n, st.ranges, st.ids, st.proj["mean2d"], st.proj["conic"], dev["opacities"],
                              st.proj["rgb"], st.opts, st.fwd["image"], st.fwd["T_final"], st.fwd["n_contrib"])
-        tuned = {"chunk": st.opts.chunk, "stages": st.opts.stages}
+        scratch = {k: torch.empty(n * c, device="cuda") for k, c in (("mean2d", 2), ("conic", 3), ("opacity", 1),
+                                                                       ("rgb", 3))}
+        gs.gs_blend_autotune_backward([W], [H], n, st.ranges, st.ids, st.proj["mean2d"], st.proj["conic"],
+                                      dev["opacities"], st.proj["rgb"], st.opts, st.fwd["T_final"],
+                                      st.fwd["n_contrib"], dL, scratch)
+        del scratch
+        tuned = {"chunk": st.opts.chunk, "stages": st.opts.stages, "bwd_stages": st.opts.bwd_stages}
     g_eager = st.eager(dL)
     torch.cuda.synchronize()
     evals_fwd = int(st.fwd["n_contrib"].sum().item())
@@ -571,13 +599,14 @@ def run_ours(args):
     roofline["stage_ms"] = {k: round(v, 5) for k, v in stages.items()}
 
     # ---- blend-only ms/frame per variant, TC vs FP32 CUDA core, and the 1920x1080 workload
-    sweep, sweep_c2 = None, None
+    sweep, sweep_c2, sweep_c1 = None, None, None
     if not args.quick:
         reps = min(max(K, 10), 30)
         sweep = variant_sweep(gs, torch, st, dL, flush, stream, reps,
-                              ["fp32", "fp16", "bf16", "fp16_split", "bf16_split", "fp8_split"])
+                              ["fp32", "fp32_persistent", "fp16", "bf16", "fp16_split", "bf16_split", "fp8_split"])
         if args.config == 4 and ws_n == 1:
             sweep_c2 = run_config2(gs, torch, scenes, flush, stream, reps, args.variant)
+            sweep_c1 = run_config1(gs, torch, scenes, flush, stream, reps)
 
     # ---- projection backward (§8(f) row 1) and the small-scene fused front end (row 4)
     pb_line = run_project_backward(gs, torch, dev, sc, cam, st, g_eager, flush, stream, min(K, 100))
@@ -614,6 +643,7 @@ def run_ours(args):
         **({"sustained": sus} if sus else {}),
         **({"blend_by_variant": sweep} if sweep else {}),
         **({"workload_1920x1080": sweep_c2} if sweep_c2 else {}),
+        **({"workload_1280x720": sweep_c1} if sweep_c1 else {}),
         "forward_pairs": {"evaluated_per_frame": evals_fwd, "issued_per_frame": issued_fwd,
                           "backward_issued_per_frame": issued_bwd,
                           "note": "evaluated = sum of n_contrib (the metric's pairs); issued = 256 x the splats of "
@@ -672,7 +702,28 @@ def run_config2(gs, torch, scenes, flush, stream, reps, variant):
            "step_ms_eager": round(statistics.median(e[0].elapsed_time(e[4]) for e in ev), 5),
            "evals_per_frame": int(st.fwd["n_contrib"].sum().item())}
     out["blend_by_variant"] = variant_sweep(gs, torch, st, dL, flush, stream, reps,
-                                            ["fp32", "bf16", "fp16_split", "bf16_split", "fp8_split"])
+                                            ["fp32", "fp32_persistent", "bf16", "fp16_split", "bf16_split",
+                                             "fp8_split"])
+    del st
+    return out
+
+
+def run_config1(gs, torch, scenes, flush, stream, reps):
+    """The 1280x720, 200k-Gaussian workload (full 3-sigma lists): every
+    variant's blend, FP32 Alg. 1 and the persistent kernel on CUDA cores
+    beside the tensor-core variants."""
+    sc = scenes.make_config(1, seed=0)
+    cam = sc.cameras[0]
+    dev = gs.scene_to_device(sc)
+    dL = torch.from_numpy(scenes.upstream_grad(0, [cam])[0]).cuda()
+    st = Step(gs, torch, dev, cam, "bf16_split", tight=False)
+    for _ in range(3):
+        st.eager(dL)
+    torch.cuda.synchronize()
+    out = {"workload": WORKLOADS[1] + WORKLOAD_NOTE, "lists": "full 3-sigma rectangles", "instances": st.count0,
+           "evals_per_frame": int(st.fwd["n_contrib"].sum().item())}
+    out["blend_by_variant"] = variant_sweep(gs, torch, st, dL, flush, stream, reps,
+                                            ["fp32", "fp32_persistent", "fp16_split", "bf16_split"])
     del st
     return out
 

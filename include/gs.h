@@ -76,14 +76,20 @@ typedef struct gs_camera {
  * the given operand type and FP32 accumulation.  _SPLIT variants store v_g as
  * an unevaluated sum of 2 (fp16) or 3 (bf16) operand-type terms.  FP8_SPLIT
  * (a precision trial) uses e4m3 operands: every v_g row scaled by a power of
- * two and split into 5 terms, the pixel monomials into 2 exact terms. */
+ * two and split into 5 terms, the pixel monomials into 2 exact terms.
+ * PERSISTENT_FP32 is the TC variants' kernel (persistent tile queue, pixel
+ * pairs, branch-free compositing, the same FP32 v_g rows of Eq. 6) with the
+ * contraction v_g . v_p evaluated by FP32 FMAs on the CUDA cores instead of
+ * tcgen05.mma: it isolates what the tensor cores contribute (forward only;
+ * gs_blend_backward returns GS_ERR_UNSUPPORTED for it). */
 typedef enum gs_variant {
     GS_BLEND_FP32 = 0,
     GS_BLEND_TC_FP16 = 1,
     GS_BLEND_TC_BF16 = 2,
     GS_BLEND_TC_FP16_SPLIT = 3,
     GS_BLEND_TC_BF16_SPLIT = 4,
-    GS_BLEND_TC_FP8_SPLIT = 5
+    GS_BLEND_TC_FP8_SPLIT = 5,
+    GS_BLEND_PERSISTENT_FP32 = 6
 } gs_variant;
 
 /* Options of the blend calls.  All-zero is valid: FP32 variant, defaults. */
@@ -96,7 +102,9 @@ typedef struct gs_blend_opts {
                             first pixel): 0 = its centre (x0 + 8, y0 + 4),
                             1 = the centre of its first pixel (x0 + 0.5, y0 + 0.5) */
     float bg[3];         /* background colour added as T_final * bg */
-    int32_t reserved;
+    int32_t bwd_stages;  /* TC backward: depth of its shared-memory ring, 0 = the variant's default
+                            (6 for fp16 operands, 2 for bf16 and FP8, the deepest that keeps 3 blocks
+                            per SM); built: 2, 4, 6 (gs_blend_autotune_backward picks one) */
     int64_t timeout_ns;  /* limit of every device-side wait; 0 = 1 s */
     int32_t shard_count; /* tile sharding across ranks: the call blends only the tiles t
                             (global tile ids) with t % shard_count == shard_index and leaves
@@ -443,6 +451,22 @@ gs_status gs_blend_autotune(int32_t n_views, const int32_t* widths, const int32_
                             const float* conic, const float* opacity, const float* rgb, gs_blend_opts* opts,
                             float* image, float* T_final, int32_t* n_contrib, int32_t reps, float* best_ms,
                             gs_stream stream);
+
+/*
+ * gs_blend_autotune_backward - the same for the tensor-core backward pass:
+ * runs gs_blend_backward_views with each built ring depth (bwd_stages 2, 4,
+ * 6), `reps` timed calls each, and sets opts->bwd_stages to the fastest
+ * (not in the paper: its batch-size study, Sec. 4.4, picks the mini-batch
+ * shape by measurement).  Arguments as gs_blend_backward_views; the gradient
+ * buffers are accumulated into many times, so their contents afterwards are
+ * unspecified: zero them before the real call.  Synchronises `stream`.
+ */
+gs_status gs_blend_autotune_backward(int32_t n_views, const int32_t* widths, const int32_t* heights,
+                                     int32_t n_per_view, const uint32_t* tile_ranges, const uint32_t* ids_sorted,
+                                     const float* mean2d, const float* conic, const float* opacity, const float* rgb,
+                                     gs_blend_opts* opts, const float* T_final, const int32_t* n_contrib,
+                                     const float* dL_dimage, float* dmean2d, float* dconic, float* dopacity,
+                                     float* drgb, int32_t reps, float* best_ms, gs_stream stream);
 
 /*
  * gs_tile_power - the exponent matrix M_power = M_g . M_p of Eq. 8 exactly as a

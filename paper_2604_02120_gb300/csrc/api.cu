@@ -144,6 +144,8 @@ bool make_args(BlendArgs& a, int32_t n_views, const int32_t* widths, const int32
 }
 
 bool is_tc(int v) { return v >= GS_BLEND_TC_FP16 && v <= GS_BLEND_TC_FP8_SPLIT; }
+// the persistent kernel: the TC variants, and the same kernel with the exponent on CUDA cores
+bool is_persistent(int v) { return is_tc(v) || v == GS_BLEND_PERSISTENT_FP32; }
 
 }  // namespace
 
@@ -432,7 +434,7 @@ gs_status gs_blend_forward_views(int32_t n_views, const int32_t* widths, const i
     a.n_contrib = n_contrib;
     if (!a.err) return cuda_status(cudaGetLastError(), "gs_blend_forward: error word");
     if (o->variant == GS_BLEND_FP32) return cuda_status(launch_blend_fp32_fwd(a, stream), "gs_blend_forward fp32");
-    if (!is_tc(o->variant)) {
+    if (!is_persistent(o->variant)) {
         set_error("gs_blend_forward: unknown variant %d", o->variant);
         return GS_ERR_INVALID_ARG;
     }
@@ -471,6 +473,10 @@ gs_status gs_blend_backward_views(int32_t n_views, const int32_t* widths, const 
     }
     gs_blend_opts def{};
     const gs_blend_opts* o = opts ? opts : &def;
+    if (o->variant == GS_BLEND_PERSISTENT_FP32) {
+        set_error("gs_blend_backward: variant %d is forward only", o->variant);
+        return GS_ERR_UNSUPPORTED;
+    }
     if (o->variant != GS_BLEND_FP32 && !is_tc(o->variant)) {
         set_error("gs_blend_backward: unknown variant %d", o->variant);
         return GS_ERR_INVALID_ARG;
@@ -481,8 +487,13 @@ gs_status gs_blend_backward_views(int32_t n_views, const int32_t* widths, const 
         return GS_ERR_INVALID_ARG;
     }
     GradArgs g{T_final, n_contrib, dL_dimage, reinterpret_cast<float2*>(dmean2d), dconic, dopacity, drgb};
-    if (is_tc(o->variant))
-        return cuda_status(launch_blend_tc_bwd(a, g, o->variant, stream), "gs_blend_backward");
+    if (is_tc(o->variant)) {
+        if (!tc_bwd_stages_supported(o->bwd_stages)) {
+            set_error("gs_blend_backward: bwd_stages %d not built (0, 2, 4, 6)", o->bwd_stages);
+            return GS_ERR_UNSUPPORTED;
+        }
+        return cuda_status(launch_blend_tc_bwd(a, g, o->variant, o->bwd_stages, stream), "gs_blend_backward");
+    }
     return cuda_status(launch_blend_fp32_bwd(a, g, stream), "gs_blend_backward");
 }
 
@@ -501,8 +512,8 @@ gs_status gs_blend_autotune(int32_t n_views, const int32_t* widths, const int32_
                             float* image, float* T_final, int32_t* n_contrib, int32_t reps, float* best_ms,
                             gs_stream stream) {
     g_last_error[0] = 0;
-    if (!opts || !is_tc(opts->variant) || reps < 1) {
-        set_error("gs_blend_autotune: needs a TC variant and reps >= 1");
+    if (!opts || !is_persistent(opts->variant) || reps < 1) {
+        set_error("gs_blend_autotune: needs a TC (or the persistent FP32) variant and reps >= 1");
         return GS_ERR_INVALID_ARG;
     }
     static const int kShapes[][2] = {{32, 2}, {32, 4}, {16, 4}, {16, 6}};
@@ -543,6 +554,54 @@ gs_status gs_blend_autotune(int32_t n_views, const int32_t* widths, const int32_
     }
     opts->chunk = kShapes[best_i][0];
     opts->stages = kShapes[best_i][1];
+    if (best_ms) *best_ms = best;
+    return gs_sync_status(stream);
+}
+
+gs_status gs_blend_autotune_backward(int32_t n_views, const int32_t* widths, const int32_t* heights,
+                                     int32_t n_per_view, const uint32_t* tile_ranges, const uint32_t* ids_sorted,
+                                     const float* mean2d, const float* conic, const float* opacity, const float* rgb,
+                                     gs_blend_opts* opts, const float* T_final, const int32_t* n_contrib,
+                                     const float* dL_dimage, float* dmean2d, float* dconic, float* dopacity,
+                                     float* drgb, int32_t reps, float* best_ms, gs_stream stream) {
+    g_last_error[0] = 0;
+    if (!opts || !is_tc(opts->variant) || reps < 1) {
+        set_error("gs_blend_autotune_backward: needs a TC variant and reps >= 1");
+        return GS_ERR_INVALID_ARG;
+    }
+    static const int kStages[] = {2, 4, 6};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    gs_status st = cuda_status(cudaEventCreate(&e0), "gs_blend_autotune_backward: event");
+    if (st == GS_OK) st = cuda_status(cudaEventCreate(&e1), "gs_blend_autotune_backward: event");
+    float best = 1e30f;
+    int best_i = -1;
+    for (int i = 0; st == GS_OK && i < 3; ++i) {
+        gs_blend_opts o = *opts;
+        o.bwd_stages = kStages[i];
+        auto run = [&]() {
+            return gs_blend_backward_views(n_views, widths, heights, n_per_view, tile_ranges, ids_sorted, mean2d,
+                                           conic, opacity, rgb, &o, T_final, n_contrib, dL_dimage, dmean2d, dconic,
+                                           dopacity, drgb, stream);
+        };
+        if ((st = run()) != GS_OK) break;
+        if ((st = cuda_status(cudaEventRecord(e0, stream), "gs_blend_autotune_backward: record")) != GS_OK) break;
+        for (int r = 0; st == GS_OK && r < reps; ++r) st = run();
+        if (st != GS_OK) break;
+        if ((st = cuda_status(cudaEventRecord(e1, stream), "gs_blend_autotune_backward: record")) != GS_OK) break;
+        if ((st = cuda_status(cudaEventSynchronize(e1), "gs_blend_autotune_backward: synchronize")) != GS_OK) break;
+        float ms = 0.f;
+        if ((st = cuda_status(cudaEventElapsedTime(&ms, e0, e1), "gs_blend_autotune_backward: elapsed")) != GS_OK)
+            break;
+        ms /= (float)reps;
+        if (ms < best) {
+            best = ms;
+            best_i = i;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st != GS_OK) return st;
+    opts->bwd_stages = kStages[best_i];
     if (best_ms) *best_ms = best;
     return gs_sync_status(stream);
 }

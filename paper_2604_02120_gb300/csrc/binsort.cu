@@ -2,13 +2,21 @@
 //
 // The result equals a stable sort of (tile << 32 | depth_bits) keys emitted in
 // Gaussian order, i.e. every tile's list ordered by (depth bits, Gaussian
-// index).  It is produced in two sorts instead of one wide one:
-//   1. stable LSD radix sort of the N Gaussians by depth bits (32-bit keys);
-//   2. duplication in that depth order (one instance per touched tile);
-//   3. stable LSD radix sort of the I instances by tile id alone
-//      (ceil(log2 tiles / 8) passes instead of ceil((32 + log2 tiles) / 8)).
-// Stability of step 3 keeps the depth order (and the index order of equal
-// depths from step 1) inside each tile.
+// index).  It is produced without sorting the instances themselves:
+//   1. per item: its instance count, and the number of supertiles (4 x 4
+//      tiles) holding at least one of its instances;
+//   2. stable LSD radix sort of the N items by depth bits (32-bit keys);
+//   3. coarse duplication in that depth order: one (supertile, item) pair
+//      per supertile the item touches (about an eighth of the instances);
+//   4. stable LSD radix sort of those pairs by supertile id, so each
+//      supertile's items are contiguous and in depth order;
+//   5. one block per supertile counts the instances of each of its 16 tiles,
+//      a scan over the tiles gives every tile's range, and the block walks
+//      its items again writing each instance's id once, at its tile's next
+//      position: a stable per-tile compaction, so every list keeps the depth
+//      (then index) order of step 2.
+// Each instance is written once (4 bytes of id, plus its key if asked for)
+// instead of being duplicated and moved by a radix pass per 8 bits of tile id.
 //
 // Every radix pass is one launch.  The digit histograms of all passes are
 // counted up front by the kernel that produces the keys (the counts of an LSD
@@ -19,9 +27,10 @@
 // published counts until one carries an inclusive prefix.  A block only waits
 // for blocks that started before it, so the waits always end; each is still
 // bounded in time and sets the timeout bit of the error word if it gives up.
-// The scan of instance counts in depth order is done the same way inside the
+// The scan of coarse counts in depth order is done the same way inside the
 // duplication kernel, so the whole stage is
-//   memset, count, 4 depth passes, duplicate, ceil(bits / 8) tile passes, finalize.
+//   memset, count, 4 depth passes, coarse duplicate, ceil(bits / 8) supertile
+//   passes, fine count, tile scan, fine write.
 #include <algorithm>
 
 #include "internal.h"
@@ -361,11 +370,106 @@ __device__ __forceinline__ TightRows item_tight_rows(const SortViews& sv, const 
                       sv.conic[3 * (size_t)item + 2], sv.power_min[g]);
 }
 
-// Per item: its tile count and depth key; the depth keys' four digit
-// histograms (pass ids 0..3).  Also clears the tile ranges and the look-back
-// status words for this call.  Each thread takes ITEMS items, strided by the
-// block size, with all loads issued before any use.  TIGHT: opacity-aware
-// counts, one O(1) run per rectangle row.
+// ------------------------------------------------------------ supertiles --
+//
+// A supertile is 4 x 4 tiles of one view.  Within one supertile row an item's
+// supertiles are the union of [f / 4, l / 4] over the runs [f, l] of its (at
+// most 4) tile rows there: up to 4 intervals, merged after a sorting network
+// on their starts (registers only).  Every supertile counted holds at least
+// one of the item's instances.
+constexpr int kSuper = 4;
+
+struct Iv {
+    int lo, hi;  // empty: lo > hi (lo = INT_MAX sorts last)
+};
+__device__ __forceinline__ void iv_swap(Iv& a, Iv& b) {
+    if (b.lo < a.lo) {
+        const Iv t = a;
+        a = b;
+        b = t;
+    }
+}
+// emit(lo, hi) for each maximal interval of the union; returns its size
+template <class F>
+__device__ __forceinline__ int iv_union4(Iv a, Iv b, Iv c, Iv d, F emit) {
+    iv_swap(a, b);
+    iv_swap(c, d);
+    iv_swap(a, c);
+    iv_swap(b, d);
+    iv_swap(b, c);
+    if (a.lo > a.hi) return 0;
+    int n = 0, clo = a.lo, chi = a.hi;
+    auto step = [&](const Iv& x) {
+        if (x.lo > x.hi) return;
+        if (x.lo <= chi + 1) {
+            chi = max(chi, x.hi);
+        } else {
+            emit(clo, chi);
+            n += chi - clo + 1;
+            clo = x.lo;
+            chi = x.hi;
+        }
+    };
+    step(b);
+    step(c);
+    step(d);
+    emit(clo, chi);
+    return n + chi - clo + 1;
+}
+
+// The item's supertile columns in supertile row sy (emit per interval; the
+// count is returned) and, in *fine, its instances in those tile rows.
+template <bool TIGHT, class F>
+__device__ __forceinline__ int supertile_row(const TightRows& t, int sy, int x0, int x1, int y0, int y1,
+                                             uint32_t* fine, F emit) {
+    if constexpr (!TIGHT) {
+        const int rows = min(y1, sy * kSuper + kSuper - 1) - max(y0, sy * kSuper) + 1;
+        *fine += (uint32_t)(rows * (x1 - x0 + 1));
+        emit(x0 / kSuper, x1 / kSuper);
+        return x1 / kSuper - x0 / kSuper + 1;
+    } else {
+        Iv r[kSuper];
+#pragma unroll
+        for (int k = 0; k < kSuper; ++k) {
+            r[k] = Iv{0x7fffffff, -1};
+            const int y = sy * kSuper + k;
+            if (y >= y0 && y <= y1) {
+                int f, l;
+                tight_row(t, y, x0, x1, f, l);
+                if (f <= l) {
+                    *fine += (uint32_t)(l - f + 1);
+                    r[k] = Iv{f / kSuper, l / kSuper};
+                }
+            }
+        }
+        return iv_union4(r[0], r[1], r[2], r[3], emit);
+    }
+}
+
+__device__ __forceinline__ TightRows shfl_rows(const TightRows& t, int src) {
+    TightRows b;
+    b.mode = __shfl_sync(0xffffffffu, t.mode, src);
+    b.mx = __shfl_sync(0xffffffffu, t.mx, src);
+    b.my = __shfl_sync(0xffffffffu, t.my, src);
+    b.nB = __shfl_sync(0xffffffffu, t.nB, src);
+    b.det = __shfl_sync(0xffffffffu, t.det, src);
+    b.Atau = __shfl_sync(0xffffffffu, t.Atau, src);
+    b.rA = __shfl_sync(0xffffffffu, t.rA, src);
+    b.ymax = __shfl_sync(0xffffffffu, t.ymax, src);
+    b.dyr = __shfl_sync(0xffffffffu, t.dyr, src);
+    return b;
+}
+
+// An item spanning more supertile rows than this is counted and duplicated
+// by a whole warp, one supertile row per lane.
+constexpr int kTallRows = 4;
+
+// Per item: its supertile count (cnt) and depth key; the depth keys' four
+// digit histograms (pass ids 0..3); the sum of all items' instance counts
+// (fine_total).  Also clears the tile ranges and the look-back status words
+// for this call.  Each thread takes ITEMS items, strided by the block size,
+// with all loads issued before any use.  TIGHT: opacity-aware membership,
+// one O(1) run per rectangle row.
 constexpr int kCountItems = 4, kCountItemsTight = 2;
 template <bool TIGHT, int ITEMS>
 __global__ void __launch_bounds__(kThreads) k_count(int n_items, const __grid_constant__ SortViews sv,
@@ -373,10 +477,13 @@ __global__ void __launch_bounds__(kThreads) k_count(int n_items, const __grid_co
                                                     const int* __restrict__ radius, const float* __restrict__ depth,
                                                     uint32_t* __restrict__ cnt, uint32_t* __restrict__ dkey,
                                                     uint32_t* __restrict__ dval, uint32_t* __restrict__ hist,
+                                                    unsigned long long* __restrict__ fine_total,
                                                     uint4* __restrict__ clear, size_t clear_n,
                                                     uint32_t* __restrict__ ranges, size_t ranges_n) {
     __shared__ uint32_t s_h[4 * 256];
+    __shared__ unsigned long long s_fine;
     for (int i = threadIdx.x; i < 4 * 256; i += kThreads) s_h[i] = 0;
+    if (threadIdx.x == 0) s_fine = 0;
     const int64_t base = (int64_t)blockIdx.x * (kThreads * ITEMS) + threadIdx.x;
     float2 m[ITEMS];
     int r[ITEMS];
@@ -390,31 +497,47 @@ __global__ void __launch_bounds__(kThreads) k_count(int n_items, const __grid_co
         key[q] = ok ? __float_as_uint(depth[i]) : 0u;
     }
     __syncthreads();
+    uint32_t fine = 0;
+    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int q = 0; q < ITEMS; ++q) {
         const int64_t i = base + q * kThreads;
-        if (i >= n_items) continue;
-        const ViewDesc& vd = sv.views[(int)i / sv.n_per_view];
-        int x0, x1, y0, y1;
-        uint32_t c = 0;
-        if (tile_rect(m[q].x, m[q].y, r[q], vd.W, vd.H, x0, x1, y0, y1)) {
-            if constexpr (TIGHT) {
-                const TightRows t = item_tight_rows(sv, mean2d, (uint32_t)i);
-                for (int y = y0; y <= y1; ++y) {
-                    int f, l;
-                    tight_row(t, y, x0, x1, f, l);
-                    c += (uint32_t)max(l - f + 1, 0);
-                }
-            } else {
-                c = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+        int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
+        bool tall = false;
+        TightRows t{};
+        if (i < n_items) {
+            const ViewDesc& vd = sv.views[(int)i / sv.n_per_view];
+            uint32_t c = 0;
+            if (tile_rect(m[q].x, m[q].y, r[q], vd.W, vd.H, x0, x1, y0, y1)) {
+                if constexpr (TIGHT) t = item_tight_rows(sv, mean2d, (uint32_t)i);
+                tall = y1 / kSuper - y0 / kSuper + 1 > kTallRows;
+                if (!tall)
+                    for (int sy = y0 / kSuper; sy <= y1 / kSuper; ++sy)
+                        c += (uint32_t)supertile_row<TIGHT>(t, sy, x0, x1, y0, y1, &fine, [](int, int) {});
             }
-        }
-        cnt[i] = c;
-        dkey[i] = key[q];
-        dval[i] = (uint32_t)i;
+            if (!tall) cnt[i] = c;
+            dkey[i] = key[q];
+            dval[i] = (uint32_t)i;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) hist_add(s_h, p * 256 + ((key[q] >> (8 * p)) & 0xFFu));
+            for (int p = 0; p < 4; ++p) hist_add(s_h, p * 256 + ((key[q] >> (8 * p)) & 0xFFu));
+        }
+        // a tall item: the whole warp, lane k on supertile rows sy0 + k, sy0 + k + 32, ...
+        unsigned talls = __ballot_sync(0xffffffffu, tall);
+        while (talls) {
+            const int src = __ffs(talls) - 1;
+            talls &= talls - 1;
+            const int bx0 = __shfl_sync(0xffffffffu, x0, src), bx1 = __shfl_sync(0xffffffffu, x1, src);
+            const int by0 = __shfl_sync(0xffffffffu, y0, src), by1 = __shfl_sync(0xffffffffu, y1, src);
+            const TightRows bt = shfl_rows(t, src);
+            uint32_t c = 0;
+            for (int sy = by0 / kSuper + lane; sy <= by1 / kSuper; sy += 32)
+                c += (uint32_t)supertile_row<TIGHT>(bt, sy, bx0, bx1, by0, by1, &fine, [](int, int) {});
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            if (lane == src) cnt[i] = c;
+        }
     }
+    if (fine) atomicAdd(&s_fine, (unsigned long long)fine);
     const size_t stride = (size_t)gridDim.x * kThreads;
     const uint4 z = make_uint4(0, 0, 0, 0);
     for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < clear_n; i += stride) clear[i] = z;
@@ -422,6 +545,7 @@ __global__ void __launch_bounds__(kThreads) k_count(int n_items, const __grid_co
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * 256; i += kThreads)
         if (s_h[i]) atomicAdd(&hist[i], s_h[i]);
+    if (threadIdx.x == 0 && s_fine) atomicAdd(fine_total, s_fine);
 }
 
 // Digit histograms of the tile ids [a, a + w) of one rectangle row, by runs:
@@ -439,32 +563,26 @@ __device__ __forceinline__ void row_hist(uint32_t a, uint32_t w, int passes, int
     }
 }
 
-// Duplication in depth order with the scan of instance counts folded in.
-// Tile t (from the ticket) holds the depth-ordered items
-// [t * kDupTile, (t + 1) * kDupTile) in kDupItems rounds of 256; the tile's
-// instance offset comes from decoupled look-back over the tiles before it.
-// Each item's instances are its rectangle's tiles (TIGHT: each row's run of
-// tiles that meet the opacity-aware rule), row-major, at [offset, offset +
-// count).  Full rectangles: each warp writes its items of at most 32
-// instances as one flat, coalesced sequence, then each bigger item with the
-// whole warp.  TIGHT: one thread per item, an item of more than 32 instances
-// by the whole warp.
-// Writes stop at `limit`; the total goes to *total and, in graph
-// mode, to *count_out, with kErrCapacity raised when it exceeds the capacity.
-// The digit histograms of the written instances' tile ids go to hist
-// (tile_passes of them), so a truncated list still sorts into a permutation
-// of what was written.
+// Coarse duplication in depth order with the scan of supertile counts folded
+// in.  Tile t (from the ticket) holds the depth-ordered items
+// [t * kDupTile, (t + 1) * kDupTile); the tile's pair offset comes from
+// decoupled look-back over the tiles before it.  Each item writes one
+// (global supertile id, item) pair per supertile it touches, supertile rows
+// in order, at [offset, offset + count): one thread per item, an item of more
+// than 32 supertiles by the whole warp (one supertile row per lane).  Writes
+// stop at `limit`; the total goes to *total.  The digit histograms of the
+// written pairs' supertile ids go to hist (passes of them), so a truncated
+// list still sorts into a permutation of what was written.
 template <bool TIGHT>
-__global__ void __launch_bounds__(kThreads) k_duplicate(int n_items, const uint32_t* __restrict__ perm,
-                                                        const uint32_t* __restrict__ cnt,
-                                                        const __grid_constant__ SortViews sv,
-                                                        const float2* __restrict__ mean2d,
-                                                        const int* __restrict__ radius, uint64_t limit,
-                                                        int tile_passes, uint32_t* tickets,
-                                                        unsigned long long* status, uint32_t* __restrict__ tkey,
-                                                        uint32_t* __restrict__ tval, uint32_t* __restrict__ hist,
-                                                        uint64_t* __restrict__ total, int64_t* __restrict__ count_out,
-                                                        unsigned* err) {
+__global__ void __launch_bounds__(kThreads) k_dup_coarse(int n_items, const uint32_t* __restrict__ perm,
+                                                         const uint32_t* __restrict__ cnt,
+                                                         const __grid_constant__ SortViews sv,
+                                                         const float2* __restrict__ mean2d,
+                                                         const int* __restrict__ radius, uint64_t limit, int passes,
+                                                         uint32_t* tickets, unsigned long long* status,
+                                                         uint32_t* __restrict__ ckey, uint32_t* __restrict__ cval,
+                                                         uint32_t* __restrict__ hist, uint64_t* __restrict__ total,
+                                                         unsigned* err) {
     __shared__ uint64_t s_warp[kThreads / 32 + 1];
     __shared__ uint64_t s_prefix;
     __shared__ uint32_t s_tile;
@@ -480,18 +598,11 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(int n_items, const uint3
     const int64_t base = (int64_t)tile * kDupTile;
     if (base >= n_items) return;
 
-    uint32_t item[kDupItems], c[kDupItems];
-    uint64_t local[kDupItems];
-    uint64_t tile_sum = 0;
-#pragma unroll
-    for (int r = 0; r < kDupItems; ++r) {
-        const int64_t k = base + r * kThreads + threadIdx.x;
-        item[r] = k < n_items ? perm[k] : 0u;
-        c[r] = k < n_items ? cnt[item[r]] : 0u;
-        uint64_t rt;
-        local[r] = tile_sum + block_excl_scan<uint64_t, kThreads>((uint64_t)c[r], rt, s_warp);
-        tile_sum += rt;
-    }
+    const int64_t k = base + threadIdx.x;
+    const uint32_t item = k < n_items ? perm[k] : 0u;
+    const uint32_t c = k < n_items ? cnt[item] : 0u;
+    uint64_t tile_sum;
+    const uint64_t local = block_excl_scan<uint64_t, kThreads>((uint64_t)c, tile_sum, s_warp);
     unsigned long long* mine = status + tile;
     if (warp == 0) {
         if (lane == 0) st_status(mine, tile == 0 ? 2u : 1u, tile_sum);
@@ -502,170 +613,85 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(int n_items, const uint3
         }
         if (lane == 0) {
             s_prefix = prefix;
-            if (base + kDupTile >= n_items) {  // the last tile: the total
-                const uint64_t all = prefix + tile_sum;
-                *total = all;
-                if (count_out != nullptr) {
-                    *count_out = (int64_t)all;
-                    if (all > limit) atomicOr(err, kErrCapacity);
-                }
-            }
+            if (base + kDupTile >= n_items) *total = prefix + tile_sum;  // the last tile: the total
         }
     }
     __syncthreads();
-    const uint64_t prefix = s_prefix;
+    const uint64_t off = s_prefix + local;
 
-    if constexpr (!TIGHT) {
-#pragma unroll
-    for (int r = 0; r < kDupItems; ++r) {
-        uint32_t w = 1, h = 0, tile0 = 0, tx = 0;
-        if (c[r] > 0) {
-            const ViewDesc& vd = sv.views[item[r] / (uint32_t)sv.n_per_view];
-            int x0, x1, y0, y1;
-            const float2 m = mean2d[item[r]];
-            tile_rect(m.x, m.y, radius[item[r]], vd.W, vd.H, x0, x1, y0, y1);
-            w = (uint32_t)(x1 - x0 + 1);
-            h = (uint32_t)(y1 - y0 + 1);
-            tx = (uint32_t)vd.tiles_x;
-            tile0 = (uint32_t)vd.tile_begin + (uint32_t)y0 * tx + (uint32_t)x0;
-        }
-        const uint64_t off = prefix + local[r];
-        // written: all of the item's instances unless the capacity cuts it
-        const uint32_t nw = off >= limit ? 0u : (uint32_t)min((uint64_t)c[r], limit - off);
-        const bool big = c[r] > 32;
-        if (!big)
-            for (uint32_t y = 0; y * w < nw; ++y) row_hist(tile0 + y * tx, min(w, nw - y * w), tile_passes, s_d0, s_h);
-        // Items of at most 32 instances, flat and coalesced: the warp walks the
-        // concatenation of their ranges (offsets exs, compacted over these items)
-        // 32 positions at a time; position j belongs to the last lane whose
-        // range starts at or before j (a lane without such an item shares its
-        // start with the next lane).
-        const uint32_t cs = big ? 0u : c[r];
-        uint32_t incl = cs;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += u;
-        }
-        const uint32_t exs = incl - cs, tot_s = __shfl_sync(0xffffffffu, incl, 31);
-        for (uint32_t j0 = 0; j0 < tot_s; j0 += 32) {
-            const uint32_t j = j0 + lane;
-            int k = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1)
-                if (__shfl_sync(0xffffffffu, exs, k + step) <= j) k += step;
-            const uint32_t q = j - __shfl_sync(0xffffffffu, exs, k);
-            const uint64_t p = __shfl_sync(0xffffffffu, off, k) + q;
-            const uint32_t kw = __shfl_sync(0xffffffffu, w, k);  // 1 for a lane without instances
-            const uint32_t kt = __shfl_sync(0xffffffffu, tile0, k) + (q / kw) * __shfl_sync(0xffffffffu, tx, k) + q % kw;
-            const uint32_t ki = __shfl_sync(0xffffffffu, item[r], k);
-            if (j < tot_s && p < limit) {
-                tkey[p] = kt;
-                tval[p] = ki;
-            }
-        }
-        unsigned bigs = __ballot_sync(0xffffffffu, big);
-        while (bigs) {  // a bigger item: the whole warp, one row's histogram per lane, the instances flat
-            const int src = __ffs(bigs) - 1;
-            bigs &= bigs - 1;
-            const uint32_t bi = __shfl_sync(0xffffffffu, item[r], src), bnw = __shfl_sync(0xffffffffu, nw, src);
-            const uint32_t bw = __shfl_sync(0xffffffffu, w, src), bt0 = __shfl_sync(0xffffffffu, tile0, src);
-            const uint32_t btx = __shfl_sync(0xffffffffu, tx, src), bh = __shfl_sync(0xffffffffu, h, src);
-            const uint64_t boff = __shfl_sync(0xffffffffu, off, src);
-            for (uint32_t y = lane; y < bh && y * bw < bnw; y += 32)
-                row_hist(bt0 + y * btx, min(bw, bnw - y * bw), tile_passes, s_d0, s_h);
-            for (uint32_t j = lane; j < bnw; j += 32) {
-                tkey[boff + j] = bt0 + (j / bw) * btx + j % bw;
-                tval[boff + j] = bi;
-            }
-        }
+    int x0 = 0, x1 = -1, y0 = 0, y1 = -1, stx = 0, stb = 0;
+    TightRows t{};
+    if (c > 0) {
+        const int v = (int)(item / (uint32_t)sv.n_per_view);
+        const ViewDesc& vd = sv.views[v];
+        const float2 m = mean2d[item];
+        tile_rect(m.x, m.y, radius[item], vd.W, vd.H, x0, x1, y0, y1);
+        stx = sv.st_x[v];
+        stb = sv.st_begin[v];
+        if constexpr (TIGHT) t = item_tight_rows(sv, mean2d, item);
     }
-    } else {
-#pragma unroll
-    for (int r = 0; r < kDupItems; ++r) {
-        int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
-        uint32_t rowbase = 0, tx = 0;
-        TightRows t{};
-        if (c[r] > 0) {
-            const ViewDesc& vd = sv.views[item[r] / (uint32_t)sv.n_per_view];
-            const float2 m = mean2d[item[r]];
-            tile_rect(m.x, m.y, radius[item[r]], vd.W, vd.H, x0, x1, y0, y1);
-            tx = (uint32_t)vd.tiles_x;
-            rowbase = (uint32_t)vd.tile_begin;
-            t = item_tight_rows(sv, mean2d, item[r]);
-        }
-        const uint64_t off = prefix + local[r];
-        const bool big = c[r] > 32;
-        if (c[r] > 0 && !big) {
-            uint64_t pos = off;
-            for (int y = y0; y <= y1 && pos < limit; ++y) {
-                int f, l;
-                tight_row(t, y, x0, x1, f, l);
-                if (f > l) continue;
-                const uint32_t t0 = rowbase + (uint32_t)y * tx + (uint32_t)f;
-                const uint32_t len = (uint32_t)(l - f + 1);
-                const uint32_t nw = (uint32_t)min((uint64_t)len, limit - pos);  // written (capacity)
+    // the pairs of supertile row sy at position p (written below `limit`); returns their count
+    auto write_row = [&](int sy, uint64_t p, uint32_t it) -> int {
+        uint32_t fine = 0;
+        return supertile_row<TIGHT>(t, sy, x0, x1, y0, y1, &fine, [&](int lo, int hi) {
+            const uint32_t k0 = (uint32_t)stb + (uint32_t)sy * (uint32_t)stx + (uint32_t)lo;
+            const uint32_t len = (uint32_t)(hi - lo + 1);
+            if (p < limit) {
+                const uint32_t nw = (uint32_t)min((uint64_t)len, limit - p);
                 for (uint32_t j = 0; j < nw; ++j) {
-                    tkey[pos + j] = t0 + j;
-                    tval[pos + j] = item[r];
+                    ckey[p + j] = k0 + j;
+                    cval[p + j] = it;
                 }
-                row_hist(t0, nw, tile_passes, s_d0, s_h);
-                pos += len;
+                row_hist(k0, nw, passes, s_d0, s_h);
             }
-        }
-        unsigned bigs = __ballot_sync(0xffffffffu, big);
-        while (bigs) {  // the whole warp, 32 rows at a time
-            const int src = __ffs(bigs) - 1;
-            bigs &= bigs - 1;
-            const uint32_t bi = __shfl_sync(0xffffffffu, item[r], src);
-            const int bx0 = __shfl_sync(0xffffffffu, x0, src), bx1 = __shfl_sync(0xffffffffu, x1, src);
-            const int by0 = __shfl_sync(0xffffffffu, y0, src), by1 = __shfl_sync(0xffffffffu, y1, src);
-            const uint32_t btx = __shfl_sync(0xffffffffu, tx, src), brb = __shfl_sync(0xffffffffu, rowbase, src);
-            uint64_t pos = __shfl_sync(0xffffffffu, off, src);
-            TightRows bt;
-            bt.mode = __shfl_sync(0xffffffffu, t.mode, src);
-            bt.mx = __shfl_sync(0xffffffffu, t.mx, src);
-            bt.my = __shfl_sync(0xffffffffu, t.my, src);
-            bt.nB = __shfl_sync(0xffffffffu, t.nB, src);
-            bt.det = __shfl_sync(0xffffffffu, t.det, src);
-            bt.Atau = __shfl_sync(0xffffffffu, t.Atau, src);
-            bt.rA = __shfl_sync(0xffffffffu, t.rA, src);
-            bt.ymax = __shfl_sync(0xffffffffu, t.ymax, src);
-            bt.dyr = __shfl_sync(0xffffffffu, t.dyr, src);
-            for (int yb = by0; yb <= by1 && pos < limit; yb += 32) {
-                // lane k: row yb + k's run, its offset among the 32 rows' instances and its histogram
-                int f = 0, l = -1;
-                if (yb + lane <= by1) tight_row(bt, yb + lane, bx0, bx1, f, l);
-                const uint32_t len = (uint32_t)max(l - f + 1, 0);
-                uint32_t incl = len;
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
-                    if (lane >= d) incl += v;
-                }
-                const uint32_t excl = incl - len, rows_total = __shfl_sync(0xffffffffu, incl, 31);
-                const uint32_t t0 = brb + (uint32_t)(yb + lane) * btx + (uint32_t)f;  // used where len > 0
-                const uint64_t rpos = pos + excl;
-                if (len > 0 && rpos < limit)
-                    row_hist(t0, (uint32_t)min((uint64_t)len, limit - rpos), tile_passes, s_d0, s_h);
-                // the instances flat: element j belongs to the last row whose offset is <= j
-                const uint32_t nw = (uint32_t)min((uint64_t)rows_total, limit - pos);
-                for (uint32_t j0 = 0; j0 < nw; j0 += 32) {
-                    const uint32_t j = j0 + lane;
-                    int k = 0;
-#pragma unroll
-                    for (int step = 16; step > 0; step >>= 1)
-                        if (__shfl_sync(0xffffffffu, excl, k + step) <= j) k += step;
-                    const uint32_t kt0 = __shfl_sync(0xffffffffu, t0, k), kex = __shfl_sync(0xffffffffu, excl, k);
-                    if (j < nw) {
-                        tkey[pos + j] = kt0 + (j - kex);
-                        tval[pos + j] = bi;
-                    }
-                }
-                pos += rows_total;
-            }
-        }
+            p += len;
+        });
+    };
+    const bool big = c > 32 || (c > 0 && y1 / kSuper - y0 / kSuper + 1 > kTallRows);
+    if (c > 0 && !big) {
+        uint64_t p = off;
+        for (int sy = y0 / kSuper; sy <= y1 / kSuper && p < limit; ++sy) p += (uint64_t)write_row(sy, p, item);
     }
+    unsigned bigs = __ballot_sync(0xffffffffu, big);
+    while (bigs) {  // the whole warp: lane k takes supertile rows sy0 + k, sy0 + k + 32, ...
+        const int src = __ffs(bigs) - 1;
+        bigs &= bigs - 1;
+        const uint32_t bi = __shfl_sync(0xffffffffu, item, src);
+        const int bx0 = __shfl_sync(0xffffffffu, x0, src), bx1 = __shfl_sync(0xffffffffu, x1, src);
+        const int by0 = __shfl_sync(0xffffffffu, y0, src), by1 = __shfl_sync(0xffffffffu, y1, src);
+        const int bstx = __shfl_sync(0xffffffffu, stx, src), bstb = __shfl_sync(0xffffffffu, stb, src);
+        uint64_t pos = __shfl_sync(0xffffffffu, off, src);
+        const TightRows bt = shfl_rows(t, src);
+        for (int sb = by0 / kSuper; sb <= by1 / kSuper && pos < limit; sb += 32) {
+            const int sy = sb + lane;
+            uint32_t fine = 0;
+            const int n_row = sy <= by1 / kSuper
+                                  ? supertile_row<TIGHT>(bt, sy, bx0, bx1, by0, by1, &fine, [](int, int) {}) : 0;
+            uint32_t incl = (uint32_t)n_row;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += v;
+            }
+            const uint32_t rows_total = __shfl_sync(0xffffffffu, incl, 31);
+            if (n_row > 0) {
+                uint64_t p = pos + (incl - (uint32_t)n_row);
+                supertile_row<TIGHT>(bt, sy, bx0, bx1, by0, by1, &fine, [&](int lo, int hi) {
+                    const uint32_t k0 = (uint32_t)bstb + (uint32_t)sy * (uint32_t)bstx + (uint32_t)lo;
+                    const uint32_t len = (uint32_t)(hi - lo + 1);
+                    if (p < limit) {
+                        const uint32_t nw = (uint32_t)min((uint64_t)len, limit - p);
+                        for (uint32_t j = 0; j < nw; ++j) {
+                            ckey[p + j] = k0 + j;
+                            cval[p + j] = bi;
+                        }
+                        row_hist(k0, nw, passes, s_d0, s_h);
+                    }
+                    p += len;
+                });
+            }
+            pos += rows_total;
+        }
     }
     __syncthreads();
     {
@@ -674,35 +700,213 @@ __global__ void __launch_bounds__(kThreads) k_duplicate(int n_items, const uint3
         const int d0 = block_excl_scan<int, kThreads>(v, tot, s_warp_i) + v;  // count of digit-0 value threadIdx.x
         if (d0) atomicAdd(&hist[threadIdx.x], (uint32_t)d0);
     }
-    for (int i = threadIdx.x; i < (tile_passes - 1) * 256; i += kThreads)
+    for (int i = threadIdx.x; i < (passes - 1) * 256; i += kThreads)
         if (s_h[i]) atomicAdd(&hist[256 + i], s_h[i]);
 }
 
-// Sorted keys (if asked for), ids and tile ranges.  Tile ids and item indices are checked
-// against their bounds: after a look-back that gave up (timeout bit set) the
-// passes can leave stale entries, which become item 0 and no range.
-__global__ void k_finalize(uint32_t I_host, const uint64_t* __restrict__ I_dev, const uint32_t* __restrict__ tkey,
-                           const uint32_t* __restrict__ tval, const float* __restrict__ depth, uint32_t n_items,
-                           uint32_t num_tiles, uint64_t* __restrict__ keys_sorted, uint32_t* __restrict__ ids_sorted,
-                           uint32_t* __restrict__ ranges) {
-    const uint32_t I = pass_count(I_host, I_dev);
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= I) return;
-    const uint32_t t = tkey[i];
-    const uint32_t g = tval[i] < n_items ? tval[i] : 0u;
-    if (keys_sorted != nullptr) keys_sorted[i] = ((uint64_t)t << 32) | __float_as_uint(depth[g]);
-    ids_sorted[i] = g;
-    if (t >= num_tiles) return;
-    if (i == 0 || tkey[i - 1] != t) ranges[2 * t] = i;
-    if (i == I - 1 || tkey[i + 1] != t) ranges[2 * t + 1] = i + 1;
+// First position of key >= want in the ascending keys[0, n).
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__ keys, uint32_t n, uint32_t want) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if (keys[mid] < want) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// The 16-bit mask of an item's instances in the supertile whose first tile
+// is (cx0, cy0): bit 4 r + c for tile (cx0 + c, cy0 + r).  The same rule as
+// the counts (tile_rect, then tight_row per row with the item's whole
+// rectangle), clipped to the supertile.
+template <bool TIGHT>
+__device__ __forceinline__ uint32_t supertile_mask(const SortViews& sv, const float2* mean2d, const int* radius,
+                                                   uint32_t item, const ViewDesc& vd, int cx0, int cy0) {
+    const float2 m = mean2d[item];
+    int x0, x1, y0, y1;
+    if (!tile_rect(m.x, m.y, radius[item], vd.W, vd.H, x0, x1, y0, y1)) return 0u;
+    const int a0 = max(x0, cx0), a1 = min(x1, cx0 + kSuper - 1);
+    if (a0 > a1) return 0u;
+    TightRows t{};
+    if constexpr (TIGHT) t = item_tight_rows(sv, mean2d, item);
+    uint32_t mask = 0;
+#pragma unroll
+    for (int r = 0; r < kSuper; ++r) {
+        const int y = cy0 + r;
+        if (y < y0 || y > y1) continue;
+        int f = x0, l = x1;
+        if constexpr (TIGHT) tight_row(t, y, x0, x1, f, l);
+        f = max(f, a0);
+        l = min(l, a1);
+        if (f <= l) mask |= ((1u << (l - f + 1)) - 1u) << (r * kSuper + f - cx0);
+    }
+    return mask;
+}
+
+// One block per supertile s: its items are the sorted pairs [cs, ce) with key
+// s.  WRITE = false: each pair's 16-bit tile mask (into masks[]) and the
+// instance count of each of the supertile's tiles (into ranges[2 t + 1]),
+// counted per warp with one ballot per tile.  WRITE = true (after
+// k_tile_scan): every instance's id (and key) at its tile's next position, in
+// item order, from the stored masks: rounds of kFineThreads pairs; thread
+// (q, j) places tile j's instances among the round's pairs [16 q, 16 q + 16)
+// into a shared-memory stage of the round's output of each tile, and the block
+// then writes each tile's run with consecutive threads on consecutive ids.
+constexpr int kFineThreads = 256;
+template <bool TIGHT, bool WRITE>
+__global__ void __launch_bounds__(kFineThreads) k_fine(const __grid_constant__ SortViews sv,
+                                                       const float2* __restrict__ mean2d,
+                                                       const int* __restrict__ radius, const float* __restrict__ depth,
+                                                       const uint32_t* __restrict__ ckey,
+                                                       const uint32_t* __restrict__ cval, uint32_t n_host,
+                                                       const uint64_t* __restrict__ n_dev, uint32_t n_items,
+                                                       uint16_t* __restrict__ masks, uint32_t* __restrict__ ranges,
+                                                       uint32_t* __restrict__ ids_out, uint64_t* __restrict__ keys_out) {
+    constexpr int Q = kFineThreads / 16;  // workers per tile
+    __shared__ uint32_t s_rng[2];
+    __shared__ uint32_t s_cnt[16];
+    __shared__ uint32_t s_beg[16], s_end[16], s_run[16], s_tot[16];
+    __shared__ uint16_t s_mask[kFineThreads];
+    __shared__ uint32_t s_item[kFineThreads];
+    __shared__ uint32_t s_q[Q][16];
+    __shared__ uint32_t s_out[16][kFineThreads];
+    const int s = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int v = 0;
+    while (v + 1 < sv.num_views && sv.st_begin[v + 1] <= s) ++v;
+    const ViewDesc& vd = sv.views[v];
+    const int ls = s - sv.st_begin[v];
+    const int cx0 = (ls % sv.st_x[v]) * kSuper, cy0 = (ls / sv.st_x[v]) * kSuper;
+    const int tx = vd.tiles_x, ty = tiles_y(vd.H);
+    const uint32_t Ic = pass_count(n_host, n_dev);
+    if (threadIdx.x < 2) s_rng[threadIdx.x] = lower_bound_u32(ckey, Ic, (uint32_t)s + threadIdx.x);
+    if (threadIdx.x < 16) {
+        const int c = cx0 + (threadIdx.x & 3), r = cy0 + (threadIdx.x >> 2);
+        const bool ok = c < tx && r < ty;
+        const uint32_t gt = (uint32_t)vd.tile_begin + (uint32_t)r * (uint32_t)tx + (uint32_t)c;
+        s_cnt[threadIdx.x] = 0;
+        s_run[threadIdx.x] = 0;
+        s_beg[threadIdx.x] = WRITE && ok ? ranges[2 * gt] : 0u;
+        s_end[threadIdx.x] = WRITE && ok ? ranges[2 * gt + 1] : 0u;
+    }
+    __syncthreads();
+    const uint32_t cs = s_rng[0], ce = s_rng[1];
+    if (cs >= ce) return;
+    if constexpr (!WRITE) {
+        uint32_t mine = 0;  // lane j < 16: this warp's count of tile j
+        // two pairs per thread per step, their items loaded together
+        for (uint32_t b = cs + 64 * warp; b < ce; b += 2 * kFineThreads) {
+            const uint32_t e0 = b + lane, e1 = b + 32 + lane;
+            const uint32_t it0 = e0 < ce ? cval[e0] : 0xffffffffu, it1 = e1 < ce ? cval[e1] : 0xffffffffu;
+            uint32_t m0 = it0 < n_items ? supertile_mask<TIGHT>(sv, mean2d, radius, it0, vd, cx0, cy0) : 0u;
+            uint32_t m1 = it1 < n_items ? supertile_mask<TIGHT>(sv, mean2d, radius, it1, vd, cx0, cy0) : 0u;
+            if (e0 < ce) masks[e0] = (uint16_t)m0;
+            if (e1 < ce) masks[e1] = (uint16_t)m1;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const unsigned bj = __ballot_sync(0xffffffffu, (m0 >> j) & 1u);
+                const unsigned cj = __ballot_sync(0xffffffffu, (m1 >> j) & 1u);
+                if (lane == j) mine += (uint32_t)(__popc(bj) + __popc(cj));
+            }
+        }
+        if (lane < 16 && mine) atomicAdd(&s_cnt[lane], mine);
+        __syncthreads();
+        if (threadIdx.x < 16) {
+            const int c = cx0 + (threadIdx.x & 3), r = cy0 + (threadIdx.x >> 2);
+            if (c < tx && r < ty)
+                ranges[2 * ((size_t)vd.tile_begin + (size_t)r * tx + c) + 1] = s_cnt[threadIdx.x];
+        }
+    } else {
+        const int j = threadIdx.x & 15, q = threadIdx.x >> 4;
+        for (uint32_t r0 = cs; r0 < ce; r0 += kFineThreads) {
+            const uint32_t e = r0 + threadIdx.x;
+            s_mask[threadIdx.x] = e < ce ? masks[e] : (uint16_t)0;
+            s_item[threadIdx.x] = e < ce ? cval[e] : 0u;
+            __syncthreads();
+            uint32_t cnt = 0;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) cnt += (s_mask[16 * q + k] >> j) & 1u;
+            s_q[q][j] = cnt;
+            __syncthreads();
+            uint32_t pre = 0;
+            for (int qq = 0; qq < q; ++qq) pre += s_q[qq][j];
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                if ((s_mask[16 * q + k] >> j) & 1u) s_out[j][pre++] = s_item[16 * q + k];
+            if (q == Q - 1) s_tot[j] = pre;  // the round's instances of tile j
+            __syncthreads();
+            // each tile's run of this round, consecutive threads on consecutive positions
+            for (int t = 0; t < 16; ++t) {
+                const uint32_t n_t = s_tot[t];
+                const uint64_t p0 = (uint64_t)s_beg[t] + s_run[t];
+                const uint64_t end = s_end[t];
+                const uint64_t dkey = keys_out != nullptr
+                                          ? (uint64_t)((uint32_t)vd.tile_begin + (uint32_t)(cy0 + (t >> 2)) * (uint32_t)tx +
+                                                       (uint32_t)(cx0 + (t & 3))) << 32
+                                          : 0ull;
+                for (uint32_t k = threadIdx.x; k < n_t; k += kFineThreads) {
+                    const uint64_t p = p0 + k;
+                    if (p < end) {
+                        const uint32_t g = s_out[t][k];
+                        ids_out[p] = g;
+                        if (keys_out != nullptr) keys_out[p] = dkey | __float_as_uint(depth[g]);
+                    }
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x < 16) s_run[threadIdx.x] += s_tot[threadIdx.x];
+            __syncthreads();
+        }
+    }
+}
+
+// Tile ranges from the per-tile counts in ranges[2 t + 1]: an exclusive scan
+// over all tiles (one block), each bound clamped to the capacity.  Graph mode:
+// the instance count (fine_total, from k_count) to *count_out, and the
+// capacity bit when it exceeds the capacity.
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) k_tile_scan(int num_tiles, uint32_t* __restrict__ ranges,
+                                                            uint64_t cap, const unsigned long long* fine_total,
+                                                            int64_t* count_out, unsigned* err) {
+    __shared__ uint64_t s_warp[kScanThreads / 32 + 1];
+    constexpr int PER = 4;
+    uint64_t run = 0;
+    for (int64_t b = 0; b < num_tiles; b += (int64_t)kScanThreads * PER) {
+        uint32_t c[PER];
+        uint64_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int64_t t = b + (int64_t)threadIdx.x * PER + k;
+            c[k] = t < num_tiles ? ranges[2 * t + 1] : 0u;
+            sum += c[k];
+        }
+        uint64_t tot;
+        uint64_t pre = run + block_excl_scan<uint64_t, kScanThreads>(sum, tot, s_warp);
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int64_t t = b + (int64_t)threadIdx.x * PER + k;
+            if (t < num_tiles) {
+                const uint64_t e = pre + c[k];
+                ranges[2 * t] = (uint32_t)(c[k] > 0 ? min(pre, cap) : 0);
+                ranges[2 * t + 1] = (uint32_t)(c[k] > 0 ? min(e, cap) : 0);
+            }
+            pre += c[k];
+        }
+        run += tot;
+    }
+    if (threadIdx.x == 0 && count_out != nullptr) {
+        const uint64_t all = *fine_total;
+        *count_out = (int64_t)all;
+        if (all > cap) atomicOr(err, kErrCapacity);
+    }
 }
 
 // Workspace: per-item arrays, a header cleared by one memset (digit
 // histograms, tickets, total), the look-back status words (cleared by
 // k_count), and the instance key/value double buffers.
 struct Layout {
-    size_t cnt, dk0, dk1, dv0, dv1, hdr, hist, tickets, total, hdr_bytes, status, status_bytes, tk0, tk1, tv0, tv1,
-        total_bytes;
+    size_t cnt, dk0, dk1, dv0, dv1, hdr, hist, tickets, total, ctotal, hdr_bytes, status, status_bytes, tk0, tk1, tv0,
+        tv1, total_bytes;
 };
 
 Layout make_layout(int n, int64_t capacity) {
@@ -722,7 +926,8 @@ Layout make_layout(int n, int64_t capacity) {
     L.hdr = o;
     L.hist = take(4 * 256 * kMaxPasses);
     L.tickets = take(4 * (kMaxPasses + 1));
-    L.total = take(8);
+    L.total = take(8);   // instances (k_count)
+    L.ctotal = take(8);  // supertile pairs (k_dup_coarse)
     L.hdr_bytes = o - L.hdr;
     // status words: 256 per radix tile (the largest tile count of either sort)
     // plus one per duplication tile
@@ -794,44 +999,37 @@ gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* ra
     unsigned long long* dup_status = status + radix_status_words;
     const PassScratch ps{hist, tickets, status, err};
 
-    // 1. counts, depth keys and their digit histograms; clears
+    // supertiles of every view
+    SortViews sv2 = sv;
+    {
+        int st = 0;
+        for (int v = 0; v < sv.num_views; ++v) {
+            sv2.st_begin[v] = st;
+            sv2.st_x[v] = (int)cdiv(sv.views[v].tiles_x, kSuper);
+            st += sv2.st_x[v] * (int)cdiv(tiles_y(sv.views[v].H), kSuper);
+        }
+        sv2.total_st = st;
+    }
+    uint64_t* ctotal = reinterpret_cast<uint64_t*>(base + L.ctotal);
+
+    // 1. supertile counts, depth keys and their digit histograms, the instance count; clears
     if ((e = cudaMemsetAsync(base + L.hdr, 0, L.hdr_bytes, s)) != cudaSuccess)
         return cuda_status(e, "gs_bin_sort: clear header");
     const bool tight = sv.conic != nullptr;
+    unsigned long long* fine_total = reinterpret_cast<unsigned long long*>(total);
     if (tight)
         k_count<true, kCountItemsTight><<<(int)cdiv(n, kThreads * kCountItemsTight), kThreads, 0, s>>>(
-            n, sv, mean2d, radius, depth, U32(L.cnt), U32(L.dk0), U32(L.dv0), hist, reinterpret_cast<uint4*>(status),
-            L.status_bytes / 16, tile_ranges, 2 * (size_t)ntiles);
+            n, sv2, mean2d, radius, depth, U32(L.cnt), U32(L.dk0), U32(L.dv0), hist, fine_total,
+            reinterpret_cast<uint4*>(status), L.status_bytes / 16, tile_ranges, 2 * (size_t)ntiles);
     else
         k_count<false, kCountItems><<<(int)cdiv(n, kThreads * kCountItems), kThreads, 0, s>>>(
-            n, sv, mean2d, radius, depth, U32(L.cnt), U32(L.dk0), U32(L.dv0), hist, reinterpret_cast<uint4*>(status),
-            L.status_bytes / 16, tile_ranges, 2 * (size_t)ntiles);
+            n, sv2, mean2d, radius, depth, U32(L.cnt), U32(L.dk0), U32(L.dv0), hist, fine_total,
+            reinterpret_cast<uint4*>(status), L.status_bytes / 16, tile_ranges, 2 * (size_t)ntiles);
     count_launches();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: count");
 
-    // 2. depth sort of all items (pass ids 0..3)
-    uint32_t* dk[2] = {U32(L.dk0), U32(L.dk1)};
-    uint32_t* dv[2] = {U32(L.dv0), U32(L.dv1)};
-    int which = 0;
-    if ((e = radix_sort(dk, dv, (uint32_t)n, nullptr, 32, 0, ps, &which, s)) != cudaSuccess)
-        return cuda_status(e, "gs_bin_sort: depth sort");
-    const uint32_t* perm = dv[which];
-
-    // 3. duplicate in depth order (pass ids 4.. for the tile-id histograms)
-    int tile_bits = 1;
-    while ((1ll << tile_bits) < ntiles) ++tile_bits;
-    const int tile_passes = (tile_bits + 7) / 8;
-    uint32_t* tk[2] = {U32(L.tk0), U32(L.tk1)};
-    uint32_t* tv[2] = {U32(L.tv0), U32(L.tv1)};
-    auto dup = tight ? k_duplicate<true> : k_duplicate<false>;
-    dup<<<(int)cdiv(n, kDupTile), kThreads, 0, s>>>(n, perm, U32(L.cnt), sv, mean2d, radius, (uint64_t)capacity,
-                                                    tile_passes, tickets, dup_status, tk[0], tv[0], hist + 256 * 4,
-                                                    total, graph ? n_instances_dev : nullptr, err);
-    count_launches();
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: duplicate");
-
-    uint32_t I_grid = 0;  // items the remaining kernels are launched for
-    const uint64_t* I_dev = nullptr;
+    // synchronising mode: the instance count, before any further work
+    uint32_t I_grid = 0;  // pairs / instances the later kernels are sized for
     if (!graph) {
         uint64_t I = 0;
         if ((e = cudaMemcpyAsync(&I, total, sizeof(uint64_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
@@ -842,22 +1040,60 @@ gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* ra
             set_error("gs_bin_sort: %llu instances exceed capacity %lld", (unsigned long long)I, (long long)capacity);
             return GS_ERR_CAPACITY;
         }
-        if (I == 0) return GS_OK;
-        I_grid = (uint32_t)I;
+        if (I == 0) return GS_OK;  // k_count cleared the ranges
+        I_grid = (uint32_t)I;      // supertile pairs <= instances
     } else {
-        if (capacity == 0) return GS_OK;
-        I_dev = total;
+        if (capacity == 0) {
+            k_tile_scan<<<1, kScanThreads, 0, s>>>(0, tile_ranges, 0, fine_total, n_instances_dev, err);
+            count_launches();
+            return cuda_status(cudaGetLastError(), "gs_bin_sort: count");
+        }
         I_grid = (uint32_t)capacity;
     }
 
-    // 4. stable sort by global tile id, then keys, ids and ranges
-    if ((e = radix_sort(tk, tv, I_grid, I_dev, tile_bits, 4, ps, &which, s)) != cudaSuccess)
-        return cuda_status(e, "gs_bin_sort: tile sort");
-    k_finalize<<<(int)cdiv((int64_t)I_grid, 256), 256, 0, s>>>(I_grid, I_dev, tk[which], tv[which], depth,
-                                                               (uint32_t)n, (uint32_t)ntiles, keys_sorted,
-                                                               ids_sorted, tile_ranges);
+    // 2. depth sort of all items (pass ids 0..3)
+    uint32_t* dk[2] = {U32(L.dk0), U32(L.dk1)};
+    uint32_t* dv[2] = {U32(L.dv0), U32(L.dv1)};
+    int which = 0;
+    if ((e = radix_sort(dk, dv, (uint32_t)n, nullptr, 32, 0, ps, &which, s)) != cudaSuccess)
+        return cuda_status(e, "gs_bin_sort: depth sort");
+    const uint32_t* perm = dv[which];
+
+    // 3. supertile pairs in depth order (pass ids 4.. for the supertile-id histograms)
+    int st_bits = 1;
+    while ((1ll << st_bits) < sv2.total_st) ++st_bits;
+    const int st_passes = (st_bits + 7) / 8;
+    uint32_t* ck[2] = {U32(L.tk0), U32(L.tk1)};
+    uint32_t* cv[2] = {U32(L.tv0), U32(L.tv1)};
+    auto dup = tight ? k_dup_coarse<true> : k_dup_coarse<false>;
+    dup<<<(int)cdiv(n, kDupTile), kThreads, 0, s>>>(n, perm, U32(L.cnt), sv2, mean2d, radius, (uint64_t)capacity,
+                                                    st_passes, tickets, dup_status, ck[0], cv[0], hist + 256 * 4,
+                                                    ctotal, err);
     count_launches();
-    return cuda_status(cudaGetLastError(), "gs_bin_sort: finalize");
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: duplicate");
+
+    // 4. stable sort of the pairs by supertile id: each supertile's items contiguous, in depth order
+    if ((e = radix_sort(ck, cv, I_grid, ctotal, st_bits, 4, ps, &which, s)) != cudaSuccess)
+        return cuda_status(e, "gs_bin_sort: supertile sort");
+
+    // 5. per-tile counts, tile ranges, then every instance's id at its place
+    const int nst = sv2.total_st;
+    auto fine_count = tight ? k_fine<true, false> : k_fine<false, false>;
+    auto fine_write = tight ? k_fine<true, true> : k_fine<false, true>;
+    // the pairs' tile masks go to the free half of the pair buffers (2 bytes per pair)
+    uint16_t* masks = reinterpret_cast<uint16_t*>(ck[which ^ 1]);
+    fine_count<<<nst, kFineThreads, 0, s>>>(sv2, mean2d, radius, depth, ck[which], cv[which], I_grid, ctotal,
+                                            (uint32_t)n, masks, tile_ranges, nullptr, nullptr);
+    count_launches();
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: tile counts");
+    k_tile_scan<<<1, kScanThreads, 0, s>>>(ntiles, tile_ranges, (uint64_t)capacity, fine_total,
+                                           graph ? n_instances_dev : nullptr, err);
+    count_launches();
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: tile ranges");
+    fine_write<<<nst, kFineThreads, 0, s>>>(sv2, mean2d, radius, depth, ck[which], cv[which], I_grid, ctotal,
+                                            (uint32_t)n, masks, tile_ranges, ids_sorted, keys_sorted);
+    count_launches();
+    return cuda_status(cudaGetLastError(), "gs_bin_sort: write lists");
 }
 
 }  // namespace gs

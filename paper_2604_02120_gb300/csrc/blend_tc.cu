@@ -39,7 +39,7 @@ unsigned* tile_queue_slot(cudaStream_t s, cudaError_t* err) {
 }
 
 bool tc_config_supported(int variant, int chunk, int stages) {
-    if (variant < GS_BLEND_TC_FP16 || variant > GS_BLEND_TC_FP8_SPLIT) return false;
+    if (variant < GS_BLEND_TC_FP16 || variant > GS_BLEND_PERSISTENT_FP32) return false;
     return (chunk == 32 && (stages == 2 || stages == 4)) || (chunk == 16 && stages == 4) ||
            (chunk == 16 && stages == 6);
 }
@@ -60,6 +60,9 @@ cudaError_t launch_blend_tc(const BlendArgs& a0, int variant, int chunk, int sta
             return tc::launch_variant<GS_BLEND_TC_BF16_SPLIT>(a, chunk, stages, dump, items, s);
         case GS_BLEND_TC_FP8_SPLIT:
             return tc::launch_variant<GS_BLEND_TC_FP8_SPLIT>(a, chunk, stages, dump, items, s);
+        case GS_BLEND_PERSISTENT_FP32:
+            if (dump) return cudaErrorInvalidValue;
+            return tc::launch_variant<GS_BLEND_PERSISTENT_FP32>(a, chunk, stages, dump, items, s);
     }
     return cudaErrorInvalidValue;
 }

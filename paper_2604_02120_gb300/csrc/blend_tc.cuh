@@ -68,6 +68,9 @@ constexpr float kStopScale = 1099511627776.0f;  // 2^40
 // exact terms.
 template <int V>
 struct Traits {
+    // CC: the exponent v_g . v_p by FP32 FMAs on the CUDA cores; the B stage
+    // then holds each splat's two FP32 rows (12 floats) and no MMA runs
+    static constexpr bool CC = (V == GS_BLEND_PERSISTENT_FP32);
     static constexpr bool FP8 = (V == GS_BLEND_TC_FP8_SPLIT);
     static constexpr int TERMS = FP8 ? 5 : (V == GS_BLEND_TC_FP16_SPLIT) ? 2 : (V == GS_BLEND_TC_BF16_SPLIT ? 3 : 1);
     static constexpr int PTERMS = FP8 ? 2 : 1;
@@ -297,6 +300,15 @@ __device__ __forceinline__ float store_coeff_row(uint8_t* mB, int r, const float
     }
 }
 
+// The CUDA-core variant's B stage: splat j's two FP32 rows, 12 floats at 48 j
+// (upper row 0..5, lower row 6..11).
+__device__ __forceinline__ void store_cc_rows(uint8_t* mB, int j, const float (&vu)[6], const float (&vl)[6]) {
+    float4* d = reinterpret_cast<float4*>(mB + 48 * j);
+    d[0] = make_float4(vu[0], vu[1], vu[2], vu[3]);
+    d[1] = make_float4(vu[4], vu[5], vl[0], vl[1]);
+    d[2] = make_float4(vl[2], vl[3], vl[4], vl[5]);
+}
+
 // Row `row` of M_p, the pixel-monomial operand: the 6 monomials of the pixel
 // (offsets xb, yb from its half's reference), in the slot order of
 // store_coeff_row (for FP8 each monomial as 2 exact e4m3 terms).
@@ -431,6 +443,17 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
     if (warp < kEpiWarps) {
         // ------------------------------------------------------- epilogue --
         const int r = warp * 32 + lane;  // accumulator lane: pixel r of each half
+        // this lane's pixel monomials (the same in both halves), as M_p holds them
+        float mp[5];
+        {
+            const float xb = origin ? -(float)(r & 15) : 7.5f - (float)(r & 15);
+            const float yb = origin ? -(float)(r >> 4) : 3.5f - (float)(r >> 4);
+            mp[0] = xb * xb;
+            mp[1] = yb * yb;
+            mp[2] = xb * yb;
+            mp[3] = xb;
+            mp[4] = yb;
+        }
         int cur_seq = -1, slot = 0;
         int px = 0, py_up = 0, W = 0, H = 0;
         bool in_up = false, in_lo = false, wdone = true;
@@ -488,10 +511,28 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
                 const Rec* rec = sRec + s * CH;
 #pragma unroll 1
                 for (int c0 = 0; c0 < n; c0 += 16) {
+                    // every pixel of this warp has stopped: the chunk's later splats change nothing
+                    if (!DUMP && c0 > 0 && __all_sync(0xffffffffu, T.x == 0.f && T.y == 0.f)) break;
                     uint32_t vu[16], vl[16];
-                    tmem_ld_32x32b_x16(tb + (uint32_t)c0, vu);
-                    tmem_ld_32x32b_x16(tb + (uint32_t)(CH + c0), vl);
-                    tmem_ld_wait();
+                    // CC: Eq. 6 on the CUDA cores, column by column below (both pixels of
+                    // the lane share their monomials)
+                    const float* rows = reinterpret_cast<const float*>(sB + s * LY::B_BYTES) + (size_t)c0 * 12;
+                    auto cc_power = [&](int c) {
+                        const float4 a0 = *reinterpret_cast<const float4*>(rows + 12 * c);
+                        const float4 a1 = *reinterpret_cast<const float4*>(rows + 12 * c + 4);
+                        const float4 a2 = *reinterpret_cast<const float4*>(rows + 12 * c + 8);
+                        float2 p = __fmul2_rn(make_float2(a0.x, a1.z), make_float2(mp[0], mp[0]));
+                        p = __ffma2_rn(make_float2(a0.y, a1.w), make_float2(mp[1], mp[1]), p);
+                        p = __ffma2_rn(make_float2(a0.z, a2.x), make_float2(mp[2], mp[2]), p);
+                        p = __ffma2_rn(make_float2(a0.w, a2.y), make_float2(mp[3], mp[3]), p);
+                        p = __ffma2_rn(make_float2(a1.x, a2.z), make_float2(mp[4], mp[4]), p);
+                        return __fadd2_rn(make_float2(a1.y, a2.w), p);
+                    };
+                    if constexpr (!TR::CC) {
+                        tmem_ld_32x32b_x16(tb + (uint32_t)c0, vu);
+                        tmem_ld_32x32b_x16(tb + (uint32_t)(CH + c0), vl);
+                        tmem_ld_wait();
+                    }
                     if constexpr (TR::FP8) {  // undo the per-row scaling of the e4m3 operands
                         const float2* scl = sScl + s * CH;
 #pragma unroll
@@ -517,9 +558,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
 #pragma unroll
                         for (int c = 0; c < 16; ++c) {
                             const Rec rc = rec[c0 + c];
+                            float2 pw;
+                            if constexpr (TR::CC) pw = cc_power(c);
+                            else pw = make_float2(__uint_as_float(vu[c]), __uint_as_float(vl[c]));
                             float2 al;
-                            al.x = ex2_approx(fminf(__uint_as_float(vu[c]), rc.bc.z));
-                            al.y = ex2_approx(fminf(__uint_as_float(vl[c]), rc.bc.w));
+                            al.x = ex2_approx(fminf(pw.x, rc.bc.z));
+                            al.y = ex2_approx(fminf(pw.y, rc.bc.w));
                             float2 cull;
                             cull.x = sat(fmaf(al.x, -kCullScale, kAlphaMin * kCullScale));
                             cull.y = sat(fmaf(al.y, -kCullScale, kAlphaMin * kCullScale));
@@ -674,8 +718,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
                         const float4* rp = reinterpret_cast<const float4*>(sRecT + ((size_t)rs * CH + j) * kRecFloats);
                         const float4 r0 = rp[0], r1 = rp[1], r2 = rp[2];
                         const float xh = r0.x - it.xc;
-                        coeff_row<TR::HALF>(r0.z, r0.w, r1.x, r1.y, xh, r0.y - it.yc, bx0, bx1, by0, by1, vu);
-                        coeff_row<TR::HALF>(r0.z, r0.w, r1.x, r1.y, xh, r0.y - yc_lo, bx0, bx1, by0, by1, vl);
+                        coeff_row<TR::HALF && !TR::CC>(r0.z, r0.w, r1.x, r1.y, xh, r0.y - it.yc, bx0, bx1, by0, by1, vu);
+                        coeff_row<TR::HALF && !TR::CC>(r0.z, r0.w, r1.x, r1.y, xh, r0.y - yc_lo, bx0, bx1, by0, by1, vl);
                         rc.rg = make_float4(r2.x, r2.x, r2.y, r2.y);
                         rc.bc = make_float4(r2.z, r2.z, r1.z, r1.z);
                     } else {  // padding column: dead rows, no colour
@@ -685,10 +729,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
                         rc.rg = make_float4(0.f, 0.f, 0.f, 0.f);
                         rc.bc = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
-                    const float su = store_coeff_row<V>(mB, j, vu);
-                    const float sl = store_coeff_row<V>(mB, CH + j, vl);
+                    if constexpr (TR::CC) {
+                        store_cc_rows(mB, j, vu, vl);
+                    } else {
+                        const float su = store_coeff_row<V>(mB, j, vu);
+                        const float sl = store_coeff_row<V>(mB, CH + j, vl);
+                        if constexpr (TR::FP8) sScl[s * CH + j] = make_float2(su, sl);
+                    }
                     sRec[s * CH + j] = rc;
-                    if constexpr (TR::FP8) sScl[s * CH + j] = make_float2(su, sl);
                 }
             }
             if (lane == 0) sHdr[s] = StageHdr{it.tile, n < 0 ? -2 : it.seq, it.base, n, it.q, {0, 0, 0}};
@@ -708,19 +756,31 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
         int k = 0;
         bool quit = false;
         unsigned long long issued = 0;  // splats of the chunks this block issued
+        // The next tile's queue item is taken when a tile starts and its range
+        // read once the tile's first chunk is out, so those dependent loads
+        // overlap the chunk work instead of preceding the next tile.
+        auto fetch = [&](int qq, int& tl, uint32_t& st, int& ln) {
+            tl = DUMP ? a.tiles[qq] : tile_at(a, qq * a.shard_count + a.shard_index);
+            st = a.ranges[2 * tl];
+            const uint32_t sp = a.ranges[2 * tl + 1];
+            ln = sp > st ? (int)(sp - st) : 0;
+        };
+        int q_next = 0, nt_tile = 0, nt_len = 0;
+        uint32_t nt_start = 0;
+        if (lane == 0) q_next = (int)atomicAdd(a.queue, 1u);
+        q_next = __shfl_sync(0xffffffffu, q_next, 0);
+        if (q_next < n_items) fetch(q_next, nt_tile, nt_start, nt_len);
         for (int seq = 0; !quit; ++seq) {
-            int q = 0;
-            if (lane == 0) q = (int)atomicAdd(a.queue, 1u);
-            q = __shfl_sync(0xffffffffu, q, 0);
+            const int q = q_next;
             const bool end = q >= n_items;
             int tile = 0, len = 0, vview = 0;
             uint32_t start = 0;
             float xc = 0.f, yc_up = 0.f;
+            if (!end && lane == 0) q_next = (int)atomicAdd(a.queue, 1u);  // used after this tile's first chunk
             if (!end) {
-                tile = DUMP ? a.tiles[q] : tile_at(a, q * a.shard_count + a.shard_index);
-                start = a.ranges[2 * tile];
-                const uint32_t stop = a.ranges[2 * tile + 1];
-                len = stop > start ? (int)(stop - start) : 0;
+                tile = nt_tile;
+                start = nt_start;
+                len = nt_len;
                 if (DUMP && len > a.max_len) len = a.max_len;
                 vview = view_of(a, tile);
                 const ViewDesc vd = a.views[vview];
@@ -763,8 +823,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
                             const float o = a.opac[g - (uint32_t)(vview * a.n_per_view)];
                             const float l2o = o > 0.f ? __log2f(o) : -INFINITY;
                             const float xh = m.x - xc;
-                            coeff_row<TR::HALF>(A, B, C, l2o, xh, m.y - yc_up, bx0, bx1, by0, by1, vu);
-                            coeff_row<TR::HALF>(A, B, C, l2o, xh, m.y - yc_lo, bx0, bx1, by0, by1, vl);
+                            coeff_row<TR::HALF && !TR::CC>(A, B, C, l2o, xh, m.y - yc_up, bx0, bx1, by0, by1, vu);
+                            coeff_row<TR::HALF && !TR::CC>(A, B, C, l2o, xh, m.y - yc_lo, bx0, bx1, by0, by1, vl);
                             const float cap = fminf(l2o, kLog2AlphaMax);
                             float cr = 0.f, cg = 0.f, cb = 0.f;
                             if (a.rgb) {
@@ -781,10 +841,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
                             rc.rg = make_float4(0.f, 0.f, 0.f, 0.f);
                             rc.bc = make_float4(0.f, 0.f, 0.f, 0.f);
                         }
-                        const float su = store_coeff_row<V>(mB, j, vu);
-                        const float sl = store_coeff_row<V>(mB, CH + j, vl);
+                        if constexpr (TR::CC) {
+                            store_cc_rows(mB, j, vu, vl);
+                        } else {
+                            const float su = store_coeff_row<V>(mB, j, vu);
+                            const float sl = store_coeff_row<V>(mB, CH + j, vl);
+                            if constexpr (TR::FP8) sScl[s * CH + j] = make_float2(su, sl);
+                        }
                         sRec[s * CH + j] = rc;
-                        if constexpr (TR::FP8) sScl[s * CH + j] = make_float2(su, sl);
                     }
                 }
                 if (lane == 0) sHdr[s] = StageHdr{tile, end ? -2 : seq, base, n, q, {0, 0, 0}};
@@ -792,6 +856,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar_full(s));
                 ++k;
+                if (c == 0 && !end) {  // the next tile's range, while this tile's chunks are consumed
+                    q_next = __shfl_sync(0xffffffffu, q_next, 0);
+                    if (q_next < n_items) fetch(q_next, nt_tile, nt_start, nt_len);
+                }
             }
             if (end) quit = true;
         }
@@ -819,6 +887,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_tc(const __grid_constant_
             if (n <= 0) {
                 mbar_arrive(bar_tfull(t));
                 if (n < 0) break;
+                mbar_arrive(bar_empty(s));
+                continue;
+            }
+            if constexpr (TR::CC) {  // the epilogue contracts the rows itself
+                mbar_arrive(bar_tfull(t));
                 mbar_arrive(bar_empty(s));
                 continue;
             }
@@ -898,6 +971,8 @@ template <>
 cudaError_t launch_variant<4>(const BlendArgs&, int, int, bool, int, cudaStream_t);
 template <>
 cudaError_t launch_variant<5>(const BlendArgs&, int, int, bool, int, cudaStream_t);
+template <>
+cudaError_t launch_variant<6>(const BlendArgs&, int, int, bool, int, cudaStream_t);
 
 }  // namespace tc
 }  // namespace gs

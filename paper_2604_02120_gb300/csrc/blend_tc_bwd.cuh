@@ -49,7 +49,14 @@ namespace gs {
 namespace tc {
 
 constexpr int kBwdChunk = 16;
-constexpr int kBwdStages = 6;  // the deepest ring that keeps 3 blocks per SM (75.9 KB of shared memory each)
+// Built depths of the shared-memory ring: 6 (fp16 operands: the deepest that
+// keeps 3 blocks per SM, 75.9 KB each), 4 and 2 (bf16 and FP8 rows are twice
+// as wide; 2 stages keep 3 blocks per SM for them).
+constexpr int kBwdStagesBuilt[3] = {2, 4, 6};
+template <int V>
+constexpr int bwd_default_stages() {
+    return (V == GS_BLEND_TC_BF16_SPLIT || V == GS_BLEND_TC_FP8_SPLIT) ? 2 : 6;
+}
 constexpr float kTScale = 4096.0f;  // 2^12
 
 __device__ __forceinline__ void tmem_ld_32x32b_x8(uint32_t taddr, uint32_t (&v)[8]) {
@@ -447,57 +454,73 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
         }
     } else if (warp == kEpiWarps) {
         // ------------------------------------------------------- producer --
+        // A tile's header (queue item, range, the largest n_contrib and
+        // |dL/dimage| of its pixels, the scales) is worked out for the next
+        // tile once the current tile's first stage is out, so those loads
+        // overlap the current tile's chunks.
+        struct TileHead {
+            int q, tile, len, vview, nch;
+            uint32_t start;
+            float xc, yc_up;
+            BwdHdr hd;
+        };
+        auto head = [&](int qi) {
+            TileHead th{};
+            th.q = qi;
+            if (qi >= a.total_tiles) return th;
+            th.tile = tile_at(a, qi * a.shard_count + a.shard_index);
+            th.start = a.ranges[2 * th.tile];
+            const uint32_t stop = a.ranges[2 * th.tile + 1];
+            th.len = stop > th.start ? (int)(stop - th.start) : 0;
+            th.vview = view_of(a, th.tile);
+            const ViewDesc vd = a.views[th.vview];
+            const int lt = th.tile - vd.tile_begin;
+            const int x0 = (lt % vd.tiles_x) * kTile, y0 = (lt / vd.tiles_x) * kTile;
+            th.xc = (float)x0 + (origin ? 0.5f : 8.0f);
+            th.yc_up = (float)y0 + (origin ? 0.5f : 4.0f);
+            // largest n_contrib and |dL/dimage| over the tile's pixels
+            int maxnc = 0;
+            float gmax = 0.f;
+            const size_t plane = (size_t)vd.W * vd.H;
+            for (int p = lane; p < kTilePixels; p += 32) {
+                const int px = x0 + (p & 15), py = y0 + (p >> 4);
+                if (px < vd.W && py < vd.H) {
+                    const size_t pp = (size_t)py * vd.W + px;
+                    maxnc = max(maxnc, gr.n_contrib[vd.pix_off + pp]);
+                    const float* dl = gr.dL_dimage + 3 * vd.pix_off + pp;
+                    gmax = fmaxf(gmax, fmaxf(fabsf(dl[0]), fmaxf(fabsf(dl[plane]), fabsf(dl[2 * plane]))));
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                maxnc = max(maxnc, __shfl_xor_sync(0xffffffffu, maxnc, o));
+                gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+            }
+            maxnc = min(maxnc, th.len);
+            th.nch = (maxnc + CH - 1) / CH;
+            // 2^E <= gmax < 2^(E + 1), E clamped so that every scale is a normal float
+            int E = 0;
+            if (gmax > 0.f) E = ((__float_as_int(gmax) >> 23) & 0xff) - 127;
+            E = max(-100, min(100, E));
+            th.hd.gscale = __int_as_float((127 - E - 12) << 23);
+            th.hd.bscale = __int_as_float((127 - E) << 23);
+            th.hd.undp = __int_as_float((127 + E) << 23);
+            th.hd.uncol = __int_as_float((127 + E - 12) << 23);
+            return th;
+        };
         int k = 0;
         bool quit = false;
+        int q_next = 0;
+        if (lane == 0) q_next = (int)atomicAdd(a.queue, 1u);
+        TileHead nxt = head(__shfl_sync(0xffffffffu, q_next, 0));
         for (int seq = 0; !quit; ++seq) {
-            int qi = 0;
-            if (lane == 0) qi = (int)atomicAdd(a.queue, 1u);
-            qi = __shfl_sync(0xffffffffu, qi, 0);
-            const bool end = qi >= a.total_tiles;
-            int tile = 0, len = 0, vview = 0, nch = 0;
-            uint32_t start = 0;
-            float xc = 0.f, yc_up = 0.f;
-            BwdHdr hd{};
-            if (!end) {
-                tile = tile_at(a, qi * a.shard_count + a.shard_index);
-                start = a.ranges[2 * tile];
-                const uint32_t stop = a.ranges[2 * tile + 1];
-                len = stop > start ? (int)(stop - start) : 0;
-                vview = view_of(a, tile);
-                const ViewDesc vd = a.views[vview];
-                const int lt = tile - vd.tile_begin;
-                const int x0 = (lt % vd.tiles_x) * kTile, y0 = (lt / vd.tiles_x) * kTile;
-                xc = (float)x0 + (origin ? 0.5f : 8.0f);
-                yc_up = (float)y0 + (origin ? 0.5f : 4.0f);
-                // largest n_contrib and |dL/dimage| over the tile's pixels
-                int maxnc = 0;
-                float gmax = 0.f;
-                const size_t plane = (size_t)vd.W * vd.H;
-                for (int p = lane; p < kTilePixels; p += 32) {
-                    const int px = x0 + (p & 15), py = y0 + (p >> 4);
-                    if (px < vd.W && py < vd.H) {
-                        const size_t pp = (size_t)py * vd.W + px;
-                        maxnc = max(maxnc, gr.n_contrib[vd.pix_off + pp]);
-                        const float* dl = gr.dL_dimage + 3 * vd.pix_off + pp;
-                        gmax = fmaxf(gmax, fmaxf(fabsf(dl[0]), fmaxf(fabsf(dl[plane]), fabsf(dl[2 * plane]))));
-                    }
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    maxnc = max(maxnc, __shfl_xor_sync(0xffffffffu, maxnc, o));
-                    gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
-                }
-                maxnc = min(maxnc, len);
-                nch = (maxnc + CH - 1) / CH;
-                // 2^E <= gmax < 2^(E + 1), E clamped so that every scale is a normal float
-                int E = 0;
-                if (gmax > 0.f) E = ((__float_as_int(gmax) >> 23) & 0xff) - 127;
-                E = max(-100, min(100, E));
-                hd.gscale = __int_as_float((127 - E - 12) << 23);
-                hd.bscale = __int_as_float((127 - E) << 23);
-                hd.undp = __int_as_float((127 + E) << 23);
-                hd.uncol = __int_as_float((127 + E - 12) << 23);
-            }
+            const TileHead cur = nxt;
+            const bool end = cur.q >= a.total_tiles;
+            if (!end && lane == 0) q_next = (int)atomicAdd(a.queue, 1u);  // read after this tile's first stage
+            const int tile = cur.tile, len = cur.len, vview = cur.vview, nch = cur.nch;
+            const uint32_t start = cur.start;
+            const float xc = cur.xc, yc_up = cur.yc_up;
+            BwdHdr hd = cur.hd;
             const int nst = end ? 1 : max(1, nch);
             const float bx0 = origin ? -15.0f : -7.5f, bx1 = origin ? 0.0f : 7.5f;
             const float by0 = origin ? -7.0f : -3.5f, by1 = origin ? 0.0f : 3.5f;
@@ -566,6 +589,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar_full(s));
                 ++k;
+                if (cc == 0 && !end) nxt = head(__shfl_sync(0xffffffffu, q_next, 0));  // the next tile's header
             }
             if (end) quit = true;
         }
@@ -632,11 +656,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
     if (warp == 5) tmem_dealloc(tmem, LY::TCOLS);
 }
 
-template <int V>
+template <int V, int SS>
 cudaError_t launch_bwd_inst(const BlendArgs& a, const GradArgs& g, cudaStream_t s) {
-    using LY = BwdLayout<kBwdStages, V>;
+    using LY = BwdLayout<SS, V>;
     constexpr int bytes = LY::BYTES;
-    auto kern = k_blend_tc_bwd<V, kBwdStages>;
+    auto kern = k_blend_tc_bwd<V, SS>;
     static std::mutex mu;
     static LaunchShape cache;
     LaunchShape sh;
@@ -674,19 +698,29 @@ cudaError_t launch_bwd_inst(const BlendArgs& a, const GradArgs& g, cudaStream_t 
     return cudaGetLastError();
 }
 
+// stages 0: the variant's default; otherwise one of kBwdStagesBuilt
+template <int V>
+cudaError_t launch_bwd_stages(const BlendArgs& a, const GradArgs& g, int stages, cudaStream_t s) {
+    if (stages == 0) stages = bwd_default_stages<V>();
+    if (stages == 2) return launch_bwd_inst<V, 2>(a, g, s);
+    if (stages == 4) return launch_bwd_inst<V, 4>(a, g, s);
+    if (stages == 6) return launch_bwd_inst<V, 6>(a, g, s);
+    return cudaErrorInvalidValue;
+}
+
 // Instantiated per variant in blend_tc_bwd_v<V>.cu
 template <int V>
-cudaError_t launch_bwd_variant(const BlendArgs& a, const GradArgs& g, cudaStream_t s);
+cudaError_t launch_bwd_variant(const BlendArgs& a, const GradArgs& g, int stages, cudaStream_t s);
 template <>
-cudaError_t launch_bwd_variant<1>(const BlendArgs&, const GradArgs&, cudaStream_t);
+cudaError_t launch_bwd_variant<1>(const BlendArgs&, const GradArgs&, int, cudaStream_t);
 template <>
-cudaError_t launch_bwd_variant<2>(const BlendArgs&, const GradArgs&, cudaStream_t);
+cudaError_t launch_bwd_variant<2>(const BlendArgs&, const GradArgs&, int, cudaStream_t);
 template <>
-cudaError_t launch_bwd_variant<3>(const BlendArgs&, const GradArgs&, cudaStream_t);
+cudaError_t launch_bwd_variant<3>(const BlendArgs&, const GradArgs&, int, cudaStream_t);
 template <>
-cudaError_t launch_bwd_variant<4>(const BlendArgs&, const GradArgs&, cudaStream_t);
+cudaError_t launch_bwd_variant<4>(const BlendArgs&, const GradArgs&, int, cudaStream_t);
 template <>
-cudaError_t launch_bwd_variant<5>(const BlendArgs&, const GradArgs&, cudaStream_t);
+cudaError_t launch_bwd_variant<5>(const BlendArgs&, const GradArgs&, int, cudaStream_t);
 
 }  // namespace tc
 }  // namespace gs

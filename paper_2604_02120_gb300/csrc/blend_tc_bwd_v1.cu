@@ -5,8 +5,8 @@ namespace gs {
 namespace tc {
 
 template <>
-cudaError_t launch_bwd_variant<1>(const BlendArgs& a, const GradArgs& g, cudaStream_t s) {
-    return launch_bwd_inst<1>(a, g, s);
+cudaError_t launch_bwd_variant<1>(const BlendArgs& a, const GradArgs& g, int stages, cudaStream_t s) {
+    return launch_bwd_stages<1>(a, g, stages, s);
 }
 
 }  // namespace tc

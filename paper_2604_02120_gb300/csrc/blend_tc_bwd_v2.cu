@@ -5,8 +5,8 @@ namespace gs {
 namespace tc {
 
 template <>
-cudaError_t launch_bwd_variant<2>(const BlendArgs& a, const GradArgs& g, cudaStream_t s) {
-    return launch_bwd_inst<2>(a, g, s);
+cudaError_t launch_bwd_variant<2>(const BlendArgs& a, const GradArgs& g, int stages, cudaStream_t s) {
+    return launch_bwd_stages<2>(a, g, stages, s);
 }
 
 }  // namespace tc

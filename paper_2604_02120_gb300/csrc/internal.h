@@ -163,6 +163,10 @@ struct SortViews {
     // opacity-aware tile lists when both are set: conic per item, power_min per Gaussian
     const float* conic;
     const float* power_min;
+    // supertiles (4 x 4 tiles) of each view, numbered [st_begin[v], st_begin[v] +
+    // st_x[v] * ceil(tiles_y / 4)) in one space of total_st (filled by bin_sort_run)
+    int st_begin[kMaxViews], st_x[kMaxViews];
+    int total_st;
 };
 
 size_t bin_sort_workspace_bytes(int n_items, int64_t capacity, int num_tiles);
@@ -182,7 +186,8 @@ cudaError_t launch_blend_tc(const BlendArgs& a, int variant, int chunk, int stag
 bool tc_config_supported(int variant, int chunk, int stages);
 // Gradient of the tensor-core blend of `variant` (exponents recomputed with the
 // forward pass's tensor-core arithmetic).
-cudaError_t launch_blend_tc_bwd(const BlendArgs& a, const GradArgs& g, int variant, cudaStream_t s);
+cudaError_t launch_blend_tc_bwd(const BlendArgs& a, const GradArgs& g, int variant, int stages, cudaStream_t s);
+bool tc_bwd_stages_supported(int stages);
 // A zeroed tile-queue counter for one persistent launch on stream s.
 unsigned* tile_queue_slot(cudaStream_t s, cudaError_t* err);
 

@@ -20,11 +20,25 @@
 // B^2 is recovered exactly by an FMA and added back), accurate to a few units
 // in the last place of det itself: the plain float32 difference cancels to
 // zero or below for needle-shaped splats and would keep their whole
-// rectangle.  FP32 throughout, rounding per operation in a fixed order (no
-// contraction).  A <= 0 or C <= 0: whole rows; tau2 <= 0: no tile.
+// rectangle.  FP32 throughout in a fixed order (no contraction); square
+// roots and quotients use the hardware's approximate instructions (a few
+// units in the last place, far inside the margin power_min carries), so the
+// rule is deterministic and every kernel that applies it decides alike.
+// A <= 0 or C <= 0: whole rows; tau2 <= 0: no tile.
 #pragma once
 
 namespace gs {
+
+__device__ __forceinline__ float tight_sqrt(float x) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float tight_div(float a, float b) {
+    float y;
+    asm("div.approx.f32 %0, %1, %2;" : "=f"(y) : "f"(a), "f"(b));
+    return y;
+}
 
 struct TightRows {
     int mode;  // 0: whole rows, 1: no tile, 2: ellipse (det > 0), 3: det <= 0
@@ -43,12 +57,12 @@ __device__ __forceinline__ TightRows tight_rows(float mx, float my, float A, flo
     t.nB = -B;
     t.det = det;
     t.Atau = __fmul_rn(A, tau2);
-    t.rA = __fdiv_rn(1.0f, A);
+    t.rA = tight_div(1.0f, A);
     if (det > 0.f) {
         t.mode = 2;
-        t.ymax = __fsqrt_rn(__fdiv_rn(__fmul_rn(tau2, A), det));
+        t.ymax = tight_sqrt(tight_div(__fmul_rn(tau2, A), det));
         // -(B/C) x_max = -B sqrt(tau2 / (C det)); 0 for B = 0 even if the root overflows
-        t.dyr = (B == 0.f) ? 0.f : __fmul_rn(-B, __fsqrt_rn(__fdiv_rn(tau2, __fmul_rn(C, det))));
+        t.dyr = (B == 0.f) ? 0.f : __fmul_rn(-B, tight_sqrt(tight_div(tau2, __fmul_rn(C, det))));
     } else {
         t.mode = 3;
         t.ymax = __int_as_float(0x7f800000);  // +inf: the form is unbounded along its null line
@@ -58,7 +72,7 @@ __device__ __forceinline__ TightRows tight_rows(float mx, float my, float A, flo
 
 // Right (sign +1) or left (sign -1) end of E's x-extent on the line dy = y.
 __device__ __forceinline__ float tight_end(const TightRows& t, float y, float sign) {
-    const float s = __fsqrt_rn(fmaxf(__fsub_rn(t.Atau, __fmul_rn(t.det, __fmul_rn(y, y))), 0.f));
+    const float s = tight_sqrt(fmaxf(__fsub_rn(t.Atau, __fmul_rn(t.det, __fmul_rn(y, y))), 0.f));
     return __fmul_rn(__fadd_rn(__fmul_rn(t.nB, y), sign * s), t.rA);
 }
 

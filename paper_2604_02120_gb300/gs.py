@@ -18,10 +18,12 @@ LIB_PATH = os.path.join(HERE, "libgs.so")
 
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CUDA, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, GS_ERR_UNSUPPORTED, GS_ERR_WORKSPACE = range(7)
 (GS_BLEND_FP32, GS_BLEND_TC_FP16, GS_BLEND_TC_BF16, GS_BLEND_TC_FP16_SPLIT, GS_BLEND_TC_BF16_SPLIT,
- GS_BLEND_TC_FP8_SPLIT) = range(6)
+ GS_BLEND_TC_FP8_SPLIT, GS_BLEND_PERSISTENT_FP32) = range(7)
 VARIANTS = {
     "fp32": GS_BLEND_FP32, "fp16": GS_BLEND_TC_FP16, "bf16": GS_BLEND_TC_BF16,
     "fp16_split": GS_BLEND_TC_FP16_SPLIT, "bf16_split": GS_BLEND_TC_BF16_SPLIT, "fp8_split": GS_BLEND_TC_FP8_SPLIT,
+    # the tensor-core kernel with the exponent contraction on CUDA cores (forward only)
+    "fp32_persistent": GS_BLEND_PERSISTENT_FP32,
 }
 
 # Entry points declared in include/gs.h
@@ -31,7 +33,7 @@ ABI_FUNCTIONS = (
     "gs_selftest_bounded_wait", "gs_launch_count", "gs_bin_sort_noalloc", "gs_bin_sort_noalloc_max_bytes",
     "gs_project_views", "gs_bin_sort_views", "gs_blend_forward_views", "gs_blend_backward_views",
     "gs_blend_autotune", "gs_measure_peaks", "gs_alpha_power_min", "gs_project_backward",
-    "gs_project_bin_small", "gs_tile_order", "gs_pack_splats",
+    "gs_project_bin_small", "gs_tile_order", "gs_pack_splats", "gs_blend_autotune_backward",
 )
 
 
@@ -54,7 +56,7 @@ class gs_camera(ctypes.Structure):
 
 class gs_blend_opts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("chunk", ctypes.c_int32), ("stages", ctypes.c_int32),
-                ("ref_origin", ctypes.c_int32), ("bg", ctypes.c_float * 3), ("reserved", ctypes.c_int32),
+                ("ref_origin", ctypes.c_int32), ("bg", ctypes.c_float * 3), ("bwd_stages", ctypes.c_int32),
                 ("timeout_ns", ctypes.c_int64), ("shard_count", ctypes.c_int32), ("shard_index", ctypes.c_int32),
                 ("tile_order", ctypes.c_void_p), ("issued_pairs", ctypes.c_void_p),
                 ("splat_records", ctypes.c_void_p), ("splat_record_count", ctypes.c_int64)]
@@ -103,6 +105,9 @@ def load(path: str = LIB_PATH):
                                             ctypes.POINTER(gs_blend_opts), vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gs_blend_autotune.argtypes = [i32, i32p, i32p, i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(gs_blend_opts),
                                       vp, vp, vp, i32, ctypes.POINTER(ctypes.c_float), vp]
+    lib.gs_blend_autotune_backward.argtypes = [i32, i32p, i32p, i32, vp, vp, vp, vp, vp, vp,
+                                               ctypes.POINTER(gs_blend_opts), vp, vp, vp, vp, vp, vp, vp, i32,
+                                               ctypes.POINTER(ctypes.c_float), vp]
     lib.gs_sync_status.argtypes = [vp]
     lib.gs_selftest_bounded_wait.argtypes = [i64, vp]
     lib.gs_measure_peaks.argtypes = [ctypes.POINTER(gs_peaks), vp]
@@ -147,14 +152,14 @@ def make_camera(cam) -> gs_camera:
 
 
 def make_opts(variant="fp32", chunk=0, stages=0, ref_origin=0, bg=(0.0, 0.0, 0.0), timeout_ns=0, shard_count=0,
-              shard_index=0, tile_order=None, issued_pairs=None, splat_records=None) -> gs_blend_opts:
+              shard_index=0, tile_order=None, issued_pairs=None, splat_records=None, bwd_stages=0) -> gs_blend_opts:
     """Blend options; tile_order (a device tensor from tile_order(), kept
     alive by the caller while the options are used) makes the kernels take
     the longest tile lists first; splat_records (from pack_splats, kept alive
     likewise) makes the tensor-core kernels stage splats by TMA gathers."""
     o = gs_blend_opts()
     o.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
-    o.chunk, o.stages, o.ref_origin = int(chunk), int(stages), int(ref_origin)
+    o.chunk, o.stages, o.ref_origin, o.bwd_stages = int(chunk), int(stages), int(ref_origin), int(bwd_stages)
     for i in range(3):
         o.bg[i] = float(bg[i])
     o.timeout_ns = int(timeout_ns)
@@ -356,6 +361,22 @@ def gs_blend_autotune(widths, heights, n_per_view, tile_ranges, ids_sorted, mean
                                     _ptr(ids_sorted), _ptr(mean2d), _ptr(conic), _ptr(opacity), _ptr(rgb),
                                     ctypes.byref(opts), _ptr(image), _ptr(T_final), _ptr(n_contrib), int(reps),
                                     ctypes.byref(best), _stream(stream)), "gs_blend_autotune")
+    return float(best.value)
+
+
+def gs_blend_autotune_backward(widths, heights, n_per_view, tile_ranges, ids_sorted, mean2d, conic, opacity, rgb,
+                               opts, T_final, n_contrib, dL_dimage, grads, reps=5, stream=None) -> float:
+    """Sets opts.bwd_stages to the fastest built ring depth of the tensor-core
+    backward; `grads` (mean2d, conic, opacity, rgb buffers) are overwritten
+    with unspecified values.  Returns the best ms."""
+    best = ctypes.c_float(0.0)
+    _check(load().gs_blend_autotune_backward(len(widths), _i32arr(widths), _i32arr(heights), n_per_view,
+                                             _ptr(tile_ranges), _ptr(ids_sorted), _ptr(mean2d), _ptr(conic),
+                                             _ptr(opacity), _ptr(rgb), ctypes.byref(opts), _ptr(T_final),
+                                             _ptr(n_contrib), _ptr(dL_dimage), _ptr(grads["mean2d"]),
+                                             _ptr(grads["conic"]), _ptr(grads["opacity"]), _ptr(grads["rgb"]),
+                                             int(reps), ctypes.byref(best), _stream(stream)),
+           "gs_blend_autotune_backward")
     return float(best.value)
 
 

@@ -35,6 +35,9 @@ MARGINS = {
 
 
 def margins(variant):
+    """The rounding model of a variant: the FP32 CUDA-core blend, or the Eq. 6
+    contraction with FP32 accumulation (split tensor-core operands, or FP32
+    FMAs in the persistent kernel), or the FP8 trial."""
     return MARGINS.get(variant, MARGINS["split"])
 
 

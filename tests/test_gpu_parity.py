@@ -407,6 +407,26 @@ def test_pack_splats_layout():
     assert (rec[:, 12:] == 0).all()
 
 
+@pytest.mark.parametrize("kind", ["256x256_10k", "tiny_ragged", "tiny_dense", "1280x720_200k"])
+def test_persistent_fp32_matches_oracle(kind):
+    """The tensor-core kernel with the exponent v_g . v_p taken by FP32 FMAs on
+    the CUDA cores (no MMA): FP32 colours within 1e-4 (plus the rounding
+    bound) of the oracle, n_contrib exact, for every pipeline shape; its
+    backward is refused."""
+    sc, dev, cam, proj, bs, pn, bn = pipeline(kind)
+    bg = (0.05, 0.1, 0.15)
+    ref = oracle_blend_on_gpu_params(cam, pn, bn, sc.opacities, bg=bg, variant="fp32_persistent")
+    for chunk, stages in [(32, 2), (16, 6)]:
+        out = blend_gpu(cam, proj, bs, dev["opacities"], "fp32_persistent", bg=bg, chunk=chunk, stages=stages)
+        err = _compare(out, ref, 1e-4, max_amb=MAX_AMB_SPLIT)
+    report(f"blend_fp32_persistent_{kind}", {"max_abs": float(err.max()), "ambiguous": float(ref["ambiguous"].mean())})
+    o = gs.make_opts("fp32_persistent")
+    fwd = gs.blend_forward(cam.width, cam.height, bs, proj, dev["opacities"], o)
+    with pytest.raises(gs.GsError):
+        gs.blend_backward(cam.width, cam.height, bs, proj, dev["opacities"], o, fwd,
+                          torch.zeros(3, cam.height, cam.width, device="cuda"))
+
+
 def test_blend_tc_chunk_and_stage_invariant():
     """Pipeline shape does not change a single bit of the tensor-core result."""
     sc, dev, cam, proj, bs, pn, bn = pipeline("tiny_dense")
@@ -483,6 +503,32 @@ def test_tc_blend_backward_matches_oracle_gradient(kind, variant):
     bar = 1e-2 if variant == "fp8_split" else 1e-3  # the FP8 trial's exponent is good to 2e-3
     for name, e in rel.items():
         assert e < bar, f"{name}: relative error {e:.2e}"
+
+
+@pytest.mark.parametrize("variant", ["fp16_split", "bf16_split", "fp8_split"])
+def test_tc_backward_ring_depths_agree_and_autotune(variant):
+    """Every built ring depth of the tensor-core backward (bwd_stages 2, 4, 6
+    and the variant's default) gives the same gradients up to the order of
+    atomic additions, and gs_blend_autotune_backward picks a built depth."""
+    sc, dev, cam, proj, bs, pn, bn = pipeline("1280x720_20k")
+    opts = gs.make_opts(variant, bg=(0.1, 0.2, 0.3))
+    fwd = gs.blend_forward(cam.width, cam.height, bs, proj, dev["opacities"], opts)
+    dL = torch.randn(3, cam.height, cam.width, device="cuda", generator=torch.Generator("cuda").manual_seed(2))
+    ref = gs.blend_backward(cam.width, cam.height, bs, proj, dev["opacities"], opts, fwd, dL)
+    for st in (2, 4, 6):
+        o = gs.make_opts(variant, bg=(0.1, 0.2, 0.3), bwd_stages=st)
+        g = gs.blend_backward(cam.width, cam.height, bs, proj, dev["opacities"], o, fwd, dL)
+        assert gs.gs_sync_status() == gs.GS_OK
+        for k in ref:
+            torch.testing.assert_close(g[k], ref[k], rtol=1e-4, atol=1e-6 * float(ref[k].abs().max()))
+    scratch = {k: torch.empty_like(v) for k, v in ref.items()}
+    ms = gs.gs_blend_autotune_backward([cam.width], [cam.height], 0, bs["tile_ranges"], bs["ids"], proj["mean2d"],
+                                       proj["conic"], dev["opacities"], proj["rgb"], opts, fwd["T_final"],
+                                       fwd["n_contrib"], dL, scratch, reps=2)
+    assert ms > 0 and opts.bwd_stages in (2, 4, 6)
+    with pytest.raises(gs.GsError):
+        gs.blend_backward(cam.width, cam.height, bs, proj, dev["opacities"], gs.make_opts(variant, bwd_stages=3),
+                          fwd, dL)
 
 
 @pytest.mark.parametrize("variant", ["fp16_split", "fp16"])
