@@ -246,82 +246,88 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint32_t* __rest
     __shared__ uint32_t s_key[TILE], s_val[TILE];
     const uint32_t n = pass_count(n_host, n_dev);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_tile = atomicAdd(&tickets[pass_id], 1u);
-    for (int i = threadIdx.x; i < (kThreads / 32) * 256; i += kThreads) (&s_w[0][0])[i] = 0;
-    __syncthreads();
-    const uint32_t tile = s_tile;
-    const int64_t bbase = (int64_t)tile * TILE;
-    if (bbase >= n) return;  // uniform over the block; no later tile is needed either
-    const int cnt = (int)((int64_t)n - bbase < TILE ? (int64_t)n - bbase : TILE);
-    const int wbase = warp * (ITEMS * 32);
-    uint32_t k[ITEMS], v[ITEMS];
+    // persistent: the block takes tiles until the pass is done (a tile's
+    // look-back waits only on tiles ticketed before it, which blocks are
+    // already processing)
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&tickets[pass_id], 1u);
+        for (int i = threadIdx.x; i < (kThreads / 32) * 256; i += kThreads) (&s_w[0][0])[i] = 0;
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        const int64_t bbase = (int64_t)tile * TILE;
+        if (bbase >= n) return;  // uniform over the block; no later tile is needed either
+        const int cnt = (int)((int64_t)n - bbase < TILE ? (int64_t)n - bbase : TILE);
+        const int wbase = warp * (ITEMS * 32);
+        uint32_t k[ITEMS], v[ITEMS];
 #pragma unroll
-    for (int r = 0; r < ITEMS; ++r) {
-        const int i = wbase + r * 32 + lane;
-        k[r] = i < cnt ? kin[bbase + i] : 0u;
-        v[r] = i < cnt ? vin[bbase + i] : 0u;
-    }
-    const unsigned lt = (1u << lane) - 1u;
-#pragma unroll
-    for (int r = 0; r < ITEMS; ++r) {
-        const bool valid = wbase + r * 32 + lane < cnt;
-        const uint32_t d = (k[r] >> shift) & 0xFFu;
-        const unsigned peers = digit_peers<FULL>(d, valid);
-        if (valid && (peers & lt) == 0) s_w[warp][d] += __popc(peers);
-        __syncwarp();
-    }
-    __syncthreads();
-    {
-        const int d = threadIdx.x;
-        uint32_t c = 0;
-#pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) c += s_w[w][d];
-        unsigned long long* mine = status + (size_t)tile * 256 + d;
-        const uint32_t tag_agg = 2u * pass_id + 1u;
-        st_status(mine, tile == 0 ? tag_agg + 1 : tag_agg, c);  // publish first, successors may be waiting
-        uint32_t total;
-        const uint32_t db = block_excl_scan<uint32_t, kThreads>(c, total, s_warp);
-        const uint32_t gstart = block_excl_scan<uint32_t, kThreads>(hist[d], total, s_warp);
-        uint32_t prefix = 0;
-        if (tile > 0) {
-            prefix = (uint32_t)lookback_serial(status, tile, 256, d, tag_agg, err);
-            st_status(mine, tag_agg + 1, prefix + c);
+        for (int r = 0; r < ITEMS; ++r) {
+            const int i = wbase + r * 32 + lane;
+            k[r] = i < cnt ? kin[bbase + i] : 0u;
+            v[r] = i < cnt ? vin[bbase + i] : 0u;
         }
-        s_dbase[d] = db;
-        s_goff[d] = gstart + prefix;
-        uint32_t run = db;
+        const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) {
-            const uint32_t cw = s_w[w][d];
-            s_w[w][d] = run;
-            run += cw;
+        for (int r = 0; r < ITEMS; ++r) {
+            const bool valid = wbase + r * 32 + lane < cnt;
+            const uint32_t d = (k[r] >> shift) & 0xFFu;
+            const unsigned peers = digit_peers<FULL>(d, valid);
+            if (valid && (peers & lt) == 0) s_w[warp][d] += __popc(peers);
+            __syncwarp();
         }
-    }
-    __syncthreads();
+        __syncthreads();
+        {
+            const int d = threadIdx.x;
+            uint32_t c = 0;
 #pragma unroll
-    for (int r = 0; r < ITEMS; ++r) {
-        const bool valid = wbase + r * 32 + lane < cnt;
-        const uint32_t d = (k[r] >> shift) & 0xFFu;
-        const unsigned peers = digit_peers<FULL>(d, valid);
-        uint32_t pos = 0;
-        if (valid) pos = s_w[warp][d] + __popc(peers & lt);
-        __syncwarp();
-        if (valid) {
-            s_key[pos] = k[r];
-            s_val[pos] = v[r];
-            if ((peers & lt) == 0) s_w[warp][d] += __popc(peers);
+            for (int w = 0; w < kThreads / 32; ++w) c += s_w[w][d];
+            unsigned long long* mine = status + (size_t)tile * 256 + d;
+            const uint32_t tag_agg = 2u * pass_id + 1u;
+            st_status(mine, tile == 0 ? tag_agg + 1 : tag_agg, c);  // publish first, successors may be waiting
+            uint32_t total;
+            const uint32_t db = block_excl_scan<uint32_t, kThreads>(c, total, s_warp);
+            const uint32_t gstart = block_excl_scan<uint32_t, kThreads>(hist[d], total, s_warp);
+            uint32_t prefix = 0;
+            if (tile > 0) {
+                prefix = (uint32_t)lookback_serial(status, tile, 256, d, tag_agg, err);
+                st_status(mine, tag_agg + 1, prefix + c);
+            }
+            s_dbase[d] = db;
+            s_goff[d] = gstart + prefix;
+            uint32_t run = db;
+#pragma unroll
+            for (int w = 0; w < kThreads / 32; ++w) {
+                const uint32_t cw = s_w[w][d];
+                s_w[w][d] = run;
+                run += cw;
+            }
         }
-        __syncwarp();
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += kThreads) {
-        const uint32_t key = s_key[i];
-        const uint32_t d = (key >> shift) & 0xFFu;
-        const uint32_t g = s_goff[d] + (uint32_t)i - s_dbase[d];
-        if (g < n) {  // always, unless a look-back gave up (timeout bit set)
-            kout[g] = key;
-            vout[g] = s_val[i];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r) {
+            const bool valid = wbase + r * 32 + lane < cnt;
+            const uint32_t d = (k[r] >> shift) & 0xFFu;
+            const unsigned peers = digit_peers<FULL>(d, valid);
+            uint32_t pos = 0;
+            if (valid) pos = s_w[warp][d] + __popc(peers & lt);
+            __syncwarp();
+            if (valid) {
+                s_key[pos] = k[r];
+                s_val[pos] = v[r];
+                if ((peers & lt) == 0) s_w[warp][d] += __popc(peers);
+            }
+            __syncwarp();
         }
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt; i += kThreads) {
+            const uint32_t key = s_key[i];
+            const uint32_t d = (key >> shift) & 0xFFu;
+            const uint32_t g = s_goff[d] + (uint32_t)i - s_dbase[d];
+            if (g < n) {  // always, unless a look-back gave up (timeout bit set)
+                kout[g] = key;
+                vout[g] = s_val[i];
+            }
+        }
+        __syncthreads();  // shared memory is reused by the next tile
     }
 }
 
@@ -339,7 +345,13 @@ cudaError_t radix_sort(uint32_t* k[2], uint32_t* v[2], uint32_t n_host, const ui
                        int first_pass, const PassScratch& ps, int* which, cudaStream_t s) {
     int cur = 0;
     const int items = pass_items(n_host);
-    const int nblk = (int)cdiv(n_host, (int64_t)kThreads * items);
+    int dev = 0, sms = 0;
+    cudaError_t ea = cudaGetDevice(&dev);
+    if (ea == cudaSuccess) ea = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ea != cudaSuccess) return ea;
+    // persistent blocks: at most 4 per SM (a graph-mode grid sized for the capacity would
+    // otherwise start many blocks that only find the pass done)
+    const int nblk = (int)std::min<int64_t>(cdiv(n_host, (int64_t)kThreads * items), 4 * (int64_t)sms);
     for (int p = 0, shift = 0; shift < bits; ++p, shift += 8) {
         const int id = first_pass + p;
         // ballots unless the digit has at most 4 significant bits (16 values: match_any is cheaper);
@@ -417,21 +429,49 @@ __device__ __forceinline__ int iv_union4(Iv a, Iv b, Iv c, Iv d, F emit) {
     return n + chi - clo + 1;
 }
 
-// The item's supertile columns in supertile row sy (emit per interval; the
-// count is returned) and, in *fine, its instances in those tile rows.
+// The four tile-row runs of one supertile row (f > l: none).
+struct Runs4 {
+    int f[kSuper], l[kSuper];
+};
+
+// The 16-bit mask of supertile column sx within a supertile row's runs: bit
+// 4 k + c for tile (4 sx + c) of the row's k-th tile row.
+__device__ __forceinline__ uint32_t runs_mask(const Runs4& rr, int sx) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < kSuper; ++k) {
+        const int a = max(rr.f[k], sx * kSuper), b = min(rr.l[k], sx * kSuper + kSuper - 1);
+        if (a <= b) m |= ((1u << (b - a + 1)) - 1u) << (k * kSuper + a - sx * kSuper);
+    }
+    return m;
+}
+
+// The item's supertile columns in supertile row sy (emit(lo, hi, runs) per
+// interval; the count is returned) and, in *fine, its instances in those
+// tile rows.
 template <bool TIGHT, class F>
 __device__ __forceinline__ int supertile_row(const TightRows& t, int sy, int x0, int x1, int y0, int y1,
                                              uint32_t* fine, F emit) {
+    Runs4 rr;
     if constexpr (!TIGHT) {
+#pragma unroll
+        for (int k = 0; k < kSuper; ++k) {
+            const int y = sy * kSuper + k;
+            const bool in = y >= y0 && y <= y1;
+            rr.f[k] = in ? x0 : 1;
+            rr.l[k] = in ? x1 : 0;
+        }
         const int rows = min(y1, sy * kSuper + kSuper - 1) - max(y0, sy * kSuper) + 1;
         *fine += (uint32_t)(rows * (x1 - x0 + 1));
-        emit(x0 / kSuper, x1 / kSuper);
+        emit(x0 / kSuper, x1 / kSuper, rr);
         return x1 / kSuper - x0 / kSuper + 1;
     } else {
         Iv r[kSuper];
 #pragma unroll
         for (int k = 0; k < kSuper; ++k) {
             r[k] = Iv{0x7fffffff, -1};
+            rr.f[k] = 1;
+            rr.l[k] = 0;
             const int y = sy * kSuper + k;
             if (y >= y0 && y <= y1) {
                 int f, l;
@@ -439,10 +479,12 @@ __device__ __forceinline__ int supertile_row(const TightRows& t, int sy, int x0,
                 if (f <= l) {
                     *fine += (uint32_t)(l - f + 1);
                     r[k] = Iv{f / kSuper, l / kSuper};
+                    rr.f[k] = f;
+                    rr.l[k] = l;
                 }
             }
         }
-        return iv_union4(r[0], r[1], r[2], r[3], emit);
+        return iv_union4(r[0], r[1], r[2], r[3], [&](int lo, int hi) { emit(lo, hi, rr); });
     }
 }
 
@@ -513,7 +555,7 @@ __global__ void __launch_bounds__(kThreads) k_count(int n_items, const __grid_co
                 tall = y1 / kSuper - y0 / kSuper + 1 > kTallRows;
                 if (!tall)
                     for (int sy = y0 / kSuper; sy <= y1 / kSuper; ++sy)
-                        c += (uint32_t)supertile_row<TIGHT>(t, sy, x0, x1, y0, y1, &fine, [](int, int) {});
+                        c += (uint32_t)supertile_row<TIGHT>(t, sy, x0, x1, y0, y1, &fine, [](int, int, const Runs4&) {});
             }
             if (!tall) cnt[i] = c;
             dkey[i] = key[q];
@@ -531,7 +573,7 @@ __global__ void __launch_bounds__(kThreads) k_count(int n_items, const __grid_co
             const TightRows bt = shfl_rows(t, src);
             uint32_t c = 0;
             for (int sy = by0 / kSuper + lane; sy <= by1 / kSuper; sy += 32)
-                c += (uint32_t)supertile_row<TIGHT>(bt, sy, bx0, bx1, by0, by1, &fine, [](int, int) {});
+                c += (uint32_t)supertile_row<TIGHT>(bt, sy, bx0, bx1, by0, by1, &fine, [](int, int, const Runs4&) {});
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
             if (lane == src) cnt[i] = c;
@@ -579,7 +621,7 @@ __global__ void __launch_bounds__(kThreads) k_dup_coarse(int n_items, const uint
                                                          const __grid_constant__ SortViews sv,
                                                          const float2* __restrict__ mean2d,
                                                          const int* __restrict__ radius, uint64_t limit, int passes,
-                                                         uint32_t* tickets, unsigned long long* status,
+                                                         bool pack, uint32_t* tickets, unsigned long long* status,
                                                          uint32_t* __restrict__ ckey, uint32_t* __restrict__ cval,
                                                          uint32_t* __restrict__ hist, uint64_t* __restrict__ total,
                                                          unsigned* err) {
@@ -633,13 +675,13 @@ __global__ void __launch_bounds__(kThreads) k_dup_coarse(int n_items, const uint
     // the pairs of supertile row sy at position p (written below `limit`); returns their count
     auto write_row = [&](int sy, uint64_t p, uint32_t it) -> int {
         uint32_t fine = 0;
-        return supertile_row<TIGHT>(t, sy, x0, x1, y0, y1, &fine, [&](int lo, int hi) {
+        return supertile_row<TIGHT>(t, sy, x0, x1, y0, y1, &fine, [&](int lo, int hi, const Runs4& rr) {
             const uint32_t k0 = (uint32_t)stb + (uint32_t)sy * (uint32_t)stx + (uint32_t)lo;
             const uint32_t len = (uint32_t)(hi - lo + 1);
             if (p < limit) {
                 const uint32_t nw = (uint32_t)min((uint64_t)len, limit - p);
                 for (uint32_t j = 0; j < nw; ++j) {
-                    ckey[p + j] = k0 + j;
+                    ckey[p + j] = (k0 + j) | (pack ? runs_mask(rr, lo + (int)j) << 16 : 0u);
                     cval[p + j] = it;
                 }
                 row_hist(k0, nw, passes, s_d0, s_h);
@@ -666,7 +708,7 @@ __global__ void __launch_bounds__(kThreads) k_dup_coarse(int n_items, const uint
             const int sy = sb + lane;
             uint32_t fine = 0;
             const int n_row = sy <= by1 / kSuper
-                                  ? supertile_row<TIGHT>(bt, sy, bx0, bx1, by0, by1, &fine, [](int, int) {}) : 0;
+                                  ? supertile_row<TIGHT>(bt, sy, bx0, bx1, by0, by1, &fine, [](int, int, const Runs4&) {}) : 0;
             uint32_t incl = (uint32_t)n_row;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
@@ -676,13 +718,13 @@ __global__ void __launch_bounds__(kThreads) k_dup_coarse(int n_items, const uint
             const uint32_t rows_total = __shfl_sync(0xffffffffu, incl, 31);
             if (n_row > 0) {
                 uint64_t p = pos + (incl - (uint32_t)n_row);
-                supertile_row<TIGHT>(bt, sy, bx0, bx1, by0, by1, &fine, [&](int lo, int hi) {
+                supertile_row<TIGHT>(bt, sy, bx0, bx1, by0, by1, &fine, [&](int lo, int hi, const Runs4& rr) {
                     const uint32_t k0 = (uint32_t)bstb + (uint32_t)sy * (uint32_t)bstx + (uint32_t)lo;
                     const uint32_t len = (uint32_t)(hi - lo + 1);
                     if (p < limit) {
                         const uint32_t nw = (uint32_t)min((uint64_t)len, limit - p);
                         for (uint32_t j = 0; j < nw; ++j) {
-                            ckey[p + j] = k0 + j;
+                            ckey[p + j] = (k0 + j) | (pack ? runs_mask(rr, lo + (int)j) << 16 : 0u);
                             cval[p + j] = bi;
                         }
                         row_hist(k0, nw, passes, s_d0, s_h);
@@ -704,12 +746,13 @@ __global__ void __launch_bounds__(kThreads) k_dup_coarse(int n_items, const uint
         if (s_h[i]) atomicAdd(&hist[256 + i], s_h[i]);
 }
 
-// First position of key >= want in the ascending keys[0, n).
-__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__ keys, uint32_t n, uint32_t want) {
+// First position of key >= want in keys[0, n), ascending in (key & kmask).
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__ keys, uint32_t n, uint32_t want,
+                                                    uint32_t kmask) {
     uint32_t lo = 0, hi = n;
     while (lo < hi) {
         const uint32_t mid = lo + ((hi - lo) >> 1);
-        if (keys[mid] < want) lo = mid + 1;
+        if ((keys[mid] & kmask) < want) lo = mid + 1;
         else hi = mid;
     }
     return lo;
@@ -743,33 +786,83 @@ __device__ __forceinline__ uint32_t supertile_mask(const SortViews& sv, const fl
     return mask;
 }
 
-// One block per supertile s: its items are the sorted pairs [cs, ce) with key
-// s.  WRITE = false: each pair's 16-bit tile mask (into masks[]) and the
-// instance count of each of the supertile's tiles (into ranges[2 t + 1]),
-// counted per warp with one ballot per tile.  WRITE = true (after
-// k_tile_scan): every instance's id (and key) at its tile's next position, in
-// item order, from the stored masks: rounds of kFineThreads pairs; thread
-// (q, j) places tile j's instances among the round's pairs [16 q, 16 q + 16)
-// into a shared-memory stage of the round's output of each tile, and the block
-// then writes each tile's run with consecutive threads on consecutive ids.
+// Per sorted pair: its 16-bit tile mask (into masks[]), and the instance
+// counts of the supertile's tiles added into ranges[2 t + 1] (cleared by
+// k_count).  The pairs are sorted by supertile, so a warp's lanes mostly share
+// one: lanes are grouped by supertile id, and each group adds its count of
+// each tile with one atomic.
+template <bool TIGHT>
+__global__ void __launch_bounds__(kThreads) k_pair_masks(const __grid_constant__ SortViews sv,
+                                                         const float2* __restrict__ mean2d,
+                                                         const int* __restrict__ radius,
+                                                         const uint32_t* __restrict__ ckey,
+                                                         const uint32_t* __restrict__ cval, uint32_t n_host,
+                                                         const uint64_t* __restrict__ n_dev, uint32_t n_items,
+                                                         bool pack, uint16_t* __restrict__ masks,
+                                                         uint32_t* __restrict__ ranges) {
+    const uint32_t Ic = pass_count(n_host, n_dev);
+    const int lane = threadIdx.x & 31;
+    // a grid of resident size walks the pairs (their count is known only on the device)
+    for (uint32_t b0 = blockIdx.x * kThreads; b0 < Ic; b0 += gridDim.x * kThreads) {
+        const uint32_t e = b0 + threadIdx.x;
+        uint32_t key = 0xffffffffu, m = 0;
+        int v = 0, cx0 = 0, cy0 = 0;
+        if (e < Ic) {
+            key = ckey[e];
+            if (pack) {  // the duplication packed the mask above the supertile id
+                m = key >> 16;
+                key &= 0xFFFFu;
+            }
+            while (v + 1 < sv.num_views && sv.st_begin[v + 1] <= (int)key) ++v;
+            const int ls = (int)key - sv.st_begin[v];
+            cx0 = (ls % sv.st_x[v]) * kSuper;
+            cy0 = (ls / sv.st_x[v]) * kSuper;
+            if (!pack) {
+                const uint32_t it = cval[e];
+                m = it < n_items ? supertile_mask<TIGHT>(sv, mean2d, radius, it, sv.views[v], cx0, cy0) : 0u;
+            }
+            masks[e] = (uint16_t)m;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const bool whole = peers == 0xffffffffu && key != 0xffffffffu;  // the warp shares one supertile
+        const bool leader = lane == __ffs(peers) - 1 && key != 0xffffffffu;
+        const ViewDesc& vd = sv.views[v];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const unsigned b = __ballot_sync(0xffffffffu, (m >> j) & 1u) & peers;
+            // a warp of one supertile: lane j adds tile j's count; mixed warps: each group's leader
+            if ((whole ? lane == j : leader) && b) {
+                const size_t gt = (size_t)vd.tile_begin + (size_t)(cy0 + (j >> 2)) * vd.tiles_x + (size_t)(cx0 + (j & 3));
+                atomicAdd(&ranges[2 * gt + 1], (uint32_t)__popc(b));
+            }
+        }
+    }
+}
+
+// One block per supertile s, after k_tile_scan: its items are the sorted pairs
+// [cs, ce) with key s; every instance's id (and key) goes to its tile's next
+// position, in item order, from the pairs' stored tile masks: rounds of
+// kFineThreads pairs; thread (q, j) places tile j's instances among the
+// round's pairs [16 q, 16 q + 16) into a shared-memory stage of the round's
+// output of each tile, and the block then writes each tile's run with
+// consecutive threads on consecutive ids.
 constexpr int kFineThreads = 256;
-template <bool TIGHT, bool WRITE>
 __global__ void __launch_bounds__(kFineThreads) k_fine(const __grid_constant__ SortViews sv,
                                                        const float2* __restrict__ mean2d,
                                                        const int* __restrict__ radius, const float* __restrict__ depth,
                                                        const uint32_t* __restrict__ ckey,
                                                        const uint32_t* __restrict__ cval, uint32_t n_host,
                                                        const uint64_t* __restrict__ n_dev, uint32_t n_items,
-                                                       uint16_t* __restrict__ masks, uint32_t* __restrict__ ranges,
+                                                       uint32_t kmask, uint16_t* __restrict__ masks,
+                                                       uint32_t* __restrict__ ranges,
                                                        uint32_t* __restrict__ ids_out, uint64_t* __restrict__ keys_out) {
     constexpr int Q = kFineThreads / 16;  // workers per tile
     __shared__ uint32_t s_rng[2];
-    __shared__ uint32_t s_cnt[16];
     __shared__ uint32_t s_beg[16], s_end[16], s_run[16], s_tot[16];
     __shared__ uint16_t s_mask[kFineThreads];
     __shared__ uint32_t s_item[kFineThreads];
     __shared__ uint32_t s_q[Q][16];
-    __shared__ uint32_t s_out[16][kFineThreads];
+    __shared__ uint32_t s_out[16][kFineThreads + 1];  // rows one word apart in bank: 16 tiles written at once
     const int s = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int v = 0;
@@ -779,44 +872,19 @@ __global__ void __launch_bounds__(kFineThreads) k_fine(const __grid_constant__ S
     const int cx0 = (ls % sv.st_x[v]) * kSuper, cy0 = (ls / sv.st_x[v]) * kSuper;
     const int tx = vd.tiles_x, ty = tiles_y(vd.H);
     const uint32_t Ic = pass_count(n_host, n_dev);
-    if (threadIdx.x < 2) s_rng[threadIdx.x] = lower_bound_u32(ckey, Ic, (uint32_t)s + threadIdx.x);
+    if (threadIdx.x < 2) s_rng[threadIdx.x] = lower_bound_u32(ckey, Ic, (uint32_t)s + threadIdx.x, kmask);
     if (threadIdx.x < 16) {
         const int c = cx0 + (threadIdx.x & 3), r = cy0 + (threadIdx.x >> 2);
         const bool ok = c < tx && r < ty;
         const uint32_t gt = (uint32_t)vd.tile_begin + (uint32_t)r * (uint32_t)tx + (uint32_t)c;
-        s_cnt[threadIdx.x] = 0;
         s_run[threadIdx.x] = 0;
-        s_beg[threadIdx.x] = WRITE && ok ? ranges[2 * gt] : 0u;
-        s_end[threadIdx.x] = WRITE && ok ? ranges[2 * gt + 1] : 0u;
+        s_beg[threadIdx.x] = ok ? ranges[2 * gt] : 0u;
+        s_end[threadIdx.x] = ok ? ranges[2 * gt + 1] : 0u;
     }
     __syncthreads();
     const uint32_t cs = s_rng[0], ce = s_rng[1];
     if (cs >= ce) return;
-    if constexpr (!WRITE) {
-        uint32_t mine = 0;  // lane j < 16: this warp's count of tile j
-        // two pairs per thread per step, their items loaded together
-        for (uint32_t b = cs + 64 * warp; b < ce; b += 2 * kFineThreads) {
-            const uint32_t e0 = b + lane, e1 = b + 32 + lane;
-            const uint32_t it0 = e0 < ce ? cval[e0] : 0xffffffffu, it1 = e1 < ce ? cval[e1] : 0xffffffffu;
-            uint32_t m0 = it0 < n_items ? supertile_mask<TIGHT>(sv, mean2d, radius, it0, vd, cx0, cy0) : 0u;
-            uint32_t m1 = it1 < n_items ? supertile_mask<TIGHT>(sv, mean2d, radius, it1, vd, cx0, cy0) : 0u;
-            if (e0 < ce) masks[e0] = (uint16_t)m0;
-            if (e1 < ce) masks[e1] = (uint16_t)m1;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const unsigned bj = __ballot_sync(0xffffffffu, (m0 >> j) & 1u);
-                const unsigned cj = __ballot_sync(0xffffffffu, (m1 >> j) & 1u);
-                if (lane == j) mine += (uint32_t)(__popc(bj) + __popc(cj));
-            }
-        }
-        if (lane < 16 && mine) atomicAdd(&s_cnt[lane], mine);
-        __syncthreads();
-        if (threadIdx.x < 16) {
-            const int c = cx0 + (threadIdx.x & 3), r = cy0 + (threadIdx.x >> 2);
-            if (c < tx && r < ty)
-                ranges[2 * ((size_t)vd.tile_begin + (size_t)r * tx + c) + 1] = s_cnt[threadIdx.x];
-        }
-    } else {
+    {
         const int j = threadIdx.x & 15, q = threadIdx.x >> 4;
         for (uint32_t r0 = cs; r0 < ce; r0 += kFineThreads) {
             const uint32_t e = r0 + threadIdx.x;
@@ -1065,10 +1133,12 @@ gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* ra
     const int st_passes = (st_bits + 7) / 8;
     uint32_t* ck[2] = {U32(L.tk0), U32(L.tk1)};
     uint32_t* cv[2] = {U32(L.tv0), U32(L.tv1)};
+    // up to 2^16 supertiles the pairs' tile masks ride in the key's high half
+    const bool pack = st_bits <= 16;
     auto dup = tight ? k_dup_coarse<true> : k_dup_coarse<false>;
     dup<<<(int)cdiv(n, kDupTile), kThreads, 0, s>>>(n, perm, U32(L.cnt), sv2, mean2d, radius, (uint64_t)capacity,
-                                                    st_passes, tickets, dup_status, ck[0], cv[0], hist + 256 * 4,
-                                                    ctotal, err);
+                                                    st_passes, pack, tickets, dup_status, ck[0], cv[0],
+                                                    hist + 256 * 4, ctotal, err);
     count_launches();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: duplicate");
 
@@ -1078,20 +1148,28 @@ gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* ra
 
     // 5. per-tile counts, tile ranges, then every instance's id at its place
     const int nst = sv2.total_st;
-    auto fine_count = tight ? k_fine<true, false> : k_fine<false, false>;
-    auto fine_write = tight ? k_fine<true, true> : k_fine<false, true>;
     // the pairs' tile masks go to the free half of the pair buffers (2 bytes per pair)
     uint16_t* masks = reinterpret_cast<uint16_t*>(ck[which ^ 1]);
-    fine_count<<<nst, kFineThreads, 0, s>>>(sv2, mean2d, radius, depth, ck[which], cv[which], I_grid, ctotal,
-                                            (uint32_t)n, masks, tile_ranges, nullptr, nullptr);
+    auto pair_masks = tight ? k_pair_masks<true> : k_pair_masks<false>;
+    int pair_grid = 0;  // 8 blocks per SM
+    {
+        int dev = 0, sms = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return cuda_status(e, "gs_bin_sort: device");
+        pair_grid = 8 * sms;
+    }
+    pair_masks<<<(int)std::min<int64_t>(pair_grid, cdiv(I_grid, kThreads)), kThreads, 0, s>>>(
+        sv2, mean2d, radius, ck[which], cv[which], I_grid, ctotal, (uint32_t)n, pack, masks, tile_ranges);
     count_launches();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: tile counts");
     k_tile_scan<<<1, kScanThreads, 0, s>>>(ntiles, tile_ranges, (uint64_t)capacity, fine_total,
                                            graph ? n_instances_dev : nullptr, err);
     count_launches();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: tile ranges");
-    fine_write<<<nst, kFineThreads, 0, s>>>(sv2, mean2d, radius, depth, ck[which], cv[which], I_grid, ctotal,
-                                            (uint32_t)n, masks, tile_ranges, ids_sorted, keys_sorted);
+    k_fine<<<nst, kFineThreads, 0, s>>>(sv2, mean2d, radius, depth, ck[which], cv[which], I_grid, ctotal,
+                                            (uint32_t)n, pack ? 0xFFFFu : 0xFFFFFFFFu, masks, tile_ranges,
+                                            ids_sorted, keys_sorted);
     count_launches();
     return cuda_status(cudaGetLastError(), "gs_bin_sort: write lists");
 }
