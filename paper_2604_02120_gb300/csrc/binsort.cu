@@ -446,45 +446,72 @@ __device__ __forceinline__ uint32_t runs_mask(const Runs4& rr, int sx) {
     return m;
 }
 
-// The item's supertile columns in supertile row sy (emit(lo, hi, runs) per
-// interval; the count is returned) and, in *fine, its instances in those
-// tile rows.
-template <bool TIGHT, class F>
-__device__ __forceinline__ int supertile_row(const TightRows& t, int sy, int x0, int x1, int y0, int y1,
-                                             uint32_t* fine, F emit) {
+// The four tile-row runs of supertile row sy within the rectangle [x0, x1] x
+// [y0, y1], and in *fine their instance count.
+template <bool TIGHT>
+__device__ __forceinline__ Runs4 row_runs(const TightRows& t, int sy, int x0, int x1, int y0, int y1,
+                                          uint32_t* fine) {
     Runs4 rr;
-    if constexpr (!TIGHT) {
 #pragma unroll
-        for (int k = 0; k < kSuper; ++k) {
-            const int y = sy * kSuper + k;
-            const bool in = y >= y0 && y <= y1;
-            rr.f[k] = in ? x0 : 1;
-            rr.l[k] = in ? x1 : 0;
-        }
-        const int rows = min(y1, sy * kSuper + kSuper - 1) - max(y0, sy * kSuper) + 1;
-        *fine += (uint32_t)(rows * (x1 - x0 + 1));
-        emit(x0 / kSuper, x1 / kSuper, rr);
-        return x1 / kSuper - x0 / kSuper + 1;
-    } else {
-        Iv r[kSuper];
-#pragma unroll
-        for (int k = 0; k < kSuper; ++k) {
-            r[k] = Iv{0x7fffffff, -1};
-            rr.f[k] = 1;
-            rr.l[k] = 0;
-            const int y = sy * kSuper + k;
-            if (y >= y0 && y <= y1) {
-                int f, l;
+    for (int k = 0; k < kSuper; ++k) {
+        const int y = sy * kSuper + k;
+        int f = 1, l = 0;
+        if (y >= y0 && y <= y1) {
+            if constexpr (TIGHT) {
                 tight_row(t, y, x0, x1, f, l);
-                if (f <= l) {
-                    *fine += (uint32_t)(l - f + 1);
-                    r[k] = Iv{f / kSuper, l / kSuper};
-                    rr.f[k] = f;
-                    rr.l[k] = l;
-                }
+            } else {
+                f = x0;
+                l = x1;
             }
         }
-        return iv_union4(r[0], r[1], r[2], r[3], [&](int lo, int hi) { emit(lo, hi, rr); });
+        rr.f[k] = f;
+        rr.l[k] = l;
+        if (f <= l) *fine += (uint32_t)(l - f + 1);
+    }
+    return rr;
+}
+
+// The supertile columns holding an instance of the runs rr (emit(lo, hi) per
+// maximal interval, in increasing order); returns their count.
+template <class F>
+__device__ __forceinline__ int runs_union(const Runs4& rr, F emit) {
+    Iv r[kSuper];
+#pragma unroll
+    for (int k = 0; k < kSuper; ++k)
+        r[k] = rr.f[k] <= rr.l[k] ? Iv{rr.f[k] / kSuper, rr.l[k] / kSuper} : Iv{0x7fffffff, -1};
+    return iv_union4(r[0], r[1], r[2], r[3], emit);
+}
+
+// Deals the work units of a warp's items (lane l's item has units[l] of
+// them: its supertile rows) out to the lanes, 32 per round, in lane-then-unit
+// order, so that every lane evaluates one supertile row whatever the spread
+// of the items' heights.  body(active, src, u) runs on every lane each round:
+// src is the lane whose item the unit belongs to, u the unit's index within
+// that item; active is false on the idle lanes of the last round.
+template <class F>
+__device__ __forceinline__ void warp_units(uint32_t units, F body) {
+    const int lane = threadIdx.x & 31;
+    uint32_t incl = units;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += v;
+    }
+    const uint32_t excl = incl - units, total = __shfl_sync(0xffffffffu, incl, 31);
+    for (uint32_t r0 = 0; r0 < total; r0 += 32) {
+        const uint32_t f = r0 + (uint32_t)lane;
+        // the last lane whose first unit is at or before f (the first units are nondecreasing)
+        int src = 0;
+        uint32_t start = 0;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const uint32_t v = __shfl_sync(0xffffffffu, excl, src + d);
+            if (v <= f) {
+                src += d;
+                start = v;
+            }
+        }
+        body(f < total, src, f - start);
     }
 }
 
@@ -502,16 +529,13 @@ __device__ __forceinline__ TightRows shfl_rows(const TightRows& t, int src) {
     return b;
 }
 
-// An item spanning more supertile rows than this is counted and duplicated
-// by a whole warp, one supertile row per lane.
-constexpr int kTallRows = 4;
-
 // Per item: its supertile count (cnt) and depth key; the depth keys' four
 // digit histograms (pass ids 0..3); the sum of all items' instance counts
 // (fine_total).  Also clears the tile ranges and the look-back status words
 // for this call.  Each thread takes ITEMS items, strided by the block size,
-// with all loads issued before any use.  TIGHT: opacity-aware membership,
-// one O(1) run per rectangle row.
+// with all loads issued before any use; each warp deals its items' supertile
+// rows out to its lanes (warp_units).  TIGHT: opacity-aware membership, one
+// O(1) run per rectangle row.
 constexpr int kCountItems = 4, kCountItemsTight = 2;
 template <bool TIGHT, int ITEMS>
 __global__ void __launch_bounds__(kThreads) k_count(int n_items, const __grid_constant__ SortViews sv,
@@ -523,6 +547,7 @@ __global__ void __launch_bounds__(kThreads) k_count(int n_items, const __grid_co
                                                     uint4* __restrict__ clear, size_t clear_n,
                                                     uint32_t* __restrict__ ranges, size_t ranges_n) {
     __shared__ uint32_t s_h[4 * 256];
+    __shared__ uint32_t s_c[kThreads];  // per lane: its item's supertile count
     __shared__ unsigned long long s_fine;
     for (int i = threadIdx.x; i < 4 * 256; i += kThreads) s_h[i] = 0;
     if (threadIdx.x == 0) s_fine = 0;
@@ -540,44 +565,38 @@ __global__ void __launch_bounds__(kThreads) k_count(int n_items, const __grid_co
     }
     __syncthreads();
     uint32_t fine = 0;
-    const int lane = threadIdx.x & 31;
+    const int wlane0 = threadIdx.x & ~31;
 #pragma unroll
     for (int q = 0; q < ITEMS; ++q) {
         const int64_t i = base + q * kThreads;
         int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
-        bool tall = false;
+        bool vis = false;
         TightRows t{};
         if (i < n_items) {
             const ViewDesc& vd = sv.views[(int)i / sv.n_per_view];
-            uint32_t c = 0;
-            if (tile_rect(m[q].x, m[q].y, r[q], vd.W, vd.H, x0, x1, y0, y1)) {
-                if constexpr (TIGHT) t = item_tight_rows(sv, mean2d, (uint32_t)i);
-                tall = y1 / kSuper - y0 / kSuper + 1 > kTallRows;
-                if (!tall)
-                    for (int sy = y0 / kSuper; sy <= y1 / kSuper; ++sy)
-                        c += (uint32_t)supertile_row<TIGHT>(t, sy, x0, x1, y0, y1, &fine, [](int, int, const Runs4&) {});
-            }
-            if (!tall) cnt[i] = c;
+            vis = tile_rect(m[q].x, m[q].y, r[q], vd.W, vd.H, x0, x1, y0, y1);
+            if constexpr (TIGHT)
+                if (vis) t = item_tight_rows(sv, mean2d, (uint32_t)i);
             dkey[i] = key[q];
             dval[i] = (uint32_t)i;
 #pragma unroll
             for (int p = 0; p < 4; ++p) hist_add(s_h, p * 256 + ((key[q] >> (8 * p)) & 0xFFu));
         }
-        // a tall item: the whole warp, lane k on supertile rows sy0 + k, sy0 + k + 32, ...
-        unsigned talls = __ballot_sync(0xffffffffu, tall);
-        while (talls) {
-            const int src = __ffs(talls) - 1;
-            talls &= talls - 1;
+        s_c[threadIdx.x] = 0;
+        __syncwarp();
+        warp_units(vis ? (uint32_t)(y1 / kSuper - y0 / kSuper + 1) : 0u, [&](bool act, int src, uint32_t u) {
             const int bx0 = __shfl_sync(0xffffffffu, x0, src), bx1 = __shfl_sync(0xffffffffu, x1, src);
             const int by0 = __shfl_sync(0xffffffffu, y0, src), by1 = __shfl_sync(0xffffffffu, y1, src);
-            const TightRows bt = shfl_rows(t, src);
-            uint32_t c = 0;
-            for (int sy = by0 / kSuper + lane; sy <= by1 / kSuper; sy += 32)
-                c += (uint32_t)supertile_row<TIGHT>(bt, sy, bx0, bx1, by0, by1, &fine, [](int, int, const Runs4&) {});
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-            if (lane == src) cnt[i] = c;
-        }
+            TightRows bt{};
+            if constexpr (TIGHT) bt = shfl_rows(t, src);
+            if (act) {
+                const Runs4 rr = row_runs<TIGHT>(bt, by0 / kSuper + (int)u, bx0, bx1, by0, by1, &fine);
+                atomicAdd(&s_c[wlane0 + src], (uint32_t)runs_union(rr, [](int, int) {}));
+            }
+        });
+        __syncwarp();
+        if (i < n_items) cnt[i] = s_c[threadIdx.x];
+        __syncwarp();
     }
     if (fine) atomicAdd(&s_fine, (unsigned long long)fine);
     const size_t stride = (size_t)gridDim.x * kThreads;
@@ -605,16 +624,28 @@ __device__ __forceinline__ void row_hist(uint32_t a, uint32_t w, int passes, int
     }
 }
 
+// Digit histograms of one tile id (the wide-row path: one id per lane).
+__device__ __forceinline__ void key_hist(uint32_t a, int passes, int* s_d0, uint32_t* s_h) {
+    atomicAdd(&s_d0[a & 0xFFu], 1);
+    atomicSub(&s_d0[(a & 0xFFu) + 1], 1);
+    for (int p = 1; p < passes; ++p) hist_add(s_h, (p - 1) * 256 + ((a >> (8 * p)) & 0xFFu));
+}
+
 // Coarse duplication in depth order with the scan of supertile counts folded
 // in.  Tile t (from the ticket) holds the depth-ordered items
 // [t * kDupTile, (t + 1) * kDupTile); the tile's pair offset comes from
-// decoupled look-back over the tiles before it.  Each item writes one
-// (global supertile id, item) pair per supertile it touches, supertile rows
-// in order, at [offset, offset + count): one thread per item, an item of more
-// than 32 supertiles by the whole warp (one supertile row per lane).  Writes
-// stop at `limit`; the total goes to *total.  The digit histograms of the
-// written pairs' supertile ids go to hist (passes of them), so a truncated
-// list still sorts into a permutation of what was written.
+// decoupled look-back over the tiles before it (the items' rectangles and
+// membership rules are set up first, to overlap it).  Each item writes one
+// (global supertile id, item) pair per supertile it touches, at [offset,
+// offset + count), supertile rows in order: each warp deals its items'
+// supertile rows out to its lanes (warp_units) and places them by a warp scan
+// of their pair counts; a row of more than kWideRow supertiles is written by
+// the whole warp, one supertile column per lane.  With `pack` the key's high
+// half holds the pair's 16-bit tile mask (runs_mask).  Writes stop at
+// `limit`; the total goes to *total.  The digit histograms of the written
+// pairs' supertile ids go to hist (passes of them), so a truncated list still
+// sorts into a permutation of what was written.
+constexpr uint32_t kWideRow = 8;
 template <bool TIGHT>
 __global__ void __launch_bounds__(kThreads) k_dup_coarse(int n_items, const uint32_t* __restrict__ perm,
                                                          const uint32_t* __restrict__ cnt,
@@ -643,6 +674,17 @@ __global__ void __launch_bounds__(kThreads) k_dup_coarse(int n_items, const uint
     const int64_t k = base + threadIdx.x;
     const uint32_t item = k < n_items ? perm[k] : 0u;
     const uint32_t c = k < n_items ? cnt[item] : 0u;
+    int x0 = 0, x1 = -1, y0 = 0, y1 = -1, stx = 0, stb = 0;
+    TightRows t{};
+    if (c > 0) {
+        const int v = (int)(item / (uint32_t)sv.n_per_view);
+        const ViewDesc& vd = sv.views[v];
+        const float2 m = mean2d[item];
+        tile_rect(m.x, m.y, radius[item], vd.W, vd.H, x0, x1, y0, y1);
+        stx = sv.st_x[v];
+        stb = sv.st_begin[v];
+        if constexpr (TIGHT) t = item_tight_rows(sv, mean2d, item);
+    }
     uint64_t tile_sum;
     const uint64_t local = block_excl_scan<uint64_t, kThreads>((uint64_t)c, tile_sum, s_warp);
     unsigned long long* mine = status + tile;
@@ -659,82 +701,80 @@ __global__ void __launch_bounds__(kThreads) k_dup_coarse(int n_items, const uint
         }
     }
     __syncthreads();
-    const uint64_t off = s_prefix + local;
 
-    int x0 = 0, x1 = -1, y0 = 0, y1 = -1, stx = 0, stb = 0;
-    TightRows t{};
-    if (c > 0) {
-        const int v = (int)(item / (uint32_t)sv.n_per_view);
-        const ViewDesc& vd = sv.views[v];
-        const float2 m = mean2d[item];
-        tile_rect(m.x, m.y, radius[item], vd.W, vd.H, x0, x1, y0, y1);
-        stx = sv.st_x[v];
-        stb = sv.st_begin[v];
-        if constexpr (TIGHT) t = item_tight_rows(sv, mean2d, item);
-    }
-    // the pairs of supertile row sy at position p (written below `limit`); returns their count
-    auto write_row = [&](int sy, uint64_t p, uint32_t it) -> int {
-        uint32_t fine = 0;
-        return supertile_row<TIGHT>(t, sy, x0, x1, y0, y1, &fine, [&](int lo, int hi, const Runs4& rr) {
-            const uint32_t k0 = (uint32_t)stb + (uint32_t)sy * (uint32_t)stx + (uint32_t)lo;
-            const uint32_t len = (uint32_t)(hi - lo + 1);
-            if (p < limit) {
-                const uint32_t nw = (uint32_t)min((uint64_t)len, limit - p);
-                for (uint32_t j = 0; j < nw; ++j) {
-                    ckey[p + j] = (k0 + j) | (pack ? runs_mask(rr, lo + (int)j) << 16 : 0u);
-                    cval[p + j] = it;
-                }
-                row_hist(k0, nw, passes, s_d0, s_h);
-            }
-            p += len;
-        });
-    };
-    const bool big = c > 32 || (c > 0 && y1 / kSuper - y0 / kSuper + 1 > kTallRows);
-    if (c > 0 && !big) {
-        uint64_t p = off;
-        for (int sy = y0 / kSuper; sy <= y1 / kSuper && p < limit; ++sy) p += (uint64_t)write_row(sy, p, item);
-    }
-    unsigned bigs = __ballot_sync(0xffffffffu, big);
-    while (bigs) {  // the whole warp: lane k takes supertile rows sy0 + k, sy0 + k + 32, ...
-        const int src = __ffs(bigs) - 1;
-        bigs &= bigs - 1;
-        const uint32_t bi = __shfl_sync(0xffffffffu, item, src);
+    // the warp's pairs start at its lane 0's item offset
+    uint64_t p_warp = s_prefix + __shfl_sync(0xffffffffu, local, 0);
+    const unsigned lt = (1u << lane) - 1u;
+    warp_units(c > 0 ? (uint32_t)(y1 / kSuper - y0 / kSuper + 1) : 0u, [&](bool act, int src, uint32_t u) {
         const int bx0 = __shfl_sync(0xffffffffu, x0, src), bx1 = __shfl_sync(0xffffffffu, x1, src);
         const int by0 = __shfl_sync(0xffffffffu, y0, src), by1 = __shfl_sync(0xffffffffu, y1, src);
         const int bstx = __shfl_sync(0xffffffffu, stx, src), bstb = __shfl_sync(0xffffffffu, stb, src);
-        uint64_t pos = __shfl_sync(0xffffffffu, off, src);
-        const TightRows bt = shfl_rows(t, src);
-        for (int sb = by0 / kSuper; sb <= by1 / kSuper && pos < limit; sb += 32) {
-            const int sy = sb + lane;
-            uint32_t fine = 0;
-            const int n_row = sy <= by1 / kSuper
-                                  ? supertile_row<TIGHT>(bt, sy, bx0, bx1, by0, by1, &fine, [](int, int, const Runs4&) {}) : 0;
-            uint32_t incl = (uint32_t)n_row;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
-                if (lane >= d) incl += v;
-            }
-            const uint32_t rows_total = __shfl_sync(0xffffffffu, incl, 31);
-            if (n_row > 0) {
-                uint64_t p = pos + (incl - (uint32_t)n_row);
-                supertile_row<TIGHT>(bt, sy, bx0, bx1, by0, by1, &fine, [&](int lo, int hi, const Runs4& rr) {
-                    const uint32_t k0 = (uint32_t)bstb + (uint32_t)sy * (uint32_t)bstx + (uint32_t)lo;
-                    const uint32_t len = (uint32_t)(hi - lo + 1);
-                    if (p < limit) {
-                        const uint32_t nw = (uint32_t)min((uint64_t)len, limit - p);
-                        for (uint32_t j = 0; j < nw; ++j) {
-                            ckey[p + j] = (k0 + j) | (pack ? runs_mask(rr, lo + (int)j) << 16 : 0u);
-                            cval[p + j] = bi;
-                        }
-                        row_hist(k0, nw, passes, s_d0, s_h);
-                    }
-                    p += len;
-                });
-            }
-            pos += rows_total;
+        const uint32_t bi = __shfl_sync(0xffffffffu, item, src);
+        TightRows bt{};
+        if constexpr (TIGHT) bt = shfl_rows(t, src);
+        const int sy = by0 / kSuper + (int)u;
+        Runs4 rr{};
+        uint32_t n = 0, fine = 0;
+        if (act) {
+            rr = row_runs<TIGHT>(bt, sy, bx0, bx1, by0, by1, &fine);
+            n = (uint32_t)runs_union(rr, [](int, int) {});
         }
-    }
+        uint32_t incl = n;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += v;
+        }
+        uint64_t p = p_warp + (incl - n);
+        p_warp += __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t krow = (uint32_t)bstb + (uint32_t)sy * (uint32_t)bstx;  // the row's supertile 0
+        const bool wide = n > kWideRow;
+        if (act && !wide)
+            runs_union(rr, [&](int lo, int hi) {
+                const uint32_t len = (uint32_t)(hi - lo + 1);
+                if (p < limit) {
+                    const uint32_t nw = (uint32_t)min((uint64_t)len, limit - p);
+                    for (uint32_t j = 0; j < nw; ++j) {
+                        ckey[p + j] = (krow + (uint32_t)lo + j) | (pack ? runs_mask(rr, lo + (int)j) << 16 : 0u);
+                        cval[p + j] = bi;
+                    }
+                    row_hist(krow + (uint32_t)lo, nw, passes, s_d0, s_h);
+                }
+                p += len;
+            });
+        unsigned wides = __ballot_sync(0xffffffffu, act && wide);
+        while (wides) {  // a wide row: the whole warp, supertile column lo + j on lane j
+            const int w = __ffs(wides) - 1;
+            wides &= wides - 1;
+            Runs4 wr;
+#pragma unroll
+            for (int q = 0; q < kSuper; ++q) {
+                wr.f[q] = __shfl_sync(0xffffffffu, rr.f[q], w);
+                wr.l[q] = __shfl_sync(0xffffffffu, rr.l[q], w);
+            }
+            uint64_t wp = __shfl_sync(0xffffffffu, p, w);
+            const uint32_t wk = __shfl_sync(0xffffffffu, krow, w), wi = __shfl_sync(0xffffffffu, bi, w);
+            int lo = 0x7fffffff, hi = -1;
+#pragma unroll
+            for (int q = 0; q < kSuper; ++q)
+                if (wr.f[q] <= wr.l[q]) {
+                    lo = min(lo, wr.f[q] / kSuper);
+                    hi = max(hi, wr.l[q] / kSuper);
+                }
+            for (int sx0 = lo; sx0 <= hi && wp < limit; sx0 += 32) {
+                const int sx = sx0 + lane;
+                const uint32_t m = sx <= hi ? runs_mask(wr, sx) : 0u;
+                const unsigned nz = __ballot_sync(0xffffffffu, m != 0u);
+                const uint64_t q = wp + (uint64_t)__popc(nz & lt);
+                if (m != 0u && q < limit) {
+                    ckey[q] = (wk + (uint32_t)sx) | (pack ? m << 16 : 0u);
+                    cval[q] = wi;
+                    key_hist(wk + (uint32_t)sx, passes, s_d0, s_h);
+                }
+                wp += (uint64_t)__popc(nz);
+            }
+        }
+    });
     __syncthreads();
     {
         int tot;
