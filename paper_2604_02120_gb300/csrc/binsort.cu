@@ -826,11 +826,17 @@ __device__ __forceinline__ uint32_t supertile_mask(const SortViews& sv, const fl
     return mask;
 }
 
-// Per sorted pair: its 16-bit tile mask (into masks[]), and the instance
-// counts of the supertile's tiles added into ranges[2 t + 1] (cleared by
-// k_count).  The pairs are sorted by supertile, so a warp's lanes mostly share
-// one: lanes are grouped by supertile id, and each group adds its count of
-// each tile with one atomic.
+// The instance counts of the supertile's tiles, added into ranges[2 t + 1]
+// (cleared by k_count), from the sorted pairs' 16-bit tile masks: the
+// duplication packed them above the supertile id (`pack`), else they are
+// computed here and stored to masks[].  Each warp takes segments of
+// kPairSeg consecutive pairs; the pairs are sorted by supertile, so a warp's
+// 32 pairs mostly share one, and while they do the warp counts each tile's
+// bits with four lane reductions (bit j of every mask spread to its own byte)
+// into lane j's count, adding it to ranges with one atomic per tile when the
+// supertile changes.  32 pairs of several supertiles: one atomic per group
+// of equal supertiles and tile.
+constexpr uint32_t kPairSeg = 512;
 template <bool TIGHT>
 __global__ void __launch_bounds__(kThreads) k_pair_masks(const __grid_constant__ SortViews sv,
                                                          const float2* __restrict__ mean2d,
@@ -842,67 +848,100 @@ __global__ void __launch_bounds__(kThreads) k_pair_masks(const __grid_constant__
                                                          uint32_t* __restrict__ ranges) {
     const uint32_t Ic = pass_count(n_host, n_dev);
     const int lane = threadIdx.x & 31;
-    // a grid of resident size walks the pairs (their count is known only on the device)
-    for (uint32_t b0 = blockIdx.x * kThreads; b0 < Ic; b0 += gridDim.x * kThreads) {
-        const uint32_t e = b0 + threadIdx.x;
-        uint32_t key = 0xffffffffu, m = 0;
-        int v = 0, cx0 = 0, cy0 = 0;
-        if (e < Ic) {
-            key = ckey[e];
-            if (pack) {  // the duplication packed the mask above the supertile id
-                m = key >> 16;
-                key &= 0xFFFFu;
-            }
-            while (v + 1 < sv.num_views && sv.st_begin[v + 1] <= (int)key) ++v;
-            const int ls = (int)key - sv.st_begin[v];
-            cx0 = (ls % sv.st_x[v]) * kSuper;
-            cy0 = (ls / sv.st_x[v]) * kSuper;
-            if (!pack) {
-                const uint32_t it = cval[e];
-                m = it < n_items ? supertile_mask<TIGHT>(sv, mean2d, radius, it, sv.views[v], cx0, cy0) : 0u;
-            }
-            masks[e] = (uint16_t)m;
-        }
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        const bool whole = peers == 0xffffffffu && key != 0xffffffffu;  // the warp shares one supertile
-        const bool leader = lane == __ffs(peers) - 1 && key != 0xffffffffu;
+    // tile j of supertile key (global id) as a global tile index
+    auto tile_of = [&](uint32_t key, int j) -> size_t {
+        int v = 0;
+        while (v + 1 < sv.num_views && sv.st_begin[v + 1] <= (int)key) ++v;
+        const int ls = (int)key - sv.st_begin[v];
         const ViewDesc& vd = sv.views[v];
+        return (size_t)vd.tile_begin + (size_t)((ls / sv.st_x[v]) * kSuper + (j >> 2)) * vd.tiles_x +
+               (size_t)((ls % sv.st_x[v]) * kSuper + (j & 3));
+    };
+    const uint64_t warp_id = ((uint64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const uint64_t warps = ((uint64_t)gridDim.x * kThreads) >> 5;
+    for (uint64_t s0 = warp_id * kPairSeg; s0 < Ic; s0 += warps * kPairSeg) {
+        const uint64_t s1 = min(s0 + (uint64_t)kPairSeg, (uint64_t)Ic);
+        uint32_t cur = 0xffffffffu;  // the supertile being counted (warp-uniform)
+        uint32_t acc = 0;            // lane j < 16: its count of tile j
+        auto flush = [&]() {
+            if (cur != 0xffffffffu && lane < 16 && acc) atomicAdd(&ranges[2 * tile_of(cur, lane) + 1], acc);
+            acc = 0;
+        };
+        for (uint64_t b = s0; b < s1; b += 32) {
+            const uint64_t e = b + (uint64_t)lane;
+            uint32_t key = 0xffffffffu, m = 0;
+            if (e < s1) {
+                key = ckey[e];
+                if (pack) {
+                    m = key >> 16;
+                    key &= 0xFFFFu;
+                } else {
+                    int v = 0;
+                    while (v + 1 < sv.num_views && sv.st_begin[v + 1] <= (int)key) ++v;
+                    const int ls = (int)key - sv.st_begin[v];
+                    const uint32_t it = cval[e];
+                    m = it < n_items ? supertile_mask<TIGHT>(sv, mean2d, radius, it, sv.views[v],
+                                                             (ls % sv.st_x[v]) * kSuper, (ls / sv.st_x[v]) * kSuper)
+                                     : 0u;
+                    masks[e] = (uint16_t)m;
+                }
+            }
+            const uint32_t k0 = __shfl_sync(0xffffffffu, key, 0);  // lane 0 always holds a pair
+            if (!__all_sync(0xffffffffu, key == k0 || e >= s1)) {
+                // pairs of several supertiles: one atomic per group and tile
+                flush();
+                cur = 0xffffffffu;
+                const unsigned peers = __match_any_sync(0xffffffffu, key);
+                const bool leader = lane == __ffs(peers) - 1 && key != 0xffffffffu;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const unsigned b = __ballot_sync(0xffffffffu, (m >> j) & 1u) & peers;
-            // a warp of one supertile: lane j adds tile j's count; mixed warps: each group's leader
-            if ((whole ? lane == j : leader) && b) {
-                const size_t gt = (size_t)vd.tile_begin + (size_t)(cy0 + (j >> 2)) * vd.tiles_x + (size_t)(cx0 + (j & 3));
-                atomicAdd(&ranges[2 * gt + 1], (uint32_t)__popc(b));
+                for (int j = 0; j < 16; ++j) {
+                    const unsigned bj = __ballot_sync(0xffffffffu, (m >> j) & 1u) & peers;
+                    if (leader && bj) atomicAdd(&ranges[2 * tile_of(key, j) + 1], (uint32_t)__popc(bj));
+                }
+                continue;
+            }
+            if (k0 != cur) {
+                flush();
+                cur = k0;
+            }
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                // bits 4w .. 4w + 3 of the mask to bytes 0..3, summed over the warp (<= 32 each)
+                const uint32_t spread = (((m >> (4 * w)) & 0xFu) * 0x00204081u) & 0x01010101u;
+                const uint32_t sum = __reduce_add_sync(0xffffffffu, spread);
+                if ((lane >> 2) == w) acc += (sum >> (8 * (lane & 3))) & 0xFFu;
             }
         }
+        flush();
     }
 }
 
 // One block per supertile s, after k_tile_scan: its items are the sorted pairs
 // [cs, ce) with key s; every instance's id (and key) goes to its tile's next
-// position, in item order, from the pairs' stored tile masks: rounds of
-// kFineThreads pairs; thread (q, j) places tile j's instances among the
-// round's pairs [16 q, 16 q + 16) into a shared-memory stage of the round's
-// output of each tile, and the block then writes each tile's run with
-// consecutive threads on consecutive ids.
-constexpr int kFineThreads = 256;
+// position, in item order, from the pairs' tile masks (in the key's high half
+// when kmask is 0xFFFF, else in masks[]).  Rounds of kFineRound pairs, the
+// next round's loads in flight during the current one: thread (q, j) places
+// tile j's instances among the round's pairs [P q, P q + P) into a
+// shared-memory stage of the round's output of each tile, then warp w writes
+// the runs of tiles w and w + 8 with consecutive lanes on consecutive ids.
+constexpr int kFineThreads = 256, kFineRound = 512;
 __global__ void __launch_bounds__(kFineThreads) k_fine(const __grid_constant__ SortViews sv,
-                                                       const float2* __restrict__ mean2d,
-                                                       const int* __restrict__ radius, const float* __restrict__ depth,
+                                                       const float* __restrict__ depth,
                                                        const uint32_t* __restrict__ ckey,
                                                        const uint32_t* __restrict__ cval, uint32_t n_host,
-                                                       const uint64_t* __restrict__ n_dev, uint32_t n_items,
-                                                       uint32_t kmask, uint16_t* __restrict__ masks,
-                                                       uint32_t* __restrict__ ranges,
+                                                       const uint64_t* __restrict__ n_dev, uint32_t kmask,
+                                                       const uint16_t* __restrict__ masks,
+                                                       const uint32_t* __restrict__ ranges,
                                                        uint32_t* __restrict__ ids_out, uint64_t* __restrict__ keys_out) {
-    constexpr int Q = kFineThreads / 16;  // workers per tile
+    constexpr int Q = kFineThreads / 16;        // workers per tile
+    constexpr int P = kFineRound / Q;           // pairs per worker
+    constexpr int PT = kFineRound / kFineThreads;  // pairs each thread loads
     __shared__ uint32_t s_rng[2];
     __shared__ uint32_t s_beg[16], s_end[16], s_run[16], s_tot[16];
-    __shared__ uint16_t s_mask[kFineThreads];
-    __shared__ uint32_t s_item[kFineThreads];
+    __shared__ uint16_t s_mask[kFineRound];
+    __shared__ uint32_t s_item[kFineRound];
     __shared__ uint32_t s_q[Q][16];
-    __shared__ uint32_t s_out[16][kFineThreads + 1];  // rows one word apart in bank: 16 tiles written at once
+    __shared__ uint32_t s_out[16][kFineRound + 1];  // rows one word apart in bank
     const int s = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int v = 0;
@@ -924,47 +963,60 @@ __global__ void __launch_bounds__(kFineThreads) k_fine(const __grid_constant__ S
     __syncthreads();
     const uint32_t cs = s_rng[0], ce = s_rng[1];
     if (cs >= ce) return;
-    {
-        const int j = threadIdx.x & 15, q = threadIdx.x >> 4;
-        for (uint32_t r0 = cs; r0 < ce; r0 += kFineThreads) {
-            const uint32_t e = r0 + threadIdx.x;
-            s_mask[threadIdx.x] = e < ce ? masks[e] : (uint16_t)0;
-            s_item[threadIdx.x] = e < ce ? cval[e] : 0u;
-            __syncthreads();
-            uint32_t cnt = 0;
+    const bool packed = kmask == 0xFFFFu;
+    uint32_t mk[PT], it[PT];
+    auto fetch = [&](uint32_t r0) {
 #pragma unroll
-            for (int k = 0; k < 16; ++k) cnt += (s_mask[16 * q + k] >> j) & 1u;
-            s_q[q][j] = cnt;
-            __syncthreads();
-            uint32_t pre = 0;
-            for (int qq = 0; qq < q; ++qq) pre += s_q[qq][j];
+        for (int i = 0; i < PT; ++i) {
+            const uint32_t e = r0 + (uint32_t)(i * kFineThreads + threadIdx.x);
+            mk[i] = e < ce ? (packed ? ckey[e] >> 16 : (uint32_t)masks[e]) : 0u;
+            it[i] = e < ce ? cval[e] : 0u;
+        }
+    };
+    fetch(cs);
+    const int j = threadIdx.x & 15, q = threadIdx.x >> 4;
+    for (uint32_t r0 = cs; r0 < ce; r0 += kFineRound) {
 #pragma unroll
-            for (int k = 0; k < 16; ++k)
-                if ((s_mask[16 * q + k] >> j) & 1u) s_out[j][pre++] = s_item[16 * q + k];
-            if (q == Q - 1) s_tot[j] = pre;  // the round's instances of tile j
-            __syncthreads();
-            // each tile's run of this round, consecutive threads on consecutive positions
-            for (int t = 0; t < 16; ++t) {
-                const uint32_t n_t = s_tot[t];
-                const uint64_t p0 = (uint64_t)s_beg[t] + s_run[t];
-                const uint64_t end = s_end[t];
-                const uint64_t dkey = keys_out != nullptr
-                                          ? (uint64_t)((uint32_t)vd.tile_begin + (uint32_t)(cy0 + (t >> 2)) * (uint32_t)tx +
-                                                       (uint32_t)(cx0 + (t & 3))) << 32
-                                          : 0ull;
-                for (uint32_t k = threadIdx.x; k < n_t; k += kFineThreads) {
-                    const uint64_t p = p0 + k;
-                    if (p < end) {
-                        const uint32_t g = s_out[t][k];
-                        ids_out[p] = g;
-                        if (keys_out != nullptr) keys_out[p] = dkey | __float_as_uint(depth[g]);
-                    }
+        for (int i = 0; i < PT; ++i) {
+            s_mask[i * kFineThreads + threadIdx.x] = (uint16_t)mk[i];
+            s_item[i * kFineThreads + threadIdx.x] = it[i];
+        }
+        if (r0 + kFineRound < ce) fetch(r0 + kFineRound);
+        __syncthreads();
+        uint32_t cnt = 0;
+#pragma unroll 8
+        for (int k = 0; k < P; ++k) cnt += (s_mask[P * q + k] >> j) & 1u;
+        s_q[q][j] = cnt;
+        __syncthreads();
+        uint32_t pre = 0;
+#pragma unroll
+        for (int qq = 0; qq < Q; ++qq) pre += qq < q ? s_q[qq][j] : 0u;
+#pragma unroll 8
+        for (int k = 0; k < P; ++k)
+            if ((s_mask[P * q + k] >> j) & 1u) s_out[j][pre++] = s_item[P * q + k];
+        if (q == Q - 1) s_tot[j] = pre;  // the round's instances of tile j
+        __syncthreads();
+#pragma unroll
+        for (int h = 0; h < 16 / (kFineThreads / 32); ++h) {
+            const int t = warp + h * (kFineThreads / 32);
+            const uint32_t n_t = s_tot[t];
+            const uint64_t p0 = (uint64_t)s_beg[t] + s_run[t];
+            const uint64_t end = s_end[t];
+            const uint64_t dkey = keys_out != nullptr
+                                      ? (uint64_t)((uint32_t)vd.tile_begin + (uint32_t)(cy0 + (t >> 2)) * (uint32_t)tx +
+                                                   (uint32_t)(cx0 + (t & 3))) << 32
+                                      : 0ull;
+            for (uint32_t k = lane; k < n_t; k += 32) {
+                const uint64_t p = p0 + k;
+                if (p < end) {
+                    const uint32_t g = s_out[t][k];
+                    ids_out[p] = g;
+                    if (keys_out != nullptr) keys_out[p] = dkey | __float_as_uint(depth[g]);
                 }
             }
-            __syncthreads();
-            if (threadIdx.x < 16) s_run[threadIdx.x] += s_tot[threadIdx.x];
-            __syncthreads();
         }
+        __syncthreads();
+        if (threadIdx.x < 16) s_run[threadIdx.x] += s_tot[threadIdx.x];
     }
 }
 
@@ -1191,7 +1243,7 @@ gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* ra
     // the pairs' tile masks go to the free half of the pair buffers (2 bytes per pair)
     uint16_t* masks = reinterpret_cast<uint16_t*>(ck[which ^ 1]);
     auto pair_masks = tight ? k_pair_masks<true> : k_pair_masks<false>;
-    int pair_grid = 0;  // 8 blocks per SM
+    int pair_grid = 0;  // at most 8 blocks per SM, each warp taking segments of kPairSeg pairs
     {
         int dev = 0, sms = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
@@ -1199,7 +1251,8 @@ gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* ra
             return cuda_status(e, "gs_bin_sort: device");
         pair_grid = 8 * sms;
     }
-    pair_masks<<<(int)std::min<int64_t>(pair_grid, cdiv(I_grid, kThreads)), kThreads, 0, s>>>(
+    pair_masks<<<(int)std::min<int64_t>(pair_grid, cdiv(I_grid, (int64_t)kPairSeg * (kThreads / 32))), kThreads, 0,
+                 s>>>(
         sv2, mean2d, radius, ck[which], cv[which], I_grid, ctotal, (uint32_t)n, pack, masks, tile_ranges);
     count_launches();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: tile counts");
@@ -1207,9 +1260,8 @@ gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* ra
                                            graph ? n_instances_dev : nullptr, err);
     count_launches();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: tile ranges");
-    k_fine<<<nst, kFineThreads, 0, s>>>(sv2, mean2d, radius, depth, ck[which], cv[which], I_grid, ctotal,
-                                            (uint32_t)n, pack ? 0xFFFFu : 0xFFFFFFFFu, masks, tile_ranges,
-                                            ids_sorted, keys_sorted);
+    k_fine<<<nst, kFineThreads, 0, s>>>(sv2, depth, ck[which], cv[which], I_grid, ctotal,
+                                        pack ? 0xFFFFu : 0xFFFFFFFFu, masks, tile_ranges, ids_sorted, keys_sorted);
     count_launches();
     return cuda_status(cudaGetLastError(), "gs_bin_sort: write lists");
 }
