@@ -3,18 +3,18 @@
 // The result equals a stable sort of (tile << 32 | depth_bits) keys emitted in
 // Gaussian order, i.e. every tile's list ordered by (depth bits, Gaussian
 // index).  It is produced without sorting the instances themselves:
-//   1. per item: its instance count, and the number of supertiles (4 x 4
-//      tiles) holding at least one of its instances;
-//   2. stable LSD radix sort of the N items by depth bits (32-bit keys);
-//   3. coarse duplication in that depth order: one (supertile, item) pair
-//      per supertile the item touches (about an eighth of the instances);
-//   4. stable LSD radix sort of those pairs by supertile id, so each
+//   1. stable LSD radix sort of the N items by depth bits (32-bit keys);
+//   2. coarse duplication in that depth order: one (supertile, item) pair
+//      per supertile (4 x 4 tiles) holding at least one of the item's
+//      instances (about an eighth of the instances), with the pair's 16-bit
+//      mask of those instances, and the count of all instances;
+//   3. stable LSD radix sort of those pairs by supertile id, so each
 //      supertile's items are contiguous and in depth order;
-//   5. one block per supertile counts the instances of each of its 16 tiles,
-//      a scan over the tiles gives every tile's range, and the block walks
-//      its items again writing each instance's id once, at its tile's next
+//   4. the instances of each tile counted from the pairs' masks, a scan over
+//      the tiles gives every tile's range, and one block per supertile walks
+//      its pairs writing each instance's id once, at its tile's next
 //      position: a stable per-tile compaction, so every list keeps the depth
-//      (then index) order of step 2.
+//      (then index) order of step 1.
 // Each instance is written once (4 bytes of id, plus its key if asked for)
 // instead of being duplicated and moved by a radix pass per 8 bits of tile id.
 //
@@ -29,8 +29,8 @@
 // bounded in time and sets the timeout bit of the error word if it gives up.
 // The scan of coarse counts in depth order is done the same way inside the
 // duplication kernel, so the whole stage is
-//   memset, count, 4 depth passes, coarse duplicate, ceil(bits / 8) supertile
-//   passes, fine count, tile scan, fine write.
+//   memset, keys, 4 depth passes, coarse duplicate, ceil(bits / 8) supertile
+//   passes, tile counts, tile scan, fine write.
 #include <algorithm>
 
 #include "internal.h"
@@ -190,8 +190,8 @@ __device__ __forceinline__ uint64_t lookback_warp(const unsigned long long* stat
 // The lanes of the warp whose digit equals this lane's, among the valid lanes
 // (an invalid lane gets only itself).  FULL: one ballot per bit of the 8-bit
 // digit, a cost that does not grow with the number of distinct digits in the
-// warp (random digits: up to 32); otherwise __match_any_sync, cheap when the
-// digit has only a few significant bits (the last pass over a short key).
+// warp (random digits: up to 32); otherwise __match_any_sync, the cheaper when
+// the digit has at most 4 significant bits (the last pass over a short key).
 template <bool FULL>
 __device__ __forceinline__ unsigned digit_peers(uint32_t d, bool valid) {
     const unsigned lane_bit = 1u << (threadIdx.x & 31);
@@ -206,11 +206,18 @@ __device__ __forceinline__ unsigned digit_peers(uint32_t d, bool valid) {
     return valid ? m : lane_bit;
 }
 
-// s_h[bin] += 1 for every active lane, one atomic per distinct bin in the warp
-// (digits of nearby keys often agree, and same-address shared atomics serialise).
+// s_h[bin] += 1 for every active lane: one atomic when the lanes agree on the
+// bin (the high digits of nearby keys usually do, and same-address shared
+// atomics serialise), else one per lane.
 __device__ __forceinline__ void hist_add(uint32_t* s_h, uint32_t bin) {
-    const unsigned peers = __match_any_sync(__activemask(), bin);
-    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&s_h[bin], (uint32_t)__popc(peers));
+    const unsigned act = __activemask();
+    const int first = __ffs(act) - 1;
+    const uint32_t b0 = __shfl_sync(act, bin, first);
+    if (__all_sync(act, bin == b0)) {
+        if ((int)(threadIdx.x & 31) == first) atomicAdd(&s_h[bin], (uint32_t)__popc(act));
+    } else {
+        atomicAdd(&s_h[bin], 1u);
+    }
 }
 
 // Item count of a pass: the host value, or min(*n_dev, host value) in graph mode.
@@ -354,8 +361,7 @@ cudaError_t radix_sort(uint32_t* k[2], uint32_t* v[2], uint32_t n_host, const ui
     const int nblk = (int)std::min<int64_t>(cdiv(n_host, (int64_t)kThreads * items), 4 * (int64_t)sms);
     for (int p = 0, shift = 0; shift < bits; ++p, shift += 8) {
         const int id = first_pass + p;
-        // ballots unless the digit has at most 4 significant bits (16 values: match_any is cheaper);
-        // the ballot of an unused high bit is the same for every lane
+        // ballots unless the digit has at most 4 significant bits (match_any is cheaper then)
         const bool full = bits - shift > 4;
         auto kern = items == 4 ? (full ? k_onesweep<4, true> : k_onesweep<4, false>)
                                : (full ? k_onesweep<16, true> : k_onesweep<16, false>);
@@ -485,9 +491,10 @@ __device__ __forceinline__ int runs_union(const Runs4& rr, F emit) {
 // Deals the work units of a warp's items (lane l's item has units[l] of
 // them: its supertile rows) out to the lanes, 32 per round, in lane-then-unit
 // order, so that every lane evaluates one supertile row whatever the spread
-// of the items' heights.  body(active, src, u) runs on every lane each round:
-// src is the lane whose item the unit belongs to, u the unit's index within
-// that item; active is false on the idle lanes of the last round.
+// of the items' heights.  body(active, src, u, f) runs on every lane each
+// round: src is the lane whose item the unit belongs to, u the unit's index
+// within that item, f its index among the warp's units; active is false on
+// the idle lanes of the last round.
 template <class F>
 __device__ __forceinline__ void warp_units(uint32_t units, F body) {
     const int lane = threadIdx.x & 31;
@@ -511,7 +518,7 @@ __device__ __forceinline__ void warp_units(uint32_t units, F body) {
                 start = v;
             }
         }
-        body(f < total, src, f - start);
+        body(f < total, src, f - start, f);
     }
 }
 
@@ -529,84 +536,44 @@ __device__ __forceinline__ TightRows shfl_rows(const TightRows& t, int src) {
     return b;
 }
 
-// Per item: its supertile count (cnt) and depth key; the depth keys' four
-// digit histograms (pass ids 0..3); the sum of all items' instance counts
-// (fine_total).  Also clears the tile ranges and the look-back status words
-// for this call.  Each thread takes ITEMS items, strided by the block size,
-// with all loads issued before any use; each warp deals its items' supertile
-// rows out to its lanes (warp_units).  TIGHT: opacity-aware membership, one
-// O(1) run per rectangle row.
-constexpr int kCountItems = 4, kCountItemsTight = 2;
-template <bool TIGHT, int ITEMS>
-__global__ void __launch_bounds__(kThreads) k_count(int n_items, const __grid_constant__ SortViews sv,
-                                                    const float2* __restrict__ mean2d,
-                                                    const int* __restrict__ radius, const float* __restrict__ depth,
-                                                    uint32_t* __restrict__ cnt, uint32_t* __restrict__ dkey,
-                                                    uint32_t* __restrict__ dval, uint32_t* __restrict__ hist,
-                                                    unsigned long long* __restrict__ fine_total,
-                                                    uint4* __restrict__ clear, size_t clear_n,
-                                                    uint32_t* __restrict__ ranges, size_t ranges_n) {
+// Per item: its depth key and index (the depth sort's input) and the keys'
+// four digit histograms (pass ids 0..3).  Also clears the tile ranges and the
+// look-back status words of the depth sort (clear) and of the duplication
+// (clear2).
+constexpr int kKeyItems = 4;
+__global__ void __launch_bounds__(kThreads) k_keys(int n_items, const float* __restrict__ depth,
+                                                   uint32_t* __restrict__ dkey, uint32_t* __restrict__ dval,
+                                                   uint32_t* __restrict__ hist, uint4* __restrict__ clear,
+                                                   size_t clear_n, unsigned long long* __restrict__ clear2,
+                                                   size_t clear2_n, uint32_t* __restrict__ ranges, size_t ranges_n) {
     __shared__ uint32_t s_h[4 * 256];
-    __shared__ uint32_t s_c[kThreads];  // per lane: its item's supertile count
-    __shared__ unsigned long long s_fine;
     for (int i = threadIdx.x; i < 4 * 256; i += kThreads) s_h[i] = 0;
-    if (threadIdx.x == 0) s_fine = 0;
-    const int64_t base = (int64_t)blockIdx.x * (kThreads * ITEMS) + threadIdx.x;
-    float2 m[ITEMS];
-    int r[ITEMS];
-    uint32_t key[ITEMS];
-#pragma unroll
-    for (int q = 0; q < ITEMS; ++q) {
-        const int64_t i = base + q * kThreads;
-        const bool ok = i < n_items;
-        m[q] = ok ? mean2d[i] : make_float2(0.f, 0.f);
-        r[q] = ok ? radius[i] : 0;
-        key[q] = ok ? __float_as_uint(depth[i]) : 0u;
-    }
     __syncthreads();
-    uint32_t fine = 0;
-    const int wlane0 = threadIdx.x & ~31;
+    const int64_t base = (int64_t)blockIdx.x * (kThreads * kKeyItems) + threadIdx.x;
+    uint32_t key[kKeyItems];
 #pragma unroll
-    for (int q = 0; q < ITEMS; ++q) {
+    for (int q = 0; q < kKeyItems; ++q) {
         const int64_t i = base + q * kThreads;
-        int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
-        bool vis = false;
-        TightRows t{};
+        key[q] = i < n_items ? __float_as_uint(depth[i]) : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < kKeyItems; ++q) {
+        const int64_t i = base + q * kThreads;
         if (i < n_items) {
-            const ViewDesc& vd = sv.views[(int)i / sv.n_per_view];
-            vis = tile_rect(m[q].x, m[q].y, r[q], vd.W, vd.H, x0, x1, y0, y1);
-            if constexpr (TIGHT)
-                if (vis) t = item_tight_rows(sv, mean2d, (uint32_t)i);
             dkey[i] = key[q];
             dval[i] = (uint32_t)i;
 #pragma unroll
             for (int p = 0; p < 4; ++p) hist_add(s_h, p * 256 + ((key[q] >> (8 * p)) & 0xFFu));
         }
-        s_c[threadIdx.x] = 0;
-        __syncwarp();
-        warp_units(vis ? (uint32_t)(y1 / kSuper - y0 / kSuper + 1) : 0u, [&](bool act, int src, uint32_t u) {
-            const int bx0 = __shfl_sync(0xffffffffu, x0, src), bx1 = __shfl_sync(0xffffffffu, x1, src);
-            const int by0 = __shfl_sync(0xffffffffu, y0, src), by1 = __shfl_sync(0xffffffffu, y1, src);
-            TightRows bt{};
-            if constexpr (TIGHT) bt = shfl_rows(t, src);
-            if (act) {
-                const Runs4 rr = row_runs<TIGHT>(bt, by0 / kSuper + (int)u, bx0, bx1, by0, by1, &fine);
-                atomicAdd(&s_c[wlane0 + src], (uint32_t)runs_union(rr, [](int, int) {}));
-            }
-        });
-        __syncwarp();
-        if (i < n_items) cnt[i] = s_c[threadIdx.x];
-        __syncwarp();
     }
-    if (fine) atomicAdd(&s_fine, (unsigned long long)fine);
     const size_t stride = (size_t)gridDim.x * kThreads;
     const uint4 z = make_uint4(0, 0, 0, 0);
     for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < clear_n; i += stride) clear[i] = z;
+    for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < clear2_n; i += stride) clear2[i] = 0ull;
     for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < ranges_n; i += stride) ranges[i] = 0;
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * 256; i += kThreads)
         if (s_h[i]) atomicAdd(&hist[i], s_h[i]);
-    if (threadIdx.x == 0 && s_fine) atomicAdd(fine_total, s_fine);
 }
 
 // Digit histograms of the tile ids [a, a + w) of one rectangle row, by runs:
@@ -631,39 +598,77 @@ __device__ __forceinline__ void key_hist(uint32_t a, int passes, int* s_d0, uint
     for (int p = 1; p < passes; ++p) hist_add(s_h, (p - 1) * 256 + ((a >> (8 * p)) & 0xFFu));
 }
 
-// Coarse duplication in depth order with the scan of supertile counts folded
-// in.  Tile t (from the ticket) holds the depth-ordered items
-// [t * kDupTile, (t + 1) * kDupTile); the tile's pair offset comes from
-// decoupled look-back over the tiles before it (the items' rectangles and
-// membership rules are set up first, to overlap it).  Each item writes one
-// (global supertile id, item) pair per supertile it touches, at [offset,
-// offset + count), supertile rows in order: each warp deals its items'
-// supertile rows out to its lanes (warp_units) and places them by a warp scan
-// of their pair counts; a row of more than kWideRow supertiles is written by
-// the whole warp, one supertile column per lane.  With `pack` the key's high
-// half holds the pair's 16-bit tile mask (runs_mask).  Writes stop at
-// `limit`; the total goes to *total.  The digit histograms of the written
-// pairs' supertile ids go to hist (passes of them), so a truncated list still
-// sorts into a permutation of what was written.
+// A unit's runs in four words (16 bits per end; an empty run as (1, 0)).
+__device__ __forceinline__ uint4 pack_runs(const Runs4& rr) {
+    uint32_t w[kSuper];
+#pragma unroll
+    for (int k = 0; k < kSuper; ++k)
+        w[k] = rr.f[k] <= rr.l[k] ? ((uint32_t)rr.f[k] | ((uint32_t)rr.l[k] << 16)) : 1u;
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+__device__ __forceinline__ Runs4 unpack_runs(uint4 v) {
+    const uint32_t w[kSuper] = {v.x, v.y, v.z, v.w};
+    Runs4 rr;
+#pragma unroll
+    for (int k = 0; k < kSuper; ++k) {
+        rr.f[k] = (int)(w[k] & 0xFFFFu);
+        rr.l[k] = (int)(w[k] >> 16);
+    }
+    return rr;
+}
+
+// Coarse duplication in depth order, with the supertile counts and their scan
+// folded in.  Tile t (from the ticket) holds the depth-ordered items
+// [t * kDupTile, (t + 1) * kDupTile).  Each warp deals its items' supertile
+// rows out to its lanes (warp_units) and evaluates every row's tile runs once,
+// keeping them in shared memory (the first kStashUnits of each warp; later
+// ones are evaluated again when written): the items' supertile counts and the
+// instance count, added into *fine_total.  The tile's pair count goes out for
+// the decoupled look-back over the tiles before it.  Each item then emits one
+// (global supertile id, item) pair per supertile it touches, supertile rows in
+// order, placed by a warp scan of the rows' pair counts; a row of more than
+// kWideRow supertiles is emitted by the whole warp, one supertile column per
+// lane.  A tile of at most kStagePairs pairs emits them into shared memory
+// before its look-back (so the predecessors' prefixes are usually there by
+// then) and copies them out with consecutive threads on consecutive pairs; a
+// larger tile looks back first and writes them directly.  With `pack` the
+// key's high half holds the pair's 16-bit tile mask (runs_mask).  Writes stop
+// at `limit`; the pair total goes to *total.  The digit histograms of the
+// written pairs' supertile ids go to hist (passes of them), so a truncated
+// list still sorts into a permutation of what was written.  With coarse_tile
+// > 0 the block also clears the look-back status words (256 per radix tile,
+// at radix_status) of the pair sort's tiles that start within its pairs
+// (below `limit`).
 constexpr uint32_t kWideRow = 8;
+constexpr uint32_t kStashUnits = 128;  // per warp
+constexpr uint32_t kStagePairs = 2048;
 template <bool TIGHT>
 __global__ void __launch_bounds__(kThreads) k_dup_coarse(int n_items, const uint32_t* __restrict__ perm,
-                                                         const uint32_t* __restrict__ cnt,
                                                          const __grid_constant__ SortViews sv,
                                                          const float2* __restrict__ mean2d,
                                                          const int* __restrict__ radius, uint64_t limit, int passes,
                                                          bool pack, uint32_t* tickets, unsigned long long* status,
                                                          uint32_t* __restrict__ ckey, uint32_t* __restrict__ cval,
                                                          uint32_t* __restrict__ hist, uint64_t* __restrict__ total,
-                                                         unsigned* err) {
+                                                         unsigned long long* __restrict__ fine_total,
+                                                         unsigned long long* __restrict__ radix_status,
+                                                         uint32_t coarse_tile, unsigned* err) {
     __shared__ uint64_t s_warp[kThreads / 32 + 1];
     __shared__ uint64_t s_prefix;
+    __shared__ unsigned long long s_fine;
     __shared__ uint32_t s_tile;
     __shared__ uint32_t s_h[3 * 256];  // digits 1..3
     __shared__ int s_d0[257];          // digit 0, as a difference array
     __shared__ int s_warp_i[kThreads / 32 + 1];
+    __shared__ uint32_t s_c[kThreads];  // per lane: its item's supertile count
+    __shared__ uint4 s_runs[(kThreads / 32) * kStashUnits];
+    __shared__ uint8_t s_n[(kThreads / 32) * kStashUnits];
+    __shared__ uint32_t s_pk[kStagePairs], s_pv[kStagePairs];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_tile = atomicAdd(&tickets[kMaxPasses], 1u);
+    if (threadIdx.x == 0) {
+        s_tile = atomicAdd(&tickets[kMaxPasses], 1u);
+        s_fine = 0;
+    }
     for (int i = threadIdx.x; i < 3 * 256; i += kThreads) s_h[i] = 0;
     for (int i = threadIdx.x; i < 257; i += kThreads) s_d0[i] = 0;
     __syncthreads();
@@ -673,51 +678,111 @@ __global__ void __launch_bounds__(kThreads) k_dup_coarse(int n_items, const uint
 
     const int64_t k = base + threadIdx.x;
     const uint32_t item = k < n_items ? perm[k] : 0u;
-    const uint32_t c = k < n_items ? cnt[item] : 0u;
     int x0 = 0, x1 = -1, y0 = 0, y1 = -1, stx = 0, stb = 0;
+    bool vis = false;
     TightRows t{};
-    if (c > 0) {
+    if (k < n_items) {
         const int v = (int)(item / (uint32_t)sv.n_per_view);
         const ViewDesc& vd = sv.views[v];
         const float2 m = mean2d[item];
-        tile_rect(m.x, m.y, radius[item], vd.W, vd.H, x0, x1, y0, y1);
+        vis = tile_rect(m.x, m.y, radius[item], vd.W, vd.H, x0, x1, y0, y1);
         stx = sv.st_x[v];
         stb = sv.st_begin[v];
-        if constexpr (TIGHT) t = item_tight_rows(sv, mean2d, item);
+        if constexpr (TIGHT)
+            if (vis) t = item_tight_rows(sv, mean2d, item);
     }
+    const uint32_t units = vis ? (uint32_t)(y1 / kSuper - y0 / kSuper + 1) : 0u;
+    uint4* stash = s_runs + warp * kStashUnits;
+    uint8_t* stash_n = s_n + warp * kStashUnits;
+    const int wlane0 = threadIdx.x & ~31;
+
+    // every unit's runs once: the items' supertile counts and the instance count
+    s_c[threadIdx.x] = 0;
+    __syncwarp();
+    uint32_t fine = 0;
+    warp_units(units, [&](bool act, int src, uint32_t u, uint32_t f) {
+        const int bx0 = __shfl_sync(0xffffffffu, x0, src), bx1 = __shfl_sync(0xffffffffu, x1, src);
+        const int by0 = __shfl_sync(0xffffffffu, y0, src), by1 = __shfl_sync(0xffffffffu, y1, src);
+        TightRows bt{};
+        if constexpr (TIGHT) bt = shfl_rows(t, src);
+        if (act) {
+            const Runs4 rr = row_runs<TIGHT>(bt, by0 / kSuper + (int)u, bx0, bx1, by0, by1, &fine);
+            const int n = runs_union(rr, [](int, int) {});
+            atomicAdd(&s_c[wlane0 + src], (uint32_t)n);
+            if (f < kStashUnits) {
+                stash[f] = pack_runs(rr);
+                stash_n[f] = (uint8_t)min(n, 255);
+            }
+        }
+    });
+    __syncwarp();
+    const uint32_t c = s_c[threadIdx.x];
+    if (fine) atomicAdd(&s_fine, (unsigned long long)fine);
+
     uint64_t tile_sum;
     const uint64_t local = block_excl_scan<uint64_t, kThreads>((uint64_t)c, tile_sum, s_warp);
     unsigned long long* mine = status + tile;
-    if (warp == 0) {
-        if (lane == 0) st_status(mine, tile == 0 ? 2u : 1u, tile_sum);
-        uint64_t prefix = 0;
-        if (tile > 0) {
-            prefix = lookback_warp(status, tile, 1u, err);
-            if (lane == 0) st_status(mine, 2u, prefix + tile_sum);
+    const bool staged = tile_sum <= kStagePairs;  // uniform over the block
+    if (warp == 0 && lane == 0) st_status(mine, tile == 0 ? 2u : 1u, tile_sum);
+    // the tile's offset among all pairs: the look-back, then the clears that need it
+    auto resolve = [&]() {
+        if (warp == 0) {
+            uint64_t prefix = 0;
+            if (tile > 0) {
+                prefix = lookback_warp(status, tile, 1u, err);
+                if (lane == 0) st_status(mine, 2u, prefix + tile_sum);
+            }
+            if (lane == 0) {
+                s_prefix = prefix;
+                if (base + kDupTile >= n_items) *total = prefix + tile_sum;  // the last tile: the total
+            }
         }
-        if (lane == 0) {
-            s_prefix = prefix;
-            if (base + kDupTile >= n_items) *total = prefix + tile_sum;  // the last tile: the total
+        __syncthreads();
+        if (threadIdx.x == 0 && s_fine) atomicAdd(fine_total, s_fine);
+        if (coarse_tile > 0) {
+            // the sort takes at most `limit` pairs: its tiles start below it
+            const uint64_t lo = s_prefix, hi = min(s_prefix + tile_sum, limit);
+            for (uint64_t ct = (lo + coarse_tile - 1) / coarse_tile; ct * coarse_tile < hi; ++ct)
+                radix_status[ct * 256 + threadIdx.x] = 0ull;
         }
-    }
-    __syncthreads();
+    };
+    if (!staged) resolve();
+    const uint64_t gbase = staged ? 0 : s_prefix;  // where block offset 0 goes
+    // one pair at block offset p: staged, or written below `limit` (histograms counted)
+    auto put = [&](uint64_t p, uint32_t key, uint32_t val) {
+        if (staged) {
+            s_pk[p] = key;
+            s_pv[p] = val;
+        } else if (gbase + p < limit) {
+            ckey[gbase + p] = key;
+            cval[gbase + p] = val;
+        }
+    };
 
-    // the warp's pairs start at its lane 0's item offset
-    uint64_t p_warp = s_prefix + __shfl_sync(0xffffffffu, local, 0);
+    uint64_t p_warp = __shfl_sync(0xffffffffu, local, 0);  // the warp's pairs start at its lane 0's item
     const unsigned lt = (1u << lane) - 1u;
-    warp_units(c > 0 ? (uint32_t)(y1 / kSuper - y0 / kSuper + 1) : 0u, [&](bool act, int src, uint32_t u) {
+    warp_units(units, [&](bool act, int src, uint32_t u, uint32_t f) {
         const int bx0 = __shfl_sync(0xffffffffu, x0, src), bx1 = __shfl_sync(0xffffffffu, x1, src);
         const int by0 = __shfl_sync(0xffffffffu, y0, src), by1 = __shfl_sync(0xffffffffu, y1, src);
         const int bstx = __shfl_sync(0xffffffffu, stx, src), bstb = __shfl_sync(0xffffffffu, stb, src);
         const uint32_t bi = __shfl_sync(0xffffffffu, item, src);
-        TightRows bt{};
-        if constexpr (TIGHT) bt = shfl_rows(t, src);
         const int sy = by0 / kSuper + (int)u;
+        const bool again = act && f >= kStashUnits;  // beyond the stash: evaluated again
+        TightRows bt{};
+        if constexpr (TIGHT)
+            if (__any_sync(0xffffffffu, again)) bt = shfl_rows(t, src);
         Runs4 rr{};
-        uint32_t n = 0, fine = 0;
+        uint32_t n = 0;
         if (act) {
-            rr = row_runs<TIGHT>(bt, sy, bx0, bx1, by0, by1, &fine);
-            n = (uint32_t)runs_union(rr, [](int, int) {});
+            if (again) {
+                uint32_t fine2 = 0;
+                rr = row_runs<TIGHT>(bt, sy, bx0, bx1, by0, by1, &fine2);
+                n = (uint32_t)runs_union(rr, [](int, int) {});
+            } else {
+                rr = unpack_runs(stash[f]);
+                n = stash_n[f];
+                if (n == 255) n = (uint32_t)runs_union(rr, [](int, int) {});
+            }
         }
         uint32_t incl = n;
 #pragma unroll
@@ -732,14 +797,11 @@ __global__ void __launch_bounds__(kThreads) k_dup_coarse(int n_items, const uint
         if (act && !wide)
             runs_union(rr, [&](int lo, int hi) {
                 const uint32_t len = (uint32_t)(hi - lo + 1);
-                if (p < limit) {
-                    const uint32_t nw = (uint32_t)min((uint64_t)len, limit - p);
-                    for (uint32_t j = 0; j < nw; ++j) {
-                        ckey[p + j] = (krow + (uint32_t)lo + j) | (pack ? runs_mask(rr, lo + (int)j) << 16 : 0u);
-                        cval[p + j] = bi;
-                    }
-                    row_hist(krow + (uint32_t)lo, nw, passes, s_d0, s_h);
-                }
+                for (uint32_t j = 0; j < len; ++j)
+                    put(p + j, (krow + (uint32_t)lo + j) | (pack ? runs_mask(rr, lo + (int)j) << 16 : 0u), bi);
+                if (!staged && gbase + p < limit)
+                    row_hist(krow + (uint32_t)lo, (uint32_t)min((uint64_t)len, limit - (gbase + p)), passes, s_d0,
+                             s_h);
                 p += len;
             });
         unsigned wides = __ballot_sync(0xffffffffu, act && wide);
@@ -761,20 +823,30 @@ __global__ void __launch_bounds__(kThreads) k_dup_coarse(int n_items, const uint
                     lo = min(lo, wr.f[q] / kSuper);
                     hi = max(hi, wr.l[q] / kSuper);
                 }
-            for (int sx0 = lo; sx0 <= hi && wp < limit; sx0 += 32) {
+            for (int sx0 = lo; sx0 <= hi; sx0 += 32) {
                 const int sx = sx0 + lane;
                 const uint32_t m = sx <= hi ? runs_mask(wr, sx) : 0u;
                 const unsigned nz = __ballot_sync(0xffffffffu, m != 0u);
                 const uint64_t q = wp + (uint64_t)__popc(nz & lt);
-                if (m != 0u && q < limit) {
-                    ckey[q] = (wk + (uint32_t)sx) | (pack ? m << 16 : 0u);
-                    cval[q] = wi;
-                    key_hist(wk + (uint32_t)sx, passes, s_d0, s_h);
+                if (m != 0u) {
+                    put(q, (wk + (uint32_t)sx) | (pack ? m << 16 : 0u), wi);
+                    if (!staged && gbase + q < limit) key_hist(wk + (uint32_t)sx, passes, s_d0, s_h);
                 }
                 wp += (uint64_t)__popc(nz);
             }
         }
     });
+    if (staged) {
+        resolve();  // (its barrier also orders the staging before the copy)
+        const uint64_t g0 = s_prefix;
+        for (uint32_t i = threadIdx.x; i < (uint32_t)tile_sum; i += kThreads) {
+            if (g0 + i >= limit) break;
+            const uint32_t key = s_pk[i];
+            ckey[g0 + i] = key;
+            cval[g0 + i] = s_pv[i];
+            key_hist(pack ? key & 0xFFFFu : key, passes, s_d0, s_h);
+        }
+    }
     __syncthreads();
     {
         int tot;
@@ -827,7 +899,7 @@ __device__ __forceinline__ uint32_t supertile_mask(const SortViews& sv, const fl
 }
 
 // The instance counts of the supertile's tiles, added into ranges[2 t + 1]
-// (cleared by k_count), from the sorted pairs' 16-bit tile masks: the
+// (cleared by k_keys), from the sorted pairs' 16-bit tile masks: the
 // duplication packed them above the supertile id (`pack`), else they are
 // computed here and stored to masks[].  Each warp takes segments of
 // kPairSeg consecutive pairs; the pairs are sorted by supertile, so a warp's
@@ -1022,7 +1094,7 @@ __global__ void __launch_bounds__(kFineThreads) k_fine(const __grid_constant__ S
 
 // Tile ranges from the per-tile counts in ranges[2 t + 1]: an exclusive scan
 // over all tiles (one block), each bound clamped to the capacity.  Graph mode:
-// the instance count (fine_total, from k_count) to *count_out, and the
+// the instance count (fine_total, from k_dup_coarse) to *count_out, and the
 // capacity bit when it exceeds the capacity.
 constexpr int kScanThreads = 1024;
 __global__ void __launch_bounds__(kScanThreads) k_tile_scan(int num_tiles, uint32_t* __restrict__ ranges,
@@ -1062,10 +1134,10 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(int num_tiles, uint3
 }
 
 // Workspace: per-item arrays, a header cleared by one memset (digit
-// histograms, tickets, total), the look-back status words (cleared by
-// k_count), and the instance key/value double buffers.
+// histograms, tickets, counts), the look-back status words (cleared by
+// k_keys), and the pair key/value double buffers.
 struct Layout {
-    size_t cnt, dk0, dk1, dv0, dv1, hdr, hist, tickets, total, ctotal, hdr_bytes, status, status_bytes, tk0, tk1, tv0,
+    size_t dk0, dk1, dv0, dv1, hdr, hist, tickets, total, ctotal, hdr_bytes, status, status_bytes, tk0, tk1, tv0,
         tv1, total_bytes;
 };
 
@@ -1078,7 +1150,6 @@ Layout make_layout(int n, int64_t capacity) {
         return at;
     };
     const size_t N = (size_t)(n > 0 ? n : 1), C = (size_t)(capacity > 0 ? capacity : 1);
-    L.cnt = take(4 * N);
     L.dk0 = take(4 * N);
     L.dk1 = take(4 * N);
     L.dv0 = take(4 * N);
@@ -1086,8 +1157,8 @@ Layout make_layout(int n, int64_t capacity) {
     L.hdr = o;
     L.hist = take(4 * 256 * kMaxPasses);
     L.tickets = take(4 * (kMaxPasses + 1));
-    L.total = take(8);   // instances (k_count)
-    L.ctotal = take(8);  // supertile pairs (k_dup_coarse)
+    L.total = take(16);  // instances, then supertile pairs (k_dup_coarse)
+    L.ctotal = L.total + 8;
     L.hdr_bytes = o - L.hdr;
     // status words: 256 per radix tile (the largest tile count of either sort)
     // plus one per duplication tile
@@ -1172,44 +1243,19 @@ gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* ra
     }
     uint64_t* ctotal = reinterpret_cast<uint64_t*>(base + L.ctotal);
 
-    // 1. supertile counts, depth keys and their digit histograms, the instance count; clears
+    // 1. depth keys and their digit histograms; clears
     if ((e = cudaMemsetAsync(base + L.hdr, 0, L.hdr_bytes, s)) != cudaSuccess)
         return cuda_status(e, "gs_bin_sort: clear header");
     const bool tight = sv.conic != nullptr;
     unsigned long long* fine_total = reinterpret_cast<unsigned long long*>(total);
-    if (tight)
-        k_count<true, kCountItemsTight><<<(int)cdiv(n, kThreads * kCountItemsTight), kThreads, 0, s>>>(
-            n, sv2, mean2d, radius, depth, U32(L.cnt), U32(L.dk0), U32(L.dv0), hist, fine_total,
-            reinterpret_cast<uint4*>(status), L.status_bytes / 16, tile_ranges, 2 * (size_t)ntiles);
-    else
-        k_count<false, kCountItems><<<(int)cdiv(n, kThreads * kCountItems), kThreads, 0, s>>>(
-            n, sv2, mean2d, radius, depth, U32(L.cnt), U32(L.dk0), U32(L.dv0), hist, fine_total,
-            reinterpret_cast<uint4*>(status), L.status_bytes / 16, tile_ranges, 2 * (size_t)ntiles);
+    // status words: the depth sort's here; the pair sort's by the duplication (graph mode) or a
+    // memset sized by the pair count (synchronising mode)
+    const size_t depth_status_words = 256 * (size_t)radix_tiles_max(n);
+    k_keys<<<(int)cdiv(n, kThreads * kKeyItems), kThreads, 0, s>>>(
+        n, depth, U32(L.dk0), U32(L.dv0), hist, reinterpret_cast<uint4*>(status), depth_status_words / 2, dup_status,
+        (size_t)cdiv(n, kDupTile), tile_ranges, 2 * (size_t)ntiles);
     count_launches();
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: count");
-
-    // synchronising mode: the instance count, before any further work
-    uint32_t I_grid = 0;  // pairs / instances the later kernels are sized for
-    if (!graph) {
-        uint64_t I = 0;
-        if ((e = cudaMemcpyAsync(&I, total, sizeof(uint64_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-            return cuda_status(e, "gs_bin_sort: read count");
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_status(e, "gs_bin_sort: synchronize");
-        *n_instances_host = (int64_t)I;
-        if ((int64_t)I > capacity) {
-            set_error("gs_bin_sort: %llu instances exceed capacity %lld", (unsigned long long)I, (long long)capacity);
-            return GS_ERR_CAPACITY;
-        }
-        if (I == 0) return GS_OK;  // k_count cleared the ranges
-        I_grid = (uint32_t)I;      // supertile pairs <= instances
-    } else {
-        if (capacity == 0) {
-            k_tile_scan<<<1, kScanThreads, 0, s>>>(0, tile_ranges, 0, fine_total, n_instances_dev, err);
-            count_launches();
-            return cuda_status(cudaGetLastError(), "gs_bin_sort: count");
-        }
-        I_grid = (uint32_t)capacity;
-    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: keys");
 
     // 2. depth sort of all items (pass ids 0..3)
     uint32_t* dk[2] = {U32(L.dk0), U32(L.dk1)};
@@ -1219,7 +1265,7 @@ gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* ra
         return cuda_status(e, "gs_bin_sort: depth sort");
     const uint32_t* perm = dv[which];
 
-    // 3. supertile pairs in depth order (pass ids 4.. for the supertile-id histograms)
+    // 3. supertile pairs in depth order, the instance count (pass ids 4.. for the supertile-id histograms)
     int st_bits = 1;
     while ((1ll << st_bits) < sv2.total_st) ++st_bits;
     const int st_passes = (st_bits + 7) / 8;
@@ -1228,11 +1274,38 @@ gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* ra
     // up to 2^16 supertiles the pairs' tile masks ride in the key's high half
     const bool pack = st_bits <= 16;
     auto dup = tight ? k_dup_coarse<true> : k_dup_coarse<false>;
-    dup<<<(int)cdiv(n, kDupTile), kThreads, 0, s>>>(n, perm, U32(L.cnt), sv2, mean2d, radius, (uint64_t)capacity,
-                                                    st_passes, pack, tickets, dup_status, ck[0], cv[0],
-                                                    hist + 256 * 4, ctotal, err);
+    const uint32_t coarse_tile = graph ? (uint32_t)(kThreads * pass_items((uint64_t)capacity)) : 0u;
+    dup<<<(int)cdiv(n, kDupTile), kThreads, 0, s>>>(n, perm, sv2, mean2d, radius, (uint64_t)capacity, st_passes,
+                                                    pack, tickets, dup_status, ck[0], cv[0], hist + 256 * 4, ctotal,
+                                                    fine_total, status, coarse_tile, err);
     count_launches();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: duplicate");
+
+    // synchronising mode: the instance and pair counts, before any further work
+    uint32_t I_grid = 0;  // pairs the later kernels are sized for
+    if (!graph) {
+        uint64_t counts[2] = {0, 0};  // instances, supertile pairs (adjacent in the header)
+        if ((e = cudaMemcpyAsync(counts, total, sizeof(counts), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return cuda_status(e, "gs_bin_sort: read count");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_status(e, "gs_bin_sort: synchronize");
+        *n_instances_host = (int64_t)counts[0];
+        if ((int64_t)counts[0] > capacity) {
+            set_error("gs_bin_sort: %llu instances exceed capacity %lld", (unsigned long long)counts[0],
+                      (long long)capacity);
+            return GS_ERR_CAPACITY;
+        }
+        if (counts[0] == 0) return GS_OK;  // k_keys cleared the ranges
+        I_grid = (uint32_t)counts[1];
+        if ((e = cudaMemsetAsync(status, 0, 8 * 256 * (size_t)radix_tiles_max(I_grid), s)) != cudaSuccess)
+            return cuda_status(e, "gs_bin_sort: clear pair-sort status");
+    } else {
+        if (capacity == 0) {
+            k_tile_scan<<<1, kScanThreads, 0, s>>>(0, tile_ranges, 0, fine_total, n_instances_dev, err);
+            count_launches();
+            return cuda_status(cudaGetLastError(), "gs_bin_sort: count");
+        }
+        I_grid = (uint32_t)capacity;
+    }
 
     // 4. stable sort of the pairs by supertile id: each supertile's items contiguous, in depth order
     if ((e = radix_sort(ck, cv, I_grid, ctotal, st_bits, 4, ps, &which, s)) != cudaSuccess)
