@@ -28,7 +28,7 @@
  *  - Host threads may call the library at the same time, each on its own
  *    stream: launch shapes are computed once under a lock, and each persistent
  *    blend launch takes its own tile-queue slot (a pool of 1024).  Exceptions:
- *    gs_project_bin_small and gs_bin_sort_noalloc calls must not overlap (one
+ *    gs_project_bin_small, gs_render_small and gs_bin_sort_noalloc calls must not overlap (one
  *    grid-barrier word, one scratch area), and the error word is shared, so
  *    gs_sync_status() may report another call's fault.
  *  - Calls that do not synchronise can be recorded in a CUDA graph.  The
@@ -210,6 +210,33 @@ gs_status gs_project_bin_small(int32_t n, const float* means, const float* scale
                                int32_t max_per_tile, float* mean2d, float* conic, float* depth, int32_t* radius,
                                float* rgb, uint32_t* tiles_touched, uint32_t* ids, uint32_t* tile_ranges,
                                gs_stream stream);
+
+/*
+ * gs_render_small - gs_project_bin_small and the blend forward of every tile
+ * in the SAME cooperative launch: the fused project -> bin -> blend step for
+ * small scenes, where the separate launches are mostly launch latency
+ * (Sec. 2.1 (a)-(d) in one kernel; the fusion is not in the paper).  The
+ * block that orders a tile's list blends that tile from the list it holds in
+ * shared memory: Eq. 1 with Alg. 1's skip and stop rules, the exponents by
+ * the contraction of Eq. 6 on the tensor cores, 32 splats per MMA, with the
+ * operands and arithmetic of GS_BLEND_TC_FP16_SPLIT (centre reference
+ * pixels).
+ *   Inputs and outputs of gs_project_bin_small, plus opacity (n floats), bg
+ *   (HOST, 3 floats) and the outputs of gs_blend_forward: image 3 x H x W,
+ *   T_final H x W, n_contrib H x W (int32).  The images equal
+ *   gs_blend_forward's (GS_BLEND_TC_FP16_SPLIT, ref_origin 0) on the same
+ *   lists; gs_blend_backward takes T_final, n_contrib and the lists as they
+ *   are.
+ * Errors as gs_project_bin_small; a tensor-core wait that exceeded 1 s also
+ * sets GS_ERR_TIMEOUT (the affected tiles are left unwritten).  Calls must
+ * not run concurrently with each other or with gs_project_bin_small.
+ * Asynchronous.
+ */
+gs_status gs_render_small(int32_t n, const float* means, const float* scales, const float* quats, const float* sh,
+                          int32_t sh_degree, const gs_camera* cam, const float* power_min, int32_t max_per_tile,
+                          const float* opacity, const float* bg, float* mean2d, float* conic, float* depth,
+                          int32_t* radius, float* rgb, uint32_t* tiles_touched, uint32_t* ids, uint32_t* tile_ranges,
+                          float* image, float* T_final, int32_t* n_contrib, gs_stream stream);
 
 /*
  * gs_project_backward - gradient of gs_project_views (the preprocessing stage

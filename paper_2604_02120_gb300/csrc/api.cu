@@ -283,6 +283,38 @@ gs_status gs_project_bin_small(int32_t n, const float* means, const float* scale
                        "gs_project_bin_small");
 }
 
+gs_status gs_render_small(int32_t n, const float* means, const float* scales, const float* quats, const float* sh,
+                          int32_t sh_degree, const gs_camera* cam, const float* power_min, int32_t max_per_tile,
+                          const float* opacity, const float* bg, float* mean2d, float* conic, float* depth,
+                          int32_t* radius, float* rgb, uint32_t* tiles_touched, uint32_t* ids, uint32_t* tile_ranges,
+                          float* image, float* T_final, int32_t* n_contrib, gs_stream stream) {
+    g_last_error[0] = 0;
+    gs_status st = check_project_args("gs_render_small", n, sh_degree, cam, 1);
+    if (st != GS_OK) return st;
+    CamViews cv;
+    if ((st = make_cam_views("gs_render_small", cam, 1, cv)) != GS_OK) return st;
+    const long long ntiles = (long long)tiles_x(cam->width) * tiles_y(cam->height);
+    if (max_per_tile < 1 || max_per_tile > GS_SMALL_MAX_PER_TILE || ntiles * max_per_tile >= (1ll << 32) || n < 1) {
+        set_error("gs_render_small: need n >= 1, 1 <= max_per_tile <= %d and tiles * max_per_tile < 2^32",
+                  GS_SMALL_MAX_PER_TILE);
+        return GS_ERR_INVALID_ARG;
+    }
+    if (!means || !scales || !quats || !sh || !opacity || !bg || !mean2d || !conic || !depth || !radius || !rgb ||
+        !tiles_touched || !ids || !tile_ranges || !image || !T_final || !n_contrib) {
+        set_error("gs_render_small: null pointer");
+        return GS_ERR_INVALID_ARG;
+    }
+    if ((reinterpret_cast<uintptr_t>(mean2d) & 7) != 0) {
+        set_error("gs_render_small: mean2d must be 8-byte aligned");
+        return GS_ERR_INVALID_ARG;
+    }
+    const float bgv[3] = {bg[0], bg[1], bg[2]};
+    return cuda_status(launch_render_small(n, means, scales, quats, sh, sh_degree, cv, power_min, max_per_tile, mean2d,
+                                           conic, depth, radius, rgb, tiles_touched, ids, tile_ranges, opacity, bgv,
+                                           image, T_final, n_contrib, static_cast<cudaStream_t>(stream)),
+                       "gs_render_small");
+}
+
 gs_status gs_project(int32_t n, const float* means, const float* scales, const float* quats, const float* sh,
                      int32_t sh_degree, const gs_camera* cam, float* mean2d, float* conic, float* depth,
                      int32_t* radius, float* rgb, uint32_t* tiles_touched, gs_stream stream) {

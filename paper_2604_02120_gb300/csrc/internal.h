@@ -150,6 +150,12 @@ cudaError_t launch_project_bin_small(int n, const float* means, const float* sca
                                      const float* sh, int sh_degree, const CamViews& cams, const float* power_min,
                                      int max_per_tile, float* mean2d, float* conic, float* depth, int* radius,
                                      float* rgb, uint32_t* touched, uint32_t* ids, uint32_t* ranges, cudaStream_t s);
+// the same, then each tile blended (fp16-split tensor-core exponents) by the block that ordered its list
+cudaError_t launch_render_small(int n, const float* means, const float* scales, const float* quats, const float* sh,
+                                int sh_degree, const CamViews& cams, const float* power_min, int max_per_tile,
+                                float* mean2d, float* conic, float* depth, int* radius, float* rgb, uint32_t* touched,
+                                uint32_t* ids, uint32_t* ranges, const float* opacity, const float bg[3],
+                                float* image, float* T_final, int* n_contrib, cudaStream_t s);
 // gradient of launch_project summed over the views (inputs view-major, outputs per Gaussian)
 cudaError_t launch_project_bwd(int n, const float* means, const float* scales, const float* quats, const float* sh,
                                int sh_degree, const CamViews& cams, const int* radius, const float* dmean2d,

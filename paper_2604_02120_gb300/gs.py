@@ -33,7 +33,7 @@ ABI_FUNCTIONS = (
     "gs_selftest_bounded_wait", "gs_launch_count", "gs_bin_sort_noalloc", "gs_bin_sort_noalloc_max_bytes",
     "gs_project_views", "gs_bin_sort_views", "gs_blend_forward_views", "gs_blend_backward_views",
     "gs_blend_autotune", "gs_measure_peaks", "gs_alpha_power_min", "gs_project_backward",
-    "gs_project_bin_small", "gs_tile_order", "gs_pack_splats", "gs_blend_autotune_backward",
+    "gs_project_bin_small", "gs_tile_order", "gs_pack_splats", "gs_blend_autotune_backward", "gs_render_small",
 )
 
 
@@ -97,6 +97,8 @@ def load(path: str = LIB_PATH):
     lib.gs_tile_order.argtypes = [i32, i32p, i32p, vp, vp, vp]
     lib.gs_project_bin_small.argtypes = [i32, vp, vp, vp, vp, i32, ctypes.POINTER(gs_camera), vp, i32, vp, vp, vp,
                                          vp, vp, vp, vp, vp, vp]
+    lib.gs_render_small.argtypes = [i32, vp, vp, vp, vp, i32, ctypes.POINTER(gs_camera), vp, i32, vp,
+                                    ctypes.POINTER(ctypes.c_float), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gs_project_backward.argtypes = [i32, vp, vp, vp, vp, i32, ctypes.POINTER(gs_camera), i32, vp, vp, vp, vp,
                                         vp, vp, vp, vp, vp]
     lib.gs_blend_forward_views.argtypes = [i32, i32p, i32p, i32, vp, vp, vp, vp, vp, vp,
@@ -276,6 +278,17 @@ def gs_project_bin_small(n, means, scales, quats, sh, sh_degree, cam, power_min,
                                        _ptr(ids), _ptr(tile_ranges), _stream(stream)), "gs_project_bin_small")
 
 
+def gs_render_small(n, means, scales, quats, sh, sh_degree, cam, power_min, max_per_tile, opacity, bg, mean2d, conic,
+                    depth, radius, rgb, tiles_touched, ids, tile_ranges, image, T_final, n_contrib, stream=None):
+    camera = cam if isinstance(cam, gs_camera) else make_camera(cam)
+    bgv = (ctypes.c_float * 3)(*[float(x) for x in bg])
+    _check(load().gs_render_small(n, _ptr(means), _ptr(scales), _ptr(quats), _ptr(sh), sh_degree,
+                                  ctypes.byref(camera), _ptr(power_min), int(max_per_tile), _ptr(opacity), bgv,
+                                  _ptr(mean2d), _ptr(conic), _ptr(depth), _ptr(radius), _ptr(rgb),
+                                  _ptr(tiles_touched), _ptr(ids), _ptr(tile_ranges), _ptr(image), _ptr(T_final),
+                                  _ptr(n_contrib), _stream(stream)), "gs_render_small")
+
+
 SMALL_MAX_PER_TILE = 16384
 
 
@@ -309,6 +322,29 @@ def project_bin_small(means, scales, quats, sh, sh_degree, cam, max_per_tile=102
                          proj["conic"], proj["depth"], proj["radius"], proj["rgb"], proj["tiles_touched"], ids, ranges,
                          stream)
     return proj, dict(tile_ranges=ranges, ids=ids)
+
+
+def render_small(means, scales, quats, sh, sh_degree, opacities, cam, bg=(0.0, 0.0, 0.0), max_per_tile=1024,
+                 power_min=None, stream=None):
+    """gs_render_small: projection, per-tile lists and the tensor-core blend
+    forward in one cooperative launch (small scenes).  Returns (proj, bs, fwd)
+    as project(), a bin/sort dict and blend_forward() would."""
+    n = means.shape[0]
+    dev = means.device
+    f32 = dict(device=dev, dtype=torch.float32)
+    proj = dict(mean2d=torch.empty(n, 2, **f32), conic=torch.empty(n, 3, **f32), depth=torch.empty(n, **f32),
+                radius=torch.empty(n, device=dev, dtype=torch.int32), rgb=torch.empty(n, 3, **f32),
+                tiles_touched=torch.empty(n, device=dev, dtype=torch.int32))
+    nt = num_tiles(cam.width, cam.height)
+    ids = torch.empty(nt * max_per_tile, device=dev, dtype=torch.int32)
+    ranges = torch.empty(2 * nt, device=dev, dtype=torch.int32)
+    W, H = cam.width, cam.height
+    fwd = dict(image=torch.zeros(3, H, W, **f32), T_final=torch.zeros(H, W, **f32),
+               n_contrib=torch.zeros(H, W, device=dev, dtype=torch.int32))
+    gs_render_small(n, means, scales, quats, sh, sh_degree, cam, power_min, max_per_tile, opacities, bg,
+                    proj["mean2d"], proj["conic"], proj["depth"], proj["radius"], proj["rgb"], proj["tiles_touched"],
+                    ids, ranges, fwd["image"], fwd["T_final"], fwd["n_contrib"], stream)
+    return proj, dict(tile_ranges=ranges, ids=ids), fwd
 
 
 def gs_project_backward(n, means, scales, quats, sh, sh_degree, cams, radius, dmean2d, dconic, drgb, dmeans, dscales,

@@ -152,3 +152,19 @@ def check_tight_lists(got, ref, full, max_amb_frac=1e-3):
         np.testing.assert_array_equal(np.asarray(got["keys"]).view(np.uint64)[:g.size],
                                       np.asarray(full["keys"]).view(np.uint64)[pos])
     return int(amb.shape[0]), int(diff.size)
+
+
+def compare_to_oracle(out, ref, tol, nc_exact=True, max_amb=0.01):
+    """Every pixel whose decisions are clear of their thresholds: colour and
+    T_final within tol plus the first-order bound of the variant's own
+    rounding (ref["err_bound"]), n_contrib exact; ambiguous pixels bounded."""
+    amb = ref["ambiguous"]
+    ok = ~amb
+    assert amb.mean() <= max_amb, f"{amb.mean():.4%} ambiguous pixels"
+    bound = tol + ref["err_bound"][ok]
+    err = np.abs(out["image"] - ref["image"])[:, ok]
+    assert (err <= bound).all(), f"max abs {err.max():.3e} beyond {tol} + bound"
+    assert (np.abs(out["T_final"] - ref["T_final"])[ok] <= bound).all()
+    if nc_exact:
+        np.testing.assert_array_equal(out["n_contrib"][ok], ref["n_contrib"][ok])
+    return err

@@ -75,6 +75,22 @@ def test_project_bin_small_checks(lib):
             INVALID, "gs_project_bin_small")
 
 
+def test_render_small_checks(lib):
+    cam = _cam()
+    bg = (ctypes.c_float * 3)(0.0, 0.0, 0.0)
+    proj = [P] * 8  # mean2d .. tile_ranges
+    img = [P] * 3   # image, T_final, n_contrib
+    for n, mpt in ((10, 0), (10, gs.SMALL_MAX_PER_TILE + 1), (0, 16)):
+        _expect(lib, lib.gs_render_small(n, P, P, P, P, 0, ctypes.byref(cam), None, mpt, P, bg, *proj, *img, None),
+                INVALID, "gs_render_small")
+    _expect(lib, lib.gs_render_small(10, P, P, P, P, 0, ctypes.byref(cam), None, 16, P, bg, ODD, *proj[1:], *img,
+                                     None), INVALID, "gs_render_small")
+    _expect(lib, lib.gs_render_small(10, P, P, P, P, 0, ctypes.byref(cam), None, 16, None, bg, *proj, *img, None),
+            INVALID, "gs_render_small")
+    _expect(lib, lib.gs_render_small(10, P, P, P, P, 0, ctypes.byref(cam), None, 16, P, bg, *proj, P, P, None, None),
+            INVALID, "gs_render_small")
+
+
 def test_bin_sort_checks(lib):
     w, h = _sizes(64), _sizes(48)
     cnt = ctypes.c_int64(0)

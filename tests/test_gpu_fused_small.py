@@ -1,10 +1,16 @@
 """Parity of gs_project_bin_small (projection + per-tile lists in one
 cooperative launch, for small scenes) with gs_project + gs_bin_sort and with
-the FP64 oracle's bin/sort, through the C ABI.
+the FP64 oracle's bin/sort, and of gs_render_small (the same launch with the
+tensor-core blend of every tile) with gs_blend_forward and the FP64 oracle's
+blend, through the C ABI.
 
 Bars: projection outputs bit-identical to gs_project's; every tile's list
 bit-identical to gs_bin_sort's (full rectangles and opacity-aware) and to the
-oracle's; images blended from the fused lists bit-identical; a tile over
+oracle's; images blended from the fused lists bit-identical; the fused
+render's image, T_final and n_contrib bit-identical to gs_blend_forward's
+(fp16 split) on those lists and within the split variant's bar of the
+oracle's (1e-3 plus its rounding bound; n_contrib exact off ambiguous
+pixels); the backward takes its outputs as they are; a tile over
 max_per_tile reports GS_ERR_CAPACITY."""
 import numpy as np
 import pytest
@@ -13,7 +19,7 @@ import torch
 import oracle
 from paper_2604_02120_gb300 import gs, scenes
 
-from gpu_common import check_tight_lists, to_np
+from gpu_common import MAX_AMB_SPLIT, check_tight_lists, compare_to_oracle, oracle_blend_on_gpu_params, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -89,6 +95,64 @@ def test_fused_lists_equal_bin_sort(kind, tight):
     assert gs.gs_sync_status() == gs.GS_OK
     for k in ("image", "T_final", "n_contrib"):
         assert torch.equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("tight", [False, True])
+@pytest.mark.parametrize("kind", ["256x256_10k", "1280x720_10k_sh3", "tiny_ragged", "tiny_dense"])
+def test_fused_render_equals_blend_forward_and_oracle(kind, tight):
+    sc = _scene(kind)
+    cam = sc.cameras[0]
+    dev = gs.scene_to_device(sc)
+    pmin = gs.alpha_power_min(dev["opacities"]) if tight else None
+    bg = (0.1, 0.2, 0.3)
+    rproj, rbs, rfwd = gs.render_small(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"],
+                                       dev["opacities"], cam, bg=bg, max_per_tile=2048, power_min=pmin)
+    assert gs.gs_sync_status() == gs.GS_OK
+    # projection and lists as gs_project_bin_small's
+    fproj, fbs = gs.project_bin_small(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam,
+                                      max_per_tile=2048, power_min=pmin)
+    assert gs.gs_sync_status() == gs.GS_OK
+    for k in fproj:
+        assert torch.equal(rproj[k], fproj[k]), k
+    assert _tile_lists(rbs["tile_ranges"].cpu().numpy(), rbs["ids"].cpu().numpy()) == \
+        _tile_lists(fbs["tile_ranges"].cpu().numpy(), fbs["ids"].cpu().numpy())
+    # the blend of the same lists by the persistent tensor-core kernel, every built shape
+    for chunk, stages in ((32, 2), (16, 4), (0, 0)):
+        opts = gs.make_opts("fp16_split", bg=bg, chunk=chunk, stages=stages)
+        ref = gs.blend_forward(cam.width, cam.height, fbs, fproj, dev["opacities"], opts)
+        assert gs.gs_sync_status() == gs.GS_OK
+        for k in ("image", "T_final", "n_contrib"):
+            assert torch.equal(rfwd[k], ref[k]), (k, chunk, stages)
+    # the FP64 oracle's blend over the same lists and float32 splat parameters
+    pn, bn = to_np(rproj), to_np(rbs)
+    want = oracle_blend_on_gpu_params(cam, pn, bn, sc.opacities, bg=bg, variant="fp16_split")
+    compare_to_oracle(to_np(rfwd), want, 1e-3, nc_exact=True, max_amb=MAX_AMB_SPLIT)
+    assert (rfwd["n_contrib"] > 0).float().mean() > 0.05
+    # the backward takes the fused outputs as they are
+    dL = torch.from_numpy(scenes.upstream_grad(1, [cam])[0]).cuda()
+    opts = gs.make_opts("fp16_split", bg=bg)
+    g1 = gs.blend_backward(cam.width, cam.height, rbs, rproj, dev["opacities"], opts, rfwd, dL)
+    fwd2 = gs.blend_forward(cam.width, cam.height, fbs, fproj, dev["opacities"], opts)
+    g2 = gs.blend_backward(cam.width, cam.height, fbs, fproj, dev["opacities"], opts, fwd2, dL)
+    assert gs.gs_sync_status() == gs.GS_OK
+    for k in g1:  # atomics add in any order: equal up to the order of the sums
+        rel = ((g1[k] - g2[k]).norm() / g2[k].norm().clamp_min(1e-30)).item()
+        assert rel < 1e-5, (k, rel)
+
+
+def test_fused_render_capacity_and_arguments():
+    sc = _scene("tiny_dense")
+    cam = sc.cameras[0]
+    dev = gs.scene_to_device(sc)
+    assert gs.gs_sync_status() == gs.GS_OK
+    gs.render_small(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], dev["opacities"], cam,
+                    max_per_tile=4)
+    assert gs.gs_sync_status() == gs.GS_ERR_CAPACITY
+    assert gs.gs_sync_status() == gs.GS_OK
+    for mpt in (0, gs.SMALL_MAX_PER_TILE + 1):
+        with pytest.raises(gs.GsError):
+            gs.render_small(dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], dev["opacities"],
+                            cam, max_per_tile=mpt)
 
 
 def test_fused_capacity_overflow_reports():

@@ -14,7 +14,8 @@ import oracle
 from paper_2604_02120_gb300 import gs, scenes
 
 from gpu_common import (CORES, FP8_EXP_ERR, MAX_AMB_FP32, MAX_AMB_SPLIT, PLAIN_MAX_ERR, SPLIT_EXP_ERR, blend_gpu,
-                        check_tight_lists, gpu_pipeline, oracle_blend_on_gpu_params, report, to_np)
+                        check_tight_lists, compare_to_oracle, gpu_pipeline, oracle_blend_on_gpu_params, report,
+                        to_np)
 
 pytestmark = pytest.mark.gpu
 
@@ -163,20 +164,7 @@ def test_bin_sort_capacity_error_and_empty():
 
 # ------------------------------------------------------------- blend, FP32 --
 
-def _compare(out, ref, tol, nc_exact=True, max_amb=0.01):
-    """Every pixel whose decisions are clear of their thresholds: colour and
-    T_final within tol plus the first-order bound of the variant's own
-    rounding (ref["err_bound"]), n_contrib exact; ambiguous pixels bounded."""
-    amb = ref["ambiguous"]
-    ok = ~amb
-    assert amb.mean() <= max_amb, f"{amb.mean():.4%} ambiguous pixels"
-    bound = tol + ref["err_bound"][ok]
-    err = np.abs(out["image"] - ref["image"])[:, ok]
-    assert (err <= bound).all(), f"max abs {err.max():.3e} beyond {tol} + bound"
-    assert (np.abs(out["T_final"] - ref["T_final"])[ok] <= bound).all()
-    if nc_exact:
-        np.testing.assert_array_equal(out["n_contrib"][ok], ref["n_contrib"][ok])
-    return err
+_compare = compare_to_oracle
 
 
 @pytest.mark.parametrize("kind,bg", [("256x256_10k", (0, 0, 0)), ("tiny_ragged", (0.3, 0.2, 0.1)),
