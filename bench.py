@@ -85,6 +85,11 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--sustained-seconds", type=float, default=5.0)
     p.add_argument("--quick", action="store_true", help="skip the per-variant sweeps and the 1920x1080 leg")
+    p.add_argument("--step-only", action="store_true",
+                   help="time the step alone: no sweeps, no side legs (for profiler captures)")
+    p.add_argument("--resolution", default=None,
+                   help="WxH: render the configuration's scene from the same camera position at this resolution "
+                        "(smaller captures of the same kernels); the line then names the resolution")
     return p.parse_args()
 
 
@@ -414,6 +419,9 @@ def run_ours(args):
     gs.load()
     sc = scenes.make_config(args.config, seed=0)
     cam = sc.cameras[0]
+    if args.resolution:
+        rw, rh = (int(x) for x in args.resolution.lower().split("x"))
+        cam = scenes.look_at_camera((0.0, 0.0, -3.0), (0.0, 0.0, 0.0), rw, rh)
     W, H = cam.width, cam.height
     dev = gs.scene_to_device(sc)
     tight = not args.full_lists
@@ -554,7 +562,7 @@ def run_ours(args):
 
     # ---- the forward's splat staging: TMA gathers of packed records against per-thread loads
     producer = None
-    if args.variant != "fp32" and st.rec is not None:
+    if args.variant != "fp32" and st.rec is not None and not args.step_only:
         gs.pack_splats(st.proj, dev["opacities"], out=st.rec)
         o_tma = gs.make_opts(args.variant, chunk=st.opts.chunk, stages=st.opts.stages, tile_order=st.order,
                              shard_count=ws_n, shard_index=rank, splat_records=st.rec)
@@ -576,31 +584,33 @@ def run_ours(args):
     hbm = read_peaks().get("hbm_gbs")
     sort_bytes = 32 * n + 4 * n_inst + 8 * gs.num_tiles(W, H)
     stages = {"project": p_ms, "bin_sort": s_ms, "blend_forward": f_ms, "blend_backward": b_ms}
-    dominant = max(stages, key=stages.get)
-    if dominant == "bin_sort":
-        achieved = sort_bytes / (s_ms / 1e3) / 1e9
-        tr = KNOWN_TRAFFIC.get("bin_sort")
-        roofline = {"bound": "hbm", "kernel": "bin/sort stage (gs_alpha_power_min + gs_bin_sort_views + "
-                                              "gs_tile_order, one CUDA graph)",
-                    "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                    "frac": round(achieved / hbm, 4) if hbm else None,
-                    "traffic": tr["bytes"] if tr and tr["config"] == args.config else None,
-                    "algorithmic_bytes": sort_bytes, "launch_ms": round(s_ms, 5),
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, burst) of measured",
-                    "note": "algorithmic bytes: 32 per Gaussian (inputs), 4 per instance (the sorted id), 8 per tile "
-                            "(range): the least a binning moves"}
-    else:
-        r = rf if dominant == "blend_forward" else rb
-        b = r["terms_g_evals_per_s"][r["bound"]]
-        roofline = {"bound": "alu" if r["bound"] in ("mufu", "fp32_issue") else r["bound"], "kernel": r["kernel"],
-                    "achieved": r["achieved_g_evals_per_s"], "peak": b["per_s"], "unit": "G evals/s",
-                    "frac": r["frac_of_bound"], "traffic": None, "launch_ms": r["launch_ms"],
-                    "peak_source": b["note"] + " (measured on this GPU)"}
+    # the dominant kernel: the longer of the two blends (each stage one kernel, timed live); the
+    # bin/sort stage is nine kernels, none of which is longer than the backward in the ncu launch
+    # list of this step, and it is reported as a stage beside
+    r = rf if f_ms > b_ms else rb
+    b = r["terms_g_evals_per_s"][r["bound"]]
+    tr = KNOWN_TRAFFIC.get(r["kernel"] + "/" + args.variant)
+    roofline = {"bound": "alu" if r["bound"] in ("mufu", "fp32_issue") else r["bound"],
+                "kernel": f"k_blend_tc_bwd ({args.variant})" if r is rb else f"k_blend_tc ({args.variant})",
+                "achieved": r["achieved_g_evals_per_s"], "peak": b["per_s"], "unit": "G evals/s",
+                "frac": r["frac_of_bound"],
+                "traffic": tr["bytes"] if tr and tr["config"] == args.config and not args.resolution else None,
+                "launch_ms": r["launch_ms"], "terms": {k: v["per_s"] for k, v in r["terms_g_evals_per_s"].items()},
+                "peak_source": b["note"] + " (measured on this GPU); the min of the MUFU, FP32-issue, HBM and "
+                               "tensor terms"}
+    achieved = sort_bytes / (s_ms / 1e3) / 1e9
+    stage_roofline = {"stage": "bin/sort (gs_alpha_power_min + gs_bin_sort_views + gs_tile_order, one CUDA graph)",
+                      "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                      "frac": round(achieved / hbm, 4) if hbm else None, "algorithmic_bytes": sort_bytes,
+                      "launch_ms": round(s_ms, 5),
+                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, burst) of measured",
+                      "note": "algorithmic bytes: 32 per Gaussian (inputs), 4 per instance (the sorted id), 8 per "
+                              "tile (range): the least a binning moves"}
     roofline["stage_ms"] = {k: round(v, 5) for k, v in stages.items()}
 
     # ---- blend-only ms/frame per variant, TC vs FP32 CUDA core, and the 1920x1080 workload
     sweep, sweep_c2, sweep_c1 = None, None, None
-    if not args.quick:
+    if not args.quick and not args.step_only:
         reps = min(max(K, 10), 30)
         sweep = variant_sweep(gs, torch, st, dL, flush, stream, reps,
                               ["fp32", "fp32_persistent", "fp16", "bf16", "fp16_split", "bf16_split", "fp8_split"])
@@ -609,18 +619,22 @@ def run_ours(args):
             sweep_c1 = run_config1(gs, torch, scenes, flush, stream, reps)
 
     # ---- projection backward (§8(f) row 1) and the small-scene fused front end (row 4)
-    pb_line = run_project_backward(gs, torch, dev, sc, cam, st, g_eager, flush, stream, min(K, 100))
-    small_line = run_small_fused(gs, torch, gs.make_opts(args.variant), flush, min(K, 100))
-    batched_line = run_batched(gs, torch, sc, dev, args.variant, flush, min(K, 50)) if args.config == 3 else None
+    side = not args.step_only
+    pb_line = run_project_backward(gs, torch, dev, sc, cam, st, g_eager, flush, stream, min(K, 100)) if side else None
+    small_line = run_small_fused(gs, torch, gs.make_opts(args.variant), flush, min(K, 100)) if side else None
+    batched_line = (run_batched(gs, torch, sc, dev, args.variant, flush, min(K, 50))
+                    if args.config == 3 and side else None)
 
     # ---- end to end through the public API with host buffers
-    e2e = run_e2e(args, gs, torch, sc, cam, st.opts, st.capacity, dL, flush, evals_step, ws_n, dist, tight)
+    e2e = run_e2e(args, gs, torch, sc, cam, st.opts, st.capacity, dL, flush, evals_step, ws_n, dist, tight) \
+        if side else None
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_n, "steps": K, "warmup": args.warmup,
         "ms_per_step": dev_ms / K, "higher_is_better": True, "scaling": "strong" if ws_n > 1 else "weak",
         "vs_baseline": None, "dtype": DTYPE_OF.get(args.variant, args.variant), "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.config] + WORKLOAD_NOTE, "blend_variant": args.variant,
+        "config": {"workload": WORKLOADS[args.config] + WORKLOAD_NOTE
+                   + (f" (rendered at {W}x{H})" if args.resolution else ""), "blend_variant": args.variant,
                    "step": "project + bin_sort + tile_order + blend_forward + blend_backward",
                    "lists": "opacity-aware (gs_alpha_power_min + conics): a splat keeps a tile only if alpha can "
                             "reach 1/255 there; same image as the full 3-sigma rectangles" if tight
@@ -637,7 +651,8 @@ def run_ours(args):
         "wall_ms_per_step": wall * 1e3 / K,
         "eager_ms_per_step": round(eager_ms, 5),
         "launches_per_step": launches_per_step,
-        "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
+        **({"e2e": e2e} if e2e else {}), "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
+        "bin_sort_roofline": stage_roofline,
         "blend_rooflines": {"forward": rf, "backward": rb},
         **({"forward_splat_staging": producer} if producer else {}),
         **({"sustained": sus} if sus else {}),
@@ -648,13 +663,13 @@ def run_ours(args):
                           "backward_issued_per_frame": issued_bwd,
                           "note": "evaluated = sum of n_contrib (the metric's pairs); issued = 256 x the splats of "
                                   "every chunk the tensor-core kernels evaluate before a tile's exit"},
-        "projection_backward": pb_line,
-        "small_scene_fused": small_line,
+        **({"projection_backward": pb_line} if pb_line else {}),
+        **({"small_scene_fused": small_line} if small_line else {}),
         **({"batched_views": batched_line} if batched_line else {}),
     }
     if ws_n > 1:
         line["all_reduce_bytes_per_step"] = int(g_grad["mean2d"]._base.numel() * 4)
-    if rank == 0 and ws_n == 1 and not args.no_cpu_baseline:  # the oracle on the host cores: N = 1 only
+    if rank == 0 and ws_n == 1 and not args.no_cpu_baseline and side:  # the oracle on the host cores: N = 1 only
         line["cpu_baseline"] = cpu_baseline(cam, st.proj, st.bs, sc, dL, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -729,10 +744,13 @@ def run_config1(gs, torch, scenes, flush, stream, reps):
 
 
 def run_small_fused(gs, torch, opts, flush, K):
-    """The 256x256, 10k-Gaussian scene (the launch-bound case): the step with
-    gs_project + gs_bin_sort_views (graph mode, 9 launches) against the step
-    with gs_project_bin_small (one cooperative launch), both followed by the
-    same blend forward and backward; L2 flushed before every step."""
+    """The 256x256, 10k-Gaussian scene (the launch-bound case), three ways,
+    each step (project, lists, blend forward and backward) captured once as a
+    CUDA graph and replayed K times, L2 flushed before every replay, CUDA
+    events around the replay: gs_project + gs_bin_sort_views (graph mode, 9
+    launches) then the blends; gs_project_bin_small (one cooperative launch)
+    then the blends; gs_render_small (projection, lists and the forward blend
+    in one cooperative launch) then the backward."""
     from paper_2604_02120_gb300 import scenes
     sc = scenes.make_config(0, seed=0)
     cam = sc.cameras[0]
@@ -746,40 +764,50 @@ def run_small_fused(gs, torch, opts, flush, K):
     ranges = torch.empty(2 * gs.num_tiles(W, H), dtype=torch.int32, device="cuda")
     count = torch.zeros(1, dtype=torch.int64, device="cuda")
     args3 = (dev["means"], dev["scales"], dev["quats"], dev["sh"], dev["sh_degree"], cam)
+    fwd_opts = gs.make_opts("fp16_split", bg=tuple(opts.bg))
 
     def unfused():
         proj = gs.project(*args3)
         gs.gs_bin_sort_views(1, n, proj["mean2d"], proj["radius"], proj["depth"], [W], [H], capacity, ws, None, ids,
                              ranges, count_dev=count)
-        return proj, dict(tile_ranges=ranges, ids=ids)
+        bs = dict(tile_ranges=ranges, ids=ids)
+        fwd = gs.blend_forward(W, H, bs, proj, dev["opacities"], opts)
+        gs.blend_backward(W, H, bs, proj, dev["opacities"], opts, fwd, dL)
 
-    def fused():
-        return gs.project_bin_small(*args3, max_per_tile=1024)
+    def fused_lists():
+        proj, bs = gs.project_bin_small(*args3, max_per_tile=1024)
+        fwd = gs.blend_forward(W, H, bs, proj, dev["opacities"], opts)
+        gs.blend_backward(W, H, bs, proj, dev["opacities"], opts, fwd, dL)
+
+    def fused_render():
+        proj, bs, fwd = gs.render_small(*args3[:5], dev["opacities"], cam, bg=tuple(opts.bg), max_per_tile=1024)
+        gs.blend_backward(W, H, bs, proj, dev["opacities"], fwd_opts, fwd, dL)
 
     out = {}
-    for name, front in (("unfused", unfused), ("fused", fused)):
-        def step():
-            proj, bs = front()
-            fwd = gs.blend_forward(W, H, bs, proj, dev["opacities"], opts)
-            gs.blend_backward(W, H, bs, proj, dev["opacities"], opts, fwd, dL)
+    for name, step in (("unfused", unfused), ("fused", fused_lists), ("fused_render", fused_render)):
         for _ in range(3):
             step()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            step()
+        for _ in range(3):
+            g.replay()
         ev = []
         for _ in range(K):
             flush.zero_()
-            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            proj, bs = front()
+            g.replay()
             b.record(stream)
-            fwd = gs.blend_forward(W, H, bs, proj, dev["opacities"], opts)
-            gs.blend_backward(W, H, bs, proj, dev["opacities"], opts, fwd, dL)
-            c.record(stream)
-            ev.append((a, b, c))
+            ev.append((a, b))
         torch.cuda.synchronize()
         assert gs.gs_sync_status() == gs.GS_OK
-        out[name] = {"ms_per_step": round(statistics.median(a.elapsed_time(c) for a, b, c in ev), 5),
-                     "project_bin_ms": round(statistics.median(a.elapsed_time(b) for a, b, c in ev), 5)}
+        out[name] = {"ms_per_step": round(statistics.median(a.elapsed_time(b) for a, b in ev), 5)}
     out["workload"] = "256x256, 10k Gaussians, SH degree 0, seed 0; step = project + bin + blend fwd + bwd"
+    out["note"] = ("unfused: 9 bin/sort launches; fused: gs_project_bin_small then the persistent blends; "
+                   "fused_render: gs_render_small (project, lists and the fp16-split tensor-core forward in one "
+                   "launch) then the backward; each step one CUDA graph replay")
     return out
 
 

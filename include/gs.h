@@ -103,8 +103,8 @@ typedef struct gs_blend_opts {
                             1 = the centre of its first pixel (x0 + 0.5, y0 + 0.5) */
     float bg[3];         /* background colour added as T_final * bg */
     int32_t bwd_stages;  /* TC backward: depth of its shared-memory ring, 0 = the variant's default
-                            (6 for fp16 operands, 2 for bf16 and FP8, the deepest that keeps 3 blocks
-                            per SM); built: 2, 4, 6 (gs_blend_autotune_backward picks one) */
+                            (6 for fp16 operands, 3 for bf16 and FP8, the deepest that keeps 3 blocks
+                            per SM); built: 2, 3, 4, 6 (gs_blend_autotune_backward picks one) */
     int64_t timeout_ns;  /* limit of every device-side wait; 0 = 1 s */
     int32_t shard_count; /* tile sharding across ranks: the call blends only the tiles t
                             (global tile ids) with t % shard_count == shard_index and leaves
@@ -481,8 +481,8 @@ gs_status gs_blend_autotune(int32_t n_views, const int32_t* widths, const int32_
 
 /*
  * gs_blend_autotune_backward - the same for the tensor-core backward pass:
- * runs gs_blend_backward_views with each built ring depth (bwd_stages 2, 4,
- * 6), `reps` timed calls each, and sets opts->bwd_stages to the fastest
+ * runs gs_blend_backward_views with each built ring depth (bwd_stages 2, 3,
+ * 4, 6), `reps` timed calls each, and sets opts->bwd_stages to the fastest
  * (not in the paper: its batch-size study, Sec. 4.4, picks the mini-batch
  * shape by measurement).  Arguments as gs_blend_backward_views; the gradient
  * buffers are accumulated into many times, so their contents afterwards are

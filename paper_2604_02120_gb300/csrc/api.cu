@@ -521,7 +521,7 @@ gs_status gs_blend_backward_views(int32_t n_views, const int32_t* widths, const 
     GradArgs g{T_final, n_contrib, dL_dimage, reinterpret_cast<float2*>(dmean2d), dconic, dopacity, drgb};
     if (is_tc(o->variant)) {
         if (!tc_bwd_stages_supported(o->bwd_stages)) {
-            set_error("gs_blend_backward: bwd_stages %d not built (0, 2, 4, 6)", o->bwd_stages);
+            set_error("gs_blend_backward: bwd_stages %d not built (0, 2, 3, 4, 6)", o->bwd_stages);
             return GS_ERR_UNSUPPORTED;
         }
         return cuda_status(launch_blend_tc_bwd(a, g, o->variant, o->bwd_stages, stream), "gs_blend_backward");
@@ -601,7 +601,7 @@ gs_status gs_blend_autotune_backward(int32_t n_views, const int32_t* widths, con
         set_error("gs_blend_autotune_backward: needs a TC variant and reps >= 1");
         return GS_ERR_INVALID_ARG;
     }
-    static const int kStages[] = {2, 4, 6};
+    static const int kStages[] = {2, 3, 4, 6};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     gs_status st = cuda_status(cudaEventCreate(&e0), "gs_blend_autotune_backward: event");
     if (st == GS_OK) st = cuda_status(cudaEventCreate(&e1), "gs_blend_autotune_backward: event");

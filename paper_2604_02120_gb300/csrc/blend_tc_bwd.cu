@@ -19,6 +19,8 @@ cudaError_t launch_blend_tc_bwd(const BlendArgs& a0, const GradArgs& g, int vari
     return cudaErrorInvalidValue;
 }
 
-bool tc_bwd_stages_supported(int stages) { return stages == 0 || stages == 2 || stages == 4 || stages == 6; }
+bool tc_bwd_stages_supported(int stages) {
+    return stages == 0 || stages == 2 || stages == 3 || stages == 4 || stages == 6;
+}
 
 }  // namespace gs

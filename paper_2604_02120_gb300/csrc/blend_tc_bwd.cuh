@@ -50,12 +50,12 @@ namespace tc {
 
 constexpr int kBwdChunk = 16;
 // Built depths of the shared-memory ring: 6 (fp16 operands: the deepest that
-// keeps 3 blocks per SM, 75.9 KB each), 4 and 2 (bf16 and FP8 rows are twice
-// as wide; 2 stages keep 3 blocks per SM for them).
-constexpr int kBwdStagesBuilt[3] = {2, 4, 6};
+// keeps 3 blocks per SM, 75.9 KB each), 3 (bf16 and FP8 rows are twice as
+// wide: 76.4 KB, the deepest that keeps 3 blocks per SM for them), 4 and 2.
+constexpr int kBwdStagesBuilt[4] = {2, 3, 4, 6};
 template <int V>
 constexpr int bwd_default_stages() {
-    return (V == GS_BLEND_TC_BF16_SPLIT || V == GS_BLEND_TC_FP8_SPLIT) ? 2 : 6;
+    return (V == GS_BLEND_TC_BF16_SPLIT || V == GS_BLEND_TC_FP8_SPLIT) ? 3 : 6;
 }
 constexpr float kTScale = 4096.0f;  // 2^12
 
@@ -103,8 +103,8 @@ struct BwdLayout {
     static constexpr int OFF_A1 = OFF_B2 + B2_BYTES;
     static constexpr int OFF_B1 = OFF_A1 + A1_BYTES;
     static constexpr int OFF_REC = OFF_B1 + SS * B1_BYTES;
-    static constexpr int OFF_SCL = OFF_REC + SS * CH * (int)sizeof(Rec);  // FP8: row scales
-    static constexpr int OFF_FIN = OFF_SCL + SS * CH * 8;
+    static constexpr int OFF_SCL = OFF_REC + SS * CH * (int)sizeof(Rec);  // FP8 only: row scales
+    static constexpr int OFF_FIN = OFF_SCL + (Traits<V>::FP8 ? SS * CH * 8 : 0);
     static constexpr int OFF_BAR = OFF_FIN + SS * CH * (int)sizeof(Fin);
     // full[SS], empty[SS], tfull[2], tempty[2], a2full[2], m2done[2], drain
     static constexpr int NBAR = 2 * SS + 2 * kTStages + 5;
@@ -457,7 +457,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
         // A tile's header (queue item, range, the largest n_contrib and
         // |dL/dimage| of its pixels, the scales) is worked out for the next
         // tile once the current tile's first stage is out, so those loads
-        // overlap the current tile's chunks.
+        // overlap the current tile's chunks and leave the tile's pixel data in
+        // the cache for the epilogue.
         struct TileHead {
             int q, tile, len, vview, nch;
             uint32_t start;
@@ -486,6 +487,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
                 const int px = x0 + (p & 15), py = y0 + (p >> 4);
                 if (px < vd.W && py < vd.H) {
                     const size_t pp = (size_t)py * vd.W + px;
+                    // T_final is read by the epilogue when the tile starts (n_contrib and
+                    // dL/dimage pass through the cache here already)
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(gr.T_final + vd.pix_off + pp));
                     maxnc = max(maxnc, gr.n_contrib[vd.pix_off + pp]);
                     const float* dl = gr.dL_dimage + 3 * vd.pix_off + pp;
                     gmax = fmaxf(gmax, fmaxf(fabsf(dl[0]), fmaxf(fabsf(dl[plane]), fabsf(dl[2 * plane]))));
@@ -703,6 +707,7 @@ template <int V>
 cudaError_t launch_bwd_stages(const BlendArgs& a, const GradArgs& g, int stages, cudaStream_t s) {
     if (stages == 0) stages = bwd_default_stages<V>();
     if (stages == 2) return launch_bwd_inst<V, 2>(a, g, s);
+    if (stages == 3) return launch_bwd_inst<V, 3>(a, g, s);
     if (stages == 4) return launch_bwd_inst<V, 4>(a, g, s);
     if (stages == 6) return launch_bwd_inst<V, 6>(a, g, s);
     return cudaErrorInvalidValue;

@@ -495,7 +495,7 @@ def test_tc_blend_backward_matches_oracle_gradient(kind, variant):
 
 @pytest.mark.parametrize("variant", ["fp16_split", "bf16_split", "fp8_split"])
 def test_tc_backward_ring_depths_agree_and_autotune(variant):
-    """Every built ring depth of the tensor-core backward (bwd_stages 2, 4, 6
+    """Every built ring depth of the tensor-core backward (bwd_stages 2, 3, 4, 6
     and the variant's default) gives the same gradients up to the order of
     atomic additions, and gs_blend_autotune_backward picks a built depth."""
     sc, dev, cam, proj, bs, pn, bn = pipeline("1280x720_20k")
@@ -503,7 +503,7 @@ def test_tc_backward_ring_depths_agree_and_autotune(variant):
     fwd = gs.blend_forward(cam.width, cam.height, bs, proj, dev["opacities"], opts)
     dL = torch.randn(3, cam.height, cam.width, device="cuda", generator=torch.Generator("cuda").manual_seed(2))
     ref = gs.blend_backward(cam.width, cam.height, bs, proj, dev["opacities"], opts, fwd, dL)
-    for st in (2, 4, 6):
+    for st in (2, 3, 4, 6):
         o = gs.make_opts(variant, bg=(0.1, 0.2, 0.3), bwd_stages=st)
         g = gs.blend_backward(cam.width, cam.height, bs, proj, dev["opacities"], o, fwd, dL)
         assert gs.gs_sync_status() == gs.GS_OK
@@ -513,9 +513,9 @@ def test_tc_backward_ring_depths_agree_and_autotune(variant):
     ms = gs.gs_blend_autotune_backward([cam.width], [cam.height], 0, bs["tile_ranges"], bs["ids"], proj["mean2d"],
                                        proj["conic"], dev["opacities"], proj["rgb"], opts, fwd["T_final"],
                                        fwd["n_contrib"], dL, scratch, reps=2)
-    assert ms > 0 and opts.bwd_stages in (2, 4, 6)
+    assert ms > 0 and opts.bwd_stages in (2, 3, 4, 6)
     with pytest.raises(gs.GsError):
-        gs.blend_backward(cam.width, cam.height, bs, proj, dev["opacities"], gs.make_opts(variant, bwd_stages=3),
+        gs.blend_backward(cam.width, cam.height, bs, proj, dev["opacities"], gs.make_opts(variant, bwd_stages=5),
                           fwd, dL)
 
 
