@@ -638,7 +638,7 @@ __device__ __forceinline__ Runs4 unpack_runs(uint4 v) {
 // list still sorts into a permutation of what was written.  With coarse_tile
 // > 0 the block also clears the look-back status words (256 per radix tile,
 // at radix_status) of the pair sort's tiles that start within its pairs
-// (below `limit`).
+// (below `limit`), and the blocks together zero st_zero[0, st_n).
 constexpr uint32_t kWideRow = 8;
 constexpr uint32_t kStashUnits = 128;  // per warp
 constexpr uint32_t kStagePairs = 2048;
@@ -652,10 +652,13 @@ __global__ void __launch_bounds__(kThreads) k_dup_coarse(int n_items, const uint
                                                          uint32_t* __restrict__ hist, uint64_t* __restrict__ total,
                                                          unsigned long long* __restrict__ fine_total,
                                                          unsigned long long* __restrict__ radix_status,
-                                                         uint32_t coarse_tile, unsigned* err) {
+                                                         uint32_t coarse_tile, uint32_t* __restrict__ st_zero,
+                                                         int st_n, unsigned* err) {
     __shared__ uint64_t s_warp[kThreads / 32 + 1];
     __shared__ uint64_t s_prefix;
     __shared__ unsigned long long s_fine;
+    if (st_zero != nullptr)  // the supertile counters of k_pair_masks
+        for (int i = blockIdx.x * kThreads + threadIdx.x; i < st_n; i += gridDim.x * kThreads) st_zero[i] = 0;
     __shared__ uint32_t s_tile;
     __shared__ uint32_t s_h[3 * 256];  // digits 1..3
     __shared__ int s_d0[257];          // digit 0, as a difference array
@@ -907,7 +910,8 @@ __device__ __forceinline__ uint32_t supertile_mask(const SortViews& sv, const fl
 // bits with four lane reductions (bit j of every mask spread to its own byte)
 // into lane j's count, adding it to ranges with one atomic per tile when the
 // supertile changes.  32 pairs of several supertiles: one atomic per group
-// of equal supertiles and tile.
+// of equal supertiles and tile.  With st_count (zeroed by k_dup_coarse), each
+// supertile's total is added there as well.
 constexpr uint32_t kPairSeg = 512;
 template <bool TIGHT>
 __global__ void __launch_bounds__(kThreads) k_pair_masks(const __grid_constant__ SortViews sv,
@@ -917,7 +921,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_masks(const __grid_constant__
                                                          const uint32_t* __restrict__ cval, uint32_t n_host,
                                                          const uint64_t* __restrict__ n_dev, uint32_t n_items,
                                                          bool pack, uint16_t* __restrict__ masks,
-                                                         uint32_t* __restrict__ ranges) {
+                                                         uint32_t* __restrict__ ranges, uint32_t* st_count) {
     const uint32_t Ic = pass_count(n_host, n_dev);
     const int lane = threadIdx.x & 31;
     // tile j of supertile key (global id) as a global tile index
@@ -937,6 +941,10 @@ __global__ void __launch_bounds__(kThreads) k_pair_masks(const __grid_constant__
         uint32_t acc = 0;            // lane j < 16: its count of tile j
         auto flush = [&]() {
             if (cur != 0xffffffffu && lane < 16 && acc) atomicAdd(&ranges[2 * tile_of(cur, lane) + 1], acc);
+            if (st_count != nullptr) {  // the supertile's total
+                const uint32_t all = __reduce_add_sync(0xffffffffu, lane < 16 ? acc : 0u);
+                if (cur != 0xffffffffu && lane == 0 && all) atomicAdd(&st_count[cur], all);
+            }
             acc = 0;
         };
         for (uint64_t b = s0; b < s1; b += 32) {
@@ -965,11 +973,14 @@ __global__ void __launch_bounds__(kThreads) k_pair_masks(const __grid_constant__
                 cur = 0xffffffffu;
                 const unsigned peers = __match_any_sync(0xffffffffu, key);
                 const bool leader = lane == __ffs(peers) - 1 && key != 0xffffffffu;
+                uint32_t all = 0;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const unsigned bj = __ballot_sync(0xffffffffu, (m >> j) & 1u) & peers;
                     if (leader && bj) atomicAdd(&ranges[2 * tile_of(key, j) + 1], (uint32_t)__popc(bj));
+                    all += (uint32_t)__popc(bj);
                 }
+                if (st_count != nullptr && leader && all) atomicAdd(&st_count[key], all);
                 continue;
             }
             if (k0 != cur) {
@@ -988,7 +999,8 @@ __global__ void __launch_bounds__(kThreads) k_pair_masks(const __grid_constant__
     }
 }
 
-// One block per supertile s, after k_tile_scan: its items are the sorted pairs
+// One block per supertile s (st_order[blockIdx], the largest first, when
+// given), after k_tile_scan: its items are the sorted pairs
 // [cs, ce) with key s; every instance's id (and key) goes to its tile's next
 // position, in item order, from the pairs' tile masks (in the key's high half
 // when kmask is 0xFFFF, else in masks[]).  Rounds of kFineRound pairs, the
@@ -1004,6 +1016,7 @@ __global__ void __launch_bounds__(kFineThreads) k_fine(const __grid_constant__ S
                                                        const uint64_t* __restrict__ n_dev, uint32_t kmask,
                                                        const uint16_t* __restrict__ masks,
                                                        const uint32_t* __restrict__ ranges,
+                                                       const uint32_t* __restrict__ st_order,
                                                        uint32_t* __restrict__ ids_out, uint64_t* __restrict__ keys_out) {
     constexpr int Q = kFineThreads / 16;        // workers per tile
     constexpr int P = kFineRound / Q;           // pairs per worker
@@ -1014,7 +1027,7 @@ __global__ void __launch_bounds__(kFineThreads) k_fine(const __grid_constant__ S
     __shared__ uint32_t s_item[kFineRound];
     __shared__ uint32_t s_q[Q][16];
     __shared__ uint32_t s_out[16][kFineRound + 1];  // rows one word apart in bank
-    const int s = blockIdx.x;
+    const int s = st_order != nullptr ? (int)st_order[blockIdx.x] : (int)blockIdx.x;  // largest first
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int v = 0;
     while (v + 1 < sv.num_views && sv.st_begin[v + 1] <= s) ++v;
@@ -1093,15 +1106,28 @@ __global__ void __launch_bounds__(kFineThreads) k_fine(const __grid_constant__ S
 }
 
 // Tile ranges from the per-tile counts in ranges[2 t + 1]: an exclusive scan
-// over all tiles (one block), each bound clamped to the capacity.  Graph mode:
-// the instance count (fine_total, from k_dup_coarse) to *count_out, and the
-// capacity bit when it exceeds the capacity.
+// over all tiles (one block), each bound clamped to the capacity.  With
+// st_order: the supertiles in decreasing order of their instance counts
+// (st_count, from k_pair_masks), by octave buckets
+// (st_order, total_st entries), so that the fine writes start the longest
+// supertiles first (the order within a bucket is arbitrary; the output does
+// not depend on it).  Graph mode: the instance count (fine_total, from
+// k_dup_coarse) to *count_out, and the capacity bit when it exceeds the
+// capacity.
 constexpr int kScanThreads = 1024;
-__global__ void __launch_bounds__(kScanThreads) k_tile_scan(int num_tiles, uint32_t* __restrict__ ranges,
-                                                            uint64_t cap, const unsigned long long* fine_total,
-                                                            int64_t* count_out, unsigned* err) {
+constexpr int kStBuckets = 33;  // 0: empty, b: counts in [2^(b-1), 2^b)
+__device__ __forceinline__ int octave(uint32_t x) { return x == 0 ? 0 : 32 - __clz(x); }
+__global__ void __launch_bounds__(kScanThreads) k_tile_scan(const __grid_constant__ SortViews sv, int num_tiles,
+                                                            uint32_t* __restrict__ ranges, uint64_t cap,
+                                                            const unsigned long long* fine_total,
+                                                            int64_t* count_out, const uint32_t* st_count,
+                                                            uint32_t* __restrict__ st_order, unsigned* err) {
     __shared__ uint64_t s_warp[kScanThreads / 32 + 1];
-    constexpr int PER = 4;
+    __shared__ uint32_t s_bk[kStBuckets];
+    constexpr int PER = 16;  // consecutive tiles per thread and round
+    const int nst = sv.total_st;
+    if (threadIdx.x < kStBuckets) s_bk[threadIdx.x] = 0;
+    __syncthreads();
     uint64_t run = 0;
     for (int64_t b = 0; b < num_tiles; b += (int64_t)kScanThreads * PER) {
         uint32_t c[PER];
@@ -1125,6 +1151,22 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(int num_tiles, uint3
             pre += c[k];
         }
         run += tot;
+    }
+    if (st_order != nullptr) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < nst; i += kScanThreads) atomicAdd(&s_bk[octave(__ldcg(st_count + i))], 1u);
+        __syncthreads();
+        if (threadIdx.x == 0) {  // bucket starts, the largest octave first
+            uint32_t acc = 0;
+            for (int k = kStBuckets - 1; k >= 0; --k) {
+                const uint32_t n = s_bk[k];
+                s_bk[k] = acc;
+                acc += n;
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nst; i += kScanThreads)
+            st_order[atomicAdd(&s_bk[octave(__ldcg(st_count + i))], 1u)] = (uint32_t)i;
     }
     if (threadIdx.x == 0 && count_out != nullptr) {
         const uint64_t all = *fine_total;
@@ -1275,9 +1317,14 @@ gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* ra
     const bool pack = st_bits <= 16;
     auto dup = tight ? k_dup_coarse<true> : k_dup_coarse<false>;
     const uint32_t coarse_tile = graph ? (uint32_t)(kThreads * pass_items((uint64_t)capacity)) : 0u;
+    // per-supertile instance counts and their order, largest first, in the depth keys'
+    // buffers (free once the depth sort is done), when they fit
+    const int nst = sv2.total_st;
+    uint32_t* st_count = nst <= n ? dk[0] : nullptr;
+    uint32_t* st_order = nst <= n ? dk[1] : nullptr;
     dup<<<(int)cdiv(n, kDupTile), kThreads, 0, s>>>(n, perm, sv2, mean2d, radius, (uint64_t)capacity, st_passes,
                                                     pack, tickets, dup_status, ck[0], cv[0], hist + 256 * 4, ctotal,
-                                                    fine_total, status, coarse_tile, err);
+                                                    fine_total, status, coarse_tile, st_count, nst, err);
     count_launches();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: duplicate");
 
@@ -1300,7 +1347,8 @@ gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* ra
             return cuda_status(e, "gs_bin_sort: clear pair-sort status");
     } else {
         if (capacity == 0) {
-            k_tile_scan<<<1, kScanThreads, 0, s>>>(0, tile_ranges, 0, fine_total, n_instances_dev, err);
+            k_tile_scan<<<1, kScanThreads, 0, s>>>(sv2, 0, tile_ranges, 0, fine_total, n_instances_dev, nullptr,
+                                                   nullptr, err);
             count_launches();
             return cuda_status(cudaGetLastError(), "gs_bin_sort: count");
         }
@@ -1312,7 +1360,6 @@ gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* ra
         return cuda_status(e, "gs_bin_sort: supertile sort");
 
     // 5. per-tile counts, tile ranges, then every instance's id at its place
-    const int nst = sv2.total_st;
     // the pairs' tile masks go to the free half of the pair buffers (2 bytes per pair)
     uint16_t* masks = reinterpret_cast<uint16_t*>(ck[which ^ 1]);
     auto pair_masks = tight ? k_pair_masks<true> : k_pair_masks<false>;
@@ -1326,15 +1373,16 @@ gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* ra
     }
     pair_masks<<<(int)std::min<int64_t>(pair_grid, cdiv(I_grid, (int64_t)kPairSeg * (kThreads / 32))), kThreads, 0,
                  s>>>(
-        sv2, mean2d, radius, ck[which], cv[which], I_grid, ctotal, (uint32_t)n, pack, masks, tile_ranges);
+        sv2, mean2d, radius, ck[which], cv[which], I_grid, ctotal, (uint32_t)n, pack, masks, tile_ranges, st_count);
     count_launches();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: tile counts");
-    k_tile_scan<<<1, kScanThreads, 0, s>>>(ntiles, tile_ranges, (uint64_t)capacity, fine_total,
-                                           graph ? n_instances_dev : nullptr, err);
+    k_tile_scan<<<1, kScanThreads, 0, s>>>(sv2, ntiles, tile_ranges, (uint64_t)capacity, fine_total,
+                                           graph ? n_instances_dev : nullptr, st_count, st_order, err);
     count_launches();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: tile ranges");
     k_fine<<<nst, kFineThreads, 0, s>>>(sv2, depth, ck[which], cv[which], I_grid, ctotal,
-                                        pack ? 0xFFFFu : 0xFFFFFFFFu, masks, tile_ranges, ids_sorted, keys_sorted);
+                                        pack ? 0xFFFFu : 0xFFFFFFFFu, masks, tile_ranges, st_order, ids_sorted,
+                                        keys_sorted);
     count_launches();
     return cuda_status(cudaGetLastError(), "gs_bin_sort: write lists");
 }
