@@ -1122,34 +1122,43 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(const __grid_constan
                                                             const unsigned long long* fine_total,
                                                             int64_t* count_out, const uint32_t* st_count,
                                                             uint32_t* __restrict__ st_order, unsigned* err) {
+    constexpr int PER = 4;                       // consecutive tiles per thread and round
+    constexpr int R = kScanThreads * PER;        // tiles per round
     __shared__ uint64_t s_warp[kScanThreads / 32 + 1];
     __shared__ uint32_t s_bk[kStBuckets];
-    constexpr int PER = 16;  // consecutive tiles per thread and round
+    __shared__ uint32_t s_a[R + R / 32], s_b[R + R / 32];  // counts, then begins and ends (padded)
+    auto at = [](int i) { return i + (i >> 5); };
     const int nst = sv.total_st;
     if (threadIdx.x < kStBuckets) s_bk[threadIdx.x] = 0;
-    __syncthreads();
     uint64_t run = 0;
-    for (int64_t b = 0; b < num_tiles; b += (int64_t)kScanThreads * PER) {
+    for (int64_t b = 0; b < num_tiles; b += R) {
+        // the round's counts, consecutive threads on consecutive tiles
+        for (int i = threadIdx.x; i < R; i += kScanThreads)
+            s_a[at(i)] = b + i < num_tiles ? ranges[2 * (b + i) + 1] : 0u;
+        __syncthreads();
         uint32_t c[PER];
         uint64_t sum = 0;
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            const int64_t t = b + (int64_t)threadIdx.x * PER + k;
-            c[k] = t < num_tiles ? ranges[2 * t + 1] : 0u;
+            c[k] = s_a[at(threadIdx.x * PER + k)];
             sum += c[k];
         }
         uint64_t tot;
         uint64_t pre = run + block_excl_scan<uint64_t, kScanThreads>(sum, tot, s_warp);
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            const int64_t t = b + (int64_t)threadIdx.x * PER + k;
-            if (t < num_tiles) {
-                const uint64_t e = pre + c[k];
-                ranges[2 * t] = (uint32_t)(c[k] > 0 ? min(pre, cap) : 0);
-                ranges[2 * t + 1] = (uint32_t)(c[k] > 0 ? min(e, cap) : 0);
-            }
+            const int i = threadIdx.x * PER + k;
+            s_a[at(i)] = (uint32_t)(c[k] > 0 ? min(pre, cap) : 0);
+            s_b[at(i)] = (uint32_t)(c[k] > 0 ? min(pre + c[k], cap) : 0);
             pre += c[k];
         }
+        __syncthreads();
+        for (int i = threadIdx.x; i < R; i += kScanThreads)
+            if (b + i < num_tiles) {
+                ranges[2 * (b + i)] = s_a[at(i)];
+                ranges[2 * (b + i) + 1] = s_b[at(i)];
+            }
+        __syncthreads();  // s_a is reloaded next round
         run += tot;
     }
     if (st_order != nullptr) {
