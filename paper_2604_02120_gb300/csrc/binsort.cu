@@ -1000,14 +1000,15 @@ __global__ void __launch_bounds__(kThreads) k_pair_masks(const __grid_constant__
 }
 
 // One block per supertile s (st_order[blockIdx], the largest first, when
-// given), after k_tile_scan: its items are the sorted pairs
-// [cs, ce) with key s; every instance's id (and key) goes to its tile's next
-// position, in item order, from the pairs' tile masks (in the key's high half
-// when kmask is 0xFFFF, else in masks[]).  Rounds of kFineRound pairs, the
-// next round's loads in flight during the current one: thread (q, j) places
-// tile j's instances among the round's pairs [P q, P q + P) into a
-// shared-memory stage of the round's output of each tile, then warp w writes
-// the runs of tiles w and w + 8 with consecutive lanes on consecutive ids.
+// given), after k_tile_scan: its items are the sorted pairs [cs, ce) with
+// key s; every instance's id (and key) goes to its tile's next position, in
+// item order, from the pairs' tile masks (in the key's high half when kmask
+// is 0xFFFF, else in masks[]).  Rounds of kFineRound pairs, the next round's
+// loads in flight during the current one: warp w owns tiles w and w + 8 and
+// walks the round's pairs 32 at a time, one ballot per group giving each
+// pair's place in the tile's run and the run's length, into a shared-memory
+// stage of the tile's ids; it then writes the run with consecutive lanes on
+// consecutive ids.
 constexpr int kFineThreads = 256, kFineRound = 512;
 __global__ void __launch_bounds__(kFineThreads) k_fine(const __grid_constant__ SortViews sv,
                                                        const float* __restrict__ depth,
@@ -1018,17 +1019,16 @@ __global__ void __launch_bounds__(kFineThreads) k_fine(const __grid_constant__ S
                                                        const uint32_t* __restrict__ ranges,
                                                        const uint32_t* __restrict__ st_order,
                                                        uint32_t* __restrict__ ids_out, uint64_t* __restrict__ keys_out) {
-    constexpr int Q = kFineThreads / 16;        // workers per tile
-    constexpr int P = kFineRound / Q;           // pairs per worker
     constexpr int PT = kFineRound / kFineThreads;  // pairs each thread loads
+    constexpr int TW = 16 / (kFineThreads / 32);  // tiles per warp
     __shared__ uint32_t s_rng[2];
-    __shared__ uint32_t s_beg[16], s_end[16], s_run[16], s_tot[16];
+    __shared__ uint32_t s_beg[16], s_end[16], s_run[16];
     __shared__ uint16_t s_mask[kFineRound];
     __shared__ uint32_t s_item[kFineRound];
-    __shared__ uint32_t s_q[Q][16];
-    __shared__ uint32_t s_out[16][kFineRound + 1];  // rows one word apart in bank
+    __shared__ uint32_t s_out[16][kFineRound];
     const int s = st_order != nullptr ? (int)st_order[blockIdx.x] : (int)blockIdx.x;  // largest first
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     int v = 0;
     while (v + 1 < sv.num_views && sv.st_begin[v + 1] <= s) ++v;
     const ViewDesc& vd = sv.views[v];
@@ -1059,7 +1059,6 @@ __global__ void __launch_bounds__(kFineThreads) k_fine(const __grid_constant__ S
         }
     };
     fetch(cs);
-    const int j = threadIdx.x & 15, q = threadIdx.x >> 4;
     for (uint32_t r0 = cs; r0 < ce; r0 += kFineRound) {
 #pragma unroll
         for (int i = 0; i < PT; ++i) {
@@ -1068,23 +1067,19 @@ __global__ void __launch_bounds__(kFineThreads) k_fine(const __grid_constant__ S
         }
         if (r0 + kFineRound < ce) fetch(r0 + kFineRound);
         __syncthreads();
-        uint32_t cnt = 0;
-#pragma unroll 8
-        for (int k = 0; k < P; ++k) cnt += (s_mask[P * q + k] >> j) & 1u;
-        s_q[q][j] = cnt;
-        __syncthreads();
-        uint32_t pre = 0;
+        const int ng = (int)((min(ce - r0, (uint32_t)kFineRound) + 31) / 32);  // groups of 32 pairs in the round
 #pragma unroll
-        for (int qq = 0; qq < Q; ++qq) pre += qq < q ? s_q[qq][j] : 0u;
-#pragma unroll 8
-        for (int k = 0; k < P; ++k)
-            if ((s_mask[P * q + k] >> j) & 1u) s_out[j][pre++] = s_item[P * q + k];
-        if (q == Q - 1) s_tot[j] = pre;  // the round's instances of tile j
-        __syncthreads();
-#pragma unroll
-        for (int h = 0; h < 16 / (kFineThreads / 32); ++h) {
+        for (int h = 0; h < TW; ++h) {
             const int t = warp + h * (kFineThreads / 32);
-            const uint32_t n_t = s_tot[t];
+            uint32_t n_t = 0;
+            for (int g = 0; g < ng; ++g) {
+                const int i = 32 * g + lane;
+                const bool in = (s_mask[i] >> t) & 1u;
+                const unsigned b = __ballot_sync(0xffffffffu, in);
+                if (in) s_out[t][n_t + (uint32_t)__popc(b & lt)] = s_item[i];
+                n_t += (uint32_t)__popc(b);
+            }
+            __syncwarp();
             const uint64_t p0 = (uint64_t)s_beg[t] + s_run[t];
             const uint64_t end = s_end[t];
             const uint64_t dkey = keys_out != nullptr
@@ -1099,9 +1094,10 @@ __global__ void __launch_bounds__(kFineThreads) k_fine(const __grid_constant__ S
                     if (keys_out != nullptr) keys_out[p] = dkey | __float_as_uint(depth[g]);
                 }
             }
+            __syncwarp();
+            if (lane == 0) s_run[t] += n_t;  // this warp's tile alone
         }
-        __syncthreads();
-        if (threadIdx.x < 16) s_run[threadIdx.x] += s_tot[threadIdx.x];
+        __syncthreads();  // the round's masks and items are replaced next
     }
 }
 
