@@ -512,6 +512,36 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
             th.hd.uncol = __int_as_float((127 + E - 12) << 23);
             return th;
         };
+        // The splat data of the next chunk to build, loaded while the current
+        // one is published and its stage's release is awaited (ids, then
+        // position, conic, opacity and colour; lane j and j + 16 the same splat).
+        struct Pre {
+            int seq, c;  // the chunk it belongs to (seq -1: none)
+            uint32_t g, og;
+            float2 m;
+            float A, B, C, o, cr, cg, cb;
+        };
+        Pre pf{};
+        pf.seq = -1;
+        auto prefetch = [&](int pseq, int c, uint32_t start, int len, int vview) {
+            pf.seq = pseq;
+            pf.c = c;
+            const int j = lane & 15, n = min(CH, len - c * CH);
+            if (j < n) {
+                pf.g = a.ids[start + (uint32_t)(c * CH + j)];
+                pf.m = a.mean2d[pf.g];
+                pf.A = a.conic[3 * pf.g];
+                pf.B = a.conic[3 * pf.g + 1];
+                pf.C = a.conic[3 * pf.g + 2];
+                pf.og = pf.g - (uint32_t)(vview * a.n_per_view);
+                pf.o = a.opac[pf.og];
+                if (lane < 16) {
+                    pf.cr = a.rgb[3 * pf.g];
+                    pf.cg = a.rgb[3 * pf.g + 1];
+                    pf.cb = a.rgb[3 * pf.g + 2];
+                }
+            }
+        };
         int k = 0;
         bool quit = false;
         int q_next = 0;
@@ -529,6 +559,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
             const float bx0 = origin ? -15.0f : -7.5f, bx1 = origin ? 0.0f : 7.5f;
             const float by0 = origin ? -7.0f : -3.5f, by1 = origin ? 0.0f : 3.5f;
             for (int cc = 0; cc < nst; ++cc) {
+                const int c = nch - 1 - cc;  // chunks back to front
+                const int base = c * CH;
+                const int n = end ? -1 : (nch == 0 ? 0 : min(CH, len - base));
+                if (n > 0 && !(pf.seq == seq && pf.c == c)) prefetch(seq, c, start, len, vview);
                 const int s = k % SS;
                 const uint32_t ps = (uint32_t)(k / SS) & 1u;
                 if (!mbar_wait_bounded(bar_empty(s), ps ^ 1u, tmo, sAbort)) {
@@ -540,9 +574,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
                     quit = true;
                     break;
                 }
-                const int c = nch - 1 - cc;  // chunks back to front
-                const int base = c * CH;
-                const int n = end ? -1 : (nch == 0 ? 0 : min(CH, len - base));
                 if (n > 0) {
                     // lanes 0..15: upper reference rows, 16..31: lower, for splat j = lane & 15
                     const int j = lane & 15;
@@ -550,20 +581,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
                     uint8_t* mB = sB1 + s * LY::B1_BYTES;
                     float vrow[6];
                     if (j < n) {
-                        const uint32_t g = a.ids[start + base + j];
-                        const float2 m = a.mean2d[g];
-                        const float A = a.conic[3 * g], B = a.conic[3 * g + 1], C = a.conic[3 * g + 2];
-                        const uint32_t og = g - (uint32_t)(vview * a.n_per_view);
-                        const float o = a.opac[og];
+                        const uint32_t g = pf.g, og = pf.og;
+                        const float A = pf.A, B = pf.B, C = pf.C, o = pf.o;
                         const float l2o = o > 0.f ? __log2f(o) : -INFINITY;
-                        const float xh = m.x - xc, yh = m.y - yc_up;
+                        const float xh = pf.m.x - xc, yh = pf.m.y - yc_up;
                         coeff_row<TR::HALF>(A, B, C, l2o, xh, upper ? yh : yh - 8.0f, bx0, bx1, by0, by1, vrow);
                         if (upper) {
                             const float cap = fminf(l2o, kLog2AlphaMax);
-                            const float cr = a.rgb[3 * g], cgc = a.rgb[3 * g + 1], cb = a.rgb[3 * g + 2];
                             Rec rc;
-                            rc.rg = make_float4(cr, cr, cgc, cgc);
-                            rc.bc = make_float4(cb, cb, cap, cap);
+                            rc.rg = make_float4(pf.cr, pf.cr, pf.cg, pf.cg);
+                            rc.bc = make_float4(pf.cb, pf.cb, cap, cap);
                             sRec[s * CH + j] = rc;
                             sFin[s * CH + j] = Fin{g, og, xh, yh, A, B, C, o > 0.f ? 1.0f / o : 0.f};
                         }
@@ -594,6 +621,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_tc_bwd(const __grid_const
                 if (lane == 0) mbar_arrive(bar_full(s));
                 ++k;
                 if (cc == 0 && !end) nxt = head(__shfl_sync(0xffffffffu, q_next, 0));  // the next tile's header
+                // the next chunk's splats: this tile's next chunk, or the next tile's first
+                if (!end) {
+                    if (cc + 1 < nst) {
+                        if (c - 1 >= 0) prefetch(seq, c - 1, start, len, vview);
+                    } else if (nxt.q < a.total_tiles && nxt.nch > 0) {
+                        prefetch(seq + 1, nxt.nch - 1, nxt.start, nxt.len, nxt.vview);
+                    }
+                }
             }
             if (end) quit = true;
         }
