@@ -286,6 +286,19 @@ def _events(torch, k):
     return [torch.cuda.Event(enable_timing=True) for _ in range(k)]
 
 
+def supertile_pairs(torch, gs, st):
+    """(Gaussian, supertile of 4 x 4 tiles) pairs of the step's lists: the
+    coarse duplication's output count, from the sorted ids and tile ranges."""
+    r = st.ranges.view(-1, 2).long()
+    lens = (r[:, 1] - r[:, 0]).clamp_min(0)
+    tiles = torch.repeat_interleave(torch.arange(lens.numel(), device=lens.device), lens)
+    tx = (st.W + 15) // 16
+    stx = (tx + 3) // 4
+    sup = (tiles // tx // 4) * stx + (tiles % tx) // 4
+    ids = st.ids[: int(lens.sum())].long()  # the lists are contiguous, in tile order
+    return int(torch.unique(sup * st.n + ids).numel())
+
+
 def _timed(torch, flush, stream, fn, reps):
     """Median ms of fn() over reps launches, L2 flushed before each."""
     ev = []
@@ -584,20 +597,58 @@ def run_ours(args):
     hbm = read_peaks().get("hbm_gbs")
     sort_bytes = 32 * n + 4 * n_inst + 8 * gs.num_tiles(W, H)
     stages = {"project": p_ms, "bin_sort": s_ms, "blend_forward": f_ms, "blend_backward": b_ms}
-    # the dominant kernel: the longer of the two blends (each stage one kernel, timed live); the
-    # bin/sort stage is nine kernels, none of which is longer than the backward in the ncu launch
-    # list of this step, and it is reported as a stage beside
-    r = rf if f_ms > b_ms else rb
-    b = r["terms_g_evals_per_s"][r["bound"]]
-    tr = KNOWN_TRAFFIC.get(r["kernel"] + "/" + args.variant)
-    roofline = {"bound": "alu" if r["bound"] in ("mufu", "fp32_issue") else r["bound"],
-                "kernel": f"k_blend_tc_bwd ({args.variant})" if r is rb else f"k_blend_tc ({args.variant})",
-                "achieved": r["achieved_g_evals_per_s"], "peak": b["per_s"], "unit": "G evals/s",
-                "frac": r["frac_of_bound"],
-                "traffic": tr["bytes"] if tr and tr["config"] == args.config and not args.resolution else None,
-                "launch_ms": r["launch_ms"], "terms": {k: v["per_s"] for k, v in r["terms_g_evals_per_s"].items()},
-                "peak_source": b["note"] + " (measured on this GPU); the min of the MUFU, FP32-issue, HBM and "
-                               "tensor terms"}
+    # the largest bin/sort kernel, the coarse duplication, timed live inside its stage: the stage
+    # captured again with events around that launch (gs_set_kernel_events), replayed after the
+    # projection with L2 flushed first, as in the step
+    e_dup = _events(torch, 2)
+    gs.set_kernel_events(gs.KERNEL_DUPLICATE, *e_dup)
+    try:
+        g_sort_t = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_sort_t, **mode):
+            st.sort(g_proj)
+    finally:
+        gs.set_kernel_events(gs.KERNEL_DUPLICATE, None, None)
+    dup_runs = []
+    for _ in range(min(max(K, 10), 50)):
+        flush.zero_()
+        graphs[0].replay()
+        g_sort_t.replay()
+        torch.cuda.synchronize()
+        dup_runs.append(e_dup[0].elapsed_time(e_dup[1]))
+    assert gs.gs_sync_status() == gs.GS_OK
+    dup_ms = statistics.median(dup_runs)
+    # its algorithmic bytes: per Gaussian the depth rank and inputs read (perm, mean2d, radius, conic,
+    # power_min: 32 bytes), per (Gaussian, supertile) pair the 8 bytes written
+    n_pairs = supertile_pairs(torch, gs, st)
+    dup_bytes = 32 * n + 8 * n_pairs
+
+    # the dominant kernel, by live duration: the backward or forward blend (each its stage's one
+    # kernel) or the coarse duplication; the bin/sort stage as a whole is reported beside
+    cand = {"blend_backward": b_ms, "blend_forward": f_ms, "dup": dup_ms}
+    dom = max(cand, key=cand.get)
+    if dom == "dup":
+        ach = dup_bytes / (dup_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": "k_dup_coarse (bin/sort's coarse duplication)",
+                    "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(ach / hbm, 4) if hbm else None, "traffic": None, "launch_ms": round(dup_ms, 5),
+                    "algorithmic_bytes": dup_bytes, "pairs": n_pairs,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, burst) of measured",
+                    "note": "bound by instruction issue and latency, not by HBM (ncu: issue 56% busy, 4 blocks "
+                            "per SM); algorithmic bytes: 32 per Gaussian read, 8 per supertile pair written"}
+    else:
+        r = rf if dom == "blend_forward" else rb
+        b = r["terms_g_evals_per_s"][r["bound"]]
+        tr = KNOWN_TRAFFIC.get(r["kernel"] + "/" + args.variant)
+        roofline = {"bound": "alu" if r["bound"] in ("mufu", "fp32_issue") else r["bound"],
+                    "kernel": f"k_blend_tc_bwd ({args.variant})" if r is rb else f"k_blend_tc ({args.variant})",
+                    "achieved": r["achieved_g_evals_per_s"], "peak": b["per_s"], "unit": "G evals/s",
+                    "frac": r["frac_of_bound"],
+                    "traffic": tr["bytes"] if tr and tr["config"] == args.config and not args.resolution else None,
+                    "launch_ms": r["launch_ms"],
+                    "terms": {k: v["per_s"] for k, v in r["terms_g_evals_per_s"].items()},
+                    "peak_source": b["note"] + " (measured on this GPU); the min of the MUFU, FP32-issue, HBM "
+                                   "and tensor terms"}
+    roofline["kernel_ms"] = {k: round(v, 5) for k, v in cand.items()}
     achieved = sort_bytes / (s_ms / 1e3) / 1e9
     stage_roofline = {"stage": "bin/sort (gs_alpha_power_min + gs_bin_sort_views + gs_tile_order, one CUDA graph)",
                       "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",

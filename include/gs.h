@@ -513,6 +513,21 @@ gs_status gs_tile_power(int32_t width, int32_t height, const uint32_t* tile_rang
  * devices, all host threads), for accounting of GPU work. */
 int64_t gs_launch_count(void);
 
+/*
+ * gs_set_kernel_events - timing of one kernel inside a library call (for
+ * profiling; the paper has no counterpart).  While set, every call that
+ * launches `kernel` records the CUDA event `start` (a cudaEvent_t) on its
+ * stream just before that launch and `end` just after it, as external event
+ * records, so the events also work inside a captured CUDA graph: the elapsed
+ * time between them is the kernel's duration.  kernel: GS_KERNEL_DUPLICATE,
+ * the coarse duplication of gs_bin_sort / gs_bin_sort_views /
+ * gs_bin_sort_noalloc.  start and end both NULL clear the setting; both must
+ * be events of the device the calls run on.  Process-wide: calls that run
+ * concurrently record into the same events.
+ */
+#define GS_KERNEL_DUPLICATE 1
+gs_status gs_set_kernel_events(int32_t kernel, void* start, void* end);
+
 /* Synchronise `stream`, then return and clear the device error word of the
  * current device: GS_ERR_TIMEOUT if a kernel's bounded wait gave up since the
  * last call, else GS_OK (or GS_ERR_CUDA if synchronising failed). */

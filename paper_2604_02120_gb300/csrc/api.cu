@@ -62,6 +62,18 @@ gs_status cuda_status(cudaError_t e, const char* what) {
 
 void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
+// gs_set_kernel_events: one (start, end) pair per timed kernel
+std::atomic<void*> g_kernel_events[2][2] = {};
+void set_kernel_events(int kernel, void* start, void* end) {
+    g_kernel_events[kernel][0].store(start, std::memory_order_relaxed);
+    g_kernel_events[kernel][1].store(end, std::memory_order_relaxed);
+}
+cudaError_t record_kernel_event(int kernel, bool end, cudaStream_t s) {
+    void* ev = g_kernel_events[kernel][end ? 1 : 0].load(std::memory_order_relaxed);
+    if (ev == nullptr) return cudaSuccess;
+    return cudaEventRecordWithFlags(static_cast<cudaEvent_t>(ev), s, cudaEventRecordExternal);
+}
+
 unsigned* error_word() {
     static std::atomic<unsigned*> addr[64] = {};  // per device; threads may look it up at once
     int dev = 0;
@@ -154,6 +166,16 @@ extern "C" {
 int32_t gs_version(void) { return 100; }
 
 int64_t gs_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+gs_status gs_set_kernel_events(int32_t kernel, void* start, void* end) {
+    g_last_error[0] = 0;
+    if (kernel != GS_KERNEL_DUPLICATE || (start == nullptr) != (end == nullptr)) {
+        set_error("gs_set_kernel_events: kernel must be GS_KERNEL_DUPLICATE and the events both set or both NULL");
+        return GS_ERR_INVALID_ARG;
+    }
+    gs::set_kernel_events(kernel, start, end);
+    return GS_OK;
+}
 
 const char* gs_status_string(gs_status s) {
     switch (s) {

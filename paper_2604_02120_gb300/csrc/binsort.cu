@@ -1327,11 +1327,15 @@ gs_status bin_sort_run(const SortViews& sv, const float* mean2d_f, const int* ra
     const int nst = sv2.total_st;
     uint32_t* st_count = nst <= n ? dk[0] : nullptr;
     uint32_t* st_order = nst <= n ? dk[1] : nullptr;
+    if ((e = record_kernel_event(GS_KERNEL_DUPLICATE, false, s)) != cudaSuccess)
+        return cuda_status(e, "gs_bin_sort: kernel event");
     dup<<<(int)cdiv(n, kDupTile), kThreads, 0, s>>>(n, perm, sv2, mean2d, radius, (uint64_t)capacity, st_passes,
                                                     pack, tickets, dup_status, ck[0], cv[0], hist + 256 * 4, ctotal,
                                                     fine_total, status, coarse_tile, st_count, nst, err);
     count_launches();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "gs_bin_sort: duplicate");
+    if ((e = record_kernel_event(GS_KERNEL_DUPLICATE, true, s)) != cudaSuccess)
+        return cuda_status(e, "gs_bin_sort: kernel event");
 
     // synchronising mode: the instance and pair counts, before any further work
     uint32_t I_grid = 0;  // pairs the later kernels are sized for

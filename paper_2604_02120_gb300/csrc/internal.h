@@ -133,6 +133,10 @@ gs_status cuda_status(cudaError_t e, const char* what);
 unsigned* error_word();
 // Count `k` kernel launches (gs_launch_count).
 void count_launches(int k = 1);
+// gs_set_kernel_events: store the pair, and record the start (end = false) or end
+// event of `kernel` on `s` as an external record when set.
+void set_kernel_events(int kernel, void* start, void* end);
+cudaError_t record_kernel_event(int kernel, bool end, cudaStream_t s);
 
 struct CamViews {
     int num_views;

@@ -34,6 +34,7 @@ ABI_FUNCTIONS = (
     "gs_project_views", "gs_bin_sort_views", "gs_blend_forward_views", "gs_blend_backward_views",
     "gs_blend_autotune", "gs_measure_peaks", "gs_alpha_power_min", "gs_project_backward",
     "gs_project_bin_small", "gs_tile_order", "gs_pack_splats", "gs_blend_autotune_backward", "gs_render_small",
+    "gs_set_kernel_events",
 )
 
 
@@ -97,6 +98,7 @@ def load(path: str = LIB_PATH):
     lib.gs_tile_order.argtypes = [i32, i32p, i32p, vp, vp, vp]
     lib.gs_project_bin_small.argtypes = [i32, vp, vp, vp, vp, i32, ctypes.POINTER(gs_camera), vp, i32, vp, vp, vp,
                                          vp, vp, vp, vp, vp, vp]
+    lib.gs_set_kernel_events.argtypes = [i32, vp, vp]
     lib.gs_render_small.argtypes = [i32, vp, vp, vp, vp, i32, ctypes.POINTER(gs_camera), vp, i32, vp,
                                     ctypes.POINTER(ctypes.c_float), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gs_project_backward.argtypes = [i32, vp, vp, vp, vp, i32, ctypes.POINTER(gs_camera), i32, vp, vp, vp, vp,
@@ -290,6 +292,20 @@ def gs_render_small(n, means, scales, quats, sh, sh_degree, cam, power_min, max_
 
 
 SMALL_MAX_PER_TILE = 16384
+KERNEL_DUPLICATE = 1
+
+
+def set_kernel_events(kernel, start=None, end=None):
+    """gs_set_kernel_events: record the torch.cuda.Events start and end around
+    every launch of `kernel` (KERNEL_DUPLICATE) until cleared with None."""
+    def handle(e):
+        if e is None:
+            return None
+        if not e.cuda_event:  # torch creates the CUDA event on its first record
+            e.record()
+            e.synchronize()
+        return ctypes.c_void_p(e.cuda_event)
+    _check(load().gs_set_kernel_events(int(kernel), handle(start), handle(end)), "gs_set_kernel_events")
 
 
 def gs_tile_order(widths, heights, tile_ranges, order, stream=None):

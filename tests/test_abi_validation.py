@@ -91,6 +91,12 @@ def test_render_small_checks(lib):
             INVALID, "gs_render_small")
 
 
+def test_set_kernel_events_checks(lib):
+    _expect(lib, lib.gs_set_kernel_events(0, None, None), INVALID, "gs_set_kernel_events")
+    _expect(lib, lib.gs_set_kernel_events(gs.KERNEL_DUPLICATE, P, None), INVALID, "gs_set_kernel_events")
+    assert lib.gs_set_kernel_events(gs.KERNEL_DUPLICATE, None, None) == gs.GS_OK
+
+
 def test_bin_sort_checks(lib):
     w, h = _sizes(64), _sizes(48)
     cnt = ctypes.c_int64(0)
