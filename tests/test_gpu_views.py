@@ -91,6 +91,30 @@ def test_graph_mode_bin_sort_matches_synchronising_mode_and_reports_overflow():
     assert gs.gs_sync_status() == gs.GS_OK
 
 
+def test_graph_mode_capacity_over_2_28_gives_the_same_lists():
+    """In graph mode the pair sort's grids and status words are sized by the
+    capacity: with a capacity above 2^28 (and most pair-sort tiles empty) the
+    lists equal those of a tight capacity, also on a reused workspace."""
+    sc = _ring_scene()
+    dev = gs.scene_to_device(sc)
+    br = gs.BatchRenderer(dev, sc.cameras, gs.make_opts("fp32"), capacity=1 << 17)
+    br.forward()
+    count = int(br.count.item())
+    big = (1 << 28) + 4096
+    ws = torch.empty(gs.gs_bin_sort_workspace_size(br.V * br.n, big, 64, 64) + 256, device="cuda", dtype=torch.uint8)
+    ids = torch.empty(big, device="cuda", dtype=torch.int32)
+    ranges = torch.empty_like(br.ranges)
+    cdev = torch.zeros(1, device="cuda", dtype=torch.int64)
+    for _ in range(2):  # the second call finds the first one's status words in the workspace
+        ranges.fill_(-1)
+        gs.gs_bin_sort_views(br.V, br.n, br.mean2d, br.radius, br.depth, br.widths, br.heights, big, ws, None, ids,
+                             ranges, count_dev=cdev)
+        assert gs.gs_sync_status() == gs.GS_OK
+        assert int(cdev.item()) == count > 0
+        torch.testing.assert_close(ranges, br.ranges, rtol=0, atol=0)
+        torch.testing.assert_close(ids[:count], br.ids[:count], rtol=0, atol=0)
+
+
 @pytest.mark.parametrize("variant", ["fp32", "fp16_split"])
 def test_batched_backward_equals_sum_over_views(variant):
     sc = _ring_scene(n=300)
