@@ -517,9 +517,11 @@ int64_t gs_launch_count(void);
  * gs_set_kernel_events - timing of one kernel inside a library call (for
  * profiling; the paper has no counterpart).  While set, every call that
  * launches `kernel` records the CUDA event `start` (a cudaEvent_t) on its
- * stream just before that launch and `end` just after it, as external event
- * records, so the events also work inside a captured CUDA graph: the elapsed
- * time between them is the kernel's duration.  kernel: GS_KERNEL_DUPLICATE,
+ * stream just before that launch and `end` just after it (during a stream
+ * capture as external event records, so that every replay of the graph
+ * records them): the elapsed time between them is the kernel's duration.
+ * An error of the record (e.g. an event of another device) fails the call
+ * with GS_ERR_CUDA.  kernel: GS_KERNEL_DUPLICATE,
  * the coarse duplication of gs_bin_sort / gs_bin_sort_views /
  * gs_bin_sort_noalloc.  start and end both NULL clear the setting; both must
  * be events of the device the calls run on.  Process-wide: calls that run

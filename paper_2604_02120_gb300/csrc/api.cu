@@ -71,7 +71,14 @@ void set_kernel_events(int kernel, void* start, void* end) {
 cudaError_t record_kernel_event(int kernel, bool end, cudaStream_t s) {
     void* ev = g_kernel_events[kernel][end ? 1 : 0].load(std::memory_order_relaxed);
     if (ev == nullptr) return cudaSuccess;
-    return cudaEventRecordWithFlags(static_cast<cudaEvent_t>(ev), s, cudaEventRecordExternal);
+    // inside a stream capture the record becomes an external event node of the
+    // graph (recorded at every replay); outside one it is a plain record
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    return cs == cudaStreamCaptureStatusActive
+               ? cudaEventRecordWithFlags(static_cast<cudaEvent_t>(ev), s, cudaEventRecordExternal)
+               : cudaEventRecord(static_cast<cudaEvent_t>(ev), s);
 }
 
 unsigned* error_word() {
