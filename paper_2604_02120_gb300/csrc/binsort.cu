@@ -234,7 +234,9 @@ __device__ __forceinline__ uint32_t pass_count(uint32_t n_host, const uint64_t* 
 // [w * 32 ITEMS, (w + 1) * 32 ITEMS) walked in rounds of 32, so lane order is
 // input order, and each item's rank among equal digits comes from the lanes
 // with the same digit (digit_peers; FULL: ballots, for digits of more than
-// 4 significant bits).  Items are placed in shared memory in digit order, then
+// 4 significant bits).  The ranking runs once: it keeps each item's rank among
+// its warp's items of the same digit, so placing an item needs only its warp's
+// start of the digit.  Items are placed in shared memory in digit order, then
 // written so that consecutive threads write consecutive addresses of each
 // digit's run.  hist holds the pass's global digit counts.
 template <int ITEMS, bool FULL>
@@ -265,21 +267,31 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint32_t* __rest
         if (bbase >= n) return;  // uniform over the block; no later tile is needed either
         const int cnt = (int)((int64_t)n - bbase < TILE ? (int64_t)n - bbase : TILE);
         const int wbase = warp * (ITEMS * 32);
-        uint32_t k[ITEMS], v[ITEMS];
+        uint32_t k[ITEMS];
 #pragma unroll
         for (int r = 0; r < ITEMS; ++r) {
             const int i = wbase + r * 32 + lane;
             k[r] = i < cnt ? kin[bbase + i] : 0u;
-            v[r] = i < cnt ? vin[bbase + i] : 0u;
         }
         const unsigned lt = (1u << lane) - 1u;
+        // each item's rank among the warp's items with its digit (input order),
+        // 16 bits per item: the warp's running count before this round plus the
+        // lower lanes of the round with the same digit
+        uint32_t rank[(ITEMS + 1) / 2];
 #pragma unroll
         for (int r = 0; r < ITEMS; ++r) {
             const bool valid = wbase + r * 32 + lane < cnt;
             const uint32_t d = (k[r] >> shift) & 0xFFu;
             const unsigned peers = digit_peers<FULL>(d, valid);
-            if (valid && (peers & lt) == 0) s_w[warp][d] += __popc(peers);
+            const uint32_t before = valid ? s_w[warp][d] : 0u;
             __syncwarp();
+            if (valid && (peers & lt) == 0) s_w[warp][d] = before + __popc(peers);
+            __syncwarp();
+            const uint32_t rk = before + __popc(peers & lt);
+            if (r & 1)
+                rank[r >> 1] |= rk << 16;
+            else
+                rank[r >> 1] = rk;
         }
         __syncthreads();
         {
@@ -308,21 +320,23 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint32_t* __rest
                 run += cw;
             }
         }
-        __syncthreads();
+        // the values are needed only from here on (fewer registers live across the look-back)
+        uint32_t v[ITEMS];
 #pragma unroll
         for (int r = 0; r < ITEMS; ++r) {
-            const bool valid = wbase + r * 32 + lane < cnt;
-            const uint32_t d = (k[r] >> shift) & 0xFFu;
-            const unsigned peers = digit_peers<FULL>(d, valid);
-            uint32_t pos = 0;
-            if (valid) pos = s_w[warp][d] + __popc(peers & lt);
-            __syncwarp();
-            if (valid) {
+            const int i = wbase + r * 32 + lane;
+            v[r] = i < cnt ? vin[bbase + i] : 0u;
+        }
+        __syncthreads();
+        // s_w[w][d] now holds warp w's block-local start of digit d
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r) {
+            if (wbase + r * 32 + lane < cnt) {
+                const uint32_t d = (k[r] >> shift) & 0xFFu;
+                const uint32_t pos = s_w[warp][d] + ((rank[r >> 1] >> (16 * (r & 1))) & 0xFFFFu);
                 s_key[pos] = k[r];
                 s_val[pos] = v[r];
-                if ((peers & lt) == 0) s_w[warp][d] += __popc(peers);
             }
-            __syncwarp();
         }
         __syncthreads();
         for (int i = threadIdx.x; i < cnt; i += kThreads) {
